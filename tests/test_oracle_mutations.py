@@ -1,0 +1,122 @@
+"""The oracle pins have teeth: each plausible mistake planted in a copy of the
+oracle source (a flipped sign, a dropped term, a transposed operand, a wrong
+index or factor) makes at least one pin fail.  Runs on the CPU only."""
+import importlib.util
+import math
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+from paper_2007_04881_gb300 import meshgen as mg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "dg_oracle.c")
+
+MUTATIONS = {
+    "upwind_offdiag_sign": (
+        "if (c == 1) t += bn * phi[1][j] * phi[0][i];",
+        "if (c == 1) t -= bn * phi[1][j] * phi[0][i];",
+    ),
+    "dropped_symmetry_term": (
+        "t -= avg * aa[r] * dn[r][i] * sgn[c] * phi[c][j]; /* {a grad v}.[w] */",
+        "/* dropped */",
+    ),
+    "transposed_advection": (
+        "bg += pb->b[d] * grad[j * dim + d];",
+        "bg += pb->b[d] * grad[i * dim + d];",
+    ),
+    "legendre_derivative_index": (
+        "dP[k + 1] = dP[k - 1] + (2.0 * k + 1.0) * P[k];",
+        "dP[k + 1] = dP[k - 1] + (2.0 * k - 1.0) * P[k];",
+    ),
+    "nitsche_rhs_sign": (
+        "double t = -g * (a[e] * dn - sig * phi[i]);",
+        "double t = -g * (a[e] * dn + sig * phi[i]);",
+    ),
+    "collapsed_weight_factor": (
+        "w[q] = gw[ia] * gw[ib] * (1.0 - b);",
+        "w[q] = gw[ia] * gw[ib];",
+    ),
+    "penalty_min_instead_of_max": (
+        "if (v > s) s = v;",
+        "if (s == 0.0 || v < s) s = v;",
+    ),
+    "average_weight_on_boundary": (
+        "double avg = bnd ? 1.0 : 0.5;",
+        "double avg = 0.5;",
+    ),
+}
+
+
+def _load_variant(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert old in src, f"mutation anchor missing: {name}"
+    d = tmp_path / name
+    (d / "_build").mkdir(parents=True)
+    (d / "dg_oracle.c").write_text(src.replace(old, new, 1))
+    shutil.copy(os.path.join(ROOT, "oracle", "__init__.py"), d / "__init__.py")
+    spec = importlib.util.spec_from_file_location(f"oracle_mut_{name}", d / "__init__.py")
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _pins_pass(O) -> bool:
+    """A compact subset of the pins; True when all of them hold."""
+    try:
+        # polygon moments vs divergence theorem
+        mesh = mg.voronoi_square(30, 3)
+        om = O.Mesh(mesh)
+        for e in range(0, om.ne, 5):
+            v = mesh.elem_v[mesh.elem_vptr[e]:mesh.elem_vptr[e + 1]]
+            for i, j in [(0, 0), (2, 1), (3, 3)]:
+                if abs(om.moment_rule(e, 4, i, j) - O.moment_divergence2d(mesh.x[v], mesh.y[v], i, j)) > 1e-13:
+                    return False
+        # rectangle mass / stiffness closed forms
+        rm = O.Mesh(mg.rectangle_grid(1, 1, 0.0, 0.5, 0.0, 2.0))
+        M = rm.volume_block(0, np.array([3]), np.array([0.0]), O.make_problem(2, c=1.0))
+        if np.abs(M - np.eye(10)).max() > 1e-13:
+            return False
+        K = rm.volume_block(0, np.array([2]), np.array([1.0]), O.make_problem(2))
+        # phi = sqrt(3/(Lx Ly)) P_1(xi): d/dx = sqrt(3/(Lx Ly)) 2/Lx; int = 3/(Lx Ly) 4/Lx^2 Lx Ly
+        if abs(K[1, 1] - 3.0 * 4.0 / 0.25) > 1e-12 * 48:
+            return False
+        # penalty on a two-square mesh: 10 * max(a p^2 / h)
+        two = O.Mesh(mg.rectangle_grid(2, 1, 0.0, 2.0, 0.0, 1.0))
+        kint = [k for k in range(two.nf) if two.face_info(k)[1] >= 0][0]
+        if abs(two.face_penalty(kint, np.array([1, 2]), np.array([1.0, 1.0]), 10.0) - 40 / math.sqrt(2)) > 1e-12:
+            return False
+        # polynomial reproduction with advection and reaction, mixed degrees
+        om = O.Mesh(mg.voronoi_square(24, 7))
+        p = mg.draw_degrees(om.ne, 7, 2, 3).astype(np.int32)
+        a = np.full(om.ne, 0.6)
+        pb = O.make_problem(2, b=(0.9, -0.5), c=0.7, source=2, poly=[1, 0.5, -1, 0.3, 0.2, -0.4])
+        blk = om.assemble(p, a, pb)
+        A, F, off = O.global_matrix(om, p, blk)
+        U = np.linalg.solve(A, F)
+        for e in range(om.ne):
+            xq, _ = om.volume_points(e, 3)
+            for x in xq[::7]:
+                phi, _ = O.basis(2, int(p[e]), om.lo[e], om.hi[e], x)
+                if abs(phi @ U[off[e]:off[e + 1]] - O.exact_u(pb, x)) > 1e-9:
+                    return False
+        return True
+    except Exception:
+        return False
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+def test_unmutated_copy_passes(tmp_path):
+    O = _load_variant(tmp_path, "none", "#define ORC_PI", "#define ORC_PI")
+    assert _pins_pass(O)
+
+
+@pytest.mark.skipif(shutil.which("gcc") is None, reason="needs gcc")
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_mutation_is_caught(tmp_path, name):
+    old, new = MUTATIONS[name]
+    O = _load_variant(tmp_path, name, old, new)
+    assert not _pins_pass(O), f"planted mistake '{name}' passed every pin"
