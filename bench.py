@@ -1,0 +1,460 @@
+#!/usr/bin/env python
+"""Benchmark: SIPG dG assembly throughput on GB300.
+
+One step = one pass of the whole hot path on device-resident inputs
+(dg_assemble_step): geometry kernels, then the element kernels (volume +
+own faces + load vector) and the interface kernels, writing every block of
+the BSR matrix and the load vector.
+
+Default workload: 2D advection-diffusion-reaction on 65,536 Voronoi cells,
+p ~ U{1..4}, a = 10^U(-2,2), b = (1, 0.5), c = 1 (seeded, synthetic).
+Headline form: FP32 contractions with FP64 geometry; the FP64 form is timed
+in the same run and the FP32 matrix error against it is reported.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 launch under torch.distributed.run; every rank assembles its own
+replica of the workload (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
+METRIC = "dG assembly elements/s & matrix GB/s vs roofline; reduced vs FP64 form at fixed err"
+WORKLOAD = ("adr2d_65k: 2D advection-diffusion-reaction, 65,536 clipped Voronoi cells (5 Lloyd steps), "
+            "p~U{1..4}, a=10^U(-2,2), b=(1,0.5), c=1, sin-product source, penalty 10 p^2/h")
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_alu_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
+    # 128 FP32 FMA lanes per SM, 2 flops per FMA
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+FP64_PEAK_TFLOPS = 1.25  # GB300 FP64 (nominal, profiling recipe)
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"dg_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if sm:
+            out.update(sm_mhz=statistics.median(sm), sm_max_mhz=max(smax), reasons=sorted(reasons), samples=len(sm))
+        return out
+
+
+def dist_setup(use_cuda: bool):
+    import torch
+
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        if use_cuda:
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if use_cuda else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload_config(wl, info):
+    return {
+        "workload": WORKLOAD,
+        "elements": int(info.ne),
+        "interfaces": int(info.ninterfaces),
+        "boundary_faces": int(info.nbfaces),
+        "sub_triangles": int(info.nsub),
+        "quad_points_volume": int(info.nqvol),
+        "quad_points_face": int(info.nqface),
+        "bsr_blocks": int(info.nnzb),
+        "matrix_entries": int(info.nvals),
+        "dofs": int(info.ndofs),
+        "l2": "flushed between timed steps (256 MiB write, outside the timed region)",
+    }
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 CPU oracle on a bounded sample per step
+# ---------------------------------------------------------------------------
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+    from paper_2007_04881_gb300 import configs
+
+    wl = configs.adr2d()
+    om = O.Mesh(wl.mesh)
+    pb = O.make_problem(2, **wl.problem)
+    p = wl.p.astype(np.int32)
+    cores = os.cpu_count() or 1
+    # per step: a contiguous sample of elements and the same share of interfaces
+    per_step = args.ref_sample
+    rng = np.random.default_rng(7)
+    times = []
+    tot = 0
+    for it in range(args.warmup + args.steps):
+        e0 = int(rng.integers(0, wl.ne - per_step))
+        el = np.arange(e0, e0 + per_step, dtype=np.int32)
+        i0 = int(round(e0 * om.ni / wl.ne))
+        ni = int(round(per_step * om.ni / wl.ne))
+        ifs = np.arange(i0, min(i0 + ni, om.ni), dtype=np.int32)
+        t = time.perf_counter()
+        om.assemble(p, wl.a, pb, elems=el, ifaces=ifs, nthreads=cores)
+        dt = time.perf_counter() - t
+        if it >= args.warmup:
+            times.append(dt)
+            tot += per_step
+    T = sum(times)
+    value = tot / T
+    sample = (f"{per_step} consecutive elements (diagonal blocks + load vector) and the proportional "
+              f"{int(round(per_step * om.ni / wl.ne))} interfaces (off-diagonal block pairs) per step, "
+              f"FP64, OpenMP over {cores} threads")
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "elements/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * T / max(1, len(times)),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "elements": int(wl.ne), "interfaces": int(om.ni),
+                   "boundary_faces": int(om.nbf), "sample_per_step": per_step},
+        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def cpu_baseline_sample(wl, seconds_target=12.0):
+    """The oracle as it stands, on a bounded sample of the workload, timed on
+    the host cores (rank 0, N=1 only)."""
+    import oracle as O
+
+    cores = os.cpu_count() or 1
+    om = O.Mesh(wl.mesh)
+    pb = O.make_problem(2, **wl.problem)
+    p = wl.p.astype(np.int32)
+    n = 2048
+    el = np.arange(n, dtype=np.int32)
+    ifs = np.arange(int(round(n * om.ni / wl.ne)), dtype=np.int32)
+    t = time.perf_counter()
+    om.assemble(p, wl.a, pb, elems=el, ifaces=ifs, nthreads=cores)
+    dt = time.perf_counter() - t
+    # grow the sample to ~seconds_target of CPU work (bounded by the mesh)
+    n2 = int(min(wl.ne, max(n, n * seconds_target / max(dt, 1e-3))))
+    el = np.arange(n2, dtype=np.int32)
+    ifs = np.arange(int(round(n2 * om.ni / wl.ne)), dtype=np.int32)
+    t = time.perf_counter()
+    om.assemble(p, wl.a, pb, elems=el, ifaces=ifs, nthreads=cores)
+    dt = time.perf_counter() - t
+    return {
+        "value": n2 / dt,
+        "unit": "elements/s",
+        "cores": cores,
+        "kind": "oracle",
+        "sample": f"first {n2} of {wl.ne} elements (diagonal blocks + load vector) and {ifs.size} of {om.ni} "
+                  f"interfaces, FP64, {dt:.1f} s on {cores} threads",
+    }
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+
+def time_steps(torch, stream, step, flush, steps, ctx=None):
+    """Per-step CUDA-event times (ms); L2 flushed between steps, untimed.
+    With ctx, also collects the library's per-launch timings."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    stats = {}
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+        if ctx is not None:
+            for name, ms, fl, by in ctx.dg_kernel_stats():
+                s = stats.setdefault(name, [0.0, 0, fl, by])
+                s[0] += ms
+                s[1] += 1
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ev], stats
+
+
+def run_ours(args):
+    import torch
+
+    from paper_2007_04881_gb300 import build as B
+    from paper_2007_04881_gb300 import configs, dg
+
+    ws, rank, local = dist_setup(True)
+    dev = local if ws > 1 else 0
+    torch.cuda.set_device(dev)
+    B.build()
+    wl = configs.adr2d()
+    stream = torch.cuda.current_stream()
+    ctx = dg.Context(dev, stream.cuda_stream)
+    t0 = time.perf_counter()
+    mesh = dg.Mesh(ctx, wl.mesh, wl.p, wl.a, dg.Problem(**wl.problem))
+    upload_ms = 1e3 * (time.perf_counter() - t0)
+    info = mesh.info
+    t0 = time.perf_counter()
+    dg.dg_mesh_check(wl.mesh, wl.p, wl.a, dg.Problem(**wl.problem))
+    pattern_ms = 1e3 * (time.perf_counter() - t0)
+
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    prec = dg.DG_PREC_FP32
+    v32 = torch.empty(mesh.nvals, dtype=torch.float32, device="cuda")
+    r32 = torch.empty(mesh.ndofs, dtype=torch.float32, device="cuda")
+    v64 = torch.empty(mesh.nvals, dtype=torch.float64, device="cuda")
+    r64 = torch.empty(mesh.ndofs, dtype=torch.float64, device="cuda")
+
+    def step32():
+        mesh.dg_assemble_step(dg.DG_PREC_FP32, v32, r32)
+
+    def step64():
+        mesh.dg_assemble_step(dg.DG_PREC_FP64, v64, r64)
+
+    for _ in range(args.warmup):
+        step32()
+    torch.cuda.synchronize()
+    launches_per_step = ctx.launches()
+
+    # ---- timed region (FP32 form, headline)
+    sampler = ClockSampler(dev)
+    barrier(ws)
+    torch.cuda.synchronize()
+    sampler.start()
+    ctx.dg_set_timing(True)
+    t_wall = time.perf_counter()
+    times, kstats = time_steps(torch, stream, step32, flush, args.steps, ctx)
+    t_wall = time.perf_counter() - t_wall
+    ctx.dg_set_timing(False)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    ms_step = max_over_ranks(sum(times) / len(times), ws)
+    value = ws * info.ne / (ms_step * 1e-3)
+
+    # ---- FP64 form (same workload), for the reduced-vs-FP64 comparison
+    for _ in range(max(1, args.warmup // 2)):
+        step64()
+    torch.cuda.synchronize()
+    k64 = max(3, args.steps // 10)
+    ctx.dg_set_timing(True)
+    t64, kstats64 = time_steps(torch, stream, step64, flush, k64, ctx)
+    ctx.dg_set_timing(False)
+    ms64 = max_over_ranks(sum(t64) / len(t64), ws)
+    # error of the reduced form against the FP64 form (same device inputs)
+    step32()
+    step64()
+    torch.cuda.synchronize()
+    d = (v32.double() - v64)
+    err_fro = float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(v64))
+    err_max = float(d.abs().max() / v64.abs().max())
+    err_rhs = float(torch.linalg.vector_norm(r32.double() - r64) / torch.linalg.vector_norm(r64))
+
+    # ---- end to end through the host-memory entry point
+    pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).pin_memory()  # noqa: E731
+    hx, hy, ha = pin(wl.mesh.x, np.float64), pin(wl.mesh.y, np.float64), pin(wl.a, np.float64)
+    hv = torch.empty(mesh.nvals, dtype=torch.float32).pin_memory()
+    hr = torch.empty(mesh.ndofs, dtype=torch.float32).pin_memory()
+    e2e_steps = max(3, min(args.steps, 50))
+    for _ in range(2):
+        mesh.dg_assemble_host(prec, hv, hr, x=hx, y=hy, a=ha)
+    barrier(ws)
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        mesh.dg_assemble_host(prec, hv, hr, x=hx, y=hy, a=ha)
+    e2e_s = max_over_ranks((time.perf_counter() - t) / e2e_steps, ws)
+    h2d = (hx.numel() + hy.numel() + ha.numel()) * 8
+    d2h = hv.numel() * 4 + hr.numel() * 4
+
+    if rank != 0:
+        return 0
+
+    # ---- roofline of the dominant kernel
+    peaks, peak_src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = fp32_alu_peak_tflops(sm_max)
+    dom = max(kstats.items(), key=lambda kv: kv[1][0])
+    name, (tot_ms, cnt, fl, by) = dom
+    avg_ms = tot_ms / cnt
+    achieved = fl / (avg_ms * 1e-3) / 1e12
+    step_flops = sum(s[2] for s in kstats.values())
+    step_bytes = sum(s[3] for s in kstats.values())
+    kern = {k: {"avg_ms": v[0] / v[1], "launches": v[1], "tflops": v[2] / (v[0] / v[1] * 1e-3) / 1e12,
+                "gbs": v[3] / (v[0] / v[1] * 1e-3) / 1e9} for k, v in sorted(kstats.items())}
+    dom64 = max(kstats64.items(), key=lambda kv: kv[1][0])
+    n64, (tm64, c64, fl64, _) = dom64
+    ach64 = fl64 / (tm64 / c64 * 1e-3) / 1e12
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        try:
+            tj = json.load(open(tfile))
+            traffic = tj.get(name)
+        except Exception:
+            traffic = None
+
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "elements/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": workload_config(wl, info),
+        "matrix_gbs": (info.nvals + info.ndofs) * 4 / (ms_step * 1e-3) / 1e9,
+        "roofline": {
+            "bound": "alu",
+            "kernel": name,
+            "achieved": achieved,
+            "peak": alu_peak,
+            "unit": "TFLOP/s",
+            "frac": achieved / alu_peak,
+            "traffic": traffic,
+            "peak_note": f"FP32 FMA peak = 152 SMs x 128 lanes x 2 flops x {sm_max:.0f} MHz (sm_max from "
+                         f"MEASURED_PEAKS.json, {peak_src})",
+        },
+        "step_algorithmic": {"tflops": step_flops / (ms_step * 1e-3) / 1e12,
+                             "gbs": step_bytes / (ms_step * 1e-3) / 1e9},
+        "kernels": kern,
+        "fp64_form": {
+            "value": ws * info.ne / (ms64 * 1e-3),
+            "ms_per_step": ms64,
+            "steps": k64,
+            "speedup_fp32_over_fp64": ms64 / ms_step,
+            "roofline": {"bound": "alu", "kernel": n64, "achieved": ach64, "peak": FP64_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS},
+        },
+        "reduced_vs_fp64_error": {"matrix_rel_fro": err_fro, "matrix_rel_max": err_max, "rhs_rel_fro": err_rhs},
+        "upload_ms": upload_ms,
+        "pattern_ms": pattern_ms,
+        "e2e": {"value": ws * info.ne / e2e_s, "unit": "elements/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "timed_wall_s": t_wall,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(wl)
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ref-sample", type=int, default=512, help="oracle elements per reference step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,218 @@
+/*
+ * dg.h -- C ABI of libdg: GPU assembly of the symmetric interior-penalty
+ * discontinuous Galerkin (SIPG) matrix and load vector for linear
+ * diffusion-advection-reaction problems on polygonal (2D) and polyhedral (3D)
+ * meshes, after Dong, Georgoulis & Kappas, "GPU-accelerated discontinuous
+ * Galerkin methods on polytopic meshes" (arXiv 2007.04881).
+ *
+ * Problem (Sec. 2.1, Eq. (2.1)):  -div(a grad u) + b . grad u + c u = f,
+ * with a > 0 piecewise constant per element (A = a I), b and c constant, and
+ * u = g_D on the whole boundary (a > 0 makes every boundary point part of
+ * the Dirichlet boundary, Sec. 2.1).
+ * Discretisation (Sec. 2.2): B(u_h, v) = l(v) with the bilinear form of
+ * Eq. (2.4) and the load functional of Eq. (2.5); the local space on element
+ * k is P_{p_k}, spanned by tensorised orthonormal Legendre polynomials of
+ * total degree p_k on the element's bounding box (Sec. 3.1).
+ * Quadrature (Sec. 3 intro, Sec. 3.1): each element is split into simplices
+ * (2D: triangles (centroid, v_i, v_{i+1}) of the CCW vertex loop; 3D: the
+ * element's tetrahedra) carrying collapsed Gauss-Legendre rules with p+2
+ * points per direction; faces carry Gauss rules with max(p_1, p_2) + 1 points
+ * per direction (2D edges; 3D triangles, collapsed).
+ * Penalty (Appendix A, simplified): sigma_F = C_sigma * max over the face's
+ * elements of a_k p_k^2 / h_k, h_k the element diameter.
+ *
+ * Output: a variable-block BSR matrix.  Block row r = element r; the columns
+ * of row r are r and every element sharing a face with r, ascending.  Block
+ * (r, c) is n_r x n_c, row-major (row = test function of r, column = trial
+ * function of c), n_k = C(p_k + d, d).  One block per element pair, however
+ * many faces the two elements share (the unique-index idea of Sec. 3.4).
+ * Entries are written without atomics in a fixed order, so results are
+ * bitwise reproducible.
+ *
+ * Conventions for every entry point:
+ *   - returns DG_OK (0) or a negative DG_ERR_* code; dg_last_error() gives a
+ *     message (thread-local).  No C++ exception crosses this ABI.
+ *   - "device" pointers are CUDA device memory on the context's device,
+ *     allocated and owned by the caller; "host" pointers are CPU memory.
+ *   - assembly calls are asynchronous on the context's stream; results are
+ *     valid once the stream (or dg_sync) completes.
+ */
+#ifndef DG_H
+#define DG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DG_OK 0
+#define DG_ERR_ARG (-1)     /* invalid argument (null pointer, bad size/flag) */
+#define DG_ERR_MESH (-2)    /* invalid mesh (non-manifold, bad orientation, zero area, p range) */
+#define DG_ERR_CUDA (-3)    /* a CUDA runtime call failed */
+#define DG_ERR_OOM (-4)     /* device or host allocation failed */
+#define DG_ERR_ORDER (-5)   /* dg_assemble_faces called before dg_assemble_volume */
+#define DG_ERR_TIMEOUT (-6) /* a bounded device-side wait ran out */
+
+/* precision flags (prec argument) */
+#define DG_PREC_FP64 0 /* everything in FP64; vals are double */
+#define DG_PREC_FP32 1 /* geometry (maps, Jacobians, normals, penalty) in FP64,
+                          basis evaluation and contractions in FP32; vals are float */
+
+/* source / boundary data */
+#define DG_SRC_ZERO 0    /* f = 0, g_D = 0 */
+#define DG_SRC_SINPROD 1 /* u = prod_d sin(pi x_d): f = a d pi^2 u + b.grad u + c u, g_D = u */
+#define DG_SRC_POLY 2    /* u = sum_k poly[k] m_k(x), graded monomials of degree <= 3
+                            (2D: 1,x,y,x^2,xy,y^2,x^3,x^2y,xy^2,y^3; 3D: the 20 monomials
+                            ordered as: degree k, then z-power l, then y-power j);
+                            f = -a Lap u + b.grad u + c u, g_D = u */
+
+#define DG_PMAX_2D 6
+#define DG_PMAX_3D 4
+
+typedef struct dg_ctx dg_ctx;
+typedef struct dg_mesh dg_mesh;
+
+/* Mesh description.  All pointers are HOST memory and are copied by
+ * dg_mesh_upload; the caller keeps ownership.
+ *   2D: elem_ptr[ne+1] and elem_idx[] list each element's vertex loop,
+ *       counter-clockwise; neighbouring elements share vertex ids (conforming).
+ *   3D: elem_ptr[ne+1] indexes tetrahedra; elem_idx[4*ntet] holds the 4 vertex
+ *       ids of each tetrahedron, grouped by element.  Faces between tetrahedra
+ *       of the same element are interior to it.
+ * Faces are derived from the elements: a 2D loop edge / 3D tetrahedron
+ * triangle seen by two elements is an interior face, seen by one a boundary
+ * face. */
+typedef struct {
+  int dim;                 /* 2 or 3 */
+  int nv;                  /* vertices */
+  const double *x, *y, *z; /* vertex coordinates (z unused in 2D) */
+  int ne;                  /* elements */
+  const int *elem_ptr;     /* [ne+1] */
+  const int *elem_idx;     /* 2D: loop vertex ids; 3D: 4 vertex ids per tetrahedron */
+  const int8_t *p;         /* [ne] polynomial degree, 1 <= p <= DG_PMAX_{2D,3D} */
+  const double *a;         /* [ne] diffusion coefficient, a > 0 */
+  double b[3];             /* constant advection field */
+  double c;                /* constant reaction, c >= 0 (c - div b / 2 = c >= 0, Sec. 2.1) */
+  int source;              /* DG_SRC_* */
+  double poly[20];         /* coefficients for DG_SRC_POLY */
+  double c_sigma;          /* penalty constant C_sigma (> 0; the configs use 10) */
+} dg_mesh_desc;
+
+/* Sizes of the block-sparse layout of a mesh. */
+typedef struct {
+  int ne;           /* block rows = elements */
+  int nnzb;         /* stored blocks */
+  int64_t nvals;    /* stored scalar entries = sum over blocks of n_r * n_c */
+  int64_t ndofs;    /* sum of n_k = length of the load vector */
+  int nfaces;       /* faces (interior + boundary) */
+  int ninterfaces;  /* element pairs sharing at least one face */
+  int nbfaces;      /* boundary faces */
+  int nsub;         /* sub-simplices (2D triangles, 3D tetrahedra) */
+  int64_t nqvol;    /* volume quadrature points */
+  int64_t nqface;   /* face quadrature points (interior faces counted once) */
+} dg_bsr_info;
+
+/* Create a context on CUDA device `device` that issues all work on
+ * `stream` (a cudaStream_t; NULL = the legacy default stream).  The stream
+ * stays owned by the caller. */
+int dg_create(dg_ctx **ctx, int device, void *stream);
+void dg_destroy(dg_ctx *ctx);
+const char *dg_last_error(void);
+
+/* Validate and upload a mesh, derive faces and interfaces, build the BSR
+ * pattern and work lists (host), and run the geometry kernels (device,
+ * Sec. 3 intro: subdivision data, bounding boxes, normals, penalties).
+ * Returns DG_ERR_MESH for: index out of range, a 2D loop with fewer than 3
+ * vertices or non-positive area, a zero-volume tetrahedron, a face seen by
+ * more than two elements, two neighbouring 2D loops traversing their common
+ * edge in the same direction, p out of range, a <= 0, c < 0, C_sigma <= 0. */
+int dg_mesh_upload(dg_ctx *ctx, const dg_mesh_desc *desc, dg_mesh **out);
+int dg_mesh_free(dg_mesh *mesh);
+
+/* Host-only dry run of dg_mesh_upload: the same validation, face derivation
+ * and BSR pattern, without touching a GPU.  Fills *info (may be NULL) and,
+ * for non-NULL arrays sized from a previous call's info, row_ptr[ne+1],
+ * col[nnzb] and blk_off[nnzb+1].  Same error codes as dg_mesh_upload. */
+int dg_mesh_check(const dg_mesh_desc *desc, dg_bsr_info *info, int *row_ptr, int *col,
+                  int64_t *blk_off);
+
+/* Replace vertex coordinates (host, same topology) and per-element
+ * diffusion coefficients (host, may be NULL to keep them); re-runs the
+ * geometry kernels on the context stream. */
+int dg_mesh_update(dg_ctx *ctx, dg_mesh *mesh, const double *x, const double *y, const double *z,
+                   const double *a);
+
+/* Re-run the geometry kernels (bounding boxes, sub-simplex maps, face data,
+ * penalties) from the uploaded coordinates, on the context stream. */
+int dg_geometry(dg_ctx *ctx, dg_mesh *mesh);
+
+int dg_bsr_layout(const dg_mesh *mesh, dg_bsr_info *out);
+/* Copy the pattern to HOST arrays: row_ptr[ne+1], col[nnzb], blk_off[nnzb+1]
+ * (offsets of blocks in vals, in entries), dof_off[ne+1] (offsets of each
+ * element's entries in the load vector). Any pointer may be NULL. */
+int dg_bsr_pattern(const dg_mesh *mesh, int *row_ptr, int *col, int64_t *blk_off, int64_t *dof_off);
+
+/* Volume integrals (first line of Eq. (2.4)) of every element: OVERWRITES
+ * each element's diagonal block in vals (device, nvals entries of double for
+ * DG_PREC_FP64, float for DG_PREC_FP32).  Off-diagonal blocks are untouched. */
+int dg_assemble_volume(dg_ctx *ctx, const dg_mesh *mesh, int prec, void *vals);
+
+/* Face integrals (second and third lines of Eq. (2.4)): ADDS each element's
+ * own-face contributions to its diagonal block (each element reduces its own
+ * faces in a fixed order; no atomics) and OVERWRITES the off-diagonal blocks
+ * of every interface.  Must follow dg_assemble_volume on the same vals
+ * (DG_ERR_ORDER otherwise). */
+int dg_assemble_faces(dg_ctx *ctx, const dg_mesh *mesh, int prec, void *vals);
+
+/* Load vector of Eq. (2.5) into rhs (device, ndofs entries of double /
+ * float by prec), OVERWRITTEN. */
+int dg_assemble_rhs(dg_ctx *ctx, const dg_mesh *mesh, int prec, void *rhs);
+
+/* Whole system in one pass: every block of vals and, if rhs is not NULL,
+ * the load vector; equal up to rounding to volume + faces (+ rhs). */
+int dg_assemble(dg_ctx *ctx, const dg_mesh *mesh, int prec, void *vals, void *rhs);
+
+/* End-to-end from host memory: copies x,y,z (host, nv each; may be NULL to
+ * keep the uploaded coordinates) and a (host, ne; may be NULL) to the
+ * device, recomputes the geometry, assembles the system into library-owned
+ * device buffers and copies vals (host, nvals entries) and rhs (host, ndofs
+ * entries; may be NULL) back.  Synchronous. */
+int dg_assemble_host(dg_ctx *ctx, dg_mesh *mesh, int prec, const double *x, const double *y,
+                     const double *z, const double *a, void *vals_host, void *rhs_host);
+
+/* One pass of the whole hot path on device-resident inputs: geometry
+ * kernels (dg_geometry) followed by dg_assemble.  Asynchronous. */
+int dg_assemble_step(dg_ctx *ctx, dg_mesh *mesh, int prec, void *vals, void *rhs);
+
+/* Per-launch timing.  When enabled, every kernel launch of the following
+ * calls is bracketed by CUDA events on the context stream.  dg_kernel_stats
+ * waits for the stream and copies up to cap records of the most recent call
+ * (dg_geometry, dg_assemble*, dg_assemble_step) into out, returning their
+ * number.  flops / bytes are the launch's algorithmic work: FMA = 2 flops;
+ * per quadrature point, element of n dofs in dimension d: volume
+ * d n(n+1)/2 + [b or c != 0](n^2 + n(d+1)) + basis (n d^2 + 5 d p) + n (load);
+ * own interior-face point 3 n^2 + [b != 0] n^2/2 + basis; boundary-face
+ * point 3 n^2 + [b != 0] n^2 + basis + 2n (load); interface-kernel face point
+ * 6 n0 n1 + [b != 0] n0 n1.  Bytes: values written once plus geometry
+ * records read once, in the precision's element size. */
+typedef struct {
+  char name[48];
+  float ms;
+  double flops;
+  double bytes;
+} dg_kernel_stat;
+int dg_set_timing(dg_ctx *ctx, int enable);
+int dg_kernel_stats(dg_ctx *ctx, dg_kernel_stat *out, int cap);
+
+/* Wait for all work on the context stream; reports device-side errors. */
+int dg_sync(dg_ctx *ctx);
+
+/* Number of kernel launches issued by the last assembly call (for
+ * accounting in benchmarks). */
+int dg_last_launch_count(const dg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DG_H */

@@ -1,0 +1,15 @@
+// dg_elem3d_f32.cu -- 3D element kernels (float contractions), degrees 1..4.
+#include "dg_launch.cuh"
+
+namespace dg {
+
+int launch_elem3d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, cudaStream_t st, Tracer* tr) {
+  int n = 0;
+  n += launch_elem_p<3, 1, float>(m, mode, vals, rhs, sm_count, st, tr);
+  n += launch_elem_p<3, 2, float>(m, mode, vals, rhs, sm_count, st, tr);
+  n += launch_elem_p<3, 3, float>(m, mode, vals, rhs, sm_count, st, tr);
+  n += launch_elem_p<3, 4, float>(m, mode, vals, rhs, sm_count, st, tr);
+  return n;
+}
+
+}  // namespace dg

@@ -1,0 +1,217 @@
+// dg_geom.cu -- geometry kernels (FP64): element bounding boxes, centroids,
+// measures and diameters; sub-simplex maps in bounding-box coordinates;
+// face normals, measures, per-side maps and penalties.
+//
+// Subdivision (Sec. 3 intro): 2D elements are split into the triangles
+// (centroid, v_i, v_{i+1}) of their CCW loop; 3D elements are the union of
+// their tetrahedra.  h_k = diam(k) (Sec. 2.2).  Penalty: the simplified form
+// of Appendix A, sigma_F = C_sigma max_k a_k p_k^2 / h_k over F's elements.
+#include "dg_internal.h"
+
+namespace dg {
+
+namespace {
+
+__device__ __forceinline__ double xi_of(double x, double lo, double L) { return 2.0 * (x - lo) / L - 1.0; }
+
+template <int D>
+__global__ void elem_geom_kernel(DevMesh m) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m.ne) return;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  double vol = 0.0, cen[3] = {0.0, 0.0, 0.0};
+  if (D == 2) {
+    const int b = m.eptr[e], k = m.eptr[e + 1] - b;
+    for (int i = 0; i < k; ++i) {
+      const int v0 = m.eidx[b + i], v1 = m.eidx[b + (i + 1 == k ? 0 : i + 1)];
+      const double x0 = m.X[0][v0], y0 = m.X[1][v0], x1 = m.X[0][v1], y1 = m.X[1][v1];
+      const double cr = x0 * y1 - x1 * y0;
+      vol += 0.5 * cr;
+      cen[0] += (x0 + x1) * cr;
+      cen[1] += (y0 + y1) * cr;
+    }
+    cen[0] /= 6.0 * vol;
+    cen[1] /= 6.0 * vol;
+  } else {
+    for (int t = m.eptr[e]; t < m.eptr[e + 1]; ++t) {
+      double P[4][3];
+      for (int i = 0; i < 4; ++i) {
+        const int v = m.eidx[4 * t + i];
+        for (int d = 0; d < 3; ++d) P[i][d] = m.X[d][v];
+      }
+      double u[3], v[3], w[3];
+      for (int d = 0; d < 3; ++d) {
+        u[d] = P[1][d] - P[0][d];
+        v[d] = P[2][d] - P[0][d];
+        w[d] = P[3][d] - P[0][d];
+      }
+      const double det = u[0] * (v[1] * w[2] - v[2] * w[1]) - u[1] * (v[0] * w[2] - v[2] * w[0]) +
+                         u[2] * (v[0] * w[1] - v[1] * w[0]);
+      const double tv = fabs(det) / 6.0;
+      vol += tv;
+      for (int d = 0; d < 3; ++d) cen[d] += tv * 0.25 * (P[0][d] + P[1][d] + P[2][d] + P[3][d]);
+    }
+    for (int d = 0; d < 3; ++d) cen[d] /= vol;
+  }
+  // bounding box and diameter over the element's distinct vertices
+  double h2 = 0.0;
+  const int ub = m.uvptr[e], ue = m.uvptr[e + 1];
+  for (int i = ub; i < ue; ++i) {
+    const int vi = m.uvidx[i];
+    double pi_[3];
+    for (int d = 0; d < D; ++d) {
+      pi_[d] = m.X[d][vi];
+      lo[d] = fmin(lo[d], pi_[d]);
+      hi[d] = fmax(hi[d], pi_[d]);
+    }
+    for (int j = i + 1; j < ue; ++j) {
+      const int vj = m.uvidx[j];
+      double s = 0.0;
+      for (int d = 0; d < D; ++d) {
+        const double df = m.X[d][vj] - pi_[d];
+        s += df * df;
+      }
+      h2 = fmax(h2, s);
+    }
+  }
+  for (int d = 0; d < D; ++d) {
+    m.lo[d * m.ne + e] = lo[d];
+    m.L[d * m.ne + e] = hi[d] - lo[d];
+    m.cen[d * m.ne + e] = cen[d];
+  }
+  m.vol[e] = vol;
+  m.h[e] = sqrt(h2);
+}
+
+template <int D>
+__global__ void sub_geom_kernel(DevMesh m) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m.nsub) return;
+  const int e = m.sub_elem[k];
+  double lo[3], L[3];
+  for (int d = 0; d < D; ++d) {
+    lo[d] = m.lo[d * m.ne + e];
+    L[d] = m.L[d * m.ne + e];
+  }
+  constexpr int SV = sub_vals(D);
+  double out[SV];
+  if (D == 2) {
+    const int b = m.eptr[e], n = m.eptr[e + 1] - b;
+    const int i = k - b;
+    const int v1 = m.eidx[k], v2 = m.eidx[b + (i + 1 == n ? 0 : i + 1)];
+    const double c[2] = {m.cen[e], m.cen[m.ne + e]};
+    const double p1[2] = {m.X[0][v1], m.X[1][v1]}, p2[2] = {m.X[0][v2], m.X[1][v2]};
+    for (int d = 0; d < 2; ++d) {
+      const double xc = xi_of(c[d], lo[d], L[d]);
+      out[d] = xc;
+      out[2 + d] = xi_of(p1[d], lo[d], L[d]) - xc;
+      out[4 + d] = xi_of(p2[d], lo[d], L[d]) - xc;
+    }
+    out[6] = fabs((p1[0] - c[0]) * (p2[1] - c[1]) - (p1[1] - c[1]) * (p2[0] - c[0]));
+  } else {
+    double P[4][3];
+    for (int i = 0; i < 4; ++i) {
+      const int v = m.eidx[4 * k + i];
+      for (int d = 0; d < 3; ++d) P[i][d] = m.X[d][v];
+    }
+    for (int d = 0; d < 3; ++d) {
+      const double x0 = xi_of(P[0][d], lo[d], L[d]);
+      out[d] = x0;
+      for (int i = 1; i < 4; ++i) out[3 * i + d] = xi_of(P[i][d], lo[d], L[d]) - x0;
+    }
+    double u[3], v[3], w[3];
+    for (int d = 0; d < 3; ++d) {
+      u[d] = P[1][d] - P[0][d];
+      v[d] = P[2][d] - P[0][d];
+      w[d] = P[3][d] - P[0][d];
+    }
+    out[12] = fabs(u[0] * (v[1] * w[2] - v[2] * w[1]) - u[1] * (v[0] * w[2] - v[2] * w[0]) +
+                   u[2] * (v[0] * w[1] - v[1] * w[0]));
+  }
+  for (int j = 0; j < SV; ++j) {
+    m.sg64[(size_t)j * m.nsub + k] = out[j];
+    m.sg32[(size_t)j * m.nsub + k] = (float)out[j];
+  }
+}
+
+template <int D>
+__global__ void face_geom_kernel(DevMesh m) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= m.nf) return;
+  const int es[2] = {m.f_e0[f], m.f_e1[f]};
+  double P[3][3];
+  for (int i = 0; i < D; ++i) {
+    const int v = m.f_v[D * f + i];
+    for (int d = 0; d < D; ++d) P[i][d] = m.X[d][v];
+  }
+  double n[3], J;
+  if (D == 2) {
+    const double tx = P[1][0] - P[0][0], ty = P[1][1] - P[0][1];
+    const double len = sqrt(tx * tx + ty * ty);
+    n[0] = ty / len;  // the CCW loop of e0 has its interior on the left
+    n[1] = -tx / len;
+    J = len;
+  } else {
+    double u[3], v[3];
+    for (int d = 0; d < 3; ++d) {
+      u[d] = P[1][d] - P[0][d];
+      v[d] = P[2][d] - P[0][d];
+    }
+    const double c[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+    const double len = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    for (int d = 0; d < 3; ++d) n[d] = c[d] / len;  // vertex order makes this point out of e0
+    J = len;                                         // = 2 |F| (collapsed triangle rule)
+  }
+  constexpr int FV = side_vals(D);
+  double sigma = 0.0;
+  for (int s = 0; s < 2; ++s) {
+    const int e = es[s];
+    double out[FV];
+    for (int j = 0; j < FV; ++j) out[j] = 0.0;
+    if (e >= 0) {
+      for (int d = 0; d < D; ++d) {
+        const double lo = m.lo[d * m.ne + e], L = m.L[d * m.ne + e];
+        const double x0 = xi_of(P[0][d], lo, L);
+        out[d] = x0;
+        for (int i = 1; i < D; ++i) out[i * D + d] = xi_of(P[i][d], lo, L) - x0;
+        out[D * D + d] = 2.0 * n[d] / L;
+      }
+      const int pe = m.p[e];
+      sigma = fmax(sigma, m.a[e] * pe * pe / m.h[e]);
+    }
+    for (int j = 0; j < FV; ++j) {
+      m.fs64[((size_t)s * FV + j) * m.nf + f] = out[j];
+      m.fs32[((size_t)s * FV + j) * m.nf + f] = (float)out[j];
+    }
+  }
+  sigma *= m.pb.c_sigma;
+  double bn = 0.0;
+  for (int d = 0; d < D; ++d) bn += m.pb.b[d] * n[d];
+  const double sc[3] = {J, sigma, bn};
+  for (int j = 0; j < 3; ++j) {
+    m.fsc64[(size_t)j * m.nf + f] = sc[j];
+    m.fsc32[(size_t)j * m.nf + f] = (float)sc[j];
+  }
+}
+
+inline int nblk(int n, int t) { return (n + t - 1) / t; }
+
+}  // namespace
+
+int launch_geometry(const DevMesh& m, cudaStream_t st, Tracer* tr) {
+  const int T = 128;
+  if (tr && tr->on) tr->begin(m.dim == 2 ? "geometry2d" : "geometry3d", 2, 0, 8, st);
+  if (m.dim == 2) {
+    elem_geom_kernel<2><<<nblk(m.ne, T), T, 0, st>>>(m);
+    sub_geom_kernel<2><<<nblk(m.nsub, T), T, 0, st>>>(m);
+    face_geom_kernel<2><<<nblk(m.nf, T), T, 0, st>>>(m);
+  } else {
+    elem_geom_kernel<3><<<nblk(m.ne, T), T, 0, st>>>(m);
+    sub_geom_kernel<3><<<nblk(m.nsub, T), T, 0, st>>>(m);
+    face_geom_kernel<3><<<nblk(m.nf, T), T, 0, st>>>(m);
+  }
+  if (tr && tr->on) tr->end(st);
+  return 3;
+}
+
+}  // namespace dg

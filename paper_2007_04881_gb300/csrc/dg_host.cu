@@ -1,0 +1,1008 @@
+// dg_host.cu -- host side of libdg: contexts, mesh upload (validation, face
+// and interface derivation, block-sparse pattern, work lists), reference
+// quadrature tables, and the C ABI declared in include/dg.h.
+//
+// The sparsity pattern is built before any quadrature, with one block per
+// element pair however many faces the pair shares: the "Approach 2" idea of
+// Sec. 3.4 (precomputed pattern, values written in place).  Unlike the
+// paper's atomics, every block has exactly one writer per launch, so the
+// result is bitwise reproducible.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/dg.h"
+#include "dg_internal.h"
+
+using namespace dg;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+
+#define DG_CUDA_TRY(expr)                                                                   \
+  do {                                                                                      \
+    cudaError_t _e = (expr);                                                                \
+    if (_e != cudaSuccess)                                                                  \
+      return fail(_e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA, "%s: %s", #expr, \
+                  cudaGetErrorString(_e));                                                  \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// reference quadrature (Gauss-Legendre by Newton's method, collapsed rules)
+// ---------------------------------------------------------------------------
+
+// n-point Gauss-Legendre rule on [0,1].  Newton's method on P_n, started
+// from Tricomi's asymptotic approximation of the roots.
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.assign(n, 0.0);
+  w.assign(n, 0.0);
+  const double pi = 3.14159265358979323846;
+  for (int i = 1; i <= n; ++i) {
+    double t = (1.0 - 1.0 / (8.0 * n * n) + 1.0 / (8.0 * n * n * n)) * std::cos(pi * (4.0 * i - 1.0) / (4.0 * n + 2.0));
+    double dp = 1.0;
+    for (int iter = 0; iter < 64; ++iter) {
+      // P_n(t) and P_n'(t)
+      double pm = 1.0, pc = t;
+      for (int k = 2; k <= n; ++k) {
+        const double pn = ((2.0 * k - 1.0) * t * pc - (k - 1.0) * pm) / k;
+        pm = pc;
+        pc = pn;
+      }
+      if (n == 1) {
+        pm = 1.0;
+        pc = t;
+      }
+      dp = n * (t * pc - pm) / (t * t - 1.0);
+      const double step = pc / dp;
+      t -= step;
+      if (std::fabs(step) <= 1e-16 * std::fabs(t) + 1e-300) break;
+    }
+    // recompute the derivative at the converged root for the weight
+    double pm = 1.0, pc = t;
+    for (int k = 2; k <= n; ++k) {
+      const double pn = ((2.0 * k - 1.0) * t * pc - (k - 1.0) * pm) / k;
+      pm = pc;
+      pc = pn;
+    }
+    if (n == 1) {
+      pm = 1.0;
+      pc = t;
+    }
+    dp = n * (t * pc - pm) / (t * t - 1.0);
+    const double wt = 2.0 / ((1.0 - t * t) * dp * dp);
+    x[i - 1] = 0.5 * (1.0 - t);  // roots come out descending in t; store ascending
+    w[i - 1] = 0.5 * wt;
+  }
+}
+
+// Collapsed rules.  Triangle: (r, s) = (a(1-b), b), weight w_a w_b (1-b).
+// Tetrahedron: (r, s, t) = (a(1-b)(1-c), b(1-c), c), weight w_a w_b w_c (1-b)(1-c)^2.
+void simplex_rule(int dim, int n, std::vector<double>& pts /* [q][dim+1] */) {
+  std::vector<double> g, gw;
+  gauss_legendre01(n, g, gw);
+  pts.clear();
+  if (dim == 1) {
+    for (int i = 0; i < n; ++i) {
+      pts.push_back(g[i]);
+      pts.push_back(gw[i]);
+    }
+  } else if (dim == 2) {
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        const double a = g[i], b = g[j];
+        pts.push_back(a * (1.0 - b));
+        pts.push_back(b);
+        pts.push_back(gw[i] * gw[j] * (1.0 - b));
+      }
+  } else {
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j)
+        for (int k = 0; k < n; ++k) {
+          const double a = g[i], b = g[j], c = g[k];
+          pts.push_back(a * (1.0 - b) * (1.0 - c));
+          pts.push_back(b * (1.0 - c));
+          pts.push_back(c);
+          pts.push_back(gw[i] * gw[j] * gw[k] * (1.0 - b) * (1.0 - c) * (1.0 - c));
+        }
+  }
+}
+
+struct DevBuf {
+  std::vector<void*> ptrs;
+  ~DevBuf() {
+    for (void* p : ptrs) cudaFree(p);
+  }
+  template <typename T>
+  cudaError_t alloc(T** out, size_t n) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T));
+    if (e == cudaSuccess) {
+      ptrs.push_back(p);
+      *out = static_cast<T*>(p);
+    }
+    return e;
+  }
+};
+
+}  // namespace
+
+struct dg_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int sm_count = 0;
+  int last_launches = 0;
+  DevBuf bufs;
+  RuleTables rt[4];  // indexed by dim (2, 3)
+  Tracer tracer;
+  std::vector<LaunchRec> recs;
+  ~dg_ctx() {
+    for (auto& r : recs) {
+      cudaEventDestroy(r.ev0);
+      cudaEventDestroy(r.ev1);
+    }
+  }
+};
+
+namespace dg {
+void Tracer::begin(const char* name, int kind, int p, size_t tsize, cudaStream_t st) {
+  if (!on || n >= cap) return;
+  LaunchRec& r = recs[n];
+  snprintf(r.name, sizeof r.name, "%s", name);
+  r.flops = (kind < 2 && flops) ? flops[kind * 9 + p] : 0.0;
+  r.bytes = (kind < 2 && words) ? words[kind * 9 + p] * (double)tsize : 0.0;
+  cudaEventRecord(r.ev0, st);
+}
+void Tracer::end(cudaStream_t st) {
+  if (!on || n >= cap) return;
+  cudaEventRecord(recs[n].ev1, st);
+  ++n;
+}
+}  // namespace dg
+
+struct dg_mesh {
+  dg_ctx* ctx = nullptr;
+  DevBuf bufs;
+  DevMesh dm{};
+  dg_bsr_info info{};
+  std::vector<int> row_ptr, col;
+  std::vector<int64_t> blk_off, dof_off;
+  const void* vol_vals = nullptr;  // vals last written by dg_assemble_volume
+  // library-owned buffers of the host-memory path
+  void* h_vals = nullptr;
+  void* h_rhs = nullptr;
+  int h_prec = -1;
+  double* X[3] = {nullptr, nullptr, nullptr};
+  double* a = nullptr;
+  double flops[2][9] = {{0}}, words[2][9] = {{0}};
+  ~dg_mesh() {
+    if (h_vals) cudaFree(h_vals);
+    if (h_rhs) cudaFree(h_rhs);
+  }
+};
+
+static void trace_reset(dg_ctx* ctx, const dg_mesh* mesh) {
+  ctx->tracer.n = 0;
+  ctx->tracer.flops = &mesh->flops[0][0];
+  ctx->tracer.words = &mesh->words[0][0];
+}
+
+namespace {
+
+int build_rule_tables(dg_ctx* ctx) {
+  for (int dim = 2; dim <= 3; ++dim) {
+    RuleTables& rt = ctx->rt[dim];
+    const int pmax = dim == 2 ? kPMax2 : kPMax3;
+    std::vector<double> vol, face, pts;
+    for (int p = 1; p <= pmax; ++p) {
+      simplex_rule(dim, p + 2, pts);
+      rt.vol_off[p] = (int)(vol.size() / (dim + 1));
+      rt.vol_n[p] = (int)(pts.size() / (dim + 1));
+      vol.insert(vol.end(), pts.begin(), pts.end());
+    }
+    for (int n = 1; n <= pmax + 1; ++n) {
+      simplex_rule(dim - 1, n, pts);
+      rt.face_off[n] = (int)(face.size() / dim);
+      rt.face_n[n] = (int)(pts.size() / dim);
+      face.insert(face.end(), pts.begin(), pts.end());
+    }
+    double *v64, *f64;
+    float *v32, *f32;
+    DG_CUDA_TRY(ctx->bufs.alloc(&v64, vol.size()));
+    DG_CUDA_TRY(ctx->bufs.alloc(&v32, vol.size()));
+    DG_CUDA_TRY(ctx->bufs.alloc(&f64, face.size()));
+    DG_CUDA_TRY(ctx->bufs.alloc(&f32, face.size()));
+    std::vector<float> vf(vol.begin(), vol.end()), ff(face.begin(), face.end());
+    DG_CUDA_TRY(cudaMemcpy(v64, vol.data(), vol.size() * 8, cudaMemcpyHostToDevice));
+    DG_CUDA_TRY(cudaMemcpy(v32, vf.data(), vf.size() * 4, cudaMemcpyHostToDevice));
+    DG_CUDA_TRY(cudaMemcpy(f64, face.data(), face.size() * 8, cudaMemcpyHostToDevice));
+    DG_CUDA_TRY(cudaMemcpy(f32, ff.data(), ff.size() * 4, cudaMemcpyHostToDevice));
+    rt.vol64 = v64;
+    rt.vol32 = v32;
+    rt.face64 = f64;
+    rt.face32 = f32;
+  }
+  return DG_OK;
+}
+
+template <typename T>
+int upload(DevBuf& b, const T** out, const std::vector<T>& v) {
+  T* p;
+  DG_CUDA_TRY(b.alloc(&p, v.size()));
+  if (!v.empty()) DG_CUDA_TRY(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  *out = p;
+  return DG_OK;
+}
+
+struct HalfFace {
+  int key[3];
+  int elem;
+  int v[3];  // oriented vertices (2D: v[0], v[1])
+};
+
+bool key_less(const HalfFace& a, const HalfFace& b) {
+  for (int i = 0; i < 3; ++i)
+    if (a.key[i] != b.key[i]) return a.key[i] < b.key[i];
+  return a.elem < b.elem;
+}
+
+bool key_eq(const HalfFace& a, const HalfFace& b) {
+  return a.key[0] == b.key[0] && a.key[1] == b.key[1] && a.key[2] == b.key[2];
+}
+
+struct FaceRec {
+  int e0, e1;
+  int v[3];
+  int key[3];
+};
+
+}  // namespace
+
+struct Plan {
+  std::vector<int> sub_elem, if_e0, if_e1, if_fptr, row_ptr, col, diag_blk, slot01, slot10;
+  std::vector<int64_t> blk_off, dof_off;
+  std::vector<FaceRec> F;
+  std::vector<int> f_e0, f_e1, f_v, f_nq, hf_ptr, hf_face, hf_qoff, e_nqf, uvptr, uvidx, elem_perm, if_perm;
+  std::vector<int8_t> hf_side;
+  int elem_pstart[9] = {0}, if_pstart[9] = {0};
+  int nsub = 0, nf = 0, nint = 0, ni = 0, nhf = 0;
+  int64_t nqvol = 0, nqface = 0;
+  // algorithmic flops / words per launch group [kind][p] (kind 0 element
+  // kernels with load vector, 1 interface kernels)
+  double flops[2][9] = {{0}}, words[2][9] = {{0}};
+};
+
+extern "C" {
+
+const char* dg_last_error(void) { return g_err.c_str(); }
+
+int dg_create(dg_ctx** out, int device, void* stream) {
+  if (!out) return fail(DG_ERR_ARG, "dg_create: null output pointer");
+  *out = nullptr;
+  int ndev = 0;
+  DG_CUDA_TRY(cudaGetDeviceCount(&ndev));
+  if (device < 0 || device >= ndev) return fail(DG_ERR_ARG, "dg_create: device %d out of range (%d devices)", device, ndev);
+  DG_CUDA_TRY(cudaSetDevice(device));
+  dg_ctx* ctx = new (std::nothrow) dg_ctx();
+  if (!ctx) return fail(DG_ERR_OOM, "dg_create: out of host memory");
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) {
+    delete ctx;
+    return fail(DG_ERR_CUDA, "dg_create: %s", cudaGetErrorString(e));
+  }
+  int rc = build_rule_tables(ctx);
+  if (rc != DG_OK) {
+    delete ctx;
+    return rc;
+  }
+  *out = ctx;
+  return DG_OK;
+}
+
+void dg_destroy(dg_ctx* ctx) { delete ctx; }
+
+int dg_mesh_free(dg_mesh* mesh) {
+  delete mesh;
+  return DG_OK;
+}
+
+static int plan_mesh(const dg_mesh_desc* d, Plan& P) {
+  if (!d) return fail(DG_ERR_ARG, "null mesh descriptor");
+  const int dim = d->dim;
+  if (dim != 2 && dim != 3) return fail(DG_ERR_ARG, "dim must be 2 or 3 (got %d)", dim);
+  if (d->nv <= 0 || d->ne <= 0) return fail(DG_ERR_ARG, "nv and ne must be positive");
+  if (!d->x || !d->y || (dim == 3 && !d->z) || !d->elem_ptr || !d->elem_idx || !d->p || !d->a)
+    return fail(DG_ERR_ARG, "dg_mesh_upload: null array in descriptor");
+  if (d->source < 0 || d->source > 2) return fail(DG_ERR_ARG, "unknown source %d", d->source);
+  if (!(d->c_sigma > 0.0)) return fail(DG_ERR_MESH, "C_sigma must be positive");
+  if (!(d->c >= 0.0)) return fail(DG_ERR_MESH, "c must be >= 0");
+  const int nv = d->nv, ne = d->ne;
+  const int pmax = dim == 2 ? kPMax2 : kPMax3;
+  if (d->elem_ptr[0] != 0) return fail(DG_ERR_MESH, "elem_ptr[0] must be 0");
+  for (int e = 0; e < ne; ++e) {
+    const int cnt = d->elem_ptr[e + 1] - d->elem_ptr[e];
+    if (cnt < (dim == 2 ? 3 : 1)) return fail(DG_ERR_MESH, "element %d has %d entries", e, cnt);
+    if (d->p[e] < 1 || d->p[e] > pmax) return fail(DG_ERR_MESH, "element %d: p = %d outside 1..%d", e, d->p[e], pmax);
+    if (!(d->a[e] > 0.0) || !std::isfinite(d->a[e])) return fail(DG_ERR_MESH, "element %d: a must be > 0", e);
+  }
+  const int nidx = d->elem_ptr[ne] * (dim == 2 ? 1 : 4);
+  for (int i = 0; i < nidx; ++i)
+    if (d->elem_idx[i] < 0 || d->elem_idx[i] >= nv) return fail(DG_ERR_MESH, "vertex index %d out of range", d->elem_idx[i]);
+  const double* X[3] = {d->x, d->y, dim == 3 ? d->z : nullptr};
+
+  // --- geometric validity (host, FP64)
+  if (dim == 2) {
+    for (int e = 0; e < ne; ++e) {
+      const int b = d->elem_ptr[e], k = d->elem_ptr[e + 1] - b;
+      double A = 0, cx = 0, cy = 0;
+      for (int i = 0; i < k; ++i) {
+        const int v0 = d->elem_idx[b + i], v1 = d->elem_idx[b + (i + 1) % k];
+        const double cr = X[0][v0] * X[1][v1] - X[0][v1] * X[1][v0];
+        A += 0.5 * cr;
+        cx += (X[0][v0] + X[0][v1]) * cr;
+        cy += (X[1][v0] + X[1][v1]) * cr;
+      }
+      if (!(A > 0.0)) return fail(DG_ERR_MESH, "element %d: loop is not counter-clockwise (area %g)", e, A);
+      cx /= 6 * A;
+      cy /= 6 * A;
+      for (int i = 0; i < k; ++i) {
+        const int v0 = d->elem_idx[b + i], v1 = d->elem_idx[b + (i + 1) % k];
+        const double tri = (X[0][v0] - cx) * (X[1][v1] - cy) - (X[1][v0] - cy) * (X[0][v1] - cx);
+        if (!(tri > 0.0)) return fail(DG_ERR_MESH, "element %d: fan triangle %d has non-positive area", e, i);
+      }
+    }
+  } else {
+    const int nt = d->elem_ptr[ne];
+    for (int t = 0; t < nt; ++t) {
+      const int* tv = d->elem_idx + 4 * t;
+      double u[3], v[3], w[3];
+      for (int q = 0; q < 3; ++q) {
+        u[q] = X[q][tv[1]] - X[q][tv[0]];
+        v[q] = X[q][tv[2]] - X[q][tv[0]];
+        w[q] = X[q][tv[3]] - X[q][tv[0]];
+      }
+      const double det = u[0] * (v[1] * w[2] - v[2] * w[1]) - u[1] * (v[0] * w[2] - v[2] * w[0]) +
+                         u[2] * (v[0] * w[1] - v[1] * w[0]);
+      if (!(std::fabs(det) > 0.0)) return fail(DG_ERR_MESH, "tetrahedron %d has zero volume", t);
+    }
+  }
+
+  // --- faces
+  std::vector<HalfFace> H;
+  std::vector<int>& sub_elem = P.sub_elem;
+  if (dim == 2) {
+    H.reserve(d->elem_ptr[ne]);
+    sub_elem.resize(d->elem_ptr[ne]);
+    for (int e = 0; e < ne; ++e) {
+      const int b = d->elem_ptr[e], k = d->elem_ptr[e + 1] - b;
+      for (int i = 0; i < k; ++i) {
+        HalfFace h{};
+        const int v0 = d->elem_idx[b + i], v1 = d->elem_idx[b + (i + 1) % k];
+        if (v0 == v1) return fail(DG_ERR_MESH, "element %d: repeated vertex in loop", e);
+        h.key[0] = std::min(v0, v1);
+        h.key[1] = std::max(v0, v1);
+        h.key[2] = -1;
+        h.elem = e;
+        h.v[0] = v0;
+        h.v[1] = v1;
+        h.v[2] = -1;
+        H.push_back(h);
+        sub_elem[b + i] = e;
+      }
+    }
+  } else {
+    const int nt = d->elem_ptr[ne];
+    H.reserve((size_t)4 * nt);
+    sub_elem.resize(nt);
+    for (int e = 0; e < ne; ++e)
+      for (int t = d->elem_ptr[e]; t < d->elem_ptr[e + 1]; ++t) {
+        sub_elem[t] = e;
+        const int* tv = d->elem_idx + 4 * t;
+        for (int o = 0; o < 4; ++o) {
+          HalfFace h{};
+          int c = 0;
+          for (int i = 0; i < 4; ++i)
+            if (i != o) h.v[c++] = tv[i];
+          // orient (v0, v1, v2) so that (v1-v0) x (v2-v0) points away from tv[o]
+          double u[3], v[3], w[3];
+          for (int q = 0; q < 3; ++q) {
+            u[q] = X[q][h.v[1]] - X[q][h.v[0]];
+            v[q] = X[q][h.v[2]] - X[q][h.v[0]];
+            w[q] = X[q][tv[o]] - X[q][h.v[0]];
+          }
+          const double cr[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+          if (cr[0] * w[0] + cr[1] * w[1] + cr[2] * w[2] > 0.0) std::swap(h.v[1], h.v[2]);
+          int kk[3] = {h.v[0], h.v[1], h.v[2]};
+          std::sort(kk, kk + 3);
+          for (int q = 0; q < 3; ++q) h.key[q] = kk[q];
+          h.elem = e;
+          H.push_back(h);
+        }
+      }
+  }
+  std::sort(H.begin(), H.end(), key_less);
+  std::vector<FaceRec>& F = P.F;
+  F.reserve(H.size());
+  for (size_t i = 0; i < H.size();) {
+    size_t j = i + 1;
+    while (j < H.size() && key_eq(H[i], H[j])) ++j;
+    const size_t cnt = j - i;
+    if (cnt > 2) return fail(DG_ERR_MESH, "a face is shared by %zu element pieces (non-manifold)", cnt);
+    if (cnt == 2 && H[i].elem == H[i + 1].elem) {
+      if (dim == 2) return fail(DG_ERR_MESH, "element %d traverses an edge twice", H[i].elem);
+      // interior to one 3D element: not a face
+    } else {
+      FaceRec f{};
+      f.e0 = H[i].elem;
+      f.e1 = cnt == 2 ? H[i + 1].elem : -1;
+      for (int q = 0; q < 3; ++q) {
+        f.v[q] = H[i].v[q];
+        f.key[q] = H[i].key[q];
+      }
+      if (dim == 2 && cnt == 2 && !(H[i].v[0] == H[i + 1].v[1] && H[i].v[1] == H[i + 1].v[0]))
+        return fail(DG_ERR_MESH, "elements %d and %d traverse their common edge in the same direction", f.e0, f.e1);
+      F.push_back(f);
+    }
+    i = j;
+  }
+  std::stable_sort(F.begin(), F.end(), [](const FaceRec& a, const FaceRec& b) {
+    const bool ab = a.e1 < 0, bb = b.e1 < 0;
+    if (ab != bb) return !ab;
+    if (a.e0 != b.e0) return a.e0 < b.e0;
+    if (a.e1 != b.e1) return a.e1 < b.e1;
+    for (int q = 0; q < 3; ++q)
+      if (a.key[q] != b.key[q]) return a.key[q] < b.key[q];
+    return false;
+  });
+  const int nf = (int)F.size();
+  int nint = 0;
+  while (nint < nf && F[nint].e1 >= 0) ++nint;
+
+  // --- interfaces
+  std::vector<int>&if_e0 = P.if_e0, &if_e1 = P.if_e1, &if_fptr = P.if_fptr;
+  for (int f = 0; f < nint;) {
+    int g = f + 1;
+    while (g < nint && F[g].e0 == F[f].e0 && F[g].e1 == F[f].e1) ++g;
+    if_e0.push_back(F[f].e0);
+    if_e1.push_back(F[f].e1);
+    if_fptr.push_back(f);
+    f = g;
+  }
+  if_fptr.push_back(nint);
+  const int ni = (int)if_e0.size();
+
+  // --- block-sparse pattern
+  std::vector<int> nb(ne);
+  for (int e = 0; e < ne; ++e) nb[e] = nbasis(dim, d->p[e]);
+  std::vector<std::vector<int>> nbr(ne);
+  for (int i = 0; i < ni; ++i) {
+    nbr[if_e0[i]].push_back(if_e1[i]);
+    nbr[if_e1[i]].push_back(if_e0[i]);
+  }
+  Plan* m = &P;
+  m->row_ptr.assign(ne + 1, 0);
+  std::vector<int>& diag_blk = P.diag_blk;
+  diag_blk.assign(ne, 0);
+  for (int e = 0; e < ne; ++e) {
+    nbr[e].push_back(e);
+    std::sort(nbr[e].begin(), nbr[e].end());
+    m->row_ptr[e + 1] = m->row_ptr[e] + (int)nbr[e].size();
+  }
+  m->col.resize(m->row_ptr[ne]);
+  m->blk_off.assign(m->row_ptr[ne] + 1, 0);
+  for (int e = 0; e < ne; ++e)
+    for (size_t k = 0; k < nbr[e].size(); ++k) {
+      const int idx = m->row_ptr[e] + (int)k, c = nbr[e][k];
+      m->col[idx] = c;
+      m->blk_off[idx + 1] = m->blk_off[idx] + (int64_t)nb[e] * nb[c];
+      if (c == e) diag_blk[e] = idx;
+    }
+  auto slot = [&](int r, int c) {
+    const int* b = m->col.data() + m->row_ptr[r];
+    const int* en = m->col.data() + m->row_ptr[r + 1];
+    return (int)(std::lower_bound(b, en, c) - m->col.data());
+  };
+  std::vector<int>&slot01 = P.slot01, &slot10 = P.slot10;
+  slot01.assign(ni, 0);
+  slot10.assign(ni, 0);
+  for (int i = 0; i < ni; ++i) {
+    slot01[i] = slot(if_e0[i], if_e1[i]);
+    slot10[i] = slot(if_e1[i], if_e0[i]);
+  }
+  m->dof_off.assign(ne + 1, 0);
+  for (int e = 0; e < ne; ++e) m->dof_off[e + 1] = m->dof_off[e] + nb[e];
+
+  // --- half faces (element -> faces, global face order) and face points
+  std::vector<int>&f_e0 = P.f_e0, &f_e1 = P.f_e1, &f_v = P.f_v, &f_nq = P.f_nq;
+  f_e0.assign(nf, 0);
+  f_e1.assign(nf, 0);
+  f_v.assign((size_t)dim * nf, 0);
+  f_nq.assign(nf, 0);
+  std::vector<int> hf_cnt(ne + 1, 0);
+  int64_t nqface = 0;
+  for (int f = 0; f < nf; ++f) {
+    f_e0[f] = F[f].e0;
+    f_e1[f] = F[f].e1;
+    for (int q = 0; q < dim; ++q) f_v[(size_t)dim * f + q] = F[f].v[q];
+    const int pm = F[f].e1 >= 0 ? std::max(d->p[F[f].e0], d->p[F[f].e1]) : d->p[F[f].e0];
+    f_nq[f] = pm + 1;
+    nqface += dim == 2 ? f_nq[f] : f_nq[f] * f_nq[f];
+    hf_cnt[F[f].e0 + 1]++;
+    if (F[f].e1 >= 0) hf_cnt[F[f].e1 + 1]++;
+  }
+  std::vector<int>& hf_ptr = P.hf_ptr;
+  hf_ptr.assign(ne + 1, 0);
+  for (int e = 0; e < ne; ++e) hf_ptr[e + 1] = hf_ptr[e] + hf_cnt[e + 1];
+  const int nhf = hf_ptr[ne];
+  std::vector<int>&hf_face = P.hf_face, &hf_qoff = P.hf_qoff, &e_nqf = P.e_nqf;
+  hf_face.assign(nhf, 0);
+  hf_qoff.assign(nhf, 0);
+  e_nqf.assign(ne, 0);
+  std::vector<int> fill(ne, 0);
+  std::vector<int8_t>& hf_side = P.hf_side;
+  hf_side.assign(nhf, 0);
+  for (int f = 0; f < nf; ++f)
+    for (int s = 0; s < 2; ++s) {
+      const int e = s == 0 ? F[f].e0 : F[f].e1;
+      if (e < 0) continue;
+      const int k = hf_ptr[e] + fill[e]++;
+      hf_face[k] = f;
+      hf_side[k] = (int8_t)s;
+      hf_qoff[k] = e_nqf[e];
+      e_nqf[e] += dim == 2 ? f_nq[f] : f_nq[f] * f_nq[f];
+    }
+
+  // --- unique vertices per element, sub-simplex counts
+  std::vector<int>&uvptr = P.uvptr, &uvidx = P.uvidx;
+  uvptr.assign(ne + 1, 0);
+  if (dim == 2) {
+    uvptr.assign(d->elem_ptr, d->elem_ptr + ne + 1);
+    uvidx.assign(d->elem_idx, d->elem_idx + d->elem_ptr[ne]);
+  } else {
+    std::vector<int> tmp;
+    for (int e = 0; e < ne; ++e) {
+      tmp.assign(d->elem_idx + 4 * d->elem_ptr[e], d->elem_idx + 4 * d->elem_ptr[e + 1]);
+      std::sort(tmp.begin(), tmp.end());
+      tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
+      uvidx.insert(uvidx.end(), tmp.begin(), tmp.end());
+      uvptr[e + 1] = (int)uvidx.size();
+    }
+  }
+  const int nsub = d->elem_ptr[ne];
+  int64_t nqvol = 0;
+  std::vector<int64_t> cost(ne);
+  for (int e = 0; e < ne; ++e) {
+    int qt = 1;
+    for (int q = 0; q < dim; ++q) qt *= d->p[e] + 2;
+    const int64_t nvq = (int64_t)(d->elem_ptr[e + 1] - d->elem_ptr[e]) * qt;
+    nqvol += nvq;
+    cost[e] = nvq + e_nqf[e];
+  }
+
+  // --- work lists: elements by degree (cost-descending), interfaces by max degree
+  std::vector<int>& elem_perm = P.elem_perm;
+  elem_perm.assign(ne, 0);
+  std::iota(elem_perm.begin(), elem_perm.end(), 0);
+  std::stable_sort(elem_perm.begin(), elem_perm.end(), [&](int x, int y) {
+    if (d->p[x] != d->p[y]) return d->p[x] < d->p[y];
+    return cost[x] > cost[y];
+  });
+  for (int p = 0; p <= 8; ++p) {
+    P.elem_pstart[p] = (int)(std::lower_bound(elem_perm.begin(), elem_perm.end(), p,
+                                               [&](int e, int pv) { return d->p[e] < pv; }) -
+                              elem_perm.begin());
+  }
+  std::vector<int>& if_perm = P.if_perm;
+  if_perm.assign(ni, 0);
+  std::vector<int> if_pm(ni), if_np(ni);
+  for (int i = 0; i < ni; ++i) {
+    if_pm[i] = std::max(d->p[if_e0[i]], d->p[if_e1[i]]);
+    if_np[i] = (if_fptr[i + 1] - if_fptr[i]) * (dim == 2 ? (if_pm[i] + 1) : (if_pm[i] + 1) * (if_pm[i] + 1));
+  }
+  std::iota(if_perm.begin(), if_perm.end(), 0);
+  std::stable_sort(if_perm.begin(), if_perm.end(), [&](int x, int y) {
+    if (if_pm[x] != if_pm[y]) return if_pm[x] < if_pm[y];
+    return if_np[x] > if_np[y];
+  });
+  for (int p = 0; p <= 8; ++p)
+    P.if_pstart[p] = (int)(std::lower_bound(if_perm.begin(), if_perm.end(), p,
+                                             [&](int i, int pv) { return if_pm[i] < pv; }) -
+                            if_perm.begin());
+
+  // Algorithmic work (FMA = 2 flops), per quadrature point, element of n
+  // dofs in dimension d: volume d n(n+1)/2 (symmetric diffusion) +
+  // [b or c != 0](n^2 + n(d+1)) + basis n d^2 + 5 d p; own interior-face
+  // point 3 n^2 + [b != 0] n^2/2 + basis; boundary-face point 3 n^2 +
+  // [b != 0] n^2 + basis; load vector n per volume point and 2n per boundary
+  // point.  Interface kernel: 6 n0 n1 + [b != 0] n0 n1 per face point (its
+  // basis values are counted once, in the element kernels).
+  {
+    const bool advb = d->b[0] != 0.0 || d->b[1] != 0.0 || (dim == 3 && d->b[2] != 0.0);
+    const bool adv = advb || d->c != 0.0;
+    const int SV = sub_vals(dim), FV = side_vals(dim);
+    for (int e = 0; e < ne; ++e) {
+      const int pe = d->p[e];
+      const double n = nb[e];
+      const double basis = n * dim * dim + 5.0 * dim * pe;
+      int qt = 1;
+      for (int q = 0; q < dim; ++q) qt *= pe + 2;
+      const double nvq = (double)(d->elem_ptr[e + 1] - d->elem_ptr[e]) * qt;
+      double fma = nvq * (dim * n * (n + 1) / 2 + (adv ? n * n + n * (dim + 1) : 0.0) + basis + n);
+      double w = n * n + n + (double)(d->elem_ptr[e + 1] - d->elem_ptr[e]) * SV + 2 * dim + 2;
+      for (int k = hf_ptr[e]; k < hf_ptr[e + 1]; ++k) {
+        const int f = hf_face[k];
+        const double qf = dim == 2 ? f_nq[f] : (double)f_nq[f] * f_nq[f];
+        const bool bnd = F[f].e1 < 0;
+        fma += qf * (3 * n * n + (advb ? (bnd ? n * n : n * n / 2) : 0.0) + basis + (bnd ? 2 * n : 0.0));
+        w += FV + 3;
+      }
+      P.flops[0][pe] += 2.0 * fma;
+      P.words[0][pe] += w;
+    }
+    for (int i = 0; i < ni; ++i) {
+      const int pm = std::max(d->p[if_e0[i]], d->p[if_e1[i]]);
+      const double n0 = nb[if_e0[i]], n1 = nb[if_e1[i]];
+      double fma = 0.0, w = 2 * n0 * n1;
+      for (int f = if_fptr[i]; f < if_fptr[i + 1]; ++f) {
+        const double qf = dim == 2 ? f_nq[f] : (double)f_nq[f] * f_nq[f];
+        fma += qf * (6 * n0 * n1 + (advb ? n0 * n1 : 0.0));
+        w += 2 * FV + 3;
+      }
+      P.flops[1][pm] += 2.0 * fma;
+      P.words[1][pm] += w;
+    }
+  }
+  P.nsub = nsub;
+  P.nf = nf;
+  P.nint = nint;
+  P.ni = ni;
+  P.nhf = nhf;
+  P.nqvol = nqvol;
+  P.nqface = nqface;
+  return DG_OK;
+}
+
+static void fill_info(const dg_mesh_desc* d, const Plan& P, dg_bsr_info& I) {
+  I.ne = d->ne;
+  I.nnzb = P.row_ptr[d->ne];
+  I.nvals = P.blk_off[I.nnzb];
+  I.ndofs = P.dof_off[d->ne];
+  I.nfaces = P.nf;
+  I.ninterfaces = P.ni;
+  I.nbfaces = P.nf - P.nint;
+  I.nsub = P.nsub;
+  I.nqvol = P.nqvol;
+  I.nqface = P.nqface;
+}
+
+int dg_mesh_check(const dg_mesh_desc* d, dg_bsr_info* info, int* row_ptr, int* col, int64_t* blk_off) {
+  Plan P;
+  int rc = plan_mesh(d, P);
+  if (rc != DG_OK) return rc;
+  dg_bsr_info I{};
+  fill_info(d, P, I);
+  if (info) *info = I;
+  if (row_ptr) std::copy(P.row_ptr.begin(), P.row_ptr.end(), row_ptr);
+  if (col) std::copy(P.col.begin(), P.col.end(), col);
+  if (blk_off) std::copy(P.blk_off.begin(), P.blk_off.end(), blk_off);
+  return DG_OK;
+}
+
+int dg_mesh_upload(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
+  if (!ctx || !d || !out) return fail(DG_ERR_ARG, "dg_mesh_upload: null argument");
+  *out = nullptr;
+  Plan P;
+  int prc = plan_mesh(d, P);
+  if (prc != DG_OK) return prc;
+  const int dim = d->dim, nv = d->nv, ne = d->ne;
+  const int nidx = d->elem_ptr[ne] * (dim == 2 ? 1 : 4);
+  const double* X[3] = {d->x, d->y, dim == 3 ? d->z : nullptr};
+  const int nsub = P.nsub, nf = P.nf, ni = P.ni, nhf = P.nhf;
+  dg_mesh* m = new (std::nothrow) dg_mesh();
+  if (!m) return fail(DG_ERR_OOM, "out of host memory");
+  m->ctx = ctx;
+  m->row_ptr = P.row_ptr;
+  m->col = P.col;
+  std::memcpy(m->flops, P.flops, sizeof P.flops);
+  std::memcpy(m->words, P.words, sizeof P.words);
+  m->blk_off = P.blk_off;
+  m->dof_off = P.dof_off;
+  DevMesh& dm = m->dm;
+  for (int p = 0; p <= 8; ++p) {
+    dm.elem_pstart[p] = P.elem_pstart[p];
+    dm.if_pstart[p] = P.if_pstart[p];
+  }
+  auto& sub_elem = P.sub_elem;
+  auto &uvptr = P.uvptr, &uvidx = P.uvidx;
+  auto &f_e0 = P.f_e0, &f_e1 = P.f_e1, &f_v = P.f_v, &f_nq = P.f_nq;
+  auto &hf_ptr = P.hf_ptr, &hf_face = P.hf_face, &hf_qoff = P.hf_qoff, &e_nqf = P.e_nqf;
+  auto& hf_side = P.hf_side;
+  auto &if_e0 = P.if_e0, &if_e1 = P.if_e1, &if_fptr = P.if_fptr, &slot01 = P.slot01, &slot10 = P.slot10;
+  auto& diag_blk = P.diag_blk;
+  auto &elem_perm = P.elem_perm, &if_perm = P.if_perm;
+  // --- upload
+  dm.dim = dim;
+  dm.nv = nv;
+  dm.ne = ne;
+  dm.nsub = nsub;
+  dm.nf = nf;
+  dm.ni = ni;
+  dm.nhf = nhf;
+  DevBuf& B = m->bufs;
+  int rc = DG_OK;
+  auto up_i = [&](const int** dst, const std::vector<int>& v) {
+    if (rc == DG_OK) rc = upload(B, dst, v);
+  };
+  for (int q = 0; q < 3; ++q) {
+    dm.X[q] = nullptr;
+    if (q < dim) {
+      std::vector<double> v(X[q], X[q] + nv);
+      const double* p;
+      if (rc == DG_OK) rc = upload(B, &p, v);
+      dm.X[q] = p;
+      m->X[q] = const_cast<double*>(p);
+    }
+  }
+  std::vector<int> eptr(d->elem_ptr, d->elem_ptr + ne + 1), eidx(d->elem_idx, d->elem_idx + nidx);
+  up_i(&dm.eptr, eptr);
+  up_i(&dm.eidx, eidx);
+  up_i(&dm.uvptr, uvptr);
+  up_i(&dm.uvidx, uvidx);
+  up_i(&dm.sub_elem, sub_elem);
+  dm.sub_loc = nullptr;
+  std::vector<int> pv(d->p, d->p + ne);
+  up_i(&dm.p, pv);
+  {
+    std::vector<double> av(d->a, d->a + ne);
+    if (rc == DG_OK) rc = upload(B, &dm.a, av);
+    m->a = const_cast<double*>(dm.a);
+  }
+  up_i(&dm.f_e0, f_e0);
+  up_i(&dm.f_e1, f_e1);
+  up_i(&dm.f_v, f_v);
+  {
+    const int* p;
+    up_i(&p, f_nq);
+    dm.f_nq = const_cast<int*>(p);
+  }
+  up_i(&dm.hf_ptr, hf_ptr);
+  up_i(&dm.hf_face, hf_face);
+  if (rc == DG_OK) rc = upload(B, &dm.hf_side, hf_side);
+  up_i(&dm.hf_qoff, hf_qoff);
+  up_i(&dm.e_nqf, e_nqf);
+  up_i(&dm.if_e0, if_e0);
+  up_i(&dm.if_e1, if_e1);
+  up_i(&dm.if_fptr, if_fptr);
+  up_i(&dm.if_slot01, slot01);
+  up_i(&dm.if_slot10, slot10);
+  if (rc == DG_OK) rc = upload(B, &dm.blk_off, m->blk_off);
+  up_i(&dm.diag_blk, diag_blk);
+  if (rc == DG_OK) rc = upload(B, &dm.dof_off, m->dof_off);
+  up_i(&dm.elem_perm, elem_perm);
+  up_i(&dm.if_perm, if_perm);
+  if (rc != DG_OK) {
+    delete m;
+    return rc;
+  }
+  auto alloc_d = [&](double** p, size_t n) {
+    if (rc == DG_OK && B.alloc(p, n) != cudaSuccess) rc = fail(DG_ERR_OOM, "device allocation failed");
+  };
+  auto alloc_f = [&](float** p, size_t n) {
+    if (rc == DG_OK && B.alloc(p, n) != cudaSuccess) rc = fail(DG_ERR_OOM, "device allocation failed");
+  };
+  alloc_d(&dm.lo, (size_t)dim * ne);
+  alloc_d(&dm.L, (size_t)dim * ne);
+  alloc_d(&dm.cen, (size_t)dim * ne);
+  alloc_d(&dm.vol, ne);
+  alloc_d(&dm.h, ne);
+  alloc_d(&dm.sg64, (size_t)sub_vals(dim) * nsub);
+  alloc_f(&dm.sg32, (size_t)sub_vals(dim) * nsub);
+  alloc_d(&dm.fs64, (size_t)2 * side_vals(dim) * nf);
+  alloc_f(&dm.fs32, (size_t)2 * side_vals(dim) * nf);
+  alloc_d(&dm.fsc64, (size_t)3 * nf);
+  alloc_f(&dm.fsc32, (size_t)3 * nf);
+  if (rc != DG_OK) {
+    delete m;
+    return rc;
+  }
+  for (int q = 0; q < 3; ++q) dm.pb.b[q] = d->b[q];
+  if (dim == 2) dm.pb.b[2] = 0.0;
+  dm.pb.c = d->c;
+  dm.pb.source = d->source;
+  for (int q = 0; q < 20; ++q) dm.pb.poly[q] = d->poly[q];
+  dm.pb.c_sigma = d->c_sigma;
+  dm.rt = ctx->rt[dim];
+
+  fill_info(d, P, m->info);
+
+  cudaSetDevice(ctx->device);
+  launch_geometry(dm, ctx->stream);
+  cudaError_t ce = cudaGetLastError();
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+  if (ce != cudaSuccess) {
+    delete m;
+    return fail(DG_ERR_CUDA, "geometry kernels: %s", cudaGetErrorString(ce));
+  }
+  *out = m;
+  return DG_OK;
+}
+
+int dg_bsr_layout(const dg_mesh* mesh, dg_bsr_info* out) {
+  if (!mesh || !out) return fail(DG_ERR_ARG, "dg_bsr_layout: null argument");
+  *out = mesh->info;
+  return DG_OK;
+}
+
+int dg_bsr_pattern(const dg_mesh* mesh, int* row_ptr, int* col, int64_t* blk_off, int64_t* dof_off) {
+  if (!mesh) return fail(DG_ERR_ARG, "dg_bsr_pattern: null mesh");
+  if (row_ptr) std::copy(mesh->row_ptr.begin(), mesh->row_ptr.end(), row_ptr);
+  if (col) std::copy(mesh->col.begin(), mesh->col.end(), col);
+  if (blk_off) std::copy(mesh->blk_off.begin(), mesh->blk_off.end(), blk_off);
+  if (dof_off) std::copy(mesh->dof_off.begin(), mesh->dof_off.end(), dof_off);
+  return DG_OK;
+}
+
+int dg_geometry(dg_ctx* ctx, dg_mesh* mesh) {
+  if (!ctx || !mesh) return fail(DG_ERR_ARG, "dg_geometry: null argument");
+  trace_reset(ctx, mesh);
+  ctx->last_launches = launch_geometry(mesh->dm, ctx->stream, &ctx->tracer);
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+
+int dg_mesh_update(dg_ctx* ctx, dg_mesh* mesh, const double* x, const double* y, const double* z, const double* a) {
+  if (!ctx || !mesh) return fail(DG_ERR_ARG, "dg_mesh_update: null argument");
+  const int nv = mesh->dm.nv, ne = mesh->dm.ne;
+  const double* src[3] = {x, y, z};
+  for (int q = 0; q < mesh->dm.dim; ++q)
+    if (src[q]) DG_CUDA_TRY(cudaMemcpyAsync(mesh->X[q], src[q], sizeof(double) * nv, cudaMemcpyHostToDevice, ctx->stream));
+  if (a) DG_CUDA_TRY(cudaMemcpyAsync(mesh->a, a, sizeof(double) * ne, cudaMemcpyHostToDevice, ctx->stream));
+  return dg_geometry(ctx, mesh);
+}
+
+static int run_assembly(dg_ctx* ctx, const dg_mesh* mesh, int prec, int mode, void* vals, void* rhs, bool iface,
+                        bool reset = true) {
+  if (!ctx || !mesh) return fail(DG_ERR_ARG, "null context or mesh");
+  if (prec != DG_PREC_FP64 && prec != DG_PREC_FP32) return fail(DG_ERR_ARG, "unknown precision %d", prec);
+  if ((mode & (kModeVol | kModeFace)) && !vals) return fail(DG_ERR_ARG, "vals is null");
+  if ((mode & kModeRhs) && !rhs) return fail(DG_ERR_ARG, "rhs is null");
+  const DevMesh& m = mesh->dm;
+  Tracer* tr = &ctx->tracer;
+  if (reset) trace_reset(ctx, mesh);
+  int n = 0;
+  if (prec == DG_PREC_FP64) {
+    double* v = static_cast<double*>(vals);
+    double* r = static_cast<double*>(rhs);
+    n += m.dim == 2 ? launch_elem2d_f64(m, mode, v, r, ctx->sm_count, ctx->stream, tr)
+                    : launch_elem3d_f64(m, mode, v, r, ctx->sm_count, ctx->stream, tr);
+    if (iface) n += launch_iface_f64(m, v, ctx->sm_count, ctx->stream, tr);
+  } else {
+    float* v = static_cast<float*>(vals);
+    float* r = static_cast<float*>(rhs);
+    n += m.dim == 2 ? launch_elem2d_f32(m, mode, v, r, ctx->sm_count, ctx->stream, tr)
+                    : launch_elem3d_f32(m, mode, v, r, ctx->sm_count, ctx->stream, tr);
+    if (iface) n += launch_iface_f32(m, v, ctx->sm_count, ctx->stream, tr);
+  }
+  ctx->last_launches = reset ? n : ctx->last_launches + n;
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+
+int dg_assemble_volume(dg_ctx* ctx, const dg_mesh* mesh, int prec, void* vals) {
+  int rc = run_assembly(ctx, mesh, prec, kModeVol, vals, nullptr, false);
+  if (rc == DG_OK) const_cast<dg_mesh*>(mesh)->vol_vals = vals;
+  return rc;
+}
+
+int dg_assemble_faces(dg_ctx* ctx, const dg_mesh* mesh, int prec, void* vals) {
+  if (!mesh || mesh->vol_vals != vals || !vals)
+    return fail(DG_ERR_ORDER, "dg_assemble_faces: call dg_assemble_volume on the same vals first");
+  int rc = run_assembly(ctx, mesh, prec, kModeFace | kModeAccum, vals, nullptr, true);
+  if (rc == DG_OK) const_cast<dg_mesh*>(mesh)->vol_vals = nullptr;
+  return rc;
+}
+
+int dg_assemble_rhs(dg_ctx* ctx, const dg_mesh* mesh, int prec, void* rhs) {
+  return run_assembly(ctx, mesh, prec, kModeRhs, nullptr, rhs, false);
+}
+
+int dg_assemble(dg_ctx* ctx, const dg_mesh* mesh, int prec, void* vals, void* rhs) {
+  const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
+  return run_assembly(ctx, mesh, prec, mode, vals, rhs, true);
+}
+
+int dg_assemble_host(dg_ctx* ctx, dg_mesh* mesh, int prec, const double* x, const double* y, const double* z,
+                     const double* a, void* vals_host, void* rhs_host) {
+  if (!ctx || !mesh || !vals_host) return fail(DG_ERR_ARG, "dg_assemble_host: null argument");
+  if (prec != DG_PREC_FP64 && prec != DG_PREC_FP32) return fail(DG_ERR_ARG, "unknown precision %d", prec);
+  const size_t es = prec == DG_PREC_FP64 ? 8 : 4;
+  if (mesh->h_prec != prec) {
+    if (mesh->h_vals) cudaFree(mesh->h_vals);
+    if (mesh->h_rhs) cudaFree(mesh->h_rhs);
+    mesh->h_vals = mesh->h_rhs = nullptr;
+    DG_CUDA_TRY(cudaMalloc(&mesh->h_vals, es * std::max<int64_t>(mesh->info.nvals, 1)));
+    DG_CUDA_TRY(cudaMalloc(&mesh->h_rhs, es * std::max<int64_t>(mesh->info.ndofs, 1)));
+    mesh->h_prec = prec;
+  }
+  int rc = dg_mesh_update(ctx, mesh, x, y, z, a);
+  if (rc != DG_OK) return rc;
+  const int geo = ctx->last_launches;
+  {
+    const int mode = kModeVol | kModeFace | (rhs_host ? kModeRhs : 0);
+    rc = run_assembly(ctx, mesh, prec, mode, mesh->h_vals, rhs_host ? mesh->h_rhs : nullptr, true, false);
+  }
+  if (rc != DG_OK) return rc;
+  (void)geo;
+  DG_CUDA_TRY(cudaMemcpyAsync(vals_host, mesh->h_vals, es * mesh->info.nvals, cudaMemcpyDeviceToHost, ctx->stream));
+  if (rhs_host)
+    DG_CUDA_TRY(cudaMemcpyAsync(rhs_host, mesh->h_rhs, es * mesh->info.ndofs, cudaMemcpyDeviceToHost, ctx->stream));
+  DG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return DG_OK;
+}
+
+int dg_assemble_step(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs) {
+  int rc = dg_geometry(ctx, mesh);
+  if (rc != DG_OK) return rc;
+  const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
+  return run_assembly(ctx, mesh, prec, mode, vals, rhs, true, false);
+}
+
+int dg_set_timing(dg_ctx* ctx, int enable) {
+  if (!ctx) return fail(DG_ERR_ARG, "dg_set_timing: null context");
+  if (enable && ctx->recs.empty()) {
+    ctx->recs.resize(64);
+    for (auto& r : ctx->recs) {
+      DG_CUDA_TRY(cudaEventCreate(&r.ev0));
+      DG_CUDA_TRY(cudaEventCreate(&r.ev1));
+    }
+  }
+  ctx->tracer.on = enable != 0;
+  ctx->tracer.recs = ctx->recs.data();
+  ctx->tracer.cap = (int)ctx->recs.size();
+  ctx->tracer.n = 0;
+  return DG_OK;
+}
+
+int dg_kernel_stats(dg_ctx* ctx, dg_kernel_stat* out, int cap) {
+  if (!ctx) return fail(DG_ERR_ARG, "dg_kernel_stats: null context");
+  DG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  const int n = ctx->tracer.on ? ctx->tracer.n : 0;
+  for (int i = 0; i < n && i < cap && out; ++i) {
+    const LaunchRec& r = ctx->recs[i];
+    std::memcpy(out[i].name, r.name, sizeof out[i].name);
+    float ms = 0.f;
+    DG_CUDA_TRY(cudaEventElapsedTime(&ms, r.ev0, r.ev1));
+    out[i].ms = ms;
+    out[i].flops = r.flops;
+    out[i].bytes = r.bytes;
+  }
+  return n;
+}
+
+int dg_sync(dg_ctx* ctx) {
+  if (!ctx) return fail(DG_ERR_ARG, "dg_sync: null context");
+  DG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+
+int dg_last_launch_count(const dg_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
+
+}  // extern "C"

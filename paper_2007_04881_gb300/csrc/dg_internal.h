@@ -1,0 +1,156 @@
+// dg_internal.h -- device-side mesh view and launch helpers shared by the
+// host code (dg_host.cu) and the kernels (dg_geom.cu, dg_elem*.cu,
+// dg_iface.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace dg {
+
+constexpr int kPMax2 = 6;  // highest degree with compiled kernels in 2D
+constexpr int kPMax3 = 4;  // ... in 3D
+constexpr int kWarps = 4;  // warps per CTA of the element / interface kernels
+
+// values per sub-simplex in bounding-box coordinates xi = 2(x-lo)/L - 1:
+//   2D triangle: xi0(2), e1(2), e2(2), |J|          -> 7
+//   3D tetrahedron: xi0(3), e1(3), e2(3), e3(3), |J| -> 13
+__host__ __device__ constexpr int sub_vals(int dim) { return dim == 2 ? 7 : 13; }
+// values per face side (side s frame of element e_s):
+//   2D: xi(v0)(2), xi(v1)-xi(v0)(2), n'(2)              -> 6
+//   3D: xi(v0)(3), xi(v1)-xi(v0)(3), xi(v2)-xi(v0)(3), n'(3) -> 12
+// with n'_d = 2 n_d / L_d, n the unit normal pointing out of e0.
+__host__ __device__ constexpr int side_vals(int dim) { return dim == 2 ? 6 : 12; }
+
+__host__ __device__ constexpr int nbasis(int dim, int p) {
+  return dim == 2 ? (p + 1) * (p + 2) / 2 : (p + 1) * (p + 2) * (p + 3) / 6;
+}
+
+// Reference-rule tables (host-built once per context, FP64 + FP32 copies).
+//   volume rule of degree p: (p+2)^d collapsed points (r, s[, t], w)
+//   face rule with n points per direction: 2D n Gauss points (t, w);
+//   3D n^2 collapsed triangle points (r, s, w)
+struct RuleTables {
+  const double* vol64 = nullptr;  // packed, [point][d+1]
+  const float* vol32 = nullptr;
+  int vol_off[8] = {0};  // offset (in points) of degree p's rule
+  int vol_n[8] = {0};    // points of degree p's rule
+  const double* face64 = nullptr;
+  const float* face32 = nullptr;
+  int face_off[10] = {0};  // offset (in points) of the n-point rule
+  int face_n[10] = {0};    // points of the n-point rule
+};
+
+// Problem data (constant over the mesh).
+struct Problem {
+  double b[3];
+  double c;
+  int source;
+  double poly[20];
+  double c_sigma;
+};
+
+// Everything a kernel needs, by device pointer.  Passed by value.
+struct DevMesh {
+  int dim, nv, ne, nsub, nf, ni, nhf;
+  const double* X[3];
+  // 2D: vertex loops; 3D: tetrahedra (4 vertex ids each)
+  const int* eptr;
+  const int* eidx;
+  // unique vertex list per element (2D: the loop itself)
+  const int* uvptr;
+  const int* uvidx;
+  const int* sub_elem;  // element of each sub-simplex
+  const int* sub_loc;   // 2D: loop position of the triangle's first vertex; 3D: unused
+  const int* p;         // [ne]
+  const double* a;      // [ne]
+  // element geometry (FP64)
+  double* lo;   // [dim][ne]
+  double* L;    // [dim][ne]
+  double* cen;  // [dim][ne]
+  double* vol;  // [ne]
+  double* h;    // [ne]
+  // sub-simplex data, SoA [k][nsub]
+  double* sg64;
+  float* sg32;
+  // faces
+  const int* f_e0;
+  const int* f_e1;  // -1 on the boundary
+  const int* f_v;   // [nf][dim] vertex ids, ordered so the normal points out of e0
+  double* fs64;     // [2][side_vals][nf]
+  float* fs32;
+  double* fsc64;  // [3][nf]: J (2D |F|, 3D 2|F|), sigma, b.n
+  float* fsc32;
+  int* f_nq;  // points per direction on the face: max(p0, p1) + 1
+  // element -> faces (half faces), fixed order
+  const int* hf_ptr;   // [ne+1]
+  const int* hf_face;  // [nhf]
+  const int8_t* hf_side;
+  const int* hf_qoff;  // [nhf] first face point of the half face within its element
+  const int* e_nqf;    // [ne] face points of the element
+  // interfaces
+  const int* if_e0;
+  const int* if_e1;
+  const int* if_fptr;  // [ni+1] faces of interface i (consecutive in face order)
+  const int* if_slot01;
+  const int* if_slot10;
+  // BSR
+  const int64_t* blk_off;
+  const int* diag_blk;
+  const int64_t* dof_off;
+  // work lists
+  const int* elem_perm;  // elements grouped by degree, each group cost-descending
+  int elem_pstart[9];    // group of degree p: elem_perm[elem_pstart[p] .. elem_pstart[p+1])
+  const int* if_perm;    // interfaces grouped by max degree
+  int if_pstart[9];
+  Problem pb;
+  RuleTables rt;
+};
+
+// mode bits of the element kernel
+enum : int {
+  kModeVol = 1,    // volume integrals into the diagonal block
+  kModeFace = 2,   // own-face integrals into the diagonal block
+  kModeRhs = 4,    // load vector
+  kModeAccum = 8,  // add to the diagonal block instead of overwriting it
+};
+
+// Optional per-launch timing: CUDA events recorded on the launch stream
+// around each kernel, with the kernel's label and its algorithmic flop and
+// byte counts (host-computed per launch group).
+struct LaunchRec {
+  char name[48];
+  double flops;
+  double bytes;
+  cudaEvent_t ev0, ev1;
+};
+
+struct Tracer {
+  bool on = false;
+  LaunchRec* recs = nullptr;  // capacity cap, filled from n
+  int cap = 0;
+  int n = 0;
+  // per launch-group algorithmic counts, indexed [kind][p]; kind 0 = element
+  // kernel, 1 = interface kernel; bytes for an element size of 1 (scaled by
+  // sizeof(T) by the launcher) plus a fixed part in bytes64 for FP64 inputs
+  const double* flops = nullptr;  // [2][9]
+  const double* words = nullptr;  // [2][9] values written + read (in elements of T)
+  void begin(const char* name, int kind, int p, size_t tsize, cudaStream_t st);
+  void end(cudaStream_t st);
+};
+
+// Launchers (defined in the kernel translation units).  Each returns the
+// number of kernel launches issued.
+int launch_geometry(const DevMesh& m, cudaStream_t st, Tracer* tr = nullptr);
+int launch_elem2d_f64(const DevMesh& m, int mode, double* vals, double* rhs, int sm_count, cudaStream_t st, Tracer* tr);
+int launch_elem2d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, cudaStream_t st, Tracer* tr);
+int launch_elem3d_f64(const DevMesh& m, int mode, double* vals, double* rhs, int sm_count, cudaStream_t st, Tracer* tr);
+int launch_elem3d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, cudaStream_t st, Tracer* tr);
+int launch_iface_f64(const DevMesh& m, double* vals, int sm_count, cudaStream_t st, Tracer* tr);
+int launch_iface_f32(const DevMesh& m, float* vals, int sm_count, cudaStream_t st, Tracer* tr);
+
+// Tile geometry of the element kernel of (dim, p): G elements per warp.
+int elem_tile_elems(int dim, int p);
+
+}  // namespace dg

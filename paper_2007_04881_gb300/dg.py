@@ -1,0 +1,332 @@
+"""Thin Python binding of libdg's C ABI (include/dg.h).
+
+Argument marshalling only: every step of the assembly runs in the CUDA
+library.  Device buffers are torch tensors (PyTorch provides device memory and
+streams).  If the compiled library is missing the import of this module fails
+loudly; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libdg.so")
+
+DG_OK = 0
+DG_ERR = {
+    -1: "DG_ERR_ARG",
+    -2: "DG_ERR_MESH",
+    -3: "DG_ERR_CUDA",
+    -4: "DG_ERR_OOM",
+    -5: "DG_ERR_ORDER",
+    -6: "DG_ERR_TIMEOUT",
+}
+DG_PREC_FP64 = 0
+DG_PREC_FP32 = 1
+DG_SRC_ZERO, DG_SRC_SINPROD, DG_SRC_POLY = 0, 1, 2
+DG_PMAX_2D, DG_PMAX_3D = 6, 4
+
+
+class DGError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{DG_ERR.get(code, code)}: {msg}")
+        self.code = code
+
+
+class dg_mesh_desc(C.Structure):
+    _fields_ = [
+        ("dim", C.c_int),
+        ("nv", C.c_int),
+        ("x", C.POINTER(C.c_double)),
+        ("y", C.POINTER(C.c_double)),
+        ("z", C.POINTER(C.c_double)),
+        ("ne", C.c_int),
+        ("elem_ptr", C.POINTER(C.c_int)),
+        ("elem_idx", C.POINTER(C.c_int)),
+        ("p", C.POINTER(C.c_int8)),
+        ("a", C.POINTER(C.c_double)),
+        ("b", C.c_double * 3),
+        ("c", C.c_double),
+        ("source", C.c_int),
+        ("poly", C.c_double * 20),
+        ("c_sigma", C.c_double),
+    ]
+
+
+class dg_kernel_stat(C.Structure):
+    _fields_ = [("name", C.c_char * 48), ("ms", C.c_float), ("flops", C.c_double), ("bytes", C.c_double)]
+
+
+class dg_bsr_info(C.Structure):
+    _fields_ = [
+        ("ne", C.c_int),
+        ("nnzb", C.c_int),
+        ("nvals", C.c_int64),
+        ("ndofs", C.c_int64),
+        ("nfaces", C.c_int),
+        ("ninterfaces", C.c_int),
+        ("nbfaces", C.c_int),
+        ("nsub", C.c_int),
+        ("nqvol", C.c_int64),
+        ("nqface", C.c_int64),
+    ]
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load libdg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libdg.so not built ({LIB_PATH}); run paper_2007_04881_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    V = C.c_void_p
+    lib.dg_create.argtypes = [C.POINTER(V), C.c_int, V]
+    lib.dg_destroy.argtypes = [V]
+    lib.dg_destroy.restype = None
+    lib.dg_last_error.restype = C.c_char_p
+    lib.dg_mesh_upload.argtypes = [V, C.POINTER(dg_mesh_desc), C.POINTER(V)]
+    lib.dg_mesh_free.argtypes = [V]
+    lib.dg_mesh_check.argtypes = [C.POINTER(dg_mesh_desc), C.POINTER(dg_bsr_info), V, V, V]
+    lib.dg_mesh_update.argtypes = [V, V, V, V, V, V]
+    lib.dg_geometry.argtypes = [V, V]
+    lib.dg_bsr_layout.argtypes = [V, C.POINTER(dg_bsr_info)]
+    lib.dg_bsr_pattern.argtypes = [V, V, V, V, V]
+    for n in ("dg_assemble_volume", "dg_assemble_faces", "dg_assemble_rhs"):
+        getattr(lib, n).argtypes = [V, V, C.c_int, V]
+    lib.dg_assemble.argtypes = [V, V, C.c_int, V, V]
+    lib.dg_assemble_host.argtypes = [V, V, C.c_int, V, V, V, V, V, V]
+    lib.dg_assemble_step.argtypes = [V, V, C.c_int, V, V]
+    lib.dg_set_timing.argtypes = [V, C.c_int]
+    lib.dg_kernel_stats.argtypes = [V, C.POINTER(dg_kernel_stat), C.c_int]
+    lib.dg_sync.argtypes = [V]
+    lib.dg_last_launch_count.argtypes = [V]
+    _lib = lib
+    return lib
+
+
+# names of every symbol declared in include/dg.h
+EXPORTS = (
+    "dg_create", "dg_destroy", "dg_last_error", "dg_mesh_upload", "dg_mesh_free", "dg_mesh_check",
+    "dg_mesh_update",
+    "dg_geometry", "dg_bsr_layout", "dg_bsr_pattern", "dg_assemble_volume", "dg_assemble_faces",
+    "dg_assemble_rhs", "dg_assemble", "dg_assemble_host", "dg_sync", "dg_last_launch_count",
+    "dg_assemble_step", "dg_set_timing", "dg_kernel_stats",
+)
+
+
+def _check(rc: int):
+    if rc != DG_OK:
+        raise DGError(rc, load().dg_last_error().decode())
+
+
+def _ptr(a: Optional[np.ndarray], ct):
+    return None if a is None else a.ctypes.data_as(C.POINTER(ct))
+
+
+def _vp(x) -> Optional[int]:
+    """Raw pointer of a torch tensor / numpy array / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+@dataclass
+class Problem:
+    """Constant problem data of Eq. (2.1): advection b, reaction c, source."""
+
+    b: Sequence[float] = (0.0, 0.0, 0.0)
+    c: float = 0.0
+    source: int = DG_SRC_ZERO
+    poly: Sequence[float] = field(default_factory=list)
+    c_sigma: float = 10.0
+
+
+class Context:
+    """dg_create / dg_destroy.  ``stream`` is a cudaStream_t handle (int) or None."""
+
+    def __init__(self, device: int = 0, stream: Optional[int] = None):
+        lib = load()
+        h = C.c_void_p()
+        _check(lib.dg_create(C.byref(h), int(device), stream))
+        self._h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().dg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def dg_sync(self):
+        _check(load().dg_sync(self._h))
+
+    def launches(self) -> int:
+        return load().dg_last_launch_count(self._h)
+
+    def dg_set_timing(self, enable: bool):
+        _check(load().dg_set_timing(self._h, int(bool(enable))))
+
+    def dg_kernel_stats(self):
+        """[(name, ms, flops, bytes)] of the most recent call's launches."""
+        buf = (dg_kernel_stat * 64)()
+        n = load().dg_kernel_stats(self._h, buf, 64)
+        if n < 0:
+            _check(n)
+        return [(buf[i].name.decode(), float(buf[i].ms), float(buf[i].flops), float(buf[i].bytes)) for i in range(n)]
+
+
+def make_desc(mesh, p, a, problem: Problem):
+    """dg_mesh_desc for a generator mesh; returns (desc, arrays kept alive)."""
+    d = dg_mesh_desc()
+    keep = []
+    dim = mesh.dim
+
+    def arr(x, dt):
+        v = np.ascontiguousarray(x, dtype=dt)
+        keep.append(v)
+        return v
+
+    x = arr(mesh.x, np.float64)
+    y = arr(mesh.y, np.float64)
+    z = arr(mesh.z, np.float64) if dim == 3 else None
+    if dim == 2:
+        eptr, eidx = arr(mesh.elem_vptr, np.int32), arr(mesh.elem_v, np.int32)
+    else:
+        eptr, eidx = arr(mesh.elem_tptr, np.int32), arr(mesh.tet_v, np.int32)
+    pp = arr(p, np.int8)
+    aa = arr(a, np.float64)
+    d.dim = dim
+    d.nv = int(x.shape[0])
+    d.x, d.y, d.z = _ptr(x, C.c_double), _ptr(y, C.c_double), _ptr(z, C.c_double)
+    d.ne = int(eptr.shape[0] - 1)
+    d.elem_ptr, d.elem_idx = _ptr(eptr, C.c_int), _ptr(eidx, C.c_int)
+    d.p, d.a = _ptr(pp, C.c_int8), _ptr(aa, C.c_double)
+    for i in range(3):
+        d.b[i] = float(problem.b[i]) if i < len(problem.b) else 0.0
+    d.c = float(problem.c)
+    d.source = int(problem.source)
+    for i in range(20):
+        d.poly[i] = float(problem.poly[i]) if i < len(problem.poly) else 0.0
+    d.c_sigma = float(problem.c_sigma)
+    return d, keep
+
+
+def dg_mesh_check(mesh, p, a, problem: Problem, pattern: bool = False):
+    """Host-only validation + pattern (no GPU).  Returns info or (info, row_ptr, col, blk_off)."""
+    lib = load()
+    d, keep = make_desc(mesh, p, a, problem)
+    info = dg_bsr_info()
+    _check(lib.dg_mesh_check(C.byref(d), C.byref(info), None, None, None))
+    if not pattern:
+        return info
+    row_ptr = np.zeros(info.ne + 1, np.int32)
+    col = np.zeros(info.nnzb, np.int32)
+    blk_off = np.zeros(info.nnzb + 1, np.int64)
+    _check(lib.dg_mesh_check(C.byref(d), C.byref(info), _vp(row_ptr), _vp(col), _vp(blk_off)))
+    return info, row_ptr, col, blk_off
+
+
+class Mesh:
+    """dg_mesh_upload of a generator mesh (meshgen.Mesh2D / Mesh3D)."""
+
+    def __init__(self, ctx: Context, mesh, p, a, problem: Problem):
+        lib = load()
+        self.ctx = ctx
+        self.dim = mesh.dim
+        d, keep = make_desc(mesh, p, a, problem)
+        pp = keep[-2]
+        h = C.c_void_p()
+        _check(lib.dg_mesh_upload(ctx._h, C.byref(d), C.byref(h)))
+        self._h = h
+        self.p = np.asarray(pp)
+        info = dg_bsr_info()
+        _check(lib.dg_bsr_layout(h, C.byref(info)))
+        self.info = info
+        self.ne = info.ne
+        self.nvals = int(info.nvals)
+        self.ndofs = int(info.ndofs)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().dg_mesh_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def dg_bsr_pattern(self):
+        ne, nnzb = self.info.ne, self.info.nnzb
+        row_ptr = np.zeros(ne + 1, np.int32)
+        col = np.zeros(nnzb, np.int32)
+        blk_off = np.zeros(nnzb + 1, np.int64)
+        dof_off = np.zeros(ne + 1, np.int64)
+        _check(load().dg_bsr_pattern(self._h, _vp(row_ptr), _vp(col), _vp(blk_off), _vp(dof_off)))
+        return row_ptr, col, blk_off, dof_off
+
+    def dg_assemble_volume(self, prec: int, vals):
+        _check(load().dg_assemble_volume(self.ctx._h, self._h, prec, _vp(vals)))
+
+    def dg_assemble_faces(self, prec: int, vals):
+        _check(load().dg_assemble_faces(self.ctx._h, self._h, prec, _vp(vals)))
+
+    def dg_assemble_rhs(self, prec: int, rhs):
+        _check(load().dg_assemble_rhs(self.ctx._h, self._h, prec, _vp(rhs)))
+
+    def dg_assemble(self, prec: int, vals, rhs=None):
+        _check(load().dg_assemble(self.ctx._h, self._h, prec, _vp(vals), _vp(rhs)))
+
+    def dg_assemble_step(self, prec: int, vals, rhs=None):
+        _check(load().dg_assemble_step(self.ctx._h, self._h, prec, _vp(vals), _vp(rhs)))
+
+    def dg_geometry(self):
+        _check(load().dg_geometry(self.ctx._h, self._h))
+
+    def dg_mesh_update(self, x=None, y=None, z=None, a=None):
+        _check(load().dg_mesh_update(self.ctx._h, self._h, _vp(x), _vp(y), _vp(z), _vp(a)))
+
+    def dg_assemble_host(self, prec: int, vals_host, rhs_host=None, x=None, y=None, z=None, a=None):
+        _check(load().dg_assemble_host(self.ctx._h, self._h, prec, _vp(x), _vp(y), _vp(z), _vp(a),
+                                       _vp(vals_host), _vp(rhs_host)))
+
+
+def to_blocks(mesh: Mesh, vals: np.ndarray, rhs: Optional[np.ndarray] = None):
+    """Split BSR values (host array) into per-element diagonal blocks and
+    per-(row, col) off-diagonal blocks (dicts keyed by element ids)."""
+    row_ptr, col, blk_off, dof_off = mesh.dg_bsr_pattern()
+    from math import comb
+
+    nb = np.array([comb(int(q) + mesh.dim, mesh.dim) for q in mesh.p])
+    diag, off = {}, {}
+    for r in range(mesh.ne):
+        for k in range(row_ptr[r], row_ptr[r + 1]):
+            c = int(col[k])
+            blk = vals[blk_off[k]:blk_off[k + 1]].reshape(nb[r], nb[c])
+            if c == r:
+                diag[r] = blk
+            else:
+                off[(r, c)] = blk
+    out = {"diag": diag, "off": off}
+    if rhs is not None:
+        out["rhs"] = {e: rhs[dof_off[e]:dof_off[e + 1]] for e in range(mesh.ne)}
+    return out

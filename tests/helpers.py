@@ -1,0 +1,46 @@
+"""Shared helpers of the parity tests: run the oracle and the CUDA library on
+the same workload and compare block by block."""
+from __future__ import annotations
+
+import numpy as np
+
+import oracle as O
+from paper_2007_04881_gb300 import dg
+
+
+def oracle_problem(wl):
+    pb = wl.problem
+    return O.make_problem(wl.dim, b=pb["b"], c=pb["c"], source=pb["source"], poly=pb["poly"], c_sigma=pb["c_sigma"])
+
+
+def dg_problem(wl):
+    pb = wl.problem
+    return dg.Problem(b=pb["b"], c=pb["c"], source=pb["source"], poly=pb["poly"], c_sigma=pb["c_sigma"])
+
+
+def oracle_blocks(wl, elems=None, ifaces=None, om=None, rhs=True):
+    om = om or O.Mesh(wl.mesh)
+    return om, om.assemble(wl.p.astype(np.int32), wl.a, oracle_problem(wl), elems=elems, ifaces=ifaces, rhs=rhs)
+
+
+def rel_block_err(got, ref):
+    """max |got - ref| / max |ref| over one block (block max-norm relative)."""
+    s = np.abs(ref).max()
+    if s == 0:
+        return float(np.abs(got).max())
+    return float(np.abs(got - ref).max() / s)
+
+
+def compare(gpu, om, ob, wl):
+    """Largest block-relative error over the diagonal blocks, off-diagonal
+    blocks and per-element load vectors present in the oracle result."""
+    ed = eo = er = 0.0
+    for k, e in enumerate(ob["elems"]):
+        ed = max(ed, rel_block_err(gpu["diag"][int(e)], ob["diag"][k]))
+        if "rhs" in ob and "rhs" in gpu:
+            er = max(er, rel_block_err(gpu["rhs"][int(e)], ob["rhs"][k]))
+    for k, i in enumerate(ob["ifaces"]):
+        e0, e1 = int(om.if_e0[i]), int(om.if_e1[i])
+        eo = max(eo, rel_block_err(gpu["off"][(e0, e1)], ob["a01"][k]))
+        eo = max(eo, rel_block_err(gpu["off"][(e1, e0)], ob["a10"][k]))
+    return ed, eo, er
