@@ -245,14 +245,35 @@ static double ipow(double x, int k) {
   return r;
 }
 
+/* sin(pi x) and cos(pi x) with the argument reduced exactly (x - 2 round(x/2)
+ * and 1 - r are exact in floating point), so that sin(pi x) is exactly 0 at
+ * integer x: u = g_D vanishes on the sides of the unit square / cube, and an
+ * O(eps) residue there would be amplified by sigma in the Nitsche term of
+ * the load functional. */
+static double sin_pi(double x) {
+  double r = x - 2.0 * nearbyint(0.5 * x); /* r in [-1, 1] */
+  double sg = 1.0;
+  if (r < 0.0) {
+    r = -r;
+    sg = -1.0;
+  }
+  if (r > 0.5) r = 1.0 - r; /* sin(pi r) = sin(pi (1 - r)) */
+  return sg * sin(ORC_PI * r);
+}
+
+static double cos_pi(double x) {
+  double r = fabs(x - 2.0 * nearbyint(0.5 * x)); /* cos is even, r in [0, 1] */
+  return sin_pi(0.5 - r);                          /* cos(pi r) = sin(pi (1/2 - r)) */
+}
+
 /* Exact solution u, its gradient and Laplacian for the manufactured sources. */
 static void exact_u(const orc_problem *pb, const double *x, double *u, double *gu, double *lap) {
   int dim = pb->dim;
   if (pb->source == 1) {
     double s[3], c[3];
     for (int d = 0; d < dim; ++d) {
-      s[d] = sin(ORC_PI * x[d]);
-      c[d] = cos(ORC_PI * x[d]);
+      s[d] = sin_pi(x[d]);
+      c[d] = cos_pi(x[d]);
     }
     double prod = 1.0;
     for (int d = 0; d < dim; ++d) prod *= s[d];
