@@ -621,7 +621,8 @@ __global__ void __launch_bounds__(kWarps * 32)
 template <int D, int PM, typename T>
 struct IfaceSmem {
   static constexpr int NM = nbasis(D, PM);
-  static constexpr int CP = 32;  // points per chunk (one per lane)
+  // points per chunk (one per lane); halved where 32 would not fit 4 warps
+  static constexpr int CP = (size_t)kWarps * 4 * 32 * 2 * NM * sizeof(T) > 160 * 1024 ? 16 : 32;
   static constexpr size_t arr = sizeof(T) * CP * 2 * NM;
   static constexpr size_t warp_bytes = align_up(4 * arr + sizeof(T) * 2 * NM, 16);
   static constexpr size_t total(int warps) { return warps * warp_bytes; }
@@ -673,6 +674,7 @@ __global__ void __launch_bounds__(kWarps * 32) iface_kernel(const DevMesh m, T* 
     const int npass = (nent + 32 * EPP - 1) / (32 * EPP);
 
     auto eval_chunk = [&](int ch) {
+      if (lane >= CP) return;
       const int q = ch * CP + lane;
       T* u0 = U0 + lane * 2 * NM;
       T* u1 = U1 + lane * 2 * NM;

@@ -26,6 +26,7 @@ inline int launch_elem_p(const DevMesh& m, int mode, T* vals, T* rhs, int sm_cou
   if (count <= 0) return 0;
   constexpr int G = TileCfg<D, P>::G;
   const int ntiles = (count + G - 1) / G;
+  static_assert(ElemSmem<D, P, T>::total(kWarps) <= 227 * 1024, "element kernel shared memory exceeds 227 KB");
   const size_t smem = ElemSmem<D, P, T>::total(kWarps);
   auto k = elem_kernel<D, P, T>;
   const int grid = resident_grid(k, smem, sm_count, (ntiles + kWarps - 1) / kWarps);
@@ -43,6 +44,7 @@ template <int D, int PM, typename T>
 inline int launch_iface_p(const DevMesh& m, T* vals, int sm_count, cudaStream_t st, Tracer* tr) {
   const int count = m.if_pstart[PM + 1] - m.if_pstart[PM];
   if (count <= 0) return 0;
+  static_assert(IfaceSmem<D, PM, T>::total(kWarps) <= 227 * 1024, "interface kernel shared memory exceeds 227 KB");
   const size_t smem = IfaceSmem<D, PM, T>::total(kWarps);
   auto k = iface_kernel<D, PM, T>;
   const int grid = resident_grid(k, smem, sm_count, (count + kWarps - 1) / kWarps);
