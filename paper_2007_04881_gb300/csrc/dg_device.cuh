@@ -252,54 +252,157 @@ __device__ __forceinline__ const float* pick<float>(const double*, const float* 
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // --------------------------------------------------------------------------
-// element kernel: volume + own faces (+ load vector) of G elements per warp
+// tile loads from shared memory (vectorised where the padded stride allows)
 // --------------------------------------------------------------------------
 
+template <typename T, int TM, int TMP>
+__device__ __forceinline__ void load_tile(const T* __restrict__ p, T (&o)[TM]) {
+  if constexpr (sizeof(T) == 4 && TMP % 4 == 0) {
+#pragma unroll
+    for (int a = 0; a < TMP / 4; ++a) {
+      const float4 v = reinterpret_cast<const float4*>(p)[a];
+      if (4 * a + 0 < TM) o[4 * a + 0 < TM ? 4 * a + 0 : 0] = v.x;
+      if (4 * a + 1 < TM) o[4 * a + 1 < TM ? 4 * a + 1 : 0] = v.y;
+      if (4 * a + 2 < TM) o[4 * a + 2 < TM ? 4 * a + 2 : 0] = v.z;
+      if (4 * a + 3 < TM) o[4 * a + 3 < TM ? 4 * a + 3 : 0] = v.w;
+    }
+  } else if constexpr (sizeof(T) == 4 && TMP % 2 == 0) {
+#pragma unroll
+    for (int a = 0; a < TMP / 2; ++a) {
+      const float2 v = reinterpret_cast<const float2*>(p)[a];
+      if (2 * a + 0 < TM) o[2 * a + 0 < TM ? 2 * a + 0 : 0] = v.x;
+      if (2 * a + 1 < TM) o[2 * a + 1 < TM ? 2 * a + 1 : 0] = v.y;
+    }
+  } else if constexpr (sizeof(T) == 8 && TMP % 2 == 0) {
+#pragma unroll
+    for (int a = 0; a < TMP / 2; ++a) {
+      const double2 v = reinterpret_cast<const double2*>(p)[a];
+      if (2 * a + 0 < TM) o[2 * a + 0 < TM ? 2 * a + 0 : 0] = v.x;
+      if (2 * a + 1 < TM) o[2 * a + 1 < TM ? 2 * a + 1 : 0] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < TM; ++a) o[a] = p[a];
+  }
+}
+
+// Basis of a neighbouring element whose degree pk is known only at run time:
+// dispatch to the compiled degree and hand each function to sink(i, Phi, D).
+template <int D, int PK, typename T, typename Sink>
+__device__ __forceinline__ void nbr_basis_p(const T* xi, Sink& sink) {
+  constexpr int N = nbasis(D, PK);
+  T Phi[N], Dd[D][N];
+  basis_eval<D, PK, T>(xi, Phi, Dd);
+#pragma unroll
+  for (int i = 0; i < N; ++i) {
+    T dv[D];
+#pragma unroll
+    for (int d = 0; d < D; ++d) dv[d] = Dd[d][i];
+    sink(i, Phi[i], dv);
+  }
+}
+
+template <int D, typename T, typename Sink>
+__device__ __forceinline__ void nbr_basis(int pk, const T* xi, Sink& sink) {
+  switch (pk) {
+    case 1: nbr_basis_p<D, 1, T>(xi, sink); break;
+    case 2: nbr_basis_p<D, 2, T>(xi, sink); break;
+    case 3: nbr_basis_p<D, 3, T>(xi, sink); break;
+    case 4: nbr_basis_p<D, 4, T>(xi, sink); break;
+    case 5: if constexpr (D == 2) nbr_basis_p<D, 5, T>(xi, sink); break;
+    case 6: if constexpr (D == 2) nbr_basis_p<D, 6, T>(xi, sink); break;
+    default: break;
+  }
+}
+
+// --------------------------------------------------------------------------
+// row kernel: the whole block row of G elements of degree P per warp
+// --------------------------------------------------------------------------
+
+// Shared-memory layout (bytes) for a given neighbour stride VS (the widest
+// neighbour block, rounded up to the column span TR*TM of one pass).
 template <int D, int P, typename T>
-struct ElemSmem {
+struct RowSmem {
   using Cfg = TileCfg<D, P>;
   static constexpr int C = ChunkCfg<D, T>::CW / Cfg::G > 0 ? ChunkCfg<D, T>::CW / Cfg::G : 1;
   static constexpr int NROWS = Cfg::G * C * Cfg::NT;
+  static constexpr int PT = 4 * D + 2;  // T parameters per element
+  static constexpr int PI = 16;         // int parameters per element
   static constexpr size_t rule_bytes = align_up(sizeof(T) * Cfg::QT * (D + 1), 16);
-  static constexpr size_t uv_bytes = sizeof(T) * NROWS * Cfg::ROW;  // U or V
-  static constexpr size_t r_bytes = align_up(sizeof(T) * NROWS, 16);
-  static constexpr size_t s_bytes = align_up(sizeof(T) * Cfg::G * Cfg::ROW, 16);
-  // per-element parameters: T[G][4D + 2] and int[G][8]
-  static constexpr size_t pt_bytes = align_up(sizeof(T) * Cfg::G * (4 * D + 2), 16);
-  static constexpr size_t pi_bytes = align_up(sizeof(int) * Cfg::G * 8, 16);
-  static constexpr size_t warp_bytes = 2 * uv_bytes + r_bytes + s_bytes + pt_bytes + pi_bytes;
-  static constexpr size_t total(int warps) { return rule_bytes + warps * warp_bytes; }
+  __host__ __device__ static constexpr int vs(int nmax) {
+    return (nmax + Cfg::TR * Cfg::TM - 1) / (Cfg::TR * Cfg::TM) * (Cfg::TR * Cfg::TM);
+  }
+  __host__ __device__ static constexpr size_t u_bytes() { return align_up(sizeof(T) * NROWS * Cfg::ROW, 16); }
+  __host__ __device__ static constexpr size_t v_bytes(int VS) {
+    return align_up(sizeof(T) * (NROWS * Cfg::ROW > Cfg::G * C * 2 * VS ? NROWS * Cfg::ROW : Cfg::G * C * 2 * VS), 16);
+  }
+  __host__ __device__ static constexpr size_t r_bytes() { return align_up(sizeof(T) * NROWS, 16); }
+  __host__ __device__ static constexpr size_t s_bytes(int VS) {
+    return align_up(sizeof(T) * Cfg::G * (Cfg::ROW + VS), 16);
+  }
+  __host__ __device__ static constexpr size_t p_bytes() {
+    return align_up(sizeof(T) * Cfg::G * PT, 16) + align_up(sizeof(int) * Cfg::G * PI, 16);
+  }
+  __host__ __device__ static constexpr size_t warp_bytes(int VS) {
+    return u_bytes() + v_bytes(VS) + r_bytes() + s_bytes(VS) + p_bytes();
+  }
+  __host__ __device__ static constexpr size_t total(int warps, int nmax) {
+    return rule_bytes + warps * warp_bytes(vs(nmax));
+  }
+};
+
+// Integer parameter slots per element (PI array).
+enum : int {
+  kPiElem = 0,   // element id (-1: empty slot)
+  kPiNvol,       // volume points
+  kPiNface,      // own-face points
+  kPiSub0,       // first sub-simplex
+  kPiHf0,        // first half face
+  kPiNhf,        // half faces
+  kPiRow0,       // first block of the BSR row
+  kPiNslot,      // off-diagonal blocks in the row
+  kPiDpos,       // position of the diagonal block in the row
+  kPiSBlk,       // current slot: block index
+  kPiSSide,      // current slot: side of this element in the interface
+  kPiSNk,        // current slot: neighbour basis size
+  kPiSPk,        // current slot: neighbour degree
+  kPiSF0,        // current slot: first face of the interface
+  kPiSQF,        // current slot: points per face
+  kPiSNpts,      // current slot: points of the interface
 };
 
 template <int D, int P, typename T>
 __global__ void __launch_bounds__(kWarps * 32)
-    elem_kernel(const DevMesh m, int mode, T* __restrict__ vals, T* __restrict__ rhs) {
+    row_kernel(const DevMesh m, int mode, T* __restrict__ vals, T* __restrict__ rhs) {
   using Cfg = TileCfg<D, P>;
-  using SM = ElemSmem<D, P, T>;
+  using SM = RowSmem<D, P, T>;
   constexpr int N = Cfg::N, TM = Cfg::TM, TR = Cfg::TR, TPE = Cfg::TPE, G = Cfg::G;
   constexpr int TMP = Cfg::TMP, ROW = Cfg::ROW, NT = Cfg::NT, QT = Cfg::QT, C = SM::C;
-  constexpr int SV = sub_vals(D), FV = side_vals(D);
-  // parameter slots (T): a'[D], b'[D], lo[D], L[D], c, a
-  constexpr int PT = 4 * D + 2;
+  constexpr int SV = sub_vals(D), FV = side_vals(D), PT = SM::PT, PI = SM::PI;
+  constexpr int NPASS_COLS = TR * TM;  // columns covered by one pass over a neighbour block
 
+  const int VS = SM::vs(m.nmax);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   T* rule = reinterpret_cast<T*>(smem_raw);
-  unsigned char* wbase = smem_raw + SM::rule_bytes + warp * SM::warp_bytes;
-  T* U = reinterpret_cast<T*>(wbase);
-  T* V = reinterpret_cast<T*>(wbase + SM::uv_bytes);
-  T* R = reinterpret_cast<T*>(wbase + 2 * SM::uv_bytes);
-  T* S = reinterpret_cast<T*>(wbase + 2 * SM::uv_bytes + SM::r_bytes);
-  T* PTv = reinterpret_cast<T*>(wbase + 2 * SM::uv_bytes + SM::r_bytes + SM::s_bytes);
-  int* PIv = reinterpret_cast<int*>(wbase + 2 * SM::uv_bytes + SM::r_bytes + SM::s_bytes + SM::pt_bytes);
+  unsigned char* wb = smem_raw + SM::rule_bytes + warp * SM::warp_bytes(VS);
+  T* U = reinterpret_cast<T*>(wb);
+  wb += SM::u_bytes();
+  T* V = reinterpret_cast<T*>(wb);
+  wb += SM::v_bytes(VS);
+  T* R = reinterpret_cast<T*>(wb);
+  wb += SM::r_bytes();
+  T* S = reinterpret_cast<T*>(wb);  // [G][ROW] own scaling, then [G][VS] neighbour scaling
+  T* SK = S + G * ROW;
+  wb += SM::s_bytes(VS);
+  T* PTv = reinterpret_cast<T*>(wb);
+  int* PIv = reinterpret_cast<int*>(wb + align_up(sizeof(T) * G * PT, 16));
 
   const T* vrule = pick<T>(m.rt.vol64, m.rt.vol32) + (size_t)m.rt.vol_off[P] * (D + 1);
   for (int i = threadIdx.x; i < QT * (D + 1); i += blockDim.x) rule[i] = vrule[i];
-  // zero U/V once: padding slots are never written afterwards
-  for (int i = lane; i < SM::NROWS * ROW; i += 32) {
-    U[i] = T(0);
-    V[i] = T(0);
-  }
+  // zero U / V once: padding slots of the tiles are never written afterwards
+  for (int i = lane; i < SM::NROWS * ROW; i += 32) U[i] = T(0);
+  for (int i = lane; i < (int)(SM::v_bytes(VS) / sizeof(T)); i += 32) V[i] = T(0);
   __syncthreads();
 
   const T* SG = pick<T>(m.sg64, m.sg32);
@@ -314,26 +417,30 @@ __global__ void __launch_bounds__(kWarps * 32)
 
   const int g_me = lane / TPE;
   const int tr = (lane % TPE) / TR, tc = lane % TR;
+  const bool lane_in_tile = g_me < G;
 
   for (int tile = blockIdx.x * kWarps + warp; tile < ntiles; tile += gridDim.x * kWarps) {
     const int gcount = min(G, count - tile * G);
     // ---- per-element setup (one lane per element), FP64 -> T
     if (lane < G) {
-      int* pi = PIv + lane * 8;
+      int* pi = PIv + lane * PI;
       T* pt = PTv + lane * PT;
       if (lane < gcount) {
         const int e = m.elem_perm[base + tile * G + lane];
         const double a = m.a[e];
-        pi[0] = e;
-        pi[1] = (m.eptr[e + 1] - m.eptr[e]) * QT;  // volume points
-        pi[2] = m.e_nqf[e];                         // face points
-        pi[3] = m.eptr[e];                          // first sub-simplex
-        pi[4] = m.hf_ptr[e];
-        pi[5] = m.hf_ptr[e + 1] - m.hf_ptr[e];
+        pi[kPiElem] = e;
+        pi[kPiNvol] = (m.eptr[e + 1] - m.eptr[e]) * QT;
+        pi[kPiNface] = m.e_nqf[e];
+        pi[kPiSub0] = m.eptr[e];
+        pi[kPiHf0] = m.hf_ptr[e];
+        pi[kPiNhf] = m.hf_ptr[e + 1] - m.hf_ptr[e];
+        pi[kPiRow0] = m.row_ptr[e];
+        pi[kPiNslot] = m.row_ptr[e + 1] - m.row_ptr[e] - 1;
+        pi[kPiDpos] = m.diag_blk[e] - m.row_ptr[e];
 #pragma unroll
         for (int d = 0; d < D; ++d) {
           const double L = m.L[d * m.ne + e], iL = 1.0 / L;
-          pt[d] = T(4.0 * a * iL * iL);      // a'_d
+          pt[d] = T(4.0 * a * iL * iL);         // a'_d
           pt[D + d] = T(2.0 * m.pb.b[d] * iL);  // b'_d
           pt[2 * D + d] = T(m.lo[d * m.ne + e]);
           pt[3 * D + d] = T(L);
@@ -341,33 +448,34 @@ __global__ void __launch_bounds__(kWarps * 32)
         pt[4 * D] = T(m.pb.c);
         pt[4 * D + 1] = T(a);
       } else {
-        pi[0] = -1;
-        pi[1] = 0;
-        pi[2] = 0;
+        pi[kPiElem] = -1;
+        pi[kPiNvol] = 0;
+        pi[kPiNface] = 0;
+        pi[kPiNslot] = 0;
       }
     }
     __syncwarp();
-    // scaling s_i of each element
     for (int idx = lane; idx < G * N; idx += 32) {
       const int g = idx / N, i = idx - g * N;
       if (g < gcount) {
         int al[3];
         basis_alpha<D>(i, al);
-        double s = 1.0;
-        const int e = PIv[g * 8];
+        double sc = 1.0;
+        const int e = PIv[g * PI + kPiElem];
 #pragma unroll
-        for (int d = 0; d < D; ++d) s *= (2.0 * al[d] + 1.0) / m.L[d * m.ne + e];
-        S[g * ROW + i] = T(sqrt(s));
+        for (int d = 0; d < D; ++d) sc *= (2.0 * al[d] + 1.0) / m.L[d * m.ne + e];
+        S[g * ROW + i] = T(sqrt(sc));
       }
     }
-    // chunk counts: max over the warp's elements
-    int nv_l = 0, nf_l = 0;
+    int nv_l = 0, nf_l = 0, ns_l = 0;
     if (lane < gcount) {
-      nv_l = (PIv[lane * 8 + 1] + C - 1) / C;
-      nf_l = (PIv[lane * 8 + 2] + C - 1) / C;
+      nv_l = (PIv[lane * PI + kPiNvol] + C - 1) / C;
+      nf_l = (PIv[lane * PI + kPiNface] + C - 1) / C;
+      ns_l = PIv[lane * PI + kPiNslot];
     }
     const int nvch = __reduce_max_sync(0xffffffffu, nv_l);
     const int nfch = __reduce_max_sync(0xffffffffu, nf_l);
+    const int nslot = __reduce_max_sync(0xffffffffu, ns_l);
     __syncwarp();
 
     T acc[TM][TM];
@@ -378,7 +486,7 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
       for (int b = 0; b < TM; ++b) acc[a][b] = T(0);
     }
-    const bool active = g_me < gcount;
+    const bool active = lane_in_tile && g_me < gcount;
 
     // ---- volume points
     if (mat_vol || do_rhs) {
@@ -388,10 +496,10 @@ __global__ void __launch_bounds__(kWarps * 32)
           const int row0 = (g * C + c) * NT;
           T* Ur = U + row0 * ROW;
           T* Vr = V + row0 * ROW;
-          if (g < gcount && q < PIv[g * 8 + 1]) {
+          if (g < gcount && q < PIv[g * PI + kPiNvol]) {
             const T* pt = PTv + g * PT;
             const int t = q / QT, r = q - t * QT;
-            const int sub = PIv[g * 8 + 3] + t;
+            const int sub = PIv[g * PI + kPiSub0] + t;
             T sv[SV];
 #pragma unroll
             for (int k = 0; k < SV; ++k) sv[k] = SG[(size_t)k * m.nsub + sub];
@@ -400,7 +508,7 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
             for (int d = 0; d < D; ++d) {
               T v = sv[d] + rr[0] * sv[D + d] + rr[1] * sv[2 * D + d];
-              if (D == 3) v += rr[2] * sv[3 * D + d];
+              if constexpr (D == 3) v += rr[2] * sv[3 * D + d];
               xi[d] = v;
             }
             const T W = rr[D] * sv[SV - 1];
@@ -443,14 +551,9 @@ __global__ void __launch_bounds__(kWarps * 32)
             const int row0 = (g_me * C + c) * NT;
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
-              const T* ur = U + (row0 + t) * ROW + tr * TMP;
-              const T* vr = V + (row0 + t) * ROW + tc * TMP;
               T u[TM], v[TM];
-#pragma unroll
-              for (int a = 0; a < TM; ++a) {
-                u[a] = ur[a];
-                v[a] = vr[a];
-              }
+              load_tile<T, TM, TMP>(U + (row0 + t) * ROW + tr * TMP, u);
+              load_tile<T, TM, TMP>(V + (row0 + t) * ROW + tc * TMP, v);
               if (mat_vol) {
 #pragma unroll
                 for (int a = 0; a < TM; ++a)
@@ -469,7 +572,7 @@ __global__ void __launch_bounds__(kWarps * 32)
       }
     }
 
-    // ---- own-face points
+    // ---- own-face points (diagonal-block face terms, boundary load terms)
     if (mat_face || do_rhs) {
       for (int ch = 0; ch < nfch; ++ch) {
         for (int idx = lane; idx < G * C; idx += 32) {
@@ -477,10 +580,9 @@ __global__ void __launch_bounds__(kWarps * 32)
           const int row0 = (g * C + c) * NT;
           T* Ur = U + row0 * ROW;
           T* Vr = V + row0 * ROW;
-          if (g < gcount && q < PIv[g * 8 + 2]) {
+          if (g < gcount && q < PIv[g * PI + kPiNface]) {
             const T* pt = PTv + g * PT;
-            // half face holding point q (binary search over the element's offsets)
-            int lo_ = PIv[g * 8 + 4], hi_ = lo_ + PIv[g * 8 + 5] - 1;
+            int lo_ = PIv[g * PI + kPiHf0], hi_ = lo_ + PIv[g * PI + kPiNhf] - 1;
             while (lo_ < hi_) {
               const int mid = (lo_ + hi_ + 1) >> 1;
               if (m.hf_qoff[mid] <= q)
@@ -499,7 +601,7 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
             for (int d = 0; d < D; ++d) {
               T v = fsd[(size_t)d * m.nf] + fr[0] * fsd[(size_t)(D + d) * m.nf];
-              if (D == 3) v += fr[1] * fsd[(size_t)(2 * D + d) * m.nf];
+              if constexpr (D == 3) v += fr[1] * fsd[(size_t)(2 * D + d) * m.nf];
               xi[d] = v;
               np[d] = fsd[(size_t)((D == 2 ? 2 : 3) * D + d) * m.nf];
             }
@@ -553,14 +655,9 @@ __global__ void __launch_bounds__(kWarps * 32)
             const int row0 = (g_me * C + c) * NT;
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
-              const T* ur = U + (row0 + t) * ROW + tr * TMP;
-              const T* vr = V + (row0 + t) * ROW + tc * TMP;
               T u[TM], v[TM];
-#pragma unroll
-              for (int a = 0; a < TM; ++a) {
-                u[a] = ur[a];
-                v[a] = vr[a];
-              }
+              load_tile<T, TM, TMP>(U + (row0 + t) * ROW + tr * TMP, u);
+              load_tile<T, TM, TMP>(V + (row0 + t) * ROW + tc * TMP, v);
               if (mat_face) {
 #pragma unroll
                 for (int a = 0; a < TM; ++a)
@@ -581,7 +678,7 @@ __global__ void __launch_bounds__(kWarps * 32)
 
     // ---- write the diagonal block and the load vector
     if (active) {
-      const int e = PIv[g_me * 8];
+      const int e = PIv[g_me * PI + kPiElem];
       const T* Sg = S + g_me * ROW;
       if (mat_vol || mat_face) {
         T* out = vals + m.blk_off[m.diag_blk[e]];
@@ -610,192 +707,173 @@ __global__ void __launch_bounds__(kWarps * 32)
         }
       }
     }
-    __syncwarp();
-  }
-}
 
-// --------------------------------------------------------------------------
-// interface kernel: the two off-diagonal blocks of one interface per warp
-// --------------------------------------------------------------------------
-
-template <int D, int PM, typename T>
-struct IfaceSmem {
-  static constexpr int NM = nbasis(D, PM);
-  // points per chunk (one per lane); halved where 32 would not fit 4 warps
-  static constexpr int CP = (size_t)kWarps * 4 * 32 * 2 * NM * sizeof(T) > 160 * 1024 ? 16 : 32;
-  static constexpr size_t arr = sizeof(T) * CP * 2 * NM;
-  static constexpr size_t warp_bytes = align_up(4 * arr + sizeof(T) * 2 * NM, 16);
-  static constexpr size_t total(int warps) { return warps * warp_bytes; }
-};
-
-template <int D, int PM, typename T>
-__global__ void __launch_bounds__(kWarps * 32) iface_kernel(const DevMesh m, T* __restrict__ vals) {
-  using SM = IfaceSmem<D, PM, T>;
-  constexpr int NM = SM::NM, CP = SM::CP, EPP = 16;
-  constexpr int FV = side_vals(D);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char* wb = smem_raw + warp * SM::warp_bytes;
-  T* U0 = reinterpret_cast<T*>(wb);
-  T* U1 = reinterpret_cast<T*>(wb + SM::arr);
-  T* V01 = reinterpret_cast<T*>(wb + 2 * SM::arr);
-  T* V10 = reinterpret_cast<T*>(wb + 3 * SM::arr);
-  T* S0 = reinterpret_cast<T*>(wb + 4 * SM::arr);
-  T* S1 = S0 + NM;
-
-  const T* FS = pick<T>(m.fs64, m.fs32);
-  const T* FSC = pick<T>(m.fsc64, m.fsc32);
-  const T* FR = pick<T>(m.rt.face64, m.rt.face32);
-  const int base = m.if_pstart[PM], count = m.if_pstart[PM + 1] - base;
-
-  for (int w = blockIdx.x * kWarps + warp; w < count; w += gridDim.x * kWarps) {
-    const int it = m.if_perm[base + w];
-    const int e0 = m.if_e0[it], e1 = m.if_e1[it];
-    const int n0 = nbasis(D, m.p[e0]), n1 = nbasis(D, m.p[e1]);
-    const T a0 = T(m.a[e0]), a1 = T(m.a[e1]);
-    const int fbeg = m.if_fptr[it], nfc = m.if_fptr[it + 1] - fbeg;
-    const int nq = m.f_nq[fbeg];
-    const int QF = D == 2 ? nq : nq * nq;
-    const int npts = nfc * QF;
-    const int nch = (npts + CP - 1) / CP;
-    // scaling of both sides
-    for (int idx = lane; idx < n0 + n1; idx += 32) {
-      const int side = idx < n0 ? 0 : 1;
-      const int i = side ? idx - n0 : idx;
-      const int e = side ? e1 : e0;
-      int al[3];
-      basis_alpha<D>(i, al);
-      double s = 1.0;
-#pragma unroll
-      for (int d = 0; d < D; ++d) s *= (2.0 * al[d] + 1.0) / m.L[d * m.ne + e];
-      (side ? S1 : S0)[i] = T(sqrt(s));
-    }
-    const int nent = 2 * n0 * n1;
-    const int npass = (nent + 32 * EPP - 1) / (32 * EPP);
-
-    auto eval_chunk = [&](int ch) {
-      if (lane >= CP) return;
-      const int q = ch * CP + lane;
-      T* u0 = U0 + lane * 2 * NM;
-      T* u1 = U1 + lane * 2 * NM;
-      T* v01 = V01 + lane * 2 * NM;
-      T* v10 = V10 + lane * 2 * NM;
-      if (q < npts) {
-        const int f = fbeg + q / QF, lq = q - (q / QF) * QF;
-        const T* fr = FR + (size_t)(m.rt.face_off[nq] + lq) * (D == 2 ? 2 : 3);
-        const T W = fr[D == 2 ? 1 : 2] * FSC[f];
-        const T sig = FSC[(size_t)m.nf + f];
-        const T bn = FSC[(size_t)2 * m.nf + f];
-        T xi0[D], xi1[D], np0[D], np1[D];
-#pragma unroll
-        for (int d = 0; d < D; ++d) {
-          const T* f0 = FS + f;
-          const T* f1 = FS + (size_t)FV * m.nf + f;
-          T v0 = f0[(size_t)d * m.nf] + fr[0] * f0[(size_t)(D + d) * m.nf];
-          T v1 = f1[(size_t)d * m.nf] + fr[0] * f1[(size_t)(D + d) * m.nf];
-          if (D == 3) {
-            v0 += fr[1] * f0[(size_t)(2 * D + d) * m.nf];
-            v1 += fr[1] * f1[(size_t)(2 * D + d) * m.nf];
-          }
-          xi0[d] = v0;
-          xi1[d] = v1;
-          np0[d] = f0[(size_t)((D == 2 ? 2 : 3) * D + d) * m.nf];
-          np1[d] = f1[(size_t)((D == 2 ? 2 : 3) * D + d) * m.nf];
-        }
-        const T upn = bn < T(0) ? bn : T(0);
-        const T upp = bn > T(0) ? bn : T(0);
-        {
-          T Phi[NM], Dd[D][NM];
-          basis_eval<D, PM, T>(xi0, Phi, Dd);
-#pragma unroll
-          for (int i = 0; i < NM; ++i) {
-            T dn = T(0);
-#pragma unroll
-            for (int d = 0; d < D; ++d) dn += np0[d] * Dd[d][i];
-            u0[i] = Phi[i];
-            u0[NM + i] = dn;
-            v10[i] = W * (T(0.5) * a0 * dn - (sig + upp) * Phi[i]);
-            v10[NM + i] = W * (T(-0.5) * a1 * Phi[i]);
+    // ---- off-diagonal blocks of the row: one per neighbour (interface)
+    if (mat_face) {
+      for (int sl = 0; sl < nslot; ++sl) {
+        __syncwarp();
+        if (lane < G) {
+          int* pi = PIv + lane * PI;
+          if (lane < gcount && sl < pi[kPiNslot]) {
+            const int e = pi[kPiElem];
+            const int bk = pi[kPiRow0] + sl + (sl >= pi[kPiDpos] ? 1 : 0);
+            const int it = m.blk_if[bk];
+            const int k = m.col[bk];
+            const int pk = m.p[k];
+            const int f0 = m.if_fptr[it];
+            const int nq = m.f_nq[f0];
+            const int qf = D == 2 ? nq : nq * nq;
+            pi[kPiSBlk] = bk;
+            pi[kPiSSide] = m.if_e0[it] == e ? 0 : 1;
+            pi[kPiSPk] = pk;
+            pi[kPiSNk] = nbasis(D, pk);
+            pi[kPiSF0] = f0;
+            pi[kPiSQF] = qf;
+            pi[kPiSNpts] = (m.if_fptr[it + 1] - f0) * qf;
+            PTv[lane * PT + 4 * D] = T(m.a[k]);  // neighbour diffusion (slot c is free here)
+          } else {
+            pi[kPiSNk] = 0;
+            pi[kPiSNpts] = 0;
           }
         }
-        {
-          T Phi[NM], Dd[D][NM];
-          basis_eval<D, PM, T>(xi1, Phi, Dd);
+        __syncwarp();
+        // neighbour scaling s_j
+        for (int idx = lane; idx < G * VS; idx += 32) {
+          const int g = idx / VS, j = idx - g * VS;
+          if (g < gcount && j < PIv[g * PI + kPiSNk]) {
+            const int k = m.col[PIv[g * PI + kPiSBlk]];
+            int al[3];
+            basis_alpha<D>(j, al);
+            double sc = 1.0;
 #pragma unroll
-          for (int i = 0; i < NM; ++i) {
-            T dn = T(0);
-#pragma unroll
-            for (int d = 0; d < D; ++d) dn += np1[d] * Dd[d][i];
-            u1[i] = Phi[i];
-            u1[NM + i] = dn;
-            v01[i] = W * (T(-0.5) * a1 * dn - (sig - upn) * Phi[i]);
-            v01[NM + i] = W * (T(0.5) * a0 * Phi[i]);
+            for (int d = 0; d < D; ++d) sc *= (2.0 * al[d] + 1.0) / m.L[d * m.ne + k];
+            SK[g * VS + j] = T(sqrt(sc));
           }
         }
-      } else {
-#pragma unroll
-        for (int i = 0; i < 2 * NM; ++i) {
-          v01[i] = T(0);
-          v10[i] = T(0);
+        int np_l = 0, pc_l = 0;
+        if (lane < gcount) {
+          np_l = (PIv[lane * PI + kPiSNpts] + C - 1) / C;
+          pc_l = ((PIv[lane * PI + kPiSNk] + TM - 1) / TM + TR - 1) / TR;
         }
-      }
-    };
+        const int nch = __reduce_max_sync(0xffffffffu, np_l);
+        const int npass = __reduce_max_sync(0xffffffffu, pc_l);
+        __syncwarp();
 
-    if (nch == 1) eval_chunk(0);
-    __syncwarp();
-    T* out01 = vals + m.blk_off[m.if_slot01[it]];
-    T* out10 = vals + m.blk_off[m.if_slot10[it]];
-    for (int pass = 0; pass < npass; ++pass) {
-      T acc[EPP];
-      int ii[EPP], jj[EPP];
+        for (int pass = 0; pass < npass; ++pass) {
 #pragma unroll
-      for (int k = 0; k < EPP; ++k) {
-        acc[k] = T(0);
-        const int ent = pass * 32 * EPP + k * 32 + lane;
-        if (ent < n0 * n1) {
-          ii[k] = ent / n1;
-          jj[k] = ent - ii[k] * n1;
-        } else if (ent < nent) {
-          const int e2 = ent - n0 * n1;
-          ii[k] = e2 / n0;
-          jj[k] = e2 - ii[k] * n0;
-        } else {
-          ii[k] = 0;
-          jj[k] = 0;
-        }
-      }
-      for (int ch = 0; ch < nch; ++ch) {
-        if (nch > 1) {
-          __syncwarp();
-          eval_chunk(ch);
-          __syncwarp();
-        }
-        const int cnt = min(CP, npts - ch * CP);
+          for (int a = 0; a < TM; ++a)
 #pragma unroll
-        for (int k = 0; k < EPP; ++k) {
-          const int ent = pass * 32 * EPP + k * 32 + lane;
-          if (ent < nent) {
-            const bool first = ent < n0 * n1;
-            const T* Ua = first ? U0 : U1;
-            const T* Vb = first ? V01 : V10;
-            T s = acc[k];
-            for (int c = 0; c < cnt; ++c) {
-              const T* ur = Ua + c * 2 * NM;
-              const T* vr = Vb + c * 2 * NM;
-              s = fma(ur[ii[k]], vr[jj[k]], s);
-              s = fma(ur[NM + ii[k]], vr[NM + jj[k]], s);
+            for (int b = 0; b < TM; ++b) acc[a][b] = T(0);
+          const int col0 = (pass * TR + tc) * TM;
+          for (int ch = 0; ch < nch; ++ch) {
+            if (pass == 0 || nch > 1) {
+              __syncwarp();
+              for (int idx = lane; idx < G * C; idx += 32) {
+                const int g = idx / C, c = idx - g * C, q = ch * C + c;
+                const int rowu = (g * C + c) * 2;
+                T* Ur = U + rowu * ROW;
+                T* Vr = V + (size_t)rowu * VS;
+                const int* pi = PIv + g * PI;
+                if (g < gcount && q < pi[kPiSNpts]) {
+                  const int qf = pi[kPiSQF];
+                  const int f = pi[kPiSF0] + q / qf, lq = q - (q / qf) * qf;
+                  const int se = pi[kPiSSide], sk = 1 - se;
+                  const int nq = m.f_nq[f];
+                  const T* fr = FR + (size_t)(m.rt.face_off[nq] + lq) * (D == 2 ? 2 : 3);
+                  const T* fe = FS + (size_t)se * FV * m.nf + f;
+                  const T* fk = FS + (size_t)sk * FV * m.nf + f;
+                  const T sgn = se == 0 ? T(1) : T(-1);
+                  T xe[D], xk[D], ne_[D], nk_[D];
+#pragma unroll
+                  for (int d = 0; d < D; ++d) {
+                    T v0 = fe[(size_t)d * m.nf] + fr[0] * fe[(size_t)(D + d) * m.nf];
+                    T v1 = fk[(size_t)d * m.nf] + fr[0] * fk[(size_t)(D + d) * m.nf];
+                    if constexpr (D == 3) {
+                      v0 += fr[1] * fe[(size_t)(2 * D + d) * m.nf];
+                      v1 += fr[1] * fk[(size_t)(2 * D + d) * m.nf];
+                    }
+                    xe[d] = v0;
+                    xk[d] = v1;
+                    ne_[d] = sgn * fe[(size_t)((D == 2 ? 2 : 3) * D + d) * m.nf];
+                    nk_[d] = sgn * fk[(size_t)((D == 2 ? 2 : 3) * D + d) * m.nf];
+                  }
+                  const T W = fr[D == 2 ? 1 : 2] * FSC[f];
+                  const T sig = FSC[(size_t)m.nf + f];
+                  const T bn = sgn * FSC[(size_t)2 * m.nf + f];
+                  const T upw = bn < T(0) ? bn : T(0);
+                  const T ae = PTv[g * PT + 4 * D + 1];
+                  const T ak = PTv[g * PT + 4 * D];
+                  {
+                    T Phi[N], Dd[D][N];
+                    basis_eval<D, P, T>(xe, Phi, Dd);
+#pragma unroll
+                    for (int i = 0; i < N; ++i) {
+                      const int pos = (i / TM) * TMP + (i % TM);
+                      T dn = T(0);
+#pragma unroll
+                      for (int d = 0; d < D; ++d) dn += ne_[d] * Dd[d][i];
+                      Ur[pos] = Phi[i];
+                      Ur[ROW + pos] = dn;
+                    }
+                  }
+                  auto sink = [&](int j, T phik, const T* dk) {
+                    T dn = T(0);
+#pragma unroll
+                    for (int d = 0; d < D; ++d) dn += nk_[d] * dk[d];
+                    Vr[j] = W * (T(-0.5) * ak * dn + (upw - sig) * phik);
+                    Vr[VS + j] = W * (T(0.5) * ae * phik);
+                  };
+                  nbr_basis<D, T>(pi[kPiSPk], xk, sink);
+                } else {
+                  for (int j = 0; j < VS; ++j) {
+                    Vr[j] = T(0);
+                    Vr[VS + j] = T(0);
+                  }
+                }
+              }
+              __syncwarp();
             }
-            acc[k] = s;
-          }
-        }
-      }
+            if (active) {
+              const int cnt = C;
+#pragma unroll 1
+              for (int c = 0; c < cnt; ++c) {
+                const int rowu = (g_me * C + c) * 2;
 #pragma unroll
-      for (int k = 0; k < EPP; ++k) {
-        const int ent = pass * 32 * EPP + k * 32 + lane;
-        if (ent < n0 * n1) {
-          out01[ent] = S0[ii[k]] * S1[jj[k]] * acc[k];
-        } else if (ent < nent) {
-          out10[ent - n0 * n1] = S1[ii[k]] * S0[jj[k]] * acc[k];
+                for (int t = 0; t < 2; ++t) {
+                  T u[TM], v[TM];
+                  load_tile<T, TM, TMP>(U + (rowu + t) * ROW + tr * TMP, u);
+                  const T* vr = V + (size_t)(rowu + t) * VS + col0;
+#pragma unroll
+                  for (int b = 0; b < TM; ++b) v[b] = vr[b];
+#pragma unroll
+                  for (int a = 0; a < TM; ++a)
+#pragma unroll
+                    for (int b = 0; b < TM; ++b) acc[a][b] = fma(u[a], v[b], acc[a][b]);
+                }
+              }
+            }
+          }
+          // write this pass's columns of the off-diagonal block
+          if (active) {
+            const int* pi = PIv + g_me * PI;
+            const int nk = pi[kPiSNk];
+            if (nk > 0 && col0 < nk) {
+              T* out = vals + m.blk_off[pi[kPiSBlk]];
+              const T* Sg = S + g_me * ROW;
+              const T* Sk = SK + g_me * VS;
+#pragma unroll
+              for (int a = 0; a < TM; ++a) {
+                const int i = tr * TM + a;
+                if (i < N) {
+#pragma unroll
+                  for (int b = 0; b < TM; ++b) {
+                    const int j = col0 + b;
+                    if (j < nk) out[i * nk + j] = Sg[i] * Sk[j] * acc[a][b];
+                  }
+                }
+              }
+            }
+          }
         }
       }
     }

@@ -159,7 +159,8 @@ __global__ void face_geom_kernel(DevMesh m) {
     }
     const double c[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
     const double len = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
-    for (int d = 0; d < 3; ++d) n[d] = c[d] / len;  // vertex order makes this point out of e0
+    const double sg = m.f_flip[f] ? -1.0 : 1.0;  // point out of e0
+    for (int d = 0; d < 3; ++d) n[d] = sg * c[d] / len;
     J = len;                                         // = 2 |F| (collapsed triangle rule)
   }
   constexpr int FV = side_vals(D);

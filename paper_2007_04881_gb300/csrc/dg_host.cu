@@ -252,7 +252,8 @@ int upload(DevBuf& b, const T** out, const std::vector<T>& v) {
 struct HalfFace {
   int key[3];
   int elem;
-  int v[3];  // oriented vertices (2D: v[0], v[1])
+  int v[3];   // vertices in the element's order (2D: v[0] -> v[1] along its CCW loop)
+  bool flip;  // 3D: (v1-v0) x (v2-v0) points into the element
 };
 
 bool key_less(const HalfFace& a, const HalfFace& b) {
@@ -269,21 +270,22 @@ struct FaceRec {
   int e0, e1;
   int v[3];
   int key[3];
+  bool flip;
 };
 
 }  // namespace
 
 struct Plan {
-  std::vector<int> sub_elem, if_e0, if_e1, if_fptr, row_ptr, col, diag_blk, slot01, slot10;
+  std::vector<int> sub_elem, if_e0, if_e1, if_fptr, row_ptr, col, diag_blk, slot01, slot10, blk_if;
   std::vector<int64_t> blk_off, dof_off;
   std::vector<FaceRec> F;
   std::vector<int> f_e0, f_e1, f_v, f_nq, hf_ptr, hf_face, hf_qoff, e_nqf, uvptr, uvidx, elem_perm, if_perm;
-  std::vector<int8_t> hf_side;
+  std::vector<int8_t> hf_side, f_flip;
   int elem_pstart[9] = {0}, if_pstart[9] = {0};
   int nsub = 0, nf = 0, nint = 0, ni = 0, nhf = 0;
   int64_t nqvol = 0, nqface = 0;
-  // algorithmic flops / words per launch group [kind][p] (kind 0 element
-  // kernels with load vector, 1 interface kernels)
+  // algorithmic flops / words per launch group [kind][p] (kind 0: row
+  // kernel of degree p, whole block rows and load vector)
   double flops[2][9] = {{0}}, words[2][9] = {{0}};
 };
 
@@ -428,7 +430,9 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P) {
             w[q] = X[q][tv[o]] - X[q][h.v[0]];
           }
           const double cr[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
-          if (cr[0] * w[0] + cr[1] * w[1] + cr[2] * w[2] > 0.0) std::swap(h.v[1], h.v[2]);
+          // keep the tetrahedron's vertex order (the face rule is applied in
+          // this order); record whether the right-hand normal points inward
+          h.flip = cr[0] * w[0] + cr[1] * w[1] + cr[2] * w[2] > 0.0;
           int kk[3] = {h.v[0], h.v[1], h.v[2]};
           std::sort(kk, kk + 3);
           for (int q = 0; q < 3; ++q) h.key[q] = kk[q];
@@ -456,6 +460,7 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P) {
         f.v[q] = H[i].v[q];
         f.key[q] = H[i].key[q];
       }
+      f.flip = H[i].flip;
       if (dim == 2 && cnt == 2 && !(H[i].v[0] == H[i + 1].v[1] && H[i].v[1] == H[i + 1].v[0]))
         return fail(DG_ERR_MESH, "elements %d and %d traverse their common edge in the same direction", f.e0, f.e1);
       F.push_back(f);
@@ -522,15 +527,19 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P) {
   std::vector<int>&slot01 = P.slot01, &slot10 = P.slot10;
   slot01.assign(ni, 0);
   slot10.assign(ni, 0);
+  P.blk_if.assign(m->row_ptr[ne], -1);
   for (int i = 0; i < ni; ++i) {
     slot01[i] = slot(if_e0[i], if_e1[i]);
     slot10[i] = slot(if_e1[i], if_e0[i]);
+    P.blk_if[slot01[i]] = i;
+    P.blk_if[slot10[i]] = i;
   }
   m->dof_off.assign(ne + 1, 0);
   for (int e = 0; e < ne; ++e) m->dof_off[e + 1] = m->dof_off[e] + nb[e];
 
   // --- half faces (element -> faces, global face order) and face points
   std::vector<int>&f_e0 = P.f_e0, &f_e1 = P.f_e1, &f_v = P.f_v, &f_nq = P.f_nq;
+  P.f_flip.assign(nf, 0);
   f_e0.assign(nf, 0);
   f_e1.assign(nf, 0);
   f_v.assign((size_t)dim * nf, 0);
@@ -541,6 +550,7 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P) {
     f_e0[f] = F[f].e0;
     f_e1[f] = F[f].e1;
     for (int q = 0; q < dim; ++q) f_v[(size_t)dim * f + q] = F[f].v[q];
+    P.f_flip[f] = F[f].flip ? 1 : 0;
     const int pm = F[f].e1 >= 0 ? std::max(d->p[F[f].e0], d->p[F[f].e1]) : d->p[F[f].e0];
     f_nq[f] = pm + 1;
     nqface += dim == 2 ? f_nq[f] : f_nq[f] * f_nq[f];
@@ -631,8 +641,8 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P) {
   // [b or c != 0](n^2 + n(d+1)) + basis n d^2 + 5 d p; own interior-face
   // point 3 n^2 + [b != 0] n^2/2 + basis; boundary-face point 3 n^2 +
   // [b != 0] n^2 + basis; load vector n per volume point and 2n per boundary
-  // point.  Interface kernel: 6 n0 n1 + [b != 0] n0 n1 per face point (its
-  // basis values are counted once, in the element kernels).
+  // point.  Off-diagonal block (e, k): 3 n_e n_k + [b != 0] n_e n_k / 2 per
+  // interface point (each side's basis is counted once, with its own faces).
   {
     const bool advb = d->b[0] != 0.0 || d->b[1] != 0.0 || (dim == 3 && d->b[2] != 0.0);
     const bool adv = advb || d->c != 0.0;
@@ -657,16 +667,18 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P) {
       P.words[0][pe] += w;
     }
     for (int i = 0; i < ni; ++i) {
-      const int pm = std::max(d->p[if_e0[i]], d->p[if_e1[i]]);
-      const double n0 = nb[if_e0[i]], n1 = nb[if_e1[i]];
-      double fma = 0.0, w = 2 * n0 * n1;
-      for (int f = if_fptr[i]; f < if_fptr[i + 1]; ++f) {
-        const double qf = dim == 2 ? f_nq[f] : (double)f_nq[f] * f_nq[f];
-        fma += qf * (6 * n0 * n1 + (advb ? n0 * n1 : 0.0));
-        w += 2 * FV + 3;
+      for (int side = 0; side < 2; ++side) {
+        const int e = side == 0 ? if_e0[i] : if_e1[i], k = side == 0 ? if_e1[i] : if_e0[i];
+        const double ne_ = nb[e], nk = nb[k];
+        double fma = 0.0, w = ne_ * nk;
+        for (int f = if_fptr[i]; f < if_fptr[i + 1]; ++f) {
+          const double qf = dim == 2 ? f_nq[f] : (double)f_nq[f] * f_nq[f];
+          fma += qf * (3 * ne_ * nk + (advb ? ne_ * nk / 2 : 0.0));
+          w += 2 * FV + 3;
+        }
+        P.flops[0][d->p[e]] += 2.0 * fma;
+        P.words[0][d->p[e]] += w;
       }
-      P.flops[1][pm] += 2.0 * fma;
-      P.words[1][pm] += w;
     }
   }
   P.nsub = nsub;
@@ -777,6 +789,7 @@ int dg_mesh_upload(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
   up_i(&dm.f_e0, f_e0);
   up_i(&dm.f_e1, f_e1);
   up_i(&dm.f_v, f_v);
+  if (rc == DG_OK) rc = upload(B, &dm.f_flip, P.f_flip);
   {
     const int* p;
     up_i(&p, f_nq);
@@ -793,6 +806,11 @@ int dg_mesh_upload(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
   up_i(&dm.if_slot01, slot01);
   up_i(&dm.if_slot10, slot10);
   if (rc == DG_OK) rc = upload(B, &dm.blk_off, m->blk_off);
+  up_i(&dm.row_ptr, P.row_ptr);
+  up_i(&dm.col, P.col);
+  up_i(&dm.blk_if, P.blk_if);
+  dm.nmax = 0;
+  for (int e = 0; e < ne; ++e) dm.nmax = std::max(dm.nmax, nbasis(dim, d->p[e]));
   up_i(&dm.diag_blk, diag_blk);
   if (rc == DG_OK) rc = upload(B, &dm.dof_off, m->dof_off);
   up_i(&dm.elem_perm, elem_perm);
@@ -887,18 +905,17 @@ static int run_assembly(dg_ctx* ctx, const dg_mesh* mesh, int prec, int mode, vo
   Tracer* tr = &ctx->tracer;
   if (reset) trace_reset(ctx, mesh);
   int n = 0;
+  (void)iface;
   if (prec == DG_PREC_FP64) {
     double* v = static_cast<double*>(vals);
     double* r = static_cast<double*>(rhs);
-    n += m.dim == 2 ? launch_elem2d_f64(m, mode, v, r, ctx->sm_count, ctx->stream, tr)
-                    : launch_elem3d_f64(m, mode, v, r, ctx->sm_count, ctx->stream, tr);
-    if (iface) n += launch_iface_f64(m, v, ctx->sm_count, ctx->stream, tr);
+    n += m.dim == 2 ? launch_row2d_f64(m, mode, v, r, ctx->sm_count, ctx->stream, tr)
+                    : launch_row3d_f64(m, mode, v, r, ctx->sm_count, ctx->stream, tr);
   } else {
     float* v = static_cast<float*>(vals);
     float* r = static_cast<float*>(rhs);
-    n += m.dim == 2 ? launch_elem2d_f32(m, mode, v, r, ctx->sm_count, ctx->stream, tr)
-                    : launch_elem3d_f32(m, mode, v, r, ctx->sm_count, ctx->stream, tr);
-    if (iface) n += launch_iface_f32(m, v, ctx->sm_count, ctx->stream, tr);
+    n += m.dim == 2 ? launch_row2d_f32(m, mode, v, r, ctx->sm_count, ctx->stream, tr)
+                    : launch_row3d_f32(m, mode, v, r, ctx->sm_count, ctx->stream, tr);
   }
   ctx->last_launches = reset ? n : ctx->last_launches + n;
   DG_CUDA_TRY(cudaGetLastError());

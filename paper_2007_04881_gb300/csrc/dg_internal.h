@@ -77,7 +77,8 @@ struct DevMesh {
   // faces
   const int* f_e0;
   const int* f_e1;  // -1 on the boundary
-  const int* f_v;   // [nf][dim] vertex ids, ordered so the normal points out of e0
+  const int* f_v;   // [nf][dim] vertex ids in e0's order (2D: along e0's CCW loop; 3D: e0's tetrahedron)
+  const int8_t* f_flip;  // 3D: 1 if (v1-v0) x (v2-v0) points into e0
   double* fs64;     // [2][side_vals][nf]
   float* fs32;
   double* fsc64;  // [3][nf]: J (2D |F|, 3D 2|F|), sigma, b.n
@@ -96,9 +97,13 @@ struct DevMesh {
   const int* if_slot01;
   const int* if_slot10;
   // BSR
+  const int* row_ptr;  // [ne+1]
+  const int* col;      // [nnzb]
+  const int* blk_if;   // [nnzb] interface of an off-diagonal block, -1 on the diagonal
   const int64_t* blk_off;
   const int* diag_blk;
   const int64_t* dof_off;
+  int nmax;  // largest basis size in the mesh
   // work lists
   const int* elem_perm;  // elements grouped by degree, each group cost-descending
   int elem_pstart[9];    // group of degree p: elem_perm[elem_pstart[p] .. elem_pstart[p+1])
@@ -131,11 +136,10 @@ struct Tracer {
   LaunchRec* recs = nullptr;  // capacity cap, filled from n
   int cap = 0;
   int n = 0;
-  // per launch-group algorithmic counts, indexed [kind][p]; kind 0 = element
-  // kernel, 1 = interface kernel; bytes for an element size of 1 (scaled by
-  // sizeof(T) by the launcher) plus a fixed part in bytes64 for FP64 inputs
+  // per launch-group algorithmic counts, indexed [kind][p]; kind 0 = row
+  // kernel of degree p; words = values written + read, scaled by sizeof(T)
   const double* flops = nullptr;  // [2][9]
-  const double* words = nullptr;  // [2][9] values written + read (in elements of T)
+  const double* words = nullptr;  // [2][9]
   void begin(const char* name, int kind, int p, size_t tsize, cudaStream_t st);
   void end(cudaStream_t st);
 };
@@ -143,14 +147,9 @@ struct Tracer {
 // Launchers (defined in the kernel translation units).  Each returns the
 // number of kernel launches issued.
 int launch_geometry(const DevMesh& m, cudaStream_t st, Tracer* tr = nullptr);
-int launch_elem2d_f64(const DevMesh& m, int mode, double* vals, double* rhs, int sm_count, cudaStream_t st, Tracer* tr);
-int launch_elem2d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, cudaStream_t st, Tracer* tr);
-int launch_elem3d_f64(const DevMesh& m, int mode, double* vals, double* rhs, int sm_count, cudaStream_t st, Tracer* tr);
-int launch_elem3d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, cudaStream_t st, Tracer* tr);
-int launch_iface_f64(const DevMesh& m, double* vals, int sm_count, cudaStream_t st, Tracer* tr);
-int launch_iface_f32(const DevMesh& m, float* vals, int sm_count, cudaStream_t st, Tracer* tr);
-
-// Tile geometry of the element kernel of (dim, p): G elements per warp.
-int elem_tile_elems(int dim, int p);
+int launch_row2d_f64(const DevMesh& m, int mode, double* vals, double* rhs, int sm_count, cudaStream_t st, Tracer* tr);
+int launch_row2d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, cudaStream_t st, Tracer* tr);
+int launch_row3d_f64(const DevMesh& m, int mode, double* vals, double* rhs, int sm_count, cudaStream_t st, Tracer* tr);
+int launch_row3d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, cudaStream_t st, Tracer* tr);
 
 }  // namespace dg
