@@ -316,60 +316,389 @@ __device__ __forceinline__ void nbr_basis(int pk, const T* xi, Sink& sink) {
 }
 
 // --------------------------------------------------------------------------
-// row kernel: the whole block row of G elements of degree P per warp
+// common pieces of the row kernels
 // --------------------------------------------------------------------------
 
-// Shared-memory layout (bytes) for a given neighbour stride VS (the widest
-// neighbour block, rounded up to the column span TR*TM of one pass).
+// C_i = prod_d sqrt(2 alpha_d + 1): with R = 1/sqrt(|bbox|) the basis scale is
+// s_i = R C_i, so a block (e, k) is R_e R_k C_i C_j (U^T V)_ij.
+template <int D, typename T>
+__device__ __forceinline__ void fill_ctab(T* ctab, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int al[3];
+    basis_alpha<D>(i, al);
+    double c = 1.0;
+#pragma unroll
+    for (int d = 0; d < D; ++d) c *= 2.0 * al[d] + 1.0;
+    ctab[i] = T(sqrt(c));
+  }
+}
+
+// per-element parameters in T, read from the contraction-precision record
+template <int D, typename T>
+struct ElemPar {
+  T ap[D], bp[D], lo[D], L[D];
+  T c, a, R;
+};
+
+template <int D, typename T>
+__device__ __forceinline__ void load_elem_par(const DevMesh& m, int e, ElemPar<D, T>& q) {
+  const T* EG = pick<T>(m.eg64, m.eg32);
+  const T a = T(m.a[e]);
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    const T iL = EG[(size_t)(2 * D + d) * m.ne + e];
+    q.lo[d] = EG[(size_t)d * m.ne + e];
+    q.L[d] = EG[(size_t)(D + d) * m.ne + e];
+    q.ap[d] = T(4) * a * iL * iL;      // a'_d = 4 a / L_d^2
+    q.bp[d] = T(2 * m.pb.b[d]) * iL;  // b'_d = 2 b_d / L_d
+  }
+  q.c = T(m.pb.c);
+  q.a = a;
+  q.R = EG[(size_t)(3 * D) * m.ne + e];
+}
+
+// Quadrature point on a face side: xi in that side's frame and the scaled
+// normal n' (of n0, the normal out of the face's first element).
+template <int D, typename T>
+__device__ __forceinline__ void face_side_point(const T* __restrict__ FS, int nf, int f, int s, const T* fr, T* xi,
+                                                T* np) {
+  constexpr int FV = side_vals(D);
+  const T* fs = FS + (size_t)s * FV * nf + f;
+#pragma unroll
+  for (int d = 0; d < D; ++d) {
+    T v = fs[(size_t)d * nf] + fr[0] * fs[(size_t)(D + d) * nf];
+    if constexpr (D == 3) v += fr[1] * fs[(size_t)(2 * D + d) * nf];
+    xi[d] = v;
+    np[d] = fs[(size_t)(D * D + d) * nf];
+  }
+}
+
+// Per-point stride (in T) of the staged rows: the staging lane writes 16-byte
+// vectors (8-byte for float pairs); an odd stride in vector units keeps the
+// 8 (or 16) lanes of one store phase on distinct banks.
+template <typename T, int TMP>
+__host__ __device__ constexpr int point_stride(int words) {
+  if (sizeof(T) == 4 && TMP % 4 == 0) return (words + 3) / 4 % 2 ? (words + 3) / 4 * 4 : (words + 3) / 4 * 4 + 4;
+  // float2 or double2 units of 2 elements
+  return (words + 1) / 2 % 2 ? (words + 1) / 2 * 2 : (words + 1) / 2 * 2 + 2;
+}
+
+// store N values (compile-time indexed) as TR groups of TMP (TM used, the
+// rest zero), with 16-byte (or 8-byte) vector stores
+template <typename T, int N, int TM, int TMP, int TR>
+__device__ __forceinline__ void store_groups(T* __restrict__ dst, const T* v) {
+  if constexpr (sizeof(T) == 4 && TMP % 4 == 0) {
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+#pragma unroll
+      for (int q = 0; q < TMP / 4; ++q) {
+        T w[4];
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+          const int ll = 4 * q + l, i = r * TM + ll;
+          w[l] = (ll < TM && i < N) ? v[(ll < TM && i < N) ? i : 0] : T(0);
+        }
+        reinterpret_cast<float4*>(dst + r * TMP)[q] = make_float4(w[0], w[1], w[2], w[3]);
+      }
+  } else {
+#pragma unroll
+    for (int r = 0; r < TR; ++r)
+#pragma unroll
+      for (int q = 0; q < TMP / 2; ++q) {
+        T w[2];
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+          const int ll = 2 * q + l, i = r * TM + ll;
+          w[l] = (ll < TM && i < N) ? v[(ll < TM && i < N) ? i : 0] : T(0);
+        }
+        if constexpr (sizeof(T) == 4)
+          reinterpret_cast<float2*>(dst + r * TMP)[q] = make_float2(w[0], w[1]);
+        else
+          reinterpret_cast<double2*>(dst + r * TMP)[q] = make_double2(w[0], w[1]);
+      }
+  }
+}
+
+template <typename T, int TMP>
+__device__ __forceinline__ void zero_groups(T* __restrict__ dst, int words) {
+  if constexpr (sizeof(T) == 4 && TMP % 4 == 0) {
+    for (int q = 0; q < words / 4; ++q) reinterpret_cast<float4*>(dst)[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  } else if constexpr (sizeof(T) == 4) {
+    for (int q = 0; q < words / 2; ++q) reinterpret_cast<float2*>(dst)[q] = make_float2(0.f, 0.f);
+  } else {
+    for (int q = 0; q < words / 2; ++q) reinterpret_cast<double2*>(dst)[q] = make_double2(0.0, 0.0);
+  }
+}
+
+// --------------------------------------------------------------------------
+// lane kernel: one thread assembles the whole block row of one element
+// (degree 1: the n x n block fits in registers, no staging needed)
+// --------------------------------------------------------------------------
+
+template <int D, int P, int PK, typename T>
+__device__ __forceinline__ void lane_offdiag(const DevMesh& m, const ElemPar<D, T>& q, int it, int se, int k, int64_t off,
+                                             const T* __restrict__ FS, const T* __restrict__ FSC,
+                                             const T* __restrict__ FR, const T* ctab, T* __restrict__ vals) {
+  constexpr int N = nbasis(D, P), NK = nbasis(D, PK);
+  T acc[N][NK];
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < NK; ++j) acc[i][j] = T(0);
+  const T* EG = pick<T>(m.eg64, m.eg32);
+  const T ak = T(m.a[k]);
+  const T Rk = EG[(size_t)(3 * D) * m.ne + k];
+  const T sgn = se == 0 ? T(1) : T(-1);
+  for (int f = m.if_fptr[it]; f < m.if_fptr[it + 1]; ++f) {
+    const int nq = m.f_nq[f];
+    const int qf = D == 2 ? nq : nq * nq;
+    const T J = FSC[f], sig = FSC[(size_t)m.nf + f], bn = sgn * FSC[(size_t)2 * m.nf + f];
+    const T upw = bn < T(0) ? bn : T(0);
+    for (int lq = 0; lq < qf; ++lq) {
+      const T* fr = FR + (size_t)(m.rt.face_off[nq] + lq) * (D == 2 ? 2 : 3);
+      T xe[D], ne_[D], xk[D], nk_[D];
+      face_side_point<D, T>(FS, m.nf, f, se, fr, xe, ne_);
+      face_side_point<D, T>(FS, m.nf, f, 1 - se, fr, xk, nk_);
+      const T W = fr[D == 2 ? 1 : 2] * J;
+      T Pe[N], De[D][N], Pk[NK], Dk[D][NK];
+      basis_eval<D, P, T>(xe, Pe, De);
+      basis_eval<D, PK, T>(xk, Pk, Dk);
+      T dne[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        T v = T(0);
+#pragma unroll
+        for (int d = 0; d < D; ++d) v += sgn * ne_[d] * De[d][i];
+        dne[i] = v;
+      }
+#pragma unroll
+      for (int j = 0; j < NK; ++j) {
+        T dn = T(0);
+#pragma unroll
+        for (int d = 0; d < D; ++d) dn += sgn * nk_[d] * Dk[d][j];
+        const T v0 = W * (T(-0.5) * ak * dn + (upw - sig) * Pk[j]);
+        const T v1 = W * (T(0.5) * q.a * Pk[j]);
+#pragma unroll
+        for (int i = 0; i < N; ++i) acc[i][j] = fma(Pe[i], v0, fma(dne[i], v1, acc[i][j]));
+      }
+    }
+  }
+  T* out = vals + off;
+  const T RR = q.R * Rk;
+#pragma unroll
+  for (int i = 0; i < N; ++i)
+#pragma unroll
+    for (int j = 0; j < NK; ++j) out[i * NK + j] = RR * ctab[i] * ctab[j] * acc[i][j];
+}
+
+template <int D, int P, typename T>
+__global__ void __launch_bounds__(kWarps * 32)
+    row_lane_kernel(const DevMesh m, int mode, T* __restrict__ vals, T* __restrict__ rhs) {
+  constexpr int N = nbasis(D, P), QT = ipow_c(P + 2, D), SV = sub_vals(D);
+  constexpr int NMAXC = nbasis(D, D == 2 ? kPMax2 : kPMax3);
+  __shared__ T rule[QT * (D + 1)];
+  __shared__ T ctab[NMAXC];
+  const T* vrule = pick<T>(m.rt.vol64, m.rt.vol32) + (size_t)m.rt.vol_off[P] * (D + 1);
+  for (int i = threadIdx.x; i < QT * (D + 1); i += blockDim.x) rule[i] = vrule[i];
+  fill_ctab<D, T>(ctab, NMAXC);
+  __syncthreads();
+  const T* SG = pick<T>(m.sg64, m.sg32);
+  const T* FS = pick<T>(m.fs64, m.fs32);
+  const T* FSC = pick<T>(m.fsc64, m.fsc32);
+  const T* FR = pick<T>(m.rt.face64, m.rt.face32);
+  const bool mat_vol = mode & kModeVol, mat_face = mode & kModeFace, do_rhs = mode & kModeRhs;
+  const bool accum = mode & kModeAccum;
+  const int base = m.elem_pstart[P], count = m.elem_pstart[P + 1] - base;
+
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < count; w += gridDim.x * blockDim.x) {
+    const int e = m.elem_perm[base + w];
+    ElemPar<D, T> q;
+    load_elem_par<D, T>(m, e, q);
+    T acc[N][N], racc[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+      racc[i] = T(0);
+#pragma unroll
+      for (int j = 0; j < N; ++j) acc[i][j] = T(0);
+    }
+    if (mat_vol || do_rhs) {
+      for (int sub = m.eptr[e]; sub < m.eptr[e + 1]; ++sub) {
+        T sv[SV];
+#pragma unroll
+        for (int k = 0; k < SV; ++k) sv[k] = SG[(size_t)k * m.nsub + sub];
+        for (int r = 0; r < QT; ++r) {
+          const T* rr = rule + r * (D + 1);
+          T xi[D];
+#pragma unroll
+          for (int d = 0; d < D; ++d) {
+            T v = sv[d] + rr[0] * sv[D + d] + rr[1] * sv[2 * D + d];
+            if constexpr (D == 3) v += rr[2] * sv[3 * D + d];
+            xi[d] = v;
+          }
+          const T W = rr[D] * sv[SV - 1];
+          T Phi[N], Dd[D][N];
+          basis_eval<D, P, T>(xi, Phi, Dd);
+          if (mat_vol) {
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+              T adv = q.c * Phi[j];
+              T vd[D];
+#pragma unroll
+              for (int d = 0; d < D; ++d) {
+                adv += q.bp[d] * Dd[d][j];
+                vd[d] = W * q.ap[d] * Dd[d][j];
+              }
+              adv *= W;
+#pragma unroll
+              for (int i = 0; i < N; ++i) {
+                T s = fma(Phi[i], adv, acc[i][j]);
+#pragma unroll
+                for (int d = 0; d < D; ++d) s = fma(Dd[d][i], vd[d], s);
+                acc[i][j] = s;
+              }
+            }
+          }
+          if (do_rhs) {
+            T x[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) x[d] = q.lo[d] + (xi[d] + T(1)) * T(0.5) * q.L[d];
+            const T fw = W * source_f<D, T>(m.pb, q.a, x);
+#pragma unroll
+            for (int i = 0; i < N; ++i) racc[i] = fma(Phi[i], fw, racc[i]);
+          }
+        }
+      }
+    }
+    if (mat_face || do_rhs) {
+      for (int hf = m.hf_ptr[e]; hf < m.hf_ptr[e + 1]; ++hf) {
+        const int f = m.hf_face[hf], s = m.hf_side[hf], nq = m.f_nq[f];
+        const int qf = D == 2 ? nq : nq * nq;
+        const bool bnd = m.f_e1[f] < 0;
+        if (!mat_face && !bnd) continue;
+        const T sgn = s == 0 ? T(1) : T(-1);
+        const T J = FSC[f], sig = FSC[(size_t)m.nf + f], bn = sgn * FSC[(size_t)2 * m.nf + f];
+        const T kap = bnd ? T(1) : T(0.5);
+        const T upw = bn < T(0) ? bn : T(0);
+        for (int lq = 0; lq < qf; ++lq) {
+          const T* fr = FR + (size_t)(m.rt.face_off[nq] + lq) * (D == 2 ? 2 : 3);
+          T xi[D], np[D];
+          face_side_point<D, T>(FS, m.nf, f, s, fr, xi, np);
+          const T W = fr[D == 2 ? 1 : 2] * J;
+          T Phi[N], Dd[D][N], dn[N];
+          basis_eval<D, P, T>(xi, Phi, Dd);
+#pragma unroll
+          for (int i = 0; i < N; ++i) {
+            T v = T(0);
+#pragma unroll
+            for (int d = 0; d < D; ++d) v += sgn * np[d] * Dd[d][i];
+            dn[i] = v;
+          }
+          if (mat_face) {
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+              const T v0 = W * (-kap * q.a * dn[j] + (sig - upw) * Phi[j]);
+              const T v1 = W * (-kap * q.a * Phi[j]);
+#pragma unroll
+              for (int i = 0; i < N; ++i) acc[i][j] = fma(Phi[i], v0, fma(dn[i], v1, acc[i][j]));
+            }
+          }
+          if (do_rhs && bnd) {
+            T x[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) x[d] = q.lo[d] + (xi[d] + T(1)) * T(0.5) * q.L[d];
+            const T gd = dirichlet_g<D, T>(m.pb, x);
+            const T r0 = W * (sig - upw) * gd, r1 = -W * q.a * gd;
+#pragma unroll
+            for (int i = 0; i < N; ++i) racc[i] = fma(Phi[i], r0, fma(dn[i], r1, racc[i]));
+          }
+        }
+      }
+    }
+    if (mat_vol || mat_face) {
+      T* out = vals + m.blk_off[m.diag_blk[e]];
+      const T RR = q.R * q.R;
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const T v = RR * ctab[i] * ctab[j] * acc[i][j];
+          out[i * N + j] = accum ? out[i * N + j] + v : v;
+        }
+    }
+    if (do_rhs) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) rhs[m.dof_off[e] + i] = q.R * ctab[i] * racc[i];
+    }
+    if (mat_face) {
+      for (int bk = m.row_ptr[e]; bk < m.row_ptr[e + 1]; ++bk) {
+        const int it = m.blk_if[bk];
+        if (it < 0) continue;
+        const int k = m.col[bk];
+        const int se = m.if_e0[it] == e ? 0 : 1;
+        const int64_t off = m.blk_off[bk];
+        switch (m.p[k]) {
+          case 1: lane_offdiag<D, P, 1, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
+          case 2: lane_offdiag<D, P, 2, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
+          case 3: lane_offdiag<D, P, 3, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
+          case 4: lane_offdiag<D, P, 4, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
+          case 5: if constexpr (D == 2) lane_offdiag<D, P, 5, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
+          case 6: if constexpr (D == 2) lane_offdiag<D, P, 6, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
+          default: break;
+        }
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// tile kernel: G elements of degree P per warp, each element's block held as
+// TM x TM register tiles by TPE threads; quadrature rows are staged in shared
+// memory by one lane per point and contracted by the tile threads
+// --------------------------------------------------------------------------
+
 template <int D, int P, typename T>
 struct RowSmem {
   using Cfg = TileCfg<D, P>;
-  static constexpr int C = ChunkCfg<D, T>::CW / Cfg::G > 0 ? ChunkCfg<D, T>::CW / Cfg::G : 1;
-  static constexpr int NROWS = Cfg::G * C * Cfg::NT;
-  static constexpr int PT = 4 * D + 2;  // T parameters per element
-  static constexpr int PI = 16;         // int parameters per element
-  static constexpr size_t rule_bytes = align_up(sizeof(T) * Cfg::QT * (D + 1), 16);
-  __host__ __device__ static constexpr int vs(int nmax) {
-    return (nmax + Cfg::TR * Cfg::TM - 1) / (Cfg::TR * Cfg::TM) * (Cfg::TR * Cfg::TM);
-  }
-  __host__ __device__ static constexpr size_t u_bytes() { return align_up(sizeof(T) * NROWS * Cfg::ROW, 16); }
+  static constexpr int G = Cfg::G, TM = Cfg::TM, TR = Cfg::TR, TMP = Cfg::TMP, ROW = Cfg::ROW, NT = Cfg::NT;
+  static constexpr int C = ChunkCfg<D, T>::CW / G > 0 ? ChunkCfg<D, T>::CW / G : 1;
+  static constexpr int PSU = point_stride<T, TMP>(NT * ROW);  // staged point: NT rows of ROW
+  static constexpr int PT = 4 * D + 5;                         // T parameters per element
+  static constexpr int PI = 16;                                // int parameters per element
+  static constexpr int NMAXC = nbasis(D, D == 2 ? kPMax2 : kPMax3);
+  __host__ __device__ static constexpr int vs(int nmax) { return (nmax + TR * TM - 1) / (TR * TM) * (TR * TM); }
+  __host__ __device__ static constexpr int psn(int VS) { return (2 * VS) % 2 ? 2 * VS : 2 * VS + 1; }  // odd
+  static constexpr size_t head_bytes = align_up(sizeof(T) * (Cfg::QT * (D + 1) + NMAXC), 16);
+  static constexpr size_t u_bytes = align_up(sizeof(T) * G * C * PSU, 16);
   __host__ __device__ static constexpr size_t v_bytes(int VS) {
-    return align_up(sizeof(T) * (NROWS * Cfg::ROW > Cfg::G * C * 2 * VS ? NROWS * Cfg::ROW : Cfg::G * C * 2 * VS), 16);
+    return align_up(sizeof(T) * (PSU > psn(VS) ? G * C * PSU : G * C * psn(VS)), 16);
   }
-  __host__ __device__ static constexpr size_t r_bytes() { return align_up(sizeof(T) * NROWS, 16); }
-  __host__ __device__ static constexpr size_t s_bytes(int VS) {
-    return align_up(sizeof(T) * Cfg::G * (Cfg::ROW + VS), 16);
-  }
-  __host__ __device__ static constexpr size_t p_bytes() {
-    return align_up(sizeof(T) * Cfg::G * PT, 16) + align_up(sizeof(int) * Cfg::G * PI, 16);
-  }
-  __host__ __device__ static constexpr size_t warp_bytes(int VS) {
-    return u_bytes() + v_bytes(VS) + r_bytes() + s_bytes(VS) + p_bytes();
-  }
-  __host__ __device__ static constexpr size_t total(int warps, int nmax) {
-    return rule_bytes + warps * warp_bytes(vs(nmax));
-  }
+  static constexpr size_t r_bytes = align_up(sizeof(T) * G * C * NT, 16);
+  static constexpr size_t p_bytes = align_up(sizeof(T) * G * PT, 16) + align_up(sizeof(int) * G * PI, 16);
+  __host__ __device__ static constexpr size_t warp_bytes(int VS) { return u_bytes + v_bytes(VS) + r_bytes + p_bytes; }
+  __host__ __device__ static constexpr size_t total(int warps, int nmax) { return head_bytes + warps * warp_bytes(vs(nmax)); }
 };
 
 // Integer parameter slots per element (PI array).
 enum : int {
-  kPiElem = 0,   // element id (-1: empty slot)
-  kPiNvol,       // volume points
-  kPiNface,      // own-face points
-  kPiSub0,       // first sub-simplex
-  kPiHf0,        // first half face
-  kPiNhf,        // half faces
-  kPiRow0,       // first block of the BSR row
-  kPiNslot,      // off-diagonal blocks in the row
-  kPiDpos,       // position of the diagonal block in the row
-  kPiSBlk,       // current slot: block index
-  kPiSSide,      // current slot: side of this element in the interface
-  kPiSNk,        // current slot: neighbour basis size
-  kPiSPk,        // current slot: neighbour degree
-  kPiSF0,        // current slot: first face of the interface
-  kPiSQF,        // current slot: points per face
-  kPiSNpts,      // current slot: points of the interface
+  kPiElem = 0,  // element id (-1: empty slot)
+  kPiNvol,      // volume points
+  kPiNface,     // own-face points
+  kPiSub0,      // first sub-simplex
+  kPiHf0,       // first half face
+  kPiNhf,       // half faces
+  kPiRow0,      // first block of the BSR row
+  kPiNslot,     // off-diagonal blocks in the row
+  kPiDpos,      // position of the diagonal block in the row
+  kPiSBlk,      // current slot: block index
+  kPiSSide,     // current slot: side of this element in the interface
+  kPiSNk,       // current slot: neighbour basis size
+  kPiSPk,       // current slot: neighbour degree
+  kPiSF0,       // current slot: first face of the interface
+  kPiSQF,       // current slot: points per face
+  kPiSNpts,     // current slot: points of the interface
 };
+// T parameter slots: a'[D], b'[D], lo[D], L[D], then:
+enum : int { kPtC = 0, kPtA = 1, kPtR = 2, kPtAk = 3, kPtRk = 4 };
 
 template <int D, int P, typename T>
 __global__ void __launch_bounds__(kWarps * 32)
@@ -378,37 +707,34 @@ __global__ void __launch_bounds__(kWarps * 32)
   using SM = RowSmem<D, P, T>;
   constexpr int N = Cfg::N, TM = Cfg::TM, TR = Cfg::TR, TPE = Cfg::TPE, G = Cfg::G;
   constexpr int TMP = Cfg::TMP, ROW = Cfg::ROW, NT = Cfg::NT, QT = Cfg::QT, C = SM::C;
-  constexpr int SV = sub_vals(D), FV = side_vals(D), PT = SM::PT, PI = SM::PI;
-  constexpr int NPASS_COLS = TR * TM;  // columns covered by one pass over a neighbour block
+  constexpr int SV = sub_vals(D), PT = SM::PT, PI = SM::PI, PSU = SM::PSU;
+  constexpr int X = 4 * D;  // first scalar slot in PT
 
-  const int VS = SM::vs(m.nmax);
+  const int VS = SM::vs(m.nmax), PSN = SM::psn(VS);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   T* rule = reinterpret_cast<T*>(smem_raw);
-  unsigned char* wb = smem_raw + SM::rule_bytes + warp * SM::warp_bytes(VS);
+  T* ctab = rule + QT * (D + 1);
+  unsigned char* wb = smem_raw + SM::head_bytes + warp * SM::warp_bytes(VS);
   T* U = reinterpret_cast<T*>(wb);
-  wb += SM::u_bytes();
+  wb += SM::u_bytes;
   T* V = reinterpret_cast<T*>(wb);
   wb += SM::v_bytes(VS);
   T* R = reinterpret_cast<T*>(wb);
-  wb += SM::r_bytes();
-  T* S = reinterpret_cast<T*>(wb);  // [G][ROW] own scaling, then [G][VS] neighbour scaling
-  T* SK = S + G * ROW;
-  wb += SM::s_bytes(VS);
+  wb += SM::r_bytes;
   T* PTv = reinterpret_cast<T*>(wb);
   int* PIv = reinterpret_cast<int*>(wb + align_up(sizeof(T) * G * PT, 16));
 
   const T* vrule = pick<T>(m.rt.vol64, m.rt.vol32) + (size_t)m.rt.vol_off[P] * (D + 1);
   for (int i = threadIdx.x; i < QT * (D + 1); i += blockDim.x) rule[i] = vrule[i];
-  // zero U / V once: padding slots of the tiles are never written afterwards
-  for (int i = lane; i < SM::NROWS * ROW; i += 32) U[i] = T(0);
-  for (int i = lane; i < (int)(SM::v_bytes(VS) / sizeof(T)); i += 32) V[i] = T(0);
+  fill_ctab<D, T>(ctab, SM::NMAXC);
   __syncthreads();
 
   const T* SG = pick<T>(m.sg64, m.sg32);
   const T* FS = pick<T>(m.fs64, m.fs32);
   const T* FSC = pick<T>(m.fsc64, m.fsc32);
   const T* FR = pick<T>(m.rt.face64, m.rt.face32);
+  const T* EG = pick<T>(m.eg64, m.eg32);
 
   const bool mat_vol = mode & kModeVol, mat_face = mode & kModeFace, do_rhs = mode & kModeRhs;
   const bool accum = mode & kModeAccum;
@@ -417,17 +743,16 @@ __global__ void __launch_bounds__(kWarps * 32)
 
   const int g_me = lane / TPE;
   const int tr = (lane % TPE) / TR, tc = lane % TR;
-  const bool lane_in_tile = g_me < G;
 
   for (int tile = blockIdx.x * kWarps + warp; tile < ntiles; tile += gridDim.x * kWarps) {
     const int gcount = min(G, count - tile * G);
-    // ---- per-element setup (one lane per element), FP64 -> T
+    __syncwarp();
+    // ---- per-element setup (one lane per element)
     if (lane < G) {
       int* pi = PIv + lane * PI;
       T* pt = PTv + lane * PT;
       if (lane < gcount) {
         const int e = m.elem_perm[base + tile * G + lane];
-        const double a = m.a[e];
         pi[kPiElem] = e;
         pi[kPiNvol] = (m.eptr[e + 1] - m.eptr[e]) * QT;
         pi[kPiNface] = m.e_nqf[e];
@@ -437,16 +762,18 @@ __global__ void __launch_bounds__(kWarps * 32)
         pi[kPiRow0] = m.row_ptr[e];
         pi[kPiNslot] = m.row_ptr[e + 1] - m.row_ptr[e] - 1;
         pi[kPiDpos] = m.diag_blk[e] - m.row_ptr[e];
+        ElemPar<D, T> q;
+        load_elem_par<D, T>(m, e, q);
 #pragma unroll
         for (int d = 0; d < D; ++d) {
-          const double L = m.L[d * m.ne + e], iL = 1.0 / L;
-          pt[d] = T(4.0 * a * iL * iL);         // a'_d
-          pt[D + d] = T(2.0 * m.pb.b[d] * iL);  // b'_d
-          pt[2 * D + d] = T(m.lo[d * m.ne + e]);
-          pt[3 * D + d] = T(L);
+          pt[d] = q.ap[d];
+          pt[D + d] = q.bp[d];
+          pt[2 * D + d] = q.lo[d];
+          pt[3 * D + d] = q.L[d];
         }
-        pt[4 * D] = T(m.pb.c);
-        pt[4 * D + 1] = T(a);
+        pt[X + kPtC] = q.c;
+        pt[X + kPtA] = q.a;
+        pt[X + kPtR] = q.R;
       } else {
         pi[kPiElem] = -1;
         pi[kPiNvol] = 0;
@@ -455,18 +782,6 @@ __global__ void __launch_bounds__(kWarps * 32)
       }
     }
     __syncwarp();
-    for (int idx = lane; idx < G * N; idx += 32) {
-      const int g = idx / N, i = idx - g * N;
-      if (g < gcount) {
-        int al[3];
-        basis_alpha<D>(i, al);
-        double sc = 1.0;
-        const int e = PIv[g * PI + kPiElem];
-#pragma unroll
-        for (int d = 0; d < D; ++d) sc *= (2.0 * al[d] + 1.0) / m.L[d * m.ne + e];
-        S[g * ROW + i] = T(sqrt(sc));
-      }
-    }
     int nv_l = 0, nf_l = 0, ns_l = 0;
     if (lane < gcount) {
       nv_l = (PIv[lane * PI + kPiNvol] + C - 1) / C;
@@ -476,7 +791,6 @@ __global__ void __launch_bounds__(kWarps * 32)
     const int nvch = __reduce_max_sync(0xffffffffu, nv_l);
     const int nfch = __reduce_max_sync(0xffffffffu, nf_l);
     const int nslot = __reduce_max_sync(0xffffffffu, ns_l);
-    __syncwarp();
 
     T acc[TM][TM];
     T racc[TM];
@@ -486,19 +800,19 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
       for (int b = 0; b < TM; ++b) acc[a][b] = T(0);
     }
-    const bool active = lane_in_tile && g_me < gcount;
+    const bool active = g_me < gcount;
 
     // ---- volume points
     if (mat_vol || do_rhs) {
       for (int ch = 0; ch < nvch; ++ch) {
         for (int idx = lane; idx < G * C; idx += 32) {
-          const int g = idx / C, c = idx - g * C, q = ch * C + c;
-          const int row0 = (g * C + c) * NT;
-          T* Ur = U + row0 * ROW;
-          T* Vr = V + row0 * ROW;
-          if (g < gcount && q < PIv[g * PI + kPiNvol]) {
+          const int g = idx / C, c = idx - g * C, qv = ch * C + c;
+          T* Ur = U + (size_t)(g * C + c) * PSU;
+          T* Vr = V + (size_t)(g * C + c) * PSU;
+          T* Rr = R + (g * C + c) * NT;
+          if (g < gcount && qv < PIv[g * PI + kPiNvol]) {
             const T* pt = PTv + g * PT;
-            const int t = q / QT, r = q - t * QT;
+            const int t = qv / QT, r = qv - t * QT;
             const int sub = PIv[g * PI + kPiSub0] + t;
             T sv[SV];
 #pragma unroll
@@ -514,46 +828,49 @@ __global__ void __launch_bounds__(kWarps * 32)
             const T W = rr[D] * sv[SV - 1];
             T Phi[N], Dd[D][N];
             basis_eval<D, P, T>(xi, Phi, Dd);
+            T Vv[N];
 #pragma unroll
             for (int i = 0; i < N; ++i) {
-              const int pos = (i / TM) * TMP + (i % TM);
-              Ur[pos] = Phi[i];
-              T adv = pt[4 * D] * Phi[i];
+              T adv = pt[X + kPtC] * Phi[i];
 #pragma unroll
-              for (int d = 0; d < D; ++d) {
-                Ur[(1 + d) * ROW + pos] = Dd[d][i];
-                adv += pt[D + d] * Dd[d][i];
-                Vr[(1 + d) * ROW + pos] = W * pt[d] * Dd[d][i];
-              }
-              Vr[pos] = W * adv;
+              for (int d = 0; d < D; ++d) adv += pt[D + d] * Dd[d][i];
+              Vv[i] = W * adv;
+            }
+            store_groups<T, N, TM, TMP, TR>(Ur, Phi);
+            store_groups<T, N, TM, TMP, TR>(Vr, Vv);
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+              const T s = W * pt[d];
+#pragma unroll
+              for (int i = 0; i < N; ++i) Vv[i] = s * Dd[d][i];
+              store_groups<T, N, TM, TMP, TR>(Ur + (1 + d) * ROW, Dd[d]);
+              store_groups<T, N, TM, TMP, TR>(Vr + (1 + d) * ROW, Vv);
             }
             if (do_rhs) {
               T x[D];
 #pragma unroll
               for (int d = 0; d < D; ++d) x[d] = pt[2 * D + d] + (xi[d] + T(1)) * T(0.5) * pt[3 * D + d];
-              R[row0] = W * source_f<D, T>(m.pb, pt[4 * D + 1], x);
+              Rr[0] = W * source_f<D, T>(m.pb, pt[X + kPtA], x);
 #pragma unroll
-              for (int d = 0; d < D; ++d) R[row0 + 1 + d] = T(0);
+              for (int d = 0; d < D; ++d) Rr[1 + d] = T(0);
             }
           } else {
+            zero_groups<T, TMP>(Vr, NT * ROW);
 #pragma unroll
-            for (int t = 0; t < NT; ++t) {
-#pragma unroll
-              for (int i = 0; i < N; ++i) Vr[t * ROW + (i / TM) * TMP + (i % TM)] = T(0);
-              R[row0 + t] = T(0);
-            }
+            for (int t = 0; t < NT; ++t) Rr[t] = T(0);
           }
         }
         __syncwarp();
         if (active) {
 #pragma unroll 1
           for (int c = 0; c < C; ++c) {
-            const int row0 = (g_me * C + c) * NT;
+            const T* Ub = U + (size_t)(g_me * C + c) * PSU + tr * TMP;
+            const T* Vb = V + (size_t)(g_me * C + c) * PSU + tc * TMP;
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
               T u[TM], v[TM];
-              load_tile<T, TM, TMP>(U + (row0 + t) * ROW + tr * TMP, u);
-              load_tile<T, TM, TMP>(V + (row0 + t) * ROW + tc * TMP, v);
+              load_tile<T, TM, TMP>(Ub + t * ROW, u);
+              load_tile<T, TM, TMP>(Vb + t * ROW, v);
               if (mat_vol) {
 #pragma unroll
                 for (int a = 0; a < TM; ++a)
@@ -561,7 +878,7 @@ __global__ void __launch_bounds__(kWarps * 32)
                   for (int b = 0; b < TM; ++b) acc[a][b] = fma(u[a], v[b], acc[a][b]);
               }
               if (do_rhs && tc == 0) {
-                const T rv = R[row0 + t];
+                const T rv = R[(g_me * C + c) * NT + t];
 #pragma unroll
                 for (int a = 0; a < TM; ++a) racc[a] = fma(u[a], rv, racc[a]);
               }
@@ -576,16 +893,16 @@ __global__ void __launch_bounds__(kWarps * 32)
     if (mat_face || do_rhs) {
       for (int ch = 0; ch < nfch; ++ch) {
         for (int idx = lane; idx < G * C; idx += 32) {
-          const int g = idx / C, c = idx - g * C, q = ch * C + c;
-          const int row0 = (g * C + c) * NT;
-          T* Ur = U + row0 * ROW;
-          T* Vr = V + row0 * ROW;
-          if (g < gcount && q < PIv[g * PI + kPiNface]) {
+          const int g = idx / C, c = idx - g * C, qv = ch * C + c;
+          T* Ur = U + (size_t)(g * C + c) * PSU;
+          T* Vr = V + (size_t)(g * C + c) * PSU;
+          T* Rr = R + (g * C + c) * NT;
+          if (g < gcount && qv < PIv[g * PI + kPiNface]) {
             const T* pt = PTv + g * PT;
             int lo_ = PIv[g * PI + kPiHf0], hi_ = lo_ + PIv[g * PI + kPiNhf] - 1;
             while (lo_ < hi_) {
               const int mid = (lo_ + hi_ + 1) >> 1;
-              if (m.hf_qoff[mid] <= q)
+              if (m.hf_qoff[mid] <= qv)
                 lo_ = mid;
               else
                 hi_ = mid - 1;
@@ -594,70 +911,63 @@ __global__ void __launch_bounds__(kWarps * 32)
             const int f = m.hf_face[hf];
             const int s = m.hf_side[hf];
             const int nq = m.f_nq[f];
-            const int lq = q - m.hf_qoff[hf];
+            const int lq = qv - m.hf_qoff[hf];
             const T* fr = FR + (size_t)(m.rt.face_off[nq] + lq) * (D == 2 ? 2 : 3);
-            const T* fsd = FS + (size_t)s * FV * m.nf + f;
             T xi[D], np[D];
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-              T v = fsd[(size_t)d * m.nf] + fr[0] * fsd[(size_t)(D + d) * m.nf];
-              if constexpr (D == 3) v += fr[1] * fsd[(size_t)(2 * D + d) * m.nf];
-              xi[d] = v;
-              np[d] = fsd[(size_t)((D == 2 ? 2 : 3) * D + d) * m.nf];
-            }
+            face_side_point<D, T>(FS, m.nf, f, s, fr, xi, np);
             const T sgn = s == 0 ? T(1) : T(-1);
             const T W = fr[D == 2 ? 1 : 2] * FSC[f];
             const T sig = FSC[(size_t)m.nf + f];
             const T bn = sgn * FSC[(size_t)2 * m.nf + f];
             const bool bnd = m.f_e1[f] < 0;
             const T kap = bnd ? T(1) : T(0.5);
-            const T a = pt[4 * D + 1];
+            const T a = pt[X + kPtA];
             const T upw = bn < T(0) ? bn : T(0);
-            T Phi[N], Dd[D][N];
+            T Phi[N], Dd[D][N], dn[N], V0[N], V1[N];
             basis_eval<D, P, T>(xi, Phi, Dd);
 #pragma unroll
             for (int i = 0; i < N; ++i) {
-              const int pos = (i / TM) * TMP + (i % TM);
-              T dn = T(0);
+              T v = T(0);
 #pragma unroll
-              for (int d = 0; d < D; ++d) dn += sgn * np[d] * Dd[d][i];
-              Ur[pos] = Phi[i];
-              Ur[ROW + pos] = dn;
-              Vr[pos] = W * (-kap * a * dn + (sig - upw) * Phi[i]);
-              Vr[ROW + pos] = W * (-kap * a * Phi[i]);
+              for (int d = 0; d < D; ++d) v += sgn * np[d] * Dd[d][i];
+              dn[i] = v;
+              V0[i] = W * (-kap * a * v + (sig - upw) * Phi[i]);
+              V1[i] = W * (-kap * a * Phi[i]);
             }
+            store_groups<T, N, TM, TMP, TR>(Ur, Phi);
+            store_groups<T, N, TM, TMP, TR>(Ur + ROW, dn);
+            store_groups<T, N, TM, TMP, TR>(Vr, V0);
+            store_groups<T, N, TM, TMP, TR>(Vr + ROW, V1);
             if (do_rhs) {
               if (bnd) {
                 T x[D];
 #pragma unroll
                 for (int d = 0; d < D; ++d) x[d] = pt[2 * D + d] + (xi[d] + T(1)) * T(0.5) * pt[3 * D + d];
                 const T gd = dirichlet_g<D, T>(m.pb, x);
-                R[row0] = W * (sig - upw) * gd;
-                R[row0 + 1] = -W * a * gd;
+                Rr[0] = W * (sig - upw) * gd;
+                Rr[1] = -W * a * gd;
               } else {
-                R[row0] = T(0);
-                R[row0 + 1] = T(0);
+                Rr[0] = T(0);
+                Rr[1] = T(0);
               }
             }
           } else {
-#pragma unroll
-            for (int t = 0; t < 2; ++t) {
-#pragma unroll
-              for (int i = 0; i < N; ++i) Vr[t * ROW + (i / TM) * TMP + (i % TM)] = T(0);
-              R[row0 + t] = T(0);
-            }
+            zero_groups<T, TMP>(Vr, 2 * ROW);
+            Rr[0] = T(0);
+            Rr[1] = T(0);
           }
         }
         __syncwarp();
         if (active) {
 #pragma unroll 1
           for (int c = 0; c < C; ++c) {
-            const int row0 = (g_me * C + c) * NT;
+            const T* Ub = U + (size_t)(g_me * C + c) * PSU + tr * TMP;
+            const T* Vb = V + (size_t)(g_me * C + c) * PSU + tc * TMP;
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
               T u[TM], v[TM];
-              load_tile<T, TM, TMP>(U + (row0 + t) * ROW + tr * TMP, u);
-              load_tile<T, TM, TMP>(V + (row0 + t) * ROW + tc * TMP, v);
+              load_tile<T, TM, TMP>(Ub + t * ROW, u);
+              load_tile<T, TM, TMP>(Vb + t * ROW, v);
               if (mat_face) {
 #pragma unroll
                 for (int a = 0; a < TM; ++a)
@@ -665,7 +975,7 @@ __global__ void __launch_bounds__(kWarps * 32)
                   for (int b = 0; b < TM; ++b) acc[a][b] = fma(u[a], v[b], acc[a][b]);
               }
               if (do_rhs && tc == 0) {
-                const T rv = R[row0 + t];
+                const T rv = R[(g_me * C + c) * NT + t];
 #pragma unroll
                 for (int a = 0; a < TM; ++a) racc[a] = fma(u[a], rv, racc[a]);
               }
@@ -679,19 +989,20 @@ __global__ void __launch_bounds__(kWarps * 32)
     // ---- write the diagonal block and the load vector
     if (active) {
       const int e = PIv[g_me * PI + kPiElem];
-      const T* Sg = S + g_me * ROW;
+      const T Re = PTv[g_me * PT + X + kPtR];
       if (mat_vol || mat_face) {
         T* out = vals + m.blk_off[m.diag_blk[e]];
+        const T RR = Re * Re;
 #pragma unroll
         for (int a = 0; a < TM; ++a) {
           const int i = tr * TM + a;
           if (i < N) {
-            const T si = Sg[i];
+            const T si = RR * ctab[i];
 #pragma unroll
             for (int b = 0; b < TM; ++b) {
               const int j = tc * TM + b;
               if (j < N) {
-                const T v = si * Sg[j] * acc[a][b];
+                const T v = si * ctab[j] * acc[a][b];
                 out[i * N + j] = accum ? out[i * N + j] + v : v;
               }
             }
@@ -703,7 +1014,7 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
         for (int a = 0; a < TM; ++a) {
           const int i = tr * TM + a;
-          if (i < N) out[i] = Sg[i] * racc[a];
+          if (i < N) out[i] = Re * ctab[i] * racc[a];
         }
       }
     }
@@ -730,26 +1041,14 @@ __global__ void __launch_bounds__(kWarps * 32)
             pi[kPiSF0] = f0;
             pi[kPiSQF] = qf;
             pi[kPiSNpts] = (m.if_fptr[it + 1] - f0) * qf;
-            PTv[lane * PT + 4 * D] = T(m.a[k]);  // neighbour diffusion (slot c is free here)
+            PTv[lane * PT + X + kPtAk] = T(m.a[k]);
+            PTv[lane * PT + X + kPtRk] = EG[(size_t)(3 * D) * m.ne + k];
           } else {
             pi[kPiSNk] = 0;
             pi[kPiSNpts] = 0;
           }
         }
         __syncwarp();
-        // neighbour scaling s_j
-        for (int idx = lane; idx < G * VS; idx += 32) {
-          const int g = idx / VS, j = idx - g * VS;
-          if (g < gcount && j < PIv[g * PI + kPiSNk]) {
-            const int k = m.col[PIv[g * PI + kPiSBlk]];
-            int al[3];
-            basis_alpha<D>(j, al);
-            double sc = 1.0;
-#pragma unroll
-            for (int d = 0; d < D; ++d) sc *= (2.0 * al[d] + 1.0) / m.L[d * m.ne + k];
-            SK[g * VS + j] = T(sqrt(sc));
-          }
-        }
         int np_l = 0, pc_l = 0;
         if (lane < gcount) {
           np_l = (PIv[lane * PI + kPiSNpts] + C - 1) / C;
@@ -757,7 +1056,6 @@ __global__ void __launch_bounds__(kWarps * 32)
         }
         const int nch = __reduce_max_sync(0xffffffffu, np_l);
         const int npass = __reduce_max_sync(0xffffffffu, pc_l);
-        __syncwarp();
 
         for (int pass = 0; pass < npass; ++pass) {
 #pragma unroll
@@ -769,57 +1067,43 @@ __global__ void __launch_bounds__(kWarps * 32)
             if (pass == 0 || nch > 1) {
               __syncwarp();
               for (int idx = lane; idx < G * C; idx += 32) {
-                const int g = idx / C, c = idx - g * C, q = ch * C + c;
-                const int rowu = (g * C + c) * 2;
-                T* Ur = U + rowu * ROW;
-                T* Vr = V + (size_t)rowu * VS;
+                const int g = idx / C, c = idx - g * C, qv = ch * C + c;
+                T* Ur = U + (size_t)(g * C + c) * PSU;
+                T* Vr = V + (size_t)(g * C + c) * PSN;
                 const int* pi = PIv + g * PI;
-                if (g < gcount && q < pi[kPiSNpts]) {
+                if (g < gcount && qv < pi[kPiSNpts]) {
                   const int qf = pi[kPiSQF];
-                  const int f = pi[kPiSF0] + q / qf, lq = q - (q / qf) * qf;
-                  const int se = pi[kPiSSide], sk = 1 - se;
+                  const int f = pi[kPiSF0] + qv / qf, lq = qv - (qv / qf) * qf;
+                  const int se = pi[kPiSSide];
                   const int nq = m.f_nq[f];
                   const T* fr = FR + (size_t)(m.rt.face_off[nq] + lq) * (D == 2 ? 2 : 3);
-                  const T* fe = FS + (size_t)se * FV * m.nf + f;
-                  const T* fk = FS + (size_t)sk * FV * m.nf + f;
-                  const T sgn = se == 0 ? T(1) : T(-1);
                   T xe[D], xk[D], ne_[D], nk_[D];
-#pragma unroll
-                  for (int d = 0; d < D; ++d) {
-                    T v0 = fe[(size_t)d * m.nf] + fr[0] * fe[(size_t)(D + d) * m.nf];
-                    T v1 = fk[(size_t)d * m.nf] + fr[0] * fk[(size_t)(D + d) * m.nf];
-                    if constexpr (D == 3) {
-                      v0 += fr[1] * fe[(size_t)(2 * D + d) * m.nf];
-                      v1 += fr[1] * fk[(size_t)(2 * D + d) * m.nf];
-                    }
-                    xe[d] = v0;
-                    xk[d] = v1;
-                    ne_[d] = sgn * fe[(size_t)((D == 2 ? 2 : 3) * D + d) * m.nf];
-                    nk_[d] = sgn * fk[(size_t)((D == 2 ? 2 : 3) * D + d) * m.nf];
-                  }
+                  face_side_point<D, T>(FS, m.nf, f, se, fr, xe, ne_);
+                  face_side_point<D, T>(FS, m.nf, f, 1 - se, fr, xk, nk_);
+                  const T sgn = se == 0 ? T(1) : T(-1);
                   const T W = fr[D == 2 ? 1 : 2] * FSC[f];
                   const T sig = FSC[(size_t)m.nf + f];
                   const T bn = sgn * FSC[(size_t)2 * m.nf + f];
                   const T upw = bn < T(0) ? bn : T(0);
-                  const T ae = PTv[g * PT + 4 * D + 1];
-                  const T ak = PTv[g * PT + 4 * D];
+                  const T ae = PTv[g * PT + X + kPtA];
+                  const T ak = PTv[g * PT + X + kPtAk];
                   {
-                    T Phi[N], Dd[D][N];
+                    T Phi[N], Dd[D][N], dn[N];
                     basis_eval<D, P, T>(xe, Phi, Dd);
 #pragma unroll
                     for (int i = 0; i < N; ++i) {
-                      const int pos = (i / TM) * TMP + (i % TM);
-                      T dn = T(0);
+                      T v = T(0);
 #pragma unroll
-                      for (int d = 0; d < D; ++d) dn += ne_[d] * Dd[d][i];
-                      Ur[pos] = Phi[i];
-                      Ur[ROW + pos] = dn;
+                      for (int d = 0; d < D; ++d) v += sgn * ne_[d] * Dd[d][i];
+                      dn[i] = v;
                     }
+                    store_groups<T, N, TM, TMP, TR>(Ur, Phi);
+                    store_groups<T, N, TM, TMP, TR>(Ur + ROW, dn);
                   }
                   auto sink = [&](int j, T phik, const T* dk) {
                     T dn = T(0);
 #pragma unroll
-                    for (int d = 0; d < D; ++d) dn += nk_[d] * dk[d];
+                    for (int d = 0; d < D; ++d) dn += sgn * nk_[d] * dk[d];
                     Vr[j] = W * (T(-0.5) * ak * dn + (upw - sig) * phik);
                     Vr[VS + j] = W * (T(0.5) * ae * phik);
                   };
@@ -834,17 +1118,16 @@ __global__ void __launch_bounds__(kWarps * 32)
               __syncwarp();
             }
             if (active) {
-              const int cnt = C;
 #pragma unroll 1
-              for (int c = 0; c < cnt; ++c) {
-                const int rowu = (g_me * C + c) * 2;
+              for (int c = 0; c < C; ++c) {
+                const T* Ub = U + (size_t)(g_me * C + c) * PSU + tr * TMP;
+                const T* Vb = V + (size_t)(g_me * C + c) * PSN + col0;
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
                   T u[TM], v[TM];
-                  load_tile<T, TM, TMP>(U + (rowu + t) * ROW + tr * TMP, u);
-                  const T* vr = V + (size_t)(rowu + t) * VS + col0;
+                  load_tile<T, TM, TMP>(Ub + t * ROW, u);
 #pragma unroll
-                  for (int b = 0; b < TM; ++b) v[b] = vr[b];
+                  for (int b = 0; b < TM; ++b) v[b] = Vb[t * VS + b];
 #pragma unroll
                   for (int a = 0; a < TM; ++a)
 #pragma unroll
@@ -853,22 +1136,22 @@ __global__ void __launch_bounds__(kWarps * 32)
               }
             }
           }
-          // write this pass's columns of the off-diagonal block
+          // this pass's columns of the off-diagonal block
           if (active) {
             const int* pi = PIv + g_me * PI;
             const int nk = pi[kPiSNk];
-            if (nk > 0 && col0 < nk) {
+            if (col0 < nk) {
               T* out = vals + m.blk_off[pi[kPiSBlk]];
-              const T* Sg = S + g_me * ROW;
-              const T* Sk = SK + g_me * VS;
+              const T RR = PTv[g_me * PT + X + kPtR] * PTv[g_me * PT + X + kPtRk];
 #pragma unroll
               for (int a = 0; a < TM; ++a) {
                 const int i = tr * TM + a;
                 if (i < N) {
+                  const T si = RR * ctab[i];
 #pragma unroll
                   for (int b = 0; b < TM; ++b) {
                     const int j = col0 + b;
-                    if (j < nk) out[i * nk + j] = Sg[i] * Sk[j] * acc[a][b];
+                    if (j < nk) out[i * nk + j] = si * ctab[j] * acc[a][b];
                   }
                 }
               }
@@ -877,7 +1160,6 @@ __global__ void __launch_bounds__(kWarps * 32)
         }
       }
     }
-    __syncwarp();
   }
 }
 

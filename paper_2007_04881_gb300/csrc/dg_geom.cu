@@ -81,6 +81,23 @@ __global__ void elem_geom_kernel(DevMesh m) {
   }
   m.vol[e] = vol;
   m.h[e] = sqrt(h2);
+  // contraction-precision record: lo, L, 1/L, R = 1/sqrt(|bbox|) (the basis
+  // scale is s_i = R prod_d sqrt(2 alpha_d + 1))
+  constexpr int EV = elem_vals(D);
+  double rec[EV];
+  double box = 1.0;
+  for (int d = 0; d < D; ++d) {
+    const double L = hi[d] - lo[d];
+    rec[d] = lo[d];
+    rec[D + d] = L;
+    rec[2 * D + d] = 1.0 / L;
+    box *= L;
+  }
+  rec[3 * D] = 1.0 / sqrt(box);
+  for (int k = 0; k < EV; ++k) {
+    m.eg64[(size_t)k * m.ne + e] = rec[k];
+    m.eg32[(size_t)k * m.ne + e] = (float)rec[k];
+  }
 }
 
 template <int D>

@@ -830,6 +830,8 @@ int dg_mesh_upload(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
   alloc_d(&dm.cen, (size_t)dim * ne);
   alloc_d(&dm.vol, ne);
   alloc_d(&dm.h, ne);
+  alloc_d(&dm.eg64, (size_t)elem_vals(dim) * ne);
+  alloc_f(&dm.eg32, (size_t)elem_vals(dim) * ne);
   alloc_d(&dm.sg64, (size_t)sub_vals(dim) * nsub);
   alloc_f(&dm.sg32, (size_t)sub_vals(dim) * nsub);
   alloc_d(&dm.fs64, (size_t)2 * side_vals(dim) * nf);

@@ -22,6 +22,8 @@ __host__ __device__ constexpr int sub_vals(int dim) { return dim == 2 ? 7 : 13; 
 //   3D: xi(v0)(3), xi(v1)-xi(v0)(3), xi(v2)-xi(v0)(3), n'(3) -> 12
 // with n'_d = 2 n_d / L_d, n the unit normal pointing out of e0.
 __host__ __device__ constexpr int side_vals(int dim) { return dim == 2 ? 6 : 12; }
+// values per element record: lo, L, 1/L (dim each) and R
+__host__ __device__ constexpr int elem_vals(int dim) { return 3 * dim + 1; }
 
 __host__ __device__ constexpr int nbasis(int dim, int p) {
   return dim == 2 ? (p + 1) * (p + 2) / 2 : (p + 1) * (p + 2) * (p + 3) / 6;
@@ -71,6 +73,10 @@ struct DevMesh {
   double* cen;  // [dim][ne]
   double* vol;  // [ne]
   double* h;    // [ne]
+  // per-element records in the contraction precision, SoA [k][ne]:
+  // lo[D], L[D], 1/L[D], R = 1/sqrt(prod_d L_d)
+  double* eg64;
+  float* eg32;
   // sub-simplex data, SoA [k][nsub]
   double* sg64;
   float* sg32;

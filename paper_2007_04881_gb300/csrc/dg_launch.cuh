@@ -23,20 +23,27 @@ template <int D, int P, typename T>
 inline int launch_row_p(const DevMesh& m, int mode, T* vals, T* rhs, int sm_count, cudaStream_t st, Tracer* tr) {
   const int count = m.elem_pstart[P + 1] - m.elem_pstart[P];
   if (count <= 0) return 0;
-  using SM = RowSmem<D, P, T>;
-  constexpr int G = TileCfg<D, P>::G;
-  static_assert(SM::total(kWarps, nbasis(D, D == 2 ? kPMax2 : kPMax3)) <= 227 * 1024,
-                "row kernel shared memory exceeds 227 KB");
-  const int ntiles = (count + G - 1) / G;
-  const size_t smem = SM::total(kWarps, m.nmax);
-  auto k = row_kernel<D, P, T>;
-  const int grid = resident_grid(k, smem, sm_count, (ntiles + kWarps - 1) / kWarps);
   if (tr && tr->on) {
     char name[48];
     snprintf(name, sizeof name, "row%dd_p%d_%s", D, P, sizeof(T) == 8 ? "f64" : "f32");
     tr->begin(name, 0, P, sizeof(T), st);
   }
-  k<<<grid, kWarps * 32, smem, st>>>(m, mode, vals, rhs);
+  if constexpr (TileCfg<D, P>::TPE == 1) {
+    // one element per thread, no staging
+    auto k = row_lane_kernel<D, P, T>;
+    const int grid = resident_grid(k, 0, sm_count, (count + kWarps * 32 - 1) / (kWarps * 32));
+    k<<<grid, kWarps * 32, 0, st>>>(m, mode, vals, rhs);
+  } else {
+    using SM = RowSmem<D, P, T>;
+    constexpr int G = TileCfg<D, P>::G;
+    static_assert(SM::total(kWarps, nbasis(D, D == 2 ? kPMax2 : kPMax3)) <= 227 * 1024,
+                  "row kernel shared memory exceeds 227 KB");
+    const int ntiles = (count + G - 1) / G;
+    const size_t smem = SM::total(kWarps, m.nmax);
+    auto k = row_kernel<D, P, T>;
+    const int grid = resident_grid(k, smem, sm_count, (ntiles + kWarps - 1) / kWarps);
+    k<<<grid, kWarps * 32, smem, st>>>(m, mode, vals, rhs);
+  }
   if (tr && tr->on) tr->end(st);
   return 1;
 }
