@@ -12,7 +12,8 @@ namespace dg {
 
 namespace {
 
-__device__ __forceinline__ double xi_of(double x, double lo, double L) { return 2.0 * (x - lo) / L - 1.0; }
+// bounding-box coordinate xi = 2 (x - lo) / L - 1, with iL = 1/L precomputed
+__device__ __forceinline__ double xi_of(double x, double lo, double iL) { return 2.0 * (x - lo) * iL - 1.0; }
 
 template <int D>
 __global__ void elem_geom_kernel(DevMesh m) {
@@ -53,25 +54,49 @@ __global__ void elem_geom_kernel(DevMesh m) {
     }
     for (int d = 0; d < 3; ++d) cen[d] /= vol;
   }
-  // bounding box and diameter over the element's distinct vertices
-  double h2 = 0.0;
+  // bounding box and diameter over the element's distinct vertices.  The
+  // largest squared distance is found in FP32, then every pair within a
+  // relative 1e-5 of it is re-measured in FP64: the FP64 maximum is among
+  // them, so h is the exact FP64 diameter at a fraction of the FP64 work.
   const int ub = m.uvptr[e], ue = m.uvptr[e + 1];
+  float h2f = 0.f;
   for (int i = ub; i < ue; ++i) {
     const int vi = m.uvidx[i];
-    double pi_[3];
+    float pf[3];
     for (int d = 0; d < D; ++d) {
-      pi_[d] = m.X[d][vi];
-      lo[d] = fmin(lo[d], pi_[d]);
-      hi[d] = fmax(hi[d], pi_[d]);
+      const double x = m.X[d][vi];
+      lo[d] = fmin(lo[d], x);
+      hi[d] = fmax(hi[d], x);
+      pf[d] = (float)x;
     }
     for (int j = i + 1; j < ue; ++j) {
       const int vj = m.uvidx[j];
-      double s = 0.0;
+      float sf = 0.f;
       for (int d = 0; d < D; ++d) {
-        const double df = m.X[d][vj] - pi_[d];
-        s += df * df;
+        const float df = (float)m.X[d][vj] - pf[d];
+        sf = fmaf(df, df, sf);
       }
-      h2 = fmax(h2, s);
+      h2f = fmaxf(h2f, sf);
+    }
+  }
+  const float cut = h2f * (1.0f - 1e-5f);
+  double h2 = 0.0;
+  for (int i = ub; i < ue; ++i) {
+    const int vi = m.uvidx[i];
+    for (int j = i + 1; j < ue; ++j) {
+      const int vj = m.uvidx[j];
+      float sf = 0.f;
+      for (int d = 0; d < D; ++d) {
+        const float df = (float)m.X[d][vj] - (float)m.X[d][vi];
+        sf = fmaf(df, df, sf);
+      }
+      if (sf < cut) continue;
+      double s2 = 0.0;
+      for (int d = 0; d < D; ++d) {
+        const double df = m.X[d][vj] - m.X[d][vi];
+        s2 += df * df;
+      }
+      h2 = fmax(h2, s2);
     }
   }
   for (int d = 0; d < D; ++d) {
@@ -80,7 +105,10 @@ __global__ void elem_geom_kernel(DevMesh m) {
     m.cen[d * m.ne + e] = cen[d];
   }
   m.vol[e] = vol;
-  m.h[e] = sqrt(h2);
+  const double h = sqrt(h2);
+  m.h[e] = h;
+  const int pe = m.p[e];
+  m.pen[e] = m.a[e] * pe * pe / h;  // a_k p_k^2 / h_k of the penalty
   // contraction-precision record: lo, L, 1/L, R = 1/sqrt(|bbox|) (the basis
   // scale is s_i = R prod_d sqrt(2 alpha_d + 1))
   constexpr int EV = elem_vals(D);
@@ -101,14 +129,14 @@ __global__ void elem_geom_kernel(DevMesh m) {
 }
 
 template <int D>
-__global__ void sub_geom_kernel(DevMesh m) {
+__global__ void sub_geom_kernel(DevMesh m, int wmask) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= m.nsub) return;
   const int e = m.sub_elem[k];
   double lo[3], L[3];
   for (int d = 0; d < D; ++d) {
-    lo[d] = m.lo[d * m.ne + e];
-    L[d] = m.L[d * m.ne + e];
+    lo[d] = m.eg64[(size_t)d * m.ne + e];
+    L[d] = m.eg64[(size_t)(2 * D + d) * m.ne + e];  // 1/L
   }
   constexpr int SV = sub_vals(D);
   double out[SV];
@@ -145,14 +173,14 @@ __global__ void sub_geom_kernel(DevMesh m) {
     out[12] = fabs(u[0] * (v[1] * w[2] - v[2] * w[1]) - u[1] * (v[0] * w[2] - v[2] * w[0]) +
                    u[2] * (v[0] * w[1] - v[1] * w[0]));
   }
-  for (int j = 0; j < SV; ++j) {
-    m.sg64[(size_t)j * m.nsub + k] = out[j];
-    m.sg32[(size_t)j * m.nsub + k] = (float)out[j];
-  }
+  if (wmask & 1)
+    for (int j = 0; j < SV; ++j) m.sg64[(size_t)j * m.nsub + k] = out[j];
+  if (wmask & 2)
+    for (int j = 0; j < SV; ++j) m.sg32[(size_t)j * m.nsub + k] = (float)out[j];
 }
 
 template <int D>
-__global__ void face_geom_kernel(DevMesh m) {
+__global__ void face_geom_kernel(DevMesh m, int wmask) {
   const int f = blockIdx.x * blockDim.x + threadIdx.x;
   if (f >= m.nf) return;
   const int es[2] = {m.f_e0[f], m.f_e1[f]};
@@ -188,45 +216,44 @@ __global__ void face_geom_kernel(DevMesh m) {
     for (int j = 0; j < FV; ++j) out[j] = 0.0;
     if (e >= 0) {
       for (int d = 0; d < D; ++d) {
-        const double lo = m.lo[d * m.ne + e], L = m.L[d * m.ne + e];
-        const double x0 = xi_of(P[0][d], lo, L);
+        const double lo = m.eg64[(size_t)d * m.ne + e], iL = m.eg64[(size_t)(2 * D + d) * m.ne + e];
+        const double x0 = xi_of(P[0][d], lo, iL);
         out[d] = x0;
-        for (int i = 1; i < D; ++i) out[i * D + d] = xi_of(P[i][d], lo, L) - x0;
-        out[D * D + d] = 2.0 * n[d] / L;
+        for (int i = 1; i < D; ++i) out[i * D + d] = xi_of(P[i][d], lo, iL) - x0;
+        out[D * D + d] = 2.0 * n[d] * iL;
       }
-      const int pe = m.p[e];
-      sigma = fmax(sigma, m.a[e] * pe * pe / m.h[e]);
+      sigma = fmax(sigma, m.pen[e]);
     }
-    for (int j = 0; j < FV; ++j) {
-      m.fs64[((size_t)s * FV + j) * m.nf + f] = out[j];
-      m.fs32[((size_t)s * FV + j) * m.nf + f] = (float)out[j];
-    }
+    if (wmask & 1)
+      for (int j = 0; j < FV; ++j) m.fs64[((size_t)s * FV + j) * m.nf + f] = out[j];
+    if (wmask & 2)
+      for (int j = 0; j < FV; ++j) m.fs32[((size_t)s * FV + j) * m.nf + f] = (float)out[j];
   }
   sigma *= m.pb.c_sigma;
   double bn = 0.0;
   for (int d = 0; d < D; ++d) bn += m.pb.b[d] * n[d];
   const double sc[3] = {J, sigma, bn};
-  for (int j = 0; j < 3; ++j) {
-    m.fsc64[(size_t)j * m.nf + f] = sc[j];
-    m.fsc32[(size_t)j * m.nf + f] = (float)sc[j];
-  }
+  if (wmask & 1)
+    for (int j = 0; j < 3; ++j) m.fsc64[(size_t)j * m.nf + f] = sc[j];
+  if (wmask & 2)
+    for (int j = 0; j < 3; ++j) m.fsc32[(size_t)j * m.nf + f] = (float)sc[j];
 }
 
 inline int nblk(int n, int t) { return (n + t - 1) / t; }
 
 }  // namespace
 
-int launch_geometry(const DevMesh& m, cudaStream_t st, Tracer* tr) {
+int launch_geometry(const DevMesh& m, cudaStream_t st, Tracer* tr, int wmask) {
   const int T = 128;
   if (tr && tr->on) tr->begin(m.dim == 2 ? "geometry2d" : "geometry3d", 2, 0, 8, st);
   if (m.dim == 2) {
     elem_geom_kernel<2><<<nblk(m.ne, T), T, 0, st>>>(m);
-    sub_geom_kernel<2><<<nblk(m.nsub, T), T, 0, st>>>(m);
-    face_geom_kernel<2><<<nblk(m.nf, T), T, 0, st>>>(m);
+    sub_geom_kernel<2><<<nblk(m.nsub, T), T, 0, st>>>(m, wmask);
+    face_geom_kernel<2><<<nblk(m.nf, T), T, 0, st>>>(m, wmask);
   } else {
     elem_geom_kernel<3><<<nblk(m.ne, T), T, 0, st>>>(m);
-    sub_geom_kernel<3><<<nblk(m.nsub, T), T, 0, st>>>(m);
-    face_geom_kernel<3><<<nblk(m.nf, T), T, 0, st>>>(m);
+    sub_geom_kernel<3><<<nblk(m.nsub, T), T, 0, st>>>(m, wmask);
+    face_geom_kernel<3><<<nblk(m.nf, T), T, 0, st>>>(m, wmask);
   }
   if (tr && tr->on) tr->end(st);
   return 3;

@@ -830,6 +830,7 @@ int dg_mesh_upload(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
   alloc_d(&dm.cen, (size_t)dim * ne);
   alloc_d(&dm.vol, ne);
   alloc_d(&dm.h, ne);
+  alloc_d(&dm.pen, ne);
   alloc_d(&dm.eg64, (size_t)elem_vals(dim) * ne);
   alloc_f(&dm.eg32, (size_t)elem_vals(dim) * ne);
   alloc_d(&dm.sg64, (size_t)sub_vals(dim) * nsub);
@@ -977,8 +978,12 @@ int dg_assemble_host(dg_ctx* ctx, dg_mesh* mesh, int prec, const double* x, cons
 }
 
 int dg_assemble_step(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs) {
-  int rc = dg_geometry(ctx, mesh);
-  if (rc != DG_OK) return rc;
+  if (!ctx || !mesh) return fail(DG_ERR_ARG, "dg_assemble_step: null argument");
+  if (prec != DG_PREC_FP64 && prec != DG_PREC_FP32) return fail(DG_ERR_ARG, "unknown precision %d", prec);
+  // geometry records only in the precision this pass consumes
+  trace_reset(ctx, mesh);
+  ctx->last_launches = launch_geometry(mesh->dm, ctx->stream, &ctx->tracer, prec == DG_PREC_FP64 ? 1 : 2);
+  DG_CUDA_TRY(cudaGetLastError());
   const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
   return run_assembly(ctx, mesh, prec, mode, vals, rhs, true, false);
 }

@@ -73,6 +73,7 @@ struct DevMesh {
   double* cen;  // [dim][ne]
   double* vol;  // [ne]
   double* h;    // [ne]
+  double* pen;  // [ne] a_k p_k^2 / h_k
   // per-element records in the contraction precision, SoA [k][ne]:
   // lo[D], L[D], 1/L[D], R = 1/sqrt(prod_d L_d)
   double* eg64;
@@ -152,7 +153,9 @@ struct Tracer {
 
 // Launchers (defined in the kernel translation units).  Each returns the
 // number of kernel launches issued.
-int launch_geometry(const DevMesh& m, cudaStream_t st, Tracer* tr = nullptr);
+// wmask: bit 0 writes the FP64 copies of the sub-simplex / face records,
+// bit 1 the FP32 copies (element records are always written in both).
+int launch_geometry(const DevMesh& m, cudaStream_t st, Tracer* tr = nullptr, int wmask = 3);
 int launch_row2d_f64(const DevMesh& m, int mode, double* vals, double* rhs, int sm_count, cudaStream_t st, Tracer* tr);
 int launch_row2d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, cudaStream_t st, Tracer* tr);
 int launch_row3d_f64(const DevMesh& m, int mode, double* vals, double* rhs, int sm_count, cudaStream_t st, Tracer* tr);
