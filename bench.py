@@ -33,8 +33,27 @@ sys.path.insert(0, ROOT)
 
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 METRIC = "dG assembly elements/s & matrix GB/s vs roofline; reduced vs FP64 form at fixed err"
-WORKLOAD = ("adr2d_65k: 2D advection-diffusion-reaction, 65,536 clipped Voronoi cells (5 Lloyd steps), "
-            "p~U{1..4}, a=10^U(-2,2), b=(1,0.5), c=1, sin-product source, penalty 10 p^2/h")
+WORKLOADS = {
+    "adr2d_65k": ("adr2d_65k: 2D advection-diffusion-reaction, 65,536 clipped Voronoi cells (5 Lloyd steps), "
+                  "p~U{1..4}, a=10^U(-2,2), b=(1,0.5), c=1, sin-product source, penalty 10 p^2/h"),
+    "poisson2d_1k": ("poisson2d_1k: 2D Poisson, 1,024 clipped Voronoi cells (5 Lloyd steps), p=2, a=1, b=0, c=0, "
+                     "f from u=sin(pi x)sin(pi y), penalty 10 p^2/h"),
+    "diff3d_32k": ("diff3d_32k: 3D diffusion, 64^3 cubes x 6 Kuhn tets (1,572,864 tets) agglomerated by k-means "
+                   "into 32,768 polyhedra, p=3, a=10^U(-2,2), b=0, c=0, penalty 10 p^2/h"),
+}
+WORKLOAD = WORKLOADS["adr2d_65k"]
+
+
+def make_workload(name):
+    from paper_2007_04881_gb300 import configs
+
+    if name == "adr2d_65k":
+        return configs.adr2d()
+    if name == "poisson2d_1k":
+        return configs.poisson2d()
+    if name == "diff3d_32k":
+        return configs.diff3d()
+    raise SystemExit(f"unknown workload {name}")
 
 
 def _peaks():
@@ -137,9 +156,9 @@ def max_over_ranks(x: float, ws: int) -> float:
     return float(t.item())
 
 
-def workload_config(wl, info):
+def workload_config(wl, info, name):
     return {
-        "workload": WORKLOAD,
+        "workload": WORKLOADS[name],
         "elements": int(info.ne),
         "interfaces": int(info.ninterfaces),
         "boundary_faces": int(info.nbfaces),
@@ -166,9 +185,9 @@ def run_reference(args):
     import oracle as O
     from paper_2007_04881_gb300 import configs
 
-    wl = configs.adr2d()
+    wl = make_workload(args.workload)
     om = O.Mesh(wl.mesh)
-    pb = O.make_problem(2, **wl.problem)
+    pb = O.make_problem(wl.dim, **wl.problem)
     p = wl.p.astype(np.int32)
     cores = os.cpu_count() or 1
     # per step: a contiguous sample of elements and the same share of interfaces
@@ -207,7 +226,7 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "elements": int(wl.ne), "interfaces": int(om.ni),
+        "config": {"workload": WORKLOADS[args.workload], "elements": int(wl.ne), "interfaces": int(om.ni),
                    "boundary_faces": int(om.nbf), "sample_per_step": per_step},
         "cpu_baseline": {"value": value, "unit": "elements/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -223,9 +242,9 @@ def cpu_baseline_sample(wl, seconds_target=12.0):
 
     cores = os.cpu_count() or 1
     om = O.Mesh(wl.mesh)
-    pb = O.make_problem(2, **wl.problem)
+    pb = O.make_problem(wl.dim, **wl.problem)
     p = wl.p.astype(np.int32)
-    n = 2048
+    n = min(2048, wl.ne // 2)
     el = np.arange(n, dtype=np.int32)
     ifs = np.arange(int(round(n * om.ni / wl.ne)), dtype=np.int32)
     t = time.perf_counter()
@@ -282,7 +301,7 @@ def run_ours(args):
     dev = local if ws > 1 else 0
     torch.cuda.set_device(dev)
     B.build()
-    wl = configs.adr2d()
+    wl = make_workload(args.workload)
     stream = torch.cuda.current_stream()
     ctx = dg.Context(dev, stream.cuda_stream)
     t0 = time.perf_counter()
@@ -331,7 +350,7 @@ def run_ours(args):
     for _ in range(max(1, args.warmup // 2)):
         step64()
     torch.cuda.synchronize()
-    k64 = max(3, args.steps // 10)
+    k64 = max(3, min(args.steps // 10, 20))
     ctx.dg_set_timing(True)
     t64, kstats64 = time_steps(torch, stream, step64, flush, k64, ctx)
     ctx.dg_set_timing(False)
@@ -348,17 +367,18 @@ def run_ours(args):
     # ---- end to end through the host-memory entry point
     pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).pin_memory()  # noqa: E731
     hx, hy, ha = pin(wl.mesh.x, np.float64), pin(wl.mesh.y, np.float64), pin(wl.a, np.float64)
+    hz = pin(wl.mesh.z, np.float64) if wl.dim == 3 else None
     hv = torch.empty(mesh.nvals, dtype=torch.float32).pin_memory()
     hr = torch.empty(mesh.ndofs, dtype=torch.float32).pin_memory()
-    e2e_steps = max(3, min(args.steps, 50))
+    e2e_steps = max(3, min(args.steps, 50 if wl.dim == 2 else 10))
     for _ in range(2):
-        mesh.dg_assemble_host(prec, hv, hr, x=hx, y=hy, a=ha)
+        mesh.dg_assemble_host(prec, hv, hr, x=hx, y=hy, z=hz, a=ha)
     barrier(ws)
     t = time.perf_counter()
     for _ in range(e2e_steps):
-        mesh.dg_assemble_host(prec, hv, hr, x=hx, y=hy, a=ha)
+        mesh.dg_assemble_host(prec, hv, hr, x=hx, y=hy, z=hz, a=ha)
     e2e_s = max_over_ranks((time.perf_counter() - t) / e2e_steps, ws)
-    h2d = (hx.numel() + hy.numel() + ha.numel()) * 8
+    h2d = (hx.numel() + hy.numel() + ha.numel() + (hz.numel() if hz is not None else 0)) * 8
     d2h = hv.numel() * 4 + hr.numel() * 4
 
     if rank != 0:
@@ -401,7 +421,7 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": workload_config(wl, info),
+        "config": workload_config(wl, info, args.workload),
         "matrix_gbs": (info.nvals + info.ndofs) * 4 / (ms_step * 1e-3) / 1e9,
         "roofline": {
             "bound": "alu",
@@ -446,6 +466,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="adr2d_65k", choices=sorted(WORKLOADS))
     ap.add_argument("--ref-sample", type=int, default=512, help="oracle elements per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -738,6 +738,8 @@ __global__ void __launch_bounds__(kWarps * 32)
 
   const bool mat_vol = mode & kModeVol, mat_face = mode & kModeFace, do_rhs = mode & kModeRhs;
   const bool accum = mode & kModeAccum;
+  // with b = 0 and c = 0 the Phi row of a volume point carries no matrix term
+  const bool no_adv = m.pb.b[0] == 0.0 && m.pb.b[1] == 0.0 && m.pb.b[2] == 0.0 && m.pb.c == 0.0;
   const int base = m.elem_pstart[P], count = m.elem_pstart[P + 1] - base;
   const int ntiles = (count + G - 1) / G;
 
@@ -869,9 +871,10 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
             for (int t = 0; t < NT; ++t) {
               T u[TM], v[TM];
+              if (t == 0 && no_adv && !do_rhs) continue;
               load_tile<T, TM, TMP>(Ub + t * ROW, u);
               load_tile<T, TM, TMP>(Vb + t * ROW, v);
-              if (mat_vol) {
+              if (mat_vol && !(t == 0 && no_adv)) {
 #pragma unroll
                 for (int a = 0; a < TM; ++a)
 #pragma unroll

@@ -209,3 +209,23 @@ def test_host_entry_point_matches_device(ctx):
     m.dg_assemble_host(dg.DG_PREC_FP64, vh, rh, x=np.ascontiguousarray(wl.mesh.x), y=np.ascontiguousarray(wl.mesh.y),
                        a=np.ascontiguousarray(wl.a))
     assert np.array_equal(vh, v) and np.array_equal(rh, r)
+
+
+def test_diff3d_32k_sampled(ctx):
+    """Full-size 3D diffusion workload (32,768 agglomerated polyhedra, p=3):
+    FP64 and FP32 forms against oracle blocks of a seeded sample."""
+    wl = configs.diff3d()
+    m, v, r = run_gpu(ctx, wl, dg.DG_PREC_FP64)
+    assert np.isfinite(v).all() and np.isfinite(r).all()
+    rng = np.random.default_rng(321)
+    om = O.Mesh(wl.mesh)
+    elems = np.sort(rng.choice(wl.ne, 48, replace=False))
+    ifs = np.sort(rng.choice(om.ni, 200, replace=False))
+    _, ob = oracle_blocks(wl, elems=elems, ifaces=ifs, om=om)
+    ed, eo, er = compare(blocks(m, v, r), om, ob, wl)
+    assert ed < TOL64 and eo < TOL64 and er < TOL64, (ed, eo, er)
+    m32, v32, r32 = run_gpu(ctx, wl, dg.DG_PREC_FP32)
+    ed, eo, er = compare(blocks(m32, v32, r32), om, ob, wl)
+    assert ed < TOL32 and eo < TOL32 and er < TOL32, (ed, eo, er)
+    rel_fro = np.linalg.norm(v32 - v) / np.linalg.norm(v)
+    assert rel_fro < 1e-6, rel_fro
