@@ -185,6 +185,31 @@ int dg_assemble_host(dg_ctx *ctx, dg_mesh *mesh, int prec, const double *x, cons
  * kernels (dg_geometry) followed by dg_assemble.  Asynchronous. */
 int dg_assemble_step(dg_ctx *ctx, dg_mesh *mesh, int prec, void *vals, void *rhs);
 
+/* Batches (many independent meshes in one pass).  dg_batch_upload merges n
+ * descriptors (same dim and problem data b, c, source, poly, C_sigma) into
+ * one mesh, their disjoint union: its block-sparse matrix is the
+ * block-diagonal concatenation of the members' matrices, member k owning
+ * element rows elem_off[k] .. elem_off[k+1], values val_off[k] ..
+ * val_off[k+1] and load-vector entries dof_off[k] .. dof_off[k+1]
+ * (dg_batch_offsets; arrays of n+1 entries, any may be NULL).  All degree
+ * groups of all members are then assembled by the same launches. */
+int dg_batch_upload(dg_ctx *ctx, const dg_mesh_desc *const *descs, int n, dg_mesh **out);
+int dg_batch_offsets(const dg_mesh *mesh, int *nmesh, int *elem_off, int64_t *val_off, int64_t *dof_off);
+
+/* CUDA graphs.  dg_graph_create records one whole pass (geometry kernels and
+ * the row kernels, as dg_assemble_step) of mesh into vals / rhs (device,
+ * fixed for the graph's life) as a CUDA graph.  With autotune != 0 it first
+ * times the candidate launch shapes (co-resident CTAs per SM capped at 1, 2
+ * or the occupancy limit; degree groups serial on one stream or concurrent
+ * on forked streams) and records the fastest.  The first call must precede
+ * any stream capture by the caller.  dg_graph_launch replays the pass on the
+ * context stream. */
+typedef struct dg_graph dg_graph;
+int dg_graph_create(dg_ctx *ctx, dg_mesh *mesh, int prec, void *vals, void *rhs, int autotune, dg_graph **out);
+int dg_graph_launch(dg_ctx *ctx, dg_graph *graph);
+int dg_graph_info(const dg_graph *graph, int *occ_cap, int *concurrent, float *tuned_ms, int *launches);
+int dg_graph_free(dg_graph *graph);
+
 /* Per-launch timing.  When enabled, every kernel launch of the following
  * calls is bracketed by CUDA events on the context stream.  dg_kernel_stats
  * waits for the stream and copies up to cap records of the most recent call

@@ -78,14 +78,41 @@ def diff3d(n: int = 64, clusters: int = 32768, seed: int = 2, p: int = 3) -> Wor
     )
 
 
-def batch2d(n_meshes: int = 256, lo: int = 512, hi: int = 16384, pmax: int = 5, base_seed: int = 3) -> List[Workload]:
-    """Independent 2D meshes; mesh m uses seed base_seed + m."""
+def _batch_member(k: int, lo: int, hi: int, pmax: int, base_seed: int):
+    s = base_seed + k
+    rng = np.random.default_rng(10_000 + s)
+    n = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
+    pm = int(rng.integers(1, pmax + 1))
+    return n, s, pm
+
+
+def _gen_member(args):
+    n, s = args
+    mg.voronoi_square(n, s)  # fills the mesh cache
+    return True
+
+
+def batch2d(n_meshes: int = 256, lo: int = 512, hi: int = 16384, pmax: int = 5, base_seed: int = 3,
+            workers: int = 0) -> List[Workload]:
+    """Independent 2D meshes; mesh k uses seed base_seed + k, cell count
+    round(exp(U(ln lo, ln hi))) and degree U{1..pmax} from rng(10000 + seed).
+
+    Missing meshes are generated in a spawned process pool (workers = 0: all
+    cores) and cached, so the serial pass below only reads the cache."""
+    members = [_batch_member(k, lo, hi, pmax, base_seed) for k in range(n_meshes)]
+    if workers >= 0 and mg._cache_dir() is not None:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        import os
+
+        nw = workers or (os.cpu_count() or 1)
+        if nw > 1:
+            todo = [(n, s) for n, s, _ in members]
+            todo.sort(key=lambda t: -t[0])
+            with cf.ProcessPoolExecutor(max_workers=nw, mp_context=mp.get_context("spawn")) as ex:
+                list(ex.map(_gen_member, todo, chunksize=1))
     out = []
-    for k in range(n_meshes):
-        s = base_seed + k
-        rng = np.random.default_rng(10_000 + s)
-        n = int(round(math.exp(rng.uniform(math.log(lo), math.log(hi)))))
-        pm = int(rng.integers(1, pmax + 1))
+    for k, (n, s, pm) in enumerate(members):
         m = mg.voronoi_square(n, s)
         out.append(
             Workload(

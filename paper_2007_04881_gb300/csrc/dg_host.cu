@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <climits>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -151,11 +152,34 @@ struct dg_ctx {
   RuleTables rt[4];  // indexed by dim (2, 3)
   Tracer tracer;
   std::vector<LaunchRec> recs;
+  // forked streams for concurrent per-degree launches (created on first use)
+  cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t fork = nullptr, join[4] = {nullptr, nullptr, nullptr, nullptr};
   ~dg_ctx() {
     for (auto& r : recs) {
       cudaEventDestroy(r.ev0);
       cudaEventDestroy(r.ev1);
     }
+    for (int i = 0; i < 4; ++i) {
+      if (side[i]) cudaStreamDestroy(side[i]);
+      if (join[i]) cudaEventDestroy(join[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+  }
+};
+
+struct dg_graph {
+  cudaStream_t stream = nullptr;  // capture stream
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int occ_cap = 0;
+  int concurrent = 0;
+  float tuned_ms = 0.f;
+  int launches = 0;
+  ~dg_graph() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    if (stream) cudaStreamDestroy(stream);
   }
 };
 
@@ -190,6 +214,7 @@ struct dg_mesh {
   double* X[3] = {nullptr, nullptr, nullptr};
   double* a = nullptr;
   double flops[2][9] = {{0}}, words[2][9] = {{0}};
+  std::vector<int> batch_elem_off;  // element offset of each batch member (empty: one mesh)
   ~dg_mesh() {
     if (h_vals) cudaFree(h_vals);
     if (h_rhs) cudaFree(h_rhs);
@@ -898,27 +923,51 @@ int dg_mesh_update(dg_ctx* ctx, dg_mesh* mesh, const double* x, const double* y,
   return dg_geometry(ctx, mesh);
 }
 
+// Issue the row kernels of one assembly pass on stream st.  concurrent:
+// the per-degree launches go to forked side streams and join back into st.
 static int run_assembly(dg_ctx* ctx, const dg_mesh* mesh, int prec, int mode, void* vals, void* rhs, bool iface,
-                        bool reset = true) {
+                        bool reset = true, cudaStream_t st = nullptr, bool use_ctx_stream = true, int occ_cap = 0,
+                        bool concurrent = false) {
   if (!ctx || !mesh) return fail(DG_ERR_ARG, "null context or mesh");
   if (prec != DG_PREC_FP64 && prec != DG_PREC_FP32) return fail(DG_ERR_ARG, "unknown precision %d", prec);
   if ((mode & (kModeVol | kModeFace)) && !vals) return fail(DG_ERR_ARG, "vals is null");
   if ((mode & kModeRhs) && !rhs) return fail(DG_ERR_ARG, "rhs is null");
+  if (use_ctx_stream) st = ctx->stream;
   const DevMesh& m = mesh->dm;
   Tracer* tr = &ctx->tracer;
   if (reset) trace_reset(ctx, mesh);
-  int n = 0;
   (void)iface;
+  LaunchOpts lo;
+  lo.occ_cap = occ_cap;
+  for (int p = 0; p < 9; ++p) lo.pst[p] = st;
+  if (concurrent) {
+    if (!ctx->fork) {
+      DG_CUDA_TRY(cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming));
+      for (int i = 0; i < 4; ++i) {
+        DG_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side[i], cudaStreamNonBlocking));
+        DG_CUDA_TRY(cudaEventCreateWithFlags(&ctx->join[i], cudaEventDisableTiming));
+      }
+    }
+    DG_CUDA_TRY(cudaEventRecord(ctx->fork, st));
+    for (int i = 0; i < 4; ++i) DG_CUDA_TRY(cudaStreamWaitEvent(ctx->side[i], ctx->fork, 0));
+    // highest degrees (longest launches) first on their own streams
+    for (int p = 1; p < 9; ++p) lo.pst[p] = ctx->side[(8 - p) % 4];
+  }
+  int n = 0;
   if (prec == DG_PREC_FP64) {
     double* v = static_cast<double*>(vals);
     double* r = static_cast<double*>(rhs);
-    n += m.dim == 2 ? launch_row2d_f64(m, mode, v, r, ctx->sm_count, ctx->stream, tr)
-                    : launch_row3d_f64(m, mode, v, r, ctx->sm_count, ctx->stream, tr);
+    n += m.dim == 2 ? launch_row2d_f64(m, mode, v, r, ctx->sm_count, lo, tr) : launch_row3d_f64(m, mode, v, r, ctx->sm_count, lo, tr);
   } else {
     float* v = static_cast<float*>(vals);
     float* r = static_cast<float*>(rhs);
-    n += m.dim == 2 ? launch_row2d_f32(m, mode, v, r, ctx->sm_count, ctx->stream, tr)
-                    : launch_row3d_f32(m, mode, v, r, ctx->sm_count, ctx->stream, tr);
+    n += m.dim == 2 ? launch_row2d_f32(m, mode, v, r, ctx->sm_count, lo, tr) : launch_row3d_f32(m, mode, v, r, ctx->sm_count, lo, tr);
+  }
+  if (concurrent) {
+    for (int i = 0; i < 4; ++i) {
+      DG_CUDA_TRY(cudaEventRecord(ctx->join[i], ctx->side[i]));
+      DG_CUDA_TRY(cudaStreamWaitEvent(st, ctx->join[i], 0));
+    }
   }
   ctx->last_launches = reset ? n : ctx->last_launches + n;
   DG_CUDA_TRY(cudaGetLastError());
@@ -986,6 +1035,189 @@ int dg_assemble_step(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs
   DG_CUDA_TRY(cudaGetLastError());
   const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
   return run_assembly(ctx, mesh, prec, mode, vals, rhs, true, false);
+}
+
+int dg_batch_upload(dg_ctx* ctx, const dg_mesh_desc* const* descs, int n, dg_mesh** out) {
+  if (!ctx || !descs || n <= 0 || !out) return fail(DG_ERR_ARG, "dg_batch_upload: bad argument");
+  *out = nullptr;
+  const dg_mesh_desc* d0 = descs[0];
+  if (!d0) return fail(DG_ERR_ARG, "dg_batch_upload: null descriptor 0");
+  const int dim = d0->dim;
+  int64_t nv = 0, ne = 0, nidx = 0;
+  for (int k = 0; k < n; ++k) {
+    const dg_mesh_desc* d = descs[k];
+    if (!d || d->dim != dim) return fail(DG_ERR_ARG, "dg_batch_upload: descriptor %d null or of another dimension", k);
+    if (d->c != d0->c || d->source != d0->source || d->c_sigma != d0->c_sigma || d->b[0] != d0->b[0] ||
+        d->b[1] != d0->b[1] || d->b[2] != d0->b[2] || std::memcmp(d->poly, d0->poly, sizeof d->poly) != 0)
+      return fail(DG_ERR_ARG, "dg_batch_upload: descriptor %d has different problem data", k);
+    if (d->nv <= 0 || d->ne <= 0 || !d->elem_ptr || !d->elem_idx)
+      return fail(DG_ERR_ARG, "dg_batch_upload: descriptor %d is empty", k);
+    nv += d->nv;
+    ne += d->ne;
+    nidx += (int64_t)d->elem_ptr[d->ne] * (dim == 2 ? 1 : 4);
+  }
+  if (nv > INT32_MAX || ne > INT32_MAX || nidx > INT32_MAX) return fail(DG_ERR_ARG, "dg_batch_upload: batch too large");
+  // disjoint union: vertex ids and element pointers shifted per mesh
+  std::vector<double> X[3];
+  std::vector<int> eptr(1, 0), eidx;
+  std::vector<int8_t> p;
+  std::vector<double> a;
+  std::vector<int> elem_off(1, 0);
+  for (int q = 0; q < dim; ++q) X[q].reserve(nv);
+  eidx.reserve(nidx);
+  int voff = 0;
+  for (int k = 0; k < n; ++k) {
+    const dg_mesh_desc* d = descs[k];
+    const double* src[3] = {d->x, d->y, d->z};
+    for (int q = 0; q < dim; ++q) {
+      if (!src[q]) return fail(DG_ERR_ARG, "dg_batch_upload: descriptor %d lacks coordinates", k);
+      X[q].insert(X[q].end(), src[q], src[q] + d->nv);
+    }
+    const int nk = d->elem_ptr[d->ne] * (dim == 2 ? 1 : 4);
+    for (int i = 0; i < nk; ++i) {
+      const int v = d->elem_idx[i];
+      if (v < 0 || v >= d->nv) return fail(DG_ERR_MESH, "dg_batch_upload: mesh %d vertex index out of range", k);
+      eidx.push_back(v + voff);
+    }
+    const int base = eptr.back();
+    for (int e = 0; e < d->ne; ++e) eptr.push_back(base + d->elem_ptr[e + 1]);
+    p.insert(p.end(), d->p, d->p + d->ne);
+    a.insert(a.end(), d->a, d->a + d->ne);
+    voff += d->nv;
+    elem_off.push_back(elem_off.back() + d->ne);
+  }
+  dg_mesh_desc u = *d0;
+  u.nv = (int)nv;
+  u.x = X[0].data();
+  u.y = X[1].data();
+  u.z = dim == 3 ? X[2].data() : nullptr;
+  u.ne = (int)ne;
+  u.elem_ptr = eptr.data();
+  u.elem_idx = eidx.data();
+  u.p = p.data();
+  u.a = a.data();
+  int rc = dg_mesh_upload(ctx, &u, out);
+  if (rc != DG_OK) return rc;
+  (*out)->batch_elem_off = elem_off;
+  return DG_OK;
+}
+
+int dg_batch_offsets(const dg_mesh* mesh, int* nmesh, int* elem_off, int64_t* val_off, int64_t* dof_off) {
+  if (!mesh) return fail(DG_ERR_ARG, "dg_batch_offsets: null mesh");
+  const std::vector<int>& eo = mesh->batch_elem_off;
+  const int n = eo.empty() ? 1 : (int)eo.size() - 1;
+  if (nmesh) *nmesh = n;
+  for (int k = 0; k <= n; ++k) {
+    const int e = eo.empty() ? (k == 0 ? 0 : mesh->dm.ne) : eo[k];
+    if (elem_off) elem_off[k] = e;
+    if (val_off) val_off[k] = mesh->blk_off[mesh->row_ptr[e]];
+    if (dof_off) dof_off[k] = mesh->dof_off[e];
+  }
+  return DG_OK;
+}
+
+// One whole pass (geometry + row kernels) on stream st with a launch shape.
+static int issue_pass(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs, cudaStream_t st, int occ_cap,
+                      bool concurrent) {
+  int n = launch_geometry(mesh->dm, st, nullptr, prec == DG_PREC_FP64 ? 1 : 2);
+  DG_CUDA_TRY(cudaGetLastError());
+  const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
+  int rc = run_assembly(ctx, mesh, prec, mode, vals, rhs, true, true, st, false, occ_cap, concurrent);
+  if (rc != DG_OK) return rc;
+  ctx->last_launches += n;
+  return DG_OK;
+}
+
+int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs, int autotune, dg_graph** out) {
+  if (!ctx || !mesh || !vals || !out) return fail(DG_ERR_ARG, "dg_graph_create: null argument");
+  if (prec != DG_PREC_FP64 && prec != DG_PREC_FP32) return fail(DG_ERR_ARG, "unknown precision %d", prec);
+  *out = nullptr;
+  dg_graph* g = new (std::nothrow) dg_graph();
+  if (!g) return fail(DG_ERR_OOM, "out of host memory");
+  auto bail = [&](int rc) {
+    delete g;
+    return rc;
+  };
+  if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(DG_ERR_CUDA, "dg_graph_create: stream creation failed"));
+  const bool was_on = ctx->tracer.on;
+  ctx->tracer.on = false;
+  // autotuner: time each candidate launch shape (best of 3 after a warm-up)
+  int best_occ = 0, best_conc = 0;
+  float best = 1e30f;
+  if (autotune) {
+    const int occs[3] = {0, 1, 2};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int conc = 0; conc < 2; ++conc)
+      for (int oi = 0; oi < 3; ++oi) {
+        float t = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+          cudaEventRecord(e0, g->stream);
+          int rc = issue_pass(ctx, mesh, prec, vals, rhs, g->stream, occs[oi], conc != 0);
+          if (rc != DG_OK) {
+            ctx->tracer.on = was_on;
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return bail(rc);
+          }
+          cudaEventRecord(e1, g->stream);
+          if (cudaEventSynchronize(e1) != cudaSuccess) {
+            ctx->tracer.on = was_on;
+            return bail(fail(DG_ERR_CUDA, "dg_graph_create: tuning pass failed"));
+          }
+          float ms = 0.f;
+          cudaEventElapsedTime(&ms, e0, e1);
+          if (rep > 0 && ms < t) t = ms;
+        }
+        if (t < best) {
+          best = t;
+          best_occ = occs[oi];
+          best_conc = conc;
+        }
+      }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+  }
+  g->occ_cap = best_occ;
+  g->concurrent = best_conc;
+  g->tuned_ms = autotune ? best : 0.f;
+  if (cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    ctx->tracer.on = was_on;
+    return bail(fail(DG_ERR_CUDA, "dg_graph_create: begin capture failed"));
+  }
+  int rc = issue_pass(ctx, mesh, prec, vals, rhs, g->stream, g->occ_cap, g->concurrent != 0);
+  cudaError_t ce = cudaStreamEndCapture(g->stream, &g->graph);
+  ctx->tracer.on = was_on;
+  if (rc != DG_OK) return bail(rc);
+  if (ce != cudaSuccess) return bail(fail(DG_ERR_CUDA, "dg_graph_create: capture failed: %s", cudaGetErrorString(ce)));
+  ce = cudaGraphInstantiate(&g->exec, g->graph, 0);
+  if (ce != cudaSuccess) return bail(fail(DG_ERR_CUDA, "dg_graph_create: instantiate: %s", cudaGetErrorString(ce)));
+  g->launches = ctx->last_launches;
+  *out = g;
+  return DG_OK;
+}
+
+int dg_graph_launch(dg_ctx* ctx, dg_graph* g) {
+  if (!ctx || !g) return fail(DG_ERR_ARG, "dg_graph_launch: null argument");
+  DG_CUDA_TRY(cudaGraphLaunch(g->exec, ctx->stream));
+  ctx->last_launches = g->launches;
+  return DG_OK;
+}
+
+int dg_graph_info(const dg_graph* g, int* occ_cap, int* concurrent, float* tuned_ms, int* launches) {
+  if (!g) return fail(DG_ERR_ARG, "dg_graph_info: null graph");
+  if (occ_cap) *occ_cap = g->occ_cap;
+  if (concurrent) *concurrent = g->concurrent;
+  if (tuned_ms) *tuned_ms = g->tuned_ms;
+  if (launches) *launches = g->launches;
+  return DG_OK;
+}
+
+int dg_graph_free(dg_graph* g) {
+  delete g;
+  return DG_OK;
 }
 
 int dg_set_timing(dg_ctx* ctx, int enable) {

@@ -156,9 +156,16 @@ struct Tracer {
 // wmask: bit 0 writes the FP64 copies of the sub-simplex / face records,
 // bit 1 the FP32 copies (element records are always written in both).
 int launch_geometry(const DevMesh& m, cudaStream_t st, Tracer* tr = nullptr, int wmask = 3);
-int launch_row2d_f64(const DevMesh& m, int mode, double* vals, double* rhs, int sm_count, cudaStream_t st, Tracer* tr);
-int launch_row2d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, cudaStream_t st, Tracer* tr);
-int launch_row3d_f64(const DevMesh& m, int mode, double* vals, double* rhs, int sm_count, cudaStream_t st, Tracer* tr);
-int launch_row3d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, cudaStream_t st, Tracer* tr);
+// Launch shape of the row kernels: cap on co-resident CTAs per SM (0: the
+// occupancy limit) and the stream of each degree's launch (index p).
+struct LaunchOpts {
+  int occ_cap = 0;
+  cudaStream_t pst[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+};
+
+int launch_row2d_f64(const DevMesh& m, int mode, double* vals, double* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);
+int launch_row2d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);
+int launch_row3d_f64(const DevMesh& m, int mode, double* vals, double* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);
+int launch_row3d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);
 
 }  // namespace dg

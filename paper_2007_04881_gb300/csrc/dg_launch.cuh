@@ -10,19 +10,21 @@
 namespace dg {
 
 template <typename K>
-inline int resident_grid(K kernel, size_t smem, int sm_count, int want_blocks) {
+inline int resident_grid(K kernel, size_t smem, int sm_count, int want_blocks, int occ_cap = 0) {
   int occ = 0;
   if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, kWarps * 32, smem);
+  if (occ_cap > 0 && occ > occ_cap) occ = occ_cap;
   if (occ < 1) occ = 1;
   int g = occ * sm_count;
   return want_blocks < g ? want_blocks : g;
 }
 
 template <int D, int P, typename T>
-inline int launch_row_p(const DevMesh& m, int mode, T* vals, T* rhs, int sm_count, cudaStream_t st, Tracer* tr) {
+inline int launch_row_p(const DevMesh& m, int mode, T* vals, T* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr) {
   const int count = m.elem_pstart[P + 1] - m.elem_pstart[P];
   if (count <= 0) return 0;
+  cudaStream_t st = lo.pst[P];
   if (tr && tr->on) {
     char name[48];
     snprintf(name, sizeof name, "row%dd_p%d_%s", D, P, sizeof(T) == 8 ? "f64" : "f32");
@@ -31,7 +33,7 @@ inline int launch_row_p(const DevMesh& m, int mode, T* vals, T* rhs, int sm_coun
   if constexpr (TileCfg<D, P>::TPE == 1) {
     // one element per thread, no staging
     auto k = row_lane_kernel<D, P, T>;
-    const int grid = resident_grid(k, 0, sm_count, (count + kWarps * 32 - 1) / (kWarps * 32));
+    const int grid = resident_grid(k, 0, sm_count, (count + kWarps * 32 - 1) / (kWarps * 32), lo.occ_cap);
     k<<<grid, kWarps * 32, 0, st>>>(m, mode, vals, rhs);
   } else {
     using SM = RowSmem<D, P, T>;
@@ -41,7 +43,7 @@ inline int launch_row_p(const DevMesh& m, int mode, T* vals, T* rhs, int sm_coun
     const int ntiles = (count + G - 1) / G;
     const size_t smem = SM::total(kWarps, m.nmax);
     auto k = row_kernel<D, P, T>;
-    const int grid = resident_grid(k, smem, sm_count, (ntiles + kWarps - 1) / kWarps);
+    const int grid = resident_grid(k, smem, sm_count, (ntiles + kWarps - 1) / kWarps, lo.occ_cap);
     k<<<grid, kWarps * 32, smem, st>>>(m, mode, vals, rhs);
   }
   if (tr && tr->on) tr->end(st);

@@ -107,6 +107,12 @@ def load() -> C.CDLL:
     lib.dg_assemble_step.argtypes = [V, V, C.c_int, V, V]
     lib.dg_set_timing.argtypes = [V, C.c_int]
     lib.dg_kernel_stats.argtypes = [V, C.POINTER(dg_kernel_stat), C.c_int]
+    lib.dg_batch_upload.argtypes = [V, C.POINTER(C.POINTER(dg_mesh_desc)), C.c_int, C.POINTER(V)]
+    lib.dg_batch_offsets.argtypes = [V, V, V, V, V]
+    lib.dg_graph_create.argtypes = [V, V, C.c_int, V, V, C.c_int, C.POINTER(V)]
+    lib.dg_graph_launch.argtypes = [V, V]
+    lib.dg_graph_info.argtypes = [V, V, V, V, V]
+    lib.dg_graph_free.argtypes = [V]
     lib.dg_sync.argtypes = [V]
     lib.dg_last_launch_count.argtypes = [V]
     _lib = lib
@@ -119,7 +125,8 @@ EXPORTS = (
     "dg_mesh_update",
     "dg_geometry", "dg_bsr_layout", "dg_bsr_pattern", "dg_assemble_volume", "dg_assemble_faces",
     "dg_assemble_rhs", "dg_assemble", "dg_assemble_host", "dg_sync", "dg_last_launch_count",
-    "dg_assemble_step", "dg_set_timing", "dg_kernel_stats",
+    "dg_assemble_step", "dg_set_timing", "dg_kernel_stats", "dg_batch_upload", "dg_batch_offsets",
+    "dg_graph_create", "dg_graph_launch", "dg_graph_info", "dg_graph_free",
 )
 
 
@@ -245,18 +252,30 @@ def dg_mesh_check(mesh, p, a, problem: Problem, pattern: bool = False):
 
 
 class Mesh:
-    """dg_mesh_upload of a generator mesh (meshgen.Mesh2D / Mesh3D)."""
+    """dg_mesh_upload of a generator mesh (meshgen.Mesh2D / Mesh3D), or, with
+    a list of (mesh, p, a) members, dg_batch_upload of their disjoint union."""
 
-    def __init__(self, ctx: Context, mesh, p, a, problem: Problem):
+    def __init__(self, ctx: Context, mesh, p=None, a=None, problem: Problem = None, members=None):
         lib = load()
         self.ctx = ctx
-        self.dim = mesh.dim
-        d, keep = make_desc(mesh, p, a, problem)
-        pp = keep[-2]
         h = C.c_void_p()
-        _check(lib.dg_mesh_upload(ctx._h, C.byref(d), C.byref(h)))
+        if members is None:
+            self.dim = mesh.dim
+            d, keep = make_desc(mesh, p, a, problem)
+            pp = keep[-2]
+            _check(lib.dg_mesh_upload(ctx._h, C.byref(d), C.byref(h)))
+            self.p = np.asarray(pp)
+        else:
+            self.dim = members[0][0].dim
+            descs, keeps = [], []
+            for (mm, pm, am) in members:
+                d, keep = make_desc(mm, pm, am, problem)
+                descs.append(d)
+                keeps.append(keep)
+            arr = (C.POINTER(dg_mesh_desc) * len(descs))(*[C.pointer(d) for d in descs])
+            _check(lib.dg_batch_upload(ctx._h, arr, len(descs), C.byref(h)))
+            self.p = np.concatenate([np.asarray(k[-2]) for k in keeps])
         self._h = h
-        self.p = np.asarray(pp)
         info = dg_bsr_info()
         _check(lib.dg_bsr_layout(h, C.byref(info)))
         self.info = info
@@ -296,6 +315,20 @@ class Mesh:
     def dg_assemble(self, prec: int, vals, rhs=None):
         _check(load().dg_assemble(self.ctx._h, self._h, prec, _vp(vals), _vp(rhs)))
 
+    def dg_batch_offsets(self):
+        n = C.c_int()
+        _check(load().dg_batch_offsets(self._h, C.byref(n), None, None, None))
+        eo = np.zeros(n.value + 1, np.int32)
+        vo = np.zeros(n.value + 1, np.int64)
+        do = np.zeros(n.value + 1, np.int64)
+        _check(load().dg_batch_offsets(self._h, None, _vp(eo), _vp(vo), _vp(do)))
+        return eo, vo, do
+
+    def dg_graph_create(self, prec: int, vals, rhs=None, autotune: bool = True) -> "Graph":
+        h = C.c_void_p()
+        _check(load().dg_graph_create(self.ctx._h, self._h, prec, _vp(vals), _vp(rhs), int(autotune), C.byref(h)))
+        return Graph(self.ctx, h)
+
     def dg_assemble_step(self, prec: int, vals, rhs=None):
         _check(load().dg_assemble_step(self.ctx._h, self._h, prec, _vp(vals), _vp(rhs)))
 
@@ -308,6 +341,33 @@ class Mesh:
     def dg_assemble_host(self, prec: int, vals_host, rhs_host=None, x=None, y=None, z=None, a=None):
         _check(load().dg_assemble_host(self.ctx._h, self._h, prec, _vp(x), _vp(y), _vp(z), _vp(a),
                                        _vp(vals_host), _vp(rhs_host)))
+
+
+class Graph:
+    """A recorded assembly pass (dg_graph_create); keep the buffers alive."""
+
+    def __init__(self, ctx: Context, h):
+        self.ctx = ctx
+        self._h = h
+
+    def dg_graph_launch(self):
+        _check(load().dg_graph_launch(self.ctx._h, self._h))
+
+    def dg_graph_info(self):
+        occ, conc, ms, nl = C.c_int(), C.c_int(), C.c_float(), C.c_int()
+        _check(load().dg_graph_info(self._h, C.byref(occ), C.byref(conc), C.byref(ms), C.byref(nl)))
+        return {"occ_cap": occ.value, "concurrent": bool(conc.value), "tuned_ms": ms.value, "launches": nl.value}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().dg_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def to_blocks(mesh: Mesh, vals: np.ndarray, rhs: Optional[np.ndarray] = None):

@@ -1,0 +1,94 @@
+"""Batches of independent meshes in one pass, and recorded (CUDA-graph)
+passes with the launch-shape autotuner."""
+import numpy as np
+import pytest
+
+from paper_2007_04881_gb300 import configs, dg
+
+from .helpers import compare, dg_problem, oracle_blocks
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(cuda):
+    import torch
+
+    from paper_2007_04881_gb300 import build as B
+
+    B.build()
+    c = dg.Context(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    c.close()
+
+
+def _members():
+    out = []
+    for k, (n, p) in enumerate([(60, 1), (150, 3), (40, 5), (95, 2), (120, 4), (33, 6)]):
+        wl = configs.small2d(n, 50 + k, p, p, b=(1.0, 0.5), c=1.0)
+        out.append(wl)
+    return out
+
+
+def _assemble(ctx, mesh, prec):
+    import torch
+
+    dt = torch.float64 if prec == dg.DG_PREC_FP64 else torch.float32
+    v = torch.full((mesh.nvals,), float("nan"), dtype=dt, device="cuda")
+    r = torch.full((mesh.ndofs,), float("nan"), dtype=dt, device="cuda")
+    mesh.dg_assemble_step(prec, v, r)
+    ctx.dg_sync()
+    return v.double().cpu().numpy(), r.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("prec", [dg.DG_PREC_FP64, dg.DG_PREC_FP32])
+def test_batch_equals_members(ctx, prec):
+    members = _members()
+    pb = dg_problem(members[0])
+    bm = dg.Mesh(ctx, None, problem=pb, members=[(w.mesh, w.p, w.a) for w in members])
+    eo, vo, do = bm.dg_batch_offsets()
+    assert len(eo) == len(members) + 1
+    vb, rb = _assemble(ctx, bm, prec)
+    for k, w in enumerate(members):
+        m = dg.Mesh(ctx, w.mesh, w.p, w.a, pb)
+        v, r = _assemble(ctx, m, prec)
+        assert vo[k + 1] - vo[k] == m.nvals and do[k + 1] - do[k] == m.ndofs
+        # the same element computations, grouped differently: bitwise equal
+        assert np.array_equal(vb[vo[k]:vo[k + 1]], v)
+        assert np.array_equal(rb[do[k]:do[k + 1]], r)
+
+
+def test_batch_member_vs_oracle(ctx):
+    members = _members()
+    pb = dg_problem(members[0])
+    bm = dg.Mesh(ctx, None, problem=pb, members=[(w.mesh, w.p, w.a) for w in members])
+    eo, vo, do = bm.dg_batch_offsets()
+    vb, rb = _assemble(ctx, bm, dg.DG_PREC_FP64)
+    k = 2
+    w = members[k]
+    m = dg.Mesh(ctx, w.mesh, w.p, w.a, pb)
+    got = dg.to_blocks(m, vb[vo[k]:vo[k + 1]], rb[do[k]:do[k + 1]])
+    om, ob = oracle_blocks(w)
+    ed, eo_, er = compare(got, om, ob, w)
+    assert max(ed, eo_, er) < 1e-12
+
+
+@pytest.mark.parametrize("autotune", [False, True])
+def test_graph_replay_equals_direct(ctx, autotune):
+    import torch
+
+    w = configs.small2d(400, 77, 1, 5)
+    m = dg.Mesh(ctx, w.mesh, w.p, w.a, dg_problem(w))
+    v_ref, r_ref = _assemble(ctx, m, dg.DG_PREC_FP32)
+    v = torch.zeros(m.nvals, dtype=torch.float32, device="cuda")
+    r = torch.zeros(m.ndofs, dtype=torch.float32, device="cuda")
+    g = m.dg_graph_create(dg.DG_PREC_FP32, v, r, autotune=autotune)
+    info = g.dg_graph_info()
+    assert info["launches"] >= 3 + 5
+    for _ in range(3):
+        v.zero_()
+        g.dg_graph_launch()
+        ctx.dg_sync()
+        assert np.array_equal(v.double().cpu().numpy(), v_ref)
+        assert np.array_equal(r.double().cpu().numpy(), r_ref)
+    g.close()
