@@ -40,7 +40,30 @@ WORKLOADS = {
                      "f from u=sin(pi x)sin(pi y), penalty 10 p^2/h"),
     "diff3d_32k": ("diff3d_32k: 3D diffusion, 64^3 cubes x 6 Kuhn tets (1,572,864 tets) agglomerated by k-means "
                    "into 32,768 polyhedra, p=3, a=10^U(-2,2), b=0, c=0, penalty 10 p^2/h"),
+    "batch2d_256": ("batch2d_256: 256 independent 2D clipped-Voronoi meshes (5 Lloyd steps), cell counts "
+                    "log-uniform in 512..16,384, per-mesh p~U{1..5}, a=10^U(-2,2), b=(1,0.5), c=1, one recorded "
+                    "pass over the whole batch"),
 }
+
+
+class _Batch:
+    """The batch workload as one object: members plus their concatenated
+    coordinates and coefficients (for the host-memory path)."""
+
+    def __init__(self, members):
+        self.members = members
+        self.dim = 2
+        self.ne = sum(w.ne for w in members)
+        self.problem = members[0].problem
+        self.a = np.concatenate([w.a for w in members])
+        self.p = np.concatenate([w.p for w in members])
+
+        class _M:
+            pass
+
+        self.mesh = _M()
+        self.mesh.x = np.concatenate([w.mesh.x for w in members])
+        self.mesh.y = np.concatenate([w.mesh.y for w in members])
 WORKLOAD = WORKLOADS["adr2d_65k"]
 
 
@@ -53,6 +76,8 @@ def make_workload(name):
         return configs.poisson2d()
     if name == "diff3d_32k":
         return configs.diff3d()
+    if name == "batch2d_256":
+        return _Batch(configs.batch2d())
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -186,6 +211,10 @@ def run_reference(args):
     from paper_2007_04881_gb300 import configs
 
     wl = make_workload(args.workload)
+    batch_ne = None
+    if isinstance(wl, _Batch):  # the oracle samples the largest member
+        batch_ne = wl.ne
+        wl = max(wl.members, key=lambda w: w.ne)
     om = O.Mesh(wl.mesh)
     pb = O.make_problem(wl.dim, **wl.problem)
     p = wl.p.astype(np.int32)
@@ -226,7 +255,7 @@ def run_reference(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOADS[args.workload], "elements": int(wl.ne), "interfaces": int(om.ni),
+        "config": {"workload": WORKLOADS[args.workload], "elements": int(batch_ne or wl.ne), "interfaces": int(om.ni),
                    "boundary_faces": int(om.nbf), "sample_per_step": per_step},
         "cpu_baseline": {"value": value, "unit": "elements/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -292,41 +321,48 @@ def time_steps(torch, stream, step, flush, steps, ctx=None):
 
 
 def run_ours(args):
+    # mesh generation (process pools for the batch) before any CUDA call
+    wl = make_workload(args.workload)
     import torch
 
     from paper_2007_04881_gb300 import build as B
-    from paper_2007_04881_gb300 import configs, dg
+    from paper_2007_04881_gb300 import dg
 
     ws, rank, local = dist_setup(True)
     dev = local if ws > 1 else 0
     torch.cuda.set_device(dev)
     B.build()
-    wl = make_workload(args.workload)
     stream = torch.cuda.current_stream()
     ctx = dg.Context(dev, stream.cuda_stream)
+    pb = dg.Problem(**wl.problem)
     t0 = time.perf_counter()
-    mesh = dg.Mesh(ctx, wl.mesh, wl.p, wl.a, dg.Problem(**wl.problem))
+    if isinstance(wl, _Batch):
+        mesh = dg.Mesh(ctx, None, problem=pb, members=[(w.mesh, w.p, w.a) for w in wl.members])
+    else:
+        mesh = dg.Mesh(ctx, wl.mesh, wl.p, wl.a, pb)
     upload_ms = 1e3 * (time.perf_counter() - t0)
     info = mesh.info
-    t0 = time.perf_counter()
-    dg.dg_mesh_check(wl.mesh, wl.p, wl.a, dg.Problem(**wl.problem))
-    pattern_ms = 1e3 * (time.perf_counter() - t0)
+    pattern_ms = None
+    if not isinstance(wl, _Batch):
+        t0 = time.perf_counter()
+        dg.dg_mesh_check(wl.mesh, wl.p, wl.a, pb)
+        pattern_ms = 1e3 * (time.perf_counter() - t0)
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     prec = dg.DG_PREC_FP32
     v32 = torch.empty(mesh.nvals, dtype=torch.float32, device="cuda")
     r32 = torch.empty(mesh.ndofs, dtype=torch.float32, device="cuda")
-    v64 = torch.empty(mesh.nvals, dtype=torch.float64, device="cuda")
-    r64 = torch.empty(mesh.ndofs, dtype=torch.float64, device="cuda")
-
-    def step32():
-        mesh.dg_assemble_step(dg.DG_PREC_FP32, v32, r32)
-
-    def step64():
-        mesh.dg_assemble_step(dg.DG_PREC_FP64, v64, r64)
 
     for _ in range(args.warmup):
-        step32()
+        mesh.dg_assemble_step(prec, v32, r32)
+    torch.cuda.synchronize()
+    # one recorded pass (CUDA graph), launch shape picked by the autotuner;
+    # per-launch timing events are recorded inside the graph
+    ctx.dg_set_timing(True)
+    g32 = mesh.dg_graph_create(prec, v32, r32, autotune=True)
+    ginfo = g32.dg_graph_info()
+    for _ in range(args.warmup):
+        g32.dg_graph_launch()
     torch.cuda.synchronize()
     launches_per_step = ctx.launches()
 
@@ -335,11 +371,9 @@ def run_ours(args):
     barrier(ws)
     torch.cuda.synchronize()
     sampler.start()
-    ctx.dg_set_timing(True)
     t_wall = time.perf_counter()
-    times, kstats = time_steps(torch, stream, step32, flush, args.steps, ctx)
+    times, kstats = time_steps(torch, stream, g32.dg_graph_launch, flush, args.steps, ctx)
     t_wall = time.perf_counter() - t_wall
-    ctx.dg_set_timing(False)
     torch.cuda.synchronize()
     barrier(ws)
     clocks = sampler.stop()
@@ -347,22 +381,25 @@ def run_ours(args):
     value = ws * info.ne / (ms_step * 1e-3)
 
     # ---- FP64 form (same workload), for the reduced-vs-FP64 comparison
-    for _ in range(max(1, args.warmup // 2)):
-        step64()
+    v64 = torch.empty(mesh.nvals, dtype=torch.float64, device="cuda")
+    r64 = torch.empty(mesh.ndofs, dtype=torch.float64, device="cuda")
+    g64 = mesh.dg_graph_create(dg.DG_PREC_FP64, v64, r64, autotune=False)
+    g64.dg_graph_launch()
     torch.cuda.synchronize()
-    k64 = max(3, min(args.steps // 10, 20))
-    ctx.dg_set_timing(True)
-    t64, kstats64 = time_steps(torch, stream, step64, flush, k64, ctx)
+    k64 = max(3, min(args.steps // 10, 20 if info.ne < 200000 and mesh.dim == 2 else 3))
+    t64, kstats64 = time_steps(torch, stream, g64.dg_graph_launch, flush, k64, ctx)
     ctx.dg_set_timing(False)
     ms64 = max_over_ranks(sum(t64) / len(t64), ws)
     # error of the reduced form against the FP64 form (same device inputs)
-    step32()
-    step64()
+    g32.dg_graph_launch()
+    g64.dg_graph_launch()
     torch.cuda.synchronize()
     d = (v32.double() - v64)
     err_fro = float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(v64))
     err_max = float(d.abs().max() / v64.abs().max())
     err_rhs = float(torch.linalg.vector_norm(r32.double() - r64) / torch.linalg.vector_norm(r64))
+    del v64, r64, g64, d
+    torch.cuda.empty_cache()
 
     # ---- end to end through the host-memory entry point
     pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).pin_memory()  # noqa: E731
@@ -370,7 +407,7 @@ def run_ours(args):
     hz = pin(wl.mesh.z, np.float64) if wl.dim == 3 else None
     hv = torch.empty(mesh.nvals, dtype=torch.float32).pin_memory()
     hr = torch.empty(mesh.ndofs, dtype=torch.float32).pin_memory()
-    e2e_steps = max(3, min(args.steps, 50 if wl.dim == 2 else 10))
+    e2e_steps = max(3, min(args.steps, 50 if info.ne < 200000 and wl.dim == 2 else 5))
     for _ in range(2):
         mesh.dg_assemble_host(prec, hv, hr, x=hx, y=hy, z=hz, a=ha)
     barrier(ws)
@@ -404,7 +441,9 @@ def run_ours(args):
     if os.path.exists(tfile):
         try:
             tj = json.load(open(tfile))
-            traffic = tj.get(name)
+            ent = tj.get(args.workload, {}).get(name)
+            if ent and ent.get("source_sha") == _kernel_source_sha():
+                traffic = ent.get("bytes_per_launch")
         except Exception:
             traffic = None
 
@@ -437,6 +476,7 @@ def run_ours(args):
         "step_algorithmic": {"tflops": step_flops / (ms_step * 1e-3) / 1e12,
                              "gbs": step_bytes / (ms_step * 1e-3) / 1e9},
         "kernels": kern,
+        "graph": ginfo,
         "fp64_form": {
             "value": ws * info.ne / (ms64 * 1e-3),
             "ms_per_step": ms64,
@@ -454,10 +494,24 @@ def run_ours(args):
         "clocks": clocks,
         "timed_wall_s": t_wall,
     }
-    if ws == 1 and not args.no_cpu_baseline:
+    if ws == 1 and not args.no_cpu_baseline and not isinstance(wl, _Batch):
         line["cpu_baseline"] = cpu_baseline_sample(wl)
+    elif ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_sample(wl.members[0])
+        line["cpu_baseline"]["sample"] = "batch member 0: " + line["cpu_baseline"]["sample"]
     print(json.dumps(line))
     return 0
+
+
+def _kernel_source_sha() -> str:
+    import hashlib
+
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2007_04881_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(csrc, fn), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def main():

@@ -176,6 +176,7 @@ struct dg_graph {
   int concurrent = 0;
   float tuned_ms = 0.f;
   int launches = 0;
+  int ntrace = 0;  // timing events recorded inside the graph (tracing on at capture)
   ~dg_graph() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
@@ -1183,13 +1184,20 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
   g->occ_cap = best_occ;
   g->concurrent = best_conc;
   g->tuned_ms = autotune ? best : 0.f;
-  if (cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
-    ctx->tracer.on = was_on;
-    return bail(fail(DG_ERR_CUDA, "dg_graph_create: begin capture failed"));
-  }
-  int rc = issue_pass(ctx, mesh, prec, vals, rhs, g->stream, g->occ_cap, g->concurrent != 0);
-  cudaError_t ce = cudaStreamEndCapture(g->stream, &g->graph);
+  // with timing enabled the per-launch events are recorded into the graph
   ctx->tracer.on = was_on;
+  trace_reset(ctx, mesh);
+  if (cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    return bail(fail(DG_ERR_CUDA, "dg_graph_create: begin capture failed"));
+  int rc = DG_OK;
+  {
+    const int gl = launch_geometry(mesh->dm, g->stream, &ctx->tracer, prec == DG_PREC_FP64 ? 1 : 2);
+    const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
+    rc = run_assembly(ctx, mesh, prec, mode, vals, rhs, true, false, g->stream, false, g->occ_cap, g->concurrent != 0);
+    ctx->last_launches += gl;
+  }
+  cudaError_t ce = cudaStreamEndCapture(g->stream, &g->graph);
+  g->ntrace = ctx->tracer.on ? ctx->tracer.n : 0;
   if (rc != DG_OK) return bail(rc);
   if (ce != cudaSuccess) return bail(fail(DG_ERR_CUDA, "dg_graph_create: capture failed: %s", cudaGetErrorString(ce)));
   ce = cudaGraphInstantiate(&g->exec, g->graph, 0);
@@ -1203,6 +1211,7 @@ int dg_graph_launch(dg_ctx* ctx, dg_graph* g) {
   if (!ctx || !g) return fail(DG_ERR_ARG, "dg_graph_launch: null argument");
   DG_CUDA_TRY(cudaGraphLaunch(g->exec, ctx->stream));
   ctx->last_launches = g->launches;
+  ctx->tracer.n = g->ntrace;  // the graph's own timing events, if any
   return DG_OK;
 }
 
