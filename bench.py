@@ -372,7 +372,16 @@ def run_ours(args):
     torch.cuda.synchronize()
     sampler.start()
     t_wall = time.perf_counter()
-    times, kstats = time_steps(torch, stream, g32.dg_graph_launch, flush, args.steps, ctx)
+    kstats_src = "per-launch events recorded inside the graph"
+    try:
+        times, kstats = time_steps(torch, stream, g32.dg_graph_launch, flush, args.steps, ctx)
+    except dg.DGError:
+        # in-graph events not timeable here: time the graph alone, then the
+        # same launches issued directly with per-launch events
+        times, _ = time_steps(torch, stream, g32.dg_graph_launch, flush, args.steps, None)
+        _, kstats = time_steps(torch, stream, lambda: mesh.dg_assemble_step(prec, v32, r32), flush,
+                               args.steps, ctx)
+        kstats_src = "per-launch events of the same launches issued directly (second timed loop)"
     t_wall = time.perf_counter() - t_wall
     torch.cuda.synchronize()
     barrier(ws)
@@ -387,7 +396,12 @@ def run_ours(args):
     g64.dg_graph_launch()
     torch.cuda.synchronize()
     k64 = max(3, min(args.steps // 10, 20 if info.ne < 200000 and mesh.dim == 2 else 3))
-    t64, kstats64 = time_steps(torch, stream, g64.dg_graph_launch, flush, k64, ctx)
+    try:
+        t64, kstats64 = time_steps(torch, stream, g64.dg_graph_launch, flush, k64, ctx)
+    except dg.DGError:
+        t64, _ = time_steps(torch, stream, g64.dg_graph_launch, flush, k64, None)
+        _, kstats64 = time_steps(torch, stream, lambda: mesh.dg_assemble_step(dg.DG_PREC_FP64, v64, r64), flush,
+                                 k64, ctx)
     ctx.dg_set_timing(False)
     ms64 = max_over_ranks(sum(t64) / len(t64), ws)
     # error of the reduced form against the FP64 form (same device inputs)
@@ -476,6 +490,7 @@ def run_ours(args):
         "step_algorithmic": {"tflops": step_flops / (ms_step * 1e-3) / 1e12,
                              "gbs": step_bytes / (ms_step * 1e-3) / 1e9},
         "kernels": kern,
+        "kernel_timing": kstats_src,
         "graph": ginfo,
         "fp64_form": {
             "value": ws * info.ne / (ms64 * 1e-3),

@@ -191,12 +191,22 @@ void Tracer::begin(const char* name, int kind, int p, size_t tsize, cudaStream_t
   snprintf(r.name, sizeof r.name, "%s", name);
   r.flops = (kind < 2 && flops) ? flops[kind * 9 + p] : 0.0;
   r.bytes = (kind < 2 && words) ? words[kind * 9 + p] * (double)tsize : 0.0;
-  cudaEventRecord(r.ev0, st);
+  record(r.ev0, st);
 }
 void Tracer::end(cudaStream_t st) {
   if (!on || n >= cap) return;
-  cudaEventRecord(recs[n].ev1, st);
+  record(recs[n].ev1, st);
   ++n;
+}
+// Inside a stream capture the record becomes an external event node, so the
+// event is stamped on every replay of the graph and stays timeable.
+void Tracer::record(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cs);
+  if (cs == cudaStreamCaptureStatusActive)
+    cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+  else
+    cudaEventRecord(ev, st);
 }
 }  // namespace dg
 

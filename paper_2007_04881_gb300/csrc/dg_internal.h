@@ -149,6 +149,7 @@ struct Tracer {
   const double* words = nullptr;  // [2][9]
   void begin(const char* name, int kind, int p, size_t tsize, cudaStream_t st);
   void end(cudaStream_t st);
+  static void record(cudaEvent_t ev, cudaStream_t st);
 };
 
 // Launchers (defined in the kernel translation units).  Each returns the
