@@ -220,7 +220,10 @@ int dg_graph_free(dg_graph *graph);
  * own interior-face point 3 n^2 + [b != 0] n^2/2 + basis; boundary-face
  * point 3 n^2 + [b != 0] n^2 + basis + 2n (load); interface-kernel face point
  * 6 n0 n1 + [b != 0] n0 n1.  Bytes: values written once plus geometry
- * records read once, in the precision's element size. */
+ * records read once, in the precision's element size.  When the call issued
+ * row kernels, one more record named "row_pass" follows: the span from the
+ * first row-kernel start to the last row-kernel end (degree groups may run
+ * concurrently) with their summed flops and bytes. */
 typedef struct {
   char name[48];
   float ms;

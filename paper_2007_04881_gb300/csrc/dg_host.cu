@@ -1268,6 +1268,30 @@ int dg_kernel_stats(dg_ctx* ctx, dg_kernel_stat* out, int cap) {
     out[i].flops = r.flops;
     out[i].bytes = r.bytes;
   }
+  // one more record, "row_pass": from the first row-kernel start to the last
+  // row-kernel end (the per-degree launches may overlap on forked streams)
+  int nrow = 0;
+  float t0 = 1e30f, t1 = -1e30f;
+  double fl = 0.0, by = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const LaunchRec& r = ctx->recs[i];
+    if (std::strncmp(r.name, "row", 3) != 0) continue;
+    float a = 0.f, b = 0.f;
+    DG_CUDA_TRY(cudaEventElapsedTime(&a, ctx->recs[0].ev0, r.ev0));
+    DG_CUDA_TRY(cudaEventElapsedTime(&b, ctx->recs[0].ev0, r.ev1));
+    t0 = std::min(t0, a);
+    t1 = std::max(t1, b);
+    fl += r.flops;
+    by += r.bytes;
+    ++nrow;
+  }
+  if (nrow > 0 && n < cap && out) {
+    std::snprintf(out[n].name, sizeof out[n].name, "row_pass");
+    out[n].ms = t1 - t0;
+    out[n].flops = fl;
+    out[n].bytes = by;
+    return n + 1;
+  }
   return n;
 }
 
