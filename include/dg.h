@@ -233,6 +233,31 @@ typedef struct {
 int dg_set_timing(dg_ctx *ctx, int enable);
 int dg_kernel_stats(dg_ctx *ctx, dg_kernel_stat *out, int cap);
 
+/* Volume blocks without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc (code running inside another framework's memory pool or under a
+ * fixed memory budget, processes that must not grow their device footprint
+ * after start-up).  The caller passes every input and output as its own
+ * device buffers:
+ *   x, y [nv] vertex coordinates; elem_ptr [ne+1], elem_idx [nsub] CCW vertex
+ *   loops (nsub = elem_ptr[ne], the number of fan triangles); a [ne];
+ *   blocks [ne * n * n] output, element-major, each n x n block row-major,
+ *   n = (p+1)(p+2)/2, double for DG_PREC_FP64, float for DG_PREC_FP32.
+ * It computes, for every element of uniform degree p, the volume part of
+ * Eq. (2.4) with advection (bx, by) and reaction c, exactly as
+ * dg_assemble_volume does for the element's diagonal block.  Intermediate
+ * records live in one file-scope device array of 16 MiB that every GPU
+ * loading the library keeps until exit; ne <= 16384 and nsub <= 131072, and
+ * larger meshes are rejected with DG_ERR_ARG before any GPU work.  The first
+ * call on a device looks up the array's device address and writes the
+ * reference rules into it (synchronous copies): make that first call before
+ * any stream capture.  Calls that overlap on the GPU share the array and
+ * race; serialise them (one stream, or events).  Asynchronous on stream
+ * (a cudaStream_t, NULL = legacy default stream) on device `device`. */
+int dg_volume_noalloc(void *stream, int device, int prec, int p, int nv, const double *x, const double *y,
+                      int ne, int nsub, const int *elem_ptr, const int *elem_idx, const double *a, double bx,
+                      double by, double c, void *blocks);
+
 /* Wait for all work on the context stream; reports device-side errors. */
 int dg_sync(dg_ctx *ctx);
 

@@ -247,13 +247,13 @@ int launch_geometry(const DevMesh& m, cudaStream_t st, Tracer* tr, int wmask) {
   const int T = 128;
   if (tr && tr->on) tr->begin(m.dim == 2 ? "geometry2d" : "geometry3d", 2, 0, 8, st);
   if (m.dim == 2) {
-    elem_geom_kernel<2><<<nblk(m.ne, T), T, 0, st>>>(m);
-    sub_geom_kernel<2><<<nblk(m.nsub, T), T, 0, st>>>(m, wmask);
-    face_geom_kernel<2><<<nblk(m.nf, T), T, 0, st>>>(m, wmask);
+    if (m.ne > 0) elem_geom_kernel<2><<<nblk(m.ne, T), T, 0, st>>>(m);
+    if (m.nsub > 0) sub_geom_kernel<2><<<nblk(m.nsub, T), T, 0, st>>>(m, wmask);
+    if (m.nf > 0) face_geom_kernel<2><<<nblk(m.nf, T), T, 0, st>>>(m, wmask);
   } else {
-    elem_geom_kernel<3><<<nblk(m.ne, T), T, 0, st>>>(m);
-    sub_geom_kernel<3><<<nblk(m.nsub, T), T, 0, st>>>(m, wmask);
-    face_geom_kernel<3><<<nblk(m.nf, T), T, 0, st>>>(m, wmask);
+    if (m.ne > 0) elem_geom_kernel<3><<<nblk(m.ne, T), T, 0, st>>>(m);
+    if (m.nsub > 0) sub_geom_kernel<3><<<nblk(m.nsub, T), T, 0, st>>>(m, wmask);
+    if (m.nf > 0) face_geom_kernel<3><<<nblk(m.nf, T), T, 0, st>>>(m, wmask);
   }
   if (tr && tr->on) tr->end(st);
   return 3;

@@ -143,6 +143,11 @@ struct DevBuf {
 
 }  // namespace
 
+namespace dg {
+void reference_rule(int dim, int n, std::vector<double>& pts) { simplex_rule(dim, n, pts); }
+int fail_na_impl(int code, const char* msg) { return fail(code, "%s", msg); }
+}  // namespace dg
+
 struct dg_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;

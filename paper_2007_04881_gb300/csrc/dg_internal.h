@@ -169,4 +169,11 @@ int launch_row2d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm
 int launch_row3d_f64(const DevMesh& m, int mode, double* vals, double* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);
 int launch_row3d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);
 
+// Host: collapsed reference rule on the d-simplex with n Gauss points per
+// direction, packed as [point][d+1] = (coordinates, weight); d = 1 gives the
+// n-point Gauss-Legendre rule on [0,1].
+}  // namespace dg
+#include <vector>
+namespace dg {
+void reference_rule(int dim, int n, std::vector<double>& pts);
 }  // namespace dg

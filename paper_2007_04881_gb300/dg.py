@@ -113,6 +113,8 @@ def load() -> C.CDLL:
     lib.dg_graph_launch.argtypes = [V, V]
     lib.dg_graph_info.argtypes = [V, V, V, V, V]
     lib.dg_graph_free.argtypes = [V]
+    lib.dg_volume_noalloc.argtypes = [V, C.c_int, C.c_int, C.c_int, C.c_int, V, V, C.c_int, C.c_int, V, V, V,
+                                      C.c_double, C.c_double, C.c_double, V]
     lib.dg_sync.argtypes = [V]
     lib.dg_last_launch_count.argtypes = [V]
     _lib = lib
@@ -126,7 +128,7 @@ EXPORTS = (
     "dg_geometry", "dg_bsr_layout", "dg_bsr_pattern", "dg_assemble_volume", "dg_assemble_faces",
     "dg_assemble_rhs", "dg_assemble", "dg_assemble_host", "dg_sync", "dg_last_launch_count",
     "dg_assemble_step", "dg_set_timing", "dg_kernel_stats", "dg_batch_upload", "dg_batch_offsets",
-    "dg_graph_create", "dg_graph_launch", "dg_graph_info", "dg_graph_free",
+    "dg_graph_create", "dg_graph_launch", "dg_graph_info", "dg_graph_free", "dg_volume_noalloc",
 )
 
 
@@ -341,6 +343,14 @@ class Mesh:
     def dg_assemble_host(self, prec: int, vals_host, rhs_host=None, x=None, y=None, z=None, a=None):
         _check(load().dg_assemble_host(self.ctx._h, self._h, prec, _vp(x), _vp(y), _vp(z), _vp(a),
                                        _vp(vals_host), _vp(rhs_host)))
+
+
+def dg_volume_noalloc(stream, device: int, prec: int, p: int, x, y, elem_ptr, elem_idx, a, bx: float, by: float,
+                      c: float, blocks, nsub: int):
+    """Allocation-free volume blocks (all array arguments are device buffers)."""
+    _check(load().dg_volume_noalloc(stream, int(device), int(prec), int(p), int(x.numel()), _vp(x), _vp(y),
+                                    int(a.numel()), int(nsub), _vp(elem_ptr), _vp(elem_idx), _vp(a), float(bx),
+                                    float(by), float(c), _vp(blocks)))
 
 
 class Graph:
