@@ -210,6 +210,65 @@ int dg_graph_launch(dg_ctx *ctx, dg_graph *graph);
 int dg_graph_info(const dg_graph *graph, int *occ_cap, int *concurrent, float *tuned_ms, int *launches);
 int dg_graph_free(dg_graph *graph);
 
+/* Learned reduced volume rules (2D).  For each element mapped to its
+ * bounding box [-1,1]^2, a rule of 28 points and weights that reproduces
+ * the 28 moments of P_6 (so the p <= 3 volume integrands with constant
+ * coefficients are integrated exactly) replaces the sub-triangle rule.  The
+ * paper notes that tailored polytope rules need a costly optimisation per
+ * element (Sec. 1); here a small network proposes the rule and a few FP64
+ * Gauss-Newton steps finish it, with the sub-triangle rule as the fallback.
+ *   dg_quad_prepare: exact moments of the normalised element by the
+ *     divergence theorem (FP64) and the network input: the vertex loop in
+ *     bounding-box coordinates from the vertex of largest x, zero-padded to
+ *     12 vertices, as 24 bfloat16 values per element.
+ *   dg_quad_fit: minimum-norm Gauss-Newton, iters steps from init (device,
+ *     [ne][84] network outputs (x[28], y[28], 28 w / area - 1), or NULL for
+ *     a fixed 4 x 7 tensor rule); an element is accepted when the monomial
+ *     moment residual / area < 1e-10 and every point lies in the bounding
+ *     box; install != 0 makes accepted rules the elements' volume rules for
+ *     the following assembly calls.  stats may be NULL.
+ *   dg_quad_targets: the current rules encoded as network targets (device,
+ *     [ne][84] float).
+ *   dg_quad_buffers: library-owned device arrays (features [ne][24] bf16,
+ *     rules [ne][84] double in bounding-box coordinates and weights,
+ *     residuals [ne] float, accepted flags [ne] int, Legendre-product moments
+ *     [ne][28] double).  Any output may be NULL.
+ *   dg_quad_clear: back to the sub-triangle rules. */
+typedef struct {
+  int elements;
+  int eligible;  /* elements with at most 12 vertices */
+  int accepted;
+  float max_accepted_residual;
+} dg_quad_stats;
+int dg_quad_prepare(dg_ctx *ctx, dg_mesh *mesh);
+int dg_quad_fit(dg_ctx *ctx, dg_mesh *mesh, const float *init, int iters, int install, dg_quad_stats *stats);
+int dg_quad_targets(dg_ctx *ctx, dg_mesh *mesh, float *targets);
+int dg_quad_buffers(const dg_mesh *mesh, const void **feat, const double **rules, const float **resid, const int **ok,
+                    const double **moments);
+int dg_quad_clear(dg_ctx *ctx, dg_mesh *mesh);
+
+/* The proposal network: 24 -> 128 -> 128 -> 84, tanh hidden layers, linear
+ * output; bfloat16 operands with FP32 accumulation on the tensor cores, FP32
+ * master parameters and Adam (beta 0.9 / 0.999, eps 1e-8).  Loss: mean over
+ * rows of |out - target|^2 / 2.  Parameters are one flat FP32 array of
+ * dg_mlp_num_params() values: W1 [24][128], b1, W2 [128][128], b2,
+ * W3 [128][84], b3 (weights row-major, input index first).  x_bf16 are
+ * device arrays [n][24] of bfloat16, target / out / grad device FP32.
+ * dg_mlp_get/set_params and get/set_state (Adam moments) copy to and from
+ * HOST arrays for checkpoints. */
+typedef struct dg_mlp dg_mlp;
+int dg_mlp_create(dg_ctx *ctx, int seed, dg_mlp **out);
+int dg_mlp_free(dg_mlp *net);
+int64_t dg_mlp_num_params(void);
+int dg_mlp_get_params(const dg_mlp *net, float *host, int64_t *step);
+int dg_mlp_set_params(dg_mlp *net, const float *host, int64_t step);
+int dg_mlp_get_state(const dg_mlp *net, float *m1, float *m2);
+int dg_mlp_set_state(dg_mlp *net, const float *m1, const float *m2);
+int dg_mlp_forward(dg_ctx *ctx, dg_mlp *net, const void *x_bf16, int n, float *out);
+int dg_mlp_grad(dg_ctx *ctx, dg_mlp *net, const void *x_bf16, const float *target, int n, float *grad, float *loss);
+int dg_mlp_train_step(dg_ctx *ctx, dg_mlp *net, const void *x_bf16, const float *target, int n, float lr,
+                      float *loss);
+
 /* Per-launch timing.  When enabled, every kernel launch of the following
  * calls is bracketed by CUDA events on the context stream.  dg_kernel_stats
  * waits for the stream and copies up to cap records of the most recent call

@@ -521,7 +521,47 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
       for (int j = 0; j < N; ++j) acc[i][j] = T(0);
     }
-    if (mat_vol || do_rhs) {
+    const bool learned = m.lq_ok && m.lq_ok[e];
+    if ((mat_vol || do_rhs) && learned) {
+      const T* LQ = pick<T>(m.lq64, m.lq32) + (size_t)e * 84;
+      for (int r = 0; r < 28; ++r) {
+        T xi[D];
+        xi[0] = LQ[r];
+        xi[1] = LQ[28 + r];
+        const T W = LQ[56 + r];
+        T Phi[N], Dd[D][N];
+        basis_eval<D, P, T>(xi, Phi, Dd);
+        if (mat_vol) {
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            T adv = q.c * Phi[j];
+            T vd[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+              adv += q.bp[d] * Dd[d][j];
+              vd[d] = W * q.ap[d] * Dd[d][j];
+            }
+            adv *= W;
+#pragma unroll
+            for (int i = 0; i < N; ++i) {
+              T s = fma(Phi[i], adv, acc[i][j]);
+#pragma unroll
+              for (int d = 0; d < D; ++d) s = fma(Dd[d][i], vd[d], s);
+              acc[i][j] = s;
+            }
+          }
+        }
+        if (do_rhs) {
+          T x[D];
+#pragma unroll
+          for (int d = 0; d < D; ++d) x[d] = q.lo[d] + (xi[d] + T(1)) * T(0.5) * q.L[d];
+          const T fw = W * source_f<D, T>(m.pb, q.a, x);
+#pragma unroll
+          for (int i = 0; i < N; ++i) racc[i] = fma(Phi[i], fw, racc[i]);
+        }
+      }
+    }
+    if ((mat_vol || do_rhs) && !learned) {
       for (int sub = m.eptr[e]; sub < m.eptr[e + 1]; ++sub) {
         T sv[SV];
 #pragma unroll
@@ -663,7 +703,7 @@ struct RowSmem {
   static constexpr int C = ChunkCfg<D, T>::CW / G > 0 ? ChunkCfg<D, T>::CW / G : 1;
   static constexpr int PSU = point_stride<T, TMP>(NT * ROW);  // staged point: NT rows of ROW
   static constexpr int PT = 4 * D + 5;                         // T parameters per element
-  static constexpr int PI = 16;                                // int parameters per element
+  static constexpr int PI = 17;                                // int parameters per element
   static constexpr int NMAXC = nbasis(D, D == 2 ? kPMax2 : kPMax3);
   __host__ __device__ static constexpr int vs(int nmax) { return (nmax + TR * TM - 1) / (TR * TM) * (TR * TM); }
   __host__ __device__ static constexpr int psn(int VS) { return (2 * VS) % 2 ? 2 * VS : 2 * VS + 1; }  // odd
@@ -696,6 +736,7 @@ enum : int {
   kPiSF0,       // current slot: first face of the interface
   kPiSQF,       // current slot: points per face
   kPiSNpts,     // current slot: points of the interface
+  kPiLrn,       // 1: the element has a learned volume rule
 };
 // T parameter slots: a'[D], b'[D], lo[D], L[D], then:
 enum : int { kPtC = 0, kPtA = 1, kPtR = 2, kPtAk = 3, kPtRk = 4 };
@@ -755,8 +796,10 @@ __global__ void __launch_bounds__(kWarps * 32)
       T* pt = PTv + lane * PT;
       if (lane < gcount) {
         const int e = m.elem_perm[base + tile * G + lane];
+        const int lrn = m.lq_ok && m.lq_ok[e] ? 1 : 0;
         pi[kPiElem] = e;
-        pi[kPiNvol] = (m.eptr[e + 1] - m.eptr[e]) * QT;
+        pi[kPiLrn] = lrn;
+        pi[kPiNvol] = lrn ? 28 : (m.eptr[e + 1] - m.eptr[e]) * QT;
         pi[kPiNface] = m.e_nqf[e];
         pi[kPiSub0] = m.eptr[e];
         pi[kPiHf0] = m.hf_ptr[e];
@@ -814,20 +857,28 @@ __global__ void __launch_bounds__(kWarps * 32)
           T* Rr = R + (g * C + c) * NT;
           if (g < gcount && qv < PIv[g * PI + kPiNvol]) {
             const T* pt = PTv + g * PT;
-            const int t = qv / QT, r = qv - t * QT;
-            const int sub = PIv[g * PI + kPiSub0] + t;
-            T sv[SV];
+            T xi[D], W;
+            if (D == 2 && PIv[g * PI + kPiLrn]) {
+              // learned rule: 28 points in bounding-box coordinates, physical weights
+              const T* LQ = pick<T>(m.lq64, m.lq32) + (size_t)PIv[g * PI + kPiElem] * 84;
+              xi[0] = LQ[qv];
+              xi[1 % D] = LQ[28 + qv];
+              W = LQ[56 + qv];
+            } else {
+              const int t = qv / QT, r = qv - t * QT;
+              const int sub = PIv[g * PI + kPiSub0] + t;
+              T sv[SV];
 #pragma unroll
-            for (int k = 0; k < SV; ++k) sv[k] = SG[(size_t)k * m.nsub + sub];
-            const T* rr = rule + r * (D + 1);
-            T xi[D];
+              for (int k = 0; k < SV; ++k) sv[k] = SG[(size_t)k * m.nsub + sub];
+              const T* rr = rule + r * (D + 1);
 #pragma unroll
-            for (int d = 0; d < D; ++d) {
-              T v = sv[d] + rr[0] * sv[D + d] + rr[1] * sv[2 * D + d];
-              if constexpr (D == 3) v += rr[2] * sv[3 * D + d];
-              xi[d] = v;
+              for (int d = 0; d < D; ++d) {
+                T v = sv[d] + rr[0] * sv[D + d] + rr[1] * sv[2 * D + d];
+                if constexpr (D == 3) v += rr[2] * sv[3 * D + d];
+                xi[d] = v;
+              }
+              W = rr[D] * sv[SV - 1];
             }
-            const T W = rr[D] * sv[SV - 1];
             T Phi[N], Dd[D][N];
             basis_eval<D, P, T>(xi, Phi, Dd);
             T Vv[N];

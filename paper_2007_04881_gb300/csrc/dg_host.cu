@@ -143,6 +143,9 @@ struct DevBuf {
 
 }  // namespace
 
+int dg_fail_msg(int code, const char* msg) { return fail(code, "%s", msg); }
+cudaStream_t dg_ctx_stream(dg_ctx* ctx);
+
 namespace dg {
 void reference_rule(int dim, int n, std::vector<double>& pts) { simplex_rule(dim, n, pts); }
 int fail_na_impl(int code, const char* msg) { return fail(code, "%s", msg); }
@@ -231,9 +234,22 @@ struct dg_mesh {
   double* a = nullptr;
   double flops[2][9] = {{0}}, words[2][9] = {{0}};
   std::vector<int> batch_elem_off;  // element offset of each batch member (empty: one mesh)
+  // host copies used to rebuild the work list when volume rules change
+  std::vector<int> p_h, nvq_h, nqf_h;
+  std::vector<double> vfma_h;  // algorithmic FMAs per volume point of each element
+  std::vector<int> perm_fan;  // the sub-simplex-rule work list
+  // learned quadrature (2D)
+  double *lq_mom = nullptr, *lq_mmom = nullptr, *lq_rule = nullptr, *lq64 = nullptr;
+  float *lq32 = nullptr, *lq_resid = nullptr;
+  int *lq_elig = nullptr, *lq_ok = nullptr, *lq_okm = nullptr;
+  void* lq_feat = nullptr;
+  int* perm_dev = nullptr;  // device work list (owned by bufs)
   ~dg_mesh() {
     if (h_vals) cudaFree(h_vals);
     if (h_rhs) cudaFree(h_rhs);
+    void* q[] = {lq_mom, lq_mmom, lq_rule, lq64, lq32, lq_resid, lq_elig, lq_ok, lq_okm, lq_feat};
+    for (void* x : q)
+      if (x) cudaFree(x);
   }
 };
 
@@ -893,6 +909,25 @@ int dg_mesh_upload(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
   dm.rt = ctx->rt[dim];
 
   fill_info(d, P, m->info);
+  m->p_h.assign(d->p, d->p + ne);
+  m->nqf_h = e_nqf;
+  m->nvq_h.resize(ne);
+  m->vfma_h.resize(ne);
+  {
+    const bool adv = d->b[0] != 0.0 || d->b[1] != 0.0 || (dim == 3 && d->b[2] != 0.0) || d->c != 0.0;
+    for (int e = 0; e < ne; ++e) {
+      int qt = 1;
+      for (int q = 0; q < dim; ++q) qt *= d->p[e] + 2;
+      m->nvq_h[e] = (d->elem_ptr[e + 1] - d->elem_ptr[e]) * qt;
+      const double n = nbasis(dim, d->p[e]);
+      m->vfma_h[e] = dim * n * (n + 1) / 2 + (adv ? n * n + n * (dim + 1) : 0.0) + n * dim * dim + 5.0 * dim * d->p[e] + n;
+    }
+  }
+  m->perm_fan = elem_perm;
+  m->perm_dev = const_cast<int*>(dm.elem_perm);
+  dm.lq_ok = nullptr;
+  dm.lq64 = nullptr;
+  dm.lq32 = nullptr;
 
   cudaSetDevice(ctx->device);
   launch_geometry(dm, ctx->stream);
@@ -1244,6 +1279,126 @@ int dg_graph_free(dg_graph* g) {
   return DG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// learned quadrature
+// ---------------------------------------------------------------------------
+
+int dg_quad_prepare(dg_ctx* ctx, dg_mesh* mesh) {
+  if (!ctx || !mesh) return fail(DG_ERR_ARG, "dg_quad_prepare: null argument");
+  if (mesh->dm.dim != 2) return fail(DG_ERR_ARG, "dg_quad_prepare: learned rules are 2D only");
+  const int ne = mesh->dm.ne;
+  if (!mesh->lq_mom) {
+    struct {
+      void** p;
+      size_t bytes;
+    } a[] = {{(void**)&mesh->lq_mom, 28 * 8}, {(void**)&mesh->lq_mmom, 28 * 8}, {(void**)&mesh->lq_rule, 84 * 8},
+             {(void**)&mesh->lq64, 84 * 8},   {(void**)&mesh->lq32, 84 * 4},   {(void**)&mesh->lq_resid, 4},
+             {(void**)&mesh->lq_elig, 4},     {(void**)&mesh->lq_ok, 4},       {(void**)&mesh->lq_okm, 4},
+             {(void**)&mesh->lq_feat, 24 * 2}};
+    for (auto& x : a)
+      if (cudaMalloc(x.p, x.bytes * (size_t)ne) != cudaSuccess) return fail(DG_ERR_OOM, "dg_quad_prepare: buffers");
+    DG_CUDA_TRY(cudaMemsetAsync(mesh->lq_okm, 0, sizeof(int) * ne, ctx->stream));
+  }
+  lq_prepare(mesh->dm, mesh->lq_mom, mesh->lq_mmom, mesh->lq_feat, mesh->lq_elig, ctx->stream);
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+
+int dg_quad_buffers(const dg_mesh* mesh, const void** feat, const double** rules, const float** resid,
+                    const int** ok, const double** moments) {
+  if (!mesh || !mesh->lq_mom) return fail(DG_ERR_ARG, "dg_quad_buffers: call dg_quad_prepare first");
+  if (feat) *feat = mesh->lq_feat;
+  if (rules) *rules = mesh->lq_rule;
+  if (resid) *resid = mesh->lq_resid;
+  if (ok) *ok = mesh->lq_ok;
+  if (moments) *moments = mesh->lq_mom;
+  return DG_OK;
+}
+
+// rebuild the degree-grouped, cost-descending work list for the current rules
+static int rebuild_worklist(dg_ctx* ctx, dg_mesh* mesh, const std::vector<int>& learned) {
+  const int ne = mesh->dm.ne;
+  std::vector<int64_t> cost(ne);
+  for (int e = 0; e < ne; ++e) cost[e] = (learned.empty() || !learned[e] ? mesh->nvq_h[e] : 28) + mesh->nqf_h[e];
+  std::vector<int> perm(ne);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) {
+    if (mesh->p_h[x] != mesh->p_h[y]) return mesh->p_h[x] < mesh->p_h[y];
+    return cost[x] > cost[y];
+  });
+  DG_CUDA_TRY(cudaMemcpyAsync(mesh->perm_dev, perm.data(), sizeof(int) * ne, cudaMemcpyHostToDevice, ctx->stream));
+  DG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return DG_OK;
+}
+
+int dg_quad_fit(dg_ctx* ctx, dg_mesh* mesh, const float* init, int iters, int install, dg_quad_stats* stats) {
+  if (!ctx || !mesh || iters < 0) return fail(DG_ERR_ARG, "dg_quad_fit: bad argument");
+  if (!mesh->lq_mom) return fail(DG_ERR_ARG, "dg_quad_fit: call dg_quad_prepare first");
+  const int ne = mesh->dm.ne;
+  lq_gn(mesh->dm, mesh->lq_mom, mesh->lq_mmom, mesh->lq_elig, init, iters, mesh->lq_rule, mesh->lq_resid, mesh->lq_ok,
+        ctx->sm_count, ctx->stream);
+  DG_CUDA_TRY(cudaGetLastError());
+  if (install) {
+    lq_install(mesh->dm, mesh->lq_rule, mesh->lq_ok, mesh->lq64, mesh->lq32, mesh->lq_okm, ctx->stream);
+    DG_CUDA_TRY(cudaGetLastError());
+  }
+  if (stats || install) {
+    std::vector<int> ok(ne), elig(ne);
+    std::vector<float> res(ne);
+    DG_CUDA_TRY(cudaMemcpyAsync(ok.data(), mesh->lq_ok, sizeof(int) * ne, cudaMemcpyDeviceToHost, ctx->stream));
+    DG_CUDA_TRY(cudaMemcpyAsync(elig.data(), mesh->lq_elig, sizeof(int) * ne, cudaMemcpyDeviceToHost, ctx->stream));
+    DG_CUDA_TRY(cudaMemcpyAsync(res.data(), mesh->lq_resid, sizeof(float) * ne, cudaMemcpyDeviceToHost, ctx->stream));
+    DG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    if (stats) {
+      dg_quad_stats st{};
+      st.elements = ne;
+      float mx = 0.f;
+      for (int e = 0; e < ne; ++e) {
+        st.eligible += elig[e];
+        st.accepted += ok[e];
+        if (ok[e]) mx = std::max(mx, res[e]);
+      }
+      st.max_accepted_residual = mx;
+      *stats = st;
+    }
+    if (install) {
+      int rc = rebuild_worklist(ctx, mesh, ok);
+      if (rc != DG_OK) return rc;
+      mesh->dm.lq_ok = mesh->lq_okm;
+      mesh->dm.lq64 = mesh->lq64;
+      mesh->dm.lq32 = mesh->lq32;
+      // algorithmic volume work of learned elements: 28 points instead of the sub-triangle rule
+      for (int e = 0; e < ne; ++e)
+        if (ok[e]) mesh->flops[0][mesh->p_h[e]] -= 2.0 * (mesh->nvq_h[e] - 28) * mesh->vfma_h[e];
+    }
+  }
+  return DG_OK;
+}
+
+int dg_quad_targets(dg_ctx* ctx, dg_mesh* mesh, float* targets) {
+  if (!ctx || !mesh || !targets || !mesh->lq_rule) return fail(DG_ERR_ARG, "dg_quad_targets: bad argument");
+  lq_targets(mesh->dm.ne, mesh->lq_rule, mesh->lq_mmom, targets, ctx->stream);
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+
+int dg_quad_clear(dg_ctx* ctx, dg_mesh* mesh) {
+  if (!ctx || !mesh) return fail(DG_ERR_ARG, "dg_quad_clear: null argument");
+  if (mesh->dm.lq_ok) {
+    std::vector<int> ok(mesh->dm.ne, 0);
+    std::vector<int> okd(mesh->dm.ne);
+    DG_CUDA_TRY(cudaMemcpy(okd.data(), mesh->lq_okm, sizeof(int) * mesh->dm.ne, cudaMemcpyDeviceToHost));
+    for (int e = 0; e < mesh->dm.ne; ++e)
+      if (okd[e]) mesh->flops[0][mesh->p_h[e]] += 2.0 * (mesh->nvq_h[e] - 28) * mesh->vfma_h[e];
+    int rc = rebuild_worklist(ctx, mesh, ok);
+    if (rc != DG_OK) return rc;
+  }
+  mesh->dm.lq_ok = nullptr;
+  mesh->dm.lq64 = nullptr;
+  mesh->dm.lq32 = nullptr;
+  return DG_OK;
+}
+
 int dg_set_timing(dg_ctx* ctx, int enable) {
   if (!ctx) return fail(DG_ERR_ARG, "dg_set_timing: null context");
   if (enable && ctx->recs.empty()) {
@@ -1308,5 +1463,11 @@ int dg_sync(dg_ctx* ctx) {
 }
 
 int dg_last_launch_count(const dg_ctx* ctx) { return ctx ? ctx->last_launches : 0; }
+
+}  // extern "C"
+
+cudaStream_t dg_ctx_stream(dg_ctx* ctx) { return ctx->stream; }
+
+extern "C" {
 
 }  // extern "C"

@@ -118,6 +118,11 @@ struct DevMesh {
   int if_pstart[9];
   Problem pb;
   RuleTables rt;
+  // learned volume rules (2D): per element 28 points (xi, eta) and physical
+  // weights, used where lq_ok[e] != 0; null when none are installed
+  const int* lq_ok;
+  const double* lq64;  // [ne][84]
+  const float* lq32;
 };
 
 // mode bits of the element kernel
@@ -169,6 +174,14 @@ int launch_row2d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm
 int launch_row3d_f64(const DevMesh& m, int mode, double* vals, double* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);
 int launch_row3d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);
 
+// learned quadrature (dg_learned.cu)
+void lq_prepare(const DevMesh& m, double* mom, double* mmom, void* feat, int* elig, cudaStream_t st);
+void lq_gn(const DevMesh& m, const double* mom, const double* mmom, const int* elig, const float* init, int iters,
+           double* rule, float* resid, int* ok, int sm_count, cudaStream_t st);
+void lq_install(const DevMesh& m, const double* rule, const int* ok, double* lq64, float* lq32, int* lq_ok,
+                cudaStream_t st);
+void lq_targets(int ne, const double* rule, const double* mmom, float* tgt, cudaStream_t st);
+
 // Host: collapsed reference rule on the d-simplex with n Gauss points per
 // direction, packed as [point][d+1] = (coordinates, weight); d = 1 gives the
 // n-point Gauss-Legendre rule on [0,1].
@@ -177,3 +190,8 @@ int launch_row3d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm
 namespace dg {
 void reference_rule(int dim, int n, std::vector<double>& pts);
 }  // namespace dg
+
+// shared by the host translation units
+struct dg_ctx;
+cudaStream_t dg_ctx_stream(dg_ctx* ctx);
+int dg_fail_msg(int code, const char* msg);

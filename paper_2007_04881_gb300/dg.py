@@ -62,6 +62,11 @@ class dg_kernel_stat(C.Structure):
     _fields_ = [("name", C.c_char * 48), ("ms", C.c_float), ("flops", C.c_double), ("bytes", C.c_double)]
 
 
+class dg_quad_stats(C.Structure):
+    _fields_ = [("elements", C.c_int), ("eligible", C.c_int), ("accepted", C.c_int),
+                ("max_accepted_residual", C.c_float)]
+
+
 class dg_bsr_info(C.Structure):
     _fields_ = [
         ("ne", C.c_int),
@@ -115,6 +120,21 @@ def load() -> C.CDLL:
     lib.dg_graph_free.argtypes = [V]
     lib.dg_volume_noalloc.argtypes = [V, C.c_int, C.c_int, C.c_int, C.c_int, V, V, C.c_int, C.c_int, V, V, V,
                                       C.c_double, C.c_double, C.c_double, V]
+    lib.dg_quad_prepare.argtypes = [V, V]
+    lib.dg_quad_fit.argtypes = [V, V, V, C.c_int, C.c_int, C.POINTER(dg_quad_stats)]
+    lib.dg_quad_targets.argtypes = [V, V, V]
+    lib.dg_quad_buffers.argtypes = [V, C.POINTER(V), C.POINTER(V), C.POINTER(V), C.POINTER(V), C.POINTER(V)]
+    lib.dg_quad_clear.argtypes = [V, V]
+    lib.dg_mlp_create.argtypes = [V, C.c_int, C.POINTER(V)]
+    lib.dg_mlp_free.argtypes = [V]
+    lib.dg_mlp_num_params.restype = C.c_int64
+    lib.dg_mlp_get_params.argtypes = [V, V, C.POINTER(C.c_int64)]
+    lib.dg_mlp_set_params.argtypes = [V, V, C.c_int64]
+    lib.dg_mlp_get_state.argtypes = [V, V, V]
+    lib.dg_mlp_set_state.argtypes = [V, V, V]
+    lib.dg_mlp_forward.argtypes = [V, V, V, C.c_int, V]
+    lib.dg_mlp_grad.argtypes = [V, V, V, V, C.c_int, V, V]
+    lib.dg_mlp_train_step.argtypes = [V, V, V, V, C.c_int, C.c_float, V]
     lib.dg_sync.argtypes = [V]
     lib.dg_last_launch_count.argtypes = [V]
     _lib = lib
@@ -129,6 +149,9 @@ EXPORTS = (
     "dg_assemble_rhs", "dg_assemble", "dg_assemble_host", "dg_sync", "dg_last_launch_count",
     "dg_assemble_step", "dg_set_timing", "dg_kernel_stats", "dg_batch_upload", "dg_batch_offsets",
     "dg_graph_create", "dg_graph_launch", "dg_graph_info", "dg_graph_free", "dg_volume_noalloc",
+    "dg_quad_prepare", "dg_quad_fit", "dg_quad_targets", "dg_quad_buffers", "dg_quad_clear",
+    "dg_mlp_create", "dg_mlp_free", "dg_mlp_num_params", "dg_mlp_get_params", "dg_mlp_set_params",
+    "dg_mlp_get_state", "dg_mlp_set_state", "dg_mlp_forward", "dg_mlp_grad", "dg_mlp_train_step",
 )
 
 
@@ -331,6 +354,28 @@ class Mesh:
         _check(load().dg_graph_create(self.ctx._h, self._h, prec, _vp(vals), _vp(rhs), int(autotune), C.byref(h)))
         return Graph(self.ctx, h)
 
+    # ---- learned volume rules (2D)
+    def dg_quad_prepare(self):
+        _check(load().dg_quad_prepare(self.ctx._h, self._h))
+
+    def dg_quad_fit(self, init=None, iters: int = 3, install: bool = False):
+        st = dg_quad_stats()
+        _check(load().dg_quad_fit(self.ctx._h, self._h, _vp(init), int(iters), int(install), C.byref(st)))
+        return {"elements": st.elements, "eligible": st.eligible, "accepted": st.accepted,
+                "max_accepted_residual": st.max_accepted_residual}
+
+    def dg_quad_targets(self, out):
+        _check(load().dg_quad_targets(self.ctx._h, self._h, _vp(out)))
+
+    def dg_quad_buffers(self):
+        """Raw device addresses of the library-owned learned-rule arrays."""
+        f, r, e, o, mo = (C.c_void_p() for _ in range(5))
+        _check(load().dg_quad_buffers(self._h, C.byref(f), C.byref(r), C.byref(e), C.byref(o), C.byref(mo)))
+        return {"feat": f.value, "rules": r.value, "resid": e.value, "ok": o.value, "moments": mo.value}
+
+    def dg_quad_clear(self):
+        _check(load().dg_quad_clear(self.ctx._h, self._h))
+
     def dg_assemble_step(self, prec: int, vals, rhs=None):
         _check(load().dg_assemble_step(self.ctx._h, self._h, prec, _vp(vals), _vp(rhs)))
 
@@ -351,6 +396,73 @@ def dg_volume_noalloc(stream, device: int, prec: int, p: int, x, y, elem_ptr, el
     _check(load().dg_volume_noalloc(stream, int(device), int(prec), int(p), int(x.numel()), _vp(x), _vp(y),
                                     int(a.numel()), int(nsub), _vp(elem_ptr), _vp(elem_idx), _vp(a), float(bx),
                                     float(by), float(c), _vp(blocks)))
+
+
+def device_view(ptr: int, shape, dtype: str):
+    """A torch tensor viewing library-owned device memory (no copy).
+    dtype: 'f8', 'f4', 'i4' or 'bf16'."""
+    import torch
+
+    typestr = {"f8": "<f8", "f4": "<f4", "i4": "<i4", "bf16": "<i2"}[dtype]
+
+    class _View:
+        __cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (int(ptr), False),
+                                    "version": 3}
+
+    t = torch.as_tensor(_View(), device="cuda")
+    return t.view(torch.bfloat16) if dtype == "bf16" else t
+
+
+class MLP:
+    """The quadrature-proposal network (dg_mlp_*)."""
+
+    def __init__(self, ctx: Context, seed: int = 0):
+        self.ctx = ctx
+        h = C.c_void_p()
+        _check(load().dg_mlp_create(ctx._h, int(seed), C.byref(h)))
+        self._h = h
+        self.nparams = int(load().dg_mlp_num_params())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().dg_mlp_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        out = np.zeros(self.nparams, np.float32)
+        step = C.c_int64()
+        _check(load().dg_mlp_get_params(self._h, _vp(out), C.byref(step)))
+        return out, step.value
+
+    def set_params(self, params, step: int = 0):
+        params = np.ascontiguousarray(params, dtype=np.float32)
+        _check(load().dg_mlp_set_params(self._h, _vp(params), int(step)))
+
+    def get_state(self):
+        m1 = np.zeros(self.nparams, np.float32)
+        m2 = np.zeros(self.nparams, np.float32)
+        _check(load().dg_mlp_get_state(self._h, _vp(m1), _vp(m2)))
+        return m1, m2
+
+    def set_state(self, m1, m2):
+        m1 = np.ascontiguousarray(m1, dtype=np.float32)
+        m2 = np.ascontiguousarray(m2, dtype=np.float32)
+        _check(load().dg_mlp_set_state(self._h, _vp(m1), _vp(m2)))
+
+    def forward(self, x_bf16, n: int, out):
+        _check(load().dg_mlp_forward(self.ctx._h, self._h, _vp(x_bf16), int(n), _vp(out)))
+
+    def grad(self, x_bf16, target, n: int, grad, loss):
+        _check(load().dg_mlp_grad(self.ctx._h, self._h, _vp(x_bf16), _vp(target), int(n), _vp(grad), _vp(loss)))
+
+    def train_step(self, x_bf16, target, n: int, lr: float, loss=None):
+        _check(load().dg_mlp_train_step(self.ctx._h, self._h, _vp(x_bf16), _vp(target), int(n), float(lr), _vp(loss)))
 
 
 class Graph:

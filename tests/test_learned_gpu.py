@@ -1,0 +1,223 @@
+"""GPU parity of the learned reduced quadrature against its oracle: moments,
+network input, Gauss-Newton, network gradients, learned-rule assembly, and
+the gain the trained network brings over the fixed starting rule."""
+import numpy as np
+import pytest
+
+import oracle.learned as L
+from paper_2007_04881_gb300 import configs, dg
+
+from .helpers import dg_problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(cuda):
+    import torch
+
+    from paper_2007_04881_gb300 import build as B
+
+    B.build()
+    c = dg.Context(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    c.close()
+
+
+def _mesh(ctx, n=300, seed=41, p=3):
+    wl = configs.small2d(n, seed, p, p)
+    return wl, dg.Mesh(ctx, wl.mesh, wl.p, wl.a, dg_problem(wl))
+
+
+def _cell(wl, e):
+    v = wl.mesh.elem_v[wl.mesh.elem_vptr[e]:wl.mesh.elem_vptr[e + 1]]
+    return wl.mesh.x[v], wl.mesh.y[v]
+
+
+def test_moments_and_features(ctx):
+    import torch
+
+    wl, m = _mesh(ctx)
+    m.dg_quad_prepare()
+    ctx.dg_sync()
+    b = m.dg_quad_buffers()
+    mom = dg.device_view(b["moments"], (m.ne, 28), "f8").cpu().numpy()
+    feat = dg.device_view(b["feat"], (m.ne, 24), "bf16").float().cpu().numpy()
+    for e in range(m.ne):
+        xi, eta = L.normalize(*_cell(wl, e))
+        np.testing.assert_allclose(mom[e], L.lp_moments(xi, eta), atol=1e-13)
+        s = int(np.lexsort((eta, xi))[-1])  # largest xi, then largest eta
+        ref = np.zeros(24, np.float32)
+        k = xi.size
+        for i in range(min(k, 12)):
+            ref[2 * i] = xi[(s + i) % k]
+            ref[2 * i + 1] = eta[(s + i) % k]
+        np.testing.assert_allclose(feat[e], L.bf16_round(ref), atol=1e-2, rtol=8e-3)
+
+
+def test_gauss_newton_matches_oracle(ctx):
+    wl, m = _mesh(ctx)
+    m.dg_quad_prepare()
+    st = m.dg_quad_fit(None, iters=8, install=False)
+    ctx.dg_sync()
+    b = m.dg_quad_buffers()
+    rules = dg.device_view(b["rules"], (m.ne, 84), "f8").cpu().numpy()
+    ok = dg.device_view(b["ok"], (m.ne,), "i4").cpu().numpy()
+    assert st["eligible"] == m.ne and st["accepted"] == int(ok.sum())
+    agree = 0
+    for e in range(0, m.ne, 3):
+        xi, eta = L.normalize(*_cell(wl, e))
+        M = L.lp_moments(xi, eta)
+        z = L.canonical_rule(M[0])
+        for _ in range(8):
+            z = L.gn_step(z, M)
+        o_ok, _ = L.accept(z, xi, eta)
+        g_ok, g_res = L.accept(rules[e], xi, eta)
+        assert g_ok == bool(ok[e])
+        if o_ok and g_ok:
+            np.testing.assert_allclose(rules[e], z, atol=1e-8)
+            agree += 1
+    assert agree > 0.9 * len(range(0, m.ne, 3))
+
+
+def _params_np(P):
+    sizes = [(24, 128), (128,), (128, 128), (128,), (128, 84), (84,)]
+    out, o = [], 0
+    for s in sizes:
+        n = int(np.prod(s))
+        out.append(P[o:o + n].reshape(s).astype(np.float64))
+        o += n
+    return out
+
+
+def test_mlp_gradients_match_oracle(ctx):
+    import torch
+
+    net = dg.MLP(ctx, seed=5)
+    P, _ = net.get_params()
+    rng = np.random.default_rng(2)
+    n = 300
+    X = rng.uniform(-1, 1, (n, 24)).astype(np.float32)
+    T = rng.normal(0, 0.3, (n, 84)).astype(np.float32)
+    xb = torch.from_numpy(X).cuda().to(torch.bfloat16)
+    tg = torch.from_numpy(T).cuda()
+    grad = torch.zeros(net.nparams, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    net.grad(xb, tg, n, grad, loss)
+    ctx.dg_sync()
+    # oracle in FP64 on the same bfloat16-rounded inputs and weights
+    params = _params_np(P)
+    for i in (0, 2, 4):
+        params[i] = L.bf16_round(params[i]).astype(np.float64)
+    lo, go = L.mlp_loss_grad(params, L.bf16_round(X).astype(np.float64), T.astype(np.float64))
+    assert abs(float(loss.item()) - lo) < 2e-2 * lo
+    g = grad.cpu().numpy()
+    off = 0
+    for G in go:
+        k = G.size
+        got = g[off:off + k]
+        rel = np.linalg.norm(got - G.ravel()) / np.linalg.norm(G)
+        assert rel < 3e-2, rel
+        off += k
+    net.close()
+
+
+def test_training_reduces_loss(ctx):
+    import torch
+
+    net = dg.MLP(ctx, seed=1)
+    rng = np.random.default_rng(3)
+    n = 2048
+    X = rng.uniform(-1, 1, (n, 24)).astype(np.float32)
+    W = rng.normal(0, 0.3, (24, 84)).astype(np.float32)
+    T = np.tanh(X @ W).astype(np.float32)
+    xb = torch.from_numpy(X).cuda().to(torch.bfloat16)
+    tg = torch.from_numpy(T).cuda()
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    net.grad(xb, tg, n, None, loss)
+    l0 = float(loss.item())
+    for _ in range(300):
+        net.train_step(xb, tg, n, 3e-3, loss)
+    ctx.dg_sync()
+    assert float(loss.item()) < 0.1 * l0
+    # checkpoint round trip: parameters and Adam state
+    P, step = net.get_params()
+    m1, m2 = net.get_state()
+    net2 = dg.MLP(ctx, seed=9)
+    net2.set_params(P, step)
+    net2.set_state(m1, m2)
+    o1 = torch.zeros(n, 84, device="cuda")
+    o2 = torch.zeros(n, 84, device="cuda")
+    net.forward(xb, n, o1)
+    net2.forward(xb, n, o2)
+    ctx.dg_sync()
+    assert torch.equal(o1, o2)
+    net.close()
+    net2.close()
+
+
+def test_learned_rule_assembly_matches_subtriangle_rule(ctx):
+    """Accepted rules reproduce the P_6 moments to 1e-10, so the p = 3
+    volume blocks (polynomial integrands) agree with the sub-triangle rule."""
+    import torch
+
+    wl, m = _mesh(ctx, n=400, seed=44)
+    vals_f = torch.zeros(m.nvals, dtype=torch.float64, device="cuda")
+    m.dg_assemble(dg.DG_PREC_FP64, vals_f)
+    m.dg_quad_prepare()
+    st = m.dg_quad_fit(None, iters=8, install=True)
+    assert st["accepted"] > 0.9 * m.ne
+    vals_l = torch.zeros(m.nvals, dtype=torch.float64, device="cuda")
+    m.dg_assemble(dg.DG_PREC_FP64, vals_l)
+    ctx.dg_sync()
+    a = dg.to_blocks(m, vals_f.cpu().numpy())["diag"]
+    b = dg.to_blocks(m, vals_l.cpu().numpy())["diag"]
+    worst = max(np.abs(a[e] - b[e]).max() / np.abs(a[e]).max() for e in range(m.ne))
+    assert worst < 1e-8, worst
+    m.dg_quad_clear()
+    vals_c = torch.zeros(m.nvals, dtype=torch.float64, device="cuda")
+    m.dg_assemble(dg.DG_PREC_FP64, vals_c)
+    ctx.dg_sync()
+    assert torch.equal(vals_c, vals_f)
+
+
+def test_trained_network_beats_fixed_start(ctx):
+    """Train on the method's own converged rules; with 3 Gauss-Newton steps
+    the network's proposals are accepted far more often than the fixed
+    starting rule's."""
+    import torch
+
+    feats, tgts = [], []
+    for seed in (101, 102, 103):
+        wl, m = _mesh(ctx, n=3000, seed=seed)
+        m.dg_quad_prepare()
+        m.dg_quad_fit(None, iters=10, install=False)
+        t = torch.zeros(m.ne, 84, dtype=torch.float32, device="cuda")
+        m.dg_quad_targets(t)
+        b = m.dg_quad_buffers()
+        ok = dg.device_view(b["ok"], (m.ne,), "i4").clone().bool()
+        feats.append(dg.device_view(b["feat"], (m.ne, 24), "bf16").clone()[ok])
+        tgts.append(t[ok])
+    X = torch.cat(feats)
+    T = torch.cat(tgts)
+    net = dg.MLP(ctx, seed=0)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    bs = 512
+    for epoch in range(60):
+        perm = torch.randperm(X.shape[0], device="cuda", generator=g)
+        for i in range(0, X.shape[0] - bs + 1, bs):
+            idx = perm[i:i + bs]
+            net.train_step(X[idx].contiguous(), T[idx].contiguous(), bs, 2e-3 if epoch < 40 else 5e-4)
+    wl, m = _mesh(ctx, n=2000, seed=200)
+    m.dg_quad_prepare()
+    fixed = m.dg_quad_fit(None, iters=3, install=False)
+    b = m.dg_quad_buffers()
+    out = torch.zeros(m.ne, 84, dtype=torch.float32, device="cuda")
+    net.forward(b["feat"], m.ne, out)
+    learned = m.dg_quad_fit(out, iters=3, install=False)
+    ctx.dg_sync()
+    r_fixed = fixed["accepted"] / m.ne
+    r_learned = learned["accepted"] / m.ne
+    assert r_learned > r_fixed + 0.3, (r_fixed, r_learned)
+    net.close()
