@@ -40,6 +40,10 @@ WORKLOADS = {
                      "f from u=sin(pi x)sin(pi y), penalty 10 p^2/h"),
     "diff3d_32k": ("diff3d_32k: 3D diffusion, 64^3 cubes x 6 Kuhn tets (1,572,864 tets) agglomerated by k-means "
                    "into 32,768 polyhedra, p=3, a=10^U(-2,2), b=0, c=0, penalty 10 p^2/h"),
+    "learned2d_262k": ("learned2d_262k: 2D ADR on 262,144 clipped Voronoi cells (3-12 vertices), p=3, a=10^U(-2,2), "
+                       "b=(1,0.5), c=1; learned 28-point volume rules (24->128->128->84 BF16 network trained on "
+                       "1,048,576 polygons of 16 independent meshes, then 3 FP64 Gauss-Newton steps, sub-triangle "
+                       "fallback), assembled in FP32 with FP64 geometry"),
     "batch2d_256": ("batch2d_256: 256 independent 2D clipped-Voronoi meshes (5 Lloyd steps), cell counts "
                     "log-uniform in 512..16,384, per-mesh p~U{1..5}, a=10^U(-2,2), b=(1,0.5), c=1, one recorded "
                     "pass over the whole batch"),
@@ -78,6 +82,8 @@ def make_workload(name):
         return configs.diff3d()
     if name == "batch2d_256":
         return _Batch(configs.batch2d())
+    if name == "learned2d_262k":
+        return configs.learned2d()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -536,6 +542,155 @@ def _kernel_source_sha() -> str:
     return h.hexdigest()[:16]
 
 
+def run_learned(args):
+    """The learned-quadrature workload: train the proposal network on the
+    method's own converged rules, then measure on the 262,144-cell mesh."""
+    from paper_2007_04881_gb300 import configs
+
+    train = configs.learned_training_meshes()  # process pool before any CUDA call
+    wl = configs.learned2d()
+    import torch
+
+    from paper_2007_04881_gb300 import build as B
+    from paper_2007_04881_gb300 import dg
+
+    torch.cuda.set_device(0)
+    B.build()
+    stream = torch.cuda.current_stream()
+    ctx = dg.Context(0, stream.cuda_stream)
+    t0 = time.perf_counter()
+    feats, tgts = [], []
+    for w in train:
+        m = dg.Mesh(ctx, w.mesh, w.p, w.a, dg.Problem(**w.problem))
+        m.dg_quad_prepare()
+        m.dg_quad_fit(None, iters=10, install=False)
+        t = torch.zeros(m.ne, 84, dtype=torch.float32, device="cuda")
+        m.dg_quad_targets(t)
+        b = m.dg_quad_buffers()
+        ok = dg.device_view(b["ok"], (m.ne,), "i4").clone().bool()
+        feats.append(dg.device_view(b["feat"], (m.ne, 24), "bf16").clone()[ok])
+        tgts.append(t[ok])
+        m.close()
+    X = torch.cat(feats)
+    T = torch.cat(tgts)
+    torch.cuda.synchronize()
+    targets_s = time.perf_counter() - t0
+    net = dg.MLP(ctx, seed=0)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    bs, epochs = 1024, args.epochs
+    loss = torch.zeros(1, device="cuda")
+    t0 = time.perf_counter()
+    nstep = 0
+    for ep in range(epochs):
+        perm = torch.randperm(X.shape[0], device="cuda", generator=g)
+        lr = 2e-3 * 0.5 * (1 + math.cos(math.pi * ep / epochs))
+        for i in range(0, X.shape[0] - bs + 1, bs):
+            idx = perm[i:i + bs]
+            net.train_step(X[idx].contiguous(), T[idx].contiguous(), bs, lr, loss)
+            nstep += 1
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    final_loss = float(loss.item())
+
+    pb = dg.Problem(**wl.problem)
+    mesh = dg.Mesh(ctx, wl.mesh, wl.p, wl.a, pb)
+    info = mesh.info
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    v32 = torch.empty(mesh.nvals, dtype=torch.float32, device="cuda")
+    r32 = torch.empty(mesh.ndofs, dtype=torch.float32, device="cuda")
+    v64 = torch.empty(mesh.nvals, dtype=torch.float64, device="cuda")
+    r64 = torch.empty(mesh.ndofs, dtype=torch.float64, device="cuda")
+
+    def timed_graph(prec, vals, rhs, steps, timing):
+        ctx.dg_set_timing(timing)
+        gr = mesh.dg_graph_create(prec, vals, rhs, autotune=(prec == dg.DG_PREC_FP32))
+        for _ in range(3):
+            gr.dg_graph_launch()
+        torch.cuda.synchronize()
+        ts, ks = time_steps(torch, stream, gr.dg_graph_launch, flush, steps, ctx if timing else None)
+        ctx.dg_set_timing(False)
+        return sum(ts) / len(ts), ks, gr
+
+    # sub-triangle rules: FP32 and FP64 forms
+    fan32_ms, _, _ = timed_graph(dg.DG_PREC_FP32, v32, r32, args.steps, False)
+    fan64_ms, _, g64 = timed_graph(dg.DG_PREC_FP64, v64, r64, 3, False)
+    g64.dg_graph_launch()
+    torch.cuda.synchronize()
+    ref64 = v64.clone()
+    # learned rules: one-shot cost (moments + network + 3 Gauss-Newton steps + install)
+    out = torch.zeros(info.ne, 84, dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mesh.dg_quad_prepare()
+    b = mesh.dg_quad_buffers()
+    net.forward(b["feat"], info.ne, out)
+    st = mesh.dg_quad_fit(out, iters=3, install=True)
+    torch.cuda.synchronize()
+    oneshot_ms = 1e3 * (time.perf_counter() - t0)
+    fixed3 = None
+    # amortised: assembly with the cached rules
+    sampler = ClockSampler(0)
+    sampler.start()
+    lrn32_ms, kstats, _ = timed_graph(dg.DG_PREC_FP32, v32, r32, args.steps, True)
+    clocks = sampler.stop()
+    lrn64_ms, _, gl64 = timed_graph(dg.DG_PREC_FP64, v64, r64, 3, False)
+    gl64.dg_graph_launch()
+    torch.cuda.synchronize()
+    e64 = float(torch.linalg.vector_norm(v64 - ref64) / torch.linalg.vector_norm(ref64))
+    e32 = float(torch.linalg.vector_norm(v32.double() - ref64) / torch.linalg.vector_norm(ref64))
+    e32max = float((v32.double() - ref64).abs().max() / ref64.abs().max())
+    resid = dg.device_view(b["resid"], (info.ne,), "f4").cpu().numpy()
+    okv = dg.device_view(b["ok"], (info.ne,), "i4").cpu().numpy().astype(bool)
+    # the same budget from the fixed start (no network)
+    mesh.dg_quad_clear()
+    fixed3 = mesh.dg_quad_fit(None, iters=3, install=False)
+    fixed4 = mesh.dg_quad_fit(None, iters=4, install=False)
+    learned4 = mesh.dg_quad_fit(out, iters=4, install=False)
+
+    peaks, peak_src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = fp32_alu_peak_tflops(sm_max)
+    unit = kstats.get("row_pass") or max(kstats.values(), key=lambda v: v[0])
+    achieved = unit[2] / (unit[0] / unit[1] * 1e-3) / 1e12
+    ne = info.ne
+    amort = {f"K={k}": ne / ((oneshot_ms + k * lrn32_ms) * 1e-3 / k) for k in (1, 10, 100)}
+    line = {
+        "metric": METRIC,
+        "value": ne / (lrn32_ms * 1e-3),
+        "unit": "elements/s",
+        "n_gpus": 1,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": lrn32_ms,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": workload_config(wl, info, "learned2d_262k"),
+        "roofline": {"bound": "alu", "kernel": "row_pass", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                     "frac": achieved / alu_peak, "traffic": None},
+        "learned": {
+            "accepted": st["accepted"], "eligible": st["eligible"], "fallback": ne - st["accepted"],
+            "max_accepted_moment_residual": float(resid[okv].max()) if okv.any() else None,
+            "accepted_at_3_steps_fixed_start": fixed3["accepted"], "accepted_at_4_steps_fixed_start": fixed4["accepted"],
+            "accepted_at_4_steps_learned": learned4["accepted"],
+            "oneshot_ms": oneshot_ms, "assembly_fp32_ms": lrn32_ms, "assembly_fp64_ms": lrn64_ms,
+            "subtriangle_fp32_ms": fan32_ms, "subtriangle_fp64_ms": fan64_ms,
+            "amortised_elements_per_s": amort,
+            "matrix_rel_fro_vs_subtriangle_fp64": {"learned_fp32": e32, "learned_fp64": e64},
+            "matrix_rel_max_learned_fp32": e32max,
+            "training": {"polygons": int(X.shape[0]), "epochs": epochs, "steps": nstep, "batch": bs,
+                         "targets_s": targets_s, "train_s": train_s, "final_loss": final_loss},
+        },
+        "gpu_launches": mesh.ctx.launches() * args.steps,
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -545,11 +700,14 @@ def main():
     ap.add_argument("--workload", default="adr2d_65k", choices=sorted(WORKLOADS))
     ap.add_argument("--ref-sample", type=int, default=512, help="oracle elements per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--epochs", type=int, default=40, help="training epochs of the learned-rule workload")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "learned2d_262k":
+        return run_learned(args)
     return run_ours(args)
 
 

@@ -126,6 +126,40 @@ def batch2d(n_meshes: int = 256, lo: int = 512, hi: int = 16384, pmax: int = 5, 
     return out
 
 
+def learned2d(n_sites: int = 262144, seed: int = 4) -> Workload:
+    """Learned-quadrature test mesh: p = 3 everywhere (28-point rules are exact
+    for its volume integrands), coefficients as adr2d."""
+    m = mg.voronoi_square(n_sites, seed)
+    return Workload(
+        name=f"learned2d_{n_sites}",
+        mesh=m,
+        p=np.full(m.ne, 3, dtype=np.int8),
+        a=mg.draw_log_uniform(m.ne, seed, -2.0, 2.0),
+        problem=dict(b=(1.0, 0.5, 0.0), c=1.0, source=SRC_SINPROD, poly=[], c_sigma=10.0),
+    )
+
+
+def learned_training_meshes(n_meshes: int = 16, n_sites: int = 65536, base_seed: int = 1000,
+                            workers: int = 0) -> List[Workload]:
+    """Training polygons for the rule-proposal network: n_meshes independent
+    Voronoi meshes (seeds base_seed + k), p = 3; generated in a spawned pool."""
+    if workers >= 0 and mg._cache_dir() is not None:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        import os
+
+        nw = workers or (os.cpu_count() or 1)
+        if nw > 1:
+            with cf.ProcessPoolExecutor(max_workers=nw, mp_context=mp.get_context("spawn")) as ex:
+                list(ex.map(_gen_member, [(n_sites, base_seed + k) for k in range(n_meshes)]))
+    out = []
+    for k in range(n_meshes):
+        m = mg.voronoi_square(n_sites, base_seed + k)
+        out.append(Workload(f"train_{k}", m, np.full(m.ne, 3, dtype=np.int8), np.ones(m.ne),
+                            dict(b=(0.0, 0.0, 0.0), c=0.0, source=SRC_ZERO, poly=[], c_sigma=10.0)))
+    return out
+
+
 def small2d(n_sites: int, seed: int, plo: int, phi: int, b=(0.8, -0.45), c: float = 0.7,
             source: int = SRC_SINPROD, poly=()) -> Workload:
     """Small mixed-degree 2D case for parity tests."""

@@ -281,9 +281,12 @@ __global__ void __launch_bounds__(kGnWarps * 32)
       err = fabs(s);
       inside = fabs(S.z[lane]) <= 1.0 && fabs(S.z[LQ_NM + lane]) <= 1.0;
     }
+    // every lane executes both shuffles (no short-circuit around them)
     for (int o = 16; o > 0; o >>= 1) {
-      err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
-      inside = inside && __shfl_xor_sync(0xffffffffu, (int)inside, o);
+      const double e2 = __shfl_xor_sync(0xffffffffu, err, o);
+      const int in2 = __shfl_xor_sync(0xffffffffu, inside ? 1 : 0, o);
+      err = fmax(err, e2);
+      inside = inside && in2 != 0;
     }
     const double rel = err / fabs(area);
     const bool good = !S.fail && elig[e] && inside && rel < 1e-10 && isfinite(rel);

@@ -182,14 +182,16 @@ def test_learned_rule_assembly_matches_subtriangle_rule(ctx):
 
 
 def test_trained_network_beats_fixed_start(ctx):
-    """Train on the method's own converged rules; with 3 Gauss-Newton steps
-    the network's proposals are accepted far more often than the fixed
-    starting rule's."""
+    """Train on the method's own converged rules (Gauss-Newton run to
+    convergence from the fixed 4 x 7 start).  Under the same Gauss-Newton
+    budget the network's proposals are accepted far more often than the
+    fixed start: at 3 steps the fixed start never reaches 1e-10, and at 4
+    steps well under half of its rules do."""
     import torch
 
     feats, tgts = [], []
     for seed in (101, 102, 103):
-        wl, m = _mesh(ctx, n=3000, seed=seed)
+        wl, m = _mesh(ctx, n=16384, seed=seed)
         m.dg_quad_prepare()
         m.dg_quad_fit(None, iters=10, install=False)
         t = torch.zeros(m.ne, 84, dtype=torch.float32, device="cuda")
@@ -203,21 +205,24 @@ def test_trained_network_beats_fixed_start(ctx):
     net = dg.MLP(ctx, seed=0)
     g = torch.Generator(device="cuda")
     g.manual_seed(0)
-    bs = 512
-    for epoch in range(60):
+    bs, epochs = 1024, 120
+    for epoch in range(epochs):
         perm = torch.randperm(X.shape[0], device="cuda", generator=g)
+        lr = 2e-3 * 0.5 * (1 + np.cos(np.pi * epoch / epochs))
         for i in range(0, X.shape[0] - bs + 1, bs):
             idx = perm[i:i + bs]
-            net.train_step(X[idx].contiguous(), T[idx].contiguous(), bs, 2e-3 if epoch < 40 else 5e-4)
-    wl, m = _mesh(ctx, n=2000, seed=200)
+            net.train_step(X[idx].contiguous(), T[idx].contiguous(), bs, lr)
+    wl, m = _mesh(ctx, n=4096, seed=200)
     m.dg_quad_prepare()
-    fixed = m.dg_quad_fit(None, iters=3, install=False)
     b = m.dg_quad_buffers()
     out = torch.zeros(m.ne, 84, dtype=torch.float32, device="cuda")
     net.forward(b["feat"], m.ne, out)
-    learned = m.dg_quad_fit(out, iters=3, install=False)
+    rate = {}
+    for it in (3, 4):
+        rate[("fixed", it)] = m.dg_quad_fit(None, iters=it)["accepted"] / m.ne
+        rate[("learned", it)] = m.dg_quad_fit(out, iters=it)["accepted"] / m.ne
     ctx.dg_sync()
-    r_fixed = fixed["accepted"] / m.ne
-    r_learned = learned["accepted"] / m.ne
-    assert r_learned > r_fixed + 0.3, (r_fixed, r_learned)
+    assert rate[("fixed", 3)] < 0.01, rate
+    assert rate[("learned", 3)] > 0.25, rate
+    assert rate[("learned", 4)] > rate[("fixed", 4)] + 0.4, rate
     net.close()
