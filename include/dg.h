@@ -196,6 +196,43 @@ int dg_assemble_step(dg_ctx *ctx, dg_mesh *mesh, int prec, void *vals, void *rhs
 int dg_batch_upload(dg_ctx *ctx, const dg_mesh_desc *const *descs, int n, dg_mesh **out);
 int dg_batch_offsets(const dg_mesh *mesh, int *nmesh, int *elem_off, int64_t *val_off, int64_t *dof_off);
 
+/* Partitions (Sec. 4.2: the elements are split across GPUs, each GPU builds
+ * and assembles its own rows, faces on a cut are computed by both owners, and
+ * assembly needs no communication).
+ *
+ * dg_partition (host only) writes part[e] in 0..nparts-1 for every element
+ * of desc: elements are ordered along a space-filling curve through their
+ * vertex means (Hilbert in 2D, Morton in 3D) and cut into nparts contiguous
+ * runs of about equal cost, the cost of an element being its volume
+ * quadrature points times n^2.  Deterministic.  DG_ERR_ARG if nparts is
+ * outside 1..ne.
+ *
+ * dg_mesh_upload_part uploads the part my_part of desc (host arrays of the
+ * whole mesh; part as written by dg_partition or by any other partitioner):
+ * its owned elements (part[e] == my_part) plus the halo, the elements that
+ * share a face with an owned one.  Local elements and vertices keep the
+ * increasing order of their global ids.  Only owned elements have block
+ * rows (halo rows are empty; column indices are local ids) and load-vector
+ * entries (halo elements have none), and only they are assembled.  Each
+ * owned block row, mapped to global ids, is bitwise equal to the same row of
+ * the whole mesh assembled by dg_mesh_upload.  dg_mesh_update and
+ * dg_assemble_host then take arrays in the local numbering.
+ *
+ * dg_part_map returns the local -> global element map (elem_global[ne]),
+ * owned flags (owned[ne]), and the local -> global vertex map
+ * (vert_global[nv_local]); any output may be NULL.  DG_ERR_ARG for a mesh
+ * not made by dg_mesh_upload_part.
+ *
+ * dg_part_check is the host part of dg_mesh_upload_part (no GPU): the local
+ * layout (info, nowned, row_ptr[ne+1], col[nnzb], blk_off[nnzb+1],
+ * elem_global[ne], owned[ne]; sizes from info, any output may be NULL). */
+int dg_partition(const dg_mesh_desc *desc, int nparts, int *part);
+int dg_mesh_upload_part(dg_ctx *ctx, const dg_mesh_desc *desc, const int *part, int my_part, dg_mesh **out);
+int dg_part_map(const dg_mesh *mesh, int *nowned, int *nv_local, int *elem_global, int8_t *owned,
+                int *vert_global);
+int dg_part_check(const dg_mesh_desc *desc, const int *part, int my_part, dg_bsr_info *info, int *nowned,
+                  int *row_ptr, int *col, int64_t *blk_off, int *elem_global, int8_t *owned);
+
 /* CUDA graphs.  dg_graph_create records one whole pass (geometry kernels and
  * the row kernels, as dg_assemble_step) of mesh into vals / rhs (device,
  * fixed for the graph's life) as a CUDA graph.  With autotune != 0 it first

@@ -8,6 +8,7 @@
 // paper's atomics, every block has exactly one writer per launch, so the
 // result is bitwise reproducible.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -234,6 +235,9 @@ struct dg_mesh {
   double* a = nullptr;
   double flops[2][9] = {{0}}, words[2][9] = {{0}};
   std::vector<int> batch_elem_off;  // element offset of each batch member (empty: one mesh)
+  // partition meshes: local -> global element and vertex ids, owned flags
+  std::vector<int> part_elem, part_vert;
+  std::vector<int8_t> owned_h;  // empty: every element owned
   // host copies used to rebuild the work list when volume rules change
   std::vector<int> p_h, nvq_h, nqf_h;
   std::vector<double> vfma_h;  // algorithmic FMAs per volume point of each element
@@ -382,7 +386,10 @@ int dg_mesh_free(dg_mesh* mesh) {
   return DG_OK;
 }
 
-static int plan_mesh(const dg_mesh_desc* d, Plan& P) {
+// owned == nullptr: every element is assembled.  Otherwise only elements
+// with owned[e] != 0 get block rows, load-vector entries and work-list
+// entries; the others (the halo of a partition) only supply geometry.
+static int plan_mesh(const dg_mesh_desc* d, Plan& P, const int8_t* owned = nullptr) {
   if (!d) return fail(DG_ERR_ARG, "null mesh descriptor");
   const int dim = d->dim;
   if (dim != 2 && dim != 3) return fail(DG_ERR_ARG, "dim must be 2 or 3 (got %d)", dim);
@@ -562,9 +569,15 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P) {
   m->row_ptr.assign(ne + 1, 0);
   std::vector<int>& diag_blk = P.diag_blk;
   diag_blk.assign(ne, 0);
+  auto own = [&](int e) { return owned == nullptr || owned[e] != 0; };
   for (int e = 0; e < ne; ++e) {
-    nbr[e].push_back(e);
-    std::sort(nbr[e].begin(), nbr[e].end());
+    if (own(e)) {
+      nbr[e].push_back(e);
+      std::sort(nbr[e].begin(), nbr[e].end());
+    } else {
+      nbr[e].clear();  // halo element: no block row
+      diag_blk[e] = -1;
+    }
     m->row_ptr[e + 1] = m->row_ptr[e] + (int)nbr[e].size();
   }
   m->col.resize(m->row_ptr[ne]);
@@ -586,13 +599,13 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P) {
   slot10.assign(ni, 0);
   P.blk_if.assign(m->row_ptr[ne], -1);
   for (int i = 0; i < ni; ++i) {
-    slot01[i] = slot(if_e0[i], if_e1[i]);
-    slot10[i] = slot(if_e1[i], if_e0[i]);
-    P.blk_if[slot01[i]] = i;
-    P.blk_if[slot10[i]] = i;
+    slot01[i] = own(if_e0[i]) ? slot(if_e0[i], if_e1[i]) : -1;
+    slot10[i] = own(if_e1[i]) ? slot(if_e1[i], if_e0[i]) : -1;
+    if (slot01[i] >= 0) P.blk_if[slot01[i]] = i;
+    if (slot10[i] >= 0) P.blk_if[slot10[i]] = i;
   }
   m->dof_off.assign(ne + 1, 0);
-  for (int e = 0; e < ne; ++e) m->dof_off[e + 1] = m->dof_off[e] + nb[e];
+  for (int e = 0; e < ne; ++e) m->dof_off[e + 1] = m->dof_off[e] + (own(e) ? nb[e] : 0);
 
   // --- half faces (element -> faces, global face order) and face points
   std::vector<int>&f_e0 = P.f_e0, &f_e1 = P.f_e1, &f_v = P.f_v, &f_nq = P.f_nq;
@@ -659,14 +672,15 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P) {
     int qt = 1;
     for (int q = 0; q < dim; ++q) qt *= d->p[e] + 2;
     const int64_t nvq = (int64_t)(d->elem_ptr[e + 1] - d->elem_ptr[e]) * qt;
-    nqvol += nvq;
+    if (own(e)) nqvol += nvq;
     cost[e] = nvq + e_nqf[e];
   }
 
   // --- work lists: elements by degree (cost-descending), interfaces by max degree
   std::vector<int>& elem_perm = P.elem_perm;
-  elem_perm.assign(ne, 0);
-  std::iota(elem_perm.begin(), elem_perm.end(), 0);
+  elem_perm.clear();
+  for (int e = 0; e < ne; ++e)
+    if (own(e)) elem_perm.push_back(e);
   std::stable_sort(elem_perm.begin(), elem_perm.end(), [&](int x, int y) {
     if (d->p[x] != d->p[y]) return d->p[x] < d->p[y];
     return cost[x] > cost[y];
@@ -705,6 +719,7 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P) {
     const bool adv = advb || d->c != 0.0;
     const int SV = sub_vals(dim), FV = side_vals(dim);
     for (int e = 0; e < ne; ++e) {
+      if (!own(e)) continue;
       const int pe = d->p[e];
       const double n = nb[e];
       const double basis = n * dim * dim + 5.0 * dim * pe;
@@ -726,6 +741,7 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P) {
     for (int i = 0; i < ni; ++i) {
       for (int side = 0; side < 2; ++side) {
         const int e = side == 0 ? if_e0[i] : if_e1[i], k = side == 0 ? if_e1[i] : if_e0[i];
+        if (!own(e)) continue;
         const double ne_ = nb[e], nk = nb[k];
         double fma = 0.0, w = ne_ * nk;
         for (int f = if_fptr[i]; f < if_fptr[i + 1]; ++f) {
@@ -774,11 +790,13 @@ int dg_mesh_check(const dg_mesh_desc* d, dg_bsr_info* info, int* row_ptr, int* c
   return DG_OK;
 }
 
-int dg_mesh_upload(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
+}  // extern "C"
+
+static int upload_impl(dg_ctx* ctx, const dg_mesh_desc* d, const int8_t* owned, dg_mesh** out) {
   if (!ctx || !d || !out) return fail(DG_ERR_ARG, "dg_mesh_upload: null argument");
   *out = nullptr;
   Plan P;
-  int prc = plan_mesh(d, P);
+  int prc = plan_mesh(d, P, owned);
   if (prc != DG_OK) return prc;
   const int dim = d->dim, nv = d->nv, ne = d->ne;
   const int nidx = d->elem_ptr[ne] * (dim == 2 ? 1 : 4);
@@ -925,6 +943,7 @@ int dg_mesh_upload(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
   }
   m->perm_fan = elem_perm;
   m->perm_dev = const_cast<int*>(dm.elem_perm);
+  if (owned) m->owned_h.assign(owned, owned + ne);
   dm.lq_ok = nullptr;
   dm.lq64 = nullptr;
   dm.lq32 = nullptr;
@@ -940,6 +959,10 @@ int dg_mesh_upload(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
   *out = m;
   return DG_OK;
 }
+
+extern "C" {
+
+int dg_mesh_upload(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) { return upload_impl(ctx, d, nullptr, out); }
 
 int dg_bsr_layout(const dg_mesh* mesh, dg_bsr_info* out) {
   if (!mesh || !out) return fail(DG_ERR_ARG, "dg_bsr_layout: null argument");
@@ -1153,6 +1176,255 @@ int dg_batch_upload(dg_ctx* ctx, const dg_mesh_desc* const* descs, int n, dg_mes
   return DG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Partitions (Sec. 4.2: elements split across GPUs, cut faces computed by both
+// owners, no communication during assembly).
+// ---------------------------------------------------------------------------
+
+}  // extern "C"
+
+namespace {
+
+// Hilbert index of (x, y) on an n x n grid, n a power of two: the classic
+// quadrant rotate-and-reflect construction.
+uint64_t hilbert2(uint32_t x, uint32_t y, uint32_t n) {
+  uint64_t d = 0;
+  for (uint32_t s = n / 2; s > 0; s /= 2) {
+    const uint32_t rx = (x & s) ? 1u : 0u, ry = (y & s) ? 1u : 0u;
+    d += (uint64_t)s * s * ((3u * rx) ^ ry);
+    if (ry == 0) {
+      if (rx == 1) {
+        x = n - 1 - x;
+        y = n - 1 - y;
+      }
+      std::swap(x, y);
+    }
+  }
+  return d;
+}
+
+// Morton (Z-order) index of three 21-bit coordinates
+uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+  uint64_t d = 0;
+  for (int b = 20; b >= 0; --b)
+    d = (d << 3) | ((uint64_t)((x >> b) & 1u) << 2) | ((uint64_t)((y >> b) & 1u) << 1) | ((z >> b) & 1u);
+  return d;
+}
+
+int check_desc_arrays(const dg_mesh_desc* d, const char* who) {
+  if (!d) return fail(DG_ERR_ARG, "%s: null descriptor", who);
+  if (d->dim != 2 && d->dim != 3) return fail(DG_ERR_ARG, "%s: dim must be 2 or 3", who);
+  if (d->nv <= 0 || d->ne <= 0) return fail(DG_ERR_ARG, "%s: nv and ne must be positive", who);
+  if (!d->x || !d->y || (d->dim == 3 && !d->z) || !d->elem_ptr || !d->elem_idx || !d->p || !d->a)
+    return fail(DG_ERR_ARG, "%s: null array in descriptor", who);
+  if (d->elem_ptr[0] != 0) return fail(DG_ERR_MESH, "%s: elem_ptr[0] must be 0", who);
+  for (int e = 0; e < d->ne; ++e)
+    if (d->elem_ptr[e + 1] <= d->elem_ptr[e]) return fail(DG_ERR_MESH, "%s: element %d is empty", who, e);
+  const int64_t nidx = (int64_t)d->elem_ptr[d->ne] * (d->dim == 2 ? 1 : 4);
+  for (int64_t i = 0; i < nidx; ++i)
+    if (d->elem_idx[i] < 0 || d->elem_idx[i] >= d->nv) return fail(DG_ERR_MESH, "%s: vertex index out of range", who);
+  return DG_OK;
+}
+
+// The local mesh of one part: its owned elements plus every element sharing
+// a face with one of them (the halo), in increasing global element order;
+// vertices renumbered in increasing global order.  Both orders are kept so
+// that faces, interfaces and neighbour slots come out in the same relative
+// order as in the whole mesh, which makes each owned block row bitwise equal
+// to the whole mesh's.
+struct PartMesh {
+  dg_mesh_desc d{};
+  std::vector<double> X[3];
+  std::vector<int> eptr, eidx, elem_global, vert_global;
+  std::vector<int8_t> p, owned;
+  std::vector<double> a;
+  int nowned = 0;
+};
+
+void half_face_keys(const dg_mesh_desc* d, int e, std::vector<std::array<int, 3>>& out) {
+  const int b = d->elem_ptr[e], k = d->elem_ptr[e + 1] - b;
+  if (d->dim == 2) {
+    for (int i = 0; i < k; ++i) {
+      const int v0 = d->elem_idx[b + i], v1 = d->elem_idx[b + (i + 1) % k];
+      out.push_back({std::min(v0, v1), std::max(v0, v1), -1});
+    }
+  } else {
+    for (int t = b; t < b + k; ++t) {
+      const int* tv = d->elem_idx + 4 * t;
+      for (int o = 0; o < 4; ++o) {
+        std::array<int, 3> kk{};
+        int c = 0;
+        for (int i = 0; i < 4; ++i)
+          if (i != o) kk[c++] = tv[i];
+        std::sort(kk.begin(), kk.end());
+        out.push_back(kk);
+      }
+    }
+  }
+}
+
+int build_part(const dg_mesh_desc* d, const int* part, int my_part, PartMesh& L, const char* who) {
+  int rc = check_desc_arrays(d, who);
+  if (rc != DG_OK) return rc;
+  if (!part) return fail(DG_ERR_ARG, "%s: null part array", who);
+  const int ne = d->ne, dim = d->dim;
+  std::vector<std::array<int, 3>> own_keys, keys;
+  std::vector<int8_t> sel(ne, 0);  // 0 outside, 1 halo, 2 owned
+  for (int e = 0; e < ne; ++e) {
+    if (part[e] < 0) return fail(DG_ERR_ARG, "%s: part[%d] = %d is negative", who, e, part[e]);
+    if (part[e] == my_part) {
+      sel[e] = 2;
+      half_face_keys(d, e, own_keys);
+    }
+  }
+  if (own_keys.empty()) return fail(DG_ERR_ARG, "%s: part %d owns no element", who, my_part);
+  std::sort(own_keys.begin(), own_keys.end());
+  own_keys.erase(std::unique(own_keys.begin(), own_keys.end()), own_keys.end());
+  for (int e = 0; e < ne; ++e) {
+    if (sel[e]) continue;
+    keys.clear();
+    half_face_keys(d, e, keys);
+    for (const auto& k : keys)
+      if (std::binary_search(own_keys.begin(), own_keys.end(), k)) {
+        sel[e] = 1;
+        break;
+      }
+  }
+  std::vector<int> vmap(d->nv, -1);
+  for (int e = 0; e < ne; ++e) {
+    if (!sel[e]) continue;
+    const int64_t b = (int64_t)d->elem_ptr[e] * (dim == 2 ? 1 : 4), en = (int64_t)d->elem_ptr[e + 1] * (dim == 2 ? 1 : 4);
+    for (int64_t i = b; i < en; ++i) vmap[d->elem_idx[i]] = 0;
+  }
+  const double* Xg[3] = {d->x, d->y, d->z};
+  for (int v = 0; v < d->nv; ++v)
+    if (vmap[v] == 0) {
+      vmap[v] = (int)L.vert_global.size();
+      L.vert_global.push_back(v);
+      for (int q = 0; q < dim; ++q) L.X[q].push_back(Xg[q][v]);
+    }
+  L.eptr.assign(1, 0);
+  for (int e = 0; e < ne; ++e) {
+    if (!sel[e]) continue;
+    const int64_t b = (int64_t)d->elem_ptr[e] * (dim == 2 ? 1 : 4), en = (int64_t)d->elem_ptr[e + 1] * (dim == 2 ? 1 : 4);
+    for (int64_t i = b; i < en; ++i) L.eidx.push_back(vmap[d->elem_idx[i]]);
+    L.eptr.push_back(L.eptr.back() + d->elem_ptr[e + 1] - d->elem_ptr[e]);
+    L.elem_global.push_back(e);
+    L.owned.push_back(sel[e] == 2 ? 1 : 0);
+    L.nowned += sel[e] == 2;
+    L.p.push_back(d->p[e]);
+    L.a.push_back(d->a[e]);
+  }
+  L.d = *d;
+  L.d.nv = (int)L.vert_global.size();
+  L.d.x = L.X[0].data();
+  L.d.y = L.X[1].data();
+  L.d.z = dim == 3 ? L.X[2].data() : nullptr;
+  L.d.ne = (int)L.elem_global.size();
+  L.d.elem_ptr = L.eptr.data();
+  L.d.elem_idx = L.eidx.data();
+  L.d.p = L.p.data();
+  L.d.a = L.a.data();
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dg_partition(const dg_mesh_desc* d, int nparts, int* part) {
+  int rc = check_desc_arrays(d, "dg_partition");
+  if (rc != DG_OK) return rc;
+  if (!part) return fail(DG_ERR_ARG, "dg_partition: null output");
+  const int ne = d->ne, dim = d->dim;
+  if (nparts < 1 || nparts > ne) return fail(DG_ERR_ARG, "dg_partition: nparts = %d outside 1..%d", nparts, ne);
+  for (int e = 0; e < ne; ++e)
+    if (d->p[e] < 1 || d->p[e] > (dim == 2 ? kPMax2 : kPMax3))
+      return fail(DG_ERR_MESH, "dg_partition: element %d has degree %d", e, d->p[e]);
+  const double* X[3] = {d->x, d->y, d->z};
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  for (int q = 0; q < dim; ++q) {
+    lo[q] = *std::min_element(X[q], X[q] + d->nv);
+    hi[q] = *std::max_element(X[q], X[q] + d->nv);
+  }
+  const uint32_t grid = dim == 2 ? (1u << 16) : (1u << 21);
+  std::vector<uint64_t> key(ne);
+  std::vector<double> w(ne);
+  for (int e = 0; e < ne; ++e) {
+    const int64_t b = (int64_t)d->elem_ptr[e] * (dim == 2 ? 1 : 4), en = (int64_t)d->elem_ptr[e + 1] * (dim == 2 ? 1 : 4);
+    uint32_t c[3] = {0, 0, 0};
+    for (int q = 0; q < dim; ++q) {
+      double s = 0;
+      for (int64_t i = b; i < en; ++i) s += X[q][d->elem_idx[i]];
+      s /= (double)(en - b);
+      const double t = hi[q] > lo[q] ? (s - lo[q]) / (hi[q] - lo[q]) : 0.0;
+      c[q] = (uint32_t)std::min<double>(grid - 1, std::max(0.0, std::floor(t * grid)));
+    }
+    key[e] = dim == 2 ? hilbert2(c[0], c[1], grid) : morton3(c[0], c[1], c[2]);
+    // cost ~ volume points x n^2 (the volume contraction)
+    int qt = 1;
+    for (int q = 0; q < dim; ++q) qt *= d->p[e] + 2;
+    const double n = nbasis(dim, d->p[e]);
+    w[e] = (double)(d->elem_ptr[e + 1] - d->elem_ptr[e]) * qt * n * n;
+  }
+  std::vector<int> order(ne);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return key[x] < key[y]; });
+  double total = 0;
+  for (int e : order) total += w[e];
+  double before = 0;
+  for (int e : order) {
+    const int k = (int)std::floor((before + 0.5 * w[e]) * nparts / total);
+    part[e] = std::min(nparts - 1, std::max(0, k));
+    before += w[e];
+  }
+  return DG_OK;
+}
+
+int dg_part_check(const dg_mesh_desc* d, const int* part, int my_part, dg_bsr_info* info, int* nowned, int* row_ptr,
+                  int* col, int64_t* blk_off, int* elem_global, int8_t* owned) {
+  PartMesh L;
+  int rc = build_part(d, part, my_part, L, "dg_part_check");
+  if (rc != DG_OK) return rc;
+  Plan P;
+  rc = plan_mesh(&L.d, P, L.owned.data());
+  if (rc != DG_OK) return rc;
+  dg_bsr_info I{};
+  fill_info(&L.d, P, I);
+  if (info) *info = I;
+  if (nowned) *nowned = L.nowned;
+  if (row_ptr) std::copy(P.row_ptr.begin(), P.row_ptr.end(), row_ptr);
+  if (col) std::copy(P.col.begin(), P.col.end(), col);
+  if (blk_off) std::copy(P.blk_off.begin(), P.blk_off.end(), blk_off);
+  if (elem_global) std::copy(L.elem_global.begin(), L.elem_global.end(), elem_global);
+  if (owned) std::copy(L.owned.begin(), L.owned.end(), owned);
+  return DG_OK;
+}
+
+int dg_mesh_upload_part(dg_ctx* ctx, const dg_mesh_desc* d, const int* part, int my_part, dg_mesh** out) {
+  if (!ctx || !out) return fail(DG_ERR_ARG, "dg_mesh_upload_part: null argument");
+  *out = nullptr;
+  PartMesh L;
+  int rc = build_part(d, part, my_part, L, "dg_mesh_upload_part");
+  if (rc != DG_OK) return rc;
+  rc = upload_impl(ctx, &L.d, L.owned.data(), out);
+  if (rc != DG_OK) return rc;
+  (*out)->part_elem = L.elem_global;
+  (*out)->part_vert = L.vert_global;
+  return DG_OK;
+}
+
+int dg_part_map(const dg_mesh* mesh, int* nowned, int* nvlocal, int* elem_global, int8_t* owned, int* vert_global) {
+  if (!mesh) return fail(DG_ERR_ARG, "dg_part_map: null mesh");
+  if (mesh->part_elem.empty()) return fail(DG_ERR_ARG, "dg_part_map: not a partition mesh");
+  if (nowned) *nowned = (int)std::count(mesh->owned_h.begin(), mesh->owned_h.end(), (int8_t)1);
+  if (nvlocal) *nvlocal = (int)mesh->part_vert.size();
+  if (elem_global) std::copy(mesh->part_elem.begin(), mesh->part_elem.end(), elem_global);
+  if (owned) std::copy(mesh->owned_h.begin(), mesh->owned_h.end(), owned);
+  if (vert_global) std::copy(mesh->part_vert.begin(), mesh->part_vert.end(), vert_global);
+  return DG_OK;
+}
+
 int dg_batch_offsets(const dg_mesh* mesh, int* nmesh, int* elem_off, int64_t* val_off, int64_t* dof_off) {
   if (!mesh) return fail(DG_ERR_ARG, "dg_batch_offsets: null mesh");
   const std::vector<int>& eo = mesh->batch_elem_off;
@@ -1320,13 +1592,15 @@ static int rebuild_worklist(dg_ctx* ctx, dg_mesh* mesh, const std::vector<int>& 
   const int ne = mesh->dm.ne;
   std::vector<int64_t> cost(ne);
   for (int e = 0; e < ne; ++e) cost[e] = (learned.empty() || !learned[e] ? mesh->nvq_h[e] : 28) + mesh->nqf_h[e];
-  std::vector<int> perm(ne);
-  std::iota(perm.begin(), perm.end(), 0);
+  std::vector<int> perm;
+  for (int e = 0; e < ne; ++e)
+    if (mesh->owned_h.empty() || mesh->owned_h[e]) perm.push_back(e);
   std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) {
     if (mesh->p_h[x] != mesh->p_h[y]) return mesh->p_h[x] < mesh->p_h[y];
     return cost[x] > cost[y];
   });
-  DG_CUDA_TRY(cudaMemcpyAsync(mesh->perm_dev, perm.data(), sizeof(int) * ne, cudaMemcpyHostToDevice, ctx->stream));
+  DG_CUDA_TRY(cudaMemcpyAsync(mesh->perm_dev, perm.data(), sizeof(int) * perm.size(), cudaMemcpyHostToDevice,
+                              ctx->stream));
   DG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   return DG_OK;
 }
@@ -1369,7 +1643,8 @@ int dg_quad_fit(dg_ctx* ctx, dg_mesh* mesh, const float* init, int iters, int in
       mesh->dm.lq32 = mesh->lq32;
       // algorithmic volume work of learned elements: 28 points instead of the sub-triangle rule
       for (int e = 0; e < ne; ++e)
-        if (ok[e]) mesh->flops[0][mesh->p_h[e]] -= 2.0 * (mesh->nvq_h[e] - 28) * mesh->vfma_h[e];
+        if (ok[e] && (mesh->owned_h.empty() || mesh->owned_h[e]))
+          mesh->flops[0][mesh->p_h[e]] -= 2.0 * (mesh->nvq_h[e] - 28) * mesh->vfma_h[e];
     }
   }
   return DG_OK;
@@ -1389,7 +1664,8 @@ int dg_quad_clear(dg_ctx* ctx, dg_mesh* mesh) {
     std::vector<int> okd(mesh->dm.ne);
     DG_CUDA_TRY(cudaMemcpy(okd.data(), mesh->lq_okm, sizeof(int) * mesh->dm.ne, cudaMemcpyDeviceToHost));
     for (int e = 0; e < mesh->dm.ne; ++e)
-      if (okd[e]) mesh->flops[0][mesh->p_h[e]] += 2.0 * (mesh->nvq_h[e] - 28) * mesh->vfma_h[e];
+      if (okd[e] && (mesh->owned_h.empty() || mesh->owned_h[e]))
+        mesh->flops[0][mesh->p_h[e]] += 2.0 * (mesh->nvq_h[e] - 28) * mesh->vfma_h[e];
     int rc = rebuild_worklist(ctx, mesh, ok);
     if (rc != DG_OK) return rc;
   }

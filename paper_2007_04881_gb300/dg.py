@@ -135,6 +135,10 @@ def load() -> C.CDLL:
     lib.dg_mlp_forward.argtypes = [V, V, V, C.c_int, V]
     lib.dg_mlp_grad.argtypes = [V, V, V, V, C.c_int, V, V]
     lib.dg_mlp_train_step.argtypes = [V, V, V, V, C.c_int, C.c_float, V]
+    lib.dg_partition.argtypes = [C.POINTER(dg_mesh_desc), C.c_int, V]
+    lib.dg_mesh_upload_part.argtypes = [V, C.POINTER(dg_mesh_desc), V, C.c_int, C.POINTER(V)]
+    lib.dg_part_map.argtypes = [V, V, V, V, V, V]
+    lib.dg_part_check.argtypes = [C.POINTER(dg_mesh_desc), V, C.c_int, C.POINTER(dg_bsr_info), V, V, V, V, V, V]
     lib.dg_sync.argtypes = [V]
     lib.dg_last_launch_count.argtypes = [V]
     _lib = lib
@@ -152,6 +156,7 @@ EXPORTS = (
     "dg_quad_prepare", "dg_quad_fit", "dg_quad_targets", "dg_quad_buffers", "dg_quad_clear",
     "dg_mlp_create", "dg_mlp_free", "dg_mlp_num_params", "dg_mlp_get_params", "dg_mlp_set_params",
     "dg_mlp_get_state", "dg_mlp_set_state", "dg_mlp_forward", "dg_mlp_grad", "dg_mlp_train_step",
+    "dg_partition", "dg_mesh_upload_part", "dg_part_map", "dg_part_check",
 )
 
 
@@ -276,15 +281,63 @@ def dg_mesh_check(mesh, p, a, problem: Problem, pattern: bool = False):
     return info, row_ptr, col, blk_off
 
 
-class Mesh:
-    """dg_mesh_upload of a generator mesh (meshgen.Mesh2D / Mesh3D), or, with
-    a list of (mesh, p, a) members, dg_batch_upload of their disjoint union."""
+def dg_partition(mesh, p, a, problem: Problem, nparts: int) -> np.ndarray:
+    """Space-filling-curve partition of the elements into nparts runs of equal cost (host only)."""
+    d, keep = make_desc(mesh, p, a, problem)
+    part = np.zeros(d.ne, np.int32)
+    _check(load().dg_partition(C.byref(d), int(nparts), _vp(part)))
+    return part
 
-    def __init__(self, ctx: Context, mesh, p=None, a=None, problem: Problem = None, members=None):
+
+def dg_part_check(mesh, p, a, problem: Problem, part, my_part: int):
+    """Host part of a partition upload: local layout and local -> global element map."""
+    lib = load()
+    d, keep = make_desc(mesh, p, a, problem)
+    part = np.ascontiguousarray(part, dtype=np.int32)
+    info = dg_bsr_info()
+    nowned = C.c_int()
+    _check(lib.dg_part_check(C.byref(d), _vp(part), int(my_part), C.byref(info), C.byref(nowned),
+                             None, None, None, None, None))
+    row_ptr = np.zeros(info.ne + 1, np.int32)
+    col = np.zeros(info.nnzb, np.int32)
+    blk_off = np.zeros(info.nnzb + 1, np.int64)
+    elem_global = np.zeros(info.ne, np.int32)
+    owned = np.zeros(info.ne, np.int8)
+    _check(lib.dg_part_check(C.byref(d), _vp(part), int(my_part), C.byref(info), C.byref(nowned),
+                             _vp(row_ptr), _vp(col), _vp(blk_off), _vp(elem_global), _vp(owned)))
+    return dict(info=info, nowned=nowned.value, row_ptr=row_ptr, col=col, blk_off=blk_off,
+                elem_global=elem_global, owned=owned)
+
+
+class Mesh:
+    """dg_mesh_upload of a generator mesh (meshgen.Mesh2D / Mesh3D); with
+    ``part`` and ``my_part``, dg_mesh_upload_part of one part of it; with a
+    list of (mesh, p, a) members, dg_batch_upload of their disjoint union."""
+
+    def __init__(self, ctx: Context, mesh, p=None, a=None, problem: Problem = None, members=None,
+                 part=None, my_part=None):
         lib = load()
         self.ctx = ctx
         h = C.c_void_p()
-        if members is None:
+        if part is not None:
+            self.dim = mesh.dim
+            d, keep = make_desc(mesh, p, a, problem)
+            prt = np.ascontiguousarray(part, dtype=np.int32)
+            _check(lib.dg_mesh_upload_part(ctx._h, C.byref(d), _vp(prt), int(my_part), C.byref(h)))
+            self._h = h
+            ne_loc = C.c_int()
+            info = dg_bsr_info()
+            _check(lib.dg_bsr_layout(h, C.byref(info)))
+            self.elem_global = np.zeros(info.ne, np.int32)
+            self.owned = np.zeros(info.ne, np.int8)
+            nv_loc = C.c_int()
+            _check(lib.dg_part_map(h, C.byref(ne_loc), C.byref(nv_loc), _vp(self.elem_global), _vp(self.owned),
+                                   None))
+            self.nowned = ne_loc.value
+            self.vert_global = np.zeros(nv_loc.value, np.int32)
+            _check(lib.dg_part_map(h, None, None, None, None, _vp(self.vert_global)))
+            self.p = np.asarray(keep[-2])[self.elem_global]
+        elif members is None:
             self.dim = mesh.dim
             d, keep = make_desc(mesh, p, a, problem)
             pp = keep[-2]
