@@ -33,6 +33,9 @@ sys.path.insert(0, ROOT)
 
 L2_FLUSH_BYTES = 256 << 20  # > 129 MB L2
 METRIC = "dG assembly elements/s & matrix GB/s vs roofline; reduced vs FP64 form at fixed err"
+# reduced forms of the timed pass: binding constant and arithmetic type
+PRECS = {"fp32": "DG_PREC_FP32", "bf16x3": "DG_PREC_BF16X3", "tf32x3": "DG_PREC_TF32X3"}
+DTYPES = {"fp32": "f32", "bf16x3": "bf16x3 (f32 accumulate)", "tf32x3": "tf32x3 (f32 accumulate)"}
 WORKLOADS = {
     "adr2d_65k": ("adr2d_65k: 2D advection-diffusion-reaction, 65,536 clipped Voronoi cells (5 Lloyd steps), "
                   "p~U{1..4}, a=10^U(-2,2), b=(1,0.5), c=1, sin-product source, penalty 10 p^2/h"),
@@ -355,7 +358,7 @@ def run_ours(args):
         pattern_ms = 1e3 * (time.perf_counter() - t0)
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    prec = dg.DG_PREC_FP32
+    prec = getattr(dg, PRECS[args.prec])
     v32 = torch.empty(mesh.nvals, dtype=torch.float32, device="cuda")
     r32 = torch.empty(mesh.ndofs, dtype=torch.float32, device="cuda")
 
@@ -418,7 +421,39 @@ def run_ours(args):
     err_fro = float(torch.linalg.vector_norm(d) / torch.linalg.vector_norm(v64))
     err_max = float(d.abs().max() / v64.abs().max())
     err_rhs = float(torch.linalg.vector_norm(r32.double() - r64) / torch.linalg.vector_norm(r64))
-    del v64, r64, g64, d
+    del d
+
+    # ---- the other reduced forms (FP32 ALU and tensor-core contractions), same inputs
+    forms = {}
+    kf = max(3, min(args.steps // 4, 50 if info.ne < 200000 and mesh.dim == 2 else 5))
+    for fname, fconst in PRECS.items():
+        fprec = getattr(dg, fconst)
+        if fprec == prec:
+            continue
+        vf = torch.empty(mesh.nvals, dtype=torch.float32, device="cuda")
+        rf = torch.empty(mesh.ndofs, dtype=torch.float32, device="cuda")
+        ctx.dg_set_timing(False)
+        gf = mesh.dg_graph_create(fprec, vf, rf, autotune=True)
+        for _ in range(2):
+            gf.dg_graph_launch()
+        torch.cuda.synchronize()
+        tf, _ = time_steps(torch, stream, gf.dg_graph_launch, flush, kf, None)
+        ctx.dg_set_timing(True)
+        _, ksf = time_steps(torch, stream, lambda: mesh.dg_assemble_step(fprec, vf, rf), flush, 3, ctx)
+        ctx.dg_set_timing(False)
+        df = vf.double() - v64
+        msf = max_over_ranks(sum(tf) / len(tf), ws)
+        rp = ksf.get("row_pass")
+        forms[fname] = {
+            "ms_per_step": msf, "value": ws * info.ne / (msf * 1e-3), "steps": kf,
+            "row_pass_ms_direct_launch": rp[0] / rp[1] if rp else None,
+            "row_pass_tflops_direct_launch": rp[2] / (rp[0] / rp[1] * 1e-3) / 1e12 if rp else None,
+            "matrix_rel_fro": float(torch.linalg.vector_norm(df) / torch.linalg.vector_norm(v64)),
+            "matrix_rel_max": float(df.abs().max() / v64.abs().max()),
+            "rhs_rel_fro": float(torch.linalg.vector_norm(rf.double() - r64) / torch.linalg.vector_norm(r64)),
+        }
+        del vf, rf, gf, df
+    del v64, r64, g64
     torch.cuda.empty_cache()
 
     # ---- end to end through the host-memory entry point
@@ -483,7 +518,7 @@ def run_ours(args):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32",
+        "dtype": DTYPES[args.prec],
         "data": "synthetic",
         "config": workload_config(wl, info, args.workload),
         "matrix_gbs": (info.nvals + info.ndofs) * 4 / (ms_step * 1e-3) / 1e9,
@@ -513,7 +548,9 @@ def run_ours(args):
             "roofline": {"bound": "alu", "kernel": n64, "achieved": ach64, "peak": FP64_PEAK_TFLOPS,
                          "unit": "TFLOP/s", "frac": ach64 / FP64_PEAK_TFLOPS},
         },
+        "form": args.prec,
         "reduced_vs_fp64_error": {"matrix_rel_fro": err_fro, "matrix_rel_max": err_max, "rhs_rel_fro": err_rhs},
+        "other_forms": forms,
         "upload_ms": upload_ms,
         "pattern_ms": pattern_ms,
         "e2e": {"value": ws * info.ne / e2e_s, "unit": "elements/s", "h2d_bytes_per_step": h2d,
@@ -700,6 +737,8 @@ def main():
     ap.add_argument("--workload", default="adr2d_65k", choices=sorted(WORKLOADS))
     ap.add_argument("--ref-sample", type=int, default=512, help="oracle elements per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--prec", default="fp32", choices=sorted(PRECS),
+                    help="form of the timed pass: FP32 contractions, or split-BF16 / 3xTF32 tensor-core contractions")
     ap.add_argument("--epochs", type=int, default=40, help="training epochs of the learned-rule workload")
     args = ap.parse_args()
     if args.warmup < 3:

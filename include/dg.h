@@ -58,6 +58,13 @@ extern "C" {
 #define DG_PREC_FP64 0 /* everything in FP64; vals are double */
 #define DG_PREC_FP32 1 /* geometry (maps, Jacobians, normals, penalty) in FP64,
                           basis evaluation and contractions in FP32; vals are float */
+/* Tensor-core forms: geometry, points, weights and basis values as
+ * DG_PREC_FP32; the local contractions U^T V (and the load vector, as one
+ * more column of V) run on the tensor cores with FP32 accumulation, every
+ * operand split as x = hi + lo and each product taken as hi*hi + hi*lo +
+ * lo*hi.  Degree-1 elements use the FP32 form.  vals and rhs are float. */
+#define DG_PREC_BF16X3 2 /* hi, lo in bfloat16 */
+#define DG_PREC_TF32X3 3 /* hi, lo in TF32 */
 
 /* source / boundary data */
 #define DG_SRC_ZERO 0    /* f = 0, g_D = 0 */
@@ -155,7 +162,7 @@ int dg_bsr_pattern(const dg_mesh *mesh, int *row_ptr, int *col, int64_t *blk_off
 
 /* Volume integrals (first line of Eq. (2.4)) of every element: OVERWRITES
  * each element's diagonal block in vals (device, nvals entries of double for
- * DG_PREC_FP64, float for DG_PREC_FP32).  Off-diagonal blocks are untouched. */
+ * DG_PREC_FP64, float for the other forms).  Off-diagonal blocks are untouched. */
 int dg_assemble_volume(dg_ctx *ctx, const dg_mesh *mesh, int prec, void *vals);
 
 /* Face integrals (second and third lines of Eq. (2.4)): ADDS each element's

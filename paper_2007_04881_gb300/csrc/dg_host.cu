@@ -1003,7 +1003,7 @@ static int run_assembly(dg_ctx* ctx, const dg_mesh* mesh, int prec, int mode, vo
                         bool reset = true, cudaStream_t st = nullptr, bool use_ctx_stream = true, int occ_cap = 0,
                         bool concurrent = false) {
   if (!ctx || !mesh) return fail(DG_ERR_ARG, "null context or mesh");
-  if (prec != DG_PREC_FP64 && prec != DG_PREC_FP32) return fail(DG_ERR_ARG, "unknown precision %d", prec);
+  if (prec < DG_PREC_FP64 || prec > DG_PREC_TF32X3) return fail(DG_ERR_ARG, "unknown precision %d", prec);
   if ((mode & (kModeVol | kModeFace)) && !vals) return fail(DG_ERR_ARG, "vals is null");
   if ((mode & kModeRhs) && !rhs) return fail(DG_ERR_ARG, "rhs is null");
   if (use_ctx_stream) st = ctx->stream;
@@ -1032,10 +1032,19 @@ static int run_assembly(dg_ctx* ctx, const dg_mesh* mesh, int prec, int mode, vo
     double* v = static_cast<double*>(vals);
     double* r = static_cast<double*>(rhs);
     n += m.dim == 2 ? launch_row2d_f64(m, mode, v, r, ctx->sm_count, lo, tr) : launch_row3d_f64(m, mode, v, r, ctx->sm_count, lo, tr);
-  } else {
+  } else if (prec == DG_PREC_FP32) {
     float* v = static_cast<float*>(vals);
     float* r = static_cast<float*>(rhs);
     n += m.dim == 2 ? launch_row2d_f32(m, mode, v, r, ctx->sm_count, lo, tr) : launch_row3d_f32(m, mode, v, r, ctx->sm_count, lo, tr);
+  } else {
+    float* v = static_cast<float*>(vals);
+    float* r = static_cast<float*>(rhs);
+    if (prec == DG_PREC_BF16X3)
+      n += m.dim == 2 ? launch_row2d_bf16(m, mode, v, r, ctx->sm_count, lo, tr)
+                      : launch_row3d_bf16(m, mode, v, r, ctx->sm_count, lo, tr);
+    else
+      n += m.dim == 2 ? launch_row2d_tf32(m, mode, v, r, ctx->sm_count, lo, tr)
+                      : launch_row3d_tf32(m, mode, v, r, ctx->sm_count, lo, tr);
   }
   if (concurrent) {
     for (int i = 0; i < 4; ++i) {
@@ -1074,7 +1083,7 @@ int dg_assemble(dg_ctx* ctx, const dg_mesh* mesh, int prec, void* vals, void* rh
 int dg_assemble_host(dg_ctx* ctx, dg_mesh* mesh, int prec, const double* x, const double* y, const double* z,
                      const double* a, void* vals_host, void* rhs_host) {
   if (!ctx || !mesh || !vals_host) return fail(DG_ERR_ARG, "dg_assemble_host: null argument");
-  if (prec != DG_PREC_FP64 && prec != DG_PREC_FP32) return fail(DG_ERR_ARG, "unknown precision %d", prec);
+  if (prec < DG_PREC_FP64 || prec > DG_PREC_TF32X3) return fail(DG_ERR_ARG, "unknown precision %d", prec);
   const size_t es = prec == DG_PREC_FP64 ? 8 : 4;
   if (mesh->h_prec != prec) {
     if (mesh->h_vals) cudaFree(mesh->h_vals);
@@ -1102,7 +1111,7 @@ int dg_assemble_host(dg_ctx* ctx, dg_mesh* mesh, int prec, const double* x, cons
 
 int dg_assemble_step(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs) {
   if (!ctx || !mesh) return fail(DG_ERR_ARG, "dg_assemble_step: null argument");
-  if (prec != DG_PREC_FP64 && prec != DG_PREC_FP32) return fail(DG_ERR_ARG, "unknown precision %d", prec);
+  if (prec < DG_PREC_FP64 || prec > DG_PREC_TF32X3) return fail(DG_ERR_ARG, "unknown precision %d", prec);
   // geometry records only in the precision this pass consumes
   trace_reset(ctx, mesh);
   ctx->last_launches = launch_geometry(mesh->dm, ctx->stream, &ctx->tracer, prec == DG_PREC_FP64 ? 1 : 2);
@@ -1453,7 +1462,7 @@ static int issue_pass(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rh
 
 int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs, int autotune, dg_graph** out) {
   if (!ctx || !mesh || !vals || !out) return fail(DG_ERR_ARG, "dg_graph_create: null argument");
-  if (prec != DG_PREC_FP64 && prec != DG_PREC_FP32) return fail(DG_ERR_ARG, "unknown precision %d", prec);
+  if (prec < DG_PREC_FP64 || prec > DG_PREC_TF32X3) return fail(DG_ERR_ARG, "unknown precision %d", prec);
   *out = nullptr;
   dg_graph* g = new (std::nothrow) dg_graph();
   if (!g) return fail(DG_ERR_OOM, "out of host memory");

@@ -173,6 +173,11 @@ int launch_row2d_f64(const DevMesh& m, int mode, double* vals, double* rhs, int 
 int launch_row2d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);
 int launch_row3d_f64(const DevMesh& m, int mode, double* vals, double* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);
 int launch_row3d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);
+// tensor-core forms (split-BF16 and 3xTF32 contractions)
+int launch_row2d_bf16(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);
+int launch_row2d_tf32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);
+int launch_row3d_bf16(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);
+int launch_row3d_tf32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);
 
 // learned quadrature (dg_learned.cu)
 void lq_prepare(const DevMesh& m, double* mom, double* mmom, void* feat, int* elig, cudaStream_t st);

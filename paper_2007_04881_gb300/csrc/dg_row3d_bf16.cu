@@ -1,0 +1,16 @@
+// dg_row3d_bf16.cu -- 3D row kernels with split-BF16 tensor-core contractions, degrees 1..4.
+#include "dg_launch.cuh"
+#include "dg_mma.cuh"
+
+namespace dg {
+
+int launch_row3d_bf16(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr) {
+  int n = 0;
+  n += launch_row_mma_p<3, 1, kMmaBf16>(m, mode, vals, rhs, sm_count, lo, tr);
+  n += launch_row_mma_p<3, 2, kMmaBf16>(m, mode, vals, rhs, sm_count, lo, tr);
+  n += launch_row_mma_p<3, 3, kMmaBf16>(m, mode, vals, rhs, sm_count, lo, tr);
+  n += launch_row_mma_p<3, 4, kMmaBf16>(m, mode, vals, rhs, sm_count, lo, tr);
+  return n;
+}
+
+}  // namespace dg

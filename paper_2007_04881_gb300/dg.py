@@ -28,6 +28,8 @@ DG_ERR = {
 }
 DG_PREC_FP64 = 0
 DG_PREC_FP32 = 1
+DG_PREC_BF16X3 = 2
+DG_PREC_TF32X3 = 3
 DG_SRC_ZERO, DG_SRC_SINPROD, DG_SRC_POLY = 0, 1, 2
 DG_PMAX_2D, DG_PMAX_3D = 6, 4
 
