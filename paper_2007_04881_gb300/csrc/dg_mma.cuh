@@ -17,9 +17,12 @@
 // test rows, NW columns; column N carries the load-vector weights R, so
 // the load vector comes out of the same product as column N of U^T V).
 // split-BF16 stores hi and lo planes and feeds the MMAs with ldmatrix.trans;
-// 3xTF32 stores FP32 and splits while building the fragments.  Row strides
-// are an odd number of 16-byte units (conflict-free ldmatrix) and 8 or 24
-// mod 32 words (conflict-free FP32 fragment loads).
+// 3xTF32 stores FP32 and splits while building the fragments.  BF16 rows
+// of 2 or 4 16-byte units are XOR-swizzled (unit u of row r stored at
+// u ^ f(r)), which keeps the 8 rows of every ldmatrix phase and of every
+// staging-store phase on distinct banks without padding; other widths are
+// padded to an odd number of units.  FP32 rows are padded to 8 or 24 mod 32
+// words (conflict-free fragment loads).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -42,12 +45,17 @@ struct MmaCfg {
   static constexpr int NTV = D + 1;                    // rows (terms) of a volume point
   static constexpr int C = 16;                         // points per element per chunk
   static constexpr int RW = C * NTV;                   // staged rows per element
-  static constexpr int SU = 16 * MT + 8, SV = NW + 8;  // row strides, elements
+  static constexpr int WU = 2 * MT, WV = NW / 8;      // 16-byte units of a BF16 row
+  static constexpr int ZU = K == kMmaBf16 && (WU == 2 || WU == 4) ? WU : 0;  // swizzle width (0: padded)
+  static constexpr int ZV = K == kMmaBf16 && (WV == 2 || WV == 4) ? WV : 0;
+  static constexpr int SU = ZU ? 16 * MT : 16 * MT + 8;  // row strides, elements
+  static constexpr int SV = ZV ? NW : NW + 8;
   static constexpr int ESZ = K == kMmaBf16 ? 2 : 4;
   static constexpr int NPL = K == kMmaBf16 ? 2 : 1;    // planes (hi, lo) or one FP32 plane
   static constexpr size_t per_elem = (size_t)RW * (SU + SV) * ESZ * NPL;
   static constexpr int G = per_elem <= 10 * 1024 ? 2 : 1;  // elements per warp
   static constexpr int KS = K == kMmaBf16 ? 16 : 8;         // rows per MMA k-step
+  static constexpr int MINB = G == 2 ? 4 : 2;               // CTAs per SM the registers must allow
   static constexpr int PT = 4 * D + 5, PI = 17;
   static constexpr int QT = ipow_c(P + 2, D);
   static constexpr int NMAXC = nbasis(D, D == 2 ? kPMax2 : kPMax3);
@@ -65,6 +73,14 @@ struct MmaCfg {
 // ---------------------------------------------------------------------------
 // fragments
 // ---------------------------------------------------------------------------
+
+// XOR swizzle of the 16-byte units of a row (Z units per row; 0: none)
+template <int Z>
+__device__ __forceinline__ int swz(int row) {
+  if constexpr (Z == 2) return (row >> 2) & 1;
+  if constexpr (Z == 4) return (row >> 1) & 3;
+  return 0;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -123,7 +139,7 @@ __device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t& hi, u
 // column NV (when NV < NC), zeros after
 // ---------------------------------------------------------------------------
 
-template <int K, int S, int NC, int NV>
+template <int K, int S, int Z, int NC, int NV>
 __device__ __forceinline__ void put_row(unsigned char* plane, size_t plane_elems, int row, const float* v,
                                         float extra) {
   auto val = [&](int j) -> float { return j < NV ? v[j < NV ? j : 0] : (j == NV ? extra : 0.f); };
@@ -135,8 +151,9 @@ __device__ __forceinline__ void put_row(unsigned char* plane, size_t plane_elems
       uint32_t h[4], l[4];
 #pragma unroll
       for (int w = 0; w < 4; ++w) split_bf16x2(val(8 * q + 2 * w), val(8 * q + 2 * w + 1), h[w], l[w]);
-      reinterpret_cast<uint4*>(hi)[q] = make_uint4(h[0], h[1], h[2], h[3]);
-      reinterpret_cast<uint4*>(lo)[q] = make_uint4(l[0], l[1], l[2], l[3]);
+      const int u = q ^ swz<Z>(row);
+      reinterpret_cast<uint4*>(hi)[u] = make_uint4(h[0], h[1], h[2], h[3]);
+      reinterpret_cast<uint4*>(lo)[u] = make_uint4(l[0], l[1], l[2], l[3]);
     }
   } else {
     float* f = reinterpret_cast<float*>(plane) + (size_t)row * S;
@@ -162,10 +179,11 @@ __device__ __forceinline__ void zero_row(unsigned char* plane, size_t plane_elem
   }
 }
 
-template <int K, int S>
+template <int K, int S, int Z>
 __device__ __forceinline__ void put_one(unsigned char* plane, size_t plane_elems, int row, int j, float x) {
   if constexpr (K == kMmaBf16) {
-    __nv_bfloat16* hi = reinterpret_cast<__nv_bfloat16*>(plane) + (size_t)row * S + j;
+    __nv_bfloat16* hi =
+        reinterpret_cast<__nv_bfloat16*>(plane) + (size_t)row * S + (((j >> 3) ^ swz<Z>(row)) << 3) + (j & 7);
     const __nv_bfloat16 h = __float2bfloat16_rn(x);
     hi[0] = h;
     hi[plane_elems] = __float2bfloat16_rn(x - __bfloat162float(h));
@@ -179,9 +197,11 @@ __device__ __forceinline__ void put_one(unsigned char* plane, size_t plane_elems
 // tiles nj in [jt0, jt1) (warp-uniform range)
 // ---------------------------------------------------------------------------
 
-template <int K, int MT, int NTA, int SU, int SV>
+// acc takes hi*hi, accx the two cross products (two shorter dependency chains)
+template <int K, int MT, int NTA, int SU, int SV, int ZU, int ZV>
 __device__ __forceinline__ void mma_kstep(const unsigned char* Up, size_t u_plane, const unsigned char* Vp,
-                                          size_t v_plane, int k0, int jt0, int jt1, float (&acc)[MT][NTA][4]) {
+                                          size_t v_plane, int k0, int jt0, int jt1, float (&acc)[MT][NTA][4],
+                                          float (&accx)[MT][NTA][4]) {
   const int lane = threadIdx.x & 31;
   if constexpr (K == kMmaBf16) {
     const __nv_bfloat16* Uh = reinterpret_cast<const __nv_bfloat16*>(Up);
@@ -191,7 +211,8 @@ __device__ __forceinline__ void mma_kstep(const unsigned char* Up, size_t u_plan
 #pragma unroll
     for (int mi = 0; mi < MT; ++mi) {
       // matrices (i 0-7, k 0-7), (i 8-15, k 0-7), (i 0-7, k 8-15), (i 8-15, k 8-15)
-      const size_t off = (size_t)(k0 + (mq >> 1) * 8 + r) * SU + 16 * mi + (mq & 1) * 8;
+      const int row = k0 + (mq >> 1) * 8 + r;
+      const size_t off = (size_t)row * SU + (((2 * mi + (mq & 1)) ^ swz<ZU>(row)) << 3);
       ldsm_x4_t(ah[mi], Uh + off);
       ldsm_x4_t(al[mi], Uh + u_plane + off);
     }
@@ -199,15 +220,16 @@ __device__ __forceinline__ void mma_kstep(const unsigned char* Up, size_t u_plan
     for (int nj = 0; nj < NTA; ++nj) {
       if (nj < jt0 || nj >= jt1) continue;
       // matrices (k 0-7, j), (k 8-15, j) from lanes 0-15
-      const size_t off = (size_t)(k0 + (mq & 1) * 8 + r) * SV + 8 * nj;
+      const int row = k0 + (mq & 1) * 8 + r;
+      const size_t off = (size_t)row * SV + ((nj ^ swz<ZV>(row)) << 3);
       uint32_t bh[2], bl[2];
       ldsm_x2_t(bh, Vh + off);
       ldsm_x2_t(bl, Vh + v_plane + off);
 #pragma unroll
       for (int mi = 0; mi < MT; ++mi) {
-        mma_bf16_16816(acc[mi][nj], al[mi], bh);
-        mma_bf16_16816(acc[mi][nj], ah[mi], bl);
+        mma_bf16_16816(accx[mi][nj], al[mi], bh);
         mma_bf16_16816(acc[mi][nj], ah[mi], bh);
+        mma_bf16_16816(accx[mi][nj], ah[mi], bl);
       }
     }
   } else {
@@ -233,9 +255,9 @@ __device__ __forceinline__ void mma_kstep(const unsigned char* Up, size_t u_plan
       split_tf32(v0[4 * SV], bh[1], bl[1]);
 #pragma unroll
       for (int mi = 0; mi < MT; ++mi) {
-        mma_tf32_1688(acc[mi][nj], al[mi], bh);
-        mma_tf32_1688(acc[mi][nj], ah[mi], bl);
+        mma_tf32_1688(accx[mi][nj], al[mi], bh);
         mma_tf32_1688(acc[mi][nj], ah[mi], bh);
+        mma_tf32_1688(accx[mi][nj], ah[mi], bl);
       }
     }
   }
@@ -246,11 +268,15 @@ __device__ __forceinline__ void mma_kstep(const unsigned char* Up, size_t u_plan
 // ---------------------------------------------------------------------------
 
 template <int D, int P, int K>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, MmaCfg<D, P, K>::MINB)
     row_mma_kernel(const DevMesh m, int mode, float* __restrict__ vals, float* __restrict__ rhs) {
   using Cfg = MmaCfg<D, P, K>;
   constexpr int N = Cfg::N, MT = Cfg::MT, NW = Cfg::NW, NT8 = Cfg::NT8, NTA = Cfg::NTA, NTV = Cfg::NTV;
   constexpr int C = Cfg::C, RW = Cfg::RW, SU = Cfg::SU, SV = Cfg::SV, G = Cfg::G, KS = Cfg::KS;
+  constexpr int ZU = Cfg::ZU, ZV = Cfg::ZV;
+  // separate accumulators for the cross products only where few tiles
+  // would otherwise leave the MMA dependency chains exposed
+  constexpr bool XACC = MT * NTA <= 2;
   constexpr int PT = Cfg::PT, PI = Cfg::PI, QT = Cfg::QT, SVL = sub_vals(D);
   constexpr int X = 4 * D;  // first scalar slot in PT
   constexpr size_t UPL = Cfg::u_plane, VPL = Cfg::v_plane;
@@ -335,7 +361,7 @@ __global__ void __launch_bounds__(kWarps * 32)
     const int nfch = __reduce_max_sync(0xffffffffu, nf_l);
     const int nslot = __reduce_max_sync(0xffffffffu, ns_l);
 
-    float acc[G][MT][NTA][4];
+    float acc[G][MT][NTA][4], accx[G][MT][NTA][4];
 #pragma unroll
     for (int g = 0; g < G; ++g)
 #pragma unroll
@@ -343,7 +369,7 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
         for (int nj = 0; nj < NTA; ++nj)
 #pragma unroll
-          for (int r = 0; r < 4; ++r) acc[g][mi][nj][r] = 0.f;
+          for (int r = 0; r < 4; ++r) acc[g][mi][nj][r] = accx[g][mi][nj][r] = 0.f;
 
     // ---- volume points
     if (mat_vol || do_rhs) {
@@ -391,15 +417,15 @@ __global__ void __launch_bounds__(kWarps * 32)
               for (int d = 0; d < D; ++d) x[d] = pt[2 * D + d] + (xi[d] + 1.f) * 0.5f * pt[3 * D + d];
               R0 = W * source_f<D, float>(m.pb, pt[X + kPtA], x);
             }
-            put_row<K, SU, 16 * MT, N>(Ug, UPL, c, Phi, 0.f);
-            put_row<K, SV, NW, N>(Vg, VPL, c, Vv, R0);
+            put_row<K, SU, ZU, 16 * MT, N>(Ug, UPL, c, Phi, 0.f);
+            put_row<K, SV, ZV, NW, N>(Vg, VPL, c, Vv, R0);
 #pragma unroll
             for (int d = 0; d < D; ++d) {
               const float s = W * pt[d];
 #pragma unroll
               for (int i = 0; i < N; ++i) Vv[i] = s * Dd[d][i];
-              put_row<K, SU, 16 * MT, N>(Ug, UPL, (1 + d) * C + c, Dd[d], 0.f);
-              put_row<K, SV, NW, N>(Vg, VPL, (1 + d) * C + c, Vv, 0.f);
+              put_row<K, SU, ZU, 16 * MT, N>(Ug, UPL, (1 + d) * C + c, Dd[d], 0.f);
+              put_row<K, SV, ZV, NW, N>(Vg, VPL, (1 + d) * C + c, Vv, 0.f);
             }
           } else {
 #pragma unroll
@@ -410,22 +436,25 @@ __global__ void __launch_bounds__(kWarps * 32)
           }
         }
         __syncwarp();
+        bool gv[G];
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-          if (g >= gcount || ch * C >= PIv[g * PI + kPiNvol]) continue;
+        for (int g = 0; g < G; ++g) gv[g] = g < gcount && ch * C < PIv[g * PI + kPiNvol];
 #pragma unroll 1
-          for (int k0 = 0; k0 < RW; k0 += KS) {
-            const int t = k0 / C;
-            int jt0 = 0, jt1 = 0;
-            if (mat_vol && !(t == 0 && no_adv)) {
-              jt1 = NT8;
-            } else if (do_rhs && t == 0) {
-              jt0 = RT;
-              jt1 = RT + 1;
-            }
-            if (jt1 > jt0)
-              mma_kstep<K, MT, NTA, SU, SV>(Ust + g * EU, UPL, Vst + g * EV, VPL, k0, jt0, jt1, acc[g]);
+        for (int k0 = 0; k0 < RW; k0 += KS) {
+          const int t = k0 / C;
+          int jt0 = 0, jt1 = 0;
+          if (mat_vol && !(t == 0 && no_adv)) {
+            jt1 = NT8;
+          } else if (do_rhs && t == 0) {
+            jt0 = RT;
+            jt1 = RT + 1;
           }
+          if (jt1 <= jt0) continue;
+#pragma unroll
+          for (int g = 0; g < G; ++g)
+            if (gv[g])
+              mma_kstep<K, MT, NTA, SU, SV, ZU, ZV>(Ust + g * EU, UPL, Vst + g * EV, VPL, k0, jt0, jt1, acc[g],
+                                                    XACC ? accx[g] : acc[g]);
         }
         __syncwarp();
       }
@@ -484,10 +513,10 @@ __global__ void __launch_bounds__(kWarps * 32)
               R0 = W * (sig - upw) * gd;
               R1 = -W * a * gd;
             }
-            put_row<K, SU, 16 * MT, N>(Ug, UPL, c, Phi, 0.f);
-            put_row<K, SU, 16 * MT, N>(Ug, UPL, C + c, dn, 0.f);
-            put_row<K, SV, NW, N>(Vg, VPL, c, V0, R0);
-            put_row<K, SV, NW, N>(Vg, VPL, C + c, V1, R1);
+            put_row<K, SU, ZU, 16 * MT, N>(Ug, UPL, c, Phi, 0.f);
+            put_row<K, SU, ZU, 16 * MT, N>(Ug, UPL, C + c, dn, 0.f);
+            put_row<K, SV, ZV, NW, N>(Vg, VPL, c, V0, R0);
+            put_row<K, SV, ZV, NW, N>(Vg, VPL, C + c, V1, R1);
           } else {
 #pragma unroll
             for (int t = 0; t < 2; ++t) {
@@ -497,14 +526,17 @@ __global__ void __launch_bounds__(kWarps * 32)
           }
         }
         __syncwarp();
+        bool gv[G];
 #pragma unroll
-        for (int g = 0; g < G; ++g) {
-          if (g >= gcount || ch * C >= PIv[g * PI + kPiNface]) continue;
-          const int jt0 = mat_face ? 0 : RT, jt1 = mat_face ? NT8 : RT + 1;
+        for (int g = 0; g < G; ++g) gv[g] = g < gcount && ch * C < PIv[g * PI + kPiNface];
+        const int jt0 = mat_face ? 0 : RT, jt1 = mat_face ? NT8 : RT + 1;
 #pragma unroll 1
-          for (int k0 = 0; k0 < 2 * C; k0 += KS)
-            mma_kstep<K, MT, NTA, SU, SV>(Ust + g * EU, UPL, Vst + g * EV, VPL, k0, jt0, jt1, acc[g]);
-        }
+        for (int k0 = 0; k0 < 2 * C; k0 += KS)
+#pragma unroll
+          for (int g = 0; g < G; ++g)
+            if (gv[g])
+              mma_kstep<K, MT, NTA, SU, SV, ZU, ZV>(Ust + g * EU, UPL, Vst + g * EV, VPL, k0, jt0, jt1, acc[g],
+                                                    XACC ? accx[g] : acc[g]);
         __syncwarp();
       }
     }
@@ -527,10 +559,10 @@ __global__ void __launch_bounds__(kWarps * 32)
             const int i = 16 * mi + gq + 8 * (r >> 1), j = 8 * nj + 2 * cq + (r & 1);
             if (i >= N) continue;
             if (j < N && (mat_vol || mat_face)) {
-              const float v = RR * ctab[i] * ctab[j] * acc[g][mi][nj][r];
+              const float v = RR * ctab[i] * ctab[j] * (acc[g][mi][nj][r] + accx[g][mi][nj][r]);
               out[i * N + j] = accum ? out[i * N + j] + v : v;
             } else if (j == N && do_rhs) {
-              rout[i] = Re * ctab[i] * acc[g][mi][nj][r];
+              rout[i] = Re * ctab[i] * (acc[g][mi][nj][r] + accx[g][mi][nj][r]);
             }
           }
     }
@@ -582,7 +614,7 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
               for (int nj = 0; nj < NTA; ++nj)
 #pragma unroll
-                for (int r = 0; r < 4; ++r) acc[g][mi][nj][r] = 0.f;
+                for (int r = 0; r < 4; ++r) acc[g][mi][nj][r] = accx[g][mi][nj][r] = 0.f;
           for (int ch = 0; ch < nch; ++ch) {
             __syncwarp();
             if (lane < G * C) {
@@ -618,8 +650,8 @@ __global__ void __launch_bounds__(kWarps * 32)
                     for (int d = 0; d < D; ++d) v += sgn * ne_[d] * Dd[d][i];
                     dn[i] = v;
                   }
-                  put_row<K, SU, 16 * MT, N>(Ug, UPL, c, Phi, 0.f);
-                  put_row<K, SU, 16 * MT, N>(Ug, UPL, C + c, dn, 0.f);
+                  put_row<K, SU, ZU, 16 * MT, N>(Ug, UPL, c, Phi, 0.f);
+                  put_row<K, SU, ZU, 16 * MT, N>(Ug, UPL, C + c, dn, 0.f);
                 }
                 auto sink = [&](int j, float phik, const float* dk) {
                   const int jj = j - col0;
@@ -627,8 +659,8 @@ __global__ void __launch_bounds__(kWarps * 32)
                   float dnk = 0.f;
 #pragma unroll
                   for (int d = 0; d < D; ++d) dnk += sgn * nk_[d] * dk[d];
-                  put_one<K, SV>(Vg, VPL, c, jj, W * (-0.5f * ak * dnk + (upw - sig) * phik));
-                  put_one<K, SV>(Vg, VPL, C + c, jj, W * (0.5f * ae * phik));
+                  put_one<K, SV, ZV>(Vg, VPL, c, jj, W * (-0.5f * ak * dnk + (upw - sig) * phik));
+                  put_one<K, SV, ZV>(Vg, VPL, C + c, jj, W * (0.5f * ae * phik));
                 };
                 nbr_basis<D, float>(pi[kPiSPk], xk, sink);
               } else {
@@ -637,16 +669,21 @@ __global__ void __launch_bounds__(kWarps * 32)
               }
             }
             __syncwarp();
+            bool gv[G];
+            int gj[G];
 #pragma unroll
             for (int g = 0; g < G; ++g) {
-              if (g >= gcount) continue;
               const int* pi = PIv + g * PI;
-              if (ch * C >= pi[kPiSNpts] || col0 >= pi[kPiSNk]) continue;
-              const int jt1 = min(NTA, (pi[kPiSNk] - col0 + 7) / 8);
-#pragma unroll 1
-              for (int k0 = 0; k0 < 2 * C; k0 += KS)
-                mma_kstep<K, MT, NTA, SU, SV>(Ust + g * EU, UPL, Vst + g * EV, VPL, k0, 0, jt1, acc[g]);
+              gv[g] = g < gcount && ch * C < pi[kPiSNpts] && col0 < pi[kPiSNk];
+              gj[g] = gv[g] ? min(NTA, (pi[kPiSNk] - col0 + 7) / 8) : 0;
             }
+#pragma unroll 1
+            for (int k0 = 0; k0 < 2 * C; k0 += KS)
+#pragma unroll
+              for (int g = 0; g < G; ++g)
+                if (gv[g])
+                  mma_kstep<K, MT, NTA, SU, SV, ZU, ZV>(Ust + g * EU, UPL, Vst + g * EV, VPL, k0, 0, gj[g], acc[g],
+                                                        XACC ? accx[g] : acc[g]);
           }
           // this pass's columns of the off-diagonal blocks
 #pragma unroll
@@ -664,7 +701,8 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                   const int i = 16 * mi + gq + 8 * (r >> 1), j = col0 + 8 * nj + 2 * cq + (r & 1);
-                  if (i < N && j < nk && j < col0 + NW) out[i * nk + j] = RR * ctab[i] * ctab[j] * acc[g][mi][nj][r];
+                  if (i < N && j < nk)
+                    out[i * nk + j] = RR * ctab[i] * ctab[j] * (acc[g][mi][nj][r] + accx[g][mi][nj][r]);
                 }
           }
         }

@@ -9,6 +9,9 @@ Tolerances (block max-norm relative, as the other parity tests):
   split-BF16: bfloat16 halves keep x to 2^-18 and drop lo*lo below 2^-18
   |uv|: about 1e-5 relative per product, summed over up to ~10^3 rows with
   partial cancellation; 2e-4 per block and 2e-5 relative Frobenius.
+  Load vectors: the same products, but each element's vector is dominated
+  by the FP32 evaluation of the sin source near cancellation (3.4e-5 on the
+  65k-cell mesh for FP32 and both tensor forms alike); 1e-4 per element.
 """
 import numpy as np
 import pytest
@@ -22,6 +25,7 @@ pytestmark = pytest.mark.gpu
 
 TOL = {dg.DG_PREC_TF32X3: 5e-5, dg.DG_PREC_BF16X3: 2e-4}
 FRO = {dg.DG_PREC_TF32X3: 1e-6, dg.DG_PREC_BF16X3: 2e-5}
+TOL_RHS = 1e-4
 FORMS = [dg.DG_PREC_BF16X3, dg.DG_PREC_TF32X3]
 
 
@@ -64,7 +68,7 @@ def test_against_oracle(ctx, prec, which):
     om, ob = oracle_blocks(wl)
     ed, eo, er = compare(dg.to_blocks(m, v, r), om, ob, wl)
     print(f"\n{which} prec={prec}: diag {ed:.2e} off {eo:.2e} rhs {er:.2e}")
-    assert ed < TOL[prec] and eo < TOL[prec] and er < TOL[prec], (ed, eo, er)
+    assert ed < TOL[prec] and eo < TOL[prec] and er < TOL_RHS, (ed, eo, er)
     _, v64, _ = run_gpu(ctx, wl, dg.DG_PREC_FP64, m=m)
     fro = np.linalg.norm(v - v64) / np.linalg.norm(v64)
     print(f"{which} prec={prec}: rel Frobenius vs FP64 {fro:.2e}")
@@ -86,7 +90,7 @@ def test_adr2d_65k_sampled(ctx, prec):
     ed, eo, er = compare(dg.to_blocks(m, v, r), om, ob, wl)
     fro = np.linalg.norm(v - v64) / np.linalg.norm(v64)
     print(f"\nadr2d_65k prec={prec}: diag {ed:.2e} off {eo:.2e} rhs {er:.2e} fro {fro:.2e}")
-    assert ed < TOL[prec] and eo < TOL[prec] and er < TOL[prec], (ed, eo, er)
+    assert ed < TOL[prec] and eo < TOL[prec] and er < TOL_RHS, (ed, eo, er)
     assert fro < FRO[prec], fro
 
 
@@ -110,4 +114,4 @@ def test_diffusion_only_3d(ctx, prec):
     m, v, r = run_gpu(ctx, wl, prec)
     om, ob = oracle_blocks(wl)
     ed, eo, er = compare(dg.to_blocks(m, v, r), om, ob, wl)
-    assert ed < TOL[prec] and eo < TOL[prec] and er < TOL[prec], (ed, eo, er)
+    assert ed < TOL[prec] and eo < TOL[prec] and er < TOL_RHS, (ed, eo, er)
