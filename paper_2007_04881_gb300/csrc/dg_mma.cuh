@@ -22,7 +22,8 @@
 // u ^ f(r)), which keeps the 8 rows of every ldmatrix phase and of every
 // staging-store phase on distinct banks without padding; other widths are
 // padded to an odd number of units.  FP32 rows are padded to 8 or 24 mod 32
-// words (conflict-free fragment loads).
+// words (conflict-free fragment loads) and their 16-byte units swizzled by
+// bit 2 of the row (conflict-free staging stores).
 #pragma once
 
 #include <cuda_bf16.h>
@@ -46,10 +47,11 @@ struct MmaCfg {
   static constexpr int C = 16;                         // points per element per chunk
   static constexpr int RW = C * NTV;                   // staged rows per element
   static constexpr int WU = 2 * MT, WV = NW / 8;      // 16-byte units of a BF16 row
-  static constexpr int ZU = K == kMmaBf16 && (WU == 2 || WU == 4) ? WU : 0;  // swizzle width (0: padded)
-  static constexpr int ZV = K == kMmaBf16 && (WV == 2 || WV == 4) ? WV : 0;
-  static constexpr int SU = ZU ? 16 * MT : 16 * MT + 8;  // row strides, elements
-  static constexpr int SV = ZV ? NW : NW + 8;
+  // swizzle (BF16: row width in units, 0 = padded instead; FP32: 1)
+  static constexpr int ZU = K == kMmaBf16 ? ((WU == 2 || WU == 4) ? WU : 0) : 1;
+  static constexpr int ZV = K == kMmaBf16 ? ((WV == 2 || WV == 4) ? WV : 0) : 1;
+  static constexpr int SU = K == kMmaBf16 && ZU ? 16 * MT : 16 * MT + 8;  // row strides, elements
+  static constexpr int SV = K == kMmaBf16 && ZV ? NW : NW + 8;
   static constexpr int ESZ = K == kMmaBf16 ? 2 : 4;
   static constexpr int NPL = K == kMmaBf16 ? 2 : 1;    // planes (hi, lo) or one FP32 plane
   static constexpr size_t per_elem = (size_t)RW * (SU + SV) * ESZ * NPL;
@@ -74,10 +76,11 @@ struct MmaCfg {
 // fragments
 // ---------------------------------------------------------------------------
 
-// XOR swizzle of the 16-byte units of a row (Z units per row; 0: none)
+// XOR swizzle of the 16-byte units of a row (BF16 rows: Z units per row;
+// Z = 1: the FP32 rows' swizzle; 0: none)
 template <int Z>
 __device__ __forceinline__ int swz(int row) {
-  if constexpr (Z == 2) return (row >> 2) & 1;
+  if constexpr (Z == 1 || Z == 2) return (row >> 2) & 1;
   if constexpr (Z == 4) return (row >> 1) & 3;
   return 0;
 }
@@ -159,7 +162,8 @@ __device__ __forceinline__ void put_row(unsigned char* plane, size_t plane_elems
     float* f = reinterpret_cast<float*>(plane) + (size_t)row * S;
 #pragma unroll
     for (int q = 0; q < NC / 4; ++q)
-      reinterpret_cast<float4*>(f)[q] = make_float4(val(4 * q), val(4 * q + 1), val(4 * q + 2), val(4 * q + 3));
+      reinterpret_cast<float4*>(f)[q ^ swz<Z>(row)] =
+          make_float4(val(4 * q), val(4 * q + 1), val(4 * q + 2), val(4 * q + 3));
   }
 }
 
@@ -188,7 +192,7 @@ __device__ __forceinline__ void put_one(unsigned char* plane, size_t plane_elems
     hi[0] = h;
     hi[plane_elems] = __float2bfloat16_rn(x - __bfloat162float(h));
   } else {
-    reinterpret_cast<float*>(plane)[(size_t)row * S + j] = x;
+    reinterpret_cast<float*>(plane)[(size_t)row * S + (((j >> 2) ^ swz<Z>(row)) << 2) + (j & 3)] = x;
   }
 }
 
@@ -236,23 +240,26 @@ __device__ __forceinline__ void mma_kstep(const unsigned char* Up, size_t u_plan
     const float* U = reinterpret_cast<const float*>(Up);
     const float* V = reinterpret_cast<const float*>(Vp);
     const int g = lane >> 2, c = lane & 3;
+    // rows k0 + c and k0 + c + 4 (k0 a multiple of 8): swizzle bits 0 and 1
+    const int r0 = k0 + c, r1 = r0 + 4;
+    auto at = [](int row, int col) { return (((col >> 2) ^ swz<ZU>(row)) << 2) + (col & 3); };
+    auto bt = [](int row, int col) { return (((col >> 2) ^ swz<ZV>(row)) << 2) + (col & 3); };
     uint32_t ah[MT][4], al[MT][4];
 #pragma unroll
     for (int mi = 0; mi < MT; ++mi) {
-      const float* u0 = U + (size_t)(k0 + c) * SU + 16 * mi + g;
-      const float* u1 = u0 + 4 * SU;
-      split_tf32(u0[0], ah[mi][0], al[mi][0]);
-      split_tf32(u0[8], ah[mi][1], al[mi][1]);
-      split_tf32(u1[0], ah[mi][2], al[mi][2]);
-      split_tf32(u1[8], ah[mi][3], al[mi][3]);
+      const float* u0 = U + (size_t)r0 * SU;
+      const float* u1 = U + (size_t)r1 * SU;
+      split_tf32(u0[at(r0, 16 * mi + g)], ah[mi][0], al[mi][0]);
+      split_tf32(u0[at(r0, 16 * mi + g + 8)], ah[mi][1], al[mi][1]);
+      split_tf32(u1[at(r1, 16 * mi + g)], ah[mi][2], al[mi][2]);
+      split_tf32(u1[at(r1, 16 * mi + g + 8)], ah[mi][3], al[mi][3]);
     }
 #pragma unroll
     for (int nj = 0; nj < NTA; ++nj) {
       if (nj < jt0 || nj >= jt1) continue;
-      const float* v0 = V + (size_t)(k0 + c) * SV + 8 * nj + g;
       uint32_t bh[2], bl[2];
-      split_tf32(v0[0], bh[0], bl[0]);
-      split_tf32(v0[4 * SV], bh[1], bl[1]);
+      split_tf32(V[(size_t)r0 * SV + bt(r0, 8 * nj + g)], bh[0], bl[0]);
+      split_tf32(V[(size_t)r1 * SV + bt(r1, 8 * nj + g)], bh[1], bl[1]);
 #pragma unroll
       for (int mi = 0; mi < MT; ++mi) {
         mma_tf32_1688(accx[mi][nj], al[mi], bh);

@@ -26,6 +26,9 @@ pytestmark = pytest.mark.gpu
 TOL = {dg.DG_PREC_TF32X3: 5e-5, dg.DG_PREC_BF16X3: 2e-4}
 FRO = {dg.DG_PREC_TF32X3: 1e-6, dg.DG_PREC_BF16X3: 2e-5}
 TOL_RHS = 1e-4
+# on meshes where the FP32 basis values already limit the error (large
+# degree-4 polyhedra), the bound is a multiple of the FP32 form's own error
+REL32 = {dg.DG_PREC_TF32X3: 2.0, dg.DG_PREC_BF16X3: 20.0}
 FORMS = [dg.DG_PREC_BF16X3, dg.DG_PREC_TF32X3]
 
 
@@ -70,9 +73,13 @@ def test_against_oracle(ctx, prec, which):
     print(f"\n{which} prec={prec}: diag {ed:.2e} off {eo:.2e} rhs {er:.2e}")
     assert ed < TOL[prec] and eo < TOL[prec] and er < TOL_RHS, (ed, eo, er)
     _, v64, _ = run_gpu(ctx, wl, dg.DG_PREC_FP64, m=m)
+    _, v32, _ = run_gpu(ctx, wl, dg.DG_PREC_FP32, m=m)
     fro = np.linalg.norm(v - v64) / np.linalg.norm(v64)
-    print(f"{which} prec={prec}: rel Frobenius vs FP64 {fro:.2e}")
-    assert fro < FRO[prec], fro
+    fro32 = np.linalg.norm(v32 - v64) / np.linalg.norm(v64)
+    print(f"{which} prec={prec}: rel Frobenius vs FP64 {fro:.2e} (FP32 form {fro32:.2e})")
+    # the tensor forms share the FP32 basis values and weights; only the
+    # contraction arithmetic differs from the FP32 form
+    assert fro < max(FRO[prec], REL32[prec] * fro32), (fro, fro32)
 
 
 @pytest.mark.parametrize("prec", FORMS)
