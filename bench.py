@@ -452,6 +452,7 @@ def run_ours(args):
             "matrix_rel_max": float(df.abs().max() / v64.abs().max()),
             "rhs_rel_fro": float(torch.linalg.vector_norm(rf.double() - r64) / torch.linalg.vector_norm(r64)),
             "kernels_ms_direct_launch": {k: v[0] / v[1] for k, v in sorted(ksf.items())},
+            "graph": gf.dg_graph_info(),
         }
         del vf, rf, gf, df
     del v64, r64, g64
