@@ -6,7 +6,11 @@
 //   3xTF32: the same split with TF32 halves, m16n8k8, FP32 accumulation.
 // Geometry, quadrature points and weights, basis values and the per-point
 // rows are the FP32 form's (FP32 values of the FP64 geometry); only the
-// contractions change.  Block rows are owned by warps exactly as in
+// contractions change.  The tensor cores' FP32 accumulation is not rounded
+// to nearest at every addition, so its accumulators live for one chunk of
+// points only and are added to IEEE FP32 running sums after each chunk:
+// large elements (thousands of points) then keep the FP32 form's accuracy.
+// Block rows are owned by warps exactly as in
 // row_kernel: the diagonal block (volume + own faces, fixed order), the load
 // vector and the off-diagonal blocks of an element are written once by the
 // warp that owns it, with no atomics.
@@ -368,7 +372,24 @@ __global__ void __launch_bounds__(kWarps * 32, MmaCfg<D, P, K>::MINB)
     const int nfch = __reduce_max_sync(0xffffffffu, nf_l);
     const int nslot = __reduce_max_sync(0xffffffffu, ns_l);
 
-    float acc[G][MT][NTA][4], accx[G][MT][NTA][4];
+    // acc / accx: the MMA accumulators of one chunk (at most RW / KS
+    // k-steps); acct: the running sums, added in IEEE FP32 after every chunk,
+    // so no accumulation chain inside the tensor cores spans more than one
+    // chunk however many points an element has
+    float acc[G][MT][NTA][4], accx[G][MT][NTA][4], acct[G][MT][NTA][4];
+    auto flush = [&]() {
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+#pragma unroll
+        for (int mi = 0; mi < MT; ++mi)
+#pragma unroll
+          for (int nj = 0; nj < NTA; ++nj)
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              acct[g][mi][nj][r] += acc[g][mi][nj][r] + accx[g][mi][nj][r];
+              acc[g][mi][nj][r] = accx[g][mi][nj][r] = 0.f;
+            }
+    };
 #pragma unroll
     for (int g = 0; g < G; ++g)
 #pragma unroll
@@ -376,7 +397,7 @@ __global__ void __launch_bounds__(kWarps * 32, MmaCfg<D, P, K>::MINB)
 #pragma unroll
         for (int nj = 0; nj < NTA; ++nj)
 #pragma unroll
-          for (int r = 0; r < 4; ++r) acc[g][mi][nj][r] = accx[g][mi][nj][r] = 0.f;
+          for (int r = 0; r < 4; ++r) acc[g][mi][nj][r] = accx[g][mi][nj][r] = acct[g][mi][nj][r] = 0.f;
 
     // ---- volume points
     if (mat_vol || do_rhs) {
@@ -463,6 +484,7 @@ __global__ void __launch_bounds__(kWarps * 32, MmaCfg<D, P, K>::MINB)
               mma_kstep<K, MT, NTA, SU, SV, ZU, ZV>(Ust + g * EU, UPL, Vst + g * EV, VPL, k0, jt0, jt1, acc[g],
                                                     XACC ? accx[g] : acc[g]);
         }
+        flush();
         __syncwarp();
       }
     }
@@ -544,6 +566,7 @@ __global__ void __launch_bounds__(kWarps * 32, MmaCfg<D, P, K>::MINB)
             if (gv[g])
               mma_kstep<K, MT, NTA, SU, SV, ZU, ZV>(Ust + g * EU, UPL, Vst + g * EV, VPL, k0, jt0, jt1, acc[g],
                                                     XACC ? accx[g] : acc[g]);
+        flush();
         __syncwarp();
       }
     }
@@ -566,10 +589,10 @@ __global__ void __launch_bounds__(kWarps * 32, MmaCfg<D, P, K>::MINB)
             const int i = 16 * mi + gq + 8 * (r >> 1), j = 8 * nj + 2 * cq + (r & 1);
             if (i >= N) continue;
             if (j < N && (mat_vol || mat_face)) {
-              const float v = RR * ctab[i] * ctab[j] * (acc[g][mi][nj][r] + accx[g][mi][nj][r]);
+              const float v = RR * ctab[i] * ctab[j] * acct[g][mi][nj][r];
               out[i * N + j] = accum ? out[i * N + j] + v : v;
             } else if (j == N && do_rhs) {
-              rout[i] = Re * ctab[i] * (acc[g][mi][nj][r] + accx[g][mi][nj][r]);
+              rout[i] = Re * ctab[i] * acct[g][mi][nj][r];
             }
           }
     }
@@ -621,7 +644,7 @@ __global__ void __launch_bounds__(kWarps * 32, MmaCfg<D, P, K>::MINB)
 #pragma unroll
               for (int nj = 0; nj < NTA; ++nj)
 #pragma unroll
-                for (int r = 0; r < 4; ++r) acc[g][mi][nj][r] = accx[g][mi][nj][r] = 0.f;
+                for (int r = 0; r < 4; ++r) acc[g][mi][nj][r] = accx[g][mi][nj][r] = acct[g][mi][nj][r] = 0.f;
           for (int ch = 0; ch < nch; ++ch) {
             __syncwarp();
             if (lane < G * C) {
@@ -691,6 +714,7 @@ __global__ void __launch_bounds__(kWarps * 32, MmaCfg<D, P, K>::MINB)
                 if (gv[g])
                   mma_kstep<K, MT, NTA, SU, SV, ZU, ZV>(Ust + g * EU, UPL, Vst + g * EV, VPL, k0, 0, gj[g], acc[g],
                                                         XACC ? accx[g] : acc[g]);
+            flush();
           }
           // this pass's columns of the off-diagonal blocks
 #pragma unroll
@@ -709,7 +733,7 @@ __global__ void __launch_bounds__(kWarps * 32, MmaCfg<D, P, K>::MINB)
                 for (int r = 0; r < 4; ++r) {
                   const int i = 16 * mi + gq + 8 * (r >> 1), j = col0 + 8 * nj + 2 * cq + (r & 1);
                   if (i < N && j < nk)
-                    out[i * nk + j] = RR * ctab[i] * ctab[j] * (acc[g][mi][nj][r] + accx[g][mi][nj][r]);
+                    out[i * nk + j] = RR * ctab[i] * ctab[j] * acct[g][mi][nj][r];
                 }
           }
         }
