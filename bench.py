@@ -293,16 +293,53 @@ def cpu_baseline_sample(wl, seconds_target=12.0):
     el = np.arange(n2, dtype=np.int32)
     ifs = np.arange(int(round(n2 * om.ni / wl.ne)), dtype=np.int32)
     t = time.perf_counter()
-    om.assemble(p, wl.a, pb, elems=el, ifaces=ifs, nthreads=cores)
+    ob = om.assemble(p, wl.a, pb, elems=el, ifaces=ifs, nthreads=cores)
     dt = time.perf_counter() - t
-    return {
+    # one thread, on a sample of about a third of the OpenMP run's CPU time per core
+    n1 = max(16, min(n2, int(n2 * 4.0 / max(dt * cores, 1e-3))))
+    el1 = np.arange(n1, dtype=np.int32)
+    ifs1 = np.arange(int(round(n1 * om.ni / wl.ne)), dtype=np.int32)
+    t = time.perf_counter()
+    om.assemble(p, wl.a, pb, elems=el1, ifaces=ifs1, nthreads=1)
+    dt1 = time.perf_counter() - t
+    line = {
         "value": n2 / dt,
         "unit": "elements/s",
         "cores": cores,
         "kind": "oracle",
         "sample": f"first {n2} of {wl.ne} elements (diagonal blocks + load vector) and {ifs.size} of {om.ni} "
                   f"interfaces, FP64, {dt:.1f} s on {cores} threads",
+        "one_thread": {"value": n1 / dt1, "unit": "elements/s",
+                       "sample": f"first {n1} elements and {ifs1.size} interfaces, {dt1:.1f} s on 1 thread"},
     }
+    return line, (om, ob)
+
+
+def oracle_error(mesh, vals, rhs, om, ob):
+    """Largest block max-norm relative difference between the library's
+    result (host arrays) and the oracle's sampled blocks."""
+    from math import comb
+
+    row_ptr, col, blk_off, dof_off = mesh.dg_bsr_pattern()
+    nb = np.array([comb(int(q) + mesh.dim, mesh.dim) for q in mesh.p])
+
+    def block(r, c):
+        cols = col[row_ptr[r]:row_ptr[r + 1]]
+        k = row_ptr[r] + int(np.searchsorted(cols, c))
+        return vals[blk_off[k]:blk_off[k + 1]].reshape(nb[r], nb[c])
+
+    def rel(g, o):
+        s = np.abs(o).max()
+        return float(np.abs(g - o).max() / s) if s > 0 else float(np.abs(g).max())
+
+    ed = max(rel(block(int(e), int(e)), ob["diag"][i]) for i, e in enumerate(ob["elems"]))
+    er = max(rel(rhs[dof_off[int(e)]:dof_off[int(e) + 1]], ob["rhs"][i]) for i, e in enumerate(ob["elems"]))
+    eo = 0.0
+    for k, i in enumerate(ob["ifaces"]):
+        e0, e1 = int(om.if_e0[i]), int(om.if_e1[i])
+        eo = max(eo, rel(block(e0, e1), ob["a01"][k]), rel(block(e1, e0), ob["a10"][k]))
+    return {"diag_block_rel_max": ed, "offdiag_block_rel_max": eo, "rhs_rel_max": er,
+            "sample": f"{len(ob['elems'])} elements and {len(ob['ifaces'])} interfaces of the oracle sample"}
 
 
 # ---------------------------------------------------------------------------
@@ -562,9 +599,13 @@ def run_ours(args):
         "timed_wall_s": t_wall,
     }
     if ws == 1 and not args.no_cpu_baseline and not isinstance(wl, _Batch):
-        line["cpu_baseline"] = cpu_baseline_sample(wl)
+        line["cpu_baseline"], (om, ob) = cpu_baseline_sample(wl)
+        # the headline form's result against the oracle on the same sample
+        g32.dg_graph_launch()
+        torch.cuda.synchronize()
+        line["error_vs_oracle"] = oracle_error(mesh, v32.double().cpu().numpy(), r32.double().cpu().numpy(), om, ob)
     elif ws == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline_sample(wl.members[0])
+        line["cpu_baseline"], _ = cpu_baseline_sample(wl.members[0])
         line["cpu_baseline"]["sample"] = "batch member 0: " + line["cpu_baseline"]["sample"]
     print(json.dumps(line))
     return 0
