@@ -722,6 +722,21 @@ def run_learned(args):
     e32max = float((v32.double() - ref64).abs().max() / ref64.abs().max())
     resid = dg.device_view(b["resid"], (info.ne,), "f4").cpu().numpy()
     okv = dg.device_view(b["ok"], (info.ne,), "i4").cpu().numpy().astype(bool)
+    # end to end through the host-memory entry point, learned rules installed
+    pin = lambda a, dt: torch.from_numpy(np.ascontiguousarray(a, dtype=dt)).pin_memory()  # noqa: E731
+    hx, hy, ha = pin(wl.mesh.x, np.float64), pin(wl.mesh.y, np.float64), pin(wl.a, np.float64)
+    hv = torch.empty(mesh.nvals, dtype=torch.float32).pin_memory()
+    hr = torch.empty(mesh.ndofs, dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        mesh.dg_assemble_host(dg.DG_PREC_FP32, hv, hr, x=hx, y=hy, a=ha)
+    e2e_steps = max(3, min(args.steps, 20))
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        mesh.dg_assemble_host(dg.DG_PREC_FP32, hv, hr, x=hx, y=hy, a=ha)
+    e2e_s = (time.perf_counter() - t) / e2e_steps
+    e2e = {"value": info.ne / e2e_s, "unit": "elements/s",
+           "h2d_bytes_per_step": (hx.numel() + hy.numel() + ha.numel()) * 8,
+           "d2h_bytes_per_step": (hv.numel() + hr.numel()) * 4, "ms_per_step": 1e3 * e2e_s}
     # the same budget from the fixed start (no network)
     mesh.dg_quad_clear()
     fixed3 = mesh.dg_quad_fit(None, iters=3, install=False)
@@ -764,6 +779,7 @@ def run_learned(args):
             "training": {"polygons": int(X.shape[0]), "epochs": epochs, "steps": nstep, "batch": bs,
                          "targets_s": targets_s, "train_s": train_s, "final_loss": final_loss},
         },
+        "e2e": e2e,
         "gpu_launches": mesh.ctx.launches() * args.steps,
         "clocks": clocks,
     }
