@@ -35,15 +35,13 @@ namespace dg {
 __host__ __device__ constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
 
 // Register-tile geometry of the element kernel for (D, P): each thread owns a
-// TM x TM tile of the (padded) n x n block; G elements share a warp.  SYM:
-// the diagonal block is symmetric (b = 0), so only its TR (TR + 1) / 2 upper
-// tiles are computed (and mirrored when written).
-template <int D, int P, bool SYM = false>
+// TM x TM tile of the (padded) n x n block; G elements share a warp.
+template <int D, int P>
 struct TileCfg {
   static constexpr int N = nbasis(D, P);
   static constexpr int TM = D == 2 ? (P <= 2 ? 3 : P == 3 ? 5 : P == 4 ? 4 : 7) : (P == 1 ? 4 : P <= 3 ? 5 : 7);
   static constexpr int TR = (N + TM - 1) / TM;
-  static constexpr int TPE = SYM ? TR * (TR + 1) / 2 : TR * TR;
+  static constexpr int TPE = TR * TR;
   static constexpr int G = 32 / TPE;
   static constexpr int TMP = (TM + 1) / 2 * 2;  // padded tile stride (paired loads)
   static constexpr int ROW = TR * TMP;
@@ -698,9 +696,9 @@ __global__ void __launch_bounds__(kWarps * 32)
 // memory by one lane per point and contracted by the tile threads
 // --------------------------------------------------------------------------
 
-template <int D, int P, typename T, bool SYM = false>
+template <int D, int P, typename T>
 struct RowSmem {
-  using Cfg = TileCfg<D, P, SYM>;
+  using Cfg = TileCfg<D, P>;
   static constexpr int G = Cfg::G, TM = Cfg::TM, TR = Cfg::TR, TMP = Cfg::TMP, ROW = Cfg::ROW, NT = Cfg::NT;
   static constexpr int C = ChunkCfg<D, T>::CW / G > 0 ? ChunkCfg<D, T>::CW / G : 1;
   static constexpr int PSU = point_stride<T, TMP>(NT * ROW);  // staged point: NT rows of ROW
@@ -743,11 +741,11 @@ enum : int {
 // T parameter slots: a'[D], b'[D], lo[D], L[D], then:
 enum : int { kPtC = 0, kPtA = 1, kPtR = 2, kPtAk = 3, kPtRk = 4 };
 
-template <int D, int P, typename T, bool SYM>
+template <int D, int P, typename T>
 __global__ void __launch_bounds__(kWarps * 32)
     row_kernel(const DevMesh m, int mode, T* __restrict__ vals, T* __restrict__ rhs) {
-  using Cfg = TileCfg<D, P, SYM>;
-  using SM = RowSmem<D, P, T, SYM>;
+  using Cfg = TileCfg<D, P>;
+  using SM = RowSmem<D, P, T>;
   constexpr int N = Cfg::N, TM = Cfg::TM, TR = Cfg::TR, TPE = Cfg::TPE, G = Cfg::G;
   constexpr int TMP = Cfg::TMP, ROW = Cfg::ROW, NT = Cfg::NT, QT = Cfg::QT, C = SM::C;
   constexpr int SV = sub_vals(D), PT = SM::PT, PI = SM::PI, PSU = SM::PSU;
@@ -787,22 +785,7 @@ __global__ void __launch_bounds__(kWarps * 32)
   const int ntiles = (count + G - 1) / G;
 
   const int g_me = lane / TPE;
-  int tr, tc;
-  if constexpr (SYM) {
-    // upper tiles in row order: (0,0), (0,1), .., (0,TR-1), (1,1), ..
-    int k = lane % TPE, r = 0;
-    while (k >= TR - r) {
-      k -= TR - r;
-      ++r;
-    }
-    tr = r;
-    tc = r + k;
-  } else {
-    tr = (lane % TPE) / TR;
-    tc = lane % TR;
-  }
-  // one thread per row group accumulates the load vector
-  const bool rhs_thr = SYM ? tr == tc : tc == 0;
+  const int tr = (lane % TPE) / TR, tc = lane % TR;
 
   for (int tile = blockIdx.x * kWarps + warp; tile < ntiles; tile += gridDim.x * kWarps) {
     const int gcount = min(G, count - tile * G);
@@ -948,7 +931,7 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
                   for (int b = 0; b < TM; ++b) acc[a][b] = fma(u[a], v[b], acc[a][b]);
               }
-              if (do_rhs && rhs_thr) {
+              if (do_rhs && tc == 0) {
                 const T rv = R[(g_me * C + c) * NT + t];
 #pragma unroll
                 for (int a = 0; a < TM; ++a) racc[a] = fma(u[a], rv, racc[a]);
@@ -1045,7 +1028,7 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
                   for (int b = 0; b < TM; ++b) acc[a][b] = fma(u[a], v[b], acc[a][b]);
               }
-              if (do_rhs && rhs_thr) {
+              if (do_rhs && tc == 0) {
                 const T rv = R[(g_me * C + c) * NT + t];
 #pragma unroll
                 for (int a = 0; a < TM; ++a) racc[a] = fma(u[a], rv, racc[a]);
@@ -1075,13 +1058,12 @@ __global__ void __launch_bounds__(kWarps * 32)
               if (j < N) {
                 const T v = si * ctab[j] * acc[a][b];
                 out[i * N + j] = accum ? out[i * N + j] + v : v;
-                if (SYM && tr != tc) out[j * N + i] = accum ? out[j * N + i] + v : v;
               }
             }
           }
         }
       }
-      if (do_rhs && rhs_thr) {
+      if (do_rhs && tc == 0) {
         T* out = rhs + m.dof_off[e];
 #pragma unroll
         for (int a = 0; a < TM; ++a) {
@@ -1124,9 +1106,7 @@ __global__ void __launch_bounds__(kWarps * 32)
         int np_l = 0, pc_l = 0;
         if (lane < gcount) {
           np_l = (PIv[lane * PI + kPiSNpts] + C - 1) / C;
-          // tiles of the off-diagonal block: TR row groups x ceil(nk / TM)
-          // column groups, TPE of them per pass
-          pc_l = (TR * ((PIv[lane * PI + kPiSNk] + TM - 1) / TM) + TPE - 1) / TPE;
+          pc_l = ((PIv[lane * PI + kPiSNk] + TM - 1) / TM + TR - 1) / TR;
         }
         const int nch = __reduce_max_sync(0xffffffffu, np_l);
         const int npass = __reduce_max_sync(0xffffffffu, pc_l);
@@ -1136,8 +1116,7 @@ __global__ void __launch_bounds__(kWarps * 32)
           for (int a = 0; a < TM; ++a)
 #pragma unroll
             for (int b = 0; b < TM; ++b) acc[a][b] = T(0);
-          const int lt = pass * TPE + lane % TPE;
-          const int str = lt % TR, col0 = (lt / TR) * TM;
+          const int col0 = (pass * TR + tc) * TM;
           for (int ch = 0; ch < nch; ++ch) {
             if (pass == 0 || nch > 1) {
               __syncwarp();
@@ -1192,12 +1171,10 @@ __global__ void __launch_bounds__(kWarps * 32)
               }
               __syncwarp();
             }
-            // a tile past the neighbour's columns reads nothing: col0 < nk
-            // keeps col0 + TM within the staged row of VS columns
-            if (active && col0 < PIv[g_me * PI + kPiSNk]) {
+            if (active) {
 #pragma unroll 1
               for (int c = 0; c < C; ++c) {
-                const T* Ub = U + (size_t)(g_me * C + c) * PSU + str * TMP;
+                const T* Ub = U + (size_t)(g_me * C + c) * PSU + tr * TMP;
                 const T* Vb = V + (size_t)(g_me * C + c) * PSN + col0;
 #pragma unroll
                 for (int t = 0; t < 2; ++t) {
@@ -1222,7 +1199,7 @@ __global__ void __launch_bounds__(kWarps * 32)
               const T RR = PTv[g_me * PT + X + kPtR] * PTv[g_me * PT + X + kPtRk];
 #pragma unroll
               for (int a = 0; a < TM; ++a) {
-                const int i = str * TM + a;
+                const int i = tr * TM + a;
                 if (i < N) {
                   const T si = RR * ctab[i];
 #pragma unroll

@@ -20,20 +20,6 @@ inline int resident_grid(K kernel, size_t smem, int sm_count, int want_blocks, i
   return want_blocks < g ? want_blocks : g;
 }
 
-template <int D, int P, typename T, bool SYM>
-inline void launch_tiles(const DevMesh& m, int mode, T* vals, T* rhs, int count, int sm_count, const LaunchOpts& lo,
-                         cudaStream_t st) {
-  using SM = RowSmem<D, P, T, SYM>;
-  constexpr int G = TileCfg<D, P, SYM>::G;
-  static_assert(SM::total(kWarps, nbasis(D, D == 2 ? kPMax2 : kPMax3)) <= 227 * 1024,
-                "row kernel shared memory exceeds 227 KB");
-  const int ntiles = (count + G - 1) / G;
-  const size_t smem = SM::total(kWarps, m.nmax);
-  auto k = row_kernel<D, P, T, SYM>;
-  const int grid = resident_grid(k, smem, sm_count, (ntiles + kWarps - 1) / kWarps, lo.occ_cap);
-  k<<<grid, kWarps * 32, smem, st>>>(m, mode, vals, rhs);
-}
-
 template <int D, int P, typename T>
 inline int launch_row_p(const DevMesh& m, int mode, T* vals, T* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr) {
   const int count = m.elem_pstart[P + 1] - m.elem_pstart[P];
@@ -49,11 +35,16 @@ inline int launch_row_p(const DevMesh& m, int mode, T* vals, T* rhs, int sm_coun
     auto k = row_lane_kernel<D, P, T>;
     const int grid = resident_grid(k, 0, sm_count, (count + kWarps * 32 - 1) / (kWarps * 32), lo.occ_cap);
     k<<<grid, kWarps * 32, 0, st>>>(m, mode, vals, rhs);
-  } else if (m.pb.b[0] == 0.0 && m.pb.b[1] == 0.0 && m.pb.b[2] == 0.0) {
-    // no advection: symmetric diagonal blocks, upper tiles only
-    launch_tiles<D, P, T, true>(m, mode, vals, rhs, count, sm_count, lo, st);
   } else {
-    launch_tiles<D, P, T, false>(m, mode, vals, rhs, count, sm_count, lo, st);
+    using SM = RowSmem<D, P, T>;
+    constexpr int G = TileCfg<D, P>::G;
+    static_assert(SM::total(kWarps, nbasis(D, D == 2 ? kPMax2 : kPMax3)) <= 227 * 1024,
+                  "row kernel shared memory exceeds 227 KB");
+    const int ntiles = (count + G - 1) / G;
+    const size_t smem = SM::total(kWarps, m.nmax);
+    auto k = row_kernel<D, P, T>;
+    const int grid = resident_grid(k, smem, sm_count, (ntiles + kWarps - 1) / kWarps, lo.occ_cap);
+    k<<<grid, kWarps * 32, smem, st>>>(m, mode, vals, rhs);
   }
   if (tr && tr->on) tr->end(st);
   return 1;
