@@ -35,11 +35,18 @@ namespace dg {
 __host__ __device__ constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b * ipow_c(b, e - 1); }
 
 // Register-tile geometry of the element kernel for (D, P): each thread owns a
-// TM x TM tile of the (padded) n x n block; G elements share a warp.
-template <int D, int P>
+// TM x TM tile of the (padded) n x n block; G elements share a warp.  TM = n
+// (one tile) selects the one-thread-per-element kernel.  The FP32 table was
+// picked by measurement on the 65k-cell 2D workload: degree 2 runs a whole
+// element per thread (36 accumulators) and degree 4 uses 8 x 8 tiles, 4
+// threads per element; other tile sizes and chunk widths measured slower.
+template <int D, int P, typename T = float>
 struct TileCfg {
   static constexpr int N = nbasis(D, P);
-  static constexpr int TM = D == 2 ? (P <= 2 ? 3 : P == 3 ? 5 : P == 4 ? 4 : 7) : (P == 1 ? 4 : P <= 3 ? 5 : 7);
+  static constexpr int TM = sizeof(T) == 4 && D == 2 && P == 2   ? 6
+                            : sizeof(T) == 4 && D == 2 && P == 4 ? 8
+                            : D == 2 ? (P <= 2 ? 3 : P == 3 ? 5 : P == 4 ? 4 : 7)
+                                     : (P == 1 ? 4 : P <= 3 ? 5 : 7);
   static constexpr int TR = (N + TM - 1) / TM;
   static constexpr int TPE = TR * TR;
   static constexpr int G = 32 / TPE;
@@ -698,7 +705,7 @@ __global__ void __launch_bounds__(kWarps * 32)
 
 template <int D, int P, typename T>
 struct RowSmem {
-  using Cfg = TileCfg<D, P>;
+  using Cfg = TileCfg<D, P, T>;
   static constexpr int G = Cfg::G, TM = Cfg::TM, TR = Cfg::TR, TMP = Cfg::TMP, ROW = Cfg::ROW, NT = Cfg::NT;
   static constexpr int C = ChunkCfg<D, T>::CW / G > 0 ? ChunkCfg<D, T>::CW / G : 1;
   static constexpr int PSU = point_stride<T, TMP>(NT * ROW);  // staged point: NT rows of ROW
@@ -744,7 +751,7 @@ enum : int { kPtC = 0, kPtA = 1, kPtR = 2, kPtAk = 3, kPtRk = 4 };
 template <int D, int P, typename T>
 __global__ void __launch_bounds__(kWarps * 32)
     row_kernel(const DevMesh m, int mode, T* __restrict__ vals, T* __restrict__ rhs) {
-  using Cfg = TileCfg<D, P>;
+  using Cfg = TileCfg<D, P, T>;
   using SM = RowSmem<D, P, T>;
   constexpr int N = Cfg::N, TM = Cfg::TM, TR = Cfg::TR, TPE = Cfg::TPE, G = Cfg::G;
   constexpr int TMP = Cfg::TMP, ROW = Cfg::ROW, NT = Cfg::NT, QT = Cfg::QT, C = SM::C;

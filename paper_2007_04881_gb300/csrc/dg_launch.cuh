@@ -30,14 +30,14 @@ inline int launch_row_p(const DevMesh& m, int mode, T* vals, T* rhs, int sm_coun
     snprintf(name, sizeof name, "row%dd_p%d_%s", D, P, sizeof(T) == 8 ? "f64" : "f32");
     tr->begin(name, 0, P, sizeof(T), st);
   }
-  if constexpr (TileCfg<D, P>::TPE == 1) {
+  if constexpr (TileCfg<D, P, T>::TPE == 1) {
     // one element per thread, no staging
     auto k = row_lane_kernel<D, P, T>;
     const int grid = resident_grid(k, 0, sm_count, (count + kWarps * 32 - 1) / (kWarps * 32), lo.occ_cap);
     k<<<grid, kWarps * 32, 0, st>>>(m, mode, vals, rhs);
   } else {
     using SM = RowSmem<D, P, T>;
-    constexpr int G = TileCfg<D, P>::G;
+    constexpr int G = TileCfg<D, P, T>::G;
     static_assert(SM::total(kWarps, nbasis(D, D == 2 ? kPMax2 : kPMax3)) <= 227 * 1024,
                   "row kernel shared memory exceeds 227 KB");
     const int ntiles = (count + G - 1) / G;
