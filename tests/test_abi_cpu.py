@@ -137,3 +137,32 @@ def test_single_element_and_rectangles(lib):
     m = mg.rectangle_grid(3, 2)
     info = dg.dg_mesh_check(m, np.full(6, 1, np.int8), np.ones(6), dg.Problem())
     assert info.ninterfaces == 7 and info.nbfaces == 10 and info.nnzb == 6 + 14
+
+
+def test_empty_and_degenerate_inputs_rejected(lib):
+    # no elements
+    m = mg.Mesh2D(np.zeros(3), np.zeros(3), np.zeros(1, np.int32), np.zeros(0, np.int32))
+    with pytest.raises(dg.DGError) as ei:
+        dg.dg_mesh_check(m, np.zeros(0, np.int8), np.zeros(0), dg.Problem())
+    assert ei.value.code == -1
+    # a flat tetrahedron (zero volume)
+    x = np.array([0.0, 1.0, 0.0, 0.5])
+    y = np.array([0.0, 0.0, 1.0, 0.5])
+    z = np.zeros(4)
+    m = mg.Mesh3D(x, y, z, np.array([0, 1], np.int32), np.array([0, 1, 2, 3], np.int32))
+    with pytest.raises(dg.DGError) as ei:
+        dg.dg_mesh_check(m, np.ones(1, np.int8), np.ones(1), dg.Problem())
+    assert ei.value.code == -2
+    # a polygon with two vertices
+    m = mg.Mesh2D(np.array([0.0, 1.0]), np.array([0.0, 0.0]), np.array([0, 2], np.int32), np.array([0, 1], np.int32))
+    with pytest.raises(dg.DGError) as ei:
+        dg.dg_mesh_check(m, np.ones(1, np.int8), np.ones(1), dg.Problem())
+    assert ei.value.code == -2
+
+
+def test_precision_flags_match_header(lib):
+    # the precision flags of include/dg.h: FP64, FP32, split-BF16, 3xTF32
+    assert (dg.DG_PREC_FP64, dg.DG_PREC_FP32, dg.DG_PREC_BF16X3, dg.DG_PREC_TF32X3) == (0, 1, 2, 3)
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "dg.h")).read()
+    for name, val in (("DG_PREC_BF16X3", 2), ("DG_PREC_TF32X3", 3)):
+        assert f"#define {name} {val}" in hdr

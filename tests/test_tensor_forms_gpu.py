@@ -122,3 +122,19 @@ def test_diffusion_only_3d(ctx, prec):
     om, ob = oracle_blocks(wl)
     ed, eo, er = compare(dg.to_blocks(m, v, r), om, ob, wl)
     assert ed < TOL[prec] and eo < TOL[prec] and er < TOL_RHS, (ed, eo, er)
+
+
+@pytest.mark.parametrize("prec", FORMS)
+def test_learned_rules_in_tensor_forms(ctx, prec):
+    """Elements with an installed 28-point learned rule take the same
+    tensor-core contraction as the sub-triangle elements."""
+    wl = configs.small2d(300, 45, 3, 3, b=(1.0, 0.5), c=1.0)
+    m = dg.Mesh(ctx, wl.mesh, wl.p, wl.a, dg_problem(wl))
+    m.dg_quad_prepare()
+    st = m.dg_quad_fit(None, iters=8, install=True)
+    assert st["accepted"] > 0.8 * m.ne
+    _, v64, r64 = run_gpu(ctx, wl, dg.DG_PREC_FP64, m=m)
+    _, v, r = run_gpu(ctx, wl, prec, m=m)
+    fro = np.linalg.norm(v - v64) / np.linalg.norm(v64)
+    assert np.isfinite(v).all() and fro < FRO[prec], fro
+    assert np.linalg.norm(r - r64) / np.linalg.norm(r64) < FRO[prec]
