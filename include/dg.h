@@ -203,6 +203,23 @@ int dg_assemble_step(dg_ctx *ctx, dg_mesh *mesh, int prec, void *vals, void *rhs
 int dg_batch_upload(dg_ctx *ctx, const dg_mesh_desc *const *descs, int n, dg_mesh **out);
 int dg_batch_offsets(const dg_mesh *mesh, int *nmesh, int *elem_off, int64_t *val_off, int64_t *dof_off);
 
+/* How the row passes evaluate the volume terms of Eq. (2.4):
+ *   path 1 (default): the quadrature sums over each element's rule (the
+ *     sub-simplex rules of Sec. 3, or its learned rule) are accumulated as
+ *     weighted Legendre-product moments sum_q W_q P_c(xi_q) P_d(eta_q)
+ *     (P_e(zeta_q)), c + d (+ e) <= 2p, and every block entry is formed from
+ *     them through the exact Legendre linearisation of the basis products:
+ *     the same rule and points, the sums taken in another order.  Used for
+ *     degrees whose moments fit in registers (2D p >= 3 in FP32, p = 3, 4
+ *     in FP64; 3D p = 2, 3 in FP32, p = 2 in FP64) in the FP32 and FP64
+ *     forms; the diagonal block is then written by a separate moment
+ *     launch and the row kernel adds the face terms to it.
+ *   path 0: the per-point block contraction in the row kernels throughout.
+ * The tensor-core forms always take their own contraction.  Applies to
+ * later calls and recorded passes made after it; DG_ERR_ARG for another
+ * path. */
+int dg_set_volume_path(dg_ctx *ctx, int path);
+
 /* Partitions (Sec. 4.2: the elements are split across GPUs, each GPU builds
  * and assembles its own rows, faces on a cut are computed by both owners, and
  * assembly needs no communication).

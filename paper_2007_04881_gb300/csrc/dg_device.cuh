@@ -786,6 +786,8 @@ __global__ void __launch_bounds__(kWarps * 32)
 
   const bool mat_vol = mode & kModeVol, mat_face = mode & kModeFace, do_rhs = mode & kModeRhs;
   const bool accum = mode & kModeAccum;
+  // volume terms already written by the moment kernel: faces only, load vector added
+  const bool skip_vol = mode & kModeSkipVol;
   // with b = 0 and c = 0 the Phi row of a volume point carries no matrix term
   const bool no_adv = m.pb.b[0] == 0.0 && m.pb.b[1] == 0.0 && m.pb.b[2] == 0.0 && m.pb.c == 0.0;
   const int base = m.elem_pstart[P], count = m.elem_pstart[P + 1] - base;
@@ -855,7 +857,7 @@ __global__ void __launch_bounds__(kWarps * 32)
     const bool active = g_me < gcount;
 
     // ---- volume points
-    if (mat_vol || do_rhs) {
+    if ((mat_vol || do_rhs) && !skip_vol) {
       for (int ch = 0; ch < nvch; ++ch) {
         for (int idx = lane; idx < G * C; idx += 32) {
           const int g = idx / C, c = idx - g * C, qv = ch * C + c;
@@ -1075,7 +1077,7 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
         for (int a = 0; a < TM; ++a) {
           const int i = tr * TM + a;
-          if (i < N) out[i] = Re * ctab[i] * racc[a];
+          if (i < N) out[i] = skip_vol ? out[i] + Re * ctab[i] * racc[a] : Re * ctab[i] * racc[a];
         }
       }
     }

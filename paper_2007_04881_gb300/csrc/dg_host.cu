@@ -160,6 +160,7 @@ struct dg_ctx {
   DevBuf bufs;
   RuleTables rt[4];  // indexed by dim (2, 3)
   Tracer tracer;
+  bool vol_moments = true;  // volume blocks through Legendre-product moments
   std::vector<LaunchRec> recs;
   // forked streams for concurrent per-degree launches (created on first use)
   cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};
@@ -198,8 +199,8 @@ void Tracer::begin(const char* name, int kind, int p, size_t tsize, cudaStream_t
   if (!on || n >= cap) return;
   LaunchRec& r = recs[n];
   snprintf(r.name, sizeof r.name, "%s", name);
-  r.flops = (kind < 2 && flops) ? flops[kind * 9 + p] : 0.0;
-  r.bytes = (kind < 2 && words) ? words[kind * 9 + p] * (double)tsize : 0.0;
+  r.flops = (kind < kKinds && flops) ? flops[kind * 9 + p] : 0.0;
+  r.bytes = (kind < kKinds && words) ? words[kind * 9 + p] * (double)tsize : 0.0;
   record(r.ev0, st);
 }
 void Tracer::end(cudaStream_t st) {
@@ -233,7 +234,8 @@ struct dg_mesh {
   int h_prec = -1;
   double* X[3] = {nullptr, nullptr, nullptr};
   double* a = nullptr;
-  double flops[2][9] = {{0}}, words[2][9] = {{0}};
+  double flops[kKinds][9] = {{0}}, words[kKinds][9] = {{0}};
+  double mom_pt[9] = {0};
   std::vector<int> batch_elem_off;  // element offset of each batch member (empty: one mesh)
   // partition meshes: local -> global element and vertex ids, owned flags
   std::vector<int> part_elem, part_vert;
@@ -298,6 +300,58 @@ int build_rule_tables(dg_ctx* ctx) {
     rt.face64 = f64;
     rt.face32 = f32;
   }
+  // Legendre linearisation: P_a P_b, P'_a P_b, P'_a P'_b = sum_c coef P_c,
+  // coef = (2c + 1)/2 int_{-1}^{1} (product) P_c, by Gauss-Legendre with
+  // enough points for degree 4 kPMaxLin (exact)
+  {
+    constexpr int PL = kPMaxLin + 1, CL = 2 * kPMaxLin + 1;
+    std::vector<double> gx, gw;
+    gauss_legendre01(2 * kPMaxLin + 2, gx, gw);
+    const int ng = (int)gx.size();
+    std::vector<double> Pv((size_t)ng * (CL + 1)), dPv((size_t)ng * (CL + 1));
+    for (int g = 0; g < ng; ++g) {
+      const double t = 2.0 * gx[g] - 1.0;
+      double* P = &Pv[(size_t)g * (CL + 1)];
+      double* dP = &dPv[(size_t)g * (CL + 1)];
+      P[0] = 1.0;
+      dP[0] = 0.0;
+      P[1] = t;
+      dP[1] = 1.0;
+      for (int k = 1; k < CL; ++k) {
+        P[k + 1] = ((2 * k + 1) * t * P[k] - k * P[k - 1]) / (k + 1);
+        dP[k + 1] = dP[k - 1] + (2 * k + 1) * P[k];
+      }
+    }
+    std::vector<double> lin((size_t)3 * PL * PL * CL, 0.0);
+    for (int a = 0; a < PL; ++a)
+      for (int b = 0; b < PL; ++b)
+        for (int c = 0; c < CL; ++c) {
+          double s0 = 0, s1 = 0, s2 = 0;
+          for (int g = 0; g < ng; ++g) {
+            const double* P = &Pv[(size_t)g * (CL + 1)];
+            const double* dP = &dPv[(size_t)g * (CL + 1)];
+            const double w = 2.0 * gw[g] * P[c];
+            s0 += w * P[a] * P[b];
+            s1 += w * dP[a] * P[b];
+            s2 += w * dP[a] * dP[b];
+          }
+          const double nc = 0.5 * (2 * c + 1);
+          lin[(size_t)(a * PL + b) * CL + c] = nc * s0;
+          lin[(size_t)PL * PL * CL + (a * PL + b) * CL + c] = nc * s1;
+          lin[(size_t)2 * PL * PL * CL + (a * PL + b) * CL + c] = nc * s2;
+        }
+    double* l64;
+    float* l32;
+    DG_CUDA_TRY(ctx->bufs.alloc(&l64, lin.size()));
+    DG_CUDA_TRY(ctx->bufs.alloc(&l32, lin.size()));
+    std::vector<float> lf(lin.begin(), lin.end());
+    DG_CUDA_TRY(cudaMemcpy(l64, lin.data(), lin.size() * 8, cudaMemcpyHostToDevice));
+    DG_CUDA_TRY(cudaMemcpy(l32, lf.data(), lf.size() * 4, cudaMemcpyHostToDevice));
+    for (int dim = 2; dim <= 3; ++dim) {
+      ctx->rt[dim].lin64 = l64;
+      ctx->rt[dim].lin32 = l32;
+    }
+  }
   return DG_OK;
 }
 
@@ -347,7 +401,8 @@ struct Plan {
   int64_t nqvol = 0, nqface = 0;
   // algorithmic flops / words per launch group [kind][p] (kind 0: row
   // kernel of degree p, whole block rows and load vector)
-  double flops[2][9] = {{0}}, words[2][9] = {{0}};
+  double flops[kKinds][9] = {{0}}, words[kKinds][9] = {{0}};
+  double mom_pt[9] = {0};  // moment kernel operations per volume point, by degree
 };
 
 extern "C" {
@@ -753,6 +808,52 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P, const int8_t* owned = nullp
         P.words[0][d->p[e]] += w;
       }
     }
+    // The moment form of the volume terms (kind 2) and the row kernel's
+    // faces-only launch beside it (kind 1 = kind 0 without the volume
+    // terms).  Moment kernel, FMA-equivalent operations: per volume point
+    // 2 d (2p - 1) for the Legendre values to degree 2p, 2p + 1 weighted
+    // values, one update per moment (c + d (+ e) <= 2p; in 3D also the
+    // (2p+1)(2p+2)/2 partial products) and n d for the load vector; per
+    // element 3 per moment combination of every block entry (in 3D also 3
+    // per (c, d) pair) and 3 d per exponent pair and degree for the
+    // coefficient tables.
+    double map_ops[9] = {0}, pt_ops[9] = {0};
+    for (int pp = 1; pp <= 8; ++pp) {
+      const int q = 2 * pp, nn = nbasis(dim, pp);
+      const double nmom = dim == 2 ? (q + 1) * (q + 2) / 2.0 : (q + 1) * (q + 2) * (q + 3) / 6.0;
+      pt_ops[pp] = 2.0 * dim * (q - 1) + (q + 1) + nmom + (dim == 3 ? (q + 1) * (q + 2) / 2.0 : 0.0) + nn * dim;
+      std::vector<std::array<int, 3>> al;
+      for (int k = 0; k <= pp; ++k)
+        for (int l = 0; l <= (dim == 3 ? k : 0); ++l)
+          for (int j = 0; j <= k - l; ++j) al.push_back({k - j - l, j, l});
+      double ops = 3.0 * dim * (pp + 1) * (pp + 1) * (q + 1);
+      for (const auto& a : al)
+        for (const auto& b : al) {
+          const double cx = a[0] + b[0] + 1, cy = a[1] + b[1] + 1, cz = dim == 3 ? a[2] + b[2] + 1 : 1;
+          ops += dim == 2 ? 3.0 * cx * cy : 3.0 * cx * cy * cz + 3.0 * cx * cy;
+        }
+      map_ops[pp] = ops;
+    }
+    for (int e = 0; e < ne; ++e) {
+      if (!own(e)) continue;
+      const int pe = d->p[e];
+      const double n = nb[e];
+      int qt = 1;
+      for (int q = 0; q < dim; ++q) qt *= pe + 2;
+      const double nvq = (double)(d->elem_ptr[e + 1] - d->elem_ptr[e]) * qt;
+      const double vol_direct = nvq * (dim * n * (n + 1) / 2 + (adv ? n * n + n * (dim + 1) : 0.0) +
+                                       n * dim * dim + 5.0 * dim * pe + n);
+      const double vol_words = n * n + n + (double)(d->elem_ptr[e + 1] - d->elem_ptr[e]) * SV + 2 * dim + 2;
+      P.flops[1][pe] -= 2.0 * vol_direct;
+      P.words[1][pe] -= vol_words;
+      P.flops[2][pe] += 2.0 * (nvq * pt_ops[pe] + map_ops[pe]);
+      P.words[2][pe] += vol_words;
+    }
+    for (int pp = 0; pp <= 8; ++pp) {
+      P.flops[1][pp] += P.flops[0][pp];
+      P.words[1][pp] += P.words[0][pp];
+      P.mom_pt[pp] = pt_ops[pp];
+    }
   }
   P.nsub = nsub;
   P.nf = nf;
@@ -809,6 +910,7 @@ static int upload_impl(dg_ctx* ctx, const dg_mesh_desc* d, const int8_t* owned, 
   m->col = P.col;
   std::memcpy(m->flops, P.flops, sizeof P.flops);
   std::memcpy(m->words, P.words, sizeof P.words);
+  std::memcpy(m->mom_pt, P.mom_pt, sizeof P.mom_pt);
   m->blk_off = P.blk_off;
   m->dof_off = P.dof_off;
   DevMesh& dm = m->dm;
@@ -1013,6 +1115,7 @@ static int run_assembly(dg_ctx* ctx, const dg_mesh* mesh, int prec, int mode, vo
   (void)iface;
   LaunchOpts lo;
   lo.occ_cap = occ_cap;
+  lo.vol_moments = ctx->vol_moments;
   for (int p = 0; p < 9; ++p) lo.pst[p] = st;
   if (concurrent) {
     if (!ctx->fork) {
@@ -1652,8 +1755,10 @@ int dg_quad_fit(dg_ctx* ctx, dg_mesh* mesh, const float* init, int iters, int in
       mesh->dm.lq32 = mesh->lq32;
       // algorithmic volume work of learned elements: 28 points instead of the sub-triangle rule
       for (int e = 0; e < ne; ++e)
-        if (ok[e] && (mesh->owned_h.empty() || mesh->owned_h[e]))
+        if (ok[e] && (mesh->owned_h.empty() || mesh->owned_h[e])) {
           mesh->flops[0][mesh->p_h[e]] -= 2.0 * (mesh->nvq_h[e] - 28) * mesh->vfma_h[e];
+          mesh->flops[2][mesh->p_h[e]] -= 2.0 * (mesh->nvq_h[e] - 28) * mesh->mom_pt[mesh->p_h[e]];
+        }
     }
   }
   return DG_OK;
@@ -1673,8 +1778,10 @@ int dg_quad_clear(dg_ctx* ctx, dg_mesh* mesh) {
     std::vector<int> okd(mesh->dm.ne);
     DG_CUDA_TRY(cudaMemcpy(okd.data(), mesh->lq_okm, sizeof(int) * mesh->dm.ne, cudaMemcpyDeviceToHost));
     for (int e = 0; e < mesh->dm.ne; ++e)
-      if (okd[e] && (mesh->owned_h.empty() || mesh->owned_h[e]))
+      if (okd[e] && (mesh->owned_h.empty() || mesh->owned_h[e])) {
         mesh->flops[0][mesh->p_h[e]] += 2.0 * (mesh->nvq_h[e] - 28) * mesh->vfma_h[e];
+        mesh->flops[2][mesh->p_h[e]] += 2.0 * (mesh->nvq_h[e] - 28) * mesh->mom_pt[mesh->p_h[e]];
+      }
     int rc = rebuild_worklist(ctx, mesh, ok);
     if (rc != DG_OK) return rc;
   }
@@ -1738,6 +1845,12 @@ int dg_kernel_stats(dg_ctx* ctx, dg_kernel_stat* out, int cap) {
     return n + 1;
   }
   return n;
+}
+
+int dg_set_volume_path(dg_ctx* ctx, int path) {
+  if (!ctx || (path != 0 && path != 1)) return fail(DG_ERR_ARG, "dg_set_volume_path: bad argument");
+  ctx->vol_moments = path == 1;
+  return DG_OK;
 }
 
 int dg_sync(dg_ctx* ctx) {

@@ -11,6 +11,7 @@ namespace dg {
 
 constexpr int kPMax2 = 6;  // highest degree with compiled kernels in 2D
 constexpr int kPMax3 = 4;  // ... in 3D
+constexpr int kPMaxLin = 6;  // Legendre linearisation tables: degrees 0..6, products to 12
 constexpr int kWarps = 4;  // warps per CTA of the element / interface kernels
 
 // values per sub-simplex in bounding-box coordinates xi = 2(x-lo)/L - 1:
@@ -42,6 +43,10 @@ struct RuleTables {
   const float* face32 = nullptr;
   int face_off[10] = {0};  // offset (in points) of the n-point rule
   int face_n[10] = {0};    // points of the n-point rule
+  // Legendre linearisation coefficients [3][kPMaxLin+1][kPMaxLin+1][2 kPMaxLin+1]:
+  // P_a P_b, P'_a P_b and P'_a P'_b expanded in P_c
+  const double* lin64 = nullptr;
+  const float* lin32 = nullptr;
 };
 
 // Problem data (constant over the mesh).
@@ -131,6 +136,7 @@ enum : int {
   kModeFace = 2,   // own-face integrals into the diagonal block
   kModeRhs = 4,    // load vector
   kModeAccum = 8,  // add to the diagonal block instead of overwriting it
+  kModeSkipVol = 16,  // volume terms done by the moment kernel: faces only, load vector added
 };
 
 // Optional per-launch timing: CUDA events recorded on the launch stream
@@ -143,15 +149,18 @@ struct LaunchRec {
   cudaEvent_t ev0, ev1;
 };
 
+constexpr int kKinds = 3;
 struct Tracer {
   bool on = false;
   LaunchRec* recs = nullptr;  // capacity cap, filled from n
   int cap = 0;
   int n = 0;
   // per launch-group algorithmic counts, indexed [kind][p]; kind 0 = row
-  // kernel of degree p; words = values written + read, scaled by sizeof(T)
-  const double* flops = nullptr;  // [2][9]
-  const double* words = nullptr;  // [2][9]
+  // kernel of degree p (volume and faces), 1 = its faces-only launch next to
+  // the moment kernel, 2 = the moment volume kernel; words = values written +
+  // read, scaled by sizeof(T)
+  const double* flops = nullptr;  // [kKinds][9]
+  const double* words = nullptr;  // [kKinds][9]
   void begin(const char* name, int kind, int p, size_t tsize, cudaStream_t st);
   void end(cudaStream_t st);
   static void record(cudaEvent_t ev, cudaStream_t st);
@@ -166,6 +175,7 @@ int launch_geometry(const DevMesh& m, cudaStream_t st, Tracer* tr = nullptr, int
 // occupancy limit) and the stream of each degree's launch (index p).
 struct LaunchOpts {
   int occ_cap = 0;
+  bool vol_moments = true;  // volume blocks through Legendre-product moments where supported
   cudaStream_t pst[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 

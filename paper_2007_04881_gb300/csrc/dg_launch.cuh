@@ -6,6 +6,7 @@
 #include <cstdio>
 
 #include "dg_device.cuh"
+#include "dg_moment.cuh"
 
 namespace dg {
 
@@ -25,10 +26,33 @@ inline int launch_row_p(const DevMesh& m, int mode, T* vals, T* rhs, int sm_coun
   const int count = m.elem_pstart[P + 1] - m.elem_pstart[P];
   if (count <= 0) return 0;
   cudaStream_t st = lo.pst[P];
+  const char* tn = sizeof(T) == 8 ? "f64" : "f32";
+  int n = 0, kind = 0;
+  if constexpr (TileCfg<D, P, T>::TPE != 1 && moment_volume_ok<D, P, T>()) {
+    if (lo.vol_moments && (mode & (kModeVol | kModeRhs))) {
+      // volume terms through the moments, then the faces added by the row kernel
+      using MC = MomCfg<D, P, T>;
+      static_assert(MC::total <= 227 * 1024, "moment kernel shared memory exceeds 227 KB");
+      if (tr && tr->on) {
+        char name[48];
+        snprintf(name, sizeof name, "row%dd_vol_p%d_%s", D, P, tn);
+        tr->begin(name, 2, P, sizeof(T), st);
+      }
+      auto k = vol_moment_kernel<D, P, T>;
+      const int ngroups = (count + MC::G - 1) / MC::G;
+      const int grid = resident_grid(k, MC::total, sm_count, (ngroups + kWarps - 1) / kWarps, lo.occ_cap);
+      k<<<grid, kWarps * 32, MC::total, st>>>(m, mode & (kModeVol | kModeRhs | kModeAccum), vals, rhs);
+      if (tr && tr->on) tr->end(st);
+      ++n;
+      if (!(mode & (kModeFace | kModeRhs))) return n;
+      mode = (mode & ~kModeVol) | kModeSkipVol | ((mode & kModeVol) ? kModeAccum : 0);
+      kind = 1;
+    }
+  }
   if (tr && tr->on) {
     char name[48];
-    snprintf(name, sizeof name, "row%dd_p%d_%s", D, P, sizeof(T) == 8 ? "f64" : "f32");
-    tr->begin(name, 0, P, sizeof(T), st);
+    snprintf(name, sizeof name, "row%dd_p%d_%s", D, P, tn);
+    tr->begin(name, kind, P, sizeof(T), st);
   }
   if constexpr (TileCfg<D, P, T>::TPE == 1) {
     // one element per thread, no staging
@@ -47,7 +71,7 @@ inline int launch_row_p(const DevMesh& m, int mode, T* vals, T* rhs, int sm_coun
     k<<<grid, kWarps * 32, smem, st>>>(m, mode, vals, rhs);
   }
   if (tr && tr->on) tr->end(st);
-  return 1;
+  return n + 1;
 }
 
 }  // namespace dg

@@ -1,0 +1,289 @@
+// dg_moment.cuh -- volume blocks through Legendre-product moments.
+//
+// The volume part of Eq. (2.4) for an element with constant a, b, c is a
+// sum over the element's quadrature points (the sub-simplex rules of Sec. 3,
+// or a learned rule) of products of two basis functions or their
+// derivatives.  With the bounding-box basis phi_i = s_i P_a(xi) P_b(eta)
+// (P_c(zeta)), every such product is a product, per coordinate, of two
+// Legendre polynomials or their derivatives, and each of those is a short
+// exact combination of Legendre polynomials (linearisation):
+//   P_a P_a' = sum_c G(a, a', c) P_c,  P'_a P_a' = sum_c G1(a, a', c) P_c,
+//   P'_a P'_a' = sum_c G2(a, a', c) P_c.
+// So the quadrature sum factors through the weighted moments
+//   mu_{c d (e)} = sum_q W_q P_c(xi_q) P_d(eta_q) (P_e(zeta_q)),  c + d (+ e) <= 2p,
+// (the same rule, the same points, the same weights, added in another
+// order), and each block entry is a fixed combination of moments:
+//   2D: A_ij = sum_{c,d} mu_cd [Y0(d) Xa(c) + X0(c) Yb(d)],
+//   3D: A_ij = sum_{c,d,e} mu_cde [Z0(e) (Y0(d) Xa(c) + X0(c) Yb(d)) + X0(c) Y0(d) Zs(e)],
+// X0 = G(ai, aj), Xa = c G(ai, aj) + b'_1 G1(aj, ai) + a'_1 G2(ai, aj),
+// Yb = b'_2 G1(bj, bi) + a'_2 G2(bi, bj), Zs = b'_3 G1(cj, ci) + a'_3 G2(ci, cj),
+// with the trial function j carrying the advection derivative.  Per point
+// this costs the moments (45 for 2D p = 4) instead of the 3 n^2 block
+// updates; per element, the combination above.  The load vector's volume
+// term (non-polynomial f) is accumulated per point as before.
+//
+// Layout: LPE lanes per element.  Each lane accumulates the moments and the
+// load vector of every LPE-th point in registers; a butterfly reduction over
+// the lanes gives the sums (a fixed order, no atomics).  The lanes then write
+// the element's diagonal block (overwritten, or added with kModeAccum) and
+// the volume part of its load vector; the row kernel adds the face terms.
+#pragma once
+
+#include "dg_device.cuh"
+
+namespace dg {
+
+// moments c + d (+ e) <= 2p, in total-degree order
+template <int D>
+__host__ __device__ constexpr int nmom(int q) {
+  return D == 2 ? (q + 1) * (q + 2) / 2 : (q + 1) * (q + 2) * (q + 3) / 6;
+}
+// index of moment (c, d) / (c, d, e): s = total degree, t = d + e
+__device__ __forceinline__ int mom2(int c, int d) {
+  const int s = c + d;
+  return s * (s + 1) / 2 + d;
+}
+__device__ __forceinline__ int mom3(int c, int d, int e) {
+  const int s = c + d + e, t = d + e;
+  return s * (s + 1) * (s + 2) / 6 + t * (t + 1) / 2 + e;
+}
+
+template <int D, int P, typename T>
+struct MomCfg {
+  static constexpr int N = nbasis(D, P);
+  static constexpr int Q = 2 * P;
+  static constexpr int NM = nmom<D>(Q);
+  static constexpr int LPE = D == 2 ? (P <= 2 ? 8 : 16) : 32;  // lanes per element
+  static constexpr int G = 32 / LPE;                             // elements per warp
+  static constexpr int QT = ipow_c(P + 2, D);
+  static constexpr int PL = kPMaxLin + 1;   // table stride: degrees 0..kPMaxLin
+  static constexpr int CL = 2 * kPMaxLin + 1;
+  static constexpr int NLIN = 3 * PL * PL * CL;  // G, G1, G2
+  static constexpr int NPAIR = (P + 1) * (P + 1);
+  // per element: moments, and Xa, Yb (and Zs) for every exponent pair
+  static constexpr int PER_ELEM = NM + D * NPAIR * (Q + 1);
+  static constexpr int NMAXC = nbasis(D, D == 2 ? kPMax2 : kPMax3);
+  static constexpr size_t head_elems = NLIN + QT * (D + 1) + NMAXC;
+  static constexpr size_t total = align_up(sizeof(T) * (head_elems + (size_t)kWarps * G * PER_ELEM), 16);
+};
+
+// whether the moment path serves (D, P, T): moments held in registers
+template <int D, int P, typename T>
+__host__ __device__ constexpr bool moment_volume_ok() {
+  return P >= 2 && P <= kPMaxLin && nmom<D>(2 * P) <= (sizeof(T) == 4 ? 96 : 56);
+}
+
+template <int D, int P, typename T>
+__global__ void __launch_bounds__(kWarps * 32)
+    vol_moment_kernel(const DevMesh m, int mode, T* __restrict__ vals, T* __restrict__ rhs) {
+  using Cfg = MomCfg<D, P, T>;
+  constexpr int N = Cfg::N, Q = Cfg::Q, NM = Cfg::NM, LPE = Cfg::LPE, G = Cfg::G, QT = Cfg::QT;
+  constexpr int PL = Cfg::PL, CL = Cfg::CL, NLIN = Cfg::NLIN, NPAIR = Cfg::NPAIR;
+  constexpr int SV = sub_vals(D);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* lin = reinterpret_cast<T*>(smem_raw);  // [3][PL][PL][CL]
+  T* rule = lin + NLIN;
+  T* ctab = rule + QT * (D + 1);
+  T* pe = reinterpret_cast<T*>(smem_raw) + Cfg::head_elems;  // per element scratch
+  const T* glin = pick<T>(m.rt.lin64, m.rt.lin32);
+  for (int i = threadIdx.x; i < NLIN; i += blockDim.x) lin[i] = glin[i];
+  const T* vrule = pick<T>(m.rt.vol64, m.rt.vol32) + (size_t)m.rt.vol_off[P] * (D + 1);
+  for (int i = threadIdx.x; i < QT * (D + 1); i += blockDim.x) rule[i] = vrule[i];
+  fill_ctab<D, T>(ctab, Cfg::NMAXC);
+  __syncthreads();
+  auto L0 = [&](int a, int b, int c) { return lin[(a * PL + b) * CL + c]; };
+  auto L1 = [&](int a, int b, int c) { return lin[PL * PL * CL + (a * PL + b) * CL + c]; };
+  auto L2 = [&](int a, int b, int c) { return lin[2 * PL * PL * CL + (a * PL + b) * CL + c]; };
+
+  const T* SG = pick<T>(m.sg64, m.sg32);
+  const bool mat_vol = mode & kModeVol, do_rhs = mode & kModeRhs, accum = mode & kModeAccum;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / LPE, lig = lane % LPE;
+  T* my = pe + (size_t)(warp * G + grp) * Cfg::PER_ELEM;  // this element's scratch
+  T* smu = my;
+  T* sXa = my + NM;                // [NPAIR][Q+1] per exponent pair (a, a') of dimension 0
+  T* sYb = sXa + NPAIR * (Q + 1);  // dimension 1
+  T* sZs = sYb + NPAIR * (Q + 1);  // dimension 2 (3D)
+  const int base = m.elem_pstart[P], count = m.elem_pstart[P + 1] - base;
+  const int ngroups = (count + G - 1) / G;
+
+  for (int tile = blockIdx.x * kWarps + warp; tile < ngroups; tile += gridDim.x * kWarps) {
+    const int slot = tile * G + grp;
+    const bool active = slot < count;
+    const int e = active ? m.elem_perm[base + slot] : 0;
+    ElemPar<D, T> q;
+    if (active) load_elem_par<D, T>(m, e, q);
+    const bool lrn = active && m.lq_ok && m.lq_ok[e];
+    const int npts = !active ? 0 : lrn ? 28 : (m.eptr[e + 1] - m.eptr[e]) * QT;
+
+    // ---- moments and the load vector's volume term, LPE lanes per element
+    T mu[NM], racc[N];
+#pragma unroll
+    for (int k = 0; k < NM; ++k) mu[k] = T(0);
+#pragma unroll
+    for (int i = 0; i < N; ++i) racc[i] = T(0);
+    for (int qv = lig; qv < npts; qv += LPE) {
+      T xi[D], W;
+      if (D == 2 && lrn) {
+        const T* LQ = pick<T>(m.lq64, m.lq32) + (size_t)e * 84;
+        xi[0] = LQ[qv];
+        xi[1 % D] = LQ[28 + qv];
+        W = LQ[56 + qv];
+      } else {
+        const int t = qv / QT, r = qv - t * QT;
+        const int sub = m.eptr[e] + t;
+        T sv[SV];
+#pragma unroll
+        for (int k = 0; k < SV; ++k) sv[k] = SG[(size_t)k * m.nsub + sub];
+        const T* rr = rule + r * (D + 1);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          T v = sv[d] + rr[0] * sv[D + d] + rr[1] * sv[2 * D + d];
+          if constexpr (D == 3) v += rr[2] * sv[3 * D + d];
+          xi[d] = v;
+        }
+        W = rr[D] * sv[SV - 1];
+      }
+      T Lv[3][Q + 1];
+#pragma unroll
+      for (int d = 0; d < D; ++d) {
+        Lv[d][0] = T(1);
+        Lv[d][1] = xi[d];
+#pragma unroll
+        for (int k = 1; k < Q; ++k)
+          Lv[d][k + 1] = (T(2 * k + 1) / T(k + 1)) * xi[d] * Lv[d][k] - (T(k) / T(k + 1)) * Lv[d][k - 1];
+      }
+      if (mat_vol) {
+        if constexpr (D == 2) {
+#pragma unroll
+          for (int c = 0; c <= Q; ++c) {
+            const T wc = W * Lv[0][c];
+#pragma unroll
+            for (int d = 0; c + d <= Q; ++d) {
+              const int s = c + d;
+              mu[s * (s + 1) / 2 + d] = fma(wc, Lv[1][d], mu[s * (s + 1) / 2 + d]);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c <= Q; ++c) {
+            const T wc = W * Lv[0][c];
+#pragma unroll
+            for (int d = 0; c + d <= Q; ++d) {
+              const T wcd = wc * Lv[1][d];
+#pragma unroll
+              for (int ee = 0; c + d + ee <= Q; ++ee) {
+                const int s = c + d + ee, t = d + ee;
+                const int k = s * (s + 1) * (s + 2) / 6 + t * (t + 1) / 2 + ee;
+                mu[k] = fma(wcd, Lv[2][ee], mu[k]);
+              }
+            }
+          }
+        }
+      }
+      if (do_rhs) {
+        T x[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) x[d] = q.lo[d] + (xi[d] + T(1)) * T(0.5) * q.L[d];
+        const T wf = W * source_f<D, T>(m.pb, q.a, x);
+        int i = 0;
+#pragma unroll
+        for (int k = 0; k <= P; ++k) {
+          if constexpr (D == 2) {
+#pragma unroll
+            for (int j = 0; j <= k; ++j) {
+              racc[i] = fma(wf, Lv[0][k - j] * Lv[1][j], racc[i]);
+              ++i;
+            }
+          } else {
+#pragma unroll
+            for (int l = 0; l <= k; ++l)
+#pragma unroll
+              for (int j = 0; j <= k - l; ++j) {
+                racc[i] = fma(wf, Lv[0][k - j - l] * Lv[1][j] * Lv[2][l], racc[i]);
+                ++i;
+              }
+          }
+        }
+      }
+    }
+    // butterfly sums over the element's lanes (fixed order)
+#pragma unroll
+    for (int off = LPE / 2; off > 0; off >>= 1) {
+      if (mat_vol) {
+#pragma unroll
+        for (int k = 0; k < NM; ++k) mu[k] += __shfl_xor_sync(0xffffffffu, mu[k], off);
+      }
+      if (do_rhs) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) racc[i] += __shfl_xor_sync(0xffffffffu, racc[i], off);
+      }
+    }
+
+    // ---- load vector (volume term): overwritten
+    if (active && do_rhs) {
+      T* out = rhs + m.dof_off[e];
+#pragma unroll
+      for (int i = 0; i < N; ++i)
+        if (i % LPE == lig) out[i] = q.R * ctab[i] * racc[i];
+    }
+
+    // ---- diagonal block from the moments
+    if (mat_vol) {
+      __syncwarp();
+      if (active) {
+#pragma unroll
+        for (int k = 0; k < NM; ++k)
+          if (k % LPE == lig) smu[k] = mu[k];
+        // per exponent pair (a, a'): the element's coefficient combinations
+        for (int k = lig; k < NPAIR * (Q + 1); k += LPE) {
+          const int pr = k / (Q + 1), c = k - pr * (Q + 1);
+          const int a = pr / (P + 1), ap = pr - a * (P + 1);
+          sXa[k] = q.c * L0(a, ap, c) + q.bp[0] * L1(ap, a, c) + q.ap[0] * L2(a, ap, c);
+          sYb[k] = q.bp[1 % D] * L1(ap, a, c) + q.ap[1 % D] * L2(a, ap, c);
+          if constexpr (D == 3) sZs[k] = q.bp[2 % D] * L1(ap, a, c) + q.ap[2 % D] * L2(a, ap, c);
+        }
+      }
+      __syncwarp();
+      if (active) {
+        T* out = vals + m.blk_off[m.diag_blk[e]];
+        const T RR = q.R * q.R;
+        for (int ent = lig; ent < N * N; ent += LPE) {
+          const int i = ent / N, j = ent - (ent / N) * N;
+          int ai[3], aj[3];
+          basis_alpha<D>(i, ai);
+          basis_alpha<D>(j, aj);
+          T acc = T(0);
+          const int px = ai[0] * (P + 1) + aj[0], py = ai[1] * (P + 1) + aj[1];
+          const int cmax = ai[0] + aj[0], dmax = ai[1] + aj[1];
+          if constexpr (D == 2) {
+            for (int c = 0; c <= cmax; ++c) {
+              const T x0 = L0(ai[0], aj[0], c), xa = sXa[px * (Q + 1) + c];
+              for (int d = 0; d <= dmax; ++d) {
+                const T coef = L0(ai[1], aj[1], d) * xa + x0 * sYb[py * (Q + 1) + d];
+                acc = fma(smu[mom2(c, d)], coef, acc);
+              }
+            }
+          } else {
+            const int pz = ai[2] * (P + 1) + aj[2], emax = ai[2] + aj[2];
+            for (int c = 0; c <= cmax; ++c) {
+              const T x0 = L0(ai[0], aj[0], c), xa = sXa[px * (Q + 1) + c];
+              for (int d = 0; d <= dmax; ++d) {
+                const T y0 = L0(ai[1], aj[1], d);
+                const T k1 = y0 * xa + x0 * sYb[py * (Q + 1) + d], k2 = x0 * y0;
+                T s = T(0);
+                for (int ee = 0; ee <= emax; ++ee)
+                  s = fma(smu[mom3(c, d, ee)], L0(ai[2], aj[2], ee) * k1 + sZs[pz * (Q + 1) + ee] * k2, s);
+                acc += s;
+              }
+            }
+          }
+          const T v = RR * ctab[i] * ctab[j] * acc;
+          out[i * N + j] = accum ? out[i * N + j] + v : v;
+        }
+      }
+    }
+  }
+}
+
+}  // namespace dg

@@ -137,6 +137,7 @@ def load() -> C.CDLL:
     lib.dg_mlp_forward.argtypes = [V, V, V, C.c_int, V]
     lib.dg_mlp_grad.argtypes = [V, V, V, V, C.c_int, V, V]
     lib.dg_mlp_train_step.argtypes = [V, V, V, V, C.c_int, C.c_float, V]
+    lib.dg_set_volume_path.argtypes = [V, C.c_int]
     lib.dg_partition.argtypes = [C.POINTER(dg_mesh_desc), C.c_int, V]
     lib.dg_mesh_upload_part.argtypes = [V, C.POINTER(dg_mesh_desc), V, C.c_int, C.POINTER(V)]
     lib.dg_part_map.argtypes = [V, V, V, V, V, V]
@@ -158,7 +159,7 @@ EXPORTS = (
     "dg_quad_prepare", "dg_quad_fit", "dg_quad_targets", "dg_quad_buffers", "dg_quad_clear",
     "dg_mlp_create", "dg_mlp_free", "dg_mlp_num_params", "dg_mlp_get_params", "dg_mlp_set_params",
     "dg_mlp_get_state", "dg_mlp_set_state", "dg_mlp_forward", "dg_mlp_grad", "dg_mlp_train_step",
-    "dg_partition", "dg_mesh_upload_part", "dg_part_map", "dg_part_check",
+    "dg_partition", "dg_mesh_upload_part", "dg_part_map", "dg_part_check", "dg_set_volume_path",
 )
 
 
@@ -216,6 +217,10 @@ class Context:
 
     def dg_sync(self):
         _check(load().dg_sync(self._h))
+
+    def dg_set_volume_path(self, path: int):
+        """1: volume blocks through Legendre-product moments (default); 0: per-point contraction."""
+        _check(load().dg_set_volume_path(self._h, int(path)))
 
     def launches(self) -> int:
         return load().dg_last_launch_count(self._h)

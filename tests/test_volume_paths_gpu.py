@@ -1,0 +1,91 @@
+"""Both ways of forming the volume blocks, against the FP64 oracle: the
+per-point contraction in the row kernels (path 0) and the Legendre-product
+moments (path 1, the default), in FP64 and FP32, with every degree, with
+learned rules, and through the separate volume / faces / load-vector calls.
+The moment path adds the same quadrature terms in another order, so the
+tolerances are those of the other parity tests."""
+import numpy as np
+import pytest
+
+from paper_2007_04881_gb300 import configs, dg
+
+from .helpers import compare, dg_problem, oracle_blocks
+
+pytestmark = pytest.mark.gpu
+
+TOL = {dg.DG_PREC_FP64: 1e-12, dg.DG_PREC_FP32: 5e-5}
+TOL_RHS = {dg.DG_PREC_FP64: 1e-12, dg.DG_PREC_FP32: 1e-4}
+
+
+@pytest.fixture(scope="module")
+def ctx(cuda):
+    import torch
+
+    from paper_2007_04881_gb300 import build as B
+
+    B.build()
+    c = dg.Context(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    c.dg_set_volume_path(1)
+    c.close()
+
+
+def run(ctx, wl, prec, path, how="fused", m=None):
+    import torch
+
+    ctx.dg_set_volume_path(path)
+    m = m or dg.Mesh(ctx, wl.mesh, wl.p, wl.a, dg_problem(wl))
+    dt = torch.float64 if prec == dg.DG_PREC_FP64 else torch.float32
+    v = torch.full((m.nvals,), float("nan"), dtype=dt, device="cuda")
+    r = torch.full((m.ndofs,), float("nan"), dtype=dt, device="cuda")
+    if how == "split":
+        m.dg_assemble_volume(prec, v)
+        m.dg_assemble_faces(prec, v)
+        m.dg_assemble_rhs(prec, r)
+    else:
+        m.dg_assemble(prec, v, r)
+    ctx.dg_sync()
+    ctx.dg_set_volume_path(1)
+    return m, v.double().cpu().numpy(), r.double().cpu().numpy()
+
+
+@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("prec", [dg.DG_PREC_FP64, dg.DG_PREC_FP32])
+@pytest.mark.parametrize("which", ["2d", "3d"])
+def test_paths_against_oracle(ctx, path, prec, which):
+    wl = configs.small2d(180, 7, 1, 6) if which == "2d" else configs.small3d(4, 10, 5, 1, 4)
+    m, v, r = run(ctx, wl, prec, path)
+    assert np.isfinite(v).all() and np.isfinite(r).all()
+    om, ob = oracle_blocks(wl)
+    ed, eo, er = compare(dg.to_blocks(m, v, r), om, ob, wl)
+    assert ed < TOL[prec] and eo < TOL[prec] and er < TOL_RHS[prec], (ed, eo, er)
+
+
+@pytest.mark.parametrize("prec", [dg.DG_PREC_FP64, dg.DG_PREC_FP32])
+def test_moment_path_split_calls(ctx, prec):
+    """volume (moments) then faces (row kernel adds to the diagonal), and the
+    load vector alone, equal the fused pass within the parity tolerance"""
+    wl = configs.small2d(220, 17, 2, 5, b=(1.0, 0.5), c=1.0)
+    m, v1, r1 = run(ctx, wl, prec, 1)
+    _, v2, r2 = run(ctx, wl, prec, 1, how="split", m=m)
+    assert np.abs(v1 - v2).max() <= TOL[prec] * np.abs(v1).max()
+    assert np.abs(r1 - r2).max() <= TOL[prec] * np.abs(r1).max()
+    _, v3, r3 = run(ctx, wl, prec, 1, m=m)
+    assert np.array_equal(v1, v3) and np.array_equal(r1, r3)  # deterministic
+
+
+def test_moment_path_with_learned_rules(ctx):
+    wl = configs.small2d(300, 45, 3, 3, b=(1.0, 0.5), c=1.0)
+    m = dg.Mesh(ctx, wl.mesh, wl.p, wl.a, dg_problem(wl))
+    m.dg_quad_prepare()
+    st = m.dg_quad_fit(None, iters=8, install=True)
+    assert st["accepted"] > 0.8 * m.ne
+    _, v0, r0 = run(ctx, wl, dg.DG_PREC_FP64, 0, m=m)
+    _, v1, r1 = run(ctx, wl, dg.DG_PREC_FP64, 1, m=m)
+    assert np.abs(v1 - v0).max() <= 1e-12 * np.abs(v0).max()
+    assert np.abs(r1 - r0).max() <= 1e-12 * np.abs(r0).max()
+
+
+def test_bad_path_rejected(ctx):
+    with pytest.raises(dg.DGError):
+        ctx.dg_set_volume_path(2)
