@@ -214,6 +214,7 @@ extern "C" int dg_volume_noalloc(void* stream, int device, int prec, int p, int 
       reinterpret_cast<int*>(b + o_hf), reinterpret_cast<int*>(b + o_p), reinterpret_cast<int*>(b + o_sub));
   launch_geometry(m, st, nullptr, prec == DG_PREC_FP64 ? 1 : 2);
   LaunchOpts lo;
+  lo.vol_moments = false;  // the per-point contraction: needs no linearisation tables
   for (int q = 0; q < 9; ++q) lo.pst[q] = st;
   if (prec == DG_PREC_FP64)
     launch_row2d_f64(m, kModeVol, static_cast<double*>(blocks), nullptr, nd->sm_count, lo, nullptr);
