@@ -338,12 +338,20 @@ int dg_mlp_train_step(dg_ctx *ctx, dg_mlp *net, const void *x_bf16, const float 
  * per quadrature point, element of n dofs in dimension d: volume
  * d n(n+1)/2 + [b or c != 0](n^2 + n(d+1)) + basis (n d^2 + 5 d p) + n (load);
  * own interior-face point 3 n^2 + [b != 0] n^2/2 + basis; boundary-face
- * point 3 n^2 + [b != 0] n^2 + basis + 2n (load); interface-kernel face point
- * 6 n0 n1 + [b != 0] n0 n1.  Bytes: values written once plus geometry
- * records read once, in the precision's element size.  When the call issued
- * row kernels, one more record named "row_pass" follows: the span from the
- * first row-kernel start to the last row-kernel end (degree groups may run
- * concurrently) with their summed flops and bytes. */
+ * point 3 n^2 + [b != 0] n^2 + basis + 2n (load); off-diagonal block, per
+ * interface point 3 n_e n_k + [b != 0] n_e n_k / 2.  Bytes: values written
+ * once plus geometry records read once, in the precision's element size.
+ * With the moment path (dg_set_volume_path), a degree group is two launches
+ * ("row2d_vol_p<p>_<t>" for the volume terms, then the faces); the volume
+ * launch is credited with the volume terms' work above.  When the call
+ * issued row kernels, two more records follow: "row_pass", the span from
+ * the first row-kernel start to the last row-kernel end (degree groups may
+ * run concurrently) with their summed flops and bytes, and
+ * "row_pass_executed", the same span with the flops the launches executed
+ * (the moment form executes fewer: per volume point 2 d (2p-1) + (2p+1) +
+ * one per moment (+ (2p+1)(2p+2)/2 in 3D) + n d FMAs, per element 3 per
+ * moment combination of each block entry (+ 3 per (c, d) pair in 3D) and
+ * 3 d (p+1)^2 (2p+1) for the coefficient tables). */
 typedef struct {
   char name[48];
   float ms;

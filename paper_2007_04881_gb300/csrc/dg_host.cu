@@ -200,6 +200,7 @@ void Tracer::begin(const char* name, int kind, int p, size_t tsize, cudaStream_t
   LaunchRec& r = recs[n];
   snprintf(r.name, sizeof r.name, "%s", name);
   r.flops = (kind < kKinds && flops) ? flops[kind * 9 + p] : 0.0;
+  r.xflops = (kind == 2 && xflops) ? xflops[p] : r.flops;
   r.bytes = (kind < kKinds && words) ? words[kind * 9 + p] * (double)tsize : 0.0;
   record(r.ev0, st);
 }
@@ -235,7 +236,7 @@ struct dg_mesh {
   double* X[3] = {nullptr, nullptr, nullptr};
   double* a = nullptr;
   double flops[kKinds][9] = {{0}}, words[kKinds][9] = {{0}};
-  double mom_pt[9] = {0};
+  double mom_exec[9] = {0}, mom_pt[9] = {0};
   std::vector<int> batch_elem_off;  // element offset of each batch member (empty: one mesh)
   // partition meshes: local -> global element and vertex ids, owned flags
   std::vector<int> part_elem, part_vert;
@@ -263,6 +264,7 @@ static void trace_reset(dg_ctx* ctx, const dg_mesh* mesh) {
   ctx->tracer.n = 0;
   ctx->tracer.flops = &mesh->flops[0][0];
   ctx->tracer.words = &mesh->words[0][0];
+  ctx->tracer.xflops = mesh->mom_exec;
 }
 
 namespace {
@@ -402,7 +404,8 @@ struct Plan {
   // algorithmic flops / words per launch group [kind][p] (kind 0: row
   // kernel of degree p, whole block rows and load vector)
   double flops[kKinds][9] = {{0}}, words[kKinds][9] = {{0}};
-  double mom_pt[9] = {0};  // moment kernel operations per volume point, by degree
+  double mom_exec[9] = {0};  // moment form: executed flops of the volume launch, by degree
+  double mom_pt[9] = {0};    // moment form: executed flops per volume point, by degree
 };
 
 extern "C" {
@@ -808,15 +811,17 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P, const int8_t* owned = nullp
         P.words[0][d->p[e]] += w;
       }
     }
-    // The moment form of the volume terms (kind 2) and the row kernel's
-    // faces-only launch beside it (kind 1 = kind 0 without the volume
-    // terms).  Moment kernel, FMA-equivalent operations: per volume point
-    // 2 d (2p - 1) for the Legendre values to degree 2p, 2p + 1 weighted
-    // values, one update per moment (c + d (+ e) <= 2p; in 3D also the
-    // (2p+1)(2p+2)/2 partial products) and n d for the load vector; per
-    // element 3 per moment combination of every block entry (in 3D also 3
-    // per (c, d) pair) and 3 d per exponent pair and degree for the
-    // coefficient tables.
+    // The launches of the moment path: the volume launch (kind 2) is credited
+    // with the volume terms' algorithmic work above (the quadrature sums it
+    // evaluates), the row kernel's faces-only launch beside it (kind 1) with
+    // the rest.  What the moment form executes instead, FMA-equivalent
+    // operations, is mom_exec: per volume point 2 d (2p - 1) for the Legendre
+    // values to degree 2p, 2p + 1 weighted values, one update per moment
+    // (c + d (+ e) <= 2p; in 3D also the (2p+1)(2p+2)/2 partial products) and
+    // n d for the load vector; per element 3 per moment combination of every
+    // block entry (in 3D also 3 per (c, d) pair) and 3 d per exponent pair
+    // and degree for the coefficient tables.  It is reported as the
+    // "row_pass_executed" record beside "row_pass".
     double map_ops[9] = {0}, pt_ops[9] = {0};
     for (int pp = 1; pp <= 8; ++pp) {
       const int q = 2 * pp, nn = nbasis(dim, pp);
@@ -846,13 +851,14 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P, const int8_t* owned = nullp
       const double vol_words = n * n + n + (double)(d->elem_ptr[e + 1] - d->elem_ptr[e]) * SV + 2 * dim + 2;
       P.flops[1][pe] -= 2.0 * vol_direct;
       P.words[1][pe] -= vol_words;
-      P.flops[2][pe] += 2.0 * (nvq * pt_ops[pe] + map_ops[pe]);
+      P.flops[2][pe] += 2.0 * vol_direct;
       P.words[2][pe] += vol_words;
+      P.mom_exec[pe] += 2.0 * (nvq * pt_ops[pe] + map_ops[pe]);
     }
     for (int pp = 0; pp <= 8; ++pp) {
       P.flops[1][pp] += P.flops[0][pp];
       P.words[1][pp] += P.words[0][pp];
-      P.mom_pt[pp] = pt_ops[pp];
+      P.mom_pt[pp] = 2.0 * pt_ops[pp];
     }
   }
   P.nsub = nsub;
@@ -910,6 +916,7 @@ static int upload_impl(dg_ctx* ctx, const dg_mesh_desc* d, const int8_t* owned, 
   m->col = P.col;
   std::memcpy(m->flops, P.flops, sizeof P.flops);
   std::memcpy(m->words, P.words, sizeof P.words);
+  std::memcpy(m->mom_exec, P.mom_exec, sizeof P.mom_exec);
   std::memcpy(m->mom_pt, P.mom_pt, sizeof P.mom_pt);
   m->blk_off = P.blk_off;
   m->dof_off = P.dof_off;
@@ -1757,7 +1764,8 @@ int dg_quad_fit(dg_ctx* ctx, dg_mesh* mesh, const float* init, int iters, int in
       for (int e = 0; e < ne; ++e)
         if (ok[e] && (mesh->owned_h.empty() || mesh->owned_h[e])) {
           mesh->flops[0][mesh->p_h[e]] -= 2.0 * (mesh->nvq_h[e] - 28) * mesh->vfma_h[e];
-          mesh->flops[2][mesh->p_h[e]] -= 2.0 * (mesh->nvq_h[e] - 28) * mesh->mom_pt[mesh->p_h[e]];
+          mesh->flops[2][mesh->p_h[e]] -= 2.0 * (mesh->nvq_h[e] - 28) * mesh->vfma_h[e];
+          mesh->mom_exec[mesh->p_h[e]] -= (mesh->nvq_h[e] - 28) * mesh->mom_pt[mesh->p_h[e]];
         }
     }
   }
@@ -1780,7 +1788,8 @@ int dg_quad_clear(dg_ctx* ctx, dg_mesh* mesh) {
     for (int e = 0; e < mesh->dm.ne; ++e)
       if (okd[e] && (mesh->owned_h.empty() || mesh->owned_h[e])) {
         mesh->flops[0][mesh->p_h[e]] += 2.0 * (mesh->nvq_h[e] - 28) * mesh->vfma_h[e];
-        mesh->flops[2][mesh->p_h[e]] += 2.0 * (mesh->nvq_h[e] - 28) * mesh->mom_pt[mesh->p_h[e]];
+        mesh->flops[2][mesh->p_h[e]] += 2.0 * (mesh->nvq_h[e] - 28) * mesh->vfma_h[e];
+        mesh->mom_exec[mesh->p_h[e]] += (mesh->nvq_h[e] - 28) * mesh->mom_pt[mesh->p_h[e]];
       }
     int rc = rebuild_worklist(ctx, mesh, ok);
     if (rc != DG_OK) return rc;
@@ -1842,6 +1851,18 @@ int dg_kernel_stats(dg_ctx* ctx, dg_kernel_stat* out, int cap) {
     out[n].ms = t1 - t0;
     out[n].flops = fl;
     out[n].bytes = by;
+    if (n + 1 < cap) {
+      // the same span with the flops the launches executed (the moment form
+      // of the volume terms executes fewer than the quadrature sums it forms)
+      double xf = 0.0;
+      for (int i = 0; i < n; ++i)
+        if (std::strncmp(ctx->recs[i].name, "row", 3) == 0) xf += ctx->recs[i].xflops;
+      std::snprintf(out[n + 1].name, sizeof out[n + 1].name, "row_pass_executed");
+      out[n + 1].ms = t1 - t0;
+      out[n + 1].flops = xf;
+      out[n + 1].bytes = by;
+      return n + 2;
+    }
     return n + 1;
   }
   return n;

@@ -144,7 +144,8 @@ enum : int {
 // byte counts (host-computed per launch group).
 struct LaunchRec {
   char name[48];
-  double flops;
+  double flops;   // algorithmic (the quadrature formulation's count)
+  double xflops;  // executed (differs for the moment form of the volume terms)
   double bytes;
   cudaEvent_t ev0, ev1;
 };
@@ -159,8 +160,9 @@ struct Tracer {
   // kernel of degree p (volume and faces), 1 = its faces-only launch next to
   // the moment kernel, 2 = the moment volume kernel; words = values written +
   // read, scaled by sizeof(T)
-  const double* flops = nullptr;  // [kKinds][9]
-  const double* words = nullptr;  // [kKinds][9]
+  const double* flops = nullptr;   // [kKinds][9]
+  const double* words = nullptr;   // [kKinds][9]
+  const double* xflops = nullptr;  // [9]: flops the kind-2 launch executes
   void begin(const char* name, int kind, int p, size_t tsize, cudaStream_t st);
   void end(cudaStream_t st);
   static void record(cudaEvent_t ev, cudaStream_t st);
