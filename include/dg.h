@@ -215,9 +215,10 @@ int dg_batch_offsets(const dg_mesh *mesh, int *nmesh, int *elem_off, int64_t *va
  *     forms; the diagonal block is then written by a separate moment
  *     launch and the row kernel adds the face terms to it.
  *   path 0: the per-point block contraction in the row kernels throughout.
- * The tensor-core forms always take their own contraction.  Applies to
- * later calls and recorded passes made after it; DG_ERR_ARG for another
- * path. */
+ * The tensor-core forms always take their own contraction.  A mesh with
+ * learned rules installed (28 points per element) takes the per-point path
+ * in the calls; dg_graph_create's autotuner times both.  Applies to later
+ * calls and recorded passes made after it; DG_ERR_ARG for another path. */
 int dg_set_volume_path(dg_ctx *ctx, int path);
 
 /* Partitions (Sec. 4.2: the elements are split across GPUs, each GPU builds
@@ -262,13 +263,18 @@ int dg_part_check(const dg_mesh_desc *desc, const int *part, int my_part, dg_bsr
  * fixed for the graph's life) as a CUDA graph.  With autotune != 0 it first
  * times the candidate launch shapes (co-resident CTAs per SM capped at 1, 2
  * or the occupancy limit; degree groups serial on one stream or concurrent
- * on forked streams) and records the fastest.  The first call must precede
+ * on forked streams; for the FP32 and FP64 forms, when the context's volume
+ * path is 1, also the moment and the per-point volume paths) and records
+ * the fastest.  Without autotuning the context's path is used (the per-point
+ * one for a mesh with learned rules installed).  The first call must precede
  * any stream capture by the caller.  dg_graph_launch replays the pass on the
- * context stream. */
+ * context stream.  dg_graph_info: the recorded shape (any output may be
+ * NULL; vol_path 0 per-point, 1 moments). */
 typedef struct dg_graph dg_graph;
 int dg_graph_create(dg_ctx *ctx, dg_mesh *mesh, int prec, void *vals, void *rhs, int autotune, dg_graph **out);
 int dg_graph_launch(dg_ctx *ctx, dg_graph *graph);
-int dg_graph_info(const dg_graph *graph, int *occ_cap, int *concurrent, float *tuned_ms, int *launches);
+int dg_graph_info(const dg_graph *graph, int *occ_cap, int *concurrent, float *tuned_ms, int *launches,
+                  int *vol_path);
 int dg_graph_free(dg_graph *graph);
 
 /* Learned reduced volume rules (2D).  For each element mapped to its

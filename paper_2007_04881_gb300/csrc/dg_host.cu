@@ -184,6 +184,7 @@ struct dg_graph {
   cudaGraphExec_t exec = nullptr;
   int occ_cap = 0;
   int concurrent = 0;
+  int vol_path = 1;
   float tuned_ms = 0.f;
   int launches = 0;
   int ntrace = 0;  // timing events recorded inside the graph (tracing on at capture)
@@ -1108,9 +1109,12 @@ int dg_mesh_update(dg_ctx* ctx, dg_mesh* mesh, const double* x, const double* y,
 
 // Issue the row kernels of one assembly pass on stream st.  concurrent:
 // the per-degree launches go to forked side streams and join back into st.
+// vpath: volume path (0 per-point contraction, 1 moments), -1 the context's
+// setting; meshes with learned rules installed take the per-point path
+// unless a path is given (their elements have only 28 points each)
 static int run_assembly(dg_ctx* ctx, const dg_mesh* mesh, int prec, int mode, void* vals, void* rhs, bool iface,
                         bool reset = true, cudaStream_t st = nullptr, bool use_ctx_stream = true, int occ_cap = 0,
-                        bool concurrent = false) {
+                        bool concurrent = false, int vpath = -1) {
   if (!ctx || !mesh) return fail(DG_ERR_ARG, "null context or mesh");
   if (prec < DG_PREC_FP64 || prec > DG_PREC_TF32X3) return fail(DG_ERR_ARG, "unknown precision %d", prec);
   if ((mode & (kModeVol | kModeFace)) && !vals) return fail(DG_ERR_ARG, "vals is null");
@@ -1122,7 +1126,7 @@ static int run_assembly(dg_ctx* ctx, const dg_mesh* mesh, int prec, int mode, vo
   (void)iface;
   LaunchOpts lo;
   lo.occ_cap = occ_cap;
-  lo.vol_moments = ctx->vol_moments;
+  lo.vol_moments = vpath >= 0 ? vpath == 1 : ctx->vol_moments && !mesh->dm.lq_ok;
   for (int p = 0; p < 9; ++p) lo.pst[p] = st;
   if (concurrent) {
     if (!ctx->fork) {
@@ -1560,11 +1564,11 @@ int dg_batch_offsets(const dg_mesh* mesh, int* nmesh, int* elem_off, int64_t* va
 
 // One whole pass (geometry + row kernels) on stream st with a launch shape.
 static int issue_pass(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs, cudaStream_t st, int occ_cap,
-                      bool concurrent) {
+                      bool concurrent, int vpath) {
   int n = launch_geometry(mesh->dm, st, nullptr, prec == DG_PREC_FP64 ? 1 : 2);
   DG_CUDA_TRY(cudaGetLastError());
   const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
-  int rc = run_assembly(ctx, mesh, prec, mode, vals, rhs, true, true, st, false, occ_cap, concurrent);
+  int rc = run_assembly(ctx, mesh, prec, mode, vals, rhs, true, true, st, false, occ_cap, concurrent, vpath);
   if (rc != DG_OK) return rc;
   ctx->last_launches += n;
   return DG_OK;
@@ -1584,20 +1588,26 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
     return bail(fail(DG_ERR_CUDA, "dg_graph_create: stream creation failed"));
   const bool was_on = ctx->tracer.on;
   ctx->tracer.on = false;
-  // autotuner: time each candidate launch shape (best of 3 after a warm-up)
-  int best_occ = 0, best_conc = 0;
+  // autotuner: time each candidate launch shape (best of 3 after a warm-up):
+  // residency cap x serial / concurrent degree groups x volume path (the
+  // moment path only where the context allows it and the form has it)
+  const int def_path = ctx->vol_moments && !mesh->dm.lq_ok ? 1 : 0;
+  int best_occ = 0, best_conc = 0, best_path = def_path;
   float best = 1e30f;
   if (autotune) {
     const int occs[3] = {0, 1, 2};
+    const int npath = ctx->vol_moments && (prec == DG_PREC_FP32 || prec == DG_PREC_FP64) ? 2 : 1;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
+    for (int pi = 0; pi < npath; ++pi)
     for (int conc = 0; conc < 2; ++conc)
       for (int oi = 0; oi < 3; ++oi) {
+        const int vpath = npath == 2 ? 1 - pi : 0;
         float t = 1e30f;
         for (int rep = 0; rep < 4; ++rep) {
           cudaEventRecord(e0, g->stream);
-          int rc = issue_pass(ctx, mesh, prec, vals, rhs, g->stream, occs[oi], conc != 0);
+          int rc = issue_pass(ctx, mesh, prec, vals, rhs, g->stream, occs[oi], conc != 0, vpath);
           if (rc != DG_OK) {
             ctx->tracer.on = was_on;
             cudaEventDestroy(e0);
@@ -1617,6 +1627,7 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
           best = t;
           best_occ = occs[oi];
           best_conc = conc;
+          best_path = vpath;
         }
       }
     cudaEventDestroy(e0);
@@ -1624,6 +1635,7 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
   }
   g->occ_cap = best_occ;
   g->concurrent = best_conc;
+  g->vol_path = best_path;
   g->tuned_ms = autotune ? best : 0.f;
   // with timing enabled the per-launch events are recorded into the graph
   ctx->tracer.on = was_on;
@@ -1634,7 +1646,8 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
   {
     const int gl = launch_geometry(mesh->dm, g->stream, &ctx->tracer, prec == DG_PREC_FP64 ? 1 : 2);
     const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
-    rc = run_assembly(ctx, mesh, prec, mode, vals, rhs, true, false, g->stream, false, g->occ_cap, g->concurrent != 0);
+    rc = run_assembly(ctx, mesh, prec, mode, vals, rhs, true, false, g->stream, false, g->occ_cap, g->concurrent != 0,
+                      g->vol_path);
     ctx->last_launches += gl;
   }
   cudaError_t ce = cudaStreamEndCapture(g->stream, &g->graph);
@@ -1656,8 +1669,9 @@ int dg_graph_launch(dg_ctx* ctx, dg_graph* g) {
   return DG_OK;
 }
 
-int dg_graph_info(const dg_graph* g, int* occ_cap, int* concurrent, float* tuned_ms, int* launches) {
+int dg_graph_info(const dg_graph* g, int* occ_cap, int* concurrent, float* tuned_ms, int* launches, int* vol_path) {
   if (!g) return fail(DG_ERR_ARG, "dg_graph_info: null graph");
+  if (vol_path) *vol_path = g->vol_path;
   if (occ_cap) *occ_cap = g->occ_cap;
   if (concurrent) *concurrent = g->concurrent;
   if (tuned_ms) *tuned_ms = g->tuned_ms;

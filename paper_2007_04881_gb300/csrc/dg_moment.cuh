@@ -19,8 +19,11 @@
 // Yb = b'_2 G1(bj, bi) + a'_2 G2(bi, bj), Zs = b'_3 G1(cj, ci) + a'_3 G2(ci, cj),
 // with the trial function j carrying the advection derivative.  Per point
 // this costs the moments (45 for 2D p = 4) instead of the 3 n^2 block
-// updates; per element, the combination above.  The load vector's volume
-// term (non-polynomial f) is accumulated per point as before.
+// updates; per element, the combination above, in 2D in two stages:
+//   T(c, (bi,bj)) = sum_d mu_cd Y0(d),  U(c, (bi,bj)) = sum_d mu_cd Yb(d),
+//   A_ij = sum_c [Xa(c) T(c, (bi,bj)) + X0(c) U(c, (bi,bj))].
+// The load vector's volume term (non-polynomial f) is accumulated per point
+// as before.
 //
 // Layout: LPE lanes per element.  Each lane accumulates the moments and the
 // load vector of every LPE-th point in registers; a butterfly reduction over
@@ -60,8 +63,9 @@ struct MomCfg {
   static constexpr int CL = 2 * kPMaxLin + 1;
   static constexpr int NLIN = 3 * PL * PL * CL;  // G, G1, G2
   static constexpr int NPAIR = (P + 1) * (P + 1);
-  // per element: moments, and Xa, Yb (and Zs) for every exponent pair
-  static constexpr int PER_ELEM = NM + D * NPAIR * (Q + 1);
+  // per element: moments, and three [NPAIR][Q+1] tables: Xa, then in 2D the
+  // stage-one sums T and U, in 3D Yb and Zs
+  static constexpr int PER_ELEM = NM + 3 * NPAIR * (Q + 1);
   static constexpr int NMAXC = nbasis(D, D == 2 ? kPMax2 : kPMax3);
   static constexpr size_t head_elems = NLIN + QT * (D + 1) + NMAXC;
   static constexpr size_t total = align_up(sizeof(T) * (head_elems + (size_t)kWarps * G * PER_ELEM), 16);
@@ -102,8 +106,8 @@ __global__ void __launch_bounds__(kWarps * 32)
   T* my = pe + (size_t)(warp * G + grp) * Cfg::PER_ELEM;  // this element's scratch
   T* smu = my;
   T* sXa = my + NM;                // [NPAIR][Q+1] per exponent pair (a, a') of dimension 0
-  T* sYb = sXa + NPAIR * (Q + 1);  // dimension 1
-  T* sZs = sYb + NPAIR * (Q + 1);  // dimension 2 (3D)
+  T* sYb = sXa + NPAIR * (Q + 1);  // 3D: dimension 1 [NPAIR][Q+1]; 2D: T [Q+1][NPAIR]
+  T* sZs = sYb + NPAIR * (Q + 1);  // 3D: dimension 2 [NPAIR][Q+1]; 2D: U [Q+1][NPAIR]
   const int base = m.elem_pstart[P], count = m.elem_pstart[P + 1] - base;
   const int ngroups = (count + G - 1) / G;
 
@@ -240,8 +244,29 @@ __global__ void __launch_bounds__(kWarps * 32)
           const int pr = k / (Q + 1), c = k - pr * (Q + 1);
           const int a = pr / (P + 1), ap = pr - a * (P + 1);
           sXa[k] = q.c * L0(a, ap, c) + q.bp[0] * L1(ap, a, c) + q.ap[0] * L2(a, ap, c);
-          sYb[k] = q.bp[1 % D] * L1(ap, a, c) + q.ap[1 % D] * L2(a, ap, c);
-          if constexpr (D == 3) sZs[k] = q.bp[2 % D] * L1(ap, a, c) + q.ap[2 % D] * L2(a, ap, c);
+          if constexpr (D == 3) {
+            sYb[k] = q.bp[1 % D] * L1(ap, a, c) + q.ap[1 % D] * L2(a, ap, c);
+            sZs[k] = q.bp[2 % D] * L1(ap, a, c) + q.ap[2 % D] * L2(a, ap, c);
+          }
+        }
+      }
+      if constexpr (D == 2) {
+        __syncwarp();
+        // stage one: T(c, pair) and U(c, pair) over d <= b + b', c + d <= 2p
+        if (active) {
+          for (int k = lig; k < NPAIR * (Q + 1); k += LPE) {
+            const int c = k / NPAIR, pr = k - c * NPAIR;
+            const int b = pr / (P + 1), bp = pr - b * (P + 1);
+            const int dm = min(b + bp, Q - c);
+            T t0 = T(0), u0 = T(0);
+            for (int d = 0; d <= dm; ++d) {
+              const T mu_cd = smu[mom2(c, d)];
+              t0 = fma(mu_cd, L0(b, bp, d), t0);
+              u0 = fma(mu_cd, q.bp[1] * L1(bp, b, d) + q.ap[1] * L2(b, bp, d), u0);
+            }
+            sYb[k] = t0;
+            sZs[k] = u0;
+          }
         }
       }
       __syncwarp();
@@ -257,13 +282,9 @@ __global__ void __launch_bounds__(kWarps * 32)
           const int px = ai[0] * (P + 1) + aj[0], py = ai[1] * (P + 1) + aj[1];
           const int cmax = ai[0] + aj[0], dmax = ai[1] + aj[1];
           if constexpr (D == 2) {
-            for (int c = 0; c <= cmax; ++c) {
-              const T x0 = L0(ai[0], aj[0], c), xa = sXa[px * (Q + 1) + c];
-              for (int d = 0; d <= dmax; ++d) {
-                const T coef = L0(ai[1], aj[1], d) * xa + x0 * sYb[py * (Q + 1) + d];
-                acc = fma(smu[mom2(c, d)], coef, acc);
-              }
-            }
+            (void)dmax;
+            for (int c = 0; c <= cmax; ++c)
+              acc = fma(sXa[px * (Q + 1) + c], sYb[c * NPAIR + py], fma(L0(ai[0], aj[0], c), sZs[c * NPAIR + py], acc));
           } else {
             const int pz = ai[2] * (P + 1) + aj[2], emax = ai[2] + aj[2];
             for (int c = 0; c <= cmax; ++c) {

@@ -118,7 +118,7 @@ def load() -> C.CDLL:
     lib.dg_batch_offsets.argtypes = [V, V, V, V, V]
     lib.dg_graph_create.argtypes = [V, V, C.c_int, V, V, C.c_int, C.POINTER(V)]
     lib.dg_graph_launch.argtypes = [V, V]
-    lib.dg_graph_info.argtypes = [V, V, V, V, V]
+    lib.dg_graph_info.argtypes = [V, V, V, V, V, V]
     lib.dg_graph_free.argtypes = [V]
     lib.dg_volume_noalloc.argtypes = [V, C.c_int, C.c_int, C.c_int, C.c_int, V, V, C.c_int, C.c_int, V, V, V,
                                       C.c_double, C.c_double, C.c_double, V]
@@ -536,9 +536,10 @@ class Graph:
         _check(load().dg_graph_launch(self.ctx._h, self._h))
 
     def dg_graph_info(self):
-        occ, conc, ms, nl = C.c_int(), C.c_int(), C.c_float(), C.c_int()
-        _check(load().dg_graph_info(self._h, C.byref(occ), C.byref(conc), C.byref(ms), C.byref(nl)))
-        return {"occ_cap": occ.value, "concurrent": bool(conc.value), "tuned_ms": ms.value, "launches": nl.value}
+        occ, conc, ms, nl, vp = C.c_int(), C.c_int(), C.c_float(), C.c_int(), C.c_int()
+        _check(load().dg_graph_info(self._h, C.byref(occ), C.byref(conc), C.byref(ms), C.byref(nl), C.byref(vp)))
+        return {"occ_cap": occ.value, "concurrent": bool(conc.value), "tuned_ms": ms.value, "launches": nl.value,
+                "volume_path": "moments" if vp.value == 1 else "per-point"}
 
     def close(self):
         if getattr(self, "_h", None):
