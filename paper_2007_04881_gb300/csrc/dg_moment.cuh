@@ -67,7 +67,9 @@ struct MomCfg {
   // stage-one sums T and U, in 3D Yb and Zs
   static constexpr int PER_ELEM = NM + 3 * NPAIR * (Q + 1);
   static constexpr int NMAXC = nbasis(D, D == 2 ? kPMax2 : kPMax3);
-  static constexpr size_t head_elems = NLIN + QT * (D + 1) + NMAXC;
+  // linearisation tables, rule, basis scales, then the exponents of the
+  // degree's basis functions (int, [N][3])
+  static constexpr size_t head_elems = NLIN + QT * (D + 1) + NMAXC + (3 * N * sizeof(int) + sizeof(T) - 1) / sizeof(T);
   static constexpr size_t total = align_up(sizeof(T) * (head_elems + (size_t)kWarps * G * PER_ELEM), 16);
 };
 
@@ -88,12 +90,20 @@ __global__ void __launch_bounds__(kWarps * 32)
   T* lin = reinterpret_cast<T*>(smem_raw);  // [3][PL][PL][CL]
   T* rule = lin + NLIN;
   T* ctab = rule + QT * (D + 1);
+  int* alf = reinterpret_cast<int*>(ctab + Cfg::NMAXC);       // exponents [N][3]
   T* pe = reinterpret_cast<T*>(smem_raw) + Cfg::head_elems;  // per element scratch
   const T* glin = pick<T>(m.rt.lin64, m.rt.lin32);
   for (int i = threadIdx.x; i < NLIN; i += blockDim.x) lin[i] = glin[i];
   const T* vrule = pick<T>(m.rt.vol64, m.rt.vol32) + (size_t)m.rt.vol_off[P] * (D + 1);
   for (int i = threadIdx.x; i < QT * (D + 1); i += blockDim.x) rule[i] = vrule[i];
   fill_ctab<D, T>(ctab, Cfg::NMAXC);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    int al[3] = {0, 0, 0};
+    basis_alpha<D>(i, al);
+    alf[3 * i] = al[0];
+    alf[3 * i + 1] = al[1];
+    alf[3 * i + 2] = al[2];
+  }
   __syncthreads();
   auto L0 = [&](int a, int b, int c) { return lin[(a * PL + b) * CL + c]; };
   auto L1 = [&](int a, int b, int c) { return lin[PL * PL * CL + (a * PL + b) * CL + c]; };
@@ -258,11 +268,16 @@ __global__ void __launch_bounds__(kWarps * 32)
             const int c = k / NPAIR, pr = k - c * NPAIR;
             const int b = pr / (P + 1), bp = pr - b * (P + 1);
             const int dm = min(b + bp, Q - c);
+            const T* g0 = lin + (b * PL + bp) * CL;                  // G(b, b', d)
+            const T* g1 = lin + PL * PL * CL + (bp * PL + b) * CL;   // G1(b', b, d)
+            const T* g2 = lin + 2 * PL * PL * CL + (b * PL + bp) * CL;  // G2(b, b', d)
+            int mi = c * (c + 1) / 2;  // moment (c, 0); (c, d + 1) is c + d + 2 further
             T t0 = T(0), u0 = T(0);
             for (int d = 0; d <= dm; ++d) {
-              const T mu_cd = smu[mom2(c, d)];
-              t0 = fma(mu_cd, L0(b, bp, d), t0);
-              u0 = fma(mu_cd, q.bp[1] * L1(bp, b, d) + q.ap[1] * L2(b, bp, d), u0);
+              const T mu_cd = smu[mi];
+              mi += c + d + 2;
+              t0 = fma(mu_cd, g0[d], t0);
+              u0 = fma(mu_cd, q.bp[1] * g1[d] + q.ap[1] * g2[d], u0);
             }
             sYb[k] = t0;
             sZs[k] = u0;
@@ -275,16 +290,19 @@ __global__ void __launch_bounds__(kWarps * 32)
         const T RR = q.R * q.R;
         for (int ent = lig; ent < N * N; ent += LPE) {
           const int i = ent / N, j = ent - (ent / N) * N;
-          int ai[3], aj[3];
-          basis_alpha<D>(i, ai);
-          basis_alpha<D>(j, aj);
+          const int ai[3] = {alf[3 * i], alf[3 * i + 1], alf[3 * i + 2]};
+          const int aj[3] = {alf[3 * j], alf[3 * j + 1], alf[3 * j + 2]};
           T acc = T(0);
           const int px = ai[0] * (P + 1) + aj[0], py = ai[1] * (P + 1) + aj[1];
           const int cmax = ai[0] + aj[0], dmax = ai[1] + aj[1];
           if constexpr (D == 2) {
             (void)dmax;
+            const T* xa = sXa + px * (Q + 1);
+            const T* x0 = lin + (ai[0] * PL + aj[0]) * CL;
+            const T* tt = sYb + py;
+            const T* uu = sZs + py;
             for (int c = 0; c <= cmax; ++c)
-              acc = fma(sXa[px * (Q + 1) + c], sYb[c * NPAIR + py], fma(L0(ai[0], aj[0], c), sZs[c * NPAIR + py], acc));
+              acc = fma(xa[c], tt[c * NPAIR], fma(x0[c], uu[c * NPAIR], acc));
           } else {
             const int pz = ai[2] * (P + 1) + aj[2], emax = ai[2] + aj[2];
             for (int c = 0; c <= cmax; ++c) {
