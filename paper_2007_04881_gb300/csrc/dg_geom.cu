@@ -21,18 +21,48 @@ __global__ void elem_geom_kernel(DevMesh m) {
   if (e >= m.ne) return;
   double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
   double vol = 0.0, cen[3] = {0.0, 0.0, 0.0};
+  // 2D loops of up to KV vertices are loaded once (all loads issued before
+  // use); longer loops read the vertex arrays directly
+  constexpr int KV = 16;
+  double vx[D == 2 ? KV : 1], vy[D == 2 ? KV : 1];
+  int kv = 0;
   if (D == 2) {
     const int b = m.eptr[e], k = m.eptr[e + 1] - b;
+    if (k <= KV) {
+      int vi[KV];
+#pragma unroll
+      for (int i = 0; i < KV; ++i) vi[i] = i < k ? m.eidx[b + i] : 0;
+#pragma unroll
+      for (int i = 0; i < KV; ++i)
+        if (i < k) {
+          vx[i] = m.X[0][vi[i]];
+          vy[i] = m.X[1][vi[i]];
+        }
+      kv = k;
+    }
     for (int i = 0; i < k; ++i) {
-      const int v0 = m.eidx[b + i], v1 = m.eidx[b + (i + 1 == k ? 0 : i + 1)];
-      const double x0 = m.X[0][v0], y0 = m.X[1][v0], x1 = m.X[0][v1], y1 = m.X[1][v1];
+      const int i1 = i + 1 == k ? 0 : i + 1;
+      double x0, y0, x1, y1;
+      if (kv) {
+        x0 = vx[i];
+        y0 = vy[i];
+        x1 = vx[i1];
+        y1 = vy[i1];
+      } else {
+        const int v0 = m.eidx[b + i], v1 = m.eidx[b + i1];
+        x0 = m.X[0][v0];
+        y0 = m.X[1][v0];
+        x1 = m.X[0][v1];
+        y1 = m.X[1][v1];
+      }
       const double cr = x0 * y1 - x1 * y0;
       vol += 0.5 * cr;
       cen[0] += (x0 + x1) * cr;
       cen[1] += (y0 + y1) * cr;
     }
-    cen[0] /= 6.0 * vol;
-    cen[1] /= 6.0 * vol;
+    const double i6v = 1.0 / (6.0 * vol);
+    cen[0] *= i6v;
+    cen[1] *= i6v;
   } else {
     for (int t = m.eptr[e]; t < m.eptr[e + 1]; ++t) {
       double P[4][3];
@@ -60,6 +90,32 @@ __global__ void elem_geom_kernel(DevMesh m) {
   // them, so h is the exact FP64 diameter at a fraction of the FP64 work.
   const int ub = m.uvptr[e], ue = m.uvptr[e + 1];
   float h2f = 0.f;
+  double h2 = 0.0;
+  if (D == 2 && kv) {
+    // the 2D loop's vertices are the element's distinct vertices
+    float fx[KV], fy[KV];
+    for (int i = 0; i < kv; ++i) {
+      lo[0] = fmin(lo[0], vx[i]);
+      hi[0] = fmax(hi[0], vx[i]);
+      lo[1] = fmin(lo[1], vy[i]);
+      hi[1] = fmax(hi[1], vy[i]);
+      fx[i] = (float)vx[i];
+      fy[i] = (float)vy[i];
+    }
+    for (int i = 0; i < kv; ++i)
+      for (int j = i + 1; j < kv; ++j) {
+        const float dx = fx[j] - fx[i], dy = fy[j] - fy[i];
+        h2f = fmaxf(h2f, fmaf(dx, dx, dy * dy));
+      }
+    const float cut = h2f * (1.0f - 1e-5f);
+    for (int i = 0; i < kv; ++i)
+      for (int j = i + 1; j < kv; ++j) {
+        const float dx = fx[j] - fx[i], dy = fy[j] - fy[i];
+        if (fmaf(dx, dx, dy * dy) < cut) continue;
+        const double ddx = vx[j] - vx[i], ddy = vy[j] - vy[i];
+        h2 = fmax(h2, ddx * ddx + ddy * ddy);
+      }
+  } else {
   for (int i = ub; i < ue; ++i) {
     const int vi = m.uvidx[i];
     float pf[3];
@@ -80,7 +136,6 @@ __global__ void elem_geom_kernel(DevMesh m) {
     }
   }
   const float cut = h2f * (1.0f - 1e-5f);
-  double h2 = 0.0;
   for (int i = ub; i < ue; ++i) {
     const int vi = m.uvidx[i];
     for (int j = i + 1; j < ue; ++j) {
@@ -98,6 +153,7 @@ __global__ void elem_geom_kernel(DevMesh m) {
       }
       h2 = fmax(h2, s2);
     }
+  }
   }
   for (int d = 0; d < D; ++d) {
     m.lo[d * m.ne + e] = lo[d];
@@ -129,9 +185,7 @@ __global__ void elem_geom_kernel(DevMesh m) {
 }
 
 template <int D>
-__global__ void sub_geom_kernel(DevMesh m, int wmask) {
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= m.nsub) return;
+__device__ __forceinline__ void sub_geom(const DevMesh& m, int wmask, int k) {
   const int e = m.sub_elem[k];
   double lo[3], L[3];
   for (int d = 0; d < D; ++d) {
@@ -180,9 +234,7 @@ __global__ void sub_geom_kernel(DevMesh m, int wmask) {
 }
 
 template <int D>
-__global__ void face_geom_kernel(DevMesh m, int wmask) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= m.nf) return;
+__device__ __forceinline__ void face_geom(const DevMesh& m, int wmask, int f) {
   const int es[2] = {m.f_e0[f], m.f_e1[f]};
   double P[3][3];
   for (int i = 0; i < D; ++i) {
@@ -239,24 +291,35 @@ __global__ void face_geom_kernel(DevMesh m, int wmask) {
     for (int j = 0; j < 3; ++j) m.fsc32[(size_t)j * m.nf + f] = (float)sc[j];
 }
 
+// sub-simplex records (threads 0 .. nsub-1) and face records (the rest):
+// both read only the element records, so one launch covers them
+template <int D>
+__global__ void subface_geom_kernel(DevMesh m, int wmask) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < m.nsub)
+    sub_geom<D>(m, wmask, t);
+  else if (t - m.nsub < m.nf)
+    face_geom<D>(m, wmask, t - m.nsub);
+}
+
 inline int nblk(int n, int t) { return (n + t - 1) / t; }
 
 }  // namespace
 
 int launch_geometry(const DevMesh& m, cudaStream_t st, Tracer* tr, int wmask) {
   const int T = 128;
-  if (tr && tr->on) tr->begin(m.dim == 2 ? "geometry2d" : "geometry3d", 2, 0, 8, st);
+  // no algorithmic flop count of its own (kind past the counted ones)
+  if (tr && tr->on) tr->begin(m.dim == 2 ? "geometry2d" : "geometry3d", kKinds, 0, 8, st);
+  const int nsf = m.nsub + m.nf;
   if (m.dim == 2) {
     if (m.ne > 0) elem_geom_kernel<2><<<nblk(m.ne, T), T, 0, st>>>(m);
-    if (m.nsub > 0) sub_geom_kernel<2><<<nblk(m.nsub, T), T, 0, st>>>(m, wmask);
-    if (m.nf > 0) face_geom_kernel<2><<<nblk(m.nf, T), T, 0, st>>>(m, wmask);
+    if (nsf > 0) subface_geom_kernel<2><<<nblk(nsf, T), T, 0, st>>>(m, wmask);
   } else {
     if (m.ne > 0) elem_geom_kernel<3><<<nblk(m.ne, T), T, 0, st>>>(m);
-    if (m.nsub > 0) sub_geom_kernel<3><<<nblk(m.nsub, T), T, 0, st>>>(m, wmask);
-    if (m.nf > 0) face_geom_kernel<3><<<nblk(m.nf, T), T, 0, st>>>(m, wmask);
+    if (nsf > 0) subface_geom_kernel<3><<<nblk(nsf, T), T, 0, st>>>(m, wmask);
   }
   if (tr && tr->on) tr->end(st);
-  return 3;
+  return 2;
 }
 
 }  // namespace dg
