@@ -515,8 +515,6 @@ __global__ void __launch_bounds__(kWarps * 32)
   const T* FR = pick<T>(m.rt.face64, m.rt.face32);
   const bool mat_vol = mode & kModeVol, mat_face = mode & kModeFace, do_rhs = mode & kModeRhs;
   const bool accum = mode & kModeAccum;
-  // volume terms already written by the moment kernel: faces only, load vector added
-  const bool skip_vol = mode & kModeSkipVol;
   const int base = m.elem_pstart[P], count = m.elem_pstart[P + 1] - base;
 
   for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < count; w += gridDim.x * blockDim.x) {
@@ -531,7 +529,7 @@ __global__ void __launch_bounds__(kWarps * 32)
       for (int j = 0; j < N; ++j) acc[i][j] = T(0);
     }
     const bool learned = m.lq_ok && m.lq_ok[e];
-    if ((mat_vol || do_rhs) && learned && !skip_vol) {
+    if ((mat_vol || do_rhs) && learned) {
       const T* LQ = pick<T>(m.lq64, m.lq32) + (size_t)e * 84;
       for (int r = 0; r < 28; ++r) {
         T xi[D];
@@ -570,7 +568,7 @@ __global__ void __launch_bounds__(kWarps * 32)
         }
       }
     }
-    if ((mat_vol || do_rhs) && !learned && !skip_vol) {
+    if ((mat_vol || do_rhs) && !learned) {
       for (int sub = m.eptr[e]; sub < m.eptr[e + 1]; ++sub) {
         T sv[SV];
 #pragma unroll
@@ -676,10 +674,7 @@ __global__ void __launch_bounds__(kWarps * 32)
     }
     if (do_rhs) {
 #pragma unroll
-      for (int i = 0; i < N; ++i) {
-        const T v = q.R * ctab[i] * racc[i];
-        rhs[m.dof_off[e] + i] = skip_vol ? rhs[m.dof_off[e] + i] + v : v;
-      }
+      for (int i = 0; i < N; ++i) rhs[m.dof_off[e] + i] = q.R * ctab[i] * racc[i];
     }
     if (mat_face) {
       for (int bk = m.row_ptr[e]; bk < m.row_ptr[e + 1]; ++bk) {

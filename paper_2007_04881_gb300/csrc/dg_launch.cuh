@@ -28,7 +28,7 @@ inline int launch_row_p(const DevMesh& m, int mode, T* vals, T* rhs, int sm_coun
   cudaStream_t st = lo.pst[P];
   const char* tn = sizeof(T) == 8 ? "f64" : "f32";
   int n = 0, kind = 0;
-  if constexpr (moment_volume_ok<D, P, T>()) {
+  if constexpr (TileCfg<D, P, T>::TPE != 1 && moment_volume_ok<D, P, T>()) {
     // the moment path needs the linearisation tables of the rule set
     if (lo.vol_moments && m.rt.lin32 && m.rt.lin64 && (mode & (kModeVol | kModeRhs))) {
       // volume terms through the moments, then the faces added by the row kernel

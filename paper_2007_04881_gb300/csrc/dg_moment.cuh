@@ -76,7 +76,7 @@ struct MomCfg {
 // whether the moment path serves (D, P, T): moments held in registers
 template <int D, int P, typename T>
 __host__ __device__ constexpr bool moment_volume_ok() {
-  return P >= 1 && P <= kPMaxLin && nmom<D>(2 * P) <= (sizeof(T) == 4 ? 96 : 56);
+  return P >= 2 && P <= kPMaxLin && nmom<D>(2 * P) <= (sizeof(T) == 4 ? 96 : 56);
 }
 
 template <int D, int P, typename T>
