@@ -184,6 +184,122 @@ __global__ void elem_geom_kernel(DevMesh m) {
   }
 }
 
+// 3D element records, one warp per element: an agglomerated polyhedron has
+// tens of tetrahedra and distinct vertices, so the lanes share the tetrahedra
+// (volume, centroid), the vertices (bounding box) and the vertex pairs
+// (diameter: FP32 prefilter, FP64 recheck within 1e-5 of the maximum), and
+// combine them with butterfly reductions in a fixed order.
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_min(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__global__ void elem_geom3d_warp_kernel(DevMesh m) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < m.ne; e += nw) {
+    double vol = 0.0, cen[3] = {0.0, 0.0, 0.0};
+    for (int t = m.eptr[e] + lane; t < m.eptr[e + 1]; t += 32) {
+      double P[4][3];
+      for (int i = 0; i < 4; ++i) {
+        const int v = m.eidx[4 * t + i];
+        for (int d = 0; d < 3; ++d) P[i][d] = m.X[d][v];
+      }
+      double u[3], v[3], w[3];
+      for (int d = 0; d < 3; ++d) {
+        u[d] = P[1][d] - P[0][d];
+        v[d] = P[2][d] - P[0][d];
+        w[d] = P[3][d] - P[0][d];
+      }
+      const double det = u[0] * (v[1] * w[2] - v[2] * w[1]) - u[1] * (v[0] * w[2] - v[2] * w[0]) +
+                         u[2] * (v[0] * w[1] - v[1] * w[0]);
+      const double tv = fabs(det) / 6.0;
+      vol += tv;
+      for (int d = 0; d < 3; ++d) cen[d] += tv * 0.25 * (P[0][d] + P[1][d] + P[2][d] + P[3][d]);
+    }
+    vol = warp_sum(vol);
+    for (int d = 0; d < 3; ++d) cen[d] = warp_sum(cen[d]) / vol;
+    const int ub = m.uvptr[e], ue = m.uvptr[e + 1];
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int i = ub + lane; i < ue; i += 32) {
+      const int vi = m.uvidx[i];
+      for (int d = 0; d < 3; ++d) {
+        const double x = m.X[d][vi];
+        lo[d] = fmin(lo[d], x);
+        hi[d] = fmax(hi[d], x);
+      }
+    }
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = warp_min(lo[d]);
+      hi[d] = warp_max(hi[d]);
+    }
+    float h2f = 0.f;
+    for (int i = ub; i < ue; ++i) {
+      const int vi = m.uvidx[i];
+      const float xi = (float)m.X[0][vi], yi = (float)m.X[1][vi], zi = (float)m.X[2][vi];
+      for (int j = i + 1 + lane; j < ue; j += 32) {
+        const int vj = m.uvidx[j];
+        const float dx = (float)m.X[0][vj] - xi, dy = (float)m.X[1][vj] - yi, dz = (float)m.X[2][vj] - zi;
+        h2f = fmaxf(h2f, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+      }
+    }
+    h2f = (float)warp_max((double)h2f);
+    const float cut = h2f * (1.0f - 1e-5f);
+    double h2 = 0.0;
+    for (int i = ub; i < ue; ++i) {
+      const int vi = m.uvidx[i];
+      const float xi = (float)m.X[0][vi], yi = (float)m.X[1][vi], zi = (float)m.X[2][vi];
+      for (int j = i + 1 + lane; j < ue; j += 32) {
+        const int vj = m.uvidx[j];
+        const float dx = (float)m.X[0][vj] - xi, dy = (float)m.X[1][vj] - yi, dz = (float)m.X[2][vj] - zi;
+        if (fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < cut) continue;
+        double s2 = 0.0;
+        for (int d = 0; d < 3; ++d) {
+          const double df = m.X[d][vj] - m.X[d][vi];
+          s2 += df * df;
+        }
+        h2 = fmax(h2, s2);
+      }
+    }
+    h2 = warp_max(h2);
+    if (lane == 0) {
+      for (int d = 0; d < 3; ++d) {
+        m.lo[d * m.ne + e] = lo[d];
+        m.L[d * m.ne + e] = hi[d] - lo[d];
+        m.cen[d * m.ne + e] = cen[d];
+      }
+      m.vol[e] = vol;
+      const double h = sqrt(h2);
+      m.h[e] = h;
+      const int pe = m.p[e];
+      m.pen[e] = m.a[e] * pe * pe / h;
+      constexpr int EV = elem_vals(3);
+      double rec[EV];
+      double box = 1.0;
+      for (int d = 0; d < 3; ++d) {
+        const double L = hi[d] - lo[d];
+        rec[d] = lo[d];
+        rec[3 + d] = L;
+        rec[6 + d] = 1.0 / L;
+        box *= L;
+      }
+      rec[9] = 1.0 / sqrt(box);
+      for (int k = 0; k < EV; ++k) {
+        m.eg64[(size_t)k * m.ne + e] = rec[k];
+        m.eg32[(size_t)k * m.ne + e] = (float)rec[k];
+      }
+    }
+  }
+}
+
 template <int D>
 __device__ __forceinline__ void sub_geom(const DevMesh& m, int wmask, int k) {
   const int e = m.sub_elem[k];
@@ -315,7 +431,7 @@ int launch_geometry(const DevMesh& m, cudaStream_t st, Tracer* tr, int wmask) {
     if (m.ne > 0) elem_geom_kernel<2><<<nblk(m.ne, T), T, 0, st>>>(m);
     if (nsf > 0) subface_geom_kernel<2><<<nblk(nsf, T), T, 0, st>>>(m, wmask);
   } else {
-    if (m.ne > 0) elem_geom_kernel<3><<<nblk(m.ne, T), T, 0, st>>>(m);
+    if (m.ne > 0) elem_geom3d_warp_kernel<<<nblk(m.ne * 32, T), T, 0, st>>>(m);
     if (nsf > 0) subface_geom_kernel<3><<<nblk(nsf, T), T, 0, st>>>(m, wmask);
   }
   if (tr && tr->on) tr->end(st);
