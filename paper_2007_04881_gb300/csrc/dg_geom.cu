@@ -202,8 +202,13 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
-__global__ void elem_geom3d_warp_kernel(DevMesh m) {
-  const int lane = threadIdx.x & 31;
+constexpr int kGeomWarps = 4;    // warps per block of the 3D element kernel
+constexpr int kGeomVerts = 128;  // distinct vertices staged in shared memory per element
+
+__global__ void __launch_bounds__(kGeomWarps * 32) elem_geom3d_warp_kernel(DevMesh m) {
+  // FP32 copies of the element's distinct vertices for the diameter prefilter
+  __shared__ float sv[kGeomWarps][3][kGeomVerts];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < m.ne; e += nw) {
     double vol = 0.0, cen[3] = {0.0, 0.0, 0.0};
@@ -227,40 +232,42 @@ __global__ void elem_geom3d_warp_kernel(DevMesh m) {
     }
     vol = warp_sum(vol);
     for (int d = 0; d < 3; ++d) cen[d] = warp_sum(cen[d]) / vol;
-    const int ub = m.uvptr[e], ue = m.uvptr[e + 1];
+    const int ub = m.uvptr[e], ue = m.uvptr[e + 1], nu = ue - ub;
+    const bool staged = nu <= kGeomVerts;
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-    for (int i = ub + lane; i < ue; i += 32) {
-      const int vi = m.uvidx[i];
+    for (int i = lane; i < nu; i += 32) {
+      const int vi = m.uvidx[ub + i];
       for (int d = 0; d < 3; ++d) {
         const double x = m.X[d][vi];
         lo[d] = fmin(lo[d], x);
         hi[d] = fmax(hi[d], x);
+        if (staged) sv[wib][d][i] = (float)x;
       }
     }
     for (int d = 0; d < 3; ++d) {
       lo[d] = warp_min(lo[d]);
       hi[d] = warp_max(hi[d]);
     }
+    __syncwarp();
+    // FP32 coordinate d of distinct vertex i (staged copy, or the vertex array)
+    auto xf = [&](int d, int i) -> float { return staged ? sv[wib][d][i] : (float)m.X[d][m.uvidx[ub + i]]; };
     float h2f = 0.f;
-    for (int i = ub; i < ue; ++i) {
-      const int vi = m.uvidx[i];
-      const float xi = (float)m.X[0][vi], yi = (float)m.X[1][vi], zi = (float)m.X[2][vi];
-      for (int j = i + 1 + lane; j < ue; j += 32) {
-        const int vj = m.uvidx[j];
-        const float dx = (float)m.X[0][vj] - xi, dy = (float)m.X[1][vj] - yi, dz = (float)m.X[2][vj] - zi;
+    for (int i = 0; i < nu; ++i) {
+      const float xi = xf(0, i), yi = xf(1, i), zi = xf(2, i);
+      for (int j = i + 1 + lane; j < nu; j += 32) {
+        const float dx = xf(0, j) - xi, dy = xf(1, j) - yi, dz = xf(2, j) - zi;
         h2f = fmaxf(h2f, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
       }
     }
     h2f = (float)warp_max((double)h2f);
     const float cut = h2f * (1.0f - 1e-5f);
     double h2 = 0.0;
-    for (int i = ub; i < ue; ++i) {
-      const int vi = m.uvidx[i];
-      const float xi = (float)m.X[0][vi], yi = (float)m.X[1][vi], zi = (float)m.X[2][vi];
-      for (int j = i + 1 + lane; j < ue; j += 32) {
-        const int vj = m.uvidx[j];
-        const float dx = (float)m.X[0][vj] - xi, dy = (float)m.X[1][vj] - yi, dz = (float)m.X[2][vj] - zi;
+    for (int i = 0; i < nu; ++i) {
+      const float xi = xf(0, i), yi = xf(1, i), zi = xf(2, i);
+      for (int j = i + 1 + lane; j < nu; j += 32) {
+        const float dx = xf(0, j) - xi, dy = xf(1, j) - yi, dz = xf(2, j) - zi;
         if (fmaf(dz, dz, fmaf(dy, dy, dx * dx)) < cut) continue;
+        const int vi = m.uvidx[ub + i], vj = m.uvidx[ub + j];
         double s2 = 0.0;
         for (int d = 0; d < 3; ++d) {
           const double df = m.X[d][vj] - m.X[d][vi];
@@ -270,6 +277,7 @@ __global__ void elem_geom3d_warp_kernel(DevMesh m) {
       }
     }
     h2 = warp_max(h2);
+    __syncwarp();  // the staged copy is reused by the next element
     if (lane == 0) {
       for (int d = 0; d < 3; ++d) {
         m.lo[d * m.ne + e] = lo[d];
@@ -431,7 +439,7 @@ int launch_geometry(const DevMesh& m, cudaStream_t st, Tracer* tr, int wmask) {
     if (m.ne > 0) elem_geom_kernel<2><<<nblk(m.ne, T), T, 0, st>>>(m);
     if (nsf > 0) subface_geom_kernel<2><<<nblk(nsf, T), T, 0, st>>>(m, wmask);
   } else {
-    if (m.ne > 0) elem_geom3d_warp_kernel<<<nblk(m.ne * 32, T), T, 0, st>>>(m);
+    if (m.ne > 0) elem_geom3d_warp_kernel<<<nblk(m.ne * 32, kGeomWarps * 32), kGeomWarps * 32, 0, st>>>(m);
     if (nsf > 0) subface_geom_kernel<3><<<nblk(nsf, T), T, 0, st>>>(m, wmask);
   }
   if (tr && tr->on) tr->end(st);
