@@ -37,14 +37,17 @@ __host__ __device__ constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b *
 // Register-tile geometry of the element kernel for (D, P): each thread owns a
 // TM x TM tile of the (padded) n x n block; G elements share a warp.  TM = n
 // (one tile) selects the one-thread-per-element kernel.  The FP32 table was
-// picked by measurement on the 65k-cell 2D workload: degree 2 runs a whole
+// picked by measurement: on the 65k-cell 2D workload degree 2 runs a whole
 // element per thread (36 accumulators) and degree 4 uses 8 x 8 tiles, 4
-// threads per element; other tile sizes and chunk widths measured slower.
+// threads per element; on the 3D workload degree 3 (whose volume terms take
+// the moment launch) uses 4 x 4 tiles, 25 threads per element; other tile
+// sizes and chunk widths measured slower.
 template <int D, int P, typename T = float>
 struct TileCfg {
   static constexpr int N = nbasis(D, P);
   static constexpr int TM = sizeof(T) == 4 && D == 2 && P == 2   ? 6
                             : sizeof(T) == 4 && D == 2 && P == 4 ? 8
+                            : sizeof(T) == 4 && D == 3 && P == 3 ? 4
                             : D == 2 ? (P <= 2 ? 3 : P == 3 ? 5 : P == 4 ? 4 : 7)
                                      : (P == 1 ? 4 : P <= 3 ? 5 : 7);
   static constexpr int TR = (N + TM - 1) / TM;
