@@ -519,11 +519,35 @@ __global__ void __launch_bounds__(kWarps * 32)
   const bool mat_vol = mode & kModeVol, mat_face = mode & kModeFace, do_rhs = mode & kModeRhs;
   const bool accum = mode & kModeAccum;
   const int base = m.elem_pstart[P], count = m.elem_pstart[P + 1] - base;
-
-  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < count; w += gridDim.x * blockDim.x) {
+  // two threads per element: part 0 the diagonal block and the load vector
+  // (volume and own faces), part 1 the off-diagonal blocks of the row; they
+  // write disjoint blocks
+  for (int w2 = blockIdx.x * blockDim.x + threadIdx.x; w2 < 2 * count; w2 += gridDim.x * blockDim.x) {
+    const int w = w2 >> 1, part = w2 & 1;
     const int e = m.elem_perm[base + w];
     ElemPar<D, T> q;
     load_elem_par<D, T>(m, e, q);
+    if (part == 1) {
+      if (mat_face) {
+        for (int bk = m.row_ptr[e]; bk < m.row_ptr[e + 1]; ++bk) {
+          const int it = m.blk_if[bk];
+          if (it < 0) continue;
+          const int k = m.col[bk];
+          const int se = m.if_e0[it] == e ? 0 : 1;
+          const int64_t off = m.blk_off[bk];
+          switch (m.p[k]) {
+            case 1: lane_offdiag<D, P, 1, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
+            case 2: lane_offdiag<D, P, 2, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
+            case 3: lane_offdiag<D, P, 3, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
+            case 4: lane_offdiag<D, P, 4, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
+            case 5: if constexpr (D == 2) lane_offdiag<D, P, 5, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
+            case 6: if constexpr (D == 2) lane_offdiag<D, P, 6, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
+            default: break;
+          }
+        }
+      }
+      continue;
+    }
     T acc[N][N], racc[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -678,24 +702,6 @@ __global__ void __launch_bounds__(kWarps * 32)
     if (do_rhs) {
 #pragma unroll
       for (int i = 0; i < N; ++i) rhs[m.dof_off[e] + i] = q.R * ctab[i] * racc[i];
-    }
-    if (mat_face) {
-      for (int bk = m.row_ptr[e]; bk < m.row_ptr[e + 1]; ++bk) {
-        const int it = m.blk_if[bk];
-        if (it < 0) continue;
-        const int k = m.col[bk];
-        const int se = m.if_e0[it] == e ? 0 : 1;
-        const int64_t off = m.blk_off[bk];
-        switch (m.p[k]) {
-          case 1: lane_offdiag<D, P, 1, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
-          case 2: lane_offdiag<D, P, 2, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
-          case 3: lane_offdiag<D, P, 3, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
-          case 4: lane_offdiag<D, P, 4, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
-          case 5: if constexpr (D == 2) lane_offdiag<D, P, 5, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
-          case 6: if constexpr (D == 2) lane_offdiag<D, P, 6, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
-          default: break;
-        }
-      }
     }
   }
 }
