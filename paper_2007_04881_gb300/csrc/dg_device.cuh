@@ -519,11 +519,14 @@ __global__ void __launch_bounds__(kWarps * 32)
   const bool mat_vol = mode & kModeVol, mat_face = mode & kModeFace, do_rhs = mode & kModeRhs;
   const bool accum = mode & kModeAccum;
   const int base = m.elem_pstart[P], count = m.elem_pstart[P + 1] - base;
-  // two threads per element: part 0 the diagonal block and the load vector
-  // (volume and own faces), part 1 the off-diagonal blocks of the row; they
-  // write disjoint blocks
-  for (int w2 = blockIdx.x * blockDim.x + threadIdx.x; w2 < 2 * count; w2 += gridDim.x * blockDim.x) {
-    const int w = w2 >> 1, part = w2 & 1;
+  // two threads per element, in different warps (each warp takes one part of
+  // 32 elements): part 0 the diagonal block and the load vector (volume and
+  // own faces), part 1 the off-diagonal blocks of the row; they write
+  // disjoint blocks
+  const int span = (count + 31) / 32 * 64;
+  for (int w2 = blockIdx.x * blockDim.x + threadIdx.x; w2 < span; w2 += gridDim.x * blockDim.x) {
+    const int part = (w2 >> 5) & 1, w = (w2 >> 6) * 32 + (w2 & 31);
+    if (w >= count) continue;
     const int e = m.elem_perm[base + w];
     ElemPar<D, T> q;
     load_elem_par<D, T>(m, e, q);

@@ -58,7 +58,7 @@ inline int launch_row_p(const DevMesh& m, int mode, T* vals, T* rhs, int sm_coun
   if constexpr (TileCfg<D, P, T>::TPE == 1) {
     // one element per thread, no staging
     auto k = row_lane_kernel<D, P, T>;
-    const int grid = resident_grid(k, 0, sm_count, (2 * count + kWarps * 32 - 1) / (kWarps * 32), lo.occ_cap);
+    const int grid = resident_grid(k, 0, sm_count, ((count + 31) / 32 * 64 + kWarps * 32 - 1) / (kWarps * 32), lo.occ_cap);
     k<<<grid, kWarps * 32, 0, st>>>(m, mode, vals, rhs);
   } else {
     using SM = RowSmem<D, P, T>;
