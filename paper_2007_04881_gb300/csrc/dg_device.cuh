@@ -800,10 +800,6 @@ __global__ void __launch_bounds__(kWarps * 32)
   const bool accum = mode & kModeAccum;
   // volume terms already written by the moment kernel: faces only, load vector added
   const bool skip_vol = mode & kModeSkipVol;
-  // the faces-only work split in two launches: own faces (diagonal block,
-  // load vector) and the off-diagonal blocks
-  const bool slots_only = mode & kModeSlotsOnly;
-  const bool do_slots = mat_face && !(mode & kModeNoSlots);
   // with b = 0 and c = 0 the Phi row of a volume point carries no matrix term
   const bool no_adv = m.pb.b[0] == 0.0 && m.pb.b[1] == 0.0 && m.pb.b[2] == 0.0 && m.pb.c == 0.0;
   const int base = m.elem_pstart[P], count = m.elem_pstart[P + 1] - base;
@@ -969,7 +965,7 @@ __global__ void __launch_bounds__(kWarps * 32)
     }
 
     // ---- own-face points (diagonal-block face terms, boundary load terms)
-    if ((mat_face || do_rhs) && !slots_only) {
+    if (mat_face || do_rhs) {
       for (int ch = 0; ch < nfch; ++ch) {
         for (int idx = lane; idx < G * C; idx += 32) {
           const int g = idx / C, c = idx - g * C, qv = ch * C + c;
@@ -1066,7 +1062,7 @@ __global__ void __launch_bounds__(kWarps * 32)
     }
 
     // ---- write the diagonal block and the load vector
-    if (active && !slots_only) {
+    if (active) {
       const int e = PIv[g_me * PI + kPiElem];
       const T Re = PTv[g_me * PT + X + kPtR];
       if (mat_vol || mat_face) {
@@ -1099,7 +1095,7 @@ __global__ void __launch_bounds__(kWarps * 32)
     }
 
     // ---- off-diagonal blocks of the row: one per neighbour (interface)
-    if (do_slots) {
+    if (mat_face) {
       for (int sl = 0; sl < nslot; ++sl) {
         __syncwarp();
         if (lane < G) {

@@ -165,10 +165,6 @@ struct dg_ctx {
   // forked streams for concurrent per-degree launches (created on first use)
   cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};
   cudaEvent_t fork = nullptr, join[4] = {nullptr, nullptr, nullptr, nullptr};
-  // the off-diagonal launches of the moment path, one stream per side stream
-  // and a fork / join event pair per degree
-  cudaStream_t side2[4] = {nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t fork2[9] = {}, join2[9] = {};
   ~dg_ctx() {
     for (auto& r : recs) {
       cudaEventDestroy(r.ev0);
@@ -177,11 +173,6 @@ struct dg_ctx {
     for (int i = 0; i < 4; ++i) {
       if (side[i]) cudaStreamDestroy(side[i]);
       if (join[i]) cudaEventDestroy(join[i]);
-      if (side2[i]) cudaStreamDestroy(side2[i]);
-    }
-    for (int i = 0; i < 9; ++i) {
-      if (fork2[i]) cudaEventDestroy(fork2[i]);
-      if (join2[i]) cudaEventDestroy(join2[i]);
     }
     if (fork) cudaEventDestroy(fork);
   }
@@ -819,8 +810,6 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P, const int8_t* owned = nullp
         }
         P.flops[0][d->p[e]] += 2.0 * fma;
         P.words[0][d->p[e]] += w;
-        P.flops[4][d->p[e]] += 2.0 * fma;  // the off-diagonal launch of a split faces pass
-        P.words[4][d->p[e]] += w;
       }
     }
     // The launches of the moment path: the volume launch (kind 2) is credited
@@ -870,8 +859,6 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P, const int8_t* owned = nullp
     for (int pp = 0; pp <= 8; ++pp) {
       P.flops[1][pp] += P.flops[0][pp];
       P.words[1][pp] += P.words[0][pp];
-      P.flops[3][pp] = P.flops[1][pp] - P.flops[4][pp];  // own faces of a split faces pass
-      P.words[3][pp] = P.words[1][pp] - P.words[4][pp];
       P.mom_pt[pp] = 2.0 * pt_ops[pp];
     }
   }
@@ -1147,22 +1134,12 @@ static int run_assembly(dg_ctx* ctx, const dg_mesh* mesh, int prec, int mode, vo
       for (int i = 0; i < 4; ++i) {
         DG_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side[i], cudaStreamNonBlocking));
         DG_CUDA_TRY(cudaEventCreateWithFlags(&ctx->join[i], cudaEventDisableTiming));
-        DG_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side2[i], cudaStreamNonBlocking));
-      }
-      for (int i = 0; i < 9; ++i) {
-        DG_CUDA_TRY(cudaEventCreateWithFlags(&ctx->fork2[i], cudaEventDisableTiming));
-        DG_CUDA_TRY(cudaEventCreateWithFlags(&ctx->join2[i], cudaEventDisableTiming));
       }
     }
     DG_CUDA_TRY(cudaEventRecord(ctx->fork, st));
     for (int i = 0; i < 4; ++i) DG_CUDA_TRY(cudaStreamWaitEvent(ctx->side[i], ctx->fork, 0));
     // highest degrees (longest launches) first on their own streams
-    for (int p = 1; p < 9; ++p) {
-      lo.pst[p] = ctx->side[(8 - p) % 4];
-      lo.pst2[p] = ctx->side2[(8 - p) % 4];
-      lo.fork2[p] = ctx->fork2[p];
-      lo.join2[p] = ctx->join2[p];
-    }
+    for (int p = 1; p < 9; ++p) lo.pst[p] = ctx->side[(8 - p) % 4];
   }
   int n = 0;
   if (prec == DG_PREC_FP64) {

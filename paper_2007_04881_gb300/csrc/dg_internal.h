@@ -137,8 +137,6 @@ enum : int {
   kModeRhs = 4,    // load vector
   kModeAccum = 8,  // add to the diagonal block instead of overwriting it
   kModeSkipVol = 16,  // volume terms done by the moment kernel: faces only, load vector added
-  kModeSlotsOnly = 32,  // only the off-diagonal blocks (no own faces, no diagonal / load-vector writes)
-  kModeNoSlots = 64,    // no off-diagonal blocks
 };
 
 // Optional per-launch timing: CUDA events recorded on the launch stream
@@ -152,10 +150,7 @@ struct LaunchRec {
   cudaEvent_t ev0, ev1;
 };
 
-// kinds: 0 row kernel (volume and faces), 1 its faces-only launch, 2 the
-// moment volume launch, 3 the own-face launch and 4 the off-diagonal launch
-// when the faces-only launch is split in two
-constexpr int kKinds = 5;
+constexpr int kKinds = 3;
 struct Tracer {
   bool on = false;
   LaunchRec* recs = nullptr;  // capacity cap, filled from n
@@ -183,11 +178,6 @@ int launch_geometry(const DevMesh& m, cudaStream_t st, Tracer* tr = nullptr, int
 struct LaunchOpts {
   int occ_cap = 0;
   bool vol_moments = true;  // volume blocks through Legendre-product moments where supported
-  // moment path: off-diagonal blocks of degree p on their own stream, forked
-  // from pst[p] before the volume launch and joined after the own-face launch
-  cudaStream_t pst2[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t fork2[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t join2[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   cudaStream_t pst[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 

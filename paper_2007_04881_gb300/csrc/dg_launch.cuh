@@ -21,21 +21,6 @@ inline int resident_grid(K kernel, size_t smem, int sm_count, int want_blocks, i
   return want_blocks < g ? want_blocks : g;
 }
 
-// the row kernel of degree P (warp tiles) with the given mode, on stream st
-template <int D, int P, typename T>
-inline void launch_tiles_mode(const DevMesh& m, int mode, T* vals, T* rhs, int count, int sm_count,
-                              const LaunchOpts& lo, cudaStream_t st) {
-  if constexpr (TileCfg<D, P, T>::TPE != 1) {
-    using SM = RowSmem<D, P, T>;
-    constexpr int G = TileCfg<D, P, T>::G;
-    const int ntiles = (count + G - 1) / G;
-    const size_t smem = SM::total(kWarps, m.nmax);
-    auto k = row_kernel<D, P, T>;
-    const int grid = resident_grid(k, smem, sm_count, (ntiles + kWarps - 1) / kWarps, lo.occ_cap);
-    k<<<grid, kWarps * 32, smem, st>>>(m, mode, vals, rhs);
-  }
-}
-
 template <int D, int P, typename T>
 inline int launch_row_p(const DevMesh& m, int mode, T* vals, T* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr) {
   const int count = m.elem_pstart[P + 1] - m.elem_pstart[P];
@@ -49,23 +34,6 @@ inline int launch_row_p(const DevMesh& m, int mode, T* vals, T* rhs, int sm_coun
       // volume terms through the moments, then the faces added by the row kernel
       using MC = MomCfg<D, P, T>;
       static_assert(MC::total <= 227 * 1024, "moment kernel shared memory exceeds 227 KB");
-      // the off-diagonal blocks need no volume terms: on their own stream,
-      // concurrent with the volume launch
-      const bool split = (mode & kModeFace) && lo.pst2[P] && lo.fork2[P] && lo.join2[P];
-      if (split) {
-        cudaEventRecord(lo.fork2[P], st);
-        cudaStreamWaitEvent(lo.pst2[P], lo.fork2[P], 0);
-        if (tr && tr->on) {
-          char name[48];
-          snprintf(name, sizeof name, "row%dd_offd_p%d_%s", D, P, tn);
-          tr->begin(name, 4, P, sizeof(T), lo.pst2[P]);
-        }
-        launch_tiles_mode<D, P, T>(m, kModeFace | kModeSkipVol | kModeSlotsOnly, vals, rhs, count, sm_count, lo,
-                                   lo.pst2[P]);
-        if (tr && tr->on) tr->end(lo.pst2[P]);
-        cudaEventRecord(lo.join2[P], lo.pst2[P]);
-        ++n;
-      }
       if (tr && tr->on) {
         char name[48];
         snprintf(name, sizeof name, "row%dd_vol_p%d_%s", D, P, tn);
@@ -77,23 +45,9 @@ inline int launch_row_p(const DevMesh& m, int mode, T* vals, T* rhs, int sm_coun
       k<<<grid, kWarps * 32, MC::total, st>>>(m, mode & (kModeVol | kModeRhs | kModeAccum), vals, rhs);
       if (tr && tr->on) tr->end(st);
       ++n;
-      if (!(mode & (kModeFace | kModeRhs))) {
-        if (split) cudaStreamWaitEvent(st, lo.join2[P], 0);
-        return n;
-      }
-      mode = (mode & ~kModeVol) | kModeSkipVol | ((mode & kModeVol) ? kModeAccum : 0) | (split ? kModeNoSlots : 0);
-      kind = split ? 3 : 1;
-      if (split) {
-        if (tr && tr->on) {
-          char name[48];
-          snprintf(name, sizeof name, "row%dd_p%d_%s", D, P, tn);
-          tr->begin(name, kind, P, sizeof(T), st);
-        }
-        launch_tiles_mode<D, P, T>(m, mode, vals, rhs, count, sm_count, lo, st);
-        if (tr && tr->on) tr->end(st);
-        cudaStreamWaitEvent(st, lo.join2[P], 0);
-        return n + 1;
-      }
+      if (!(mode & (kModeFace | kModeRhs))) return n;
+      mode = (mode & ~kModeVol) | kModeSkipVol | ((mode & kModeVol) ? kModeAccum : 0);
+      kind = 1;
     }
   }
   if (tr && tr->on) {
