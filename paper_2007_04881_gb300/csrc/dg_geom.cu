@@ -426,6 +426,361 @@ __global__ void subface_geom_kernel(DevMesh m, int wmask) {
     face_geom<D>(m, wmask, t - m.nsub);
 }
 
+// ---------------------------------------------------------------------------
+// Reduced-precision geometry (the FP32 and tensor-core forms).
+//
+// Those forms need the records to FP32 accuracy relative to each element's
+// own size.  What costs digits in FP32 is only the difference of two absolute
+// coordinates (x - lo, an edge vector) when the element is small against its
+// distance from the origin.  So every coordinate is split once into an
+// unevaluated float pair x = hi + lo (48 significant bits); a difference of
+// two pairs, (a.hi - b.hi) + (a.lo - b.lo), then has FP32 relative accuracy,
+// and everything else is FP32 arithmetic.  No FP64 arithmetic remains past
+// the split, which matters on a part whose FP64 rate is 1/64 of its FP32 rate.
+//
+// The records are built to agree with the rounded FP64 records, not only to
+// be accurate: the box is spanned by the pairs of its extreme vertices, a
+// vertex maps to 2 (x - lo) / L - 1 in two-float arithmetic with one final
+// rounding (the extreme vertices land on -1 and +1 exactly), and sub-simplex
+// and face edges are differences of the rounded vertex coordinates, as in the
+// FP64 records.  The map's accuracy matters: a degree-p basis function has a
+// relative slope of about p (p + 1) / 2 at the box's edge.
+// That keeps boundary points exactly on the boundary, where the Dirichlet
+// data of Eq. (2.5) is taken against a penalty of order a p^2 / h.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float pdiff(float2 a, float2 b) { return (a.x - b.x) + (a.y - b.y); }
+
+// a - b for pairs as an unevaluated sum (hi, lo), |lo| <= ulp(hi) / 2
+// (Knuth's TwoSum on the high parts, then Dekker's FastTwoSum)
+__device__ __forceinline__ float2 pdiff2(float2 a, float2 b) {
+  const float s = a.x - b.x;
+  const float bb = s - a.x;
+  const float t = ((a.x - (s - bb)) + (-b.x - bb)) + (a.y - b.y);
+  const float h = s + t;
+  return make_float2(h, t - (h - s));
+}
+
+// bounding-box coordinate 2 (x - lo) / L - 1 of the pair x in a box with
+// lower corner lo and extent L (pairs), iL = 1 / L.hi.  The quotient is
+// carried in two floats (a product, then one correction from the exact FMA
+// remainder) and 2q - 1 is formed error-free, so the single final rounding
+// leaves it as accurate as the rounded FP64 value; x = lo gives -1 and
+// x - lo = L gives +1 exactly.
+__device__ __forceinline__ float xi_pair(float2 x, float2 lo, float2 L, float iL) {
+  const float2 a = pdiff2(x, lo);
+  const float q1 = a.x * iL;
+  const float q2 = (fmaf(-q1, L.x, a.x) + (a.y - q1 * L.y)) * iL;
+  const float t = 2.f * q1, u = t - 1.f;
+  const float bv = u - t;
+  const float eu = (t - (u - bv)) + (-1.f - bv);
+  return u + (eu + 2.f * q2);
+}
+
+__device__ __forceinline__ float2 xpair(const DevMesh& m, int d, int v) { return m.xs2[(size_t)d * m.nv + v]; }
+
+// (value, index) minimum / maximum over the warp; ties go to the smaller
+// index, so every lane ends with the same pair
+__device__ __forceinline__ void warp_argmin(float& v, int& i) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+    if (ov < v || (ov == v && oi < i)) {
+      v = ov;
+      i = oi;
+    }
+  }
+}
+__device__ __forceinline__ void warp_argmax(float& v, int& i) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, i, o);
+    if (ov > v || (ov == v && oi < i)) {
+      v = ov;
+      i = oi;
+    }
+  }
+}
+__device__ __forceinline__ float warp_maxf(float v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__global__ void vertex_split_kernel(DevMesh m) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m.dim * m.nv) return;
+  const int d = i / m.nv;
+  const double x = m.X[d][i - d * m.nv];
+  const float hi = __double2float_rn(x);
+  m.xs2[i] = make_float2(hi, __double2float_rn(x - (double)hi));
+}
+
+// element record and reduced-precision scratch: lo = the pairs of the box's
+// lower corner, L its extent (pairs), h2 the squared diameter
+template <int D>
+__device__ __forceinline__ void write_elem_f32(const DevMesh& m, int e, const float2* lo, const float2* L, float h2) {
+  constexpr int EV = elem_vals(D);
+  float rec[EV], gx[EV];
+  float box = 1.f;
+  for (int d = 0; d < D; ++d) {
+    rec[d] = lo[d].x;  // the pair's high part is the rounded coordinate
+    rec[D + d] = L[d].x;
+    rec[2 * D + d] = 1.f / L[d].x;
+    box *= L[d].x;
+    gx[d] = lo[d].x;
+    gx[D + d] = lo[d].y;
+    gx[2 * D + d] = L[d].y;
+  }
+  rec[3 * D] = 1.f / sqrtf(box);
+  const int pe = m.p[e];
+  gx[3 * D] = (float)m.a[e] * (float)(pe * pe) / sqrtf(h2);
+  for (int k = 0; k < EV; ++k) {
+    m.eg32[(size_t)k * m.ne + e] = rec[k];
+    m.gx32[(size_t)k * m.ne + e] = gx[k];
+  }
+}
+
+// 2D element e with k loop vertices starting at b; u(i) = vertex i relative
+// to vertex 0.  NU > 0: loops run to the compile-time bound NU (k <= NU), so
+// u indexes registers; NU == 0: runtime loops.  Writes the element record and
+// the k sub-triangle records (centroid, v_i, v_{i+1}) of Sec. 3.
+template <int NU, class U>
+__device__ __forceinline__ void elem2d_f32_body(const DevMesh& m, int e, int b, int k, U u) {
+  const int n = NU ? NU : k;
+  float lo[2] = {0.f, 0.f}, hi[2] = {0.f, 0.f};
+  int il[2] = {0, 0}, ih[2] = {0, 0};
+  float a2 = 0.f, cx = 0.f, cy = 0.f, h2 = 0.f;
+  // vertex 0 is the origin, so the shoelace terms that touch it vanish
+#pragma unroll
+  for (int i = 1; i < n; ++i) {
+    if (NU && i >= k) break;
+    const float2 p = u(i);
+    if (p.x < lo[0]) lo[0] = p.x, il[0] = i;
+    if (p.x > hi[0]) hi[0] = p.x, ih[0] = i;
+    if (p.y < lo[1]) lo[1] = p.y, il[1] = i;
+    if (p.y > hi[1]) hi[1] = p.y, ih[1] = i;
+    h2 = fmaxf(h2, fmaf(p.x, p.x, p.y * p.y));
+    if (i + 1 < n && i + 1 < k) {
+      const float2 q = u(i + 1 < n ? i + 1 : i);
+      const float cr = p.x * q.y - q.x * p.y;
+      a2 += cr;
+      cx += (p.x + q.x) * cr;
+      cy += (p.y + q.y) * cr;
+    }
+#pragma unroll
+    for (int j = i + 1; j < n; ++j) {
+      if (NU && j >= k) break;
+      const float2 q = u(j);
+      const float dx = q.x - p.x, dy = q.y - p.y;
+      h2 = fmaxf(h2, fmaf(dx, dx, dy * dy));
+    }
+  }
+  const float i3 = 1.f / (3.f * a2);
+  cx *= i3;
+  cy *= i3;
+  float2 lp[2], L[2];
+  float iL[2];
+  for (int d = 0; d < 2; ++d) {
+    lp[d] = xpair(m, d, m.eidx[b + il[d]]);
+    L[d] = pdiff2(xpair(m, d, m.eidx[b + ih[d]]), lp[d]);
+    iL[d] = 1.f / L[d].x;
+  }
+  write_elem_f32<2>(m, e, lp, L, h2);
+  // the fan apex: any interior point gives the same polygon, so its own
+  // rounding does not matter; the vertices are mapped as accurately as FP64
+  const float xc = 2.f * ((cx - lo[0]) * iL[0]) - 1.f, yc = 2.f * ((cy - lo[1]) * iL[1]) - 1.f;
+  const int v0 = m.eidx[b];
+  const float2 q0x = xpair(m, 0, v0), q0y = xpair(m, 1, v0);
+  const float z0x = xi_pair(q0x, lp[0], L[0], iL[0]), z0y = xi_pair(q0y, lp[1], L[1], iL[1]);
+  float2 px = q0x, py = q0y;
+  float zx = z0x, zy = z0y;
+  const size_t ns = m.nsub;
+#pragma unroll
+  for (int i = 0; i < n; ++i) {
+    if (NU && i >= k) break;
+    const bool wrap = i + 1 >= k;
+    float2 qx = q0x, qy = q0y;
+    float wx = z0x, wy = z0y;
+    if (!wrap) {
+      const int v = m.eidx[b + i + 1];
+      qx = xpair(m, 0, v);
+      qy = xpair(m, 1, v);
+      wx = xi_pair(qx, lp[0], L[0], iL[0]);
+      wy = xi_pair(qy, lp[1], L[1], iL[1]);
+    }
+    // twice the area of (c, v_i, v_{i+1}) = |(v_i - c) x (v_{i+1} - v_i)|
+    const float2 p = u(i);
+    const float ax = p.x - cx, ay = p.y - cy, ex = pdiff(qx, px), ey = pdiff(qy, py);
+    float* o = m.sg32 + b + i;
+    o[0] = xc;
+    o[ns] = yc;
+    o[2 * ns] = zx - xc;
+    o[3 * ns] = zy - yc;
+    o[4 * ns] = wx - xc;
+    o[5 * ns] = wy - yc;
+    o[6 * ns] = fabsf(ax * ey - ay * ex);
+    px = qx;
+    py = qy;
+    zx = wx;
+    zy = wy;
+  }
+}
+
+__global__ void elem_geom2d_f32_kernel(DevMesh m) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m.ne) return;
+  const int b = m.eptr[e], k = m.eptr[e + 1] - b;
+  const int v0 = m.eidx[b];
+  const float2 r0 = xpair(m, 0, v0), r1 = xpair(m, 1, v0);
+  constexpr int KV = 16;
+  if (k <= KV) {
+    float ux[KV], uy[KV];
+    ux[0] = uy[0] = 0.f;
+#pragma unroll
+    for (int i = 1; i < KV; ++i)
+      if (i < k) {
+        const int v = m.eidx[b + i];
+        ux[i] = pdiff(xpair(m, 0, v), r0);
+        uy[i] = pdiff(xpair(m, 1, v), r1);
+      }
+    elem2d_f32_body<KV>(m, e, b, k, [&](int i) { return make_float2(ux[i], uy[i]); });
+  } else {
+    elem2d_f32_body<0>(m, e, b, k, [&](int i) {
+      const int v = m.eidx[b + i];
+      return make_float2(pdiff(xpair(m, 0, v), r0), pdiff(xpair(m, 1, v), r1));
+    });
+  }
+}
+
+// 3D, one warp per element: the distinct vertices relative to the first one
+// (box, diameter), then the element's tetrahedra (sub-simplex records)
+__global__ void __launch_bounds__(kGeomWarps * 32) elem_geom3d_f32_kernel(DevMesh m) {
+  __shared__ float sv[kGeomWarps][3][kGeomVerts];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; e < m.ne; e += nw) {
+    const int ub = m.uvptr[e], nu = m.uvptr[e + 1] - ub;
+    const bool staged = nu <= kGeomVerts;
+    const int vr = m.uvidx[ub];
+    float2 r[3];
+    for (int d = 0; d < 3; ++d) r[d] = xpair(m, d, vr);
+    // distinct vertex 0 is the origin: (0, 0) is a valid start on every lane
+    float lo[3] = {0.f, 0.f, 0.f}, hi[3] = {0.f, 0.f, 0.f};
+    int il[3] = {0, 0, 0}, ih[3] = {0, 0, 0};
+    for (int i = lane; i < nu; i += 32) {
+      const int v = m.uvidx[ub + i];
+      for (int d = 0; d < 3; ++d) {
+        const float x = pdiff(xpair(m, d, v), r[d]);
+        if (x < lo[d]) lo[d] = x, il[d] = i;
+        if (x > hi[d]) hi[d] = x, ih[d] = i;
+        if (staged) sv[wib][d][i] = x;
+      }
+    }
+    for (int d = 0; d < 3; ++d) {
+      warp_argmin(lo[d], il[d]);
+      warp_argmax(hi[d], ih[d]);
+    }
+    __syncwarp();
+    auto xf = [&](int d, int i) -> float { return staged ? sv[wib][d][i] : pdiff(xpair(m, d, m.uvidx[ub + i]), r[d]); };
+    float h2 = 0.f;
+    for (int i = 0; i < nu; ++i) {
+      const float xi = xf(0, i), yi = xf(1, i), zi = xf(2, i);
+      for (int j = i + 1 + lane; j < nu; j += 32) {
+        const float dx = xf(0, j) - xi, dy = xf(1, j) - yi, dz = xf(2, j) - zi;
+        h2 = fmaxf(h2, fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
+      }
+    }
+    h2 = warp_maxf(h2);
+    __syncwarp();  // the staged copy is reused by the next element
+    float2 lp[3], L[3];
+    float iL[3];
+    for (int d = 0; d < 3; ++d) {
+      lp[d] = xpair(m, d, m.uvidx[ub + il[d]]);
+      L[d] = pdiff2(xpair(m, d, m.uvidx[ub + ih[d]]), lp[d]);
+      iL[d] = 1.f / L[d].x;
+    }
+    const size_t ns = m.nsub;
+    for (int t = m.eptr[e] + lane; t < m.eptr[e + 1]; t += 32) {
+      float2 P[4][3];
+      for (int i = 0; i < 4; ++i) {
+        const int v = m.eidx[4 * t + i];
+        for (int d = 0; d < 3; ++d) P[i][d] = xpair(m, d, v);
+      }
+      float* o = m.sg32 + t;
+      float u[3][3];
+      for (int d = 0; d < 3; ++d) {
+        const float z0 = xi_pair(P[0][d], lp[d], L[d], iL[d]);
+        o[d * ns] = z0;
+        for (int i = 1; i < 4; ++i) {
+          o[(3 * i + d) * ns] = xi_pair(P[i][d], lp[d], L[d], iL[d]) - z0;
+          u[i - 1][d] = pdiff(P[i][d], P[0][d]);
+        }
+      }
+      o[12 * ns] = fabsf(u[0][0] * (u[1][1] * u[2][2] - u[1][2] * u[2][1]) -
+                         u[0][1] * (u[1][0] * u[2][2] - u[1][2] * u[2][0]) +
+                         u[0][2] * (u[1][0] * u[2][1] - u[1][1] * u[2][0]));
+    }
+    if (lane == 0) write_elem_f32<3>(m, e, lp, L, h2);
+  }
+}
+
+// face records from the split coordinates and the elements' box corners;
+// the same quantities as face_geom
+template <int D>
+__global__ void face_geom_f32_kernel(DevMesh m) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= m.nf) return;
+  float2 P[D][D];
+  for (int i = 0; i < D; ++i) {
+    const int v = m.f_v[D * f + i];
+    for (int d = 0; d < D; ++d) P[i][d] = xpair(m, d, v);
+  }
+  float t[D - 1][D];
+  for (int i = 1; i < D; ++i)
+    for (int d = 0; d < D; ++d) t[i - 1][d] = pdiff(P[i][d], P[0][d]);
+  float n[3], J;
+  if constexpr (D == 2) {
+    const float len = sqrtf(fmaf(t[0][0], t[0][0], t[0][1] * t[0][1]));
+    n[0] = t[0][1] / len;  // the CCW loop of e0 has its interior on the left
+    n[1] = -t[0][0] / len;
+    J = len;
+  } else {
+    const float* u = t[0];
+    const float* v = t[1];
+    const float c[3] = {u[1] * v[2] - u[2] * v[1], u[2] * v[0] - u[0] * v[2], u[0] * v[1] - u[1] * v[0]};
+    const float len = sqrtf(fmaf(c[0], c[0], fmaf(c[1], c[1], c[2] * c[2])));
+    const float sg = m.f_flip[f] ? -1.f : 1.f;  // point out of e0
+    for (int d = 0; d < 3; ++d) n[d] = sg * c[d] / len;
+    J = len;  // = 2 |F| (collapsed triangle rule)
+  }
+  constexpr int FV = side_vals(D);
+  const int es[2] = {m.f_e0[f], m.f_e1[f]};
+  float sigma = 0.f;
+  for (int s = 0; s < 2; ++s) {
+    const int e = es[s];
+    float out[FV];
+    for (int j = 0; j < FV; ++j) out[j] = 0.f;
+    if (e >= 0) {
+      for (int d = 0; d < D; ++d) {
+        const float2 lp = make_float2(m.gx32[(size_t)d * m.ne + e], m.gx32[(size_t)(D + d) * m.ne + e]);
+        const float2 L = make_float2(m.eg32[(size_t)(D + d) * m.ne + e], m.gx32[(size_t)(2 * D + d) * m.ne + e]);
+        const float iL = m.eg32[(size_t)(2 * D + d) * m.ne + e];
+        const float z0 = xi_pair(P[0][d], lp, L, iL);
+        out[d] = z0;
+        for (int i = 1; i < D; ++i) out[i * D + d] = xi_pair(P[i][d], lp, L, iL) - z0;
+        out[D * D + d] = 2.f * (n[d] * iL);
+      }
+      sigma = fmaxf(sigma, m.gx32[(size_t)(3 * D) * m.ne + e]);
+    }
+    for (int j = 0; j < FV; ++j) m.fs32[((size_t)s * FV + j) * m.nf + f] = out[j];
+  }
+  float bn = 0.f;
+  for (int d = 0; d < D; ++d) bn = fmaf((float)m.pb.b[d], n[d], bn);
+  m.fsc32[f] = J;
+  m.fsc32[(size_t)m.nf + f] = sigma * (float)m.pb.c_sigma;
+  m.fsc32[2 * (size_t)m.nf + f] = bn;
+}
+
 inline int nblk(int n, int t) { return (n + t - 1) / t; }
 
 }  // namespace
@@ -435,6 +790,18 @@ int launch_geometry(const DevMesh& m, cudaStream_t st, Tracer* tr, int wmask) {
   // no algorithmic flop count of its own (kind past the counted ones)
   if (tr && tr->on) tr->begin(m.dim == 2 ? "geometry2d" : "geometry3d", kKinds, 0, 8, st);
   const int nsf = m.nsub + m.nf;
+  if (wmask == 2 && m.xs2 && m.gx32) {
+    if (m.nv > 0) vertex_split_kernel<<<nblk(m.dim * m.nv, T), T, 0, st>>>(m);
+    if (m.dim == 2) {
+      if (m.ne > 0) elem_geom2d_f32_kernel<<<nblk(m.ne, T), T, 0, st>>>(m);
+      if (m.nf > 0) face_geom_f32_kernel<2><<<nblk(m.nf, T), T, 0, st>>>(m);
+    } else {
+      if (m.ne > 0) elem_geom3d_f32_kernel<<<nblk(m.ne * 32, kGeomWarps * 32), kGeomWarps * 32, 0, st>>>(m);
+      if (m.nf > 0) face_geom_f32_kernel<3><<<nblk(m.nf, T), T, 0, st>>>(m);
+    }
+    if (tr && tr->on) tr->end(st);
+    return 3;
+  }
   if (m.dim == 2) {
     if (m.ne > 0) elem_geom_kernel<2><<<nblk(m.ne, T), T, 0, st>>>(m);
     if (nsf > 0) subface_geom_kernel<2><<<nblk(nsf, T), T, 0, st>>>(m, wmask);

@@ -1018,6 +1018,8 @@ static int upload_impl(dg_ctx* ctx, const dg_mesh_desc* d, const int8_t* owned, 
   alloc_d(&dm.pen, ne);
   alloc_d(&dm.eg64, (size_t)elem_vals(dim) * ne);
   alloc_f(&dm.eg32, (size_t)elem_vals(dim) * ne);
+  if (rc == DG_OK && B.alloc(&dm.xs2, (size_t)dim * nv) != cudaSuccess) rc = fail(DG_ERR_OOM, "device allocation failed");
+  alloc_f(&dm.gx32, (size_t)elem_vals(dim) * ne);
   alloc_d(&dm.sg64, (size_t)sub_vals(dim) * nsub);
   alloc_f(&dm.sg32, (size_t)sub_vals(dim) * nsub);
   alloc_d(&dm.fs64, (size_t)2 * side_vals(dim) * nf);
@@ -1704,6 +1706,9 @@ int dg_quad_prepare(dg_ctx* ctx, dg_mesh* mesh) {
       if (cudaMalloc(x.p, x.bytes * (size_t)ne) != cudaSuccess) return fail(DG_ERR_OOM, "dg_quad_prepare: buffers");
     DG_CUDA_TRY(cudaMemsetAsync(mesh->lq_okm, 0, sizeof(int) * ne, ctx->stream));
   }
+  // the fit reads the FP64 element records, which the reduced-precision
+  // geometry of an FP32 step leaves untouched: bring them up to date
+  launch_geometry(mesh->dm, ctx->stream, nullptr, 1);
   lq_prepare(mesh->dm, mesh->lq_mom, mesh->lq_mmom, mesh->lq_feat, mesh->lq_elig, ctx->stream);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;

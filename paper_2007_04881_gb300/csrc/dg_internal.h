@@ -83,6 +83,13 @@ struct DevMesh {
   // lo[D], L[D], 1/L[D], R = 1/sqrt(prod_d L_d)
   double* eg64;
   float* eg32;
+  // reduced-precision geometry (the FP32 and tensor-core forms).  xs2: every
+  // vertex coordinate as an unevaluated float pair hi + lo, [dim][nv].  gx32,
+  // SoA [k][ne]: the box's lower corner as pairs (hi[D], lo[D]), the low
+  // parts of its extent L (the high parts are eg32's L), and a_k p_k^2 / h_k.
+  // Null where only the FP64 kernels run.
+  float2* xs2;
+  float* gx32;
   // sub-simplex data, SoA [k][nsub]
   double* sg64;
   float* sg32;
@@ -172,6 +179,10 @@ struct Tracer {
 // number of kernel launches issued.
 // wmask: bit 0 writes the FP64 copies of the sub-simplex / face records,
 // bit 1 the FP32 copies (element records are always written in both).
+// wmask == 2 on a mesh with xs2 / gx32 takes the reduced-precision kernels
+// instead: FP32 records only, with no FP64 arithmetic beyond splitting the
+// coordinates; the FP64 element arrays and records keep their last values.
+// Returns the number of launches.
 int launch_geometry(const DevMesh& m, cudaStream_t st, Tracer* tr = nullptr, int wmask = 3);
 // Launch shape of the row kernels: cap on co-resident CTAs per SM (0: the
 // occupancy limit) and the stream of each degree's launch (index p).
