@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(kWarps * 32)
     const int e = active ? m.elem_perm[base + slot] : 0;
     ElemPar<D, T> q;
     if (active) load_elem_par<D, T>(m, e, q);
-    const bool lrn = active && m.lq_ok && m.lq_ok[e];
+    const bool lrn = D == 2 && active && m.lq_ok && m.lq_ok[e];  // learned rules are 2D
     const int npts = !active ? 0 : lrn ? 28 : (m.eptr[e + 1] - m.eptr[e]) * QT;
 
     // ---- moments and the load vector's volume term, LPE lanes per element
@@ -200,13 +200,26 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
         for (int d = 0; d < D; ++d) x[d] = q.lo[d] + (xi[d] + T(1)) * T(0.5) * q.L[d];
         const T wf = W * source_f<D, T>(m.pb, q.a, x);
+        // wf P_a P_b (P_c): the products over the trailing coordinates are
+        // shared by the basis functions that have them
+        T wy[P + 1], wyz[P + 1][P + 1];
+#pragma unroll
+        for (int j = 0; j <= P; ++j) wy[j] = wf * Lv[1][j];
+        if constexpr (D == 3) {
+#pragma unroll
+          for (int l = 0; l <= P; ++l) {
+            const T wz = wf * Lv[2][l];
+#pragma unroll
+            for (int j = 0; j + l <= P; ++j) wyz[l][j] = wz * Lv[1][j];
+          }
+        }
         int i = 0;
 #pragma unroll
         for (int k = 0; k <= P; ++k) {
           if constexpr (D == 2) {
 #pragma unroll
             for (int j = 0; j <= k; ++j) {
-              racc[i] = fma(wf, Lv[0][k - j] * Lv[1][j], racc[i]);
+              racc[i] = fma(wy[j], Lv[0][k - j], racc[i]);
               ++i;
             }
           } else {
@@ -214,7 +227,7 @@ __global__ void __launch_bounds__(kWarps * 32)
             for (int l = 0; l <= k; ++l)
 #pragma unroll
               for (int j = 0; j <= k - l; ++j) {
-                racc[i] = fma(wf, Lv[0][k - j - l] * Lv[1][j] * Lv[2][l], racc[i]);
+                racc[i] = fma(wyz[l][j], Lv[0][k - j - l], racc[i]);
                 ++i;
               }
           }
