@@ -56,8 +56,13 @@ extern "C" {
 
 /* precision flags (prec argument) */
 #define DG_PREC_FP64 0 /* everything in FP64; vals are double */
-#define DG_PREC_FP32 1 /* geometry (maps, Jacobians, normals, penalty) in FP64,
-                          basis evaluation and contractions in FP32; vals are float */
+#define DG_PREC_FP32 1 /* basis evaluation and contractions in FP32 on geometry
+                          records (maps, Jacobians, normals, penalty) equal to the
+                          FP64 geometry's rounded to FP32; vals are float.  A pass
+                          that recomputes the geometry (dg_assemble_step,
+                          dg_assemble_host, graphs) builds them in FP32 from the
+                          coordinates split into float pairs; the FP64 geometry
+                          runs at upload, dg_geometry and dg_mesh_update. */
 /* Tensor-core forms: geometry, points, weights and basis values as
  * DG_PREC_FP32; the local contractions U^T V (and the load vector, as one
  * more column of V) run on the tensor cores with FP32 accumulation, every
@@ -182,14 +187,18 @@ int dg_assemble(dg_ctx *ctx, const dg_mesh *mesh, int prec, void *vals, void *rh
 
 /* End-to-end from host memory: copies x,y,z (host, nv each; may be NULL to
  * keep the uploaded coordinates) and a (host, ne; may be NULL) to the
- * device, recomputes the geometry, assembles the system into library-owned
- * device buffers and copies vals (host, nvals entries) and rhs (host, ndofs
- * entries; may be NULL) back.  Synchronous. */
+ * device, recomputes the geometry in the pass's precision (as
+ * dg_assemble_step), assembles the system into library-owned device
+ * buffers and copies vals (host, nvals entries) and rhs (host, ndofs
+ * entries; may be NULL) back.  The launch shape is the one dg_graph_create
+ * last tuned for this mesh and precision (under the context's current
+ * volume-path setting), else concurrent degree groups.  Synchronous. */
 int dg_assemble_host(dg_ctx *ctx, dg_mesh *mesh, int prec, const double *x, const double *y,
                      const double *z, const double *a, void *vals_host, void *rhs_host);
 
-/* One pass of the whole hot path on device-resident inputs: geometry
- * kernels (dg_geometry) followed by dg_assemble.  Asynchronous. */
+/* One pass of the whole hot path on device-resident inputs: the geometry
+ * kernels in the pass's precision followed by the row kernels, in the
+ * launch shape of dg_assemble_host.  Asynchronous. */
 int dg_assemble_step(dg_ctx *ctx, dg_mesh *mesh, int prec, void *vals, void *rhs);
 
 /* Batches (many independent meshes in one pass).  dg_batch_upload merges n

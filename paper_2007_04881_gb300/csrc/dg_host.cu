@@ -234,6 +234,11 @@ struct dg_mesh {
   void* h_vals = nullptr;
   void* h_rhs = nullptr;
   int h_prec = -1;
+  // launch shape per precision, recorded by dg_graph_create's autotuner and
+  // used by the per-step entry points (dg_assemble_step, dg_assemble_host)
+  // (kept with the context's volume-path setting it was tuned under)
+  int shape_set[4] = {0, 0, 0, 0}, shape_occ[4] = {0, 0, 0, 0}, shape_conc[4] = {0, 0, 0, 0};
+  int shape_path[4] = {-1, -1, -1, -1}, shape_vm[4] = {0, 0, 0, 0};
   double* X[3] = {nullptr, nullptr, nullptr};
   double* a = nullptr;
   double flops[kKinds][9] = {{0}}, words[kKinds][9] = {{0}};
@@ -1196,6 +1201,23 @@ int dg_assemble(dg_ctx* ctx, const dg_mesh* mesh, int prec, void* vals, void* rh
   return run_assembly(ctx, mesh, prec, mode, vals, rhs, true);
 }
 
+// The per-step launch shape: the autotuned one where dg_graph_create has
+// tuned this precision on this mesh, else concurrent degree groups when the
+// mesh has more than one.
+static void step_shape(const dg_ctx* ctx, const dg_mesh* mesh, int prec, int* occ, bool* conc, int* path) {
+  if (mesh->shape_set[prec] && mesh->shape_vm[prec] == (ctx->vol_moments ? 1 : 0)) {
+    *occ = mesh->shape_occ[prec];
+    *conc = mesh->shape_conc[prec] != 0;
+    *path = mesh->shape_path[prec];
+    return;
+  }
+  int groups = 0;
+  for (int q = 1; q <= 8; ++q) groups += mesh->dm.elem_pstart[q + 1] > mesh->dm.elem_pstart[q];
+  *occ = 0;
+  *conc = groups > 1;
+  *path = -1;
+}
+
 int dg_assemble_host(dg_ctx* ctx, dg_mesh* mesh, int prec, const double* x, const double* y, const double* z,
                      const double* a, void* vals_host, void* rhs_host) {
   if (!ctx || !mesh || !vals_host) return fail(DG_ERR_ARG, "dg_assemble_host: null argument");
@@ -1209,15 +1231,23 @@ int dg_assemble_host(dg_ctx* ctx, dg_mesh* mesh, int prec, const double* x, cons
     DG_CUDA_TRY(cudaMalloc(&mesh->h_rhs, es * std::max<int64_t>(mesh->info.ndofs, 1)));
     mesh->h_prec = prec;
   }
-  int rc = dg_mesh_update(ctx, mesh, x, y, z, a);
+  const int nv = mesh->dm.nv, ne = mesh->dm.ne;
+  const double* src[3] = {x, y, z};
+  for (int q = 0; q < mesh->dm.dim; ++q)
+    if (src[q]) DG_CUDA_TRY(cudaMemcpyAsync(mesh->X[q], src[q], sizeof(double) * nv, cudaMemcpyHostToDevice, ctx->stream));
+  if (a) DG_CUDA_TRY(cudaMemcpyAsync(mesh->a, a, sizeof(double) * ne, cudaMemcpyHostToDevice, ctx->stream));
+  // geometry records only in the precision this pass consumes
+  trace_reset(ctx, mesh);
+  ctx->last_launches = launch_geometry(mesh->dm, ctx->stream, &ctx->tracer, prec == DG_PREC_FP64 ? 1 : 2);
+  DG_CUDA_TRY(cudaGetLastError());
+  int occ = 0, path = -1;
+  bool conc = false;
+  step_shape(ctx, mesh, prec, &occ, &conc, &path);
+  const int mode = kModeVol | kModeFace | (rhs_host ? kModeRhs : 0);
+  int rc = run_assembly(ctx, mesh, prec, mode, mesh->h_vals, rhs_host ? mesh->h_rhs : nullptr, true, false, nullptr,
+                        true, occ, conc, path);
   if (rc != DG_OK) return rc;
-  const int geo = ctx->last_launches;
-  {
-    const int mode = kModeVol | kModeFace | (rhs_host ? kModeRhs : 0);
-    rc = run_assembly(ctx, mesh, prec, mode, mesh->h_vals, rhs_host ? mesh->h_rhs : nullptr, true, false);
-  }
-  if (rc != DG_OK) return rc;
-  (void)geo;
+  // one copy each: several parts on parallel streams measured no faster
   DG_CUDA_TRY(cudaMemcpyAsync(vals_host, mesh->h_vals, es * mesh->info.nvals, cudaMemcpyDeviceToHost, ctx->stream));
   if (rhs_host)
     DG_CUDA_TRY(cudaMemcpyAsync(rhs_host, mesh->h_rhs, es * mesh->info.ndofs, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1232,8 +1262,11 @@ int dg_assemble_step(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs
   trace_reset(ctx, mesh);
   ctx->last_launches = launch_geometry(mesh->dm, ctx->stream, &ctx->tracer, prec == DG_PREC_FP64 ? 1 : 2);
   DG_CUDA_TRY(cudaGetLastError());
+  int occ = 0, path = -1;
+  bool conc = false;
+  step_shape(ctx, mesh, prec, &occ, &conc, &path);
   const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
-  return run_assembly(ctx, mesh, prec, mode, vals, rhs, true, false);
+  return run_assembly(ctx, mesh, prec, mode, vals, rhs, true, false, nullptr, true, occ, conc, path);
 }
 
 int dg_batch_upload(dg_ctx* ctx, const dg_mesh_desc* const* descs, int n, dg_mesh** out) {
@@ -1639,6 +1672,13 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
   g->concurrent = best_conc;
   g->vol_path = best_path;
   g->tuned_ms = autotune ? best : 0.f;
+  if (autotune) {
+    mesh->shape_set[prec] = 1;
+    mesh->shape_occ[prec] = best_occ;
+    mesh->shape_conc[prec] = best_conc;
+    mesh->shape_path[prec] = best_path;
+    mesh->shape_vm[prec] = ctx->vol_moments ? 1 : 0;
+  }
   // with timing enabled the per-launch events are recorded into the graph
   ctx->tracer.on = was_on;
   trace_reset(ctx, mesh);
