@@ -43,10 +43,12 @@ WORKLOADS = {
                      "f from u=sin(pi x)sin(pi y), penalty 10 p^2/h"),
     "diff3d_32k": ("diff3d_32k: 3D diffusion, 64^3 cubes x 6 Kuhn tets (1,572,864 tets) agglomerated by k-means "
                    "into 32,768 polyhedra, p=3, a=10^U(-2,2), b=0, c=0, penalty 10 p^2/h"),
+    "diff3d_8k": ("diff3d_8k: the diff3d_32k recipe on 40^3 cubes x 6 Kuhn tets (384,000 tets) agglomerated into "
+                  "8,192 polyhedra, p=3 (the small case of the 3D kernel profiles)"),
     "learned2d_262k": ("learned2d_262k: 2D ADR on 262,144 clipped Voronoi cells (3-12 vertices), p=3, a=10^U(-2,2), "
                        "b=(1,0.5), c=1; learned 28-point volume rules (24->128->128->84 BF16 network trained on "
                        "1,048,576 polygons of 16 independent meshes, then 3 FP64 Gauss-Newton steps, sub-triangle "
-                       "fallback), assembled in FP32 with FP64 geometry"),
+                       "fallback), assembled in FP32"),
     "batch2d_256": ("batch2d_256: 256 independent 2D clipped-Voronoi meshes (5 Lloyd steps), cell counts "
                     "log-uniform in 512..16,384, per-mesh p~U{1..5}, a=10^U(-2,2), b=(1,0.5), c=1, one recorded "
                     "pass over the whole batch"),
@@ -83,6 +85,8 @@ def make_workload(name):
         return configs.poisson2d()
     if name == "diff3d_32k":
         return configs.diff3d()
+    if name == "diff3d_8k":
+        return configs.diff3d(n=40, clusters=8192)
     if name == "batch2d_256":
         return _Batch(configs.batch2d())
     if name == "learned2d_262k":
