@@ -198,7 +198,13 @@ int dg_assemble_host(dg_ctx *ctx, dg_mesh *mesh, int prec, const double *x, cons
 
 /* One pass of the whole hot path on device-resident inputs: the geometry
  * kernels in the pass's precision followed by the row kernels, in the
- * launch shape of dg_assemble_host.  Asynchronous. */
+ * launch shape of dg_assemble_host.  Asynchronous.
+ *
+ * Concurrent degree groups run on four forked streams per context (and
+ * four per graph, captured).  A process that uses more streams than the
+ * driver's hardware work queues (CUDA_DEVICE_MAX_CONNECTIONS, 8 by default)
+ * can see two groups serialised on one queue; set that variable to 32
+ * before the CUDA context is created. */
 int dg_assemble_step(dg_ctx *ctx, dg_mesh *mesh, int prec, void *vals, void *rhs);
 
 /* Batches (many independent meshes in one pass).  dg_batch_upload merges n

@@ -152,6 +152,31 @@ void reference_rule(int dim, int n, std::vector<double>& pts) { simplex_rule(dim
 int fail_na_impl(int code, const char* msg) { return fail(code, "%s", msg); }
 }  // namespace dg
 
+// Forked streams and events for concurrent per-degree launches (created on
+// first use).  The context has one set for its direct launches; every graph
+// captures through a set of its own, so that a recorded pass does not depend
+// on what the context's streams did before it.
+struct SideStreams {
+  cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaEvent_t fork = nullptr, join[4] = {nullptr, nullptr, nullptr, nullptr};
+  cudaError_t ensure() {
+    if (fork) return cudaSuccess;
+    cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+      e = cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
+    }
+    return e;
+  }
+  ~SideStreams() {
+    for (int i = 0; i < 4; ++i) {
+      if (side[i]) cudaStreamDestroy(side[i]);
+      if (join[i]) cudaEventDestroy(join[i]);
+    }
+    if (fork) cudaEventDestroy(fork);
+  }
+};
+
 struct dg_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -162,24 +187,18 @@ struct dg_ctx {
   Tracer tracer;
   bool vol_moments = true;  // volume blocks through Legendre-product moments
   std::vector<LaunchRec> recs;
-  // forked streams for concurrent per-degree launches (created on first use)
-  cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t fork = nullptr, join[4] = {nullptr, nullptr, nullptr, nullptr};
+  SideStreams streams;  // the direct launches' forked streams
   ~dg_ctx() {
     for (auto& r : recs) {
       cudaEventDestroy(r.ev0);
       cudaEventDestroy(r.ev1);
     }
-    for (int i = 0; i < 4; ++i) {
-      if (side[i]) cudaStreamDestroy(side[i]);
-      if (join[i]) cudaEventDestroy(join[i]);
-    }
-    if (fork) cudaEventDestroy(fork);
   }
 };
 
 struct dg_graph {
   cudaStream_t stream = nullptr;  // capture stream
+  SideStreams streams;            // forked streams of the captured pass
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int occ_cap = 0;
@@ -1121,7 +1140,7 @@ int dg_mesh_update(dg_ctx* ctx, dg_mesh* mesh, const double* x, const double* y,
 // unless a path is given (their elements have only 28 points each)
 static int run_assembly(dg_ctx* ctx, const dg_mesh* mesh, int prec, int mode, void* vals, void* rhs, bool iface,
                         bool reset = true, cudaStream_t st = nullptr, bool use_ctx_stream = true, int occ_cap = 0,
-                        bool concurrent = false, int vpath = -1) {
+                        bool concurrent = false, int vpath = -1, SideStreams* ss = nullptr) {
   if (!ctx || !mesh) return fail(DG_ERR_ARG, "null context or mesh");
   if (prec < DG_PREC_FP64 || prec > DG_PREC_TF32X3) return fail(DG_ERR_ARG, "unknown precision %d", prec);
   if ((mode & (kModeVol | kModeFace)) && !vals) return fail(DG_ERR_ARG, "vals is null");
@@ -1135,18 +1154,13 @@ static int run_assembly(dg_ctx* ctx, const dg_mesh* mesh, int prec, int mode, vo
   lo.occ_cap = occ_cap;
   lo.vol_moments = vpath >= 0 ? vpath == 1 : ctx->vol_moments && !mesh->dm.lq_ok;
   for (int p = 0; p < 9; ++p) lo.pst[p] = st;
+  if (!ss) ss = &ctx->streams;
   if (concurrent) {
-    if (!ctx->fork) {
-      DG_CUDA_TRY(cudaEventCreateWithFlags(&ctx->fork, cudaEventDisableTiming));
-      for (int i = 0; i < 4; ++i) {
-        DG_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side[i], cudaStreamNonBlocking));
-        DG_CUDA_TRY(cudaEventCreateWithFlags(&ctx->join[i], cudaEventDisableTiming));
-      }
-    }
-    DG_CUDA_TRY(cudaEventRecord(ctx->fork, st));
-    for (int i = 0; i < 4; ++i) DG_CUDA_TRY(cudaStreamWaitEvent(ctx->side[i], ctx->fork, 0));
+    DG_CUDA_TRY(ss->ensure());
+    DG_CUDA_TRY(cudaEventRecord(ss->fork, st));
+    for (int i = 0; i < 4; ++i) DG_CUDA_TRY(cudaStreamWaitEvent(ss->side[i], ss->fork, 0));
     // highest degrees (longest launches) first on their own streams
-    for (int p = 1; p < 9; ++p) lo.pst[p] = ctx->side[(8 - p) % 4];
+    for (int p = 1; p < 9; ++p) lo.pst[p] = ss->side[(8 - p) % 4];
   }
   int n = 0;
   if (prec == DG_PREC_FP64) {
@@ -1169,8 +1183,8 @@ static int run_assembly(dg_ctx* ctx, const dg_mesh* mesh, int prec, int mode, vo
   }
   if (concurrent) {
     for (int i = 0; i < 4; ++i) {
-      DG_CUDA_TRY(cudaEventRecord(ctx->join[i], ctx->side[i]));
-      DG_CUDA_TRY(cudaStreamWaitEvent(st, ctx->join[i], 0));
+      DG_CUDA_TRY(cudaEventRecord(ss->join[i], ss->side[i]));
+      DG_CUDA_TRY(cudaStreamWaitEvent(st, ss->join[i], 0));
     }
   }
   ctx->last_launches = reset ? n : ctx->last_launches + n;
@@ -1599,11 +1613,11 @@ int dg_batch_offsets(const dg_mesh* mesh, int* nmesh, int* elem_off, int64_t* va
 
 // One whole pass (geometry + row kernels) on stream st with a launch shape.
 static int issue_pass(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs, cudaStream_t st, int occ_cap,
-                      bool concurrent, int vpath) {
+                      bool concurrent, int vpath, SideStreams* ss) {
   int n = launch_geometry(mesh->dm, st, nullptr, prec == DG_PREC_FP64 ? 1 : 2);
   DG_CUDA_TRY(cudaGetLastError());
   const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
-  int rc = run_assembly(ctx, mesh, prec, mode, vals, rhs, true, true, st, false, occ_cap, concurrent, vpath);
+  int rc = run_assembly(ctx, mesh, prec, mode, vals, rhs, true, true, st, false, occ_cap, concurrent, vpath, ss);
   if (rc != DG_OK) return rc;
   ctx->last_launches += n;
   return DG_OK;
@@ -1619,7 +1633,7 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
     delete g;
     return rc;
   };
-  if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess)
+  if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess || g->streams.ensure() != cudaSuccess)
     return bail(fail(DG_ERR_CUDA, "dg_graph_create: stream creation failed"));
   const bool was_on = ctx->tracer.on;
   ctx->tracer.on = false;
@@ -1642,7 +1656,7 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
         float t = 1e30f;
         for (int rep = 0; rep < 4; ++rep) {
           cudaEventRecord(e0, g->stream);
-          int rc = issue_pass(ctx, mesh, prec, vals, rhs, g->stream, occs[oi], conc != 0, vpath);
+          int rc = issue_pass(ctx, mesh, prec, vals, rhs, g->stream, occs[oi], conc != 0, vpath, &g->streams);
           if (rc != DG_OK) {
             ctx->tracer.on = was_on;
             cudaEventDestroy(e0);
@@ -1689,7 +1703,7 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
     const int gl = launch_geometry(mesh->dm, g->stream, &ctx->tracer, prec == DG_PREC_FP64 ? 1 : 2);
     const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
     rc = run_assembly(ctx, mesh, prec, mode, vals, rhs, true, false, g->stream, false, g->occ_cap, g->concurrent != 0,
-                      g->vol_path);
+                      g->vol_path, &g->streams);
     ctx->last_launches += gl;
   }
   cudaError_t ce = cudaStreamEndCapture(g->stream, &g->graph);
