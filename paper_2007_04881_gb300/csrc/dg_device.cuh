@@ -196,7 +196,7 @@ __device__ T exact_u(const Problem& pb, const T* x, T* gu, T* lap) {
         for (int j = 0; j <= k - ll; ++j) {
           const int e0 = k - j - ll, e1 = j, e2 = ll;
           const int ex[3] = {e0, e1, e2};
-          const T cf = T(pb.poly[m]);
+          const T cf = pb_val<T>(pb.poly[m], pb.polyf[m]);
           ++m;
           T v = cf;
 #pragma unroll
@@ -238,8 +238,8 @@ __device__ __forceinline__ T source_f(const Problem& pb, T a, const T* x) {
   const T u = exact_u<D, T>(pb, x, gu, &lap);
   T bg = T(0);
 #pragma unroll
-  for (int d = 0; d < D; ++d) bg += T(pb.b[d]) * gu[d];
-  return -a * lap + bg + T(pb.c) * u;
+  for (int d = 0; d < D; ++d) bg += pb_val<T>(pb.b[d], pb.bf[d]) * gu[d];
+  return -a * lap + bg + pb_val<T>(pb.c, pb.cf) * u;
 }
 
 template <int D, typename T>
@@ -360,9 +360,9 @@ __device__ __forceinline__ void load_elem_par(const DevMesh& m, int e, ElemPar<D
     q.lo[d] = EG[(size_t)d * m.ne + e];
     q.L[d] = EG[(size_t)(D + d) * m.ne + e];
     q.ap[d] = T(4) * a * iL * iL;      // a'_d = 4 a / L_d^2
-    q.bp[d] = T(2 * m.pb.b[d]) * iL;  // b'_d = 2 b_d / L_d
+    q.bp[d] = T(2) * pb_val<T>(m.pb.b[d], m.pb.bf[d]) * iL;  // b'_d = 2 b_d / L_d
   }
-  q.c = T(m.pb.c);
+  q.c = pb_val<T>(m.pb.c, m.pb.cf);
   q.a = a;
   q.R = EG[(size_t)(3 * D) * m.ne + e];
 }

@@ -775,9 +775,9 @@ __global__ void face_geom_f32_kernel(DevMesh m) {
     for (int j = 0; j < FV; ++j) m.fs32[((size_t)s * FV + j) * m.nf + f] = out[j];
   }
   float bn = 0.f;
-  for (int d = 0; d < D; ++d) bn = fmaf((float)m.pb.b[d], n[d], bn);
+  for (int d = 0; d < D; ++d) bn = fmaf(m.pb.bf[d], n[d], bn);
   m.fsc32[f] = J;
-  m.fsc32[(size_t)m.nf + f] = sigma * (float)m.pb.c_sigma;
+  m.fsc32[(size_t)m.nf + f] = sigma * m.pb.c_sigmaf;
   m.fsc32[2 * (size_t)m.nf + f] = bn;
 }
 

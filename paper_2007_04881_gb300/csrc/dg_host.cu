@@ -1060,6 +1060,7 @@ static int upload_impl(dg_ctx* ctx, const dg_mesh_desc* d, const int8_t* owned, 
   dm.pb.source = d->source;
   for (int q = 0; q < 20; ++q) dm.pb.poly[q] = d->poly[q];
   dm.pb.c_sigma = d->c_sigma;
+  dm.pb.round_copies();
   dm.rt = ctx->rt[dim];
 
   fill_info(d, P, m->info);

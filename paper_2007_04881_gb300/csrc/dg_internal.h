@@ -56,7 +56,25 @@ struct Problem {
   int source;
   double poly[20];
   double c_sigma;
+  // the same constants rounded to FP32, for the FP32 kernels: on a part whose
+  // FP64 rate is 1/64 of FP32 a per-point conversion occupies the FP64 pipe
+  float bf[3], cf, polyf[20], c_sigmaf;
+  void round_copies() {
+    for (int d = 0; d < 3; ++d) bf[d] = (float)b[d];
+    cf = (float)c;
+    for (int k = 0; k < 20; ++k) polyf[k] = (float)poly[k];
+    c_sigmaf = (float)c_sigma;
+  }
 };
+
+// a problem constant in the contraction type T (FP64 value or its FP32 copy)
+template <typename T>
+__host__ __device__ __forceinline__ T pb_val(double v64, float v32) {
+  if constexpr (sizeof(T) == 4)
+    return v32;
+  else
+    return v64;
+}
 
 // Everything a kernel needs, by device pointer.  Passed by value.
 struct DevMesh {

@@ -206,6 +206,7 @@ extern "C" int dg_volume_noalloc(void* stream, int device, int prec, int p, int 
   m.pb.c = c;
   m.pb.source = DG_SRC_ZERO;
   m.pb.c_sigma = 10.0;
+  m.pb.round_copies();
   m.rt = nd->rt;
 
   noalloc_setup_kernel<<<(ne + 1 + 127) / 128, 128, 0, st>>>(
