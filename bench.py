@@ -8,8 +8,9 @@ the BSR matrix and the load vector.
 
 Default workload: 2D advection-diffusion-reaction on 65,536 Voronoi cells,
 p ~ U{1..4}, a = 10^U(-2,2), b = (1, 0.5), c = 1 (seeded, synthetic).
-Headline form: FP32 contractions with FP64 geometry; the FP64 form is timed
-in the same run and the FP32 matrix error against it is reported.
+Headline form: FP32 contractions on FP32 geometry records equal to the
+rounded FP64 ones; the FP64 form is timed in the same run and the FP32
+matrix error against it is reported.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 launch under torch.distributed.run; every rank assembles its own

@@ -23,7 +23,9 @@
 //     R = W f on volume points (Phi row),
 //     R = W [sigma g - min(b.n,0) g;  -a g] on boundary-face points.
 // Geometry (bounding boxes, sub-simplex maps, Jacobians, normals, penalty)
-// is computed in FP64 by the geometry kernels; T is the contraction type.
+// comes from the geometry kernels as records in T: FP64, or for the reduced
+// forms FP32 records equal to the rounded FP64 ones; T is the contraction
+// type.
 #pragma once
 
 #include <cuda_runtime.h>

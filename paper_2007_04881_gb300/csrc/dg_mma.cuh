@@ -5,7 +5,8 @@
 //     FP32 accumulation;
 //   3xTF32: the same split with TF32 halves, m16n8k8, FP32 accumulation.
 // Geometry, quadrature points and weights, basis values and the per-point
-// rows are the FP32 form's (FP32 values of the FP64 geometry); only the
+// rows are the FP32 form's (geometry records equal to the rounded FP64
+// ones); only the
 // contractions change.  The tensor cores' FP32 accumulation is not rounded
 // to nearest at every addition, so its accumulators live for one chunk of
 // points only and are added to IEEE FP32 running sums after each chunk:

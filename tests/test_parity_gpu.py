@@ -3,7 +3,8 @@
 Tolerances (block max-norm relative, i.e. max |G - O| / max |O| per block):
   FP64 form: 1e-12.  Both sides sum a few hundred FP64 products per entry in
   different orders; the rounding difference is ~K * 2^-53 ~ 1e-13 at most.
-  FP32 form (FP64 geometry, FP32 basis and contraction): 5e-5 per block.
+  FP32 form (geometry records equal to the rounded FP64 ones, FP32 basis and
+  contraction): 5e-5 per block.
   Basis values carry ~p^2 * 2^-24 relative error and the accumulations run
   over up to ~10^3 rows with partial cancellation; the whole-matrix relative
   Frobenius error is checked against 1e-6.  FP32 load vectors: 1e-4 per
