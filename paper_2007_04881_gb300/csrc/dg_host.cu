@@ -975,7 +975,7 @@ static int upload_impl(dg_ctx* ctx, const dg_mesh_desc* d, const int8_t* owned, 
     dm.X[q] = nullptr;
     if (q < dim) {
       std::vector<double> v(X[q], X[q] + nv);
-      const double* p;
+      const double* p = nullptr;
       if (rc == DG_OK) rc = upload(B, &p, v);
       dm.X[q] = p;
       m->X[q] = const_cast<double*>(p);
@@ -1000,7 +1000,7 @@ static int upload_impl(dg_ctx* ctx, const dg_mesh_desc* d, const int8_t* owned, 
   up_i(&dm.f_v, f_v);
   if (rc == DG_OK) rc = upload(B, &dm.f_flip, P.f_flip);
   {
-    const int* p;
+    const int* p = nullptr;
     up_i(&p, f_nq);
     dm.f_nq = const_cast<int*>(p);
   }
@@ -1227,7 +1227,7 @@ static void step_shape(const dg_ctx* ctx, const dg_mesh* mesh, int prec, int* oc
     return;
   }
   int groups = 0;
-  for (int q = 1; q <= 8; ++q) groups += mesh->dm.elem_pstart[q + 1] > mesh->dm.elem_pstart[q];
+  for (int q = 1; q + 1 < 9; ++q) groups += mesh->dm.elem_pstart[q + 1] > mesh->dm.elem_pstart[q];
   *occ = 0;
   *conc = groups > 1;
   *path = -1;

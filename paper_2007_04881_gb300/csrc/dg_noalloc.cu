@@ -13,7 +13,6 @@
 // The pass is the library's own: the geometry kernels write the element and
 // sub-triangle records into the array, then the degree-p row kernel, in
 // volume-only mode, reads them and writes the blocks.
-#include <cstring>
 #include <mutex>
 #include <vector>
 
@@ -164,8 +163,7 @@ extern "C" int dg_volume_noalloc(void* stream, int device, int prec, int p, int 
   const size_t o_sg64 = cv.take<double>((size_t)sub_vals(2) * nsub), o_sg32 = cv.take<float>((size_t)sub_vals(2) * nsub);
   if (cv.off > kNoallocScratchBytes) return fail_na(DG_ERR_ARG, "dg_volume_noalloc: mesh exceeds the scratch array");
 
-  DevMesh m;
-  std::memset(&m, 0, sizeof m);
+  DevMesh m{};  // value-initialised: every pointer null, every count zero
   m.dim = 2;
   m.nv = nv;
   m.ne = ne;
