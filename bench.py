@@ -632,12 +632,14 @@ def run_ours(args):
 
 
 def _kernel_source_sha() -> str:
+    """Hash of the sources the row-pass kernels are compiled from: the
+    dg_row*.cu translation units and every header they include."""
     import hashlib
 
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2007_04881_gb300", "csrc")
     for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cu", ".cuh", ".h")):
+        if fn.endswith((".cuh", ".h")) or (fn.startswith("dg_row") and fn.endswith(".cu")):
             h.update(open(os.path.join(csrc, fn), "rb").read())
     return h.hexdigest()[:16]
 
