@@ -478,6 +478,8 @@ def run_ours(args):
     variants = [(k, getattr(dg, v), 1) for k, v in PRECS.items() if getattr(dg, v) != prec]
     if prec in (dg.DG_PREC_FP32, dg.DG_PREC_FP64):
         variants.append((args.prec + "_pointwise_volume", prec, 0))
+        if mesh.dim == 2:  # volume moments exact, from the element's edges
+            variants.append((args.prec + "_exact_moments", prec, 2))
     for fname, fprec, vpath in variants:
         ctx.dg_set_volume_path(vpath)
         vf = torch.empty(mesh.nvals, dtype=torch.float32, device="cuda")

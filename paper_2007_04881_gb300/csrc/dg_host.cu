@@ -186,6 +186,7 @@ struct dg_ctx {
   RuleTables rt[4];  // indexed by dim (2, 3)
   Tracer tracer;
   bool vol_moments = true;  // volume blocks through Legendre-product moments
+  bool vol_exact = false;   // 2D: those moments exact, by Green's theorem along the edges
   std::vector<LaunchRec> recs;
   SideStreams streams;  // the direct launches' forked streams
   ~dg_ctx() {
@@ -195,6 +196,9 @@ struct dg_ctx {
     }
   }
 };
+
+// the context's volume path: 0 per-point, 1 quadrature moments, 2 exact 2D moments
+static int ctx_vol_path(const dg_ctx* ctx) { return !ctx->vol_moments ? 0 : ctx->vol_exact ? 2 : 1; }
 
 struct dg_graph {
   cudaStream_t stream = nullptr;  // capture stream
@@ -1136,7 +1140,7 @@ int dg_mesh_update(dg_ctx* ctx, dg_mesh* mesh, const double* x, const double* y,
 
 // Issue the row kernels of one assembly pass on stream st.  concurrent:
 // the per-degree launches go to forked side streams and join back into st.
-// vpath: volume path (0 per-point contraction, 1 moments), -1 the context's
+// vpath: volume path (0 per-point contraction, 1 moments, 2 exact 2D moments), -1 the context's
 // setting; meshes with learned rules installed take the per-point path
 // unless a path is given (their elements have only 28 points each)
 static int run_assembly(dg_ctx* ctx, const dg_mesh* mesh, int prec, int mode, void* vals, void* rhs, bool iface,
@@ -1153,7 +1157,8 @@ static int run_assembly(dg_ctx* ctx, const dg_mesh* mesh, int prec, int mode, vo
   (void)iface;
   LaunchOpts lo;
   lo.occ_cap = occ_cap;
-  lo.vol_moments = vpath >= 0 ? vpath == 1 : ctx->vol_moments && !mesh->dm.lq_ok;
+  lo.vol_moments = vpath >= 0 ? vpath >= 1 : ctx->vol_moments && !mesh->dm.lq_ok;
+  lo.vol_exact = lo.vol_moments && (vpath >= 0 ? vpath == 2 : ctx->vol_exact);
   for (int p = 0; p < 9; ++p) lo.pst[p] = st;
   if (!ss) ss = &ctx->streams;
   if (concurrent) {
@@ -1220,7 +1225,7 @@ int dg_assemble(dg_ctx* ctx, const dg_mesh* mesh, int prec, void* vals, void* rh
 // tuned this precision on this mesh, else concurrent degree groups when the
 // mesh has more than one.
 static void step_shape(const dg_ctx* ctx, const dg_mesh* mesh, int prec, int* occ, bool* conc, int* path) {
-  if (mesh->shape_set[prec] && mesh->shape_vm[prec] == (ctx->vol_moments ? 1 : 0)) {
+  if (mesh->shape_set[prec] && mesh->shape_vm[prec] == ctx_vol_path(ctx)) {
     *occ = mesh->shape_occ[prec];
     *conc = mesh->shape_conc[prec] != 0;
     *path = mesh->shape_path[prec];
@@ -1641,7 +1646,8 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
   // autotuner: time each candidate launch shape (best of 3 after a warm-up):
   // residency cap x serial / concurrent degree groups x volume path (the
   // moment path only where the context allows it and the form has it)
-  const int def_path = ctx->vol_moments && !mesh->dm.lq_ok ? 1 : 0;
+  const int mpath = ctx->vol_exact ? 2 : 1;  // the context's moment path
+  const int def_path = ctx->vol_moments && !mesh->dm.lq_ok ? mpath : 0;
   int best_occ = 0, best_conc = 0, best_path = def_path;
   float best = 1e30f;
   if (autotune) {
@@ -1653,7 +1659,7 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
     for (int pi = 0; pi < npath; ++pi)
     for (int conc = 0; conc < 2; ++conc)
       for (int oi = 0; oi < 3; ++oi) {
-        const int vpath = npath == 2 ? 1 - pi : 0;
+        const int vpath = npath == 2 ? (pi == 0 ? mpath : 0) : 0;
         float t = 1e30f;
         for (int rep = 0; rep < 4; ++rep) {
           cudaEventRecord(e0, g->stream);
@@ -1692,7 +1698,7 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
     mesh->shape_occ[prec] = best_occ;
     mesh->shape_conc[prec] = best_conc;
     mesh->shape_path[prec] = best_path;
-    mesh->shape_vm[prec] = ctx->vol_moments ? 1 : 0;
+    mesh->shape_vm[prec] = ctx_vol_path(ctx);
   }
   // with timing enabled the per-launch events are recorded into the graph
   ctx->tracer.on = was_on;
@@ -1943,8 +1949,9 @@ int dg_kernel_stats(dg_ctx* ctx, dg_kernel_stat* out, int cap) {
 }
 
 int dg_set_volume_path(dg_ctx* ctx, int path) {
-  if (!ctx || (path != 0 && path != 1)) return fail(DG_ERR_ARG, "dg_set_volume_path: bad argument");
-  ctx->vol_moments = path == 1;
+  if (!ctx || path < 0 || path > 2) return fail(DG_ERR_ARG, "dg_set_volume_path: bad argument");
+  ctx->vol_moments = path >= 1;
+  ctx->vol_exact = path == 2;
   return DG_OK;
 }
 

@@ -162,6 +162,7 @@ enum : int {
   kModeRhs = 4,    // load vector
   kModeAccum = 8,  // add to the diagonal block instead of overwriting it
   kModeSkipVol = 16,  // volume terms done by the moment kernel: faces only, load vector added
+  kModeExactMom = 32,  // 2D moment launch: volume moments by Green's theorem along the edges
 };
 
 // Optional per-launch timing: CUDA events recorded on the launch stream
@@ -207,6 +208,7 @@ int launch_geometry(const DevMesh& m, cudaStream_t st, Tracer* tr = nullptr, int
 struct LaunchOpts {
   int occ_cap = 0;
   bool vol_moments = true;  // volume blocks through Legendre-product moments where supported
+  bool vol_exact = false;   // 2D: those moments exact, from the element's edges
   cudaStream_t pst[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 

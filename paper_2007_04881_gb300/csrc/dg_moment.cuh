@@ -136,7 +136,10 @@ __global__ void __launch_bounds__(kWarps * 32)
     for (int k = 0; k < NM; ++k) mu[k] = T(0);
 #pragma unroll
     for (int i = 0; i < N; ++i) racc[i] = T(0);
-    for (int qv = lig; qv < npts; qv += LPE) {
+    // exact moments (2D, kModeExactMom): the points carry only the load vector
+    const bool exact = D == 2 && active && (mode & kModeExactMom) && !lrn;
+    const int npl = exact && !do_rhs ? 0 : npts;
+    for (int qv = lig; qv < npl; qv += LPE) {
       T xi[D], W;
       if (D == 2 && lrn) {
         const T* LQ = pick<T>(m.lq64, m.lq32) + (size_t)e * 84;
@@ -167,7 +170,7 @@ __global__ void __launch_bounds__(kWarps * 32)
         for (int k = 1; k < Q; ++k)
           Lv[d][k + 1] = (T(2 * k + 1) / T(k + 1)) * xi[d] * Lv[d][k] - (T(k) / T(k + 1)) * Lv[d][k - 1];
       }
-      if (mat_vol) {
+      if (mat_vol && !exact) {
         if constexpr (D == 2) {
 #pragma unroll
           for (int c = 0; c <= Q; ++c) {
@@ -230,6 +233,51 @@ __global__ void __launch_bounds__(kWarps * 32)
                 racc[i] = fma(wyz[l][j], Lv[0][k - j - l], racc[i]);
                 ++i;
               }
+          }
+        }
+      }
+    }
+    // exact moments by Green's theorem in the element's box coordinates:
+    // mu_cd = (L_1 L_2 / 4) * closed integral over the loop (counter-clockwise)
+    // of Q_c(xi) P_d(eta) d eta, with Q_c an antiderivative of P_c (Q_0 = P_1,
+    // Q_c = (P_{c+1} - P_{c-1}) / (2c + 1)).  Along an edge the integrand has
+    // degree c + 1 + d <= 2p + 1 in the edge parameter, so the (p + 1)-point
+    // Gauss rule of the faces integrates it exactly.  The edge of sub-triangle
+    // t runs from its second vertex to its third (the loop's v_t to v_{t+1}).
+    if constexpr (D == 2) {
+      if (exact && mat_vol) {
+        const int sub0 = m.eptr[e], ned = m.eptr[e + 1] - sub0;
+        const T* fr = pick<T>(m.rt.face64, m.rt.face32) + (size_t)m.rt.face_off[P + 1] * 2;
+        const T jac = T(0.25) * q.L[0] * q.L[1];
+        for (int ed = lig; ed < ned; ed += LPE) {
+          T sv[SV];
+#pragma unroll
+          for (int k = 0; k < SV; ++k) sv[k] = SG[(size_t)k * m.nsub + sub0 + ed];
+          const T deta = sv[5] - sv[3];
+#pragma unroll 1
+          for (int g = 0; g <= P; ++g) {
+            const T t = fr[2 * g], w = fr[2 * g + 1] * deta * jac;
+            const T x = sv[0] + (T(1) - t) * sv[2] + t * sv[4];
+            const T y = sv[1] + (T(1) - t) * sv[3] + t * sv[5];
+            T px[Q + 2], py[Q + 1];
+            px[0] = py[0] = T(1);
+            px[1] = x;
+            py[1] = y;
+#pragma unroll
+            for (int k = 1; k <= Q; ++k) {
+              px[k + 1] = (T(2 * k + 1) / T(k + 1)) * x * px[k] - (T(k) / T(k + 1)) * px[k - 1];
+              if (k < Q) py[k + 1] = (T(2 * k + 1) / T(k + 1)) * y * py[k] - (T(k) / T(k + 1)) * py[k - 1];
+            }
+#pragma unroll
+            for (int c = 0; c <= Q; ++c) {
+              const T qc = c == 0 ? px[1] : (px[c + 1] - px[c - 1]) * (T(1) / T(2 * c + 1));
+              const T wc = w * qc;
+#pragma unroll
+              for (int d = 0; c + d <= Q; ++d) {
+                const int s = c + d;
+                mu[s * (s + 1) / 2 + d] = fma(wc, py[d], mu[s * (s + 1) / 2 + d]);
+              }
+            }
           }
         }
       }

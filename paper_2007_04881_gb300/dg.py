@@ -539,7 +539,7 @@ class Graph:
         occ, conc, ms, nl, vp = C.c_int(), C.c_int(), C.c_float(), C.c_int(), C.c_int()
         _check(load().dg_graph_info(self._h, C.byref(occ), C.byref(conc), C.byref(ms), C.byref(nl), C.byref(vp)))
         return {"occ_cap": occ.value, "concurrent": bool(conc.value), "tuned_ms": ms.value, "launches": nl.value,
-                "volume_path": "moments" if vp.value == 1 else "per-point"}
+                "volume_path": {0: "per-point", 1: "moments", 2: "exact-moments"}.get(vp.value, "per-point")}
 
     def close(self):
         if getattr(self, "_h", None):

@@ -44,3 +44,19 @@ def compare(gpu, om, ob, wl):
         eo = max(eo, rel_block_err(gpu["off"][(e0, e1)], ob["a01"][k]))
         eo = max(eo, rel_block_err(gpu["off"][(e1, e0)], ob["a10"][k]))
     return ed, eo, er
+
+
+def polygon_workload(nvert: int, p: int, b=(1.0, -0.5), c: float = 1.5):
+    """One convex element: the regular nvert-gon of radius 0.4 about
+    (0.5, 0.5), counter-clockwise, every edge a boundary face.  A loop longer
+    than 16 vertices takes the kernels' runtime-length paths."""
+    from paper_2007_04881_gb300 import configs, meshgen
+
+    t = 2.0 * np.pi * np.arange(nvert) / nvert
+    mesh = meshgen.Mesh2D(x=0.5 + 0.4 * np.cos(t), y=0.5 + 0.4 * np.sin(t),
+                          elem_vptr=np.array([0, nvert], dtype=np.int32),
+                          elem_v=np.arange(nvert, dtype=np.int32))
+    return configs.Workload(name=f"polygon_{nvert}", mesh=mesh, p=np.array([p], dtype=np.int8),
+                            a=np.array([0.7]), problem=dict(b=(b[0], b[1], 0.0), c=c,
+                                                            source=configs.SRC_SINPROD, poly=[],
+                                                            c_sigma=10.0))

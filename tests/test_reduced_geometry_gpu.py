@@ -30,7 +30,7 @@ import pytest
 
 from paper_2007_04881_gb300 import configs, dg
 
-from .helpers import dg_problem
+from .helpers import dg_problem, polygon_workload
 
 pytestmark = pytest.mark.gpu
 
@@ -112,6 +112,15 @@ def test_small2d_every_degree(ctx):
 def test_strong_penalty_boundary(ctx):
     wl = configs.small2d(2000, 11, 6, 6)
     wl = dataclasses.replace(wl, a=np.full(wl.ne, 100.0))
+    m = dg.Mesh(ctx, wl.mesh, wl.p, wl.a, dg_problem(wl))
+    check_against_fp64_records(ctx, m)
+
+
+@pytest.mark.parametrize("p", [2, 4])
+def test_long_loop(ctx, p):
+    """a single 20-gon: the loop exceeds the 16 vertices the element kernel
+    keeps in registers, so its runtime-length branch runs"""
+    wl = polygon_workload(20, p)
     m = dg.Mesh(ctx, wl.mesh, wl.p, wl.a, dg_problem(wl))
     check_against_fp64_records(ctx, m)
 

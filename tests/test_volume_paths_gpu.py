@@ -1,15 +1,18 @@
-"""Both ways of forming the volume blocks, against the FP64 oracle: the
-per-point contraction in the row kernels (path 0) and the Legendre-product
-moments (path 1, the default), in FP64 and FP32, with every degree, with
-learned rules, and through the separate volume / faces / load-vector calls.
-The moment path adds the same quadrature terms in another order, so the
-tolerances are those of the other parity tests."""
+"""The ways of forming the volume blocks, against the FP64 oracle: the
+per-point contraction in the row kernels (path 0), the Legendre-product
+moments over the quadrature points (path 1, the default) and, in 2D, the same
+moments exact by Green's theorem along the element's edges (path 2), in FP64
+and FP32, with every degree, with learned rules, and through the separate
+volume / faces / load-vector calls.  The moment path adds the same quadrature
+terms in another order, and for the polynomial volume integrands of constant
+coefficients the sub-triangle rule is exact, so path 2 equals it up to
+rounding: the tolerances are those of the other parity tests."""
 import numpy as np
 import pytest
 
 from paper_2007_04881_gb300 import configs, dg
 
-from .helpers import compare, dg_problem, oracle_blocks
+from .helpers import compare, dg_problem, oracle_blocks, polygon_workload
 
 pytestmark = pytest.mark.gpu
 
@@ -49,7 +52,7 @@ def run(ctx, wl, prec, path, how="fused", m=None):
     return m, v.double().cpu().numpy(), r.double().cpu().numpy()
 
 
-@pytest.mark.parametrize("path", [0, 1])
+@pytest.mark.parametrize("path", [0, 1, 2])
 @pytest.mark.parametrize("prec", [dg.DG_PREC_FP64, dg.DG_PREC_FP32])
 @pytest.mark.parametrize("which", ["2d", "3d"])
 def test_paths_against_oracle(ctx, path, prec, which):
@@ -61,17 +64,29 @@ def test_paths_against_oracle(ctx, path, prec, which):
     assert ed < TOL[prec] and eo < TOL[prec] and er < TOL_RHS[prec], (ed, eo, er)
 
 
+@pytest.mark.parametrize("path", [1, 2])
 @pytest.mark.parametrize("prec", [dg.DG_PREC_FP64, dg.DG_PREC_FP32])
-def test_moment_path_split_calls(ctx, prec):
+def test_moment_path_split_calls(ctx, prec, path):
     """volume (moments) then faces (row kernel adds to the diagonal), and the
     load vector alone, equal the fused pass within the parity tolerance"""
     wl = configs.small2d(220, 17, 2, 5, b=(1.0, 0.5), c=1.0)
-    m, v1, r1 = run(ctx, wl, prec, 1)
-    _, v2, r2 = run(ctx, wl, prec, 1, how="split", m=m)
+    m, v1, r1 = run(ctx, wl, prec, path)
+    _, v2, r2 = run(ctx, wl, prec, path, how="split", m=m)
     assert np.abs(v1 - v2).max() <= TOL[prec] * np.abs(v1).max()
     assert np.abs(r1 - r2).max() <= TOL[prec] * np.abs(r1).max()
-    _, v3, r3 = run(ctx, wl, prec, 1, m=m)
+    _, v3, r3 = run(ctx, wl, prec, path, m=m)
     assert np.array_equal(v1, v3) and np.array_equal(r1, r3)  # deterministic
+
+
+def test_exact_moments_match_quadrature_moments(ctx):
+    """FP64: the exact moments and the quadrature moments give the same
+    matrix up to rounding, with every 2D degree, advection and reaction; the
+    load vector is the same sum"""
+    wl = configs.small2d(600, 23, 1, 6, b=(1.0, -0.7), c=2.0)
+    m, v1, r1 = run(ctx, wl, dg.DG_PREC_FP64, 1)
+    _, v2, r2 = run(ctx, wl, dg.DG_PREC_FP64, 2, m=m)
+    assert np.abs(v2 - v1).max() <= 1e-12 * np.abs(v1).max()
+    assert np.abs(r2 - r1).max() <= 1e-12 * np.abs(r1).max()
 
 
 def test_moment_path_with_learned_rules(ctx):
@@ -81,11 +96,26 @@ def test_moment_path_with_learned_rules(ctx):
     st = m.dg_quad_fit(None, iters=8, install=True)
     assert st["accepted"] > 0.8 * m.ne
     _, v0, r0 = run(ctx, wl, dg.DG_PREC_FP64, 0, m=m)
-    _, v1, r1 = run(ctx, wl, dg.DG_PREC_FP64, 1, m=m)
-    assert np.abs(v1 - v0).max() <= 1e-12 * np.abs(v0).max()
-    assert np.abs(r1 - r0).max() <= 1e-12 * np.abs(r0).max()
+    for path in (1, 2):
+        _, v1, r1 = run(ctx, wl, dg.DG_PREC_FP64, path, m=m)
+        assert np.abs(v1 - v0).max() <= 1e-12 * np.abs(v0).max(), path
+        assert np.abs(r1 - r0).max() <= 1e-12 * np.abs(r0).max(), path
 
 
-def test_bad_path_rejected(ctx):
+@pytest.mark.parametrize("path", [-1, 3])
+def test_bad_path_rejected(ctx, path):
     with pytest.raises(dg.DGError):
-        ctx.dg_set_volume_path(2)
+        ctx.dg_set_volume_path(path)
+
+
+@pytest.mark.parametrize("p", [3, 6])
+@pytest.mark.parametrize("prec", [dg.DG_PREC_FP64, dg.DG_PREC_FP32])
+def test_exact_moments_long_loop(ctx, p, prec):
+    """a single 20-gon: more edges than the lanes of an element, so a lane
+    takes two; against the oracle's sub-triangle rule"""
+    wl = polygon_workload(20, p)
+    om, ob = oracle_blocks(wl)
+    for path in (1, 2):
+        m, v, r = run(ctx, wl, prec, path)
+        ed, eo, er = compare(dg.to_blocks(m, v, r), om, ob, wl)
+        assert ed < TOL[prec] and er < TOL_RHS[prec], (path, ed, er)
