@@ -115,6 +115,50 @@ def test_fan_rule_moments_match_divergence_theorem(vor64, p):
                 assert abs(got - ex) <= 1e-13 * abs(om.vol[e]), (e, i, j, got, ex)
 
 
+@pytest.mark.parametrize("p", [2, 4, 6])
+def test_green_legendre_moments_with_p_plus_1_edge_points(vor64, p):
+    """The identity behind the exact-moment volume path.  In an element's box
+    coordinates, the integral of P_c(xi) P_d(eta) over the polygon equals the
+    closed integral of Q_c(xi) P_d(eta) d eta, with Q_0 = P_1 and
+    Q_c = (P_{c+1} - P_{c-1}) / (2c + 1).  Along an edge that integrand has
+    degree c + 1 + d <= 2p + 1, so p + 1 Gauss points per edge are exact.
+    The reference is the oracle's fan rule with (p + 2)^2 points per
+    sub-triangle, exact for the same degrees."""
+    from numpy.polynomial import legendre as npl
+
+    def leg(k, x):
+        return npl.legval(x, [0.0] * k + [1.0])
+
+    tr, ts, tw = O.tri_rule(p + 2)
+    g, gw = O.gauss01(p + 1)
+    q = 2 * p
+    for e in range(0, vor64.ne, 9):
+        xs, ys = _loop(vor64, e)
+        xi = 2 * (xs - xs.min()) / (xs.max() - xs.min()) - 1
+        eta = 2 * (ys - ys.min()) / (ys.max() - ys.min()) - 1
+        k = xi.size
+        x1, y1 = np.roll(xi, -1), np.roll(eta, -1)
+        cr = xi * y1 - x1 * eta
+        cx, cy = ((xi + x1) * cr).sum() / (3 * cr.sum()), ((eta + y1) * cr).sum() / (3 * cr.sum())
+        # fan points: (c, v_i, v_{i+1}) for every i
+        ax, ay, bx, by = xi - cx, eta - cy, x1 - cx, y1 - cy
+        det = np.abs(ax * by - ay * bx)
+        FX = cx + np.outer(ax, tr) + np.outer(bx, ts)
+        FY = cy + np.outer(ay, tr) + np.outer(by, ts)
+        FW = np.outer(det, tw)
+        # edge points of the closed integral, counter-clockwise
+        EX = xi[:, None] + np.outer(x1 - xi, g)
+        EY = eta[:, None] + np.outer(y1 - eta, g)
+        EW = np.outer(y1 - eta, gw)
+        for c in range(q + 1):
+            qc = EX if c == 0 else (leg(c + 1, EX) - leg(c - 1, EX)) / (2 * c + 1)
+            pc = leg(c, FX)
+            for d in range(q + 1 - c):
+                fan = np.sum(FW * pc * leg(d, FY))
+                green = np.sum(EW * qc * leg(d, EY))
+                assert abs(green - fan) < 1e-12, (e, k, c, d, green, fan)
+
+
 def test_faces_and_interfaces_counts(vor64):
     om = O.Mesh(vor64)
     nedges = vor64.elem_vptr[-1]
