@@ -482,8 +482,9 @@ def run_ours(args):
             variants.append((args.prec + "_exact_moments", prec, 2))
     for fname, fprec, vpath in variants:
         ctx.dg_set_volume_path(vpath)
-        vf = torch.empty(mesh.nvals, dtype=torch.float32, device="cuda")
-        rf = torch.empty(mesh.ndofs, dtype=torch.float32, device="cuda")
+        dtf = torch.float64 if fprec == dg.DG_PREC_FP64 else torch.float32  # the form's output type
+        vf = torch.empty(mesh.nvals, dtype=dtf, device="cuda")
+        rf = torch.empty(mesh.ndofs, dtype=dtf, device="cuda")
         ctx.dg_set_timing(False)
         gf = mesh.dg_graph_create(fprec, vf, rf, autotune=True)
         for _ in range(2):
