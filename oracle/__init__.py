@@ -47,6 +47,7 @@ class _Problem(C.Structure):
         ("source", C.c_int),
         ("poly", C.c_double * 20),
         ("c_sigma", C.c_double),
+        ("coef", C.c_int),
     ]
 
 
@@ -159,7 +160,9 @@ def basis(dim: int, p: int, lo, hi, x):
     return phi, grad.reshape(n, dim)
 
 
-def make_problem(dim, b=(0.0, 0.0, 0.0), c=0.0, source=0, poly=None, c_sigma=10.0) -> _Problem:
+def make_problem(dim, b=(0.0, 0.0, 0.0), c=0.0, source=0, poly=None, c_sigma=10.0, coef=0) -> _Problem:
+    """coef 0: constant b and c; coef 1: the fields b_d = 1 + x_d, c = 3 + prod x_d of
+    the paper's 3D advection-diffusion-reaction test (Sec. 4.2)."""
     pb = _Problem()
     pb.dim = dim
     for i in range(3):
@@ -170,12 +173,19 @@ def make_problem(dim, b=(0.0, 0.0, 0.0), c=0.0, source=0, poly=None, c_sigma=10.
     for i in range(20):
         pb.poly[i] = float(poly[i]) if i < len(poly) else 0.0
     pb.c_sigma = float(c_sigma)
+    pb.coef = int(coef)
     return pb
 
 
 def exact_u(pb: _Problem, x) -> float:
     x = np.ascontiguousarray(x, dtype=np.float64)
     return _load().orc_exact_u(C.byref(pb), _dp(x))
+
+
+def source_f(pb: _Problem, a: float, x) -> float:
+    """f = -a Lap u + b . grad u + c u at x, with b and c the problem's fields there."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return _load().orc_source_f(C.byref(pb), float(a), _dp(x))
 
 
 class Mesh:

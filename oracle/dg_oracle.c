@@ -213,7 +213,26 @@ typedef struct {
   int source;      /* 0: f = 0, g_D = 0; 1: u = prod sin(pi x_d); 2: u = polynomial */
   double poly[20]; /* coefficients of u for source 2 (graded monomials, degree <= 3) */
   double c_sigma;  /* penalty constant */
+  int coef;        /* 0: b and c the constants above; 1: the fields of the paper's 3D
+                      advection-diffusion-reaction test (Sec. 4.2), see coef_at */
 } orc_problem;
+
+/* Advection and reaction at x.  coef 1 is the paper's multi-GPU test problem
+ * (Sec. 4.2: b = (1+x, 1+y, 1+z), c = 3 + xyz), written for any dimension as
+ * b_d = 1 + x_d and c = 3 + prod_d x_d. */
+static void coef_at(const orc_problem *pb, const double *x, double *b, double *c) {
+  if (pb->coef == 1) {
+    double prod = 1.0;
+    for (int d = 0; d < pb->dim; ++d) {
+      b[d] = 1.0 + x[d];
+      prod *= x[d];
+    }
+    *c = 3.0 + prod;
+  } else {
+    for (int d = 0; d < pb->dim; ++d) b[d] = pb->b[d];
+    *c = pb->c;
+  }
+}
 
 /* Graded monomial exponents up to total degree 3 (2D: 10, 3D: 20). */
 static int poly_exps(int dim, int e[][3]) {
@@ -322,11 +341,12 @@ static void exact_u(const orc_problem *pb, const double *x, double *u, double *g
 /* f = -a Lap u + b . grad u + c u  (Eq. (2.1) with A = a I, a constant on
  * the element); g_D = u. */
 static double source_f(const orc_problem *pb, double a, const double *x) {
-  double u, gu[3], lap;
+  double u, gu[3], lap, b[3], c;
   exact_u(pb, x, &u, gu, &lap);
+  coef_at(pb, x, b, &c);
   double bg = 0.0;
-  for (int d = 0; d < pb->dim; ++d) bg += pb->b[d] * gu[d];
-  return -a * lap + bg + pb->c * u;
+  for (int d = 0; d < pb->dim; ++d) bg += b[d] * gu[d];
+  return -a * lap + bg + c * u;
 }
 
 static double dirichlet_g(const orc_problem *pb, const double *x) {
@@ -817,15 +837,17 @@ static void volume_block(const orc_mesh *m, int e, int p, double a, const orc_pr
   int nq = orc_volume_points(m, e, p + 2, xq, wq);
   double phi[ORC_NMAX], grad[ORC_NMAX * 3];
   for (int q = 0; q < nq; ++q) {
+    double b[3], c;
+    coef_at(pb, &xq[q * dim], b, &c);
     elem_basis(m, e, p, &xq[q * dim], phi, grad);
     for (int i = 0; i < n; ++i)
       for (int j = 0; j < n; ++j) {
         double gg = 0.0, bg = 0.0;
         for (int d = 0; d < dim; ++d) {
           gg += grad[j * dim + d] * grad[i * dim + d];
-          bg += pb->b[d] * grad[j * dim + d];
+          bg += b[d] * grad[j * dim + d];
         }
-        out[i * n + j] += wq[q] * (a * gg + bg * phi[i] + pb->c * phi[j] * phi[i]);
+        out[i * n + j] += wq[q] * (a * gg + bg * phi[i] + c * phi[j] * phi[i]);
       }
   }
   free(xq);
@@ -852,12 +874,14 @@ static void face_blocks(const orc_mesh *m, const orc_face *f, const int *p, cons
   double sig = penalty(m, f, p, a, pb->c_sigma);
   double avg = bnd ? 1.0 : 0.5; /* weight of each side in the average */
   double sgn[2] = {1.0, -1.0};  /* jump [v] = (v_0 - v_1) nF */
-  double bn = 0.0;
-  for (int d = 0; d < dim; ++d) bn += pb->b[d] * f->n[d];
   double xq[4096 * 3], wq[4096];
   int nq = face_points(m, f, pmax + 1, xq, wq);
   double phi[2][ORC_NMAX], grad[2][ORC_NMAX * 3], dn[2][ORC_NMAX];
   for (int q = 0; q < nq; ++q) {
+    /* b . nF at the point: the inflow parts are decided point by point */
+    double b[3], c, bn = 0.0;
+    coef_at(pb, &xq[q * dim], b, &c);
+    for (int d = 0; d < dim; ++d) bn += b[d] * f->n[d];
     for (int s = 0; s < ns; ++s) {
       elem_basis(m, f->e[s], pp[s], &xq[q * dim], phi[s], grad[s]);
       for (int i = 0; i < nb[s]; ++i) {
@@ -901,12 +925,13 @@ static void face_rhs(const orc_mesh *m, const orc_face *f, const int *p, const d
                      const orc_problem *pb, double *out) {
   int dim = m->dim, e = f->e[0], pe = p[e], n = orc_nbasis(dim, pe);
   double sig = penalty(m, f, p, a, pb->c_sigma);
-  double bn = 0.0;
-  for (int d = 0; d < dim; ++d) bn += pb->b[d] * f->n[d];
   double xq[4096 * 3], wq[4096];
   int nq = face_points(m, f, pe + 1, xq, wq);
   double phi[ORC_NMAX], grad[ORC_NMAX * 3];
   for (int q = 0; q < nq; ++q) {
+    double b[3], c, bn = 0.0;
+    coef_at(pb, &xq[q * dim], b, &c);
+    for (int d = 0; d < dim; ++d) bn += b[d] * f->n[d];
     double g = dirichlet_g(pb, &xq[q * dim]);
     elem_basis(m, e, pe, &xq[q * dim], phi, grad);
     for (int i = 0; i < n; ++i) {

@@ -25,8 +25,8 @@ MUTATIONS = {
         "/* dropped */",
     ),
     "transposed_advection": (
-        "bg += pb->b[d] * grad[j * dim + d];",
-        "bg += pb->b[d] * grad[i * dim + d];",
+        "bg += b[d] * grad[j * dim + d];",
+        "bg += b[d] * grad[i * dim + d];",
     ),
     "legendre_derivative_index": (
         "dP[k + 1] = dP[k - 1] + (2.0 * k + 1.0) * P[k];",
@@ -43,6 +43,14 @@ MUTATIONS = {
     "penalty_min_instead_of_max": (
         "if (v > s) s = v;",
         "if (s == 0.0 || v < s) s = v;",
+    ),
+    "variable_field_sign": (
+        "b[d] = 1.0 + x[d];",
+        "b[d] = 1.0 - x[d];",
+    ),
+    "variable_coefficients_at_centroid": (
+        "coef_at(pb, &xq[q * dim], b, &c);",
+        "coef_at(pb, &m->cen[e * dim], b, &c);",
     ),
     "average_weight_on_boundary": (
         "double avg = bnd ? 1.0 : 0.5;",
@@ -101,6 +109,28 @@ def _pins_pass(O) -> bool:
             xq, _ = om.volume_points(e, 3)
             for x in xq[::7]:
                 phi, _ = O.basis(2, int(p[e]), om.lo[e], om.hi[e], x)
+                if abs(phi @ U[off[e]:off[e + 1]] - O.exact_u(pb, x)) > 1e-9:
+                    return False
+        # the coefficient fields of coef 1 through the source term ...
+        pbc = O.make_problem(2, source=1, coef=1)
+        x = np.array([0.3, 0.7])
+        sx, cx = np.sin(np.pi * x), np.cos(np.pi * x)
+        grad = np.pi * np.array([cx[0] * sx[1], sx[0] * cx[1]])
+        f = 0.5 * 2 * np.pi ** 2 * sx.prod() + (1 + x) @ grad + (3 + x.prod()) * sx.prod()
+        if abs(O.source_f(pbc, 0.5, x) - f) > 1e-12 * abs(f):
+            return False
+        # ... and polynomial reproduction with them
+        om = O.Mesh(mg.voronoi_square(24, 9))
+        p = np.full(om.ne, 2, dtype=np.int32)
+        a = np.full(om.ne, 0.5)
+        pb = O.make_problem(2, source=2, poly=[1, 0.5, -1, 0.3, 0.2, -0.4], coef=1)
+        blk = om.assemble(p, a, pb)
+        A, F, off = O.global_matrix(om, p, blk)
+        U = np.linalg.solve(A, F)
+        for e in range(om.ne):
+            xq, _ = om.volume_points(e, 3)
+            for x in xq[::7]:
+                phi, _ = O.basis(2, 2, om.lo[e], om.hi[e], x)
                 if abs(phi @ U[off[e]:off[e + 1]] - O.exact_u(pb, x)) > 1e-9:
                     return False
         return True

@@ -410,6 +410,76 @@ def test_polynomial_reproduction_2d(b, c, poly, plo, phi_):
     assert _solve_and_error(om, p, a, pb) < 1e-9
 
 
+def test_variable_coefficient_fields_through_the_source():
+    """coef 1 is the paper's multi-GPU test problem (Sec. 4.2): b = (1+x, 1+y(, 1+z)),
+    c = 3 + xy(z).  Checked through f = -a Lap u + b . grad u + c u for
+    u = prod sin(pi x_d), with the derivatives of u written out here."""
+    rng = np.random.default_rng(8)
+    for dim in (2, 3):
+        pb = O.make_problem(dim, source=1, coef=1)
+        for _ in range(20):
+            x = rng.uniform(0.0, 1.0, dim)
+            a = float(rng.uniform(0.01, 2.0))
+            s, c = np.sin(np.pi * x), np.cos(np.pi * x)
+            u = np.prod(s)
+            grad = np.array([np.pi * c[d] * np.prod(np.delete(s, d)) for d in range(dim)])
+            lap = -dim * np.pi ** 2 * u
+            b, cc = 1.0 + x, 3.0 + np.prod(x)
+            f = -a * lap + b @ grad + cc * u
+            assert abs(O.source_f(pb, a, x) - f) < 1e-12 * (1 + abs(f)), (dim, x, f)
+
+
+@pytest.mark.parametrize(
+    "poly,plo,phi_",
+    [
+        ([1, 1, -2, 0, 1, 0], 2, 2),
+        ([0.5, -1, 2, 1, 0.5, -0.7], 2, 4),
+        ([2, -1, 0.5], 1, 3),
+        ([0, 1, 0, 0, 0, 0, 0.5, -1, 0.25, 1], 3, 4),
+    ],
+)
+def test_polynomial_reproduction_2d_variable_coefficients(poly, plo, phi_):
+    """dG consistency with the coefficient fields of coef 1: for u in P_p and
+    f from the same fields, the discrete solution is u.  The rule stays exact:
+    c u v has degree 2 + 2p <= 2p + 2, and the upwind jumps of a continuous u
+    and the boundary inflow terms cancel point by point, where b . n changes
+    sign along a face too."""
+    mesh = mg.voronoi_square(40, 23)
+    om = O.Mesh(mesh)
+    p = mg.draw_degrees(om.ne, 23, plo, phi_).astype(np.int32)
+    a = np.full(om.ne, 0.37)  # a jump in a would break the flux continuity u needs
+    pb = O.make_problem(2, source=2, poly=poly, c_sigma=10.0, coef=1)
+    assert _solve_and_error(om, p, a, pb) < 1e-9
+
+
+def test_convergence_rate_variable_coefficients():
+    """h^(p+1) L2 convergence for u = sin(pi x) sin(pi y) with the fields of
+    coef 1 and a = 1."""
+    import scipy.sparse as sps
+    import scipy.sparse.linalg as spla
+
+    for pdeg in (1, 2):
+        errs = []
+        for nsites in (64, 256, 1024):
+            mesh = mg.voronoi_square(nsites, 300 + nsites)
+            om = O.Mesh(mesh)
+            p = np.full(om.ne, pdeg, dtype=np.int32)
+            a = np.ones(om.ne)
+            pb = O.make_problem(2, source=1, c_sigma=10.0, coef=1)
+            blk = om.assemble(p, a, pb)
+            A, F, off = O.global_matrix(om, p, blk)
+            U = spla.spsolve(sps.csr_matrix(A), F)
+            e2 = 0.0
+            for e in range(om.ne):
+                xq, wq = om.volume_points(e, pdeg + 3)
+                for x, w in zip(xq, wq):
+                    phi, _ = O.basis(2, pdeg, om.lo[e], om.hi[e], x)
+                    e2 += w * (phi @ U[off[e]:off[e + 1]] - O.exact_u(pb, x)) ** 2
+            errs.append(math.sqrt(e2))
+        rate_n = math.log(errs[0] / errs[2]) / math.log(2.0 ** 2) * 2  # h ~ N^-1/2
+        assert rate_n > pdeg + 1 - 0.25, (pdeg, errs)
+
+
 def test_convergence_rate_sin_solution():
     """h^(p+1) L2 convergence for u = sin(pi x) sin(pi y) (config-0 family)."""
     import scipy.sparse as sps
