@@ -97,6 +97,8 @@ def _load():
         lib.orc_moment_divergence2d.restype = C.c_double
         lib.orc_volume_block.argtypes = [C.c_void_p, C.c_int, _I, _D, C.POINTER(_Problem), _D]
         lib.orc_face_info.argtypes = [C.c_void_p, C.c_int, _I, _I, _D, _D]
+        lib.orc_face_points.argtypes = [C.c_void_p, C.c_int, C.c_int, _D, _D]
+        lib.orc_face_points.restype = C.c_int
         lib.orc_face_blocks.argtypes = [C.c_void_p, C.c_int, _I, _D, C.POINTER(_Problem), _D, _D, _D, _D]
         lib.orc_exact_u.argtypes = [C.POINTER(_Problem), _D]
         lib.orc_exact_u.restype = C.c_double
@@ -298,6 +300,14 @@ class Mesh:
         nrm = np.zeros(3)
         _load().orc_face_info(self._h, int(k), C.byref(e0), C.byref(e1), _dp(area), _dp(nrm))
         return e0.value, e1.value, float(area[0]), nrm[: self.dim].copy()
+
+    def face_points(self, k: int, n: int):
+        """The n-point rule of face k: points [q][dim] and weights (with the face
+        measure)."""
+        xq = np.zeros(n * n * 3)
+        wq = np.zeros(n * n)
+        q = _load().orc_face_points(self._h, int(k), int(n), _dp(xq), _dp(wq))
+        return xq[: q * self.dim].reshape(q, self.dim), wq[:q]
 
     def face_blocks(self, k: int, p, a, pb: _Problem):
         p = np.ascontiguousarray(p, dtype=np.int32)

@@ -1098,6 +1098,12 @@ void orc_face_info(const orc_mesh *m, int k, int *e0, int *e1, double *area, dou
   for (int d = 0; d < 3; ++d) normal[d] = f->n[d];
 }
 
+/* The n-point rule on face k (the rule the face terms use): points xq
+ * [q][dim] and weights wq[q] including the face measure; returns q. */
+int orc_face_points(const orc_mesh *m, int k, int n, double *xq, double *wq) {
+  return face_points(m, &m->f[k], n, xq, wq);
+}
+
 /* All blocks of face k alone: b00 (n0 x n0), b01, b10, b11 (NULL allowed). */
 void orc_face_blocks(const orc_mesh *m, int k, const int *p, const double *a,
                      const orc_problem *pb, double *b00, double *b01, double *b10, double *b11) {
