@@ -414,6 +414,75 @@ int dg_volume_noalloc(void *stream, int device, int prec, int p, int nv, const d
                       int ne, int nsub, const int *elem_ptr, const int *elem_idx, const double *a, double bx,
                       double by, double c, void *blocks);
 
+/* Space-time slabs (Sec. 2.3).  The slab (t0, t1] x D over an uploaded mesh
+ * is cut into prisms kappa x (t0, t1].  A prism of degree p carries the
+ * basis T_k(t) phi_j(x): T_k = sqrt((2k+1)/tau) P_k(2 (t - t0)/tau - 1), the
+ * Legendre polynomials orthonormal on the slab (tau = t1 - t0), times the
+ * element's spatial basis phi_j.  Its dofs i = (k, j) run k-major:
+ *   DG_SPACE_P:  k = 0..p, j < nbasis(dim, p - k)  (space-time total degree <= p)
+ *   DG_SPACE_PQ: k = 0..p, j < nbasis(dim, p)      (degree <= p in t and in x)
+ * nbasis(2, q) = (q+1)(q+2)/2, nbasis(3, q) = (q+1)(q+2)(q+3)/6, and j follows
+ * the spatial order, so j < nbasis(dim, q) is exactly the degree <= q part.
+ *
+ * The slab system is the time-discontinuous Galerkin form of Sec. 2.3 for
+ * u_t - div(a grad u) + b.grad u + c u = f with the mesh's coefficients,
+ * source and Dirichlet data (all constant in time):
+ *   int_(t0,t1] [(U_t, W) + B(U, W)] dt + (U(t0+), W(t0+))
+ *     = int_(t0,t1] l(W) dt + (u_prev, W(t0+)),
+ * B and l the spatial forms of Eqs. (2.4) and (2.5); a lateral face
+ * F x (t0, t1] takes F's spatial penalty.  Its block pattern is the mesh's;
+ * block (r, s) holds nt_r x nt_s entries, row-major, rows the test
+ * functions of r, nt the dofs of a prism.
+ *
+ * HOST arithmetic only, no GPU: the slab offsets of a block pattern.
+ * row_ptr [ne+1], col [nnzb] (the layout of dg_bsr_pattern), p [ne] degrees
+ * (1..DG_PMAX_2D / DG_PMAX_3D); out: blk_off [nnzb+1] (offsets of the slab
+ * blocks in vals) and dof_off [ne+1] (of each prism's entries in the load
+ * vector), caller-owned host arrays, either may be NULL.  DG_ERR_ARG on a
+ * bad dim, space, degree, row_ptr or column. */
+#define DG_SPACE_P 0
+#define DG_SPACE_PQ 1
+int dg_slab_offsets(int dim, int ne, const int *row_ptr, const int *col, const int *p, int space,
+                    int64_t *blk_off, int64_t *dof_off);
+
+/* Sizes of the mesh's slab system: nvals block values, ndofs load-vector
+ * entries (either pointer may be NULL).  Meshes from dg_mesh_upload and
+ * dg_batch_upload; DG_ERR_ARG for a partition mesh or a bad space. */
+int dg_slab_layout(const dg_mesh *mesh, int space, int64_t *nvals, int64_t *ndofs);
+
+/* Assemble the slab system of (t0, t1] (t0 < t1, both finite):
+ *   vals (device, the slab layout's nvals entries, double for DG_PREC_FP64,
+ *     float for DG_PREC_FP32; OVERWRITTEN) the block values;
+ *   rhs (device, ndofs entries of the same type, OVERWRITTEN; may be NULL)
+ *     the load vector  rhs(k, j) = [k = 0] sqrt(tau) l_j + T_k(t0+) (M u_prev)_j,
+ *     l the element's spatial load vector (constant-in-time data against
+ *     T_k integrate to sqrt(tau) for k = 0 and to 0 otherwise) and M its
+ *     spatial mass matrix;
+ *   u_prev (device, the mesh's spatial ndofs entries in the same type; NULL
+ *     = zero): the spatial coefficients of U(t0-), the previous slab's
+ *     trace (dg_slab_trace) or the initial value's coefficients.
+ * How: with the orthonormal T_k every block is
+ *   A[(k, j), (l, m)] = [k = l] B[j, m] + [r = s] D_kl M[j, m],
+ *   D_kl = int T_l' T_k dt + T_l(t0+) T_k(t0+)
+ *        = sqrt((2k+1)(2l+1)) / tau (2 [k < l, k + l odd] + (-1)^(k+l)),
+ * B the spatial block of Eq. (2.4).  The call runs the row kernels for B
+ * and l, and once more for M (the volume pass with a = 0, b = 0, c = 1), into
+ * library-owned device scratch of 2 nvals + ndofs entries of the spatial
+ * layout (allocated at the first call, freed with the mesh), then one
+ * expansion kernel writes vals and one writes rhs.  The volume path is the
+ * context's (dg_set_volume_path).  DG_PREC_BF16X3 / DG_PREC_TF32X3:
+ * DG_ERR_ARG.  Asynchronous on the context stream. */
+int dg_assemble_slab(dg_ctx *ctx, dg_mesh *mesh, int prec, int space, double t0, double t1,
+                     const void *u_prev, void *vals, void *rhs);
+
+/* The trace U(t1-) of a slab solution in the spatial basis:
+ *   u_end_j = sum_k U(k, j) T_k(t1),  T_k(t1) = sqrt((2k+1)/tau),
+ * over the k that carry j.  U: device, the slab layout's ndofs entries;
+ * u_end: device, the mesh's spatial ndofs entries, OVERWRITTEN; double for
+ * DG_PREC_FP64, float for DG_PREC_FP32.  Asynchronous on the context stream. */
+int dg_slab_trace(dg_ctx *ctx, const dg_mesh *mesh, int prec, int space, double t0, double t1, const void *U,
+                  void *u_end);
+
 /* Wait for all work on the context stream; reports device-side errors. */
 int dg_sync(dg_ctx *ctx);
 

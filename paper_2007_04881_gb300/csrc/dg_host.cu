@@ -20,6 +20,7 @@
 
 #include "../../include/dg.h"
 #include "dg_internal.h"
+#include "dg_slab.cuh"
 
 using namespace dg;
 
@@ -280,6 +281,14 @@ struct dg_mesh {
   int *lq_elig = nullptr, *lq_ok = nullptr, *lq_okm = nullptr;
   void* lq_feat = nullptr;
   int* perm_dev = nullptr;  // device work list (owned by bufs)
+  // space-time slabs, per space (DG_SPACE_P, DG_SPACE_PQ): block and dof
+  // offsets on the host and the device (owned by bufs), and the scratch of
+  // the spatial pass: blocks B, mass matrix M (diagonal blocks' places),
+  // load vector l, and the zero diffusion of the mass pass
+  std::vector<int64_t> slab_blk_h[2], slab_dof_h[2];
+  int64_t* slab_blk[2] = {nullptr, nullptr};
+  int64_t* slab_dof[2] = {nullptr, nullptr};
+  double *slab_B = nullptr, *slab_M = nullptr, *slab_l = nullptr, *slab_zero_a = nullptr;
   ~dg_mesh() {
     if (h_vals) cudaFree(h_vals);
     if (h_rhs) cudaFree(h_rhs);
@@ -1138,6 +1147,24 @@ int dg_mesh_update(dg_ctx* ctx, dg_mesh* mesh, const double* x, const double* y,
   return dg_geometry(ctx, mesh);
 }
 
+// The row-kernel launches of one pass over m in precision prec; returns the
+// number of launches.
+static int dispatch_rows(const DevMesh& m, int prec, int mode, void* vals, void* rhs, int sm_count,
+                         const LaunchOpts& lo, Tracer* tr) {
+  if (prec == DG_PREC_FP64) {
+    double* v = static_cast<double*>(vals);
+    double* r = static_cast<double*>(rhs);
+    return m.dim == 2 ? launch_row2d_f64(m, mode, v, r, sm_count, lo, tr) : launch_row3d_f64(m, mode, v, r, sm_count, lo, tr);
+  }
+  float* v = static_cast<float*>(vals);
+  float* r = static_cast<float*>(rhs);
+  if (prec == DG_PREC_FP32)
+    return m.dim == 2 ? launch_row2d_f32(m, mode, v, r, sm_count, lo, tr) : launch_row3d_f32(m, mode, v, r, sm_count, lo, tr);
+  if (prec == DG_PREC_BF16X3)
+    return m.dim == 2 ? launch_row2d_bf16(m, mode, v, r, sm_count, lo, tr) : launch_row3d_bf16(m, mode, v, r, sm_count, lo, tr);
+  return m.dim == 2 ? launch_row2d_tf32(m, mode, v, r, sm_count, lo, tr) : launch_row3d_tf32(m, mode, v, r, sm_count, lo, tr);
+}
+
 // Issue the row kernels of one assembly pass on stream st.  concurrent:
 // the per-degree launches go to forked side streams and join back into st.
 // vpath: volume path (0 per-point contraction, 1 moments, 2 exact 2D moments), -1 the context's
@@ -1168,25 +1195,7 @@ static int run_assembly(dg_ctx* ctx, const dg_mesh* mesh, int prec, int mode, vo
     // highest degrees (longest launches) first on their own streams
     for (int p = 1; p < 9; ++p) lo.pst[p] = ss->side[(8 - p) % 4];
   }
-  int n = 0;
-  if (prec == DG_PREC_FP64) {
-    double* v = static_cast<double*>(vals);
-    double* r = static_cast<double*>(rhs);
-    n += m.dim == 2 ? launch_row2d_f64(m, mode, v, r, ctx->sm_count, lo, tr) : launch_row3d_f64(m, mode, v, r, ctx->sm_count, lo, tr);
-  } else if (prec == DG_PREC_FP32) {
-    float* v = static_cast<float*>(vals);
-    float* r = static_cast<float*>(rhs);
-    n += m.dim == 2 ? launch_row2d_f32(m, mode, v, r, ctx->sm_count, lo, tr) : launch_row3d_f32(m, mode, v, r, ctx->sm_count, lo, tr);
-  } else {
-    float* v = static_cast<float*>(vals);
-    float* r = static_cast<float*>(rhs);
-    if (prec == DG_PREC_BF16X3)
-      n += m.dim == 2 ? launch_row2d_bf16(m, mode, v, r, ctx->sm_count, lo, tr)
-                      : launch_row3d_bf16(m, mode, v, r, ctx->sm_count, lo, tr);
-    else
-      n += m.dim == 2 ? launch_row2d_tf32(m, mode, v, r, ctx->sm_count, lo, tr)
-                      : launch_row3d_tf32(m, mode, v, r, ctx->sm_count, lo, tr);
-  }
+  const int n = dispatch_rows(m, prec, mode, vals, rhs, ctx->sm_count, lo, tr);
   if (concurrent) {
     for (int i = 0; i < 4; ++i) {
       DG_CUDA_TRY(cudaEventRecord(ss->join[i], ss->side[i]));
@@ -1287,6 +1296,160 @@ int dg_assemble_step(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs
   step_shape(ctx, mesh, prec, &occ, &conc, &path);
   const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
   return run_assembly(ctx, mesh, prec, mode, vals, rhs, true, false, nullptr, true, occ, conc, path);
+}
+
+// ---------------------------------------------------------------------------
+// Space-time slabs (Sec. 2.3): prisms kappa x (t0, t1], the slab system
+// expanded from the spatial blocks by the slab kernels (dg_slab.cu).
+// ---------------------------------------------------------------------------
+
+int dg_slab_offsets(int dim, int ne, const int* row_ptr, const int* col, const int* p, int space, int64_t* blk_off,
+                    int64_t* dof_off) {
+  if (dim != 2 && dim != 3) return fail(DG_ERR_ARG, "dg_slab_offsets: dim %d", dim);
+  if (space != DG_SPACE_P && space != DG_SPACE_PQ) return fail(DG_ERR_ARG, "dg_slab_offsets: space %d", space);
+  if (ne < 0) return fail(DG_ERR_ARG, "dg_slab_offsets: ne %d", ne);
+  if (ne > 0 && (!p || (blk_off && (!row_ptr || !col)))) return fail(DG_ERR_ARG, "dg_slab_offsets: null array");
+  const int pmax = dim == 2 ? kPMax2 : kPMax3;
+  for (int e = 0; e < ne; ++e)
+    if (p[e] < 1 || p[e] > pmax) return fail(DG_ERR_ARG, "dg_slab_offsets: element %d: p = %d outside 1..%d", e, p[e], pmax);
+  if (dof_off) {
+    dof_off[0] = 0;
+    for (int e = 0; e < ne; ++e) dof_off[e + 1] = dof_off[e] + slab_count(dim, p[e], space);
+  }
+  if (blk_off) {
+    blk_off[0] = 0;
+    if (ne > 0 && row_ptr[0] != 0) return fail(DG_ERR_ARG, "dg_slab_offsets: row_ptr[0] must be 0");
+    for (int r = 0; r < ne; ++r) {
+      if (row_ptr[r + 1] < row_ptr[r]) return fail(DG_ERR_ARG, "dg_slab_offsets: row_ptr decreases at %d", r);
+      const int64_t nr = slab_count(dim, p[r], space);
+      for (int b = row_ptr[r]; b < row_ptr[r + 1]; ++b) {
+        const int c = col[b];
+        if (c < 0 || c >= ne) return fail(DG_ERR_ARG, "dg_slab_offsets: column %d out of range", c);
+        blk_off[b + 1] = blk_off[b] + nr * slab_count(dim, p[c], space);
+      }
+    }
+  }
+  return DG_OK;
+}
+
+// Host offsets of the slab layout (computed once per space) and, with a
+// context, their device copies and the spatial scratch.
+static int slab_prepare(dg_ctx* ctx, dg_mesh* mesh, int space, const char* who) {
+  if (!mesh->part_elem.empty()) return fail(DG_ERR_ARG, "%s: partition meshes are not supported", who);
+  if (space != DG_SPACE_P && space != DG_SPACE_PQ) return fail(DG_ERR_ARG, "%s: space %d", who, space);
+  const int ne = mesh->dm.ne;
+  const size_t nnzb = mesh->col.size();
+  if (mesh->slab_dof_h[space].empty()) {
+    std::vector<int64_t> bo(nnzb + 1), dofs((size_t)ne + 1);
+    const int rc = dg_slab_offsets(mesh->dm.dim, ne, mesh->row_ptr.data(), mesh->col.data(), mesh->p_h.data(), space,
+                                   bo.data(), dofs.data());
+    if (rc != DG_OK) return rc;
+    mesh->slab_blk_h[space] = std::move(bo);
+    mesh->slab_dof_h[space] = std::move(dofs);
+  }
+  if (!ctx) return DG_OK;
+  if (!mesh->slab_blk[space]) {
+    int64_t *bo = nullptr, *dofs = nullptr;
+    DG_CUDA_TRY(mesh->bufs.alloc(&bo, nnzb + 1));
+    DG_CUDA_TRY(mesh->bufs.alloc(&dofs, (size_t)ne + 1));
+    DG_CUDA_TRY(cudaMemcpy(bo, mesh->slab_blk_h[space].data(), (nnzb + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+    DG_CUDA_TRY(cudaMemcpy(dofs, mesh->slab_dof_h[space].data(), ((size_t)ne + 1) * sizeof(int64_t),
+                           cudaMemcpyHostToDevice));
+    mesh->slab_blk[space] = bo;
+    mesh->slab_dof[space] = dofs;
+  }
+  if (!mesh->slab_B) {
+    double *B = nullptr, *M = nullptr, *l = nullptr, *a0 = nullptr;
+    DG_CUDA_TRY(mesh->bufs.alloc(&B, (size_t)mesh->info.nvals));
+    DG_CUDA_TRY(mesh->bufs.alloc(&M, (size_t)mesh->info.nvals));
+    DG_CUDA_TRY(mesh->bufs.alloc(&l, (size_t)mesh->info.ndofs));
+    DG_CUDA_TRY(mesh->bufs.alloc(&a0, (size_t)ne));
+    DG_CUDA_TRY(cudaMemset(a0, 0, std::max<size_t>(ne, 1) * sizeof(double)));
+    mesh->slab_B = B;
+    mesh->slab_M = M;
+    mesh->slab_l = l;
+    mesh->slab_zero_a = a0;
+  }
+  return DG_OK;
+}
+
+static SlabPattern slab_pattern(const dg_mesh* mesh, int space) {
+  const DevMesh& m = mesh->dm;
+  SlabPattern sp;
+  sp.dim = m.dim;
+  sp.ne = m.ne;
+  sp.space = space;
+  sp.p = m.p;
+  sp.row_ptr = m.row_ptr;
+  sp.col = m.col;
+  sp.diag_blk = m.diag_blk;
+  sp.blk_off = m.blk_off;
+  sp.dof_off = m.dof_off;
+  sp.sblk_off = mesh->slab_blk[space];
+  sp.sdof_off = mesh->slab_dof[space];
+  return sp;
+}
+
+int dg_slab_layout(const dg_mesh* mesh, int space, int64_t* nvals, int64_t* ndofs) {
+  if (!mesh) return fail(DG_ERR_ARG, "dg_slab_layout: null mesh");
+  dg_mesh* m = const_cast<dg_mesh*>(mesh);  // caches the host offsets
+  const int rc = slab_prepare(nullptr, m, space, "dg_slab_layout");
+  if (rc != DG_OK) return rc;
+  if (nvals) *nvals = m->slab_blk_h[space].back();
+  if (ndofs) *ndofs = m->slab_dof_h[space].back();
+  return DG_OK;
+}
+
+int dg_assemble_slab(dg_ctx* ctx, dg_mesh* mesh, int prec, int space, double t0, double t1, const void* u_prev,
+                     void* vals, void* rhs) {
+  if (!ctx || !mesh || !vals) return fail(DG_ERR_ARG, "dg_assemble_slab: null argument");
+  if (prec != DG_PREC_FP64 && prec != DG_PREC_FP32)
+    return fail(DG_ERR_ARG, "dg_assemble_slab: precision %d (DG_PREC_FP64 or DG_PREC_FP32)", prec);
+  if (!std::isfinite(t0) || !std::isfinite(t1) || !(t1 > t0))
+    return fail(DG_ERR_ARG, "dg_assemble_slab: the slab needs finite t0 < t1");
+  int rc = slab_prepare(ctx, mesh, space, "dg_assemble_slab");
+  if (rc != DG_OK) return rc;
+  // B and l: the spatial pass
+  rc = run_assembly(ctx, mesh, prec, kModeVol | kModeFace | (rhs ? kModeRhs : 0), mesh->slab_B,
+                    rhs ? mesh->slab_l : nullptr, true);
+  if (rc != DG_OK) return rc;
+  int n = ctx->last_launches;
+  // M: the volume pass of the same rules with a = 0, b = 0, c = 1
+  DevMesh mm = mesh->dm;
+  for (int d = 0; d < 3; ++d) mm.pb.b[d] = 0.0;
+  mm.pb.c = 1.0;
+  mm.pb.round_copies();
+  mm.a = mesh->slab_zero_a;
+  LaunchOpts lo;
+  lo.vol_moments = ctx->vol_moments && !mesh->dm.lq_ok;
+  lo.vol_exact = lo.vol_moments && ctx->vol_exact;
+  for (int p = 0; p < 9; ++p) lo.pst[p] = ctx->stream;
+  n += dispatch_rows(mm, prec, kModeVol, mesh->slab_M, nullptr, ctx->sm_count, lo, &ctx->tracer);
+  DG_CUDA_TRY(cudaGetLastError());
+  const SlabPattern sp = slab_pattern(mesh, space);
+  const SlabTimes<double> tt = slab_time_data(t0, t1);
+  const bool fp32 = prec == DG_PREC_FP32;
+  n += launch_slab_matrix(sp, tt, fp32, mesh->slab_B, mesh->slab_M, vals, ctx->sm_count, ctx->stream);
+  if (rhs) n += launch_slab_rhs(sp, tt, fp32, mesh->slab_l, mesh->slab_M, u_prev, rhs, ctx->sm_count, ctx->stream);
+  DG_CUDA_TRY(cudaGetLastError());
+  ctx->last_launches = n;
+  return DG_OK;
+}
+
+int dg_slab_trace(dg_ctx* ctx, const dg_mesh* mesh, int prec, int space, double t0, double t1, const void* U,
+                  void* u_end) {
+  if (!ctx || !mesh || !U || !u_end) return fail(DG_ERR_ARG, "dg_slab_trace: null argument");
+  if (prec != DG_PREC_FP64 && prec != DG_PREC_FP32)
+    return fail(DG_ERR_ARG, "dg_slab_trace: precision %d (DG_PREC_FP64 or DG_PREC_FP32)", prec);
+  if (!std::isfinite(t0) || !std::isfinite(t1) || !(t1 > t0))
+    return fail(DG_ERR_ARG, "dg_slab_trace: the slab needs finite t0 < t1");
+  dg_mesh* m = const_cast<dg_mesh*>(mesh);  // caches the offsets and scratch
+  const int rc = slab_prepare(ctx, m, space, "dg_slab_trace");
+  if (rc != DG_OK) return rc;
+  ctx->last_launches = launch_slab_trace(slab_pattern(m, space), slab_time_data(t0, t1), prec == DG_PREC_FP32, U, u_end,
+                                         ctx->sm_count, ctx->stream);
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
 }
 
 int dg_batch_upload(dg_ctx* ctx, const dg_mesh_desc* const* descs, int n, dg_mesh** out) {

@@ -32,6 +32,7 @@ DG_PREC_BF16X3 = 2
 DG_PREC_TF32X3 = 3
 DG_SRC_ZERO, DG_SRC_SINPROD, DG_SRC_POLY = 0, 1, 2
 DG_PMAX_2D, DG_PMAX_3D = 6, 4
+DG_SPACE_P, DG_SPACE_PQ = 0, 1
 
 
 class DGError(RuntimeError):
@@ -144,6 +145,10 @@ def load() -> C.CDLL:
     lib.dg_part_check.argtypes = [C.POINTER(dg_mesh_desc), V, C.c_int, C.POINTER(dg_bsr_info), V, V, V, V, V, V]
     lib.dg_sync.argtypes = [V]
     lib.dg_last_launch_count.argtypes = [V]
+    lib.dg_slab_offsets.argtypes = [C.c_int, C.c_int, V, V, V, C.c_int, V, V]
+    lib.dg_slab_layout.argtypes = [V, C.c_int, V, V]
+    lib.dg_assemble_slab.argtypes = [V, V, C.c_int, C.c_int, C.c_double, C.c_double, V, V, V]
+    lib.dg_slab_trace.argtypes = [V, V, C.c_int, C.c_int, C.c_double, C.c_double, V, V]
     _lib = lib
     return lib
 
@@ -160,6 +165,7 @@ EXPORTS = (
     "dg_mlp_create", "dg_mlp_free", "dg_mlp_num_params", "dg_mlp_get_params", "dg_mlp_set_params",
     "dg_mlp_get_state", "dg_mlp_set_state", "dg_mlp_forward", "dg_mlp_grad", "dg_mlp_train_step",
     "dg_partition", "dg_mesh_upload_part", "dg_part_map", "dg_part_check", "dg_set_volume_path",
+    "dg_slab_offsets", "dg_slab_layout", "dg_assemble_slab", "dg_slab_trace",
 )
 
 
@@ -286,6 +292,19 @@ def dg_mesh_check(mesh, p, a, problem: Problem, pattern: bool = False):
     blk_off = np.zeros(info.nnzb + 1, np.int64)
     _check(lib.dg_mesh_check(C.byref(d), C.byref(info), _vp(row_ptr), _vp(col), _vp(blk_off)))
     return info, row_ptr, col, blk_off
+
+
+def dg_slab_offsets(dim: int, row_ptr, col, p, space: int):
+    """Host-only slab layout of a block pattern: (blk_off [nnzb+1], dof_off [ne+1])."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    p = np.ascontiguousarray(p, dtype=np.int32)
+    ne = p.size
+    blk_off = np.zeros(col.size + 1, np.int64)
+    dof_off = np.zeros(ne + 1, np.int64)
+    _check(load().dg_slab_offsets(int(dim), int(ne), _vp(row_ptr), _vp(col), _vp(p), int(space), _vp(blk_off),
+                                  _vp(dof_off)))
+    return blk_off, dof_off
 
 
 def dg_partition(mesh, p, a, problem: Problem, nparts: int) -> np.ndarray:
@@ -435,6 +454,25 @@ class Mesh:
 
     def dg_quad_clear(self):
         _check(load().dg_quad_clear(self.ctx._h, self._h))
+
+    def dg_slab_layout(self, space: int):
+        """(nvals, ndofs) of the space-time slab system over this mesh."""
+        nv, nd = C.c_int64(), C.c_int64()
+        _check(load().dg_slab_layout(self._h, int(space), C.byref(nv), C.byref(nd)))
+        return nv.value, nd.value
+
+    def dg_slab_pattern(self, space: int):
+        """Host (blk_off, dof_off) of the slab system; the block graph is dg_bsr_pattern's."""
+        row_ptr, col, _, _ = self.dg_bsr_pattern()
+        return dg_slab_offsets(self.dim, row_ptr, col, self.p, space)
+
+    def dg_assemble_slab(self, prec: int, space: int, t0: float, t1: float, vals, rhs=None, u_prev=None):
+        _check(load().dg_assemble_slab(self.ctx._h, self._h, prec, int(space), float(t0), float(t1), _vp(u_prev),
+                                       _vp(vals), _vp(rhs)))
+
+    def dg_slab_trace(self, prec: int, space: int, t0: float, t1: float, U, u_end):
+        _check(load().dg_slab_trace(self.ctx._h, self._h, prec, int(space), float(t0), float(t1), _vp(U),
+                                    _vp(u_end)))
 
     def dg_assemble_step(self, prec: int, vals, rhs=None):
         _check(load().dg_assemble_step(self.ctx._h, self._h, prec, _vp(vals), _vp(rhs)))

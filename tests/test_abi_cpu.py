@@ -166,3 +166,40 @@ def test_precision_flags_match_header(lib):
     hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "dg.h")).read()
     for name, val in (("DG_PREC_BF16X3", 2), ("DG_PREC_TF32X3", 3)):
         assert f"#define {name} {val}" in hdr
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("space", [dg.DG_SPACE_P, dg.DG_SPACE_PQ])
+def test_slab_offsets(lib, dim, space):
+    """Space-time slab layout (host only): a prism of degree p has
+    C(p + dim + 1, dim + 1) dofs in P and (p + 1) C(p + dim, dim) in PQ; 2D
+    dof offsets equal the slab oracle's, and block (r, s) holds nt_r nt_s."""
+    import math
+
+    wl = configs.small2d(150, 3, 1, 6) if dim == 2 else configs.small3d(4, 12, 5, 1, 4)
+    info, row_ptr, col, _ = _check(wl)
+    p = wl.p.astype(np.int32)
+    blk_off, dof_off = dg.dg_slab_offsets(dim, row_ptr, col, p, space)
+    nt = np.array([math.comb(int(q) + dim + 1, dim + 1) if space == dg.DG_SPACE_P
+                   else (int(q) + 1) * math.comb(int(q) + dim, dim) for q in p])
+    assert np.array_equal(np.diff(dof_off), nt)
+    sizes = [nt[r] * nt[c] for r in range(info.ne) for c in col[row_ptr[r]:row_ptr[r + 1]]]
+    assert np.array_equal(np.diff(blk_off), sizes) and blk_off[0] == 0
+    if dim == 2:
+        from oracle import spacetime as S
+
+        sl = S.Slab(O.Mesh(wl.mesh), p, wl.a, (0.0, 0.0), 0.0, "P" if space == dg.DG_SPACE_P else "PQ", 0.0, 1.0)
+        assert np.array_equal(dof_off, sl.off)
+
+
+def test_slab_offsets_rejects_bad_input(lib):
+    wl = configs.small2d(40, 3, 1, 3)
+    _, row_ptr, col, _ = _check(wl)
+    p = wl.p.astype(np.int32)
+    for bad in (dict(dim=4), dict(space=2), dict(p=np.where(np.arange(p.size) == 3, 0, p)),
+                dict(p=np.where(np.arange(p.size) == 3, 7, p)), dict(col=np.where(np.arange(col.size) == 5, p.size, col))):
+        kw = dict(dim=2, row_ptr=row_ptr, col=col, p=p, space=dg.DG_SPACE_P)
+        kw.update(bad)
+        with pytest.raises(dg.DGError) as ei:
+            dg.dg_slab_offsets(**kw)
+        assert ei.value.code == -1
