@@ -60,6 +60,10 @@ WORKLOADS = {
     "batch2d_256": ("batch2d_256: 256 independent 2D clipped-Voronoi meshes (5 Lloyd steps), cell counts "
                     "log-uniform in 512..16,384, per-mesh p~U{1..5}, a=10^U(-2,2), b=(1,0.5), c=1, one recorded "
                     "pass over the whole batch"),
+    "slab2d_65k_p": ("slab2d_65k_p: one space-time slab (Sec. 2.3) over the adr2d_65k mesh and problem, prisms "
+                     "kappa x (0, 0.01], space P_p (space-time total degree <= p, p~U{1..4}), FP32: the slab "
+                     "matrix and load vector with the previous slab's trace"),
+    "slab2d_65k_pq": ("slab2d_65k_pq: as slab2d_65k_p in the space PQ_p (degree <= p in t and in x)"),
 }
 
 
@@ -87,7 +91,7 @@ WORKLOAD = WORKLOADS["adr2d_65k"]
 def make_workload(name):
     from paper_2007_04881_gb300 import configs
 
-    if name == "adr2d_65k":
+    if name in ("adr2d_65k", "slab2d_65k_p", "slab2d_65k_pq"):
         return configs.adr2d()
     if name == "poisson2d_1k":
         return configs.poisson2d()
@@ -228,6 +232,8 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if args.workload.startswith("slab2d"):
+        return run_reference_slab(args, ws)
     import oracle as O
     from paper_2007_04881_gb300 import configs
 
@@ -279,6 +285,26 @@ def run_reference(args):
         "config": {"workload": WORKLOADS[args.workload], "elements": int(batch_ne or wl.ne), "interfaces": int(om.ni),
                    "boundary_faces": int(om.nbf), "sample_per_step": per_step},
         "cpu_baseline": {"value": value, "unit": "elements/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_reference_slab(args, ws):
+    """Reference arm of the slab workloads: the slab oracle, one bounded
+    sample per step (at most 3 timed steps: each is seconds of plain numpy)."""
+    space_name = "PQ" if args.workload.endswith("_pq") else "P"
+    steps = min(args.steps, 3)
+    slab_cpu_sample(space_name)  # warm-up
+    runs = [slab_cpu_sample(space_name) for _ in range(steps)]
+    value = sum(r["value"] for r in runs) / len(runs)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": ws,
+        "steps": steps, "warmup": 1, "ms_per_step": 1e3 * 40 / value, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS[args.workload], "elements": 65536, "sample_per_step": runs[0]["sample"]},
+        "cpu_baseline": dict(runs[0], value=value),
         "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -634,6 +660,146 @@ def run_ours(args):
     return 0
 
 
+def slab_cpu_sample(space_name: str, n_sites: int = 40):
+    """The slab oracle (oracle/spacetime.py) as it stands on a bounded sample:
+    one slab over a 40-cell mesh of the adr2d recipe (p~U{1..4}, a=10^U(-2,2),
+    b=(1,0.5), c=1, sin-product data).  Its source takes no element, so f is
+    evaluated with the first element's a (the cost is the same)."""
+    import oracle as O
+    from oracle import spacetime as S
+    from paper_2007_04881_gb300 import configs
+
+    wl = configs.small2d(n_sites, 1, 1, 4, b=(1.0, 0.5), c=1.0)
+    om = O.Mesh(wl.mesh)
+    pb = O.make_problem(2, **wl.problem)
+    a0 = float(wl.a[0])
+    sl = S.Slab(om, wl.p.astype(np.int32), wl.a, (1.0, 0.5), 1.0, space_name, 0.0, 0.01)
+    t = time.perf_counter()
+    sl.assemble(lambda tt, x: O.source_f(pb, a0, x), lambda tt, x: O.exact_u(pb, x), lambda e, x: 0.0)
+    dt = time.perf_counter() - t
+    return {"value": om.ne / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
+            "sample": f"one {space_name} slab over a {om.ne}-cell mesh of the same recipe, FP64, plain numpy "
+                      f"(one thread), {dt:.1f} s"}
+
+
+def run_slab(args):
+    """One space-time slab step (dg_assemble_slab) over the adr2d_65k mesh."""
+    wl = make_workload(args.workload)
+    import torch
+
+    from paper_2007_04881_gb300 import build as B
+    from paper_2007_04881_gb300 import dg
+
+    ws, rank, local = dist_setup(True)
+    dev = local if ws > 1 else 0
+    torch.cuda.set_device(dev)
+    B.build()
+    stream = torch.cuda.current_stream()
+    ctx = dg.Context(dev, stream.cuda_stream)
+    mesh = dg.Mesh(ctx, wl.mesh, wl.p, wl.a, dg.Problem(**wl.problem))
+    info = mesh.info
+    space = dg.DG_SPACE_PQ if args.workload.endswith("_pq") else dg.DG_SPACE_P
+    prec = dg.DG_PREC_FP32
+    t0, t1 = 0.0, 0.01
+    nv, nd = mesh.dg_slab_layout(space)
+    vals = torch.empty(nv, dtype=torch.float32, device="cuda")
+    rhs = torch.empty(nd, dtype=torch.float32, device="cuda")
+    u_prev = torch.randn(mesh.ndofs, dtype=torch.float32, device="cuda", generator=torch.Generator("cuda").manual_seed(3))
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    step = lambda: mesh.dg_assemble_slab(prec, space, t0, t1, vals, rhs, u_prev)  # noqa: E731
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    launches_per_step = ctx.launches()
+    ctx.dg_set_timing(True)
+    sampler = ClockSampler(dev)
+    barrier(ws)
+    torch.cuda.synchronize()
+    sampler.start()
+    t_wall = time.perf_counter()
+    times, kstats = time_steps(torch, stream, step, flush, args.steps, ctx)
+    t_wall = time.perf_counter() - t_wall
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    ctx.dg_set_timing(False)
+    ms_step = max_over_ranks(sum(times) / len(times), ws)
+    value = ws * info.ne / (ms_step * 1e-3)
+
+    # end to end: u_prev from pinned host memory, the slab system back to it
+    hu = u_prev.cpu().pin_memory()
+    hv = torch.empty(nv, dtype=torch.float32).pin_memory()
+    hr = torch.empty(nd, dtype=torch.float32).pin_memory()
+    du = torch.empty_like(u_prev)
+
+    def e2e_step():
+        du.copy_(hu, non_blocking=True)
+        mesh.dg_assemble_slab(prec, space, t0, t1, vals, rhs, du)
+        hv.copy_(vals, non_blocking=True)
+        hr.copy_(rhs, non_blocking=True)
+        torch.cuda.synchronize()
+
+    e2e_steps = max(3, min(args.steps, 10))
+    e2e_step()
+    barrier(ws)
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_s = max_over_ranks((time.perf_counter() - t) / e2e_steps, ws)
+    if rank != 0:
+        return 0
+
+    # roofline of the expansion kernel: it writes the slab matrix once and
+    # reads every spatial block and every diagonal block of the mass matrix once
+    row_ptr, col, blk_off, _ = mesh.dg_bsr_pattern()
+    rows = np.repeat(np.arange(info.ne), np.diff(row_ptr))
+    diag_entries = int(np.diff(blk_off)[col == rows].sum())
+    alg_bytes = 4 * (nv + int(info.nvals) + diag_entries)
+    kname = "slab_matrix_f32"
+    kt = kstats.get(kname)
+    avg_ms = kt[0] / kt[1] if kt else float("nan")
+    achieved = alg_bytes / (avg_ms * 1e-3) / 1e9
+    peaks, peak_src = _peaks()
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    kern = {k: {"avg_ms": v[0] / v[1], "launches": v[1]} for k, v in sorted(kstats.items())}
+    cfg = workload_config(wl, info, args.workload)
+    cfg.update({"slab_matrix_entries": int(nv), "slab_dofs": int(nd), "space": "PQ" if space else "P",
+                "slab": [t0, t1]})
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "elements/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": cfg,
+        "matrix_gbs": (nv + nd) * 4 / (ms_step * 1e-3) / 1e9,
+        "roofline": {
+            "bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "traffic": None,
+            "unit_note": f"algorithmic bytes per launch = 4 x (slab entries written {nv} + spatial entries read "
+                         f"{int(info.nvals)} + mass-matrix entries read {diag_entries}); peak hbm_gbs of "
+                         f"MEASURED_PEAKS.json ({peak_src})",
+        },
+        "kernels": kern,
+        "e2e": {"value": ws * info.ne / e2e_s, "unit": "elements/s", "h2d_bytes_per_step": hu.numel() * 4,
+                "d2h_bytes_per_step": (nv + nd) * 4, "ms_per_step": 1e3 * e2e_s},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "timed_wall_s": t_wall,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = slab_cpu_sample("PQ" if space else "P")
+    print(json.dumps(line))
+    return 0
+
+
 def _kernel_source_sha() -> str:
     """Hash of the sources the row-pass kernels are compiled from: the
     dg_row*.cu translation units and every header they include."""
@@ -831,6 +997,8 @@ def main():
         return run_reference(args)
     if args.workload == "learned2d_262k":
         return run_learned(args)
+    if args.workload.startswith("slab2d"):
+        return run_slab(args)
     return run_ours(args)
 
 

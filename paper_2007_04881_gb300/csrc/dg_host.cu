@@ -1429,8 +1429,16 @@ int dg_assemble_slab(dg_ctx* ctx, dg_mesh* mesh, int prec, int space, double t0,
   const SlabPattern sp = slab_pattern(mesh, space);
   const SlabTimes<double> tt = slab_time_data(t0, t1);
   const bool fp32 = prec == DG_PREC_FP32;
+  // per-launch timing records (no algorithmic flop or byte counts: kind kKinds)
+  Tracer* tr = &ctx->tracer;
+  tr->begin(fp32 ? "slab_matrix_f32" : "slab_matrix_f64", kKinds, 0, fp32 ? 4 : 8, ctx->stream);
   n += launch_slab_matrix(sp, tt, fp32, mesh->slab_B, mesh->slab_M, vals, ctx->sm_count, ctx->stream);
-  if (rhs) n += launch_slab_rhs(sp, tt, fp32, mesh->slab_l, mesh->slab_M, u_prev, rhs, ctx->sm_count, ctx->stream);
+  tr->end(ctx->stream);
+  if (rhs) {
+    tr->begin(fp32 ? "slab_rhs_f32" : "slab_rhs_f64", kKinds, 0, fp32 ? 4 : 8, ctx->stream);
+    n += launch_slab_rhs(sp, tt, fp32, mesh->slab_l, mesh->slab_M, u_prev, rhs, ctx->sm_count, ctx->stream);
+    tr->end(ctx->stream);
+  }
   DG_CUDA_TRY(cudaGetLastError());
   ctx->last_launches = n;
   return DG_OK;
