@@ -1,12 +1,13 @@
 """Space-time slab assembly for the parabolic special case (Sec. 2.3): plain
-FP64 numpy on top of the 2D oracle's geometry, rules and basis.  Test
+FP64 numpy on top of the oracle's geometry, rules and basis.  Test
 infrastructure: only the test suite may import it.
 
-The slab I_n x D = (t0, t1] x D over a 2D polygonal mesh is cut into prisms
+The slab I_n x D = (t0, t1] x D over a 2D polygonal or 3D polyhedral mesh
+(the paper's computations use 2D) is cut into prisms
 kappa_n = I_n x kappa.  On each prism the basis is psi_(k, alpha)(t, x) =
 T_k(t) phi_alpha(x), with T_k = sqrt((2k + 1) / tau) P_k(2 (t - t0) / tau - 1)
 orthonormal on I_n (tau = t1 - t0) and phi_alpha the element's orthonormal
-bounding-box Legendre basis of the 2D oracle.  Two spaces (Sec. 2.3): P_p,
+bounding-box Legendre basis of the oracle.  Two spaces (Sec. 2.3): P_p,
 space-time total degree k + |alpha| <= p, and PQ_p, k <= p with |alpha| <= p.
 
 The slab problem is the per-slab system at the end of Sec. 2.3, every
@@ -23,8 +24,9 @@ and Dirichlet faces.  Readings: a is constant per element (A = a I), w and c
 are constants; the penalty of a lateral face I_n x F is the spatial one of F
 (10 p^2 / h with the prism's degree p and the spatial diameter h), since the
 face terms are spatial jumps; time integrals use p + 2 Gauss points, the
-spatial ones the 2D oracle's rules (fan rule with p + 2 points per direction,
-max(p0, p1) + 1 points per face), exact for every integrand here.
+spatial ones the oracle's rules (sub-simplex rule with p + 2 points per
+direction, max(p0, p1) + 1 points per face direction), exact for every
+integrand here.
 """
 from __future__ import annotations
 
@@ -34,16 +36,16 @@ from numpy.polynomial import legendre as npl
 from . import Mesh, basis, gauss01, nbasis
 
 
-def st_index(p: int, space: str):
+def st_index(p: int, space: str, dim: int = 2):
     """(k, j) pairs of a prism of degree p: temporal degree k and index j of the
-    2D basis function (ordered by total degree, so j < nbasis(2, d) exactly when
-    |alpha_j| <= d)."""
+    spatial basis function (ordered by total degree, so j < nbasis(dim, d)
+    exactly when |alpha_j| <= d)."""
     if space not in ("P", "PQ"):
         raise ValueError(space)
     out = []
     for k in range(p + 1):
         d = p - k if space == "P" else p
-        out.extend((k, j) for j in range(nbasis(2, d)))
+        out.extend((k, j) for j in range(nbasis(dim, d)))
     return out
 
 
@@ -61,28 +63,32 @@ def time_basis(p: int, t: float, t0: float, tau: float):
 
 
 class Slab:
-    """The slab (t0, t1] x D over the 2D oracle mesh om, degrees p[e] (>= 1),
-    diffusion a[e], wind w (2-vector), reaction c, space "P" or "PQ"."""
+    """The slab (t0, t1] x D over the oracle mesh om (2D or 3D), degrees p[e]
+    (>= 1), diffusion a[e], wind w (dim-vector), reaction c, space "P" or
+    "PQ"."""
 
     def __init__(self, om: Mesh, p, a, w, c: float, space: str, t0: float, t1: float,
                  c_sigma: float = 10.0):
-        if om.dim != 2:
-            raise ValueError("the slab oracle takes a 2D spatial mesh")
+        if om.dim not in (2, 3):
+            raise ValueError("the slab oracle takes a 2D or 3D spatial mesh")
         self.om, self.space, self.t0, self.t1 = om, space, float(t0), float(t1)
+        self.dim = om.dim
         self.tau = self.t1 - self.t0
         self.p = np.asarray(p, dtype=np.int32)
         self.a = np.asarray(a, dtype=np.float64)
         self.w = np.asarray(w, dtype=np.float64)
+        if self.w.shape != (self.dim,):
+            raise ValueError("the wind has one component per space dimension")
         self.c = float(c)
         self.c_sigma = float(c_sigma)
-        self.idx = [st_index(int(pe), space) for pe in self.p]
+        self.idx = [st_index(int(pe), space, self.dim) for pe in self.p]
         self.off = np.concatenate([[0], np.cumsum([len(ix) for ix in self.idx])]).astype(np.int64)
 
     def _psi(self, e: int, t: float, x):
         """Values, time derivatives and spatial gradients of element e's prism
         basis at (t, x)."""
         pe = int(self.p[e])
-        phi, grad = basis(2, pe, self.om.lo[e], self.om.hi[e], x)
+        phi, grad = basis(self.dim, pe, self.om.lo[e], self.om.hi[e], x)
         T, dT = time_basis(pe, t, self.t0, self.tau)
         K = np.array([k for k, _ in self.idx[e]])
         J = np.array([j for _, j in self.idx[e]])

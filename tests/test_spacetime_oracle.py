@@ -10,7 +10,13 @@
 - dG consistency in space-time: for u in the slab space, constant a, w, c, and
   f = u_t - a Lap u + w . grad u + c u, g = u, u_0 = u(0), the discrete solution
   is u on the first slab and, fed the first slab's trace, on the second.  PQ is
-  checked with a u that has t x terms, which P of the same degree lacks.
+  checked with a u that has t x terms, which P of the same degree lacks.  The
+  same over polyhedra (3D), one slab.
+- PQ factorisation: every PQ slab block is [k = l] B + [r = s] D_kl M, B and M
+  from the 2D and 3D oracles, D in closed form; this pins the interior jump
+  terms, which an exact solution does not see.
+- P is PQ restricted: the P slab system is the PQ one on the P index set.
+- Planted mistakes in a copy of the slab oracle each fail one of these pins.
 """
 import math
 
@@ -167,6 +173,94 @@ def check_factorisation(S, n=12):
         e0, e1 = int(om.if_e0[i]), int(om.if_e1[i])
         check(e0, e1, ob["a01"][pos], False)
         check(e1, e0, ob["a10"][pos], False)
+
+
+def test_p_slab_is_the_pq_slab_restricted():
+    """P_p is a subspace of PQ_p with the same form, rules and penalty, and the
+    spatial basis is ordered by total degree: the P slab matrix and load vector
+    are the PQ ones restricted to the (k, j) with j < nbasis(2, p - k)."""
+    om = O.Mesh(mg.voronoi_square(8, 6))
+    p = mg.draw_degrees(om.ne, 6, 1, 3).astype(np.int32)
+    a = mg.draw_log_uniform(om.ne, 6, -1.0, 0.5)
+    args = (om, p, a, (0.4, 0.8), 0.9)
+    pq = S.Slab(*args, "PQ", 0.2, 0.5)
+    pp = S.Slab(*args, "P", 0.2, 0.5)
+    f = lambda t, x: np.cos(t + x[0]) * x[1]  # noqa: E731
+    g = lambda t, x: t * x[0] - x[1] ** 2  # noqa: E731
+    u0 = lambda e, x: 1.0 + x[0] * x[1]  # noqa: E731
+    Aq, Fq = pq.assemble(f, g, u0)
+    Ap, Fp = pp.assemble(f, g, u0)
+    keep = np.concatenate([pq.off[e] + np.array([pq.idx[e].index(kj) for kj in pp.idx[e]]) for e in range(om.ne)])
+    assert np.abs(Aq[np.ix_(keep, keep)] - Ap).max() <= 1e-12 * np.abs(Ap).max()
+    assert np.abs(Fq[keep] - Fp).max() <= 1e-12 * np.abs(Fp).max()
+
+
+def _mesh3d():
+    from paper_2007_04881_gb300 import configs
+
+    wl = configs.small3d(2, 4, 5, 1, 2)  # 4 polyhedra of 12 tetrahedra, p in 1..2
+    return O.Mesh(wl.mesh), wl.p.astype(np.int32), wl.a
+
+
+def test_slab_3d_factorises_into_time_and_space():
+    """The factorisation pin over polyhedra: every PQ slab block is
+    [k = l] B + [r = s] D_kl M with B, M from the 3D oracle."""
+    om, p, a = _mesh3d()
+    w, c, t0, t1 = (0.6, -0.3, 0.45), 0.5, 0.0, 0.3
+    sl = S.Slab(om, p, a, w, c, "PQ", t0, t1)
+    zero = lambda *args: 0.0  # noqa: E731
+    A, _ = sl.assemble(zero, zero, zero)
+    ob = om.assemble(p, a, O.make_problem(3, b=w, c=c, source=0, c_sigma=10.0), rhs=False)
+    mass = O.make_problem(3, c=1.0, c_sigma=0.0)
+    tau = t1 - t0
+
+    def D(k, l):
+        deriv = 2.0 if (k < l and (k + l) % 2 == 1) else 0.0
+        return math.sqrt((2 * k + 1) * (2 * l + 1)) / tau * (deriv + (-1.0) ** (k + l))
+
+    def check(r, s, B2, M):
+        got = A[sl.off[r]:sl.off[r + 1], sl.off[s]:sl.off[s + 1]]
+        want = np.zeros_like(got)
+        for i, (k, j) in enumerate(sl.idx[r]):
+            for q, (l, m) in enumerate(sl.idx[s]):
+                want[i, q] = (B2[j, m] if k == l else 0.0) + (D(k, l) * M[j, m] if M is not None else 0.0)
+        assert np.abs(got - want).max() <= 1e-11 * np.abs(want).max(), (r, s)
+
+    for pos, e in enumerate(ob["elems"]):
+        e = int(e)
+        check(e, e, ob["diag"][pos], om.volume_block(e, p, np.zeros(om.ne), mass))
+    for pos, i in enumerate(ob["ifaces"]):
+        e0, e1 = int(om.if_e0[i]), int(om.if_e1[i])
+        check(e0, e1, ob["a01"][pos], None)
+        check(e1, e0, ob["a10"][pos], None)
+
+
+@pytest.mark.parametrize("space", ["P", "PQ"])
+def test_slab_3d_reproduces_space_time_polynomials(space):
+    """u = 1 + 0.5 t + x - 0.7 y + 0.4 z (+ 0.3 t x in PQ, outside P_1) with
+    f = u_t + w . grad u + c u and g = u: the slab solution is u."""
+    om, p, _ = _mesh3d()
+    a = np.full(om.ne, 0.8)  # constant: with a jump in a, the flux of u would jump too
+    w, c, t0, t1 = np.array([0.6, -0.3, 0.45]), 0.5, 0.1, 0.35
+    tx = 0.3 if space == "PQ" else 0.0
+
+    def u(t, x):
+        return 1.0 + 0.5 * t + x[0] - 0.7 * x[1] + 0.4 * x[2] + tx * t * x[0]
+
+    def f(t, x):
+        grad = np.array([1.0 + tx * t, -0.7, 0.4])
+        return 0.5 + tx * x[0] + w @ grad + c * u(t, x)
+
+    sl = S.Slab(om, p, a, w, c, space, t0, t1)
+    A, F = sl.assemble(f, u, lambda e, x: u(t0, x))
+    U = np.linalg.solve(A, F)
+    err = 0.0
+    for e in range(om.ne):
+        xq, _ = om.volume_points(e, 2)
+        for x in xq[::11]:
+            for t in (t0, t1):
+                err = max(err, abs(sl.value(U, e, t, x) - u(t, x)))
+    assert err < 1e-9, err
 
 
 # Planted mistakes: each one, made in a copy of the slab oracle, fails a pin.
