@@ -414,6 +414,22 @@ int dg_volume_noalloc(void *stream, int device, int prec, int p, int nv, const d
                       int ne, int nsub, const int *elem_ptr, const int *elem_idx, const double *a, double bx,
                       double by, double c, void *blocks);
 
+/* Variable advection and reaction, the fields of the paper's multi-GPU test
+ * problem (Sec. 4.2): b_d(x) = 1 + x_d and c(x) = 3 + prod_d x_d, evaluated
+ * at every quadrature point, with the inflow part of each face decided
+ * point by point (b . n < 0; b . n = 0 is outflow).  The mesh must be
+ * uploaded with b = 0 and c = 0 (DG_ERR_ARG otherwise): its a, C_sigma and
+ * source (DG_SRC_ZERO, or DG_SRC_SINPROD with f = a d pi^2 u + b(x).grad u
+ * + c(x) u and g_D = u) apply, and the call supplies b(x) and c(x).
+ * vals (device, nvals doubles) and rhs (device, ndofs doubles, may be NULL)
+ * are OVERWRITTEN with the whole FP64 system: the row kernels write every
+ * term without b and c, then one warp per element row adds the b and c
+ * terms of its blocks and load-vector entries (volume points, and the
+ * inflow points of its faces).  2D meshes from dg_mesh_upload or
+ * dg_batch_upload without learned rules; DG_ERR_ARG otherwise.
+ * Asynchronous on the context stream. */
+int dg_assemble_varcoef(dg_ctx *ctx, dg_mesh *mesh, void *vals, void *rhs);
+
 /* Space-time slabs (Sec. 2.3).  The slab (t0, t1] x D over an uploaded mesh
  * is cut into prisms kappa x (t0, t1].  A prism of degree p carries the
  * basis T_k(t) phi_j(x): T_k = sqrt((2k+1)/tau) P_k(2 (t - t0)/tau - 1), the

@@ -21,6 +21,7 @@
 #include "../../include/dg.h"
 #include "dg_internal.h"
 #include "dg_slab.cuh"
+#include "dg_varcoef.cuh"
 
 using namespace dg;
 
@@ -1457,6 +1458,73 @@ int dg_slab_trace(dg_ctx* ctx, const dg_mesh* mesh, int prec, int space, double 
   ctx->last_launches = launch_slab_trace(slab_pattern(m, space), slab_time_data(t0, t1), prec == DG_PREC_FP32, U, u_end,
                                          ctx->sm_count, ctx->stream);
   DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Variable advection and reaction (Sec. 4.2): b_d = 1 + x_d, c = 3 + prod x_d
+// at every point, added by the variable-coefficient kernels (dg_varcoef.cu)
+// to a row pass without b and c.
+// ---------------------------------------------------------------------------
+
+static VcView varcoef_view(const DevMesh& m) {
+  VcView v;
+  v.ne = m.ne;
+  v.nf = m.nf;
+  v.nsub = m.nsub;
+  v.source = m.pb.source;
+  v.p = m.p;
+  v.eptr = m.eptr;
+  v.eg = m.eg64;
+  v.sg = m.sg64;
+  v.fs = m.fs64;
+  v.fsc = m.fsc64;
+  v.f_e0 = m.f_e0;
+  v.f_e1 = m.f_e1;
+  v.f_nq = m.f_nq;
+  v.hf_ptr = m.hf_ptr;
+  v.hf_face = m.hf_face;
+  v.hf_side = m.hf_side;
+  v.if_fptr = m.if_fptr;
+  v.row_ptr = m.row_ptr;
+  v.col = m.col;
+  v.blk_if = m.blk_if;
+  v.blk_off = m.blk_off;
+  v.dof_off = m.dof_off;
+  v.vol_rule = m.rt.vol64;
+  v.face_rule = m.rt.face64;
+  for (int k = 0; k < 8; ++k) {
+    v.vol_off[k] = m.rt.vol_off[k];
+    v.vol_n[k] = m.rt.vol_n[k];
+  }
+  for (int k = 0; k < 10; ++k) {
+    v.face_off[k] = m.rt.face_off[k];
+    v.face_n[k] = m.rt.face_n[k];
+  }
+  return v;
+}
+
+int dg_assemble_varcoef(dg_ctx* ctx, dg_mesh* mesh, void* vals, void* rhs) {
+  if (!ctx || !mesh || !vals) return fail(DG_ERR_ARG, "dg_assemble_varcoef: null argument");
+  const DevMesh& m = mesh->dm;
+  if (m.dim != 2) return fail(DG_ERR_ARG, "dg_assemble_varcoef: 2D meshes only");
+  if (!mesh->part_elem.empty()) return fail(DG_ERR_ARG, "dg_assemble_varcoef: partition meshes are not supported");
+  if (m.pb.b[0] != 0.0 || m.pb.b[1] != 0.0 || m.pb.b[2] != 0.0 || m.pb.c != 0.0)
+    return fail(DG_ERR_ARG, "dg_assemble_varcoef: upload the mesh with b = 0 and c = 0 (the call supplies b(x), c(x))");
+  if (m.pb.source != DG_SRC_ZERO && m.pb.source != DG_SRC_SINPROD)
+    return fail(DG_ERR_ARG, "dg_assemble_varcoef: source %d (DG_SRC_ZERO or DG_SRC_SINPROD)", m.pb.source);
+  if (m.lq_ok) return fail(DG_ERR_ARG, "dg_assemble_varcoef: learned volume rules are installed");
+  // every term without b and c: the row kernels
+  int rc = run_assembly(ctx, mesh, DG_PREC_FP64, kModeVol | kModeFace | (rhs ? kModeRhs : 0), vals, rhs, true);
+  if (rc != DG_OK) return rc;
+  int n = ctx->last_launches;
+  Tracer* tr = &ctx->tracer;
+  tr->begin("varcoef_terms_f64", kKinds, 0, 8, ctx->stream);
+  n += launch_varcoef(varcoef_view(m), m.dim, static_cast<double*>(vals), static_cast<double*>(rhs), ctx->sm_count,
+                      ctx->stream);
+  tr->end(ctx->stream);
+  DG_CUDA_TRY(cudaGetLastError());
+  ctx->last_launches = n;
   return DG_OK;
 }
 

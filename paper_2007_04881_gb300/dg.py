@@ -149,6 +149,7 @@ def load() -> C.CDLL:
     lib.dg_slab_layout.argtypes = [V, C.c_int, V, V]
     lib.dg_assemble_slab.argtypes = [V, V, C.c_int, C.c_int, C.c_double, C.c_double, V, V, V]
     lib.dg_slab_trace.argtypes = [V, V, C.c_int, C.c_int, C.c_double, C.c_double, V, V]
+    lib.dg_assemble_varcoef.argtypes = [V, V, V, V]
     _lib = lib
     return lib
 
@@ -165,7 +166,7 @@ EXPORTS = (
     "dg_mlp_create", "dg_mlp_free", "dg_mlp_num_params", "dg_mlp_get_params", "dg_mlp_set_params",
     "dg_mlp_get_state", "dg_mlp_set_state", "dg_mlp_forward", "dg_mlp_grad", "dg_mlp_train_step",
     "dg_partition", "dg_mesh_upload_part", "dg_part_map", "dg_part_check", "dg_set_volume_path",
-    "dg_slab_offsets", "dg_slab_layout", "dg_assemble_slab", "dg_slab_trace",
+    "dg_slab_offsets", "dg_slab_layout", "dg_assemble_slab", "dg_slab_trace", "dg_assemble_varcoef",
 )
 
 
@@ -454,6 +455,10 @@ class Mesh:
 
     def dg_quad_clear(self):
         _check(load().dg_quad_clear(self.ctx._h, self._h))
+
+    def dg_assemble_varcoef(self, vals, rhs=None):
+        """FP64 system with b(x) = 1 + x, c(x) = 3 + prod x (the mesh uploaded with b = 0, c = 0)."""
+        _check(load().dg_assemble_varcoef(self.ctx._h, self._h, _vp(vals), _vp(rhs)))
 
     def dg_slab_layout(self, space: int):
         """(nvals, ndofs) of the space-time slab system over this mesh."""
