@@ -425,7 +425,7 @@ int dg_volume_noalloc(void *stream, int device, int prec, int p, int nv, const d
  * are OVERWRITTEN with the whole FP64 system: the row kernels write every
  * term without b and c, then one warp per element row adds the b and c
  * terms of its blocks and load-vector entries (volume points, and the
- * inflow points of its faces).  2D meshes from dg_mesh_upload or
+ * inflow points of its faces).  2D and 3D meshes from dg_mesh_upload or
  * dg_batch_upload without learned rules; DG_ERR_ARG otherwise.
  * Asynchronous on the context stream. */
 int dg_assemble_varcoef(dg_ctx *ctx, dg_mesh *mesh, void *vals, void *rhs);

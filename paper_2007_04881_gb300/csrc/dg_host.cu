@@ -1507,7 +1507,6 @@ static VcView varcoef_view(const DevMesh& m) {
 int dg_assemble_varcoef(dg_ctx* ctx, dg_mesh* mesh, void* vals, void* rhs) {
   if (!ctx || !mesh || !vals) return fail(DG_ERR_ARG, "dg_assemble_varcoef: null argument");
   const DevMesh& m = mesh->dm;
-  if (m.dim != 2) return fail(DG_ERR_ARG, "dg_assemble_varcoef: 2D meshes only");
   if (!mesh->part_elem.empty()) return fail(DG_ERR_ARG, "dg_assemble_varcoef: partition meshes are not supported");
   if (m.pb.b[0] != 0.0 || m.pb.b[1] != 0.0 || m.pb.b[2] != 0.0 || m.pb.c != 0.0)
     return fail(DG_ERR_ARG, "dg_assemble_varcoef: upload the mesh with b = 0 and c = 0 (the call supplies b(x), c(x))");

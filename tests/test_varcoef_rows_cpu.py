@@ -1,15 +1,16 @@
-"""The variable-coefficient kernels' arithmetic on the CPU (2D).
+"""The variable-coefficient kernels' arithmetic on the CPU (2D and 3D).
 
-The row bodies that add the b(x) = 1 + x, c(x) = 3 + xy terms (Sec. 4.2;
+The row bodies that add the b_d(x) = 1 + x_d, c(x) = 3 + prod x_d terms (Sec. 4.2;
 paper_2007_04881_gb300/csrc/dg_varcoef.cuh) are host/device functions.  This
 test builds them as host code (tests/varcoef_rows_host.cpp, g++) and runs
 them, lane by lane as a warp would, on geometry records laid out as the row
-kernels' (element boxes, fan sub-triangles in box coordinates, face sides
-with their scaled normals) and on the reference rules.  What they add must
+kernels' (element boxes, fan sub-triangles or the element's tetrahedra in box
+coordinates, face sides with their scaled normals, 3D faces in the vertex
+order of the lower element's tetrahedron) and on the reference rules.  What they add must
 equal the oracle's system with the variable fields minus the oracle's system
 with b = 0, c = 0 (oracle coef 1 minus coef 0): every block and every
-load-vector entry, mixed degrees, the sin source and the zero source, at
-1e-12 of each block's largest entry.
+load-vector entry, mixed degrees, polygons and polyhedra, the sin source and
+the zero source, at 1e-12 of each block's largest entry.
 """
 import ctypes as C
 import os
@@ -40,6 +41,7 @@ def host(tmp_path_factory):
                     os.path.join(ROOT, "tests", "varcoef_rows_host.cpp"), "-o", out], check=True)
     lib = C.CDLL(out)
     lib.host_varcoef_2d.argtypes = [V] * 24
+    lib.host_varcoef_3d.argtypes = [V] * 24
     return lib
 
 
@@ -48,31 +50,138 @@ def _gauss01(n):
     return 0.5 * (x + 1.0), 0.5 * w
 
 
-def _rules():
-    """Volume rules of degree 0..7 ((p + 2)^2 collapsed points (r, s, w)) and
-    face rules of 0..9 points ((t, w)), packed, with their offsets."""
+def _rules(dim):
+    """Volume rules of degree 0..7 ((p + 2)^dim collapsed points) and face
+    rules of 0..9 points per direction (Gauss on an edge, collapsed on a
+    triangle), packed as [point][coordinates, weight], with their offsets."""
     vol, vol_off, vol_n = [], [], []
     for p in range(8):
         g, gw = _gauss01(p + 2)
-        vol_off.append(len(vol) // 3)
+        vol_off.append(len(vol) // (dim + 1))
+        n0 = len(vol)
         for ia in range(p + 2):
             for ib in range(p + 2):
-                a, b = g[ia], g[ib]
-                vol += [a * (1.0 - b), b, gw[ia] * gw[ib] * (1.0 - b)]
-        vol_n.append((p + 2) ** 2)
+                if dim == 2:
+                    a, b = g[ia], g[ib]
+                    vol += [a * (1.0 - b), b, gw[ia] * gw[ib] * (1.0 - b)]
+                    continue
+                for ic in range(p + 2):
+                    a, b, c = g[ia], g[ib], g[ic]
+                    vol += [a * (1.0 - b) * (1.0 - c), b * (1.0 - c), c,
+                            gw[ia] * gw[ib] * gw[ic] * (1.0 - b) * (1.0 - c) ** 2]
+        vol_n.append((len(vol) - n0) // (dim + 1))
     face, face_off, face_n = [], [], []
     for n in range(10):
-        face_off.append(len(face) // 2)
+        face_off.append(len(face) // dim)
+        n0 = len(face)
         if n > 0:
             g, gw = _gauss01(n)
-            for t, w in zip(g, gw):
-                face += [t, w]
-        face_n.append(n)
+            for ia in range(n):
+                if dim == 2:
+                    face += [g[ia], gw[ia]]
+                    continue
+                for ib in range(n):
+                    a, b = g[ia], g[ib]
+                    face += [a * (1.0 - b), b, gw[ia] * gw[ib] * (1.0 - b)]
+        face_n.append((len(face) - n0) // dim)
     offs = np.array(vol_off + vol_n + face_off + face_n, np.int32)
     return np.array(vol), np.array(face), offs
 
 
-def _records(mesh, p, row_ptr, col):
+def _topology(ne, faces, row_ptr, col):
+    """Interfaces (element pairs, faces grouped consecutively), half faces and
+    the interface of every off-diagonal block; faces are (e0, e1, ...)."""
+    pairs = sorted({(f[0], f[1]) for f in faces if f[1] >= 0})
+    iface = {pr: i for i, pr in enumerate(pairs)}
+    order = sorted(range(len(faces)), key=lambda k: (iface.get((faces[k][0], faces[k][1]), len(pairs)), k))
+    faces = [faces[k] for k in order]
+    if_fptr = np.zeros(len(pairs) + 1, np.int32)
+    for f in faces:
+        if f[1] >= 0:
+            if_fptr[iface[(f[0], f[1])] + 1] += 1
+    if_fptr = np.cumsum(if_fptr).astype(np.int32)
+    hf = [[] for _ in range(ne)]
+    for k, f in enumerate(faces):
+        hf[f[0]].append((k, 0))
+        if f[1] >= 0:
+            hf[f[1]].append((k, 1))
+    hf_ptr = np.concatenate([[0], np.cumsum([len(h) for h in hf])]).astype(np.int32)
+    hf_face = np.array([k for h in hf for k, _ in h], np.int32)
+    hf_side = np.array([s for h in hf for _, s in h], np.int8)
+    blk_if = np.full(col.size, -1, np.int32)
+    for r in range(ne):
+        for b in range(row_ptr[r], row_ptr[r + 1]):
+            s = int(col[b])
+            if s != r:
+                blk_if[b] = iface[(min(r, s), max(r, s))]
+    return faces, dict(if_fptr=if_fptr, hf_ptr=hf_ptr, hf_face=hf_face, hf_side=hf_side, blk_if=blk_if)
+
+
+def _records3d(mesh, p, row_ptr, col):
+    """Geometry records and face topology of a 3D mesh in the row kernels'
+    layouts: the element's tetrahedra; faces in the vertex order of the lower
+    element's tetrahedron, the normal out of that element."""
+    ne = mesh.ne
+    X = np.stack([mesh.x, mesh.y, mesh.z])
+    tptr, tv = mesh.elem_tptr, np.asarray(mesh.tet_v).reshape(-1, 4)
+    lo = np.zeros((3, ne))
+    L = np.zeros((3, ne))
+    for e in range(ne):
+        P = X[:, np.unique(tv[tptr[e]:tptr[e + 1]])]
+        lo[:, e] = P.min(axis=1)
+        L[:, e] = P.max(axis=1) - P.min(axis=1)
+    eg = np.concatenate([lo, L, 1.0 / L, (1.0 / np.sqrt(L.prod(axis=0)))[None, :]])
+
+    def xi(x, e):
+        return 2.0 * (x - lo[:, e]) / L[:, e] - 1.0
+
+    nsub = int(tptr[-1])
+    sg = np.zeros((13, nsub))
+    half = {}
+    for e in range(ne):
+        for t in range(tptr[e], tptr[e + 1]):
+            P = X[:, tv[t]]
+            sg[0:3, t] = xi(P[:, 0], e)
+            for i in range(1, 4):
+                sg[3 * i:3 * i + 3, t] = xi(P[:, i], e) - xi(P[:, 0], e)
+            sg[12, t] = abs(np.linalg.det(np.stack([P[:, 1] - P[:, 0], P[:, 2] - P[:, 0], P[:, 3] - P[:, 0]])))
+            for o in range(4):
+                v = [int(tv[t][i]) for i in range(4) if i != o]
+                cr = np.cross(X[:, v[1]] - X[:, v[0]], X[:, v[2]] - X[:, v[0]])
+                flip = float(cr @ (X[:, tv[t][o]] - X[:, v[0]])) > 0.0
+                half.setdefault(tuple(sorted(v)), []).append((e, v, flip))
+    faces = []
+    for key in sorted(half):
+        hs = sorted(half[key], key=lambda h: h[0])
+        if len(hs) == 2 and hs[0][0] == hs[1][0]:
+            continue  # between two tetrahedra of one element
+        e0, v, flip = hs[0]
+        faces.append((e0, hs[1][0] if len(hs) == 2 else -1, v, flip))
+    faces, topo = _topology(ne, faces, row_ptr, col)
+    nf = len(faces)
+    fs = np.zeros((2, 12, nf))
+    fsc = np.zeros((3, nf))
+    for k, (e0, e1, v, flip) in enumerate(faces):
+        P0, P1, P2 = X[:, v[0]], X[:, v[1]], X[:, v[2]]
+        cr = np.cross(P1 - P0, P2 - P0)
+        ln = np.linalg.norm(cr)
+        n0 = (-1.0 if flip else 1.0) * cr / ln
+        fsc[0, k] = ln  # 2 |F|, for the collapsed rule's weights summing to 1/2
+        for s, e in enumerate((e0, e1)):
+            if e < 0:
+                continue
+            fs[s, 0:3, k] = xi(P0, e)
+            fs[s, 3:6, k] = xi(P1, e) - xi(P0, e)
+            fs[s, 6:9, k] = xi(P2, e) - xi(P0, e)
+            fs[s, 9:12, k] = 2.0 * n0 / L[:, e]
+    f_e0 = np.array([f[0] for f in faces], np.int32)
+    f_e1 = np.array([f[1] for f in faces], np.int32)
+    f_nq = np.array([max(p[f[0]], p[f[1]] if f[1] >= 0 else 0) + 1 for f in faces], np.int32)
+    return dict(eg=np.ascontiguousarray(eg), sg=sg, fs=fs, fsc=fsc, f_e0=f_e0, f_e1=f_e1, f_nq=f_nq, nf=nf,
+                nsub=nsub, eptr=np.ascontiguousarray(tptr, np.int32), **topo)
+
+
+def _records2d(mesh, p, row_ptr, col):
     """Geometry records and face topology of a 2D mesh in the row kernels'
     layouts (fan apex = area centroid, faces along the first element's CCW
     loop with the normal out of it)."""
@@ -170,30 +279,44 @@ def _vp(a):
     return a.ctypes.data
 
 
+CASES = {"2d_small": (2, 12, 3, 0), "2d": (2, 30, 8, 0), "3d_small": (3, 2, 5, 4), "3d": (3, 3, 7, 9)}
+
+
 @pytest.mark.parametrize("source", [0, 1])
-@pytest.mark.parametrize("n,seed", [(12, 3), (30, 8)])
-def test_varcoef_rows_against_oracle(host, source, n, seed):
-    mesh = mg.voronoi_square(n, seed)
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_varcoef_rows_against_oracle(host, source, case):
+    dim, n, seed, clusters = CASES[case]
+    if dim == 2:
+        mesh = mg.voronoi_square(n, seed)
+        p = mg.draw_degrees(mesh.ne, seed, 1, 4).astype(np.int32)
+        a = mg.draw_log_uniform(mesh.ne, seed, -1.0, 1.0)
+    else:
+        from paper_2007_04881_gb300 import configs
+
+        wl = configs.small3d(n, clusters, seed, 1, 3)  # n^3 cubes of 6 tetrahedra in clusters polyhedra, p 1..3
+        mesh, p, a = wl.mesh, wl.p.astype(np.int32), wl.a
     om = O.Mesh(mesh)
-    p = mg.draw_degrees(om.ne, seed, 1, 4).astype(np.int32)
-    a = mg.draw_log_uniform(om.ne, seed, -1.0, 1.0)
     info, row_ptr, col, blk_off = dg.dg_mesh_check(mesh, p, a, dg.Problem(source=source), pattern=True)
-    nb = np.array([O.nbasis(2, int(q)) for q in p])
+    nb = np.array([O.nbasis(dim, int(q)) for q in p])
     dof_off = np.concatenate([[0], np.cumsum(nb)]).astype(np.int64)
-    R = _records(mesh, p, row_ptr, col)
-    vol, face, offs = _rules()
+    if dim == 2:
+        R = _records2d(mesh, p, row_ptr, col)
+        R["eptr"] = np.ascontiguousarray(mesh.elem_vptr, np.int32)
+    else:
+        R = _records3d(mesh, p, row_ptr, col)
+    vol, face, offs = _rules(dim)
     vals = np.zeros(int(info.nvals))
     rhs = np.zeros(int(info.ndofs))
     ints = np.array([om.ne, R["nf"], R["nsub"], source], np.int32)
-    eptr = np.ascontiguousarray(mesh.elem_vptr, np.int32)
-    host.host_varcoef_2d(_vp(ints), _vp(p), _vp(eptr), _vp(R["eg"]), _vp(R["sg"]), _vp(R["fs"]), _vp(R["fsc"]),
-                         _vp(R["f_e0"]), _vp(R["f_e1"]), _vp(R["f_nq"]), _vp(R["hf_ptr"]), _vp(R["hf_face"]),
-                         _vp(R["hf_side"]), _vp(R["if_fptr"]), _vp(row_ptr), _vp(col), _vp(R["blk_if"]),
-                         _vp(blk_off), _vp(dof_off), _vp(vol), _vp(face), _vp(offs), _vp(vals), _vp(rhs))
+    fn = host.host_varcoef_2d if dim == 2 else host.host_varcoef_3d
+    fn(_vp(ints), _vp(p), _vp(R["eptr"]), _vp(R["eg"]), _vp(R["sg"]), _vp(R["fs"]), _vp(R["fsc"]),
+       _vp(R["f_e0"]), _vp(R["f_e1"]), _vp(R["f_nq"]), _vp(R["hf_ptr"]), _vp(R["hf_face"]), _vp(R["hf_side"]),
+       _vp(R["if_fptr"]), _vp(row_ptr), _vp(col), _vp(R["blk_if"]), _vp(blk_off), _vp(dof_off), _vp(vol),
+       _vp(face), _vp(offs), _vp(vals), _vp(rhs))
     assert np.isfinite(vals).all() and np.isfinite(rhs).all()
 
-    o1 = om.assemble(p, a, O.make_problem(2, source=source, coef=1, c_sigma=10.0))
-    o0 = om.assemble(p, a, O.make_problem(2, b=(0.0, 0.0), c=0.0, source=source, c_sigma=10.0))
+    o1 = om.assemble(p, a, O.make_problem(dim, source=source, coef=1, c_sigma=10.0))
+    o0 = om.assemble(p, a, O.make_problem(dim, source=source, c_sigma=10.0))
 
     def block(r, s):
         b = int(row_ptr[r] + np.nonzero(col[row_ptr[r]:row_ptr[r + 1]] == s)[0][0])

@@ -7,15 +7,13 @@
 
 using namespace dg;
 
-extern "C" {
-// ints: ne, nf, nsub, source; arrays as VcView; offs: vol_off[8], vol_n[8],
-// face_off[10], face_n[10]
-void host_varcoef_2d(const int* ints, const int* p, const int* eptr, const double* eg, const double* sg,
-                     const double* fs, const double* fsc, const int* f_e0, const int* f_e1, const int* f_nq,
-                     const int* hf_ptr, const int* hf_face, const int8_t* hf_side, const int* if_fptr,
-                     const int* row_ptr, const int* col, const int* blk_if, const int64_t* blk_off,
-                     const int64_t* dof_off, const double* vol_rule, const double* face_rule, const int* offs,
-                     double* vals, double* rhs) {
+namespace {
+template <int D>
+void run(const int* ints, const int* p, const int* eptr, const double* eg, const double* sg, const double* fs,
+         const double* fsc, const int* f_e0, const int* f_e1, const int* f_nq, const int* hf_ptr, const int* hf_face,
+         const int8_t* hf_side, const int* if_fptr, const int* row_ptr, const int* col, const int* blk_if,
+         const int64_t* blk_off, const int64_t* dof_off, const double* vol_rule, const double* face_rule,
+         const int* offs, double* vals, double* rhs) {
   VcView v;
   v.ne = ints[0];
   v.nf = ints[1];
@@ -51,8 +49,25 @@ void host_varcoef_2d(const int* ints, const int* p, const int* eptr, const doubl
   }
   for (int r = 0; r < v.ne; ++r)
     for (int lane = 0; lane < 32; ++lane) {
-      vc_matrix_row<2>(v, vals, r, lane, 32);
-      vc_rhs_row<2>(v, rhs, r, lane, 32);
+      vc_matrix_row<D>(v, vals, r, lane, 32);
+      vc_rhs_row<D>(v, rhs, r, lane, 32);
     }
 }
+}  // namespace
+
+// ints: ne, nf, nsub, source; arrays as VcView; offs: vol_off[8], vol_n[8],
+// face_off[10], face_n[10]
+#define VC_ARGS                                                                                                    \
+  const int *ints, const int *p, const int *eptr, const double *eg, const double *sg, const double *fs,           \
+      const double *fsc, const int *f_e0, const int *f_e1, const int *f_nq, const int *hf_ptr, const int *hf_face, \
+      const int8_t *hf_side, const int *if_fptr, const int *row_ptr, const int *col, const int *blk_if,           \
+      const int64_t *blk_off, const int64_t *dof_off, const double *vol_rule, const double *face_rule,            \
+      const int *offs, double *vals, double *rhs
+#define VC_PASS                                                                                                \
+  ints, p, eptr, eg, sg, fs, fsc, f_e0, f_e1, f_nq, hf_ptr, hf_face, hf_side, if_fptr, row_ptr, col, blk_if, \
+      blk_off, dof_off, vol_rule, face_rule, offs, vals, rhs
+
+extern "C" {
+void host_varcoef_2d(VC_ARGS) { run<2>(VC_PASS); }
+void host_varcoef_3d(VC_ARGS) { run<3>(VC_PASS); }
 }
