@@ -6,7 +6,8 @@
  * Galerkin methods on polytopic meshes" (arXiv 2007.04881).
  *
  * Problem (Sec. 2.1, Eq. (2.1)):  -div(a grad u) + b . grad u + c u = f,
- * with a > 0 piecewise constant per element (A = a I), b and c constant, and
+ * with a > 0 piecewise constant per element (A = a I), b and c constant (or,
+ * through dg_assemble_varcoef, the variable fields of Sec. 4.2), and
  * u = g_D on the whole boundary (a > 0 makes every boundary point part of
  * the Dirichlet boundary, Sec. 2.1).
  * Discretisation (Sec. 2.2): B(u_h, v) = l(v) with the bilinear form of
