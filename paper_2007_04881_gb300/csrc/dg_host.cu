@@ -429,6 +429,38 @@ struct FaceRec {
   bool flip;
 };
 
+// Stable LSD radix sort of (key, idx) pairs by key: 11-bit digits (2048
+// buckets, whose write positions stay in cache), as many passes as the
+// largest key has digits.
+void radix_sort_u64(std::vector<uint64_t>& key, std::vector<uint32_t>& idx) {
+  const size_t n = key.size();
+  if (n < 2) return;
+  uint64_t kmax = 0;
+  for (size_t i = 0; i < n; ++i) kmax = std::max(kmax, key[i]);
+  std::vector<uint64_t> k2(n);
+  std::vector<uint32_t> i2(n);
+  constexpr int kBits = 11;
+  constexpr uint64_t kMask = (1u << kBits) - 1;
+  std::vector<size_t> cnt(kMask + 1);
+  for (int shift = 0; shift < 64 && (kmax >> shift) != 0; shift += kBits) {
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (size_t i = 0; i < n; ++i) ++cnt[(key[i] >> shift) & kMask];
+    size_t sum = 0;
+    for (size_t& c : cnt) {
+      const size_t t = c;
+      c = sum;
+      sum += t;
+    }
+    for (size_t i = 0; i < n; ++i) {
+      const size_t at = cnt[(key[i] >> shift) & kMask]++;
+      k2[at] = key[i];
+      i2[at] = idx[i];
+    }
+    key.swap(k2);
+    idx.swap(i2);
+  }
+}
+
 }  // namespace
 
 struct Plan {
@@ -602,41 +634,65 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P, const int8_t* owned = nullp
         }
       }
   }
-  std::sort(H.begin(), H.end(), key_less);
+  // Order the half faces by (key, element).  They were generated element by
+  // element, so a stable sort by the key alone gives that order: a radix sort
+  // of the sorted vertex ids as one number in base nv (below 2^64 for
+  // nv < 2^21), else a comparison sort.
+  std::vector<uint32_t> ord(H.size());
+  std::iota(ord.begin(), ord.end(), 0u);
+  if (dim == 2 || nv < (1 << 21)) {
+    std::vector<uint64_t> hk(H.size());
+    const uint64_t base = (uint64_t)nv;
+    for (size_t i = 0; i < H.size(); ++i)
+      hk[i] = dim == 2 ? (uint64_t)H[i].key[0] * base + (uint64_t)H[i].key[1]
+                       : ((uint64_t)H[i].key[0] * base + (uint64_t)H[i].key[1]) * base + (uint64_t)H[i].key[2];
+    radix_sort_u64(hk, ord);
+  } else {
+    std::stable_sort(ord.begin(), ord.end(), [&](uint32_t a, uint32_t b) { return key_less(H[a], H[b]); });
+  }
   std::vector<FaceRec>& F = P.F;
-  F.reserve(H.size());
+  F.reserve(H.size() / 2 + 1);
   for (size_t i = 0; i < H.size();) {
+    const HalfFace& h0 = H[ord[i]];
     size_t j = i + 1;
-    while (j < H.size() && key_eq(H[i], H[j])) ++j;
+    while (j < H.size() && key_eq(h0, H[ord[j]])) ++j;
     const size_t cnt = j - i;
     if (cnt > 2) return fail(DG_ERR_MESH, "a face is shared by %zu element pieces (non-manifold)", cnt);
-    if (cnt == 2 && H[i].elem == H[i + 1].elem) {
-      if (dim == 2) return fail(DG_ERR_MESH, "element %d traverses an edge twice", H[i].elem);
+    const HalfFace* h1 = cnt == 2 ? &H[ord[i + 1]] : nullptr;
+    if (h1 && h0.elem == h1->elem) {
+      if (dim == 2) return fail(DG_ERR_MESH, "element %d traverses an edge twice", h0.elem);
       // interior to one 3D element: not a face
     } else {
       FaceRec f{};
-      f.e0 = H[i].elem;
-      f.e1 = cnt == 2 ? H[i + 1].elem : -1;
+      f.e0 = h0.elem;
+      f.e1 = h1 ? h1->elem : -1;
       for (int q = 0; q < 3; ++q) {
-        f.v[q] = H[i].v[q];
-        f.key[q] = H[i].key[q];
+        f.v[q] = h0.v[q];
+        f.key[q] = h0.key[q];
       }
-      f.flip = H[i].flip;
-      if (dim == 2 && cnt == 2 && !(H[i].v[0] == H[i + 1].v[1] && H[i].v[1] == H[i + 1].v[0]))
+      f.flip = h0.flip;
+      if (dim == 2 && h1 && !(h0.v[0] == h1->v[1] && h0.v[1] == h1->v[0]))
         return fail(DG_ERR_MESH, "elements %d and %d traverse their common edge in the same direction", f.e0, f.e1);
       F.push_back(f);
     }
     i = j;
   }
-  std::stable_sort(F.begin(), F.end(), [](const FaceRec& a, const FaceRec& b) {
-    const bool ab = a.e1 < 0, bb = b.e1 < 0;
-    if (ab != bb) return !ab;
-    if (a.e0 != b.e0) return a.e0 < b.e0;
-    if (a.e1 != b.e1) return a.e1 < b.e1;
-    for (int q = 0; q < 3; ++q)
-      if (a.key[q] != b.key[q]) return a.key[q] < b.key[q];
-    return false;
-  });
+  std::vector<uint32_t>().swap(ord);
+  // Face order: interior faces first, then by (e0, e1, key).  F is in key
+  // order, so a stable sort by (boundary, e0, e1) gives it.
+  {
+    std::vector<uint64_t> fk(F.size());
+    std::vector<uint32_t> fo(F.size());
+    const uint64_t base = (uint64_t)ne + 1;  // e0 < ne, e1 + 1 <= ne
+    for (size_t i = 0; i < F.size(); ++i) {
+      fk[i] = ((uint64_t)(F[i].e1 < 0) * base + (uint64_t)F[i].e0) * base + (uint64_t)(F[i].e1 + 1);
+      fo[i] = (uint32_t)i;
+    }
+    radix_sort_u64(fk, fo);
+    std::vector<FaceRec> Fs(F.size());
+    for (size_t i = 0; i < F.size(); ++i) Fs[i] = F[fo[i]];
+    F.swap(Fs);
+  }
   const int nf = (int)F.size();
   int nint = 0;
   while (nint < nf && F[nint].e1 >= 0) ++nint;
@@ -657,32 +713,35 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P, const int8_t* owned = nullp
   // --- block-sparse pattern
   std::vector<int> nb(ne);
   for (int e = 0; e < ne; ++e) nb[e] = nbasis(dim, d->p[e]);
-  std::vector<std::vector<int>> nbr(ne);
-  for (int i = 0; i < ni; ++i) {
-    nbr[if_e0[i]].push_back(if_e1[i]);
-    nbr[if_e1[i]].push_back(if_e0[i]);
-  }
+  // rows: the element and every element it shares an interface with,
+  // ascending; a halo element (not owned) has no block row
   Plan* m = &P;
-  m->row_ptr.assign(ne + 1, 0);
   std::vector<int>& diag_blk = P.diag_blk;
-  diag_blk.assign(ne, 0);
+  diag_blk.assign(ne, -1);
   auto own = [&](int e) { return owned == nullptr || owned[e] != 0; };
-  for (int e = 0; e < ne; ++e) {
-    if (own(e)) {
-      nbr[e].push_back(e);
-      std::sort(nbr[e].begin(), nbr[e].end());
-    } else {
-      nbr[e].clear();  // halo element: no block row
-      diag_blk[e] = -1;
+  {
+    std::vector<int> deg(ne, 0);
+    for (int i = 0; i < ni; ++i) {
+      ++deg[if_e0[i]];
+      ++deg[if_e1[i]];
     }
-    m->row_ptr[e + 1] = m->row_ptr[e] + (int)nbr[e].size();
+    m->row_ptr.assign(ne + 1, 0);
+    for (int e = 0; e < ne; ++e) m->row_ptr[e + 1] = m->row_ptr[e] + (own(e) ? deg[e] + 1 : 0);
+    m->col.resize(m->row_ptr[ne]);
+    std::vector<int> fill(ne, 0);
+    for (int e = 0; e < ne; ++e)
+      if (own(e)) m->col[m->row_ptr[e] + fill[e]++] = e;
+    for (int i = 0; i < ni; ++i) {
+      const int a = if_e0[i], b = if_e1[i];
+      if (own(a)) m->col[m->row_ptr[a] + fill[a]++] = b;
+      if (own(b)) m->col[m->row_ptr[b] + fill[b]++] = a;
+    }
+    for (int e = 0; e < ne; ++e) std::sort(m->col.begin() + m->row_ptr[e], m->col.begin() + m->row_ptr[e + 1]);
   }
-  m->col.resize(m->row_ptr[ne]);
   m->blk_off.assign(m->row_ptr[ne] + 1, 0);
   for (int e = 0; e < ne; ++e)
-    for (size_t k = 0; k < nbr[e].size(); ++k) {
-      const int idx = m->row_ptr[e] + (int)k, c = nbr[e][k];
-      m->col[idx] = c;
+    for (int idx = m->row_ptr[e]; idx < m->row_ptr[e + 1]; ++idx) {
+      const int c = m->col[idx];
       m->blk_off[idx + 1] = m->blk_off[idx] + (int64_t)nb[e] * nb[c];
       if (c == e) diag_blk[e] = idx;
     }
@@ -753,11 +812,20 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P, const int8_t* owned = nullp
     uvptr.assign(d->elem_ptr, d->elem_ptr + ne + 1);
     uvidx.assign(d->elem_idx, d->elem_idx + d->elem_ptr[ne]);
   } else {
-    std::vector<int> tmp;
+    // each element's distinct vertex ids, ascending: a stamp per vertex marks
+    // the ones already taken, then the short list is sorted
+    std::vector<int> tmp, stamp(nv, -1);
+    uvidx.reserve((size_t)d->elem_ptr[ne]);
     for (int e = 0; e < ne; ++e) {
-      tmp.assign(d->elem_idx + 4 * d->elem_ptr[e], d->elem_idx + 4 * d->elem_ptr[e + 1]);
+      tmp.clear();
+      for (int i = 4 * d->elem_ptr[e]; i < 4 * d->elem_ptr[e + 1]; ++i) {
+        const int v = d->elem_idx[i];
+        if (stamp[v] != e) {
+          stamp[v] = e;
+          tmp.push_back(v);
+        }
+      }
       std::sort(tmp.begin(), tmp.end());
-      tmp.erase(std::unique(tmp.begin(), tmp.end()), tmp.end());
       uvidx.insert(uvidx.end(), tmp.begin(), tmp.end());
       uvptr[e + 1] = (int)uvidx.size();
     }
