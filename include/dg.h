@@ -71,6 +71,13 @@ extern "C" {
  * lo*hi.  Degree-1 elements use the FP32 form.  vals and rhs are float. */
 #define DG_PREC_BF16X3 2 /* hi, lo in bfloat16 */
 #define DG_PREC_TF32X3 3 /* hi, lo in TF32 */
+/* Flag OR-ed into the precision of the entry points that recompute the
+ * geometry each pass (dg_assemble_step, dg_assemble_host, dg_graph_create)
+ * for the FP32 and tensor-core forms: the pass runs the FP64 geometry
+ * kernels (maps, Jacobians, normals, penalties in FP64, stored in FP64 and
+ * rounded to FP32 for the contraction) instead of the reduced-precision
+ * ones on float-pair coordinates.  No effect on DG_PREC_FP64. */
+#define DG_GEOM_FP64 16
 
 /* source / boundary data */
 #define DG_SRC_ZERO 0    /* f = 0, g_D = 0 */
@@ -399,21 +406,27 @@ int dg_kernel_stats(dg_ctx *ctx, dg_kernel_stat *out, int cap);
  *   x, y [nv] vertex coordinates; elem_ptr [ne+1], elem_idx [nsub] CCW vertex
  *   loops (nsub = elem_ptr[ne], the number of fan triangles); a [ne];
  *   blocks [ne * n * n] output, element-major, each n x n block row-major,
- *   n = (p+1)(p+2)/2, double for DG_PREC_FP64, float for DG_PREC_FP32.
+ *   n = (p+1)(p+2)/2, double for DG_PREC_FP64, float for DG_PREC_FP32;
+ *   status (one int, may be NULL): set to DG_OK, or to DG_ERR_MESH when
+ *   elem_ptr is not a list from 0 to nsub with at least 3 vertices per loop
+ *   or a vertex id lies outside 0..nv-1.  The lists are checked on the GPU,
+ *   and a bad list is replaced by a stand-in of the same sizes, so no access
+ *   leaves the caller's buffers; the blocks of such a call are meaningless.
  * It computes, for every element of uniform degree p, the volume part of
  * Eq. (2.4) with advection (bx, by) and reaction c, exactly as
  * dg_assemble_volume does for the element's diagonal block.  Intermediate
  * records live in one file-scope device array of 16 MiB that every GPU
  * loading the library keeps until exit; ne <= 16384 and nsub <= 131072, and
- * larger meshes are rejected with DG_ERR_ARG before any GPU work.  The first
+ * larger meshes are rejected with DG_ERR_ARG before any CUDA call.  The first
  * call on a device looks up the array's device address and writes the
  * reference rules into it (synchronous copies): make that first call before
  * any stream capture.  Calls that overlap on the GPU share the array and
  * race; serialise them (one stream, or events).  Asynchronous on stream
- * (a cudaStream_t, NULL = legacy default stream) on device `device`. */
+ * (a cudaStream_t, NULL = legacy default stream) on device `device`; the
+ * calling thread's current device is restored before the call returns. */
 int dg_volume_noalloc(void *stream, int device, int prec, int p, int nv, const double *x, const double *y,
                       int ne, int nsub, const int *elem_ptr, const int *elem_idx, const double *a, double bx,
-                      double by, double c, void *blocks);
+                      double by, double c, void *blocks, int *status);
 
 /* Variable advection and reaction, the fields of the paper's multi-GPU test
  * problem (Sec. 4.2): b_d(x) = 1 + x_d and c(x) = 3 + prod_d x_d, evaluated

@@ -28,12 +28,15 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile dg_oracle.c into oracle/_build/liboracle.so (gcc, OpenMP)."""
+    """Compile dg_oracle.c into oracle/_build/liboracle.so (gcc -O3, OpenMP).
+
+    -std=c11 (ISO C) keeps floating-point contraction off, so the results are
+    the same on every host; no -march flag, for the same reason."""
     os.makedirs(os.path.dirname(_OUT), exist_ok=True)
     if not force and os.path.exists(_OUT) and os.path.getmtime(_OUT) >= os.path.getmtime(_SRC):
         return _OUT
     tmp = _OUT + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"]
+    cmd = ["gcc", "-O3", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-o", tmp, _SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _OUT)
     return _OUT

@@ -202,6 +202,18 @@ struct dg_ctx {
 // the context's volume path: 0 per-point, 1 quadrature moments, 2 exact 2D moments
 static int ctx_vol_path(const dg_ctx* ctx) { return !ctx->vol_moments ? 0 : ctx->vol_exact ? 2 : 1; }
 
+// The per-pass geometry of a precision argument that may carry DG_GEOM_FP64:
+// the launch_geometry mask (1: FP64 records; 2: the reduced-precision
+// kernels, FP32 records; 3: the FP64 kernels writing the FP64 records and
+// their FP32 roundings).  Strips the flag from *prec; -1 for an unknown value.
+static int pass_geometry(int* prec) {
+  const int flags = *prec & ~0xF, base = *prec & 0xF;
+  if ((flags & ~DG_GEOM_FP64) || base < DG_PREC_FP64 || base > DG_PREC_TF32X3) return -1;
+  *prec = base;
+  if (base == DG_PREC_FP64) return 1;
+  return (flags & DG_GEOM_FP64) ? 3 : 2;
+}
+
 struct dg_graph {
   cudaStream_t stream = nullptr;  // capture stream
   SideStreams streams;            // forked streams of the captured pass
@@ -1319,7 +1331,8 @@ static void step_shape(const dg_ctx* ctx, const dg_mesh* mesh, int prec, int* oc
 int dg_assemble_host(dg_ctx* ctx, dg_mesh* mesh, int prec, const double* x, const double* y, const double* z,
                      const double* a, void* vals_host, void* rhs_host) {
   if (!ctx || !mesh || !vals_host) return fail(DG_ERR_ARG, "dg_assemble_host: null argument");
-  if (prec < DG_PREC_FP64 || prec > DG_PREC_TF32X3) return fail(DG_ERR_ARG, "unknown precision %d", prec);
+  const int gmask = pass_geometry(&prec);
+  if (gmask < 0) return fail(DG_ERR_ARG, "unknown precision %d", prec);
   const size_t es = prec == DG_PREC_FP64 ? 8 : 4;
   if (mesh->h_prec != prec) {
     if (mesh->h_vals) cudaFree(mesh->h_vals);
@@ -1336,7 +1349,7 @@ int dg_assemble_host(dg_ctx* ctx, dg_mesh* mesh, int prec, const double* x, cons
   if (a) DG_CUDA_TRY(cudaMemcpyAsync(mesh->a, a, sizeof(double) * ne, cudaMemcpyHostToDevice, ctx->stream));
   // geometry records only in the precision this pass consumes
   trace_reset(ctx, mesh);
-  ctx->last_launches = launch_geometry(mesh->dm, ctx->stream, &ctx->tracer, prec == DG_PREC_FP64 ? 1 : 2);
+  ctx->last_launches = launch_geometry(mesh->dm, ctx->stream, &ctx->tracer, gmask);
   DG_CUDA_TRY(cudaGetLastError());
   int occ = 0, path = -1;
   bool conc = false;
@@ -1355,10 +1368,11 @@ int dg_assemble_host(dg_ctx* ctx, dg_mesh* mesh, int prec, const double* x, cons
 
 int dg_assemble_step(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs) {
   if (!ctx || !mesh) return fail(DG_ERR_ARG, "dg_assemble_step: null argument");
-  if (prec < DG_PREC_FP64 || prec > DG_PREC_TF32X3) return fail(DG_ERR_ARG, "unknown precision %d", prec);
+  const int gmask = pass_geometry(&prec);
+  if (gmask < 0) return fail(DG_ERR_ARG, "unknown precision %d", prec);
   // geometry records only in the precision this pass consumes
   trace_reset(ctx, mesh);
-  ctx->last_launches = launch_geometry(mesh->dm, ctx->stream, &ctx->tracer, prec == DG_PREC_FP64 ? 1 : 2);
+  ctx->last_launches = launch_geometry(mesh->dm, ctx->stream, &ctx->tracer, gmask);
   DG_CUDA_TRY(cudaGetLastError());
   int occ = 0, path = -1;
   bool conc = false;
@@ -1924,9 +1938,9 @@ int dg_batch_offsets(const dg_mesh* mesh, int* nmesh, int* elem_off, int64_t* va
 }
 
 // One whole pass (geometry + row kernels) on stream st with a launch shape.
-static int issue_pass(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs, cudaStream_t st, int occ_cap,
-                      bool concurrent, int vpath, SideStreams* ss) {
-  int n = launch_geometry(mesh->dm, st, nullptr, prec == DG_PREC_FP64 ? 1 : 2);
+static int issue_pass(dg_ctx* ctx, dg_mesh* mesh, int prec, int gmask, void* vals, void* rhs, cudaStream_t st,
+                      int occ_cap, bool concurrent, int vpath, SideStreams* ss) {
+  int n = launch_geometry(mesh->dm, st, nullptr, gmask);
   DG_CUDA_TRY(cudaGetLastError());
   const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
   int rc = run_assembly(ctx, mesh, prec, mode, vals, rhs, true, true, st, false, occ_cap, concurrent, vpath, ss);
@@ -1937,7 +1951,8 @@ static int issue_pass(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rh
 
 int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs, int autotune, dg_graph** out) {
   if (!ctx || !mesh || !vals || !out) return fail(DG_ERR_ARG, "dg_graph_create: null argument");
-  if (prec < DG_PREC_FP64 || prec > DG_PREC_TF32X3) return fail(DG_ERR_ARG, "unknown precision %d", prec);
+  const int gmask = pass_geometry(&prec);
+  if (gmask < 0) return fail(DG_ERR_ARG, "unknown precision %d", prec);
   *out = nullptr;
   dg_graph* g = new (std::nothrow) dg_graph();
   if (!g) return fail(DG_ERR_OOM, "out of host memory");
@@ -1969,7 +1984,7 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
         float t = 1e30f;
         for (int rep = 0; rep < 4; ++rep) {
           cudaEventRecord(e0, g->stream);
-          int rc = issue_pass(ctx, mesh, prec, vals, rhs, g->stream, occs[oi], conc != 0, vpath, &g->streams);
+          int rc = issue_pass(ctx, mesh, prec, gmask, vals, rhs, g->stream, occs[oi], conc != 0, vpath, &g->streams);
           if (rc != DG_OK) {
             ctx->tracer.on = was_on;
             cudaEventDestroy(e0);
@@ -2013,7 +2028,7 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
     return bail(fail(DG_ERR_CUDA, "dg_graph_create: begin capture failed"));
   int rc = DG_OK;
   {
-    const int gl = launch_geometry(mesh->dm, g->stream, &ctx->tracer, prec == DG_PREC_FP64 ? 1 : 2);
+    const int gl = launch_geometry(mesh->dm, g->stream, &ctx->tracer, gmask);
     const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
     rc = run_assembly(ctx, mesh, prec, mode, vals, rhs, true, false, g->stream, false, g->occ_cap, g->concurrent != 0,
                       g->vol_path, &g->streams);

@@ -26,10 +26,12 @@ DG_ERR = {
     -5: "DG_ERR_ORDER",
     -6: "DG_ERR_TIMEOUT",
 }
+DG_ERR_ARG, DG_ERR_MESH, DG_ERR_CUDA, DG_ERR_OOM, DG_ERR_ORDER, DG_ERR_TIMEOUT = -1, -2, -3, -4, -5, -6
 DG_PREC_FP64 = 0
 DG_PREC_FP32 = 1
 DG_PREC_BF16X3 = 2
 DG_PREC_TF32X3 = 3
+DG_GEOM_FP64 = 16  # OR-ed into prec: the pass's geometry in FP64 (the FP32 records its rounding)
 DG_SRC_ZERO, DG_SRC_SINPROD, DG_SRC_POLY = 0, 1, 2
 DG_PMAX_2D, DG_PMAX_3D = 6, 4
 DG_SPACE_P, DG_SPACE_PQ = 0, 1
@@ -122,7 +124,7 @@ def load() -> C.CDLL:
     lib.dg_graph_info.argtypes = [V, V, V, V, V, V]
     lib.dg_graph_free.argtypes = [V]
     lib.dg_volume_noalloc.argtypes = [V, C.c_int, C.c_int, C.c_int, C.c_int, V, V, C.c_int, C.c_int, V, V, V,
-                                      C.c_double, C.c_double, C.c_double, V]
+                                      C.c_double, C.c_double, C.c_double, V, V]
     lib.dg_quad_prepare.argtypes = [V, V]
     lib.dg_quad_fit.argtypes = [V, V, V, C.c_int, C.c_int, C.POINTER(dg_quad_stats)]
     lib.dg_quad_targets.argtypes = [V, V, V]
@@ -494,11 +496,12 @@ class Mesh:
 
 
 def dg_volume_noalloc(stream, device: int, prec: int, p: int, x, y, elem_ptr, elem_idx, a, bx: float, by: float,
-                      c: float, blocks, nsub: int):
-    """Allocation-free volume blocks (all array arguments are device buffers)."""
+                      c: float, blocks, nsub: int, status=None):
+    """Allocation-free volume blocks (all array arguments are device buffers;
+    status, a one-int device tensor or None, receives the list check's code)."""
     _check(load().dg_volume_noalloc(stream, int(device), int(prec), int(p), int(x.numel()), _vp(x), _vp(y),
                                     int(a.numel()), int(nsub), _vp(elem_ptr), _vp(elem_idx), _vp(a), float(bx),
-                                    float(by), float(c), _vp(blocks)))
+                                    float(by), float(c), _vp(blocks), _vp(status) if status is not None else None))
 
 
 def device_view(ptr: int, shape, dtype: str):
