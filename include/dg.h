@@ -366,6 +366,34 @@ int dg_mlp_grad(dg_ctx *ctx, dg_mlp *net, const void *x_bf16, const float *targe
 int dg_mlp_train_step(dg_ctx *ctx, dg_mlp *net, const void *x_bf16, const float *target, int n, float lr,
                       float *loss);
 
+/* Checkpoints of a training run.  dg_mlp_save writes, after waiting for the
+ * context stream, one file holding the FP32 parameters, both Adam moment
+ * arrays, the step count, and two values of the caller's training loop that
+ * it needs to resume where it stopped: the seed of its data order and its
+ * data cursor (opaque to the library).  Format (host byte order): "DGMLPCK1",
+ * u32 version 1, u32 dg_mlp_num_params(), i64 step, u64 seed, i64 cursor,
+ * f32 params[], f32 m1[], f32 m2[], u64 FNV-1a checksum of the preceding
+ * bytes.  It is written to "<path>.tmp" and renamed over path.
+ * dg_mlp_load restores parameters, moments and step into net (the bfloat16
+ * operand copy is refreshed) and returns seed and cursor (either pointer may
+ * be NULL); DG_ERR_ARG for a missing, foreign, truncated or corrupted file.
+ * Training resumed from a checkpoint on the same GPU reproduces the loss
+ * curve of the uninterrupted run bit for bit: every training kernel sums in a
+ * fixed order. */
+int dg_mlp_save(dg_ctx *ctx, const dg_mlp *net, const char *path, uint64_t seed, int64_t cursor);
+int dg_mlp_load(dg_ctx *ctx, dg_mlp *net, const char *path, uint64_t *seed, int64_t *cursor);
+
+/* Learned rules for a mesh in one call (Sec. 1 and Sec. 3: a reduced rule
+ * per element in place of the sub-triangle rules): dg_quad_prepare, the
+ * network's proposal for every element (net NULL: the fixed 4 x 7 start),
+ * iters Gauss-Newton steps, and installation of the accepted rules, which
+ * the following assembly calls then use; the other elements keep their
+ * sub-triangle rules.  The proposals go to a library-owned buffer of
+ * ne x 84 floats (allocated at the first call, freed with the mesh).
+ * stats may be NULL.  2D meshes; asynchronous except for the statistics and
+ * the work-list update, which wait for the context stream. */
+int dg_quad_learn(dg_ctx *ctx, dg_mesh *mesh, dg_mlp *net, int iters, dg_quad_stats *stats);
+
 /* Per-launch timing.  When enabled, every kernel launch of the following
  * calls is bracketed by CUDA events on the context stream.  dg_kernel_stats
  * waits for the stream and copies up to cap records of the most recent call

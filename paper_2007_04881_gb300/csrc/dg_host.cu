@@ -290,7 +290,7 @@ struct dg_mesh {
   std::vector<int> perm_fan;  // the sub-simplex-rule work list
   // learned quadrature (2D)
   double *lq_mom = nullptr, *lq_mmom = nullptr, *lq_rule = nullptr, *lq64 = nullptr;
-  float *lq32 = nullptr, *lq_resid = nullptr;
+  float *lq32 = nullptr, *lq_resid = nullptr, *lq_out = nullptr;
   int *lq_elig = nullptr, *lq_ok = nullptr, *lq_okm = nullptr;
   void* lq_feat = nullptr;
   int* perm_dev = nullptr;  // device work list (owned by bufs)
@@ -305,7 +305,7 @@ struct dg_mesh {
   ~dg_mesh() {
     if (h_vals) cudaFree(h_vals);
     if (h_rhs) cudaFree(h_rhs);
-    void* q[] = {lq_mom, lq_mmom, lq_rule, lq64, lq32, lq_resid, lq_elig, lq_ok, lq_okm, lq_feat};
+    void* q[] = {lq_mom, lq_mmom, lq_rule, lq64, lq32, lq_resid, lq_elig, lq_ok, lq_okm, lq_feat, lq_out};
     for (void* x : q)
       if (x) cudaFree(x);
   }
@@ -2171,6 +2171,21 @@ int dg_quad_fit(dg_ctx* ctx, dg_mesh* mesh, const float* init, int iters, int in
     }
   }
   return DG_OK;
+}
+
+int dg_quad_learn(dg_ctx* ctx, dg_mesh* mesh, dg_mlp* net, int iters, dg_quad_stats* stats) {
+  if (!ctx || !mesh || iters < 0) return fail(DG_ERR_ARG, "dg_quad_learn: bad argument");
+  int rc = dg_quad_prepare(ctx, mesh);
+  if (rc != DG_OK) return rc;
+  const float* init = nullptr;
+  if (net) {
+    if (!mesh->lq_out && cudaMalloc(&mesh->lq_out, sizeof(float) * 84 * (size_t)mesh->dm.ne) != cudaSuccess)
+      return fail(DG_ERR_OOM, "dg_quad_learn: proposal buffer");
+    rc = dg_mlp_forward(ctx, net, mesh->lq_feat, mesh->dm.ne, mesh->lq_out);
+    if (rc != DG_OK) return rc;
+    init = mesh->lq_out;
+  }
+  return dg_quad_fit(ctx, mesh, init, iters, 1, stats);
 }
 
 int dg_quad_targets(dg_ctx* ctx, dg_mesh* mesh, float* targets) {

@@ -12,7 +12,9 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <random>
 #include <vector>
 
@@ -346,6 +348,94 @@ int dg_mlp_train_step(dg_ctx* ctx, dg_mlp* net, const void* x_bf16, const float*
                                                            b2, 1e-8f, c1, c2);
   refresh_bf16(net, st);
   return cudaGetLastError() == cudaSuccess ? DG_OK : mlp_fail(DG_ERR_CUDA, "dg_mlp_train_step: launch failed");
+}
+
+// Checkpoint file (little-endian, as the host writes it):
+//   "DGMLPCK1" | u32 version = 1 | u32 NPARAM | i64 step | u64 seed |
+//   i64 cursor | f32 params[NPARAM] | f32 m1[NPARAM] | f32 m2[NPARAM] |
+//   u64 FNV-1a of every byte before it.
+// Written to "<path>.tmp" and renamed over path, so a reader never sees a
+// half-written checkpoint.
+namespace {
+constexpr char kCkMagic[8] = {'D', 'G', 'M', 'L', 'P', 'C', 'K', '1'};
+struct CkHead {
+  char magic[8];
+  uint32_t version, nparam;
+  int64_t step;
+  uint64_t seed;
+  int64_t cursor;
+};
+uint64_t fnv1a(uint64_t h, const void* data, size_t n) {
+  const unsigned char* b = static_cast<const unsigned char*>(data);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+constexpr uint64_t kFnvBasis = 14695981039346656037ull;
+}  // namespace
+
+int dg_mlp_save(dg_ctx* ctx, const dg_mlp* net, const char* path, uint64_t seed, int64_t cursor) {
+  if (!ctx || !net || !path) return mlp_fail(DG_ERR_ARG, "dg_mlp_save: null argument");
+  if (cudaStreamSynchronize(dg_ctx_stream(ctx)) != cudaSuccess) return mlp_fail(DG_ERR_CUDA, "dg_mlp_save: stream failed");
+  std::vector<float> buf((size_t)3 * NPARAM);
+  if (cudaMemcpy(buf.data(), net->p, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(buf.data() + NPARAM, net->m1, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(buf.data() + 2 * NPARAM, net->m2, sizeof(float) * NPARAM, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return mlp_fail(DG_ERR_CUDA, "dg_mlp_save: copy failed");
+  CkHead h{};
+  std::memcpy(h.magic, kCkMagic, 8);
+  h.version = 1;
+  h.nparam = (uint32_t)NPARAM;
+  h.step = net->step;
+  h.seed = seed;
+  h.cursor = cursor;
+  uint64_t sum = fnv1a(kFnvBasis, &h, sizeof h);
+  sum = fnv1a(sum, buf.data(), sizeof(float) * buf.size());
+  const std::string tmp = std::string(path) + ".tmp";
+  FILE* f = std::fopen(tmp.c_str(), "wb");
+  if (!f) return mlp_fail(DG_ERR_ARG, "dg_mlp_save: cannot open the file for writing");
+  const bool ok = std::fwrite(&h, sizeof h, 1, f) == 1 && std::fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size() &&
+                  std::fwrite(&sum, sizeof sum, 1, f) == 1;
+  if (std::fclose(f) != 0 || !ok) {
+    std::remove(tmp.c_str());
+    return mlp_fail(DG_ERR_ARG, "dg_mlp_save: write failed");
+  }
+  if (std::rename(tmp.c_str(), path) != 0) {
+    std::remove(tmp.c_str());
+    return mlp_fail(DG_ERR_ARG, "dg_mlp_save: rename failed");
+  }
+  return DG_OK;
+}
+
+int dg_mlp_load(dg_ctx* ctx, dg_mlp* net, const char* path, uint64_t* seed, int64_t* cursor) {
+  if (!ctx || !net || !path) return mlp_fail(DG_ERR_ARG, "dg_mlp_load: null argument");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return mlp_fail(DG_ERR_ARG, "dg_mlp_load: cannot open the file");
+  CkHead h{};
+  std::vector<float> buf((size_t)3 * NPARAM);
+  uint64_t sum = 0;
+  const bool ok = std::fread(&h, sizeof h, 1, f) == 1 && std::memcmp(h.magic, kCkMagic, 8) == 0 && h.version == 1 &&
+                  h.nparam == (uint32_t)NPARAM && std::fread(buf.data(), sizeof(float), buf.size(), f) == buf.size() &&
+                  std::fread(&sum, sizeof sum, 1, f) == 1;
+  std::fclose(f);
+  if (!ok) return mlp_fail(DG_ERR_ARG, "dg_mlp_load: not a checkpoint of this network");
+  uint64_t chk = fnv1a(kFnvBasis, &h, sizeof h);
+  chk = fnv1a(chk, buf.data(), sizeof(float) * buf.size());
+  if (chk != sum) return mlp_fail(DG_ERR_ARG, "dg_mlp_load: checksum mismatch");
+  cudaStream_t st = dg_ctx_stream(ctx);
+  if (cudaStreamSynchronize(st) != cudaSuccess ||
+      cudaMemcpy(net->p, buf.data(), sizeof(float) * NPARAM, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(net->m1, buf.data() + NPARAM, sizeof(float) * NPARAM, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(net->m2, buf.data() + 2 * NPARAM, sizeof(float) * NPARAM, cudaMemcpyHostToDevice) != cudaSuccess)
+    return mlp_fail(DG_ERR_CUDA, "dg_mlp_load: copy failed");
+  net->step = h.step;
+  refresh_bf16(net, nullptr);
+  if (cudaDeviceSynchronize() != cudaSuccess) return mlp_fail(DG_ERR_CUDA, "dg_mlp_load: refresh failed");
+  if (seed) *seed = h.seed;
+  if (cursor) *cursor = h.cursor;
+  return DG_OK;
 }
 
 }  // extern "C"

@@ -140,6 +140,9 @@ def load() -> C.CDLL:
     lib.dg_mlp_forward.argtypes = [V, V, V, C.c_int, V]
     lib.dg_mlp_grad.argtypes = [V, V, V, V, C.c_int, V, V]
     lib.dg_mlp_train_step.argtypes = [V, V, V, V, C.c_int, C.c_float, V]
+    lib.dg_mlp_save.argtypes = [V, V, C.c_char_p, C.c_uint64, C.c_int64]
+    lib.dg_mlp_load.argtypes = [V, V, C.c_char_p, C.POINTER(C.c_uint64), C.POINTER(C.c_int64)]
+    lib.dg_quad_learn.argtypes = [V, V, V, C.c_int, C.POINTER(dg_quad_stats)]
     lib.dg_set_volume_path.argtypes = [V, C.c_int]
     lib.dg_partition.argtypes = [C.POINTER(dg_mesh_desc), C.c_int, V]
     lib.dg_mesh_upload_part.argtypes = [V, C.POINTER(dg_mesh_desc), V, C.c_int, C.POINTER(V)]
@@ -169,6 +172,7 @@ EXPORTS = (
     "dg_mlp_get_state", "dg_mlp_set_state", "dg_mlp_forward", "dg_mlp_grad", "dg_mlp_train_step",
     "dg_partition", "dg_mesh_upload_part", "dg_part_map", "dg_part_check", "dg_set_volume_path",
     "dg_slab_offsets", "dg_slab_layout", "dg_assemble_slab", "dg_slab_trace", "dg_assemble_varcoef",
+    "dg_mlp_save", "dg_mlp_load", "dg_quad_learn",
 )
 
 
@@ -446,6 +450,14 @@ class Mesh:
         return {"elements": st.elements, "eligible": st.eligible, "accepted": st.accepted,
                 "max_accepted_residual": st.max_accepted_residual}
 
+    def dg_quad_learn(self, net=None, iters: int = 3):
+        """Proposals of net (None: the fixed start), Gauss-Newton, install."""
+        st = dg_quad_stats()
+        _check(load().dg_quad_learn(self.ctx._h, self._h, net._h if net is not None else None, int(iters),
+                                    C.byref(st)))
+        return {"elements": st.elements, "eligible": st.eligible, "accepted": st.accepted,
+                "max_accepted_residual": st.max_accepted_residual}
+
     def dg_quad_targets(self, out):
         _check(load().dg_quad_targets(self.ctx._h, self._h, _vp(out)))
 
@@ -569,6 +581,17 @@ class MLP:
 
     def train_step(self, x_bf16, target, n: int, lr: float, loss=None):
         _check(load().dg_mlp_train_step(self.ctx._h, self._h, _vp(x_bf16), _vp(target), int(n), float(lr), _vp(loss)))
+
+    def save(self, path: str, seed: int, cursor: int):
+        """Checkpoint file: parameters, Adam moments, step, and the training
+        loop's data seed and cursor (dg_mlp_save)."""
+        _check(load().dg_mlp_save(self.ctx._h, self._h, os.fsencode(path), int(seed), int(cursor)))
+
+    def load(self, path: str):
+        """Restore a checkpoint; returns (seed, cursor)."""
+        seed, cursor = C.c_uint64(), C.c_int64()
+        _check(load().dg_mlp_load(self.ctx._h, self._h, os.fsencode(path), C.byref(seed), C.byref(cursor)))
+        return seed.value, cursor.value
 
 
 class Graph:

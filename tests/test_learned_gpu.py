@@ -226,3 +226,91 @@ def test_trained_network_beats_fixed_start(ctx):
     assert rate[("learned", 3)] > 0.25, rate
     assert rate[("learned", 4)] > rate[("fixed", 4)] + 0.4, rate
     net.close()
+
+
+def _train_run(ctx, net, X, T, seed, start, stop, bs=256, lr=2e-3):
+    """Steps start..stop-1 of a training loop whose minibatch at step k is
+    drawn from a generator seeded with (seed, k): the cursor k and the seed
+    fix the data order.  Returns the per-step losses (device floats)."""
+    import torch
+
+    n = X.shape[0]
+    losses = []
+    for k in range(start, stop):
+        idx = np.random.default_rng([seed, k]).choice(n, bs, replace=False)
+        it = torch.from_numpy(idx).cuda()
+        loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+        net.train_step(X[it].contiguous(), T[it].contiguous(), bs, lr, loss)
+        losses.append(loss)
+    ctx.dg_sync()
+    return torch.cat(losses).cpu().numpy()
+
+
+def test_checkpoint_resume_reproduces_loss_curve(ctx, tmp_path):
+    """Train K steps, checkpoint to a file (parameters, Adam moments, step,
+    data seed and cursor), resume in a fresh network, train on: the loss
+    curve and the final parameters equal the uninterrupted run's bit for bit.
+    A corrupted file is refused."""
+    import torch
+
+    rng = np.random.default_rng(5)
+    n = 4096
+    Xh = rng.uniform(-1, 1, (n, 24)).astype(np.float32)
+    W = rng.normal(0, 0.3, (24, 84)).astype(np.float32)
+    X = torch.from_numpy(Xh).cuda().to(torch.bfloat16)
+    T = torch.from_numpy(np.tanh(Xh @ W).astype(np.float32)).cuda()
+    seed, k1, k2 = 77, 40, 60
+    full = dg.MLP(ctx, seed=3)
+    ref = _train_run(ctx, full, X, T, seed, 0, k1 + k2)
+    ref_params, ref_step = full.get_params()
+
+    first = dg.MLP(ctx, seed=3)
+    head = _train_run(ctx, first, X, T, seed, 0, k1)
+    path = str(tmp_path / "net.ckpt")
+    first.save(path, seed, k1)
+    first.close()
+    resumed = dg.MLP(ctx, seed=11)  # different initial weights: all state comes from the file
+    s, cursor = resumed.load(path)
+    assert (s, cursor) == (seed, k1)
+    tail = _train_run(ctx, resumed, X, T, s, cursor, k1 + k2)
+    got_params, got_step = resumed.get_params()
+    assert np.array_equal(np.concatenate([head, tail]).view(np.uint32), ref.view(np.uint32))
+    assert got_step == ref_step == k1 + k2
+    assert np.array_equal(got_params.view(np.uint32), ref_params.view(np.uint32))
+
+    raw = bytearray(open(path, "rb").read())
+    raw[100] ^= 0x40
+    bad = str(tmp_path / "bad.ckpt")
+    open(bad, "wb").write(bytes(raw))
+    with pytest.raises(dg.DGError):
+        resumed.load(bad)
+    with pytest.raises(dg.DGError):
+        resumed.load(str(tmp_path / "missing.ckpt"))
+    full.close()
+    resumed.close()
+
+
+def test_quad_learn_equals_its_steps(ctx):
+    """dg_quad_learn (prepare, proposal, Gauss-Newton, install) equals the
+    same steps called one by one: the same accepted set and bitwise the same
+    assembled matrix."""
+    import torch
+
+    wl, m1 = _mesh(ctx, n=400, seed=45)
+    _, m2 = _mesh(ctx, n=400, seed=45)
+    net = dg.MLP(ctx, seed=2)
+    st1 = m1.dg_quad_learn(net, iters=4)
+    m2.dg_quad_prepare()
+    out = torch.zeros(m2.ne, 84, dtype=torch.float32, device="cuda")
+    net.forward(m2.dg_quad_buffers()["feat"], m2.ne, out)
+    st2 = m2.dg_quad_fit(out, iters=4, install=True)
+    assert st1 == st2
+    v1 = torch.zeros(m1.nvals, dtype=torch.float64, device="cuda")
+    v2 = torch.zeros(m2.nvals, dtype=torch.float64, device="cuda")
+    m1.dg_assemble(dg.DG_PREC_FP64, v1)
+    m2.dg_assemble(dg.DG_PREC_FP64, v2)
+    ctx.dg_sync()
+    assert torch.equal(v1, v2)
+    st0 = m1.dg_quad_learn(None, iters=3)  # the fixed start, no network
+    assert st0["elements"] == m1.ne
+    net.close()
