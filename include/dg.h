@@ -224,6 +224,22 @@ int dg_assemble_step(dg_ctx *ctx, dg_mesh *mesh, int prec, void *vals, void *rhs
  * (dg_batch_offsets; arrays of n+1 entries, any may be NULL).  All degree
  * groups of all members are then assembled by the same launches. */
 int dg_batch_upload(dg_ctx *ctx, const dg_mesh_desc *const *descs, int n, dg_mesh **out);
+
+/* The other form of a batch: nmesh meshes uploaded separately (each by
+ * dg_mesh_upload or dg_batch_upload), each assembled into its own buffers in
+ * one call.  vals[k] (device, nvals of mesh k, double for DG_PREC_FP64 else
+ * float) is OVERWRITTEN with every block; rhs (may be NULL, or hold NULL
+ * entries) with the load vectors.  Each member runs its whole pass as
+ * dg_assemble_step does (geometry in the pass's precision, then the row
+ * kernels in the launch shape last tuned for that mesh, degree groups one
+ * after the other); members run concurrently on four forked streams of the
+ * context.  use_graph != 0 records the whole batch as one CUDA graph,
+ * launches it and frees it (for repeated passes over the same meshes, record
+ * once: dg_batch_upload + dg_graph_create).  prec may carry DG_GEOM_FP64.
+ * Asynchronous on the context stream; each member's result equals its own
+ * dg_assemble_step bit for bit. */
+int dg_assemble_batch(dg_ctx *ctx, dg_mesh *const *meshes, int nmesh, int prec, void *const *vals, void *const *rhs,
+                      int use_graph);
 int dg_batch_offsets(const dg_mesh *mesh, int *nmesh, int *elem_off, int64_t *val_off, int64_t *dof_off);
 
 /* How the row passes evaluate the volume terms of Eq. (2.4):

@@ -2045,6 +2045,70 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
   return DG_OK;
 }
 
+// Many independent meshes in one call: each member's whole pass (geometry
+// in the pass's precision, then its row kernels in its own tuned launch
+// shape) on one of the context's forked side streams, round robin, joined
+// back into the context stream.  use_graph records the lot as one CUDA
+// graph, launches it and frees it.
+int dg_assemble_batch(dg_ctx* ctx, dg_mesh* const* meshes, int nmesh, int prec, void* const* vals,
+                      void* const* rhs, int use_graph) {
+  if (!ctx || !meshes || !vals || nmesh <= 0) return fail(DG_ERR_ARG, "dg_assemble_batch: bad argument");
+  int base = prec;
+  const int gmask = pass_geometry(&base);
+  if (gmask < 0) return fail(DG_ERR_ARG, "unknown precision %d", prec);
+  for (int k = 0; k < nmesh; ++k)
+    if (!meshes[k] || !vals[k]) return fail(DG_ERR_ARG, "dg_assemble_batch: member %d has a null mesh or vals", k);
+  SideStreams& ss = ctx->streams;
+  DG_CUDA_TRY(ss.ensure());
+  cudaStream_t st = ctx->stream;
+  cudaStream_t cap = nullptr;
+  if (use_graph) {
+    DG_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      cudaStreamDestroy(cap);
+      return fail(DG_ERR_CUDA, "dg_assemble_batch: begin capture failed");
+    }
+    st = cap;
+  }
+  int rc = DG_OK, launches = 0;
+  if (cudaEventRecord(ss.fork, st) != cudaSuccess) rc = fail(DG_ERR_CUDA, "dg_assemble_batch: fork failed");
+  for (int i = 0; rc == DG_OK && i < 4; ++i)
+    if (cudaStreamWaitEvent(ss.side[i], ss.fork, 0) != cudaSuccess) rc = fail(DG_ERR_CUDA, "dg_assemble_batch: fork failed");
+  for (int k = 0; rc == DG_OK && k < nmesh; ++k) {
+    dg_mesh* mesh = meshes[k];
+    cudaStream_t br = ss.side[k % 4];
+    launches += launch_geometry(mesh->dm, br, nullptr, gmask);
+    int occ = 0, path = -1;
+    bool conc = false;
+    step_shape(ctx, mesh, base, &occ, &conc, &path);
+    const int mode = kModeVol | kModeFace | (rhs && rhs[k] ? kModeRhs : 0);
+    // a member's degree groups stay on its branch stream (serial): the
+    // members themselves are the concurrency
+    rc = run_assembly(ctx, mesh, base, mode, vals[k], rhs ? rhs[k] : nullptr, true, true, br, false, occ, false, path);
+    launches += ctx->last_launches;
+  }
+  for (int i = 0; rc == DG_OK && i < 4; ++i) {
+    if (cudaEventRecord(ss.join[i], ss.side[i]) != cudaSuccess || cudaStreamWaitEvent(st, ss.join[i], 0) != cudaSuccess)
+      rc = fail(DG_ERR_CUDA, "dg_assemble_batch: join failed");
+  }
+  if (use_graph) {
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(cap, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (rc == DG_OK && ce != cudaSuccess) rc = fail(DG_ERR_CUDA, "dg_assemble_batch: capture failed: %s", cudaGetErrorString(ce));
+    if (rc == DG_OK && cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+      rc = fail(DG_ERR_CUDA, "dg_assemble_batch: instantiate failed");
+    if (rc == DG_OK && cudaGraphLaunch(exec, ctx->stream) != cudaSuccess) rc = fail(DG_ERR_CUDA, "dg_assemble_batch: launch failed");
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    cudaStreamDestroy(cap);
+  }
+  if (rc != DG_OK) return rc;
+  ctx->last_launches = launches;
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+
 int dg_graph_launch(dg_ctx* ctx, dg_graph* g) {
   if (!ctx || !g) return fail(DG_ERR_ARG, "dg_graph_launch: null argument");
   DG_CUDA_TRY(cudaGraphLaunch(g->exec, ctx->stream));

@@ -143,6 +143,7 @@ def load() -> C.CDLL:
     lib.dg_mlp_save.argtypes = [V, V, C.c_char_p, C.c_uint64, C.c_int64]
     lib.dg_mlp_load.argtypes = [V, V, C.c_char_p, C.POINTER(C.c_uint64), C.POINTER(C.c_int64)]
     lib.dg_quad_learn.argtypes = [V, V, V, C.c_int, C.POINTER(dg_quad_stats)]
+    lib.dg_assemble_batch.argtypes = [V, V, C.c_int, C.c_int, V, V, C.c_int]
     lib.dg_set_volume_path.argtypes = [V, C.c_int]
     lib.dg_partition.argtypes = [C.POINTER(dg_mesh_desc), C.c_int, V]
     lib.dg_mesh_upload_part.argtypes = [V, C.POINTER(dg_mesh_desc), V, C.c_int, C.POINTER(V)]
@@ -172,7 +173,7 @@ EXPORTS = (
     "dg_mlp_get_state", "dg_mlp_set_state", "dg_mlp_forward", "dg_mlp_grad", "dg_mlp_train_step",
     "dg_partition", "dg_mesh_upload_part", "dg_part_map", "dg_part_check", "dg_set_volume_path",
     "dg_slab_offsets", "dg_slab_layout", "dg_assemble_slab", "dg_slab_trace", "dg_assemble_varcoef",
-    "dg_mlp_save", "dg_mlp_load", "dg_quad_learn",
+    "dg_mlp_save", "dg_mlp_load", "dg_quad_learn", "dg_assemble_batch",
 )
 
 
@@ -514,6 +515,16 @@ def dg_volume_noalloc(stream, device: int, prec: int, p: int, x, y, elem_ptr, el
     _check(load().dg_volume_noalloc(stream, int(device), int(prec), int(p), int(x.numel()), _vp(x), _vp(y),
                                     int(a.numel()), int(nsub), _vp(elem_ptr), _vp(elem_idx), _vp(a), float(bx),
                                     float(by), float(c), _vp(blocks), _vp(status) if status is not None else None))
+
+
+def dg_assemble_batch(ctx: Context, meshes, prec: int, vals, rhs=None, use_graph: bool = False):
+    """Separately uploaded meshes, each into its own vals[k] / rhs[k] (device
+    tensors; rhs may be None or hold None entries), in one call."""
+    n = len(meshes)
+    mh = (C.c_void_p * n)(*[m._h.value for m in meshes])
+    vh = (C.c_void_p * n)(*[_vp(v) for v in vals])
+    rh = (C.c_void_p * n)(*[_vp(r) for r in rhs]) if rhs is not None else None
+    _check(load().dg_assemble_batch(ctx._h, mh, n, int(prec), vh, rh, int(bool(use_graph))))
 
 
 def device_view(ptr: int, shape, dtype: str):
