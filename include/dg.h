@@ -267,6 +267,15 @@ int dg_batch_offsets(const dg_mesh *mesh, int *nmesh, int *elem_off, int64_t *va
  * calls and recorded passes made after it; DG_ERR_ARG for another path. */
 int dg_set_volume_path(dg_ctx *ctx, int path);
 
+/* Register-tile variant (0..2) of each degree's row kernel (variants[p], 9
+ * entries, p = 0..8; NULL: all defaults) for the calls that have no tuned
+ * launch shape: the direct calls, and dg_assemble_step / dg_assemble_host /
+ * dg_assemble_batch on a mesh and precision dg_graph_create has not tuned.
+ * A degree without that variant (see dg_graph_tiles) takes its default.
+ * Every variant sums each block entry over the same points in the same
+ * order, so the results are bitwise those of the default tiles. */
+int dg_set_tile_variants(dg_ctx *ctx, const int *variants);
+
 /* Partitions (Sec. 4.2: the elements are split across GPUs, each GPU builds
  * and assembles its own rows, faces on a cut are computed by both owners, and
  * assembly needs no communication).
@@ -321,6 +330,17 @@ int dg_graph_create(dg_ctx *ctx, dg_mesh *mesh, int prec, void *vals, void *rhs,
 int dg_graph_launch(dg_ctx *ctx, dg_graph *graph);
 int dg_graph_info(const dg_graph *graph, int *occ_cap, int *concurrent, float *tuned_ms, int *launches,
                   int *vol_path);
+/* The register tiles the recorded pass uses: tile_tm[p] (9 entries, p =
+ * 0..8) is the tile edge of the degree-p row kernel (-1 for the tensor-core
+ * forms' fixed fragment layout, 0 where the mesh has no element of degree p);
+ * trials: passes the autotuner timed (0 without autotuning).  Either output
+ * may be NULL.  With autotuning, dg_graph_create first times the launch
+ * shapes above with the default tiles, then, for each degree present, every
+ * other tile variant of its row kernel (FP32: 2D degree 3 {5, 4}, degree 4
+ * {8, 5, 4}, degree 5 {7, 6, 5}, degree 6 {7, 6}; 3D degree 2 {5, 4},
+ * degree 3 {4, 5, 7}; the first is the default) against the best pass so
+ * far, and keeps a variant only where it makes the pass faster. */
+int dg_graph_tiles(const dg_graph *graph, int *tile_tm, int *trials);
 int dg_graph_free(dg_graph *graph);
 
 /* Learned reduced volume rules (2D).  For each element mapped to its

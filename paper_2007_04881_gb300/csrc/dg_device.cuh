@@ -38,20 +38,43 @@ __host__ __device__ constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b *
 
 // Register-tile geometry of the element kernel for (D, P): each thread owns a
 // TM x TM tile of the (padded) n x n block; G elements share a warp.  TM = n
-// (one tile) selects the one-thread-per-element kernel.  The FP32 table was
-// picked by measurement: on the 65k-cell 2D workload degree 2 runs a whole
-// element per thread (36 accumulators) and degree 4 uses 8 x 8 tiles, 4
-// threads per element; on the 3D workload degree 3 (whose volume terms take
-// the moment launch) uses 4 x 4 tiles, 25 threads per element; other tile
-// sizes and chunk widths measured slower.
-template <int D, int P, typename T = float>
+// (one tile) selects the one-thread-per-element kernel.  Variant 0 of the
+// FP32 table is the measured default: on the 65k-cell 2D workload degree 2
+// runs a whole element per thread (36 accumulators) and degree 4 uses 8 x 8
+// tiles, 4 threads per element; on the 3D workload degree 3 (whose volume
+// terms take the moment launch) uses 4 x 4 tiles, 25 threads per element.
+// Variants 1 and 2 are the other tile sizes that came close on some
+// workload; the recorded pass's autotuner (dg_graph_create) times them.
+template <int D, int P, typename T>
+__host__ __device__ constexpr int tile_tm(int V) {
+  if (sizeof(T) == 4 && D == 2) {
+    if (P == 1) return 3;
+    if (P == 2) return 6;
+    if (P == 3) return V == 1 ? 4 : 5;
+    if (P == 4) return V == 1 ? 5 : V == 2 ? 4 : 8;
+    if (P == 5) return V == 1 ? 6 : V == 2 ? 5 : 7;
+    return V == 1 ? 6 : 7;
+  }
+  if (sizeof(T) == 4 && D == 3) {
+    if (P == 1) return 4;
+    if (P == 2) return V == 1 ? 4 : 5;
+    if (P == 3) return V == 1 ? 5 : V == 2 ? 7 : 4;
+    return 7;
+  }
+  return D == 2 ? (P <= 2 ? 3 : P == 3 ? 5 : P == 4 ? 4 : 7) : (P == 1 ? 4 : P <= 3 ? 5 : 7);
+}
+// number of distinct tile variants of (D, P, T)
+template <int D, int P, typename T>
+__host__ __device__ constexpr int tile_variants() {
+  return tile_tm<D, P, T>(2) != tile_tm<D, P, T>(0) && tile_tm<D, P, T>(2) != tile_tm<D, P, T>(1) ? 3
+         : tile_tm<D, P, T>(1) != tile_tm<D, P, T>(0)                                               ? 2
+                                                                                                    : 1;
+}
+
+template <int D, int P, typename T = float, int V = 0>
 struct TileCfg {
   static constexpr int N = nbasis(D, P);
-  static constexpr int TM = sizeof(T) == 4 && D == 2 && P == 2   ? 6
-                            : sizeof(T) == 4 && D == 2 && P == 4 ? 8
-                            : sizeof(T) == 4 && D == 3 && P == 3 ? 4
-                            : D == 2 ? (P <= 2 ? 3 : P == 3 ? 5 : P == 4 ? 4 : 7)
-                                     : (P == 1 ? 4 : P <= 3 ? 5 : 7);
+  static constexpr int TM = tile_tm<D, P, T>(V);
   static constexpr int TR = (N + TM - 1) / TM;
   static constexpr int TPE = TR * TR;
   static constexpr int G = 32 / TPE;
@@ -369,19 +392,17 @@ __device__ __forceinline__ void load_elem_par(const DevMesh& m, int e, ElemPar<D
   q.R = EG[(size_t)(3 * D) * m.ne + e];
 }
 
-// Quadrature point on a face side: xi in that side's frame and the scaled
-// normal n' (of n0, the normal out of the face's first element).
+// Quadrature point of one side of a half-face record (r: the record for the
+// own side, the record + FV for the other) at the reference point fr: xi in
+// that side's frame and its scaled normal, pointing out of the own element.
 template <int D, typename T>
-__device__ __forceinline__ void face_side_point(const T* __restrict__ FS, int nf, int f, int s, const T* fr, T* xi,
-                                                T* np) {
-  constexpr int FV = side_vals(D);
-  const T* fs = FS + (size_t)s * FV * nf + f;
+__device__ __forceinline__ void hf_point(const T* r, const T* fr, T* xi, T* np) {
 #pragma unroll
   for (int d = 0; d < D; ++d) {
-    T v = fs[(size_t)d * nf] + fr[0] * fs[(size_t)(D + d) * nf];
-    if constexpr (D == 3) v += fr[1] * fs[(size_t)(2 * D + d) * nf];
+    T v = r[d] + fr[0] * r[D + d];
+    if constexpr (D == 3) v += fr[1] * r[2 * D + d];
     xi[d] = v;
-    np[d] = fs[(size_t)(D * D + d) * nf];
+    np[d] = r[D * D + d];
   }
 }
 
@@ -448,29 +469,31 @@ __device__ __forceinline__ void zero_groups(T* __restrict__ dst, int words) {
 // --------------------------------------------------------------------------
 
 template <int D, int P, int PK, typename T>
-__device__ __forceinline__ void lane_offdiag(const DevMesh& m, const ElemPar<D, T>& q, int it, int se, int k, int64_t off,
-                                             const T* __restrict__ FS, const T* __restrict__ FSC,
-                                             const T* __restrict__ FR, const T* ctab, T* __restrict__ vals) {
+__device__ __forceinline__ void lane_offdiag(const DevMesh& m, const ElemPar<D, T>& q, int4 br, int64_t off,
+                                             const T* __restrict__ HFR, const T* __restrict__ FR, const T* ctab,
+                                             T* __restrict__ vals) {
   constexpr int N = nbasis(D, P), NK = nbasis(D, PK);
+  constexpr int FV = side_vals(D), RS = hf_rec_vals(D);
   T acc[N][NK];
 #pragma unroll
   for (int i = 0; i < N; ++i)
 #pragma unroll
     for (int j = 0; j < NK; ++j) acc[i][j] = T(0);
   const T* EG = pick<T>(m.eg64, m.eg32);
+  const int k = br.x;
   const T ak = T(m.a[k]);
   const T Rk = EG[(size_t)(3 * D) * m.ne + k];
-  const T sgn = se == 0 ? T(1) : T(-1);
-  for (int f = m.if_fptr[it]; f < m.if_fptr[it + 1]; ++f) {
-    const int nq = m.f_nq[f];
-    const int qf = D == 2 ? nq : nq * nq;
-    const T J = FSC[f], sig = FSC[(size_t)m.nf + f], bn = sgn * FSC[(size_t)2 * m.nf + f];
+  constexpr int nq = (P > PK ? P : PK) + 1;
+  constexpr int qf = D == 2 ? nq : nq * nq;
+  for (int fi = 0; fi < br.z; ++fi) {
+    const T* rec = HFR + (size_t)(br.y + fi) * RS;
+    const T J = rec[2 * FV], sig = rec[2 * FV + 1], bn = rec[2 * FV + 2];
     const T upw = bn < T(0) ? bn : T(0);
     for (int lq = 0; lq < qf; ++lq) {
       const T* fr = FR + (size_t)(m.rt.face_off[nq] + lq) * (D == 2 ? 2 : 3);
       T xe[D], ne_[D], xk[D], nk_[D];
-      face_side_point<D, T>(FS, m.nf, f, se, fr, xe, ne_);
-      face_side_point<D, T>(FS, m.nf, f, 1 - se, fr, xk, nk_);
+      hf_point<D, T>(rec, fr, xe, ne_);
+      hf_point<D, T>(rec + FV, fr, xk, nk_);
       const T W = fr[D == 2 ? 1 : 2] * J;
       T Pe[N], De[D][N], Pk[NK], Dk[D][NK];
       basis_eval<D, P, T>(xe, Pe, De);
@@ -480,14 +503,14 @@ __device__ __forceinline__ void lane_offdiag(const DevMesh& m, const ElemPar<D, 
       for (int i = 0; i < N; ++i) {
         T v = T(0);
 #pragma unroll
-        for (int d = 0; d < D; ++d) v += sgn * ne_[d] * De[d][i];
+        for (int d = 0; d < D; ++d) v += ne_[d] * De[d][i];
         dne[i] = v;
       }
 #pragma unroll
       for (int j = 0; j < NK; ++j) {
         T dn = T(0);
 #pragma unroll
-        for (int d = 0; d < D; ++d) dn += sgn * nk_[d] * Dk[d][j];
+        for (int d = 0; d < D; ++d) dn += nk_[d] * Dk[d][j];
         const T v0 = W * (T(-0.5) * ak * dn + (upw - sig) * Pk[j]);
         const T v1 = W * (T(0.5) * q.a * Pk[j]);
 #pragma unroll
@@ -515,9 +538,9 @@ __global__ void __launch_bounds__(kWarps * 32)
   fill_ctab<D, T>(ctab, NMAXC);
   __syncthreads();
   const T* SG = pick<T>(m.sg64, m.sg32);
-  const T* FS = pick<T>(m.fs64, m.fs32);
-  const T* FSC = pick<T>(m.fsc64, m.fsc32);
+  const T* HFR = pick<T>(m.hfr64, m.hfr32);
   const T* FR = pick<T>(m.rt.face64, m.rt.face32);
+  constexpr int FV = side_vals(D), RS = hf_rec_vals(D);
   const bool mat_vol = mode & kModeVol, mat_face = mode & kModeFace, do_rhs = mode & kModeRhs;
   const bool accum = mode & kModeAccum;
   const int base = m.elem_pstart[P], count = m.elem_pstart[P + 1] - base;
@@ -535,18 +558,16 @@ __global__ void __launch_bounds__(kWarps * 32)
     if (part == 1) {
       if (mat_face) {
         for (int bk = m.row_ptr[e]; bk < m.row_ptr[e + 1]; ++bk) {
-          const int it = m.blk_if[bk];
-          if (it < 0) continue;
-          const int k = m.col[bk];
-          const int se = m.if_e0[it] == e ? 0 : 1;
+          const int4 br = m.blk_rec[bk];  // neighbour, first half face, faces, neighbour degree
+          if (br.x < 0) continue;
           const int64_t off = m.blk_off[bk];
-          switch (m.p[k]) {
-            case 1: lane_offdiag<D, P, 1, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
-            case 2: lane_offdiag<D, P, 2, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
-            case 3: lane_offdiag<D, P, 3, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
-            case 4: lane_offdiag<D, P, 4, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
-            case 5: if constexpr (D == 2) lane_offdiag<D, P, 5, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
-            case 6: if constexpr (D == 2) lane_offdiag<D, P, 6, T>(m, q, it, se, k, off, FS, FSC, FR, ctab, vals); break;
+          switch (br.w) {
+            case 1: lane_offdiag<D, P, 1, T>(m, q, br, off, HFR, FR, ctab, vals); break;
+            case 2: lane_offdiag<D, P, 2, T>(m, q, br, off, HFR, FR, ctab, vals); break;
+            case 3: lane_offdiag<D, P, 3, T>(m, q, br, off, HFR, FR, ctab, vals); break;
+            case 4: lane_offdiag<D, P, 4, T>(m, q, br, off, HFR, FR, ctab, vals); break;
+            case 5: if constexpr (D == 2) lane_offdiag<D, P, 5, T>(m, q, br, off, HFR, FR, ctab, vals); break;
+            case 6: if constexpr (D == 2) lane_offdiag<D, P, 6, T>(m, q, br, off, HFR, FR, ctab, vals); break;
             default: break;
           }
         }
@@ -650,18 +671,19 @@ __global__ void __launch_bounds__(kWarps * 32)
     }
     if (mat_face || do_rhs) {
       for (int hf = m.hf_ptr[e]; hf < m.hf_ptr[e + 1]; ++hf) {
-        const int f = m.hf_face[hf], s = m.hf_side[hf], nq = m.f_nq[f];
+        // the half face's record: own side, then J, sigma, b.n, nq (signed)
+        const T* rec = HFR + (size_t)hf * RS;
+        const T J = rec[2 * FV], sig = rec[2 * FV + 1], bn = rec[2 * FV + 2], nqs = rec[2 * FV + 3];
+        const bool bnd = nqs < T(0);
+        const int nq = (int)(bnd ? -nqs : nqs);
         const int qf = D == 2 ? nq : nq * nq;
-        const bool bnd = m.f_e1[f] < 0;
         if (!mat_face && !bnd) continue;
-        const T sgn = s == 0 ? T(1) : T(-1);
-        const T J = FSC[f], sig = FSC[(size_t)m.nf + f], bn = sgn * FSC[(size_t)2 * m.nf + f];
         const T kap = bnd ? T(1) : T(0.5);
         const T upw = bn < T(0) ? bn : T(0);
         for (int lq = 0; lq < qf; ++lq) {
           const T* fr = FR + (size_t)(m.rt.face_off[nq] + lq) * (D == 2 ? 2 : 3);
           T xi[D], np[D];
-          face_side_point<D, T>(FS, m.nf, f, s, fr, xi, np);
+          hf_point<D, T>(rec, fr, xi, np);
           const T W = fr[D == 2 ? 1 : 2] * J;
           T Phi[N], Dd[D][N], dn[N];
           basis_eval<D, P, T>(xi, Phi, Dd);
@@ -669,7 +691,7 @@ __global__ void __launch_bounds__(kWarps * 32)
           for (int i = 0; i < N; ++i) {
             T v = T(0);
 #pragma unroll
-            for (int d = 0; d < D; ++d) v += sgn * np[d] * Dd[d][i];
+            for (int d = 0; d < D; ++d) v += np[d] * Dd[d][i];
             dn[i] = v;
           }
           if (mat_face) {
@@ -717,9 +739,9 @@ __global__ void __launch_bounds__(kWarps * 32)
 // memory by one lane per point and contracted by the tile threads
 // --------------------------------------------------------------------------
 
-template <int D, int P, typename T>
+template <int D, int P, typename T, int V = 0>
 struct RowSmem {
-  using Cfg = TileCfg<D, P, T>;
+  using Cfg = TileCfg<D, P, T, V>;
   static constexpr int G = Cfg::G, TM = Cfg::TM, TR = Cfg::TR, TMP = Cfg::TMP, ROW = Cfg::ROW, NT = Cfg::NT;
   static constexpr int C = ChunkCfg<D, T>::CW / G > 0 ? ChunkCfg<D, T>::CW / G : 1;
   static constexpr int PSU = point_stride<T, TMP>(NT * ROW);  // staged point: NT rows of ROW
@@ -751,10 +773,10 @@ enum : int {
   kPiNslot,     // off-diagonal blocks in the row
   kPiDpos,      // position of the diagonal block in the row
   kPiSBlk,      // current slot: block index
-  kPiSSide,     // current slot: side of this element in the interface
+  kPiSSide,     // current slot: face points per direction, max(p, p_k) + 1
   kPiSNk,       // current slot: neighbour basis size
   kPiSPk,       // current slot: neighbour degree
-  kPiSF0,       // current slot: first face of the interface
+  kPiSF0,       // current slot: first half face of the interface in the row
   kPiSQF,       // current slot: points per face
   kPiSNpts,     // current slot: points of the interface
   kPiLrn,       // 1: the element has a learned volume rule
@@ -762,11 +784,11 @@ enum : int {
 // T parameter slots: a'[D], b'[D], lo[D], L[D], then:
 enum : int { kPtC = 0, kPtA = 1, kPtR = 2, kPtAk = 3, kPtRk = 4 };
 
-template <int D, int P, typename T>
+template <int D, int P, typename T, int TV = 0>
 __global__ void __launch_bounds__(kWarps * 32)
     row_kernel(const DevMesh m, int mode, T* __restrict__ vals, T* __restrict__ rhs) {
-  using Cfg = TileCfg<D, P, T>;
-  using SM = RowSmem<D, P, T>;
+  using Cfg = TileCfg<D, P, T, TV>;
+  using SM = RowSmem<D, P, T, TV>;
   constexpr int N = Cfg::N, TM = Cfg::TM, TR = Cfg::TR, TPE = Cfg::TPE, G = Cfg::G;
   constexpr int TMP = Cfg::TMP, ROW = Cfg::ROW, NT = Cfg::NT, QT = Cfg::QT, C = SM::C;
   constexpr int SV = sub_vals(D), PT = SM::PT, PI = SM::PI, PSU = SM::PSU;
@@ -793,10 +815,10 @@ __global__ void __launch_bounds__(kWarps * 32)
   __syncthreads();
 
   const T* SG = pick<T>(m.sg64, m.sg32);
-  const T* FS = pick<T>(m.fs64, m.fs32);
-  const T* FSC = pick<T>(m.fsc64, m.fsc32);
+  const T* HFR = pick<T>(m.hfr64, m.hfr32);
   const T* FR = pick<T>(m.rt.face64, m.rt.face32);
   const T* EG = pick<T>(m.eg64, m.eg32);
+  constexpr int FV = side_vals(D), RS = hf_rec_vals(D);
 
   const bool mat_vol = mode & kModeVol, mat_face = mode & kModeFace, do_rhs = mode & kModeRhs;
   const bool accum = mode & kModeAccum;
@@ -985,18 +1007,20 @@ __global__ void __launch_bounds__(kWarps * 32)
                 hi_ = mid - 1;
             }
             const int hf = lo_;
-            const int f = m.hf_face[hf];
-            const int s = m.hf_side[hf];
-            const int nq = m.f_nq[f];
+            // the half face's record: own side, then J, sigma, b.n, nq (signed)
+            const T* rec = HFR + (size_t)hf * RS;
+            T sc[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) sc[j] = rec[2 * FV + j];
+            const bool bnd = sc[3] < T(0);
+            const int nq = (int)(bnd ? -sc[3] : sc[3]);
             const int lq = qv - m.hf_qoff[hf];
             const T* fr = FR + (size_t)(m.rt.face_off[nq] + lq) * (D == 2 ? 2 : 3);
             T xi[D], np[D];
-            face_side_point<D, T>(FS, m.nf, f, s, fr, xi, np);
-            const T sgn = s == 0 ? T(1) : T(-1);
-            const T W = fr[D == 2 ? 1 : 2] * FSC[f];
-            const T sig = FSC[(size_t)m.nf + f];
-            const T bn = sgn * FSC[(size_t)2 * m.nf + f];
-            const bool bnd = m.f_e1[f] < 0;
+            hf_point<D, T>(rec, fr, xi, np);
+            const T W = fr[D == 2 ? 1 : 2] * sc[0];
+            const T sig = sc[1];
+            const T bn = sc[2];
             const T kap = bnd ? T(1) : T(0.5);
             const T a = pt[X + kPtA];
             const T upw = bn < T(0) ? bn : T(0);
@@ -1006,7 +1030,7 @@ __global__ void __launch_bounds__(kWarps * 32)
             for (int i = 0; i < N; ++i) {
               T v = T(0);
 #pragma unroll
-              for (int d = 0; d < D; ++d) v += sgn * np[d] * Dd[d][i];
+              for (int d = 0; d < D; ++d) v += np[d] * Dd[d][i];
               dn[i] = v;
               V0[i] = W * (-kap * a * v + (sig - upw) * Phi[i]);
               V1[i] = W * (-kap * a * Phi[i]);
@@ -1103,21 +1127,18 @@ __global__ void __launch_bounds__(kWarps * 32)
         if (lane < G) {
           int* pi = PIv + lane * PI;
           if (lane < gcount && sl < pi[kPiNslot]) {
-            const int e = pi[kPiElem];
             const int bk = pi[kPiRow0] + sl + (sl >= pi[kPiDpos] ? 1 : 0);
-            const int it = m.blk_if[bk];
-            const int k = m.col[bk];
-            const int pk = m.p[k];
-            const int f0 = m.if_fptr[it];
-            const int nq = m.f_nq[f0];
+            const int4 br = m.blk_rec[bk];  // neighbour, first half face, faces, neighbour degree
+            const int k = br.x, pk = br.w;
+            const int nq = (P > pk ? P : pk) + 1;
             const int qf = D == 2 ? nq : nq * nq;
             pi[kPiSBlk] = bk;
-            pi[kPiSSide] = m.if_e0[it] == e ? 0 : 1;
+            pi[kPiSSide] = nq;
             pi[kPiSPk] = pk;
             pi[kPiSNk] = nbasis(D, pk);
-            pi[kPiSF0] = f0;
+            pi[kPiSF0] = br.y;
             pi[kPiSQF] = qf;
-            pi[kPiSNpts] = (m.if_fptr[it + 1] - f0) * qf;
+            pi[kPiSNpts] = br.z * qf;
             PTv[lane * PT + X + kPtAk] = T(m.a[k]);
             PTv[lane * PT + X + kPtRk] = EG[(size_t)(3 * D) * m.ne + k];
           } else {
@@ -1150,17 +1171,19 @@ __global__ void __launch_bounds__(kWarps * 32)
                 const int* pi = PIv + g * PI;
                 if (g < gcount && qv < pi[kPiSNpts]) {
                   const int qf = pi[kPiSQF];
-                  const int f = pi[kPiSF0] + qv / qf, lq = qv - (qv / qf) * qf;
-                  const int se = pi[kPiSSide];
-                  const int nq = m.f_nq[f];
+                  const int fi = qv / qf, lq = qv - fi * qf;
+                  const int nq = pi[kPiSSide];
+                  // the half face's record: both sides, then J, sigma, b.n
+                  const T* rec = HFR + (size_t)(pi[kPiSF0] + fi) * RS;
                   const T* fr = FR + (size_t)(m.rt.face_off[nq] + lq) * (D == 2 ? 2 : 3);
-                  T xe[D], xk[D], ne_[D], nk_[D];
-                  face_side_point<D, T>(FS, m.nf, f, se, fr, xe, ne_);
-                  face_side_point<D, T>(FS, m.nf, f, 1 - se, fr, xk, nk_);
-                  const T sgn = se == 0 ? T(1) : T(-1);
-                  const T W = fr[D == 2 ? 1 : 2] * FSC[f];
-                  const T sig = FSC[(size_t)m.nf + f];
-                  const T bn = sgn * FSC[(size_t)2 * m.nf + f];
+                  T xe[D], xk[D], ne_[D], nk_[D], sc[3];
+                  hf_point<D, T>(rec, fr, xe, ne_);
+                  hf_point<D, T>(rec + FV, fr, xk, nk_);
+#pragma unroll
+                  for (int j = 0; j < 3; ++j) sc[j] = rec[2 * FV + j];
+                  const T W = fr[D == 2 ? 1 : 2] * sc[0];
+                  const T sig = sc[1];
+                  const T bn = sc[2];
                   const T upw = bn < T(0) ? bn : T(0);
                   const T ae = PTv[g * PT + X + kPtA];
                   const T ak = PTv[g * PT + X + kPtAk];
@@ -1171,7 +1194,7 @@ __global__ void __launch_bounds__(kWarps * 32)
                     for (int i = 0; i < N; ++i) {
                       T v = T(0);
 #pragma unroll
-                      for (int d = 0; d < D; ++d) v += sgn * ne_[d] * Dd[d][i];
+                      for (int d = 0; d < D; ++d) v += ne_[d] * Dd[d][i];
                       dn[i] = v;
                     }
                     store_groups<T, N, TM, TMP, TR>(Ur, Phi);
@@ -1180,7 +1203,7 @@ __global__ void __launch_bounds__(kWarps * 32)
                   auto sink = [&](int j, T phik, const T* dk) {
                     T dn = T(0);
 #pragma unroll
-                    for (int d = 0; d < D; ++d) dn += sgn * nk_[d] * dk[d];
+                    for (int d = 0; d < D; ++d) dn += nk_[d] * dk[d];
                     Vr[j] = W * (T(-0.5) * ak * dn + (upw - sig) * phik);
                     Vr[VS + j] = W * (T(0.5) * ae * phik);
                   };

@@ -357,6 +357,46 @@ __device__ __forceinline__ void sub_geom(const DevMesh& m, int wmask, int k) {
     for (int j = 0; j < SV; ++j) m.sg32[(size_t)j * m.nsub + k] = (float)out[j];
 }
 
+// The two half-face records of face f (hf_rec_vals layout): from side s,
+// its own values first, then the other side's, normals and b . n times sgn_s.
+// Each record is assembled in registers and stored with 16-byte stores.
+template <int D, typename V, typename T>
+__device__ __forceinline__ void write_hf_records(const DevMesh& m, int f, const V (&sv)[2][side_vals(D)], V J, V sigma,
+                                                 V bn, T* hfr) {
+  constexpr int FV = side_vals(D), RS = hf_rec_vals(D);
+  const bool bnd = m.f_e1[f] < 0;
+  const V nq = (V)m.f_nq[f];
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const int h = m.f_hf[(size_t)s * m.nf + f];
+    if (h < 0) continue;
+    const V sg = s == 0 ? V(1) : V(-1);
+    T r[RS];
+#pragma unroll
+    for (int o = 0; o < 2; ++o)
+#pragma unroll
+      for (int j = 0; j < FV; ++j) {
+        const V x = sv[o == 0 ? s : 1 - s][j];
+        r[o * FV + j] = (T)(j >= D * D ? sg * x : x);
+      }
+    r[2 * FV] = (T)J;
+    r[2 * FV + 1] = (T)sigma;
+    r[2 * FV + 2] = (T)(sg * bn);
+    r[2 * FV + 3] = (T)(bnd ? -nq : nq);
+#pragma unroll
+    for (int j = 2 * FV + 4; j < RS; ++j) r[j] = T(0);
+    T* dst = hfr + (size_t)h * RS;
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+      for (int j = 0; j < RS; j += 4)
+        *reinterpret_cast<float4*>(dst + j) = make_float4(r[j], r[j + 1], r[j + 2], r[j + 3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < RS; j += 2) *reinterpret_cast<double2*>(dst + j) = make_double2(r[j], r[j + 1]);
+    }
+  }
+}
+
 template <int D>
 __device__ __forceinline__ void face_geom(const DevMesh& m, int wmask, int f) {
   const int es[2] = {m.f_e0[f], m.f_e1[f]};
@@ -386,9 +426,10 @@ __device__ __forceinline__ void face_geom(const DevMesh& m, int wmask, int f) {
   }
   constexpr int FV = side_vals(D);
   double sigma = 0.0;
+  double sv[2][FV];
   for (int s = 0; s < 2; ++s) {
     const int e = es[s];
-    double out[FV];
+    double* out = sv[s];
     for (int j = 0; j < FV; ++j) out[j] = 0.0;
     if (e >= 0) {
       for (int d = 0; d < D; ++d) {
@@ -402,8 +443,6 @@ __device__ __forceinline__ void face_geom(const DevMesh& m, int wmask, int f) {
     }
     if (wmask & 1)
       for (int j = 0; j < FV; ++j) m.fs64[((size_t)s * FV + j) * m.nf + f] = out[j];
-    if (wmask & 2)
-      for (int j = 0; j < FV; ++j) m.fs32[((size_t)s * FV + j) * m.nf + f] = (float)out[j];
   }
   sigma *= m.pb.c_sigma;
   double bn = 0.0;
@@ -411,8 +450,8 @@ __device__ __forceinline__ void face_geom(const DevMesh& m, int wmask, int f) {
   const double sc[3] = {J, sigma, bn};
   if (wmask & 1)
     for (int j = 0; j < 3; ++j) m.fsc64[(size_t)j * m.nf + f] = sc[j];
-  if (wmask & 2)
-    for (int j = 0; j < 3; ++j) m.fsc32[(size_t)j * m.nf + f] = (float)sc[j];
+  if (wmask & 1) write_hf_records<D>(m, f, sv, J, sigma, bn, m.hfr64);
+  if (wmask & 2) write_hf_records<D>(m, f, sv, J, sigma, bn, m.hfr32);
 }
 
 // sub-simplex records (threads 0 .. nsub-1) and face records (the rest):
@@ -756,9 +795,10 @@ __global__ void face_geom_f32_kernel(DevMesh m) {
   constexpr int FV = side_vals(D);
   const int es[2] = {m.f_e0[f], m.f_e1[f]};
   float sigma = 0.f;
+  float sv[2][FV];
   for (int s = 0; s < 2; ++s) {
     const int e = es[s];
-    float out[FV];
+    float* out = sv[s];
     for (int j = 0; j < FV; ++j) out[j] = 0.f;
     if (e >= 0) {
       for (int d = 0; d < D; ++d) {
@@ -772,13 +812,10 @@ __global__ void face_geom_f32_kernel(DevMesh m) {
       }
       sigma = fmaxf(sigma, m.gx32[(size_t)(3 * D) * m.ne + e]);
     }
-    for (int j = 0; j < FV; ++j) m.fs32[((size_t)s * FV + j) * m.nf + f] = out[j];
   }
   float bn = 0.f;
   for (int d = 0; d < D; ++d) bn = fmaf(m.pb.bf[d], n[d], bn);
-  m.fsc32[f] = J;
-  m.fsc32[(size_t)m.nf + f] = sigma * m.pb.c_sigmaf;
-  m.fsc32[2 * (size_t)m.nf + f] = bn;
+  write_hf_records<D>(m, f, sv, J, sigma * m.pb.c_sigmaf, bn, m.hfr32);
 }
 
 inline int nblk(int n, int t) { return (n + t - 1) / t; }

@@ -189,6 +189,7 @@ struct dg_ctx {
   Tracer tracer;
   bool vol_moments = true;  // volume blocks through Legendre-product moments
   bool vol_exact = false;   // 2D: those moments exact, by Green's theorem along the edges
+  int tiles[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // row-kernel tile variants of untuned passes
   std::vector<LaunchRec> recs;
   SideStreams streams;  // the direct launches' forked streams
   ~dg_ctx() {
@@ -222,6 +223,9 @@ struct dg_graph {
   int occ_cap = 0;
   int concurrent = 0;
   int vol_path = 1;
+  int tiles[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // tile variant per degree
+  int tile_tm[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // its tile edge (0: no group of that degree)
+  int trials = 0;  // passes the autotuner timed
   float tuned_ms = 0.f;
   int launches = 0;
   int ntrace = 0;  // timing events recorded inside the graph (tracing on at capture)
@@ -276,6 +280,7 @@ struct dg_mesh {
   // (kept with the context's volume-path setting it was tuned under)
   int shape_set[4] = {0, 0, 0, 0}, shape_occ[4] = {0, 0, 0, 0}, shape_conc[4] = {0, 0, 0, 0};
   int shape_path[4] = {-1, -1, -1, -1}, shape_vm[4] = {0, 0, 0, 0};
+  int shape_tile[4][9] = {{0}};  // tuned tile variant per degree
   double* X[3] = {nullptr, nullptr, nullptr};
   double* a = nullptr;
   double flops[kKinds][9] = {{0}}, words[kKinds][9] = {{0}};
@@ -481,6 +486,8 @@ struct Plan {
   std::vector<FaceRec> F;
   std::vector<int> f_e0, f_e1, f_v, f_nq, hf_ptr, hf_face, hf_qoff, e_nqf, uvptr, uvidx, elem_perm, if_perm;
   std::vector<int8_t> hf_side, f_flip;
+  std::vector<int> f_hf;     // [2][nf] half-face index of each face side (-1: none)
+  std::vector<int> blk_rec;  // [nnzb][4]: k, first half face of the interface in the row, faces, p_k
   int elem_pstart[9] = {0}, if_pstart[9] = {0};
   int nsub = 0, nf = 0, nint = 0, ni = 0, nhf = 0;
   int64_t nqvol = 0, nqface = 0;
@@ -806,6 +813,7 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P, const int8_t* owned = nullp
   std::vector<int> fill(ne, 0);
   std::vector<int8_t>& hf_side = P.hf_side;
   hf_side.assign(nhf, 0);
+  P.f_hf.assign((size_t)2 * nf, -1);
   for (int f = 0; f < nf; ++f)
     for (int s = 0; s < 2; ++s) {
       const int e = s == 0 ? F[f].e0 : F[f].e1;
@@ -814,7 +822,26 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P, const int8_t* owned = nullp
       hf_face[k] = f;
       hf_side[k] = (int8_t)s;
       hf_qoff[k] = e_nqf[e];
+      P.f_hf[(size_t)s * nf + f] = k;
       e_nqf[e] += dim == 2 ? f_nq[f] : f_nq[f] * f_nq[f];
+    }
+  // off-diagonal block records: an interface's faces are consecutive in the
+  // global face order, hence in the row element's half-face list
+  P.blk_rec.assign((size_t)4 * m->row_ptr[ne], 0);
+  for (int e = 0; e < ne; ++e)
+    for (int bk = m->row_ptr[e]; bk < m->row_ptr[e + 1]; ++bk) {
+      int* r = &P.blk_rec[(size_t)4 * bk];
+      const int it = P.blk_if[bk];
+      if (it < 0) {
+        r[0] = -1;
+        continue;
+      }
+      const int f0 = if_fptr[it];
+      const int hf0 = P.f_hf[(size_t)(if_e0[it] == e ? 0 : 1) * nf + f0];
+      r[0] = m->col[bk];
+      r[1] = hf0;
+      r[2] = if_fptr[it + 1] - f0;
+      r[3] = d->p[m->col[bk]];
     }
 
   // --- unique vertices per element, sub-simplex counts
@@ -1102,6 +1129,12 @@ static int upload_impl(dg_ctx* ctx, const dg_mesh_desc* d, const int8_t* owned, 
   up_i(&dm.hf_face, hf_face);
   if (rc == DG_OK) rc = upload(B, &dm.hf_side, hf_side);
   up_i(&dm.hf_qoff, hf_qoff);
+  up_i(&dm.f_hf, P.f_hf);
+  {
+    const int* p = nullptr;
+    up_i(&p, P.blk_rec);
+    dm.blk_rec = reinterpret_cast<const int4*>(p);
+  }
   up_i(&dm.e_nqf, e_nqf);
   up_i(&dm.if_e0, if_e0);
   up_i(&dm.if_e1, if_e1);
@@ -1141,9 +1174,9 @@ static int upload_impl(dg_ctx* ctx, const dg_mesh_desc* d, const int8_t* owned, 
   alloc_d(&dm.sg64, (size_t)sub_vals(dim) * nsub);
   alloc_f(&dm.sg32, (size_t)sub_vals(dim) * nsub);
   alloc_d(&dm.fs64, (size_t)2 * side_vals(dim) * nf);
-  alloc_f(&dm.fs32, (size_t)2 * side_vals(dim) * nf);
   alloc_d(&dm.fsc64, (size_t)3 * nf);
-  alloc_f(&dm.fsc32, (size_t)3 * nf);
+  alloc_d(&dm.hfr64, (size_t)hf_rec_vals(dim) * nhf);
+  alloc_f(&dm.hfr32, (size_t)hf_rec_vals(dim) * nhf);
   if (rc != DG_OK) {
     delete m;
     return rc;
@@ -1253,7 +1286,8 @@ static int dispatch_rows(const DevMesh& m, int prec, int mode, void* vals, void*
 // unless a path is given (their elements have only 28 points each)
 static int run_assembly(dg_ctx* ctx, const dg_mesh* mesh, int prec, int mode, void* vals, void* rhs, bool iface,
                         bool reset = true, cudaStream_t st = nullptr, bool use_ctx_stream = true, int occ_cap = 0,
-                        bool concurrent = false, int vpath = -1, SideStreams* ss = nullptr) {
+                        bool concurrent = false, int vpath = -1, SideStreams* ss = nullptr,
+                        const int* tiles = nullptr) {
   if (!ctx || !mesh) return fail(DG_ERR_ARG, "null context or mesh");
   if (prec < DG_PREC_FP64 || prec > DG_PREC_TF32X3) return fail(DG_ERR_ARG, "unknown precision %d", prec);
   if ((mode & (kModeVol | kModeFace)) && !vals) return fail(DG_ERR_ARG, "vals is null");
@@ -1267,7 +1301,10 @@ static int run_assembly(dg_ctx* ctx, const dg_mesh* mesh, int prec, int mode, vo
   lo.occ_cap = occ_cap;
   lo.vol_moments = vpath >= 0 ? vpath >= 1 : ctx->vol_moments && !mesh->dm.lq_ok;
   lo.vol_exact = lo.vol_moments && (vpath >= 0 ? vpath == 2 : ctx->vol_exact);
-  for (int p = 0; p < 9; ++p) lo.pst[p] = st;
+  for (int p = 0; p < 9; ++p) {
+    lo.pst[p] = st;
+    lo.tile[p] = tiles ? tiles[p] : ctx->tiles[p];
+  }
   if (!ss) ss = &ctx->streams;
   if (concurrent) {
     DG_CUDA_TRY(ss->ensure());
@@ -1314,11 +1351,14 @@ int dg_assemble(dg_ctx* ctx, const dg_mesh* mesh, int prec, void* vals, void* rh
 // The per-step launch shape: the autotuned one where dg_graph_create has
 // tuned this precision on this mesh, else concurrent degree groups when the
 // mesh has more than one.
-static void step_shape(const dg_ctx* ctx, const dg_mesh* mesh, int prec, int* occ, bool* conc, int* path) {
+static void step_shape(const dg_ctx* ctx, const dg_mesh* mesh, int prec, int* occ, bool* conc, int* path,
+                       const int** tiles) {
+  *tiles = ctx->tiles;
   if (mesh->shape_set[prec] && mesh->shape_vm[prec] == ctx_vol_path(ctx)) {
     *occ = mesh->shape_occ[prec];
     *conc = mesh->shape_conc[prec] != 0;
     *path = mesh->shape_path[prec];
+    *tiles = mesh->shape_tile[prec];
     return;
   }
   int groups = 0;
@@ -1353,10 +1393,11 @@ int dg_assemble_host(dg_ctx* ctx, dg_mesh* mesh, int prec, const double* x, cons
   DG_CUDA_TRY(cudaGetLastError());
   int occ = 0, path = -1;
   bool conc = false;
-  step_shape(ctx, mesh, prec, &occ, &conc, &path);
+  const int* tiles = nullptr;
+  step_shape(ctx, mesh, prec, &occ, &conc, &path, &tiles);
   const int mode = kModeVol | kModeFace | (rhs_host ? kModeRhs : 0);
   int rc = run_assembly(ctx, mesh, prec, mode, mesh->h_vals, rhs_host ? mesh->h_rhs : nullptr, true, false, nullptr,
-                        true, occ, conc, path);
+                        true, occ, conc, path, nullptr, tiles);
   if (rc != DG_OK) return rc;
   // one copy each: several parts on parallel streams measured no faster
   DG_CUDA_TRY(cudaMemcpyAsync(vals_host, mesh->h_vals, es * mesh->info.nvals, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1376,9 +1417,10 @@ int dg_assemble_step(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs
   DG_CUDA_TRY(cudaGetLastError());
   int occ = 0, path = -1;
   bool conc = false;
-  step_shape(ctx, mesh, prec, &occ, &conc, &path);
+  const int* tiles = nullptr;
+  step_shape(ctx, mesh, prec, &occ, &conc, &path, &tiles);
   const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
-  return run_assembly(ctx, mesh, prec, mode, vals, rhs, true, false, nullptr, true, occ, conc, path);
+  return run_assembly(ctx, mesh, prec, mode, vals, rhs, true, false, nullptr, true, occ, conc, path, nullptr, tiles);
 }
 
 // ---------------------------------------------------------------------------
@@ -1939,11 +1981,11 @@ int dg_batch_offsets(const dg_mesh* mesh, int* nmesh, int* elem_off, int64_t* va
 
 // One whole pass (geometry + row kernels) on stream st with a launch shape.
 static int issue_pass(dg_ctx* ctx, dg_mesh* mesh, int prec, int gmask, void* vals, void* rhs, cudaStream_t st,
-                      int occ_cap, bool concurrent, int vpath, SideStreams* ss) {
+                      int occ_cap, bool concurrent, int vpath, SideStreams* ss, const int* tiles) {
   int n = launch_geometry(mesh->dm, st, nullptr, gmask);
   DG_CUDA_TRY(cudaGetLastError());
   const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
-  int rc = run_assembly(ctx, mesh, prec, mode, vals, rhs, true, true, st, false, occ_cap, concurrent, vpath, ss);
+  int rc = run_assembly(ctx, mesh, prec, mode, vals, rhs, true, true, st, false, occ_cap, concurrent, vpath, ss, tiles);
   if (rc != DG_OK) return rc;
   ctx->last_launches += n;
   return DG_OK;
@@ -1970,6 +2012,7 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
   const int mpath = ctx->vol_exact ? 2 : 1;  // the context's moment path
   const int def_path = ctx->vol_moments && !mesh->dm.lq_ok ? mpath : 0;
   int best_occ = 0, best_conc = 0, best_path = def_path;
+  int best_tiles[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   float best = 1e30f;
   if (autotune) {
     const int occs[3] = {0, 1, 2};
@@ -1977,49 +2020,77 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    for (int pi = 0; pi < npath; ++pi)
-    for (int conc = 0; conc < 2; ++conc)
-      for (int oi = 0; oi < 3; ++oi) {
-        const int vpath = npath == 2 ? (pi == 0 ? mpath : 0) : 0;
-        float t = 1e30f;
-        for (int rep = 0; rep < 4; ++rep) {
-          cudaEventRecord(e0, g->stream);
-          int rc = issue_pass(ctx, mesh, prec, gmask, vals, rhs, g->stream, occs[oi], conc != 0, vpath, &g->streams);
-          if (rc != DG_OK) {
-            ctx->tracer.on = was_on;
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-            return bail(rc);
+    // one candidate: best of 3 timed passes after a warm-up pass
+    auto time_shape = [&](int occ, int conc, int vpath, const int* tiles, float* out) -> int {
+      float t = 1e30f;
+      for (int rep = 0; rep < 4; ++rep) {
+        cudaEventRecord(e0, g->stream);
+        int rc = issue_pass(ctx, mesh, prec, gmask, vals, rhs, g->stream, occ, conc != 0, vpath, &g->streams, tiles);
+        if (rc != DG_OK) return rc;
+        cudaEventRecord(e1, g->stream);
+        if (cudaEventSynchronize(e1) != cudaSuccess) return fail(DG_ERR_CUDA, "dg_graph_create: tuning pass failed");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0 && ms < t) t = ms;
+      }
+      ++g->trials;
+      *out = t;
+      return DG_OK;
+    };
+    int rc = DG_OK;
+    // launch shape: residency cap x serial / concurrent degree groups x volume path
+    for (int pi = 0; rc == DG_OK && pi < npath; ++pi)
+      for (int conc = 0; rc == DG_OK && conc < 2; ++conc)
+        for (int oi = 0; rc == DG_OK && oi < 3; ++oi) {
+          const int vpath = npath == 2 ? (pi == 0 ? mpath : 0) : 0;
+          float t = 0.f;
+          rc = time_shape(occs[oi], conc, vpath, best_tiles, &t);
+          if (rc == DG_OK && t < best) {
+            best = t;
+            best_occ = occs[oi];
+            best_conc = conc;
+            best_path = vpath;
           }
-          cudaEventRecord(e1, g->stream);
-          if (cudaEventSynchronize(e1) != cudaSuccess) {
-            ctx->tracer.on = was_on;
-            return bail(fail(DG_ERR_CUDA, "dg_graph_create: tuning pass failed"));
-          }
-          float ms = 0.f;
-          cudaEventElapsedTime(&ms, e0, e1);
-          if (rep > 0 && ms < t) t = ms;
         }
-        if (t < best) {
+    // tiles: for each degree present, each other register-tile variant of
+    // its row kernel against the best so far (one pass of coordinate descent)
+    for (int p = 1; rc == DG_OK && p <= 8; ++p) {
+      if (mesh->dm.elem_pstart[p + 1] <= mesh->dm.elem_pstart[p]) continue;
+      for (int v = 1; rc == DG_OK && row_tile_tm(mesh->dm.dim, p, prec, v) > 0; ++v) {
+        int cand[9];
+        std::copy(best_tiles, best_tiles + 9, cand);
+        cand[p] = v;
+        float t = 0.f;
+        rc = time_shape(best_occ, best_conc, best_path, cand, &t);
+        if (rc == DG_OK && t < best) {
           best = t;
-          best_occ = occs[oi];
-          best_conc = conc;
-          best_path = vpath;
+          best_tiles[p] = v;
         }
       }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    if (rc != DG_OK) {
+      ctx->tracer.on = was_on;
+      return bail(rc);
+    }
   }
   g->occ_cap = best_occ;
   g->concurrent = best_conc;
   g->vol_path = best_path;
   g->tuned_ms = autotune ? best : 0.f;
+  for (int p = 0; p < 9; ++p) {
+    g->tiles[p] = best_tiles[p];
+    const bool present = p >= 1 && p <= 7 && mesh->dm.elem_pstart[p + 1] > mesh->dm.elem_pstart[p];
+    g->tile_tm[p] = present ? row_tile_tm(mesh->dm.dim, p, prec, best_tiles[p]) : 0;
+  }
   if (autotune) {
     mesh->shape_set[prec] = 1;
     mesh->shape_occ[prec] = best_occ;
     mesh->shape_conc[prec] = best_conc;
     mesh->shape_path[prec] = best_path;
     mesh->shape_vm[prec] = ctx_vol_path(ctx);
+    std::copy(best_tiles, best_tiles + 9, mesh->shape_tile[prec]);
   }
   // with timing enabled the per-launch events are recorded into the graph
   ctx->tracer.on = was_on;
@@ -2031,7 +2102,7 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
     const int gl = launch_geometry(mesh->dm, g->stream, &ctx->tracer, gmask);
     const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
     rc = run_assembly(ctx, mesh, prec, mode, vals, rhs, true, false, g->stream, false, g->occ_cap, g->concurrent != 0,
-                      g->vol_path, &g->streams);
+                      g->vol_path, &g->streams, g->tiles);
     ctx->last_launches += gl;
   }
   cudaError_t ce = cudaStreamEndCapture(g->stream, &g->graph);
@@ -2080,11 +2151,13 @@ int dg_assemble_batch(dg_ctx* ctx, dg_mesh* const* meshes, int nmesh, int prec, 
     launches += launch_geometry(mesh->dm, br, nullptr, gmask);
     int occ = 0, path = -1;
     bool conc = false;
-    step_shape(ctx, mesh, base, &occ, &conc, &path);
+    const int* tiles = nullptr;
+    step_shape(ctx, mesh, base, &occ, &conc, &path, &tiles);
     const int mode = kModeVol | kModeFace | (rhs && rhs[k] ? kModeRhs : 0);
     // a member's degree groups stay on its branch stream (serial): the
     // members themselves are the concurrency
-    rc = run_assembly(ctx, mesh, base, mode, vals[k], rhs ? rhs[k] : nullptr, true, true, br, false, occ, false, path);
+    rc = run_assembly(ctx, mesh, base, mode, vals[k], rhs ? rhs[k] : nullptr, true, true, br, false, occ, false, path,
+                      nullptr, tiles);
     launches += ctx->last_launches;
   }
   for (int i = 0; rc == DG_OK && i < 4; ++i) {
@@ -2124,6 +2197,13 @@ int dg_graph_info(const dg_graph* g, int* occ_cap, int* concurrent, float* tuned
   if (concurrent) *concurrent = g->concurrent;
   if (tuned_ms) *tuned_ms = g->tuned_ms;
   if (launches) *launches = g->launches;
+  return DG_OK;
+}
+
+int dg_graph_tiles(const dg_graph* g, int* tile_tm, int* trials) {
+  if (!g) return fail(DG_ERR_ARG, "dg_graph_tiles: null graph");
+  if (tile_tm) std::copy(g->tile_tm, g->tile_tm + 9, tile_tm);
+  if (trials) *trials = g->trials;
   return DG_OK;
 }
 
@@ -2346,6 +2426,16 @@ int dg_kernel_stats(dg_ctx* ctx, dg_kernel_stat* out, int cap) {
     return n + 1;
   }
   return n;
+}
+
+int dg_set_tile_variants(dg_ctx* ctx, const int* variants) {
+  if (!ctx) return fail(DG_ERR_ARG, "dg_set_tile_variants: null context");
+  for (int p = 0; p < 9; ++p) {
+    const int v = variants ? variants[p] : 0;
+    if (v < 0 || v > 2) return fail(DG_ERR_ARG, "dg_set_tile_variants: variant %d of degree %d outside 0..2", v, p);
+  }
+  for (int p = 0; p < 9; ++p) ctx->tiles[p] = variants ? variants[p] : 0;
+  return DG_OK;
 }
 
 int dg_set_volume_path(dg_ctx* ctx, int path) {

@@ -25,6 +25,16 @@ __host__ __device__ constexpr int sub_vals(int dim) { return dim == 2 ? 7 : 13; 
 __host__ __device__ constexpr int side_vals(int dim) { return dim == 2 ? 6 : 12; }
 // values per element record: lo, L, 1/L (dim each) and R
 __host__ __device__ constexpr int elem_vals(int dim) { return 3 * dim + 1; }
+// values per half-face record (face f seen from side s, element e_s), one
+// contiguous record per half face in the element's half-face order:
+//   [0, FV)      side s's values (side_vals layout), normal part times sgn_s
+//   [FV, 2 FV)   the other side's values (zero on the boundary), normal part
+//                times sgn_s
+//   2 FV: J, 2 FV + 1: sigma, 2 FV + 2: sgn_s b . n0, 2 FV + 3: nq (points
+//   per direction), negated on a boundary face
+// with sgn_0 = +1, sgn_1 = -1, so every normal in the record points out of
+// e_s.  2D 16 values, 3D 28 padded to 32 (one or two 64-byte lines in FP32).
+__host__ __device__ constexpr int hf_rec_vals(int dim) { return dim == 2 ? 16 : 32; }
 
 __host__ __device__ constexpr int nbasis(int dim, int p) {
   return dim == 2 ? (p + 1) * (p + 2) / 2 : (p + 1) * (p + 2) * (p + 3) / 6;
@@ -116,11 +126,14 @@ struct DevMesh {
   const int* f_e1;  // -1 on the boundary
   const int* f_v;   // [nf][dim] vertex ids in e0's order (2D: along e0's CCW loop; 3D: e0's tetrahedron)
   const int8_t* f_flip;  // 3D: 1 if (v1-v0) x (v2-v0) points into e0
-  double* fs64;     // [2][side_vals][nf]
-  float* fs32;
+  double* fs64;     // [2][side_vals][nf] (FP64 only: the variable-coefficient path)
   double* fsc64;  // [3][nf]: J (2D |F|, 3D 2|F|), sigma, b.n
-  float* fsc32;
   int* f_nq;  // points per direction on the face: max(p0, p1) + 1
+  const int* f_hf;  // [2][nf] half-face index of face f on side s (-1: none)
+  // half-face records (hf_rec_vals layout), [nhf][hf_rec_vals], written by
+  // the face geometry kernels
+  double* hfr64;
+  float* hfr32;
   // element -> faces (half faces), fixed order
   const int* hf_ptr;   // [ne+1]
   const int* hf_face;  // [nhf]
@@ -137,6 +150,10 @@ struct DevMesh {
   const int* row_ptr;  // [ne+1]
   const int* col;      // [nnzb]
   const int* blk_if;   // [nnzb] interface of an off-diagonal block, -1 on the diagonal
+  // [nnzb] per off-diagonal block (r, k): k, the first of the interface's
+  // half faces in r's half-face list, the interface's faces, p_k (diagonal
+  // blocks: -1, 0, 0, 0)
+  const int4* blk_rec;
   const int64_t* blk_off;
   const int* diag_blk;
   const int64_t* dof_off;
@@ -209,8 +226,13 @@ struct LaunchOpts {
   int occ_cap = 0;
   bool vol_moments = true;  // volume blocks through Legendre-product moments where supported
   bool vol_exact = false;   // 2D: those moments exact, from the element's edges
+  int tile[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // register-tile variant of each degree's row kernel
   cudaStream_t pst[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
+
+// Edge TM of the register tiles of tile variant v of the (dim, p) row kernel
+// in precision prec (DG_PREC_*); 0 when there is no such variant.
+int row_tile_tm(int dim, int p, int prec, int v);
 
 int launch_row2d_f64(const DevMesh& m, int mode, double* vals, double* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);
 int launch_row2d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);

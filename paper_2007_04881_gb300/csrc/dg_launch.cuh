@@ -21,6 +21,47 @@ inline int resident_grid(K kernel, size_t smem, int sm_count, int want_blocks, i
   return want_blocks < g ? want_blocks : g;
 }
 
+// The row-kernel launch of one degree group with tile variant V (kind: the
+// tracer's accounting kind, 0 whole rows, 1 faces next to the moment launch).
+template <int D, int P, typename T, int V>
+int launch_row_tile(const DevMesh& m, int mode, T* vals, T* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr,
+                    int kind) {
+  const int count = m.elem_pstart[P + 1] - m.elem_pstart[P];
+  cudaStream_t st = lo.pst[P];
+  if (tr && tr->on) {
+    char name[48];
+    snprintf(name, sizeof name, "row%dd_p%d_%s", D, P, sizeof(T) == 8 ? "f64" : "f32");
+    tr->begin(name, kind, P, sizeof(T), st);
+  }
+  if constexpr (TileCfg<D, P, T, V>::TPE == 1) {
+    // one element per thread, no staging
+    auto k = row_lane_kernel<D, P, T>;
+    const int grid = resident_grid(k, 0, sm_count, ((count + 31) / 32 * 64 + kWarps * 32 - 1) / (kWarps * 32), lo.occ_cap);
+    k<<<grid, kWarps * 32, 0, st>>>(m, mode, vals, rhs);
+  } else {
+    using SM = RowSmem<D, P, T, V>;
+    constexpr int G = TileCfg<D, P, T, V>::G;
+    static_assert(SM::total(kWarps, nbasis(D, D == 2 ? kPMax2 : kPMax3)) <= 227 * 1024,
+                  "row kernel shared memory exceeds 227 KB");
+    const int ntiles = (count + G - 1) / G;
+    const size_t smem = SM::total(kWarps, m.nmax);
+    auto k = row_kernel<D, P, T, V>;
+    const int grid = resident_grid(k, smem, sm_count, (ntiles + kWarps - 1) / kWarps, lo.occ_cap);
+    k<<<grid, kWarps * 32, smem, st>>>(m, mode, vals, rhs);
+  }
+  if (tr && tr->on) tr->end(st);
+  return 1;
+}
+
+// Tile variants beyond the default, compiled in their own translation units
+// (dg_row*_tiles*.cu) so that the build runs them in parallel.
+#define DG_ROW_TILE_VARIANTS(X)                                                                               \
+  X(2, 3, float, 1) X(2, 4, float, 1) X(2, 4, float, 2) X(2, 5, float, 1) X(2, 5, float, 2) X(2, 6, float, 1) \
+  X(3, 2, float, 1) X(3, 3, float, 1) X(3, 3, float, 2)
+#define DG_EXTERN_ROW_TILE(D, P, T, V) \
+  extern template int launch_row_tile<D, P, T, V>(const DevMesh&, int, T*, T*, int, const LaunchOpts&, Tracer*, int);
+DG_ROW_TILE_VARIANTS(DG_EXTERN_ROW_TILE)
+
 template <int D, int P, typename T>
 inline int launch_row_p(const DevMesh& m, int mode, T* vals, T* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr) {
   const int count = m.elem_pstart[P + 1] - m.elem_pstart[P];
@@ -51,29 +92,13 @@ inline int launch_row_p(const DevMesh& m, int mode, T* vals, T* rhs, int sm_coun
       kind = 1;
     }
   }
-  if (tr && tr->on) {
-    char name[48];
-    snprintf(name, sizeof name, "row%dd_p%d_%s", D, P, tn);
-    tr->begin(name, kind, P, sizeof(T), st);
-  }
-  if constexpr (TileCfg<D, P, T>::TPE == 1) {
-    // one element per thread, no staging
-    auto k = row_lane_kernel<D, P, T>;
-    const int grid = resident_grid(k, 0, sm_count, ((count + 31) / 32 * 64 + kWarps * 32 - 1) / (kWarps * 32), lo.occ_cap);
-    k<<<grid, kWarps * 32, 0, st>>>(m, mode, vals, rhs);
-  } else {
-    using SM = RowSmem<D, P, T>;
-    constexpr int G = TileCfg<D, P, T>::G;
-    static_assert(SM::total(kWarps, nbasis(D, D == 2 ? kPMax2 : kPMax3)) <= 227 * 1024,
-                  "row kernel shared memory exceeds 227 KB");
-    const int ntiles = (count + G - 1) / G;
-    const size_t smem = SM::total(kWarps, m.nmax);
-    auto k = row_kernel<D, P, T>;
-    const int grid = resident_grid(k, smem, sm_count, (ntiles + kWarps - 1) / kWarps, lo.occ_cap);
-    k<<<grid, kWarps * 32, smem, st>>>(m, mode, vals, rhs);
-  }
-  if (tr && tr->on) tr->end(st);
-  return n + 1;
+  constexpr int NV = tile_variants<D, P, T>();
+  const int v = lo.tile[P] < NV ? lo.tile[P] : 0;
+  if constexpr (NV > 2)
+    if (v == 2) return n + launch_row_tile<D, P, T, 2>(m, mode, vals, rhs, sm_count, lo, tr, kind);
+  if constexpr (NV > 1)
+    if (v == 1) return n + launch_row_tile<D, P, T, 1>(m, mode, vals, rhs, sm_count, lo, tr, kind);
+  return n + launch_row_tile<D, P, T, 0>(m, mode, vals, rhs, sm_count, lo, tr, kind);
 }
 
 }  // namespace dg

@@ -311,9 +311,9 @@ __global__ void __launch_bounds__(kWarps * 32, MmaCfg<D, P, K>::MINB)
   __syncthreads();
 
   const float* SG = m.sg32;
-  const float* FS = m.fs32;
-  const float* FSC = m.fsc32;
+  const float* HFR = m.hfr32;
   const float* FR = m.rt.face32;
+  constexpr int FV = side_vals(D), RS = hf_rec_vals(D);
   const float* EG = m.eg32;
 
   const bool mat_vol = mode & kModeVol, mat_face = mode & kModeFace, do_rhs = mode & kModeRhs;
@@ -508,18 +508,20 @@ __global__ void __launch_bounds__(kWarps * 32, MmaCfg<D, P, K>::MINB)
                 hi_ = mid - 1;
             }
             const int hf = lo_;
-            const int f = m.hf_face[hf];
-            const int s = m.hf_side[hf];
-            const int nq = m.f_nq[f];
+            // the half face's record: own side, then J, sigma, b.n, nq (signed)
+            const float* rec = HFR + (size_t)hf * RS;
+            float sc[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) sc[j] = rec[2 * FV + j];
+            const bool bnd = sc[3] < 0.f;
+            const int nq = (int)(bnd ? -sc[3] : sc[3]);
             const int lq = qv - m.hf_qoff[hf];
             const float* fr = FR + (size_t)(m.rt.face_off[nq] + lq) * (D == 2 ? 2 : 3);
             float xi[D], np[D];
-            face_side_point<D, float>(FS, m.nf, f, s, fr, xi, np);
-            const float sgn = s == 0 ? 1.f : -1.f;
-            const float W = fr[D == 2 ? 1 : 2] * FSC[f];
-            const float sig = FSC[(size_t)m.nf + f];
-            const float bn = sgn * FSC[(size_t)2 * m.nf + f];
-            const bool bnd = m.f_e1[f] < 0;
+            hf_point<D, float>(rec, fr, xi, np);
+            const float W = fr[D == 2 ? 1 : 2] * sc[0];
+            const float sig = sc[1];
+            const float bn = sc[2];
             const float kap = bnd ? 1.f : 0.5f;
             const float a = pt[X + kPtA];
             const float upw = bn < 0.f ? bn : 0.f;
@@ -529,7 +531,7 @@ __global__ void __launch_bounds__(kWarps * 32, MmaCfg<D, P, K>::MINB)
             for (int i = 0; i < N; ++i) {
               float v = 0.f;
 #pragma unroll
-              for (int d = 0; d < D; ++d) v += sgn * np[d] * Dd[d][i];
+              for (int d = 0; d < D; ++d) v += np[d] * Dd[d][i];
               dn[i] = v;
               V0[i] = W * (-kap * a * v + (sig - upw) * Phi[i]);
               V1[i] = W * (-kap * a * Phi[i]);
@@ -605,21 +607,18 @@ __global__ void __launch_bounds__(kWarps * 32, MmaCfg<D, P, K>::MINB)
         if (lane < G) {
           int* pi = PIv + lane * PI;
           if (lane < gcount && sl < pi[kPiNslot]) {
-            const int e = pi[kPiElem];
             const int bk = pi[kPiRow0] + sl + (sl >= pi[kPiDpos] ? 1 : 0);
-            const int it = m.blk_if[bk];
-            const int k = m.col[bk];
-            const int pk = m.p[k];
-            const int f0 = m.if_fptr[it];
-            const int nq = m.f_nq[f0];
+            const int4 br = m.blk_rec[bk];  // neighbour, first half face, faces, neighbour degree
+            const int k = br.x, pk = br.w;
+            const int nq = (P > pk ? P : pk) + 1;
             const int qf = D == 2 ? nq : nq * nq;
             pi[kPiSBlk] = bk;
-            pi[kPiSSide] = m.if_e0[it] == e ? 0 : 1;
+            pi[kPiSSide] = nq;
             pi[kPiSPk] = pk;
             pi[kPiSNk] = nbasis(D, pk);
-            pi[kPiSF0] = f0;
+            pi[kPiSF0] = br.y;
             pi[kPiSQF] = qf;
-            pi[kPiSNpts] = (m.if_fptr[it + 1] - f0) * qf;
+            pi[kPiSNpts] = br.z * qf;
             PTv[lane * PT + X + kPtAk] = float(m.a[k]);
             PTv[lane * PT + X + kPtRk] = EG[(size_t)(3 * D) * m.ne + k];
           } else {
@@ -657,17 +656,17 @@ __global__ void __launch_bounds__(kWarps * 32, MmaCfg<D, P, K>::MINB)
               zero_row<K, SV, NW>(Vg, VPL, C + c);
               if (g < gcount && qv < pi[kPiSNpts] && col0 < pi[kPiSNk]) {
                 const int qf = pi[kPiSQF];
-                const int f = pi[kPiSF0] + qv / qf, lq = qv - (qv / qf) * qf;
-                const int se = pi[kPiSSide];
-                const int nq = m.f_nq[f];
+                const int fi = qv / qf, lq = qv - fi * qf;
+                const int nq = pi[kPiSSide];
+                // the half face's record: both sides, then J, sigma, b.n
+                const float* rec = HFR + (size_t)(pi[kPiSF0] + fi) * RS;
                 const float* fr = FR + (size_t)(m.rt.face_off[nq] + lq) * (D == 2 ? 2 : 3);
                 float xe[D], xk[D], ne_[D], nk_[D];
-                face_side_point<D, float>(FS, m.nf, f, se, fr, xe, ne_);
-                face_side_point<D, float>(FS, m.nf, f, 1 - se, fr, xk, nk_);
-                const float sgn = se == 0 ? 1.f : -1.f;
-                const float W = fr[D == 2 ? 1 : 2] * FSC[f];
-                const float sig = FSC[(size_t)m.nf + f];
-                const float bn = sgn * FSC[(size_t)2 * m.nf + f];
+                hf_point<D, float>(rec, fr, xe, ne_);
+                hf_point<D, float>(rec + FV, fr, xk, nk_);
+                const float W = fr[D == 2 ? 1 : 2] * rec[2 * FV];
+                const float sig = rec[2 * FV + 1];
+                const float bn = rec[2 * FV + 2];
                 const float upw = bn < 0.f ? bn : 0.f;
                 const float ae = PTv[g * PT + X + kPtA];
                 const float ak = PTv[g * PT + X + kPtAk];
@@ -678,7 +677,7 @@ __global__ void __launch_bounds__(kWarps * 32, MmaCfg<D, P, K>::MINB)
                   for (int i = 0; i < N; ++i) {
                     float v = 0.f;
 #pragma unroll
-                    for (int d = 0; d < D; ++d) v += sgn * ne_[d] * Dd[d][i];
+                    for (int d = 0; d < D; ++d) v += ne_[d] * Dd[d][i];
                     dn[i] = v;
                   }
                   put_row<K, SU, ZU, 16 * MT, N>(Ug, UPL, c, Phi, 0.f);
@@ -689,7 +688,7 @@ __global__ void __launch_bounds__(kWarps * 32, MmaCfg<D, P, K>::MINB)
                   if (jj < 0 || jj >= NW) return;
                   float dnk = 0.f;
 #pragma unroll
-                  for (int d = 0; d < D; ++d) dnk += sgn * nk_[d] * dk[d];
+                  for (int d = 0; d < D; ++d) dnk += nk_[d] * dk[d];
                   put_one<K, SV, ZV>(Vg, VPL, c, jj, W * (-0.5f * ak * dnk + (upw - sig) * phik));
                   put_one<K, SV, ZV>(Vg, VPL, C + c, jj, W * (0.5f * ae * phik));
                 };

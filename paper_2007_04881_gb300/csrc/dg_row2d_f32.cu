@@ -14,4 +14,30 @@ int launch_row2d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm
   return n;
 }
 
+namespace {
+template <int D, int P, typename T>
+int tm_of(int v) {
+  return v < tile_variants<D, P, T>() ? tile_tm<D, P, T>(v) : 0;
+}
+template <int D, typename T>
+int tm_dim(int p, int v) {
+  switch (p) {
+    case 1: return tm_of<D, 1, T>(v);
+    case 2: return tm_of<D, 2, T>(v);
+    case 3: return tm_of<D, 3, T>(v);
+    case 4: return tm_of<D, 4, T>(v);
+    case 5: if constexpr (D == 2) return tm_of<D, 5, T>(v); return 0;
+    case 6: if constexpr (D == 2) return tm_of<D, 6, T>(v); return 0;
+    default: return 0;
+  }
+}
+}  // namespace
+
+// the tensor-core forms have one contraction layout per degree
+int row_tile_tm(int dim, int p, int prec, int v) {
+  if (prec == 0) return dim == 2 ? tm_dim<2, double>(p, v) : tm_dim<3, double>(p, v);
+  if (prec == 1) return dim == 2 ? tm_dim<2, float>(p, v) : tm_dim<3, float>(p, v);
+  return v == 0 ? -1 : 0;
+}
+
 }  // namespace dg

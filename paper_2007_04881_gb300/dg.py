@@ -123,6 +123,8 @@ def load() -> C.CDLL:
     lib.dg_graph_launch.argtypes = [V, V]
     lib.dg_graph_info.argtypes = [V, V, V, V, V, V]
     lib.dg_graph_free.argtypes = [V]
+    lib.dg_graph_tiles.argtypes = [V, V, V]
+    lib.dg_set_tile_variants.argtypes = [V, V]
     lib.dg_volume_noalloc.argtypes = [V, C.c_int, C.c_int, C.c_int, C.c_int, V, V, C.c_int, C.c_int, V, V, V,
                                       C.c_double, C.c_double, C.c_double, V, V]
     lib.dg_quad_prepare.argtypes = [V, V]
@@ -173,7 +175,8 @@ EXPORTS = (
     "dg_mlp_get_state", "dg_mlp_set_state", "dg_mlp_forward", "dg_mlp_grad", "dg_mlp_train_step",
     "dg_partition", "dg_mesh_upload_part", "dg_part_map", "dg_part_check", "dg_set_volume_path",
     "dg_slab_offsets", "dg_slab_layout", "dg_assemble_slab", "dg_slab_trace", "dg_assemble_varcoef",
-    "dg_mlp_save", "dg_mlp_load", "dg_quad_learn", "dg_assemble_batch",
+    "dg_mlp_save", "dg_mlp_load", "dg_quad_learn", "dg_assemble_batch", "dg_graph_tiles",
+    "dg_set_tile_variants",
 )
 
 
@@ -235,6 +238,11 @@ class Context:
     def dg_set_volume_path(self, path: int):
         """1: volume blocks through Legendre-product moments (default); 0: per-point contraction."""
         _check(load().dg_set_volume_path(self._h, int(path)))
+
+    def dg_set_tile_variants(self, variants=None):
+        """Row-kernel tile variant per degree (9 ints, or None for the defaults)."""
+        v = None if variants is None else np.ascontiguousarray(variants, dtype=np.int32)
+        _check(load().dg_set_tile_variants(self._h, _vp(v)))
 
     def launches(self) -> int:
         return load().dg_last_launch_count(self._h)
@@ -618,8 +626,12 @@ class Graph:
     def dg_graph_info(self):
         occ, conc, ms, nl, vp = C.c_int(), C.c_int(), C.c_float(), C.c_int(), C.c_int()
         _check(load().dg_graph_info(self._h, C.byref(occ), C.byref(conc), C.byref(ms), C.byref(nl), C.byref(vp)))
+        tm = np.zeros(9, np.int32)
+        tr = C.c_int()
+        _check(load().dg_graph_tiles(self._h, _vp(tm), C.byref(tr)))
         return {"occ_cap": occ.value, "concurrent": bool(conc.value), "tuned_ms": ms.value, "launches": nl.value,
-                "volume_path": {0: "per-point", 1: "moments", 2: "exact-moments"}.get(vp.value, "per-point")}
+                "volume_path": {0: "per-point", 1: "moments", 2: "exact-moments"}.get(vp.value, "per-point"),
+                "tile_tm": {f"p{p}": int(tm[p]) for p in range(9) if tm[p] != 0}, "tuner_trials": tr.value}
 
     def close(self):
         if getattr(self, "_h", None):

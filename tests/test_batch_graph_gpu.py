@@ -116,3 +116,52 @@ def test_assemble_batch_equals_member_steps(ctx, prec, use_graph):
         assert np.array_equal(vals[k].double().cpu().numpy(), v), k
         if rhs[k] is not None:
             assert np.array_equal(rhs[k].double().cpu().numpy(), r), k
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_tile_variants_bitwise_equal(ctx, dim):
+    """Every register-tile variant of the FP32 row kernels (the autotuner's
+    candidates) sums each entry over the same points in the same order: the
+    matrix and load vector are bitwise those of the default tiles, on the
+    moment and on the per-point volume path."""
+    import torch
+
+    if dim == 2:
+        w = configs.small2d(500, 91, 1, 6, b=(1.0, 0.5), c=1.0)
+    else:
+        w = configs.small3d(6, 20, 92, 2, 3)
+    m = dg.Mesh(ctx, w.mesh, w.p, w.a, dg_problem(w))
+    try:
+        for path in (1, 0):
+            ctx.dg_set_volume_path(path)
+            ctx.dg_set_tile_variants(None)
+            v0, r0 = _assemble(ctx, m, dg.DG_PREC_FP32)
+            for var in (1, 2):
+                ctx.dg_set_tile_variants([var] * 9)
+                v, r = _assemble(ctx, m, dg.DG_PREC_FP32)
+                assert np.array_equal(v, v0), (path, var)
+                assert np.array_equal(r, r0), (path, var)
+    finally:
+        ctx.dg_set_volume_path(1)
+        ctx.dg_set_tile_variants(None)
+
+
+def test_autotuner_records_tiles(ctx):
+    import torch
+
+    w = configs.small2d(600, 93, 1, 5, b=(1.0, 0.5), c=1.0)
+    m = dg.Mesh(ctx, w.mesh, w.p, w.a, dg_problem(w))
+    v_ref, r_ref = _assemble(ctx, m, dg.DG_PREC_FP32)
+    v = torch.zeros(m.nvals, dtype=torch.float32, device="cuda")
+    r = torch.zeros(m.ndofs, dtype=torch.float32, device="cuda")
+    g = m.dg_graph_create(dg.DG_PREC_FP32, v, r, autotune=True)
+    info = g.dg_graph_info()
+    present = sorted(set(int(q) for q in w.p))
+    assert sorted(int(k[1:]) for k in info["tile_tm"]) == present
+    assert info["tile_tm"]["p4"] in (8, 5, 4) and info["tile_tm"]["p3"] in (5, 4)
+    assert info["tuner_trials"] >= 12 + 1 + 2 + 2
+    g.dg_graph_launch()
+    ctx.dg_sync()
+    assert np.array_equal(v.double().cpu().numpy(), v_ref)
+    assert np.array_equal(r.double().cpu().numpy(), r_ref)
+    g.close()
