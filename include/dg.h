@@ -333,14 +333,32 @@ int dg_graph_info(const dg_graph *graph, int *occ_cap, int *concurrent, float *t
 /* The register tiles the recorded pass uses: tile_tm[p] (9 entries, p =
  * 0..8) is the tile edge of the degree-p row kernel (-1 for the tensor-core
  * forms' fixed fragment layout, 0 where the mesh has no element of degree p);
- * trials: passes the autotuner timed (0 without autotuning).  Either output
- * may be NULL.  With autotuning, dg_graph_create first times the launch
- * shapes above with the default tiles, then, for each degree present, every
- * other tile variant of its row kernel (FP32: 2D degree 3 {5, 4}, degree 4
+ * trials: passes the autotuner timed (0 without autotuning); persistent: 1
+ * when the pass's row work is the persistent launch.  Any output may be
+ * NULL.  With autotuning, dg_graph_create first times the launch shapes
+ * above with the default tiles, then, for each degree present, every other
+ * tile variant of its row kernel (FP32: 2D degree 3 {5, 4}, degree 4
  * {8, 5, 4}, degree 5 {7, 6, 5}, degree 6 {7, 6}; 3D degree 2 {5, 4},
  * degree 3 {4, 5, 7}; the first is the default) against the best pass so
- * far, and keeps a variant only where it makes the pass faster. */
-int dg_graph_tiles(const dg_graph *graph, int *tile_tm, int *trials);
+ * far, keeping a variant only where it makes the pass faster; then, for the
+ * FP32 form (2D degrees <= 5, 3D degrees <= 3), the persistent pass on each
+ * volume path tried.
+ *
+ * The persistent pass is one launch with as many CTAs as fit on the GPU at
+ * once; each warp takes the next tile of a work list (an atomic counter)
+ * until the list is done.  A tile is G elements of one degree: a moment tile
+ * (the volume terms through the Legendre-product moments) or a row tile (the
+ * face terms and off-diagonal blocks, and, off the moment path, the volume
+ * terms; one element per thread degrees get warp tiles of half the block's
+ * edge).  The list holds every moment tile first, then every row tile, each
+ * part ordered by estimated work, largest first; it is built on the host at
+ * the first persistent pass of a mesh and volume path (a synchronous upload,
+ * done by the autotuner before the graph is recorded).  A row tile adds to
+ * the diagonal blocks and load vector its elements' moment tiles wrote: it
+ * waits for their flags, a wait bounded in wall time (dg_set_wait_limit); a
+ * wait that runs out skips those additions and makes the next dg_sync return
+ * DG_ERR_TIMEOUT. */
+int dg_graph_tiles(const dg_graph *graph, int *tile_tm, int *trials, int *persistent);
 int dg_graph_free(dg_graph *graph);
 
 /* Learned reduced volume rules (2D).  For each element mapped to its
@@ -577,8 +595,29 @@ int dg_assemble_slab(dg_ctx *ctx, dg_mesh *mesh, int prec, int space, double t0,
 int dg_slab_trace(dg_ctx *ctx, const dg_mesh *mesh, int prec, int space, double t0, double t1, const void *U,
                   void *u_end);
 
-/* Wait for all work on the context stream; reports device-side errors. */
+/* Wait for all work on the context stream; reports device-side errors:
+ * DG_ERR_CUDA for a failed launch, DG_ERR_TIMEOUT when a bounded device wait
+ * (the persistent pass's, or dg_wait_probe's) ran out since the last
+ * dg_sync (the context's status word, cleared by the call). */
 int dg_sync(dg_ctx *ctx);
+
+/* on != 0: the calls without a tuned launch shape (dg_assemble_step,
+ * dg_assemble_host and dg_assemble_batch on a mesh and precision that
+ * dg_graph_create has not tuned, and dg_graph_create without autotuning)
+ * take the persistent pass where it serves the mesh (FP32; 2D degrees <= 5,
+ * 3D degrees <= 3), else their usual launches.  Off by default. */
+int dg_set_persistent(dg_ctx *ctx, int on);
+
+/* Bound of each device-side wait of the context's passes, in seconds of
+ * wall time (default 2; (0, 60]). */
+int dg_set_wait_limit(dg_ctx *ctx, double seconds);
+
+/* One launch of the persistent pass's bounded wait on flag (device, one int,
+ * owned by the caller): it returns once *flag != 0 or after seconds of wall
+ * time, in which case the next dg_sync returns DG_ERR_TIMEOUT.  A check of
+ * the timeout path that needs no fault: a flag that nothing sets makes the
+ * wait run out.  Asynchronous on the context stream. */
+int dg_wait_probe(dg_ctx *ctx, const int *flag, double seconds);
 
 /* Number of kernel launches issued by the last assembly call (for
  * accounting in benchmarks). */

@@ -47,6 +47,9 @@ __host__ __device__ constexpr int ipow_c(int b, int e) { return e == 0 ? 1 : b *
 // workload; the recorded pass's autotuner (dg_graph_create) times them.
 template <int D, int P, typename T>
 __host__ __device__ constexpr int tile_tm(int V) {
+  // variant 3: the persistent pass's tiles; degrees whose default is one
+  // element per thread get warp tiles of half the block's edge there
+  if (V == 3) return tile_tm<D, P, T>(0) == nbasis(D, P) ? (nbasis(D, P) + 1) / 2 : tile_tm<D, P, T>(0);
   if (sizeof(T) == 4 && D == 2) {
     if (P == 1) return 3;
     if (P == 2) return 6;
@@ -784,9 +787,49 @@ enum : int {
 // T parameter slots: a'[D], b'[D], lo[D], L[D], then:
 enum : int { kPtC = 0, kPtA = 1, kPtR = 2, kPtAk = 3, kPtRk = 4 };
 
-template <int D, int P, typename T, int TV = 0>
-__global__ void __launch_bounds__(kWarps * 32)
-    row_kernel(const DevMesh m, int mode, T* __restrict__ vals, T* __restrict__ rhs) {
+// Bounded wait of the persistent pass: an item that adds to blocks another
+// item writes first waits for that item's flag, at most limit_ns of wall
+// time (%globaltimer); a wait that runs out sets bit 0 of *status and the
+// waiting item skips the writes that depended on it.
+struct WaitCtl {
+  const int* vdone;  // [ne]: 1 once an element's moment item has written its diagonal block and load vector
+  int* status;
+  long long limit_ns;
+};
+
+__device__ __forceinline__ long long global_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// true once *flag != 0; false when limit_ns of wall time pass first
+__device__ __forceinline__ bool wait_flag(const int* flag, long long limit_ns) {
+  if (ld_acquire(flag)) return true;
+  const long long t0 = global_ns();
+  for (;;) {
+    __nanosleep(128);
+    if (ld_acquire(flag)) return true;
+    if (global_ns() - t0 > limit_ns) return false;
+  }
+}
+
+// One tile of the row kernel: G elements of degree P on this warp.  wb: the
+// warp's shared-memory region (RowSmem layout); rule: the degree's volume
+// rule and ctab the basis scales, both in shared memory; wc: null, or the
+// persistent pass's wait on the elements' moment items before the diagonal
+// block and the load vector are added to.
+template <int D, int P, typename T, int TV>
+__device__ __forceinline__ void row_tile(const DevMesh& m, int mode, T* __restrict__ vals, T* __restrict__ rhs,
+                                         int tile, const T* __restrict__ rule, const T* __restrict__ ctab,
+                                         unsigned char* wb, const WaitCtl* wc) {
   using Cfg = TileCfg<D, P, T, TV>;
   using SM = RowSmem<D, P, T, TV>;
   constexpr int N = Cfg::N, TM = Cfg::TM, TR = Cfg::TR, TPE = Cfg::TPE, G = Cfg::G;
@@ -795,11 +838,7 @@ __global__ void __launch_bounds__(kWarps * 32)
   constexpr int X = 4 * D;  // first scalar slot in PT
 
   const int VS = SM::vs(m.nmax), PSN = SM::psn(VS);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  T* rule = reinterpret_cast<T*>(smem_raw);
-  T* ctab = rule + QT * (D + 1);
-  unsigned char* wb = smem_raw + SM::head_bytes + warp * SM::warp_bytes(VS);
+  const int lane = threadIdx.x & 31;
   T* U = reinterpret_cast<T*>(wb);
   wb += SM::u_bytes;
   T* V = reinterpret_cast<T*>(wb);
@@ -808,11 +847,6 @@ __global__ void __launch_bounds__(kWarps * 32)
   wb += SM::r_bytes;
   T* PTv = reinterpret_cast<T*>(wb);
   int* PIv = reinterpret_cast<int*>(wb + align_up(sizeof(T) * G * PT, 16));
-
-  const T* vrule = pick<T>(m.rt.vol64, m.rt.vol32) + (size_t)m.rt.vol_off[P] * (D + 1);
-  for (int i = threadIdx.x; i < QT * (D + 1); i += blockDim.x) rule[i] = vrule[i];
-  fill_ctab<D, T>(ctab, SM::NMAXC);
-  __syncthreads();
 
   const T* SG = pick<T>(m.sg64, m.sg32);
   const T* HFR = pick<T>(m.hfr64, m.hfr32);
@@ -827,12 +861,10 @@ __global__ void __launch_bounds__(kWarps * 32)
   // with b = 0 and c = 0 the Phi row of a volume point carries no matrix term
   const bool no_adv = m.pb.b[0] == 0.0 && m.pb.b[1] == 0.0 && m.pb.b[2] == 0.0 && m.pb.c == 0.0;
   const int base = m.elem_pstart[P], count = m.elem_pstart[P + 1] - base;
-  const int ntiles = (count + G - 1) / G;
 
   const int g_me = lane / TPE;
   const int tr = (lane % TPE) / TR, tc = lane % TR;
-
-  for (int tile = blockIdx.x * kWarps + warp; tile < ntiles; tile += gridDim.x * kWarps) {
+  {
     const int gcount = min(G, count - tile * G);
     __syncwarp();
     // ---- per-element setup (one lane per element)
@@ -1087,8 +1119,14 @@ __global__ void __launch_bounds__(kWarps * 32)
       }
     }
 
-    // ---- write the diagonal block and the load vector
-    if (active) {
+    // ---- write the diagonal block and the load vector (in the persistent
+    // pass, once the element's moment item has written them)
+    bool wr = active;
+    if (wc && active && skip_vol && !wait_flag(wc->vdone + PIv[g_me * PI + kPiElem], wc->limit_ns)) {
+      atomicOr(wc->status, 1);
+      wr = false;
+    }
+    if (wr) {
       const int e = PIv[g_me * PI + kPiElem];
       const T Re = PTv[g_me * PT + X + kPtR];
       if (mat_vol || mat_face) {
@@ -1261,6 +1299,28 @@ __global__ void __launch_bounds__(kWarps * 32)
       }
     }
   }
+}
+
+template <int D, int P, typename T, int TV = 0>
+__global__ void __launch_bounds__(kWarps * 32)
+    row_kernel(const DevMesh m, int mode, T* __restrict__ vals, T* __restrict__ rhs) {
+  using Cfg = TileCfg<D, P, T, TV>;
+  using SM = RowSmem<D, P, T, TV>;
+  constexpr int QT = Cfg::QT, G = Cfg::G;
+  const int VS = SM::vs(m.nmax);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5;
+  T* rule = reinterpret_cast<T*>(smem_raw);
+  T* ctab = rule + QT * (D + 1);
+  unsigned char* wb = smem_raw + SM::head_bytes + warp * SM::warp_bytes(VS);
+  const T* vrule = pick<T>(m.rt.vol64, m.rt.vol32) + (size_t)m.rt.vol_off[P] * (D + 1);
+  for (int i = threadIdx.x; i < QT * (D + 1); i += blockDim.x) rule[i] = vrule[i];
+  fill_ctab<D, T>(ctab, SM::NMAXC);
+  __syncthreads();
+  const int count = m.elem_pstart[P + 1] - m.elem_pstart[P];
+  const int ntiles = (count + G - 1) / G;
+  for (int tile = blockIdx.x * kWarps + warp; tile < ntiles; tile += gridDim.x * kWarps)
+    row_tile<D, P, T, TV>(m, mode, vals, rhs, tile, rule, ctab, wb, nullptr);
 }
 
 }  // namespace dg

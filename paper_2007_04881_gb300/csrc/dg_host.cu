@@ -190,9 +190,13 @@ struct dg_ctx {
   bool vol_moments = true;  // volume blocks through Legendre-product moments
   bool vol_exact = false;   // 2D: those moments exact, by Green's theorem along the edges
   int tiles[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // row-kernel tile variants of untuned passes
+  int* status_dev = nullptr;  // bit 0: a bounded device wait ran out (read and cleared by dg_sync)
+  long long wait_ns = 2000000000LL;  // bound of one device wait
+  bool persist = false;  // untuned per-step passes and untuned graphs take the persistent pass
   std::vector<LaunchRec> recs;
   SideStreams streams;  // the direct launches' forked streams
   ~dg_ctx() {
+    if (status_dev) cudaFree(status_dev);
     for (auto& r : recs) {
       cudaEventDestroy(r.ev0);
       cudaEventDestroy(r.ev1);
@@ -226,6 +230,7 @@ struct dg_graph {
   int tiles[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // tile variant per degree
   int tile_tm[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // its tile edge (0: no group of that degree)
   int trials = 0;  // passes the autotuner timed
+  int persist = 0;  // 1: the row work is the persistent pass
   float tuned_ms = 0.f;
   int launches = 0;
   int ntrace = 0;  // timing events recorded inside the graph (tracing on at capture)
@@ -244,6 +249,15 @@ void Tracer::begin(const char* name, int kind, int p, size_t tsize, cudaStream_t
   r.flops = (kind < kKinds && flops) ? flops[kind * 9 + p] : 0.0;
   r.xflops = (kind == 2 && xflops) ? xflops[p] : r.flops;
   r.bytes = (kind < kKinds && words) ? words[kind * 9 + p] * (double)tsize : 0.0;
+  record(r.ev0, st);
+}
+void Tracer::begin_counts(const char* name, double fl, double xfl, double by, cudaStream_t st) {
+  if (!on || n >= cap) return;
+  LaunchRec& r = recs[n];
+  snprintf(r.name, sizeof r.name, "%s", name);
+  r.flops = fl;
+  r.xflops = xfl;
+  r.bytes = by;
   record(r.ev0, st);
 }
 void Tracer::end(cudaStream_t st) {
@@ -281,6 +295,7 @@ struct dg_mesh {
   int shape_set[4] = {0, 0, 0, 0}, shape_occ[4] = {0, 0, 0, 0}, shape_conc[4] = {0, 0, 0, 0};
   int shape_path[4] = {-1, -1, -1, -1}, shape_vm[4] = {0, 0, 0, 0};
   int shape_tile[4][9] = {{0}};  // tuned tile variant per degree
+  int shape_persist[4] = {0, 0, 0, 0};  // tuned: the persistent pass
   double* X[3] = {nullptr, nullptr, nullptr};
   double* a = nullptr;
   double flops[kKinds][9] = {{0}}, words[kKinds][9] = {{0}};
@@ -293,6 +308,12 @@ struct dg_mesh {
   std::vector<int> p_h, nvq_h, nqf_h;
   std::vector<double> vfma_h;  // algorithmic FMAs per volume point of each element
   std::vector<int> perm_fan;  // the sub-simplex-rule work list
+  std::vector<int> perm_h;    // the current work list (host copy of perm_dev)
+  // persistent pass: queue word, pad and the elements' moment flags
+  // (zeroed before each launch), the work list of tiles and what it was built for
+  int* pk_sync = nullptr;
+  int4* pk_items = nullptr;
+  int pk_nitems = 0, pk_key = -1, pk_cap = 0;
   // learned quadrature (2D)
   double *lq_mom = nullptr, *lq_mmom = nullptr, *lq_rule = nullptr, *lq64 = nullptr;
   float *lq32 = nullptr, *lq_resid = nullptr, *lq_out = nullptr;
@@ -310,7 +331,7 @@ struct dg_mesh {
   ~dg_mesh() {
     if (h_vals) cudaFree(h_vals);
     if (h_rhs) cudaFree(h_rhs);
-    void* q[] = {lq_mom, lq_mmom, lq_rule, lq64, lq32, lq_resid, lq_elig, lq_ok, lq_okm, lq_feat, lq_out};
+    void* q[] = {lq_mom, lq_mmom, lq_rule, lq64, lq32, lq_resid, lq_elig, lq_ok, lq_okm, lq_feat, lq_out, pk_sync, pk_items};
     for (void* x : q)
       if (x) cudaFree(x);
   }
@@ -522,6 +543,11 @@ int dg_create(dg_ctx** out, int device, void* stream) {
   if (rc != DG_OK) {
     delete ctx;
     return rc;
+  }
+  if (cudaMalloc(&ctx->status_dev, sizeof(int)) != cudaSuccess ||
+      cudaMemset(ctx->status_dev, 0, sizeof(int)) != cudaSuccess) {
+    delete ctx;
+    return fail(DG_ERR_OOM, "dg_create: status word");
   }
   *out = ctx;
   return DG_OK;
@@ -1206,6 +1232,7 @@ static int upload_impl(dg_ctx* ctx, const dg_mesh_desc* d, const int8_t* owned, 
     }
   }
   m->perm_fan = elem_perm;
+  m->perm_h = elem_perm;
   m->perm_dev = const_cast<int*>(dm.elem_perm);
   if (owned) m->owned_h.assign(owned, owned + ne);
   dm.lq_ok = nullptr;
@@ -1351,14 +1378,18 @@ int dg_assemble(dg_ctx* ctx, const dg_mesh* mesh, int prec, void* vals, void* rh
 // The per-step launch shape: the autotuned one where dg_graph_create has
 // tuned this precision on this mesh, else concurrent degree groups when the
 // mesh has more than one.
+static bool persist_ok(const dg_ctx* ctx, const dg_mesh* mesh, int prec, int vpath, int* mom_mask);
+
 static void step_shape(const dg_ctx* ctx, const dg_mesh* mesh, int prec, int* occ, bool* conc, int* path,
-                       const int** tiles) {
+                       const int** tiles, bool* persist = nullptr) {
   *tiles = ctx->tiles;
+  if (persist) *persist = false;
   if (mesh->shape_set[prec] && mesh->shape_vm[prec] == ctx_vol_path(ctx)) {
     *occ = mesh->shape_occ[prec];
     *conc = mesh->shape_conc[prec] != 0;
     *path = mesh->shape_path[prec];
     *tiles = mesh->shape_tile[prec];
+    if (persist) *persist = mesh->shape_persist[prec] != 0;
     return;
   }
   int groups = 0;
@@ -1366,7 +1397,11 @@ static void step_shape(const dg_ctx* ctx, const dg_mesh* mesh, int prec, int* oc
   *occ = 0;
   *conc = groups > 1;
   *path = -1;
+  int mask = 0;
+  if (persist && ctx->persist) *persist = persist_ok(ctx, mesh, prec, -1, &mask);
 }
+
+static int issue_persist_step(dg_ctx* ctx, dg_mesh* mesh, int prec, int mode, void* vals, void* rhs, int vpath);
 
 int dg_assemble_host(dg_ctx* ctx, dg_mesh* mesh, int prec, const double* x, const double* y, const double* z,
                      const double* a, void* vals_host, void* rhs_host) {
@@ -1394,10 +1429,12 @@ int dg_assemble_host(dg_ctx* ctx, dg_mesh* mesh, int prec, const double* x, cons
   int occ = 0, path = -1;
   bool conc = false;
   const int* tiles = nullptr;
-  step_shape(ctx, mesh, prec, &occ, &conc, &path, &tiles);
+  bool persist = false;
+  step_shape(ctx, mesh, prec, &occ, &conc, &path, &tiles, &persist);
   const int mode = kModeVol | kModeFace | (rhs_host ? kModeRhs : 0);
-  int rc = run_assembly(ctx, mesh, prec, mode, mesh->h_vals, rhs_host ? mesh->h_rhs : nullptr, true, false, nullptr,
-                        true, occ, conc, path, nullptr, tiles);
+  int rc = persist ? issue_persist_step(ctx, mesh, prec, mode, mesh->h_vals, rhs_host ? mesh->h_rhs : nullptr, path)
+                   : run_assembly(ctx, mesh, prec, mode, mesh->h_vals, rhs_host ? mesh->h_rhs : nullptr, true, false,
+                                  nullptr, true, occ, conc, path, nullptr, tiles);
   if (rc != DG_OK) return rc;
   // one copy each: several parts on parallel streams measured no faster
   DG_CUDA_TRY(cudaMemcpyAsync(vals_host, mesh->h_vals, es * mesh->info.nvals, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1418,8 +1455,10 @@ int dg_assemble_step(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs
   int occ = 0, path = -1;
   bool conc = false;
   const int* tiles = nullptr;
-  step_shape(ctx, mesh, prec, &occ, &conc, &path, &tiles);
+  bool persist = false;
+  step_shape(ctx, mesh, prec, &occ, &conc, &path, &tiles, &persist);
   const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
+  if (persist) return issue_persist_step(ctx, mesh, prec, mode, vals, rhs, path);
   return run_assembly(ctx, mesh, prec, mode, vals, rhs, true, false, nullptr, true, occ, conc, path, nullptr, tiles);
 }
 
@@ -1979,12 +2018,163 @@ int dg_batch_offsets(const dg_mesh* mesh, int* nmesh, int* elem_off, int64_t* va
   return DG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// The persistent pass (dg_persist.cuh): one launch over a work list of tiles.
+// ---------------------------------------------------------------------------
+
+// whether the persistent pass serves this mesh and precision; *mom_mask gets
+// the degrees that take the moment path on volume path vpath
+static bool persist_ok(const dg_ctx* ctx, const dg_mesh* mesh, int prec, int vpath, int* mom_mask) {
+  if (prec != DG_PREC_FP32) return false;
+  int ok_mask = 0, gm[9], gr[9];
+  const int pserve = persist_layout(mesh->dm.dim, &ok_mask, gm, gr);
+  int present = 0, pmax = 0;
+  for (int p = 1; p <= 7; ++p)
+    if (mesh->dm.elem_pstart[p + 1] > mesh->dm.elem_pstart[p]) {
+      present |= 1 << p;
+      pmax = p;
+    }
+  if (pmax > pserve || present == 0) return false;
+  const bool moments = vpath >= 0 ? vpath >= 1 : ctx->vol_moments && !mesh->dm.lq_ok;
+  *mom_mask = moments && mesh->dm.rt.lin32 ? ok_mask & present : 0;
+  return true;
+}
+
+// The work list for mom_mask: every moment tile, then every row tile, each
+// part by estimated work (points times n^2 over the tile's elements),
+// largest first.  Built on the host and uploaded (synchronous); cached.
+static int persist_items(dg_ctx* ctx, dg_mesh* mesh, int mom_mask) {
+  const int key = mom_mask;
+  if (mesh->pk_key == key) return DG_OK;
+  int ok_mask = 0, gm[9], gr[9];
+  persist_layout(mesh->dm.dim, &ok_mask, gm, gr);
+  const int dim = mesh->dm.dim, ne = mesh->dm.ne;
+  struct Item {
+    double cost;
+    int kind, p, tile;
+  };
+  std::vector<Item> mom, row;
+  const bool lrn = mesh->dm.lq_ok != nullptr;
+  std::vector<int> okh;
+  if (lrn) {
+    okh.resize(ne);
+    DG_CUDA_TRY(cudaMemcpy(okh.data(), mesh->dm.lq_ok, sizeof(int) * ne, cudaMemcpyDeviceToHost));
+  }
+  for (int p = 1; p <= 7; ++p) {
+    const int b = mesh->dm.elem_pstart[p], cnt = mesh->dm.elem_pstart[p + 1] - b;
+    if (cnt <= 0) continue;
+    const double n2 = (double)nbasis(dim, p) * nbasis(dim, p);
+    const bool mp = (mom_mask >> p) & 1;
+    auto cost_of = [&](int lo, int hi, int kind) {
+      double c = 0.0;
+      for (int i = lo; i < hi && i < cnt; ++i) {
+        const int e = mesh->perm_h[b + i];
+        const double nvq = lrn && okh[e] ? 28.0 : (double)mesh->nvq_h[e];
+        c += kind == 1 ? nvq * n2 / 8.0 : ((mp ? 0.0 : nvq) + mesh->nqf_h[e]) * n2;
+      }
+      return c;
+    };
+    if (mp)
+      for (int t = 0; t * gm[p] < cnt; ++t) mom.push_back({cost_of(t * gm[p], (t + 1) * gm[p], 1), 1, p, t});
+    for (int t = 0; t * gr[p] < cnt; ++t) row.push_back({cost_of(t * gr[p], (t + 1) * gr[p], 0), 0, p, t});
+  }
+  auto by_cost = [](const Item& x, const Item& y) {
+    if (x.cost != y.cost) return x.cost > y.cost;
+    if (x.p != y.p) return x.p > y.p;
+    return x.tile < y.tile;
+  };
+  std::sort(mom.begin(), mom.end(), by_cost);
+  std::sort(row.begin(), row.end(), by_cost);
+  std::vector<int4> items;
+  items.reserve(mom.size() + row.size());
+  for (const auto& it : mom) items.push_back(make_int4(it.kind, it.p, it.tile, 0));
+  for (const auto& it : row) items.push_back(make_int4(it.kind, it.p, it.tile, 0));
+  if ((int)items.size() > mesh->pk_cap) {
+    if (mesh->pk_items) cudaFree(mesh->pk_items);
+    mesh->pk_items = nullptr;
+    mesh->pk_cap = 0;
+    if (cudaMalloc(&mesh->pk_items, sizeof(int4) * std::max<size_t>(items.size(), 1)) != cudaSuccess)
+      return fail(DG_ERR_OOM, "persistent pass: work list");
+    mesh->pk_cap = (int)items.size();
+  }
+  if (!mesh->pk_sync && cudaMalloc(&mesh->pk_sync, sizeof(int) * (2 + (size_t)ne)) != cudaSuccess)
+    return fail(DG_ERR_OOM, "persistent pass: flags");
+  DG_CUDA_TRY(cudaMemcpy(mesh->pk_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
+  mesh->pk_nitems = (int)items.size();
+  mesh->pk_key = key;
+  (void)ctx;
+  return DG_OK;
+}
+
+// Issue the persistent pass's row work on st (the work list must exist:
+// persist_items before any capture).
+static int issue_persist_rows(dg_ctx* ctx, dg_mesh* mesh, int prec, int mode, void* vals, void* rhs, cudaStream_t st,
+                              int vpath) {
+  int mom_mask = 0;
+  if (!persist_ok(ctx, mesh, prec, vpath, &mom_mask)) return fail(DG_ERR_ARG, "the persistent pass does not serve this mesh");
+  if (mesh->pk_key != mom_mask) return fail(DG_ERR_ARG, "persistent pass: work list not built");
+  const int ne = mesh->dm.ne;
+  DG_CUDA_TRY(cudaMemsetAsync(mesh->pk_sync, 0, sizeof(int) * (2 + (size_t)ne), st));
+  PersistArgs a{};
+  a.items = mesh->pk_items;
+  a.nitems = mesh->pk_nitems;
+  a.queue = mesh->pk_sync;
+  a.vdone = mesh->pk_sync + 2;
+  a.status = ctx->status_dev;
+  a.limit_ns = ctx->wait_ns;
+  a.mode = mode;
+  a.mom_mask = mom_mask;
+  const bool exact = vpath >= 0 ? vpath == 2 : ctx->vol_exact;
+  a.exact = exact && mesh->dm.dim == 2 ? kModeExactMom : 0;
+  int pmax = 0;
+  for (int p = 1; p <= 7; ++p)
+    if (mesh->dm.elem_pstart[p + 1] > mesh->dm.elem_pstart[p]) pmax = p;
+  float* v = static_cast<float*>(vals);
+  float* r = static_cast<float*>(rhs);
+  Tracer* tr = &ctx->tracer;
+  if (tr->on) {
+    // the whole pass's algorithmic work; executed: the moment form where taken
+    double fl = 0.0, xfl = 0.0, by = 0.0;
+    for (int p = 1; p <= 8; ++p) {
+      fl += mesh->flops[0][p];
+      by += mesh->words[0][p] * sizeof(float);
+      xfl += ((mom_mask >> p) & 1) ? mesh->mom_exec[p] + mesh->flops[1][p] : mesh->flops[0][p];
+    }
+    tr->begin_counts(mesh->dm.dim == 2 ? "row_persist2d_f32" : "row_persist3d_f32", fl, xfl, by, st);
+  }
+  const int n = mesh->dm.dim == 2 ? launch_persist2d_f32(mesh->dm, v, r, a, pmax, ctx->sm_count, st)
+                                  : launch_persist3d_f32(mesh->dm, v, r, a, pmax, ctx->sm_count, st);
+  if (tr->on) tr->end(st);
+  if (n < 0) return fail(DG_ERR_ARG, "persistent pass: shared memory does not fit");
+  DG_CUDA_TRY(cudaGetLastError());
+  return DG_OK;
+}
+
+// The persistent pass's row work on the context stream (the per-step entry
+// points), the work list built first if needed.
+static int issue_persist_step(dg_ctx* ctx, dg_mesh* mesh, int prec, int mode, void* vals, void* rhs, int vpath) {
+  int mask = 0;
+  if (!persist_ok(ctx, mesh, prec, vpath, &mask)) return fail(DG_ERR_ARG, "the persistent pass does not serve this mesh");
+  int rc = persist_items(ctx, mesh, mask);
+  if (rc != DG_OK) return rc;
+  rc = issue_persist_rows(ctx, mesh, prec, mode, vals, rhs, ctx->stream, vpath);
+  if (rc == DG_OK) ctx->last_launches += 1;
+  return rc;
+}
+
 // One whole pass (geometry + row kernels) on stream st with a launch shape.
 static int issue_pass(dg_ctx* ctx, dg_mesh* mesh, int prec, int gmask, void* vals, void* rhs, cudaStream_t st,
-                      int occ_cap, bool concurrent, int vpath, SideStreams* ss, const int* tiles) {
+                      int occ_cap, bool concurrent, int vpath, SideStreams* ss, const int* tiles, bool persist = false) {
   int n = launch_geometry(mesh->dm, st, nullptr, gmask);
   DG_CUDA_TRY(cudaGetLastError());
   const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
+  if (persist) {
+    trace_reset(ctx, mesh);
+    int rc = issue_persist_rows(ctx, mesh, prec, mode, vals, rhs, st, vpath);
+    if (rc != DG_OK) return rc;
+    ctx->last_launches = n + 1;
+    return DG_OK;
+  }
   int rc = run_assembly(ctx, mesh, prec, mode, vals, rhs, true, true, st, false, occ_cap, concurrent, vpath, ss, tiles);
   if (rc != DG_OK) return rc;
   ctx->last_launches += n;
@@ -2013,6 +2203,7 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
   const int def_path = ctx->vol_moments && !mesh->dm.lq_ok ? mpath : 0;
   int best_occ = 0, best_conc = 0, best_path = def_path;
   int best_tiles[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  int best_persist = 0;
   float best = 1e30f;
   if (autotune) {
     const int occs[3] = {0, 1, 2};
@@ -2021,11 +2212,12 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     // one candidate: best of 3 timed passes after a warm-up pass
-    auto time_shape = [&](int occ, int conc, int vpath, const int* tiles, float* out) -> int {
+    auto time_shape = [&](int occ, int conc, int vpath, const int* tiles, float* out, bool persist = false) -> int {
       float t = 1e30f;
       for (int rep = 0; rep < 4; ++rep) {
         cudaEventRecord(e0, g->stream);
-        int rc = issue_pass(ctx, mesh, prec, gmask, vals, rhs, g->stream, occ, conc != 0, vpath, &g->streams, tiles);
+        int rc = issue_pass(ctx, mesh, prec, gmask, vals, rhs, g->stream, occ, conc != 0, vpath, &g->streams, tiles,
+                            persist);
         if (rc != DG_OK) return rc;
         cudaEventRecord(e1, g->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) return fail(DG_ERR_CUDA, "dg_graph_create: tuning pass failed");
@@ -2054,7 +2246,7 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
         }
     // tiles: for each degree present, each other register-tile variant of
     // its row kernel against the best so far (one pass of coordinate descent)
-    for (int p = 1; rc == DG_OK && p <= 8; ++p) {
+    for (int p = 1; rc == DG_OK && p <= 7; ++p) {
       if (mesh->dm.elem_pstart[p + 1] <= mesh->dm.elem_pstart[p]) continue;
       for (int v = 1; rc == DG_OK && row_tile_tm(mesh->dm.dim, p, prec, v) > 0; ++v) {
         int cand[9];
@@ -2068,6 +2260,20 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
         }
       }
     }
+    // the persistent pass (its own tiles), on each volume path tried above
+    for (int pi = 0; rc == DG_OK && pi < npath; ++pi) {
+      const int vpath = npath == 2 ? (pi == 0 ? mpath : 0) : def_path;
+      int mask = 0;
+      if (!persist_ok(ctx, mesh, prec, vpath, &mask)) continue;
+      rc = persist_items(ctx, mesh, mask);
+      float t = 0.f;
+      if (rc == DG_OK) rc = time_shape(0, 0, vpath, best_tiles, &t, true);
+      if (rc == DG_OK && t < best) {
+        best = t;
+        best_path = vpath;
+        best_persist = 1;
+      }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != DG_OK) {
@@ -2075,14 +2281,26 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
       return bail(rc);
     }
   }
+  if (!autotune && ctx->persist) {
+    int mask = 0;
+    if (persist_ok(ctx, mesh, prec, best_path, &mask)) {
+      const int rc = persist_items(ctx, mesh, mask);
+      if (rc != DG_OK) {
+        ctx->tracer.on = was_on;
+        return bail(rc);
+      }
+      best_persist = 1;
+    }
+  }
   g->occ_cap = best_occ;
   g->concurrent = best_conc;
   g->vol_path = best_path;
+  g->persist = best_persist;
   g->tuned_ms = autotune ? best : 0.f;
   for (int p = 0; p < 9; ++p) {
     g->tiles[p] = best_tiles[p];
     const bool present = p >= 1 && p <= 7 && mesh->dm.elem_pstart[p + 1] > mesh->dm.elem_pstart[p];
-    g->tile_tm[p] = present ? row_tile_tm(mesh->dm.dim, p, prec, best_tiles[p]) : 0;
+    g->tile_tm[p] = present ? row_tile_tm(mesh->dm.dim, p, prec, best_persist ? 3 : best_tiles[p]) : 0;
   }
   if (autotune) {
     mesh->shape_set[prec] = 1;
@@ -2091,6 +2309,7 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
     mesh->shape_path[prec] = best_path;
     mesh->shape_vm[prec] = ctx_vol_path(ctx);
     std::copy(best_tiles, best_tiles + 9, mesh->shape_tile[prec]);
+    mesh->shape_persist[prec] = best_persist;
   }
   // with timing enabled the per-launch events are recorded into the graph
   ctx->tracer.on = was_on;
@@ -2101,8 +2320,13 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
   {
     const int gl = launch_geometry(mesh->dm, g->stream, &ctx->tracer, gmask);
     const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
-    rc = run_assembly(ctx, mesh, prec, mode, vals, rhs, true, false, g->stream, false, g->occ_cap, g->concurrent != 0,
-                      g->vol_path, &g->streams, g->tiles);
+    if (g->persist) {
+      rc = issue_persist_rows(ctx, mesh, prec, mode, vals, rhs, g->stream, g->vol_path);
+      ctx->last_launches = 1;
+    } else {
+      rc = run_assembly(ctx, mesh, prec, mode, vals, rhs, true, false, g->stream, false, g->occ_cap,
+                        g->concurrent != 0, g->vol_path, &g->streams, g->tiles);
+    }
     ctx->last_launches += gl;
   }
   cudaError_t ce = cudaStreamEndCapture(g->stream, &g->graph);
@@ -2200,10 +2424,11 @@ int dg_graph_info(const dg_graph* g, int* occ_cap, int* concurrent, float* tuned
   return DG_OK;
 }
 
-int dg_graph_tiles(const dg_graph* g, int* tile_tm, int* trials) {
+int dg_graph_tiles(const dg_graph* g, int* tile_tm, int* trials, int* persistent) {
   if (!g) return fail(DG_ERR_ARG, "dg_graph_tiles: null graph");
   if (tile_tm) std::copy(g->tile_tm, g->tile_tm + 9, tile_tm);
   if (trials) *trials = g->trials;
+  if (persistent) *persistent = g->persist;
   return DG_OK;
 }
 
@@ -2265,6 +2490,8 @@ static int rebuild_worklist(dg_ctx* ctx, dg_mesh* mesh, const std::vector<int>& 
   });
   DG_CUDA_TRY(cudaMemcpyAsync(mesh->perm_dev, perm.data(), sizeof(int) * perm.size(), cudaMemcpyHostToDevice,
                               ctx->stream));
+  mesh->perm_h = perm;
+  mesh->pk_key = -1;  // the persistent pass's tiles follow the work list
   DG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   return DG_OK;
 }
@@ -2448,6 +2675,31 @@ int dg_set_volume_path(dg_ctx* ctx, int path) {
 int dg_sync(dg_ctx* ctx) {
   if (!ctx) return fail(DG_ERR_ARG, "dg_sync: null context");
   DG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  DG_CUDA_TRY(cudaGetLastError());
+  int st = 0;
+  DG_CUDA_TRY(cudaMemcpy(&st, ctx->status_dev, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) {
+    DG_CUDA_TRY(cudaMemset(ctx->status_dev, 0, sizeof(int)));
+    return fail(DG_ERR_TIMEOUT, "a bounded device wait ran out (status 0x%x); the pass's results are incomplete", st);
+  }
+  return DG_OK;
+}
+
+int dg_set_persistent(dg_ctx* ctx, int on) {
+  if (!ctx) return fail(DG_ERR_ARG, "dg_set_persistent: null context");
+  ctx->persist = on != 0;
+  return DG_OK;
+}
+
+int dg_set_wait_limit(dg_ctx* ctx, double seconds) {
+  if (!ctx || !(seconds > 0.0) || seconds > 60.0) return fail(DG_ERR_ARG, "dg_set_wait_limit: seconds outside (0, 60]");
+  ctx->wait_ns = (long long)(seconds * 1e9);
+  return DG_OK;
+}
+
+int dg_wait_probe(dg_ctx* ctx, const int* flag, double seconds) {
+  if (!ctx || !flag || !(seconds > 0.0) || seconds > 60.0) return fail(DG_ERR_ARG, "dg_wait_probe: bad argument");
+  launch_wait_probe(flag, ctx->status_dev, (long long)(seconds * 1e9), ctx->stream);
   DG_CUDA_TRY(cudaGetLastError());
   return DG_OK;
 }

@@ -207,6 +207,8 @@ struct Tracer {
   const double* words = nullptr;   // [kKinds][9]
   const double* xflops = nullptr;  // [9]: flops the kind-2 launch executes
   void begin(const char* name, int kind, int p, size_t tsize, cudaStream_t st);
+  // a launch with its counts given directly
+  void begin_counts(const char* name, double fl, double xfl, double by, cudaStream_t st);
   void end(cudaStream_t st);
   static void record(cudaEvent_t ev, cudaStream_t st);
 };
@@ -243,6 +245,32 @@ int launch_row2d_bf16(const DevMesh& m, int mode, float* vals, float* rhs, int s
 int launch_row2d_tf32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);
 int launch_row3d_bf16(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);
 int launch_row3d_tf32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);
+
+// The persistent pass (dg_persist.cuh): one launch in which every warp
+// takes tiles from a work list until it is done.
+struct PersistArgs {
+  const int4* items;   // x: kind (0 row tile, 1 moment tile), y: degree, z: tile index
+  int nitems;
+  int* queue;          // next item; zero before the launch
+  int* vdone;          // [ne] moment-tile flags; zero before the launch
+  int* status;         // bit 0: a bounded wait ran out
+  long long limit_ns;  // bound of one wait
+  int mode;            // assembly mode of the pass (kModeVol | kModeFace | kModeRhs)
+  int mom_mask;        // bit p: degree p takes the moment path
+  int exact;           // kModeExactMom for the moment tiles (2D volume path 2), else 0
+  int warp_bytes;      // shared memory per warp (set by the launcher)
+};
+// FP32 persistent passes: the launch (1, or -1 when the shared memory does
+// not fit), the degrees that can take the moment path, and the elements per
+// tile of each kind (gmom[p], grow[p], 9 entries each).
+int launch_persist2d_f32(const DevMesh& m, float* vals, float* rhs, const PersistArgs& a, int pmax, int sm_count,
+                         cudaStream_t st);
+int launch_persist3d_f32(const DevMesh& m, float* vals, float* rhs, const PersistArgs& a, int pmax, int sm_count,
+                         cudaStream_t st);
+int persist_layout(int dim, int* mom_ok_mask, int* gmom, int* grow);
+// a one-warp launch of the persistent pass's bounded wait on flag; a wait
+// that runs out sets bit 0 of *status
+void launch_wait_probe(const int* flag, int* status, long long limit_ns, cudaStream_t st);
 
 // learned quadrature (dg_learned.cu)
 void lq_prepare(const DevMesh& m, double* mom, double* mmom, void* feat, int* elig, cudaStream_t st);

@@ -79,49 +79,36 @@ __host__ __device__ constexpr bool moment_volume_ok() {
   return P >= 2 && P <= kPMaxLin && nmom<D>(2 * P) <= (sizeof(T) == 4 ? 96 : 56);
 }
 
+// One tile of the moment kernel: G elements of degree P on this warp, LPE
+// lanes each.  lin, rule, ctab, alf: the linearisation tables, the degree's
+// volume rule, the basis scales and exponents in shared memory; pw: the
+// warp's per-element scratch (G * PER_ELEM values); wc: null, or the
+// persistent pass's flags, set once an element's diagonal block and load
+// vector are written.
 template <int D, int P, typename T>
-__global__ void __launch_bounds__(kWarps * 32)
-    vol_moment_kernel(const DevMesh m, int mode, T* __restrict__ vals, T* __restrict__ rhs) {
+__device__ __forceinline__ void mom_tile(const DevMesh& m, int mode, T* __restrict__ vals, T* __restrict__ rhs,
+                                         int tile, const T* __restrict__ lin, const T* __restrict__ rule,
+                                         const T* __restrict__ ctab, const int* __restrict__ alf, T* pw,
+                                         const WaitCtl* wc) {
   using Cfg = MomCfg<D, P, T>;
   constexpr int N = Cfg::N, Q = Cfg::Q, NM = Cfg::NM, LPE = Cfg::LPE, G = Cfg::G, QT = Cfg::QT;
-  constexpr int PL = Cfg::PL, CL = Cfg::CL, NLIN = Cfg::NLIN, NPAIR = Cfg::NPAIR;
+  constexpr int PL = Cfg::PL, CL = Cfg::CL, NPAIR = Cfg::NPAIR;
   constexpr int SV = sub_vals(D);
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* lin = reinterpret_cast<T*>(smem_raw);  // [3][PL][PL][CL]
-  T* rule = lin + NLIN;
-  T* ctab = rule + QT * (D + 1);
-  int* alf = reinterpret_cast<int*>(ctab + Cfg::NMAXC);       // exponents [N][3]
-  T* pe = reinterpret_cast<T*>(smem_raw) + Cfg::head_elems;  // per element scratch
-  const T* glin = pick<T>(m.rt.lin64, m.rt.lin32);
-  for (int i = threadIdx.x; i < NLIN; i += blockDim.x) lin[i] = glin[i];
-  const T* vrule = pick<T>(m.rt.vol64, m.rt.vol32) + (size_t)m.rt.vol_off[P] * (D + 1);
-  for (int i = threadIdx.x; i < QT * (D + 1); i += blockDim.x) rule[i] = vrule[i];
-  fill_ctab<D, T>(ctab, Cfg::NMAXC);
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    int al[3] = {0, 0, 0};
-    basis_alpha<D>(i, al);
-    alf[3 * i] = al[0];
-    alf[3 * i + 1] = al[1];
-    alf[3 * i + 2] = al[2];
-  }
-  __syncthreads();
   auto L0 = [&](int a, int b, int c) { return lin[(a * PL + b) * CL + c]; };
   auto L1 = [&](int a, int b, int c) { return lin[PL * PL * CL + (a * PL + b) * CL + c]; };
   auto L2 = [&](int a, int b, int c) { return lin[2 * PL * PL * CL + (a * PL + b) * CL + c]; };
 
   const T* SG = pick<T>(m.sg64, m.sg32);
   const bool mat_vol = mode & kModeVol, do_rhs = mode & kModeRhs, accum = mode & kModeAccum;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31;
   const int grp = lane / LPE, lig = lane % LPE;
-  T* my = pe + (size_t)(warp * G + grp) * Cfg::PER_ELEM;  // this element's scratch
+  T* my = pw + (size_t)grp * Cfg::PER_ELEM;  // this element's scratch
   T* smu = my;
   T* sXa = my + NM;                // [NPAIR][Q+1] per exponent pair (a, a') of dimension 0
   T* sYb = sXa + NPAIR * (Q + 1);  // 3D: dimension 1 [NPAIR][Q+1]; 2D: T [Q+1][NPAIR]
   T* sZs = sYb + NPAIR * (Q + 1);  // 3D: dimension 2 [NPAIR][Q+1]; 2D: U [Q+1][NPAIR]
   const int base = m.elem_pstart[P], count = m.elem_pstart[P + 1] - base;
-  const int ngroups = (count + G - 1) / G;
-
-  for (int tile = blockIdx.x * kWarps + warp; tile < ngroups; tile += gridDim.x * kWarps) {
+  {
     const int slot = tile * G + grp;
     const bool active = slot < count;
     const int e = active ? m.elem_perm[base + slot] : 0;
@@ -383,7 +370,45 @@ __global__ void __launch_bounds__(kWarps * 32)
         }
       }
     }
+    if (wc) {
+      // every lane's writes of the two elements before the flags
+      __threadfence();
+      __syncwarp();
+      if (active && lig == 0) st_release(const_cast<int*>(wc->vdone) + e, 1);
+    }
   }
+}
+
+template <int D, int P, typename T>
+__global__ void __launch_bounds__(kWarps * 32)
+    vol_moment_kernel(const DevMesh m, int mode, T* __restrict__ vals, T* __restrict__ rhs) {
+  using Cfg = MomCfg<D, P, T>;
+  constexpr int N = Cfg::N, G = Cfg::G, QT = Cfg::QT, NLIN = Cfg::NLIN;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* lin = reinterpret_cast<T*>(smem_raw);  // [3][PL][PL][CL]
+  T* rule = lin + NLIN;
+  T* ctab = rule + QT * (D + 1);
+  int* alf = reinterpret_cast<int*>(ctab + Cfg::NMAXC);       // exponents [N][3]
+  T* pe = reinterpret_cast<T*>(smem_raw) + Cfg::head_elems;  // per element scratch
+  const T* glin = pick<T>(m.rt.lin64, m.rt.lin32);
+  for (int i = threadIdx.x; i < NLIN; i += blockDim.x) lin[i] = glin[i];
+  const T* vrule = pick<T>(m.rt.vol64, m.rt.vol32) + (size_t)m.rt.vol_off[P] * (D + 1);
+  for (int i = threadIdx.x; i < QT * (D + 1); i += blockDim.x) rule[i] = vrule[i];
+  fill_ctab<D, T>(ctab, Cfg::NMAXC);
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    int al[3] = {0, 0, 0};
+    basis_alpha<D>(i, al);
+    alf[3 * i] = al[0];
+    alf[3 * i + 1] = al[1];
+    alf[3 * i + 2] = al[2];
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5;
+  T* pw = pe + (size_t)warp * G * Cfg::PER_ELEM;
+  const int count = m.elem_pstart[P + 1] - m.elem_pstart[P];
+  const int ngroups = (count + G - 1) / G;
+  for (int tile = blockIdx.x * kWarps + warp; tile < ngroups; tile += gridDim.x * kWarps)
+    mom_tile<D, P, T>(m, mode, vals, rhs, tile, lin, rule, ctab, alf, pw, nullptr);
 }
 
 }  // namespace dg

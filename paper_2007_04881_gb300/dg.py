@@ -123,7 +123,10 @@ def load() -> C.CDLL:
     lib.dg_graph_launch.argtypes = [V, V]
     lib.dg_graph_info.argtypes = [V, V, V, V, V, V]
     lib.dg_graph_free.argtypes = [V]
-    lib.dg_graph_tiles.argtypes = [V, V, V]
+    lib.dg_graph_tiles.argtypes = [V, V, V, V]
+    lib.dg_set_wait_limit.argtypes = [V, C.c_double]
+    lib.dg_set_persistent.argtypes = [V, C.c_int]
+    lib.dg_wait_probe.argtypes = [V, V, C.c_double]
     lib.dg_set_tile_variants.argtypes = [V, V]
     lib.dg_volume_noalloc.argtypes = [V, C.c_int, C.c_int, C.c_int, C.c_int, V, V, C.c_int, C.c_int, V, V, V,
                                       C.c_double, C.c_double, C.c_double, V, V]
@@ -176,7 +179,8 @@ EXPORTS = (
     "dg_partition", "dg_mesh_upload_part", "dg_part_map", "dg_part_check", "dg_set_volume_path",
     "dg_slab_offsets", "dg_slab_layout", "dg_assemble_slab", "dg_slab_trace", "dg_assemble_varcoef",
     "dg_mlp_save", "dg_mlp_load", "dg_quad_learn", "dg_assemble_batch", "dg_graph_tiles",
-    "dg_set_tile_variants",
+    "dg_set_tile_variants", "dg_set_wait_limit", "dg_wait_probe",
+    "dg_set_persistent",
 )
 
 
@@ -243,6 +247,16 @@ class Context:
         """Row-kernel tile variant per degree (9 ints, or None for the defaults)."""
         v = None if variants is None else np.ascontiguousarray(variants, dtype=np.int32)
         _check(load().dg_set_tile_variants(self._h, _vp(v)))
+
+    def dg_set_persistent(self, on: bool):
+        _check(load().dg_set_persistent(self._h, int(bool(on))))
+
+    def dg_set_wait_limit(self, seconds: float):
+        _check(load().dg_set_wait_limit(self._h, float(seconds)))
+
+    def dg_wait_probe(self, flag, seconds: float):
+        """The bounded device wait on flag (a one-int device tensor)."""
+        _check(load().dg_wait_probe(self._h, _vp(flag), float(seconds)))
 
     def launches(self) -> int:
         return load().dg_last_launch_count(self._h)
@@ -627,11 +641,12 @@ class Graph:
         occ, conc, ms, nl, vp = C.c_int(), C.c_int(), C.c_float(), C.c_int(), C.c_int()
         _check(load().dg_graph_info(self._h, C.byref(occ), C.byref(conc), C.byref(ms), C.byref(nl), C.byref(vp)))
         tm = np.zeros(9, np.int32)
-        tr = C.c_int()
-        _check(load().dg_graph_tiles(self._h, _vp(tm), C.byref(tr)))
+        tr, pk = C.c_int(), C.c_int()
+        _check(load().dg_graph_tiles(self._h, _vp(tm), C.byref(tr), C.byref(pk)))
         return {"occ_cap": occ.value, "concurrent": bool(conc.value), "tuned_ms": ms.value, "launches": nl.value,
                 "volume_path": {0: "per-point", 1: "moments", 2: "exact-moments"}.get(vp.value, "per-point"),
-                "tile_tm": {f"p{p}": int(tm[p]) for p in range(9) if tm[p] != 0}, "tuner_trials": tr.value}
+                "tile_tm": {f"p{p}": int(tm[p]) for p in range(9) if tm[p] != 0}, "tuner_trials": tr.value,
+                "persistent": bool(pk.value)}
 
     def close(self):
         if getattr(self, "_h", None):

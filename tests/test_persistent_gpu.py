@@ -1,0 +1,146 @@
+"""The persistent pass (one launch; warps take moment tiles and row tiles
+from a work list; row tiles wait, bounded, for their elements' moment
+tiles): parity with the oracle and with the per-degree launches, batches
+bitwise equal to their members, recorded graphs, and the bounded wait's
+timeout reported through dg_sync without any fault."""
+import numpy as np
+import pytest
+
+from paper_2007_04881_gb300 import configs, dg
+
+from .helpers import compare, dg_problem, oracle_blocks
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 5e-5      # block max-norm relative, FP32 contractions against the FP64 oracle
+TOL32_RHS = 1e-4  # per-element load vector (sin source evaluated in FP32)
+
+
+@pytest.fixture(scope="module")
+def ctx(cuda):
+    import torch
+
+    from paper_2007_04881_gb300 import build as B
+
+    B.build()
+    c = dg.Context(0, torch.cuda.current_stream().cuda_stream)
+    yield c
+    c.close()
+
+
+def _step(ctx, mesh, persistent, prec=dg.DG_PREC_FP32):
+    import torch
+
+    ctx.dg_set_persistent(persistent)
+    try:
+        dt = torch.float64 if prec == dg.DG_PREC_FP64 else torch.float32
+        v = torch.full((mesh.nvals,), float("nan"), dtype=dt, device="cuda")
+        r = torch.full((mesh.ndofs,), float("nan"), dtype=dt, device="cuda")
+        mesh.dg_assemble_step(prec, v, r)
+        ctx.dg_sync()
+        return v.double().cpu().numpy(), r.double().cpu().numpy()
+    finally:
+        ctx.dg_set_persistent(False)
+
+
+@pytest.mark.parametrize("path", [1, 2, 0])
+def test_persistent_2d_vs_oracle_and_launches(ctx, path):
+    """Degrees 1..5 mixed, each volume path: every block against the oracle
+    at the FP32 tolerance, and the whole matrix against the per-degree
+    launches (relative Frobenius 1e-6)."""
+    w = configs.small2d(700, 61, 1, 5, b=(1.0, 0.5), c=1.0)
+    m = dg.Mesh(ctx, w.mesh, w.p, w.a, dg_problem(w))
+    ctx.dg_set_volume_path(path)
+    try:
+        vp, rp = _step(ctx, m, True)
+        vs, rs = _step(ctx, m, False)
+    finally:
+        ctx.dg_set_volume_path(1)
+    assert np.isfinite(vp).all() and np.isfinite(rp).all()
+    assert np.linalg.norm(vp - vs) <= 1e-6 * np.linalg.norm(vs)
+    assert np.linalg.norm(rp - rs) <= 1e-6 * np.linalg.norm(rs)
+    om, ob = oracle_blocks(w)
+    ed, eo, er = compare(dg.to_blocks(m, vp, rp), om, ob, w)
+    assert ed < TOL32 and eo < TOL32 and er < TOL32_RHS, (ed, eo, er)
+
+
+def test_persistent_3d_vs_oracle(ctx):
+    w = configs.small3d(8, 40, 62, 1, 3)
+    m = dg.Mesh(ctx, w.mesh, w.p, w.a, dg_problem(w))
+    vp, rp = _step(ctx, m, True)
+    vs, rs = _step(ctx, m, False)
+    assert np.linalg.norm(vp - vs) <= 1e-6 * np.linalg.norm(vs)
+    om, ob = oracle_blocks(w)
+    ed, eo, er = compare(dg.to_blocks(m, vp, rp), om, ob, w)
+    assert ed < TOL32 and eo < TOL32 and er < TOL32_RHS, (ed, eo, er)
+
+
+def test_persistent_batch_equals_members(ctx):
+    """A batch of meshes in one persistent launch: each member's rows are
+    bitwise those of the member assembled alone by the persistent pass."""
+    # degrees <= 4 throughout, so that the batch and every member run the
+    # same persistent kernel
+    members = [configs.small2d(n, 70 + k, p0, p1, b=(1.0, 0.5), c=1.0)
+               for k, (n, p0, p1) in enumerate([(90, 1, 1), (160, 2, 4), (60, 4, 4), (120, 1, 4), (45, 3, 3)])]
+    pb = dg_problem(members[0])
+    bm = dg.Mesh(ctx, None, problem=pb, members=[(w.mesh, w.p, w.a) for w in members])
+    eo, vo, do = bm.dg_batch_offsets()
+    vb, rb = _step(ctx, bm, True)
+    for k, w in enumerate(members):
+        m = dg.Mesh(ctx, w.mesh, w.p, w.a, pb)
+        v, r = _step(ctx, m, True)
+        assert np.array_equal(vb[vo[k]:vo[k + 1]], v), k
+        assert np.array_equal(rb[do[k]:do[k + 1]], r), k
+
+
+def test_persistent_graph_replay(ctx):
+    """The persistent pass recorded in a CUDA graph (flags and queue reset
+    by the graph itself) equals the direct pass bitwise on every replay."""
+    import torch
+
+    w = configs.small2d(500, 63, 1, 4, b=(1.0, 0.5), c=1.0)
+    m = dg.Mesh(ctx, w.mesh, w.p, w.a, dg_problem(w))
+    v_ref, r_ref = _step(ctx, m, True)
+    v = torch.zeros(m.nvals, dtype=torch.float32, device="cuda")
+    r = torch.zeros(m.ndofs, dtype=torch.float32, device="cuda")
+    ctx.dg_set_persistent(True)
+    try:
+        g = m.dg_graph_create(dg.DG_PREC_FP32, v, r, autotune=False)
+    finally:
+        ctx.dg_set_persistent(False)
+    assert g.dg_graph_info()["persistent"]
+    for _ in range(3):
+        v.zero_()
+        r.zero_()
+        g.dg_graph_launch()
+        ctx.dg_sync()
+        assert np.array_equal(v.double().cpu().numpy(), v_ref)
+        assert np.array_equal(r.double().cpu().numpy(), r_ref)
+    g.close()
+
+
+def test_bounded_wait_reports_timeout(ctx):
+    """The persistent pass's bounded wait on a flag nothing sets runs out
+    after its limit and dg_sync reports DG_ERR_TIMEOUT (the context stays
+    usable); on a set flag it returns at once and dg_sync is clean."""
+    import time
+
+    import torch
+
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    t0 = time.perf_counter()
+    ctx.dg_wait_probe(flag, 0.05)
+    with pytest.raises(dg.DGError) as ei:
+        ctx.dg_sync()
+    assert ei.value.code == dg.DG_ERR_TIMEOUT
+    assert time.perf_counter() - t0 >= 0.05
+    ctx.dg_sync()  # the status word was cleared
+    flag.fill_(1)
+    ctx.dg_wait_probe(flag, 5.0)
+    ctx.dg_sync()
+    # the context still assembles correctly after the timeout
+    w = configs.small2d(200, 64, 1, 4, b=(1.0, 0.5), c=1.0)
+    m = dg.Mesh(ctx, w.mesh, w.p, w.a, dg_problem(w))
+    vp, _ = _step(ctx, m, True)
+    vs, _ = _step(ctx, m, False)
+    assert np.linalg.norm(vp - vs) <= 1e-6 * np.linalg.norm(vs)
