@@ -433,10 +433,25 @@ def run_ours(args):
     upload_ms = 1e3 * (time.perf_counter() - t0)
     info = mesh.info
     pattern_ms = None
+    pattern = None
     if not isinstance(wl, _Batch):
         t0 = time.perf_counter()
         dg.dg_mesh_check(wl.mesh, wl.p, wl.a, pb)
         pattern_ms = 1e3 * (time.perf_counter() - t0)
+        # the same pattern built on the device (dg_set_pattern_device); the
+        # second upload is timed (the first loads the pattern kernels)
+        ctx.dg_set_pattern_device(True)
+        for _ in range(2):
+            md = dg.Mesh(ctx, wl.mesh, wl.p, wl.a, pb)
+            td = md.dg_mesh_timings()
+            md.close()
+        ctx.dg_set_pattern_device(False)
+        th = mesh.dg_mesh_timings()
+        pattern = {"host_plan_ms": th["pattern_ms"], "host_upload_ms": th["upload_ms"],
+                   "device_pattern_ms": td["pattern_ms"], "device_upload_ms": td["upload_ms"],
+                   "note": "pattern = faces, interfaces, block rows and offsets, half-face lists, work lists; "
+                           "host: the C++ plan on the host cores; device: the kernels of dg_set_pattern_device "
+                           "with their host copies; both include the host checks of the descriptor"}
 
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     prec = getattr(dg, PRECS[args.prec])
@@ -654,6 +669,7 @@ def run_ours(args):
         "other_forms": forms,
         "upload_ms": upload_ms,
         "pattern_ms": pattern_ms,
+        "pattern": pattern,
         "e2e": {"value": ws * info.ne / e2e_s, "unit": "elements/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "ms_per_step": 1e3 * e2e_s},
         "gpu_launches": launches_per_step * args.steps,

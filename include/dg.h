@@ -150,6 +150,35 @@ const char *dg_last_error(void);
 int dg_mesh_upload(dg_ctx *ctx, const dg_mesh_desc *desc, dg_mesh **out);
 int dg_mesh_free(dg_mesh *mesh);
 
+/* on != 0: the context's later dg_mesh_upload calls build the block pattern
+ * on the device (the paper builds its pattern with Thrust on the GPU, Sec. 3.4
+ * and Sec. 4.2, "indices" in Tables 1, 2, 5, 6): half faces keyed by their
+ * sorted vertex ids and matched after a stable LSD radix sort, faces ordered
+ * by (boundary, e0, e1), interfaces as runs of equal element pairs, block rows
+ * from a stable sort of the interfaces by their second element, offsets by
+ * exclusive scans, the work lists by stable radix sorts.  The descriptor's
+ * scalar checks stay on the host; the geometric checks (2D loop and fan
+ * areas, 3D tetrahedron volumes) and the face checks run on the device and
+ * give the same DG_ERR_MESH cases.  The arrays are bitwise those of the host
+ * build.  Partitions (dg_mesh_upload_part) and batches keep the host build.
+ * Off by default. */
+int dg_set_pattern_device(dg_ctx *ctx, int on);
+
+/* Wall times of the mesh's upload: the pattern build (host plan or device
+ * build, including its host copies) and the whole upload, in ms; on_device
+ * 1 when the pattern was built on the device.  Any output may be NULL. */
+int dg_mesh_timings(const dg_mesh *mesh, double *pattern_ms, double *upload_ms, int *on_device);
+
+/* Copy one of the mesh's internal arrays to host memory: "row_ptr", "col",
+ * "blk_off", "dof_off", "blk_if", "diag_blk", "blk_rec" (int4 per block),
+ * "f_e0", "f_e1", "f_v", "f_flip" (int8), "f_nq", "f_hf" ([2][nf]),
+ * "hf_ptr", "hf_face", "hf_side" (int8), "hf_qoff", "e_nqf", "if_e0",
+ * "if_e1", "if_fptr", "if_slot01", "if_slot10", "elem_perm", "if_perm",
+ * "sub_elem", "uvptr", "uvidx", "elem_pstart", "if_pstart" (9 ints each).
+ * *bytes (may be NULL) gets the array's size; host may be NULL to query it;
+ * DG_ERR_ARG for an unknown name or cap_bytes too small.  Synchronous. */
+int dg_mesh_array(const dg_mesh *mesh, const char *name, void *host, int64_t cap_bytes, int64_t *bytes);
+
 /* Host-only dry run of dg_mesh_upload: the same validation, face derivation
  * and BSR pattern, without touching a GPU.  Fills *info (may be NULL) and,
  * for non-NULL arrays sized from a previous call's info, row_ptr[ne+1],

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <chrono>
 #include <climits>
 #include <cstring>
 #include <numeric>
@@ -193,6 +194,7 @@ struct dg_ctx {
   int* status_dev = nullptr;  // bit 0: a bounded device wait ran out (read and cleared by dg_sync)
   long long wait_ns = 2000000000LL;  // bound of one device wait
   bool persist = false;  // untuned per-step passes and untuned graphs take the persistent pass
+  bool pattern_device = false;  // dg_mesh_upload builds the block pattern on the device
   std::vector<LaunchRec> recs;
   SideStreams streams;  // the direct launches' forked streams
   ~dg_ctx() {
@@ -309,6 +311,8 @@ struct dg_mesh {
   std::vector<double> vfma_h;  // algorithmic FMAs per volume point of each element
   std::vector<int> perm_fan;  // the sub-simplex-rule work list
   std::vector<int> perm_h;    // the current work list (host copy of perm_dev)
+  double pattern_ms = 0.0, upload_ms = 0.0;  // wall time of the pattern build and of the whole upload
+  bool pattern_on_device = false;
   // persistent pass: queue word, pad and the elements' moment flags
   // (zeroed before each launch), the work list of tiles and what it was built for
   int* pk_sync = nullptr;
@@ -563,7 +567,9 @@ int dg_mesh_free(dg_mesh* mesh) {
 // owned == nullptr: every element is assembled.  Otherwise only elements
 // with owned[e] != 0 get block rows, load-vector entries and work-list
 // entries; the others (the halo of a partition) only supply geometry.
-static int plan_mesh(const dg_mesh_desc* d, Plan& P, const int8_t* owned = nullptr) {
+// The descriptor's arguments and per-element scalars (the checks that need
+// no faces): sizes, pointers, problem data, elem_ptr, degrees, a, vertex ids.
+static int check_desc(const dg_mesh_desc* d) {
   if (!d) return fail(DG_ERR_ARG, "null mesh descriptor");
   const int dim = d->dim;
   if (dim != 2 && dim != 3) return fail(DG_ERR_ARG, "dim must be 2 or 3 (got %d)", dim);
@@ -585,6 +591,12 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P, const int8_t* owned = nullp
   const int nidx = d->elem_ptr[ne] * (dim == 2 ? 1 : 4);
   for (int i = 0; i < nidx; ++i)
     if (d->elem_idx[i] < 0 || d->elem_idx[i] >= nv) return fail(DG_ERR_MESH, "vertex index %d out of range", d->elem_idx[i]);
+  return DG_OK;
+}
+
+static int plan_mesh(const dg_mesh_desc* d, Plan& P, const int8_t* owned = nullptr) {
+  if (int rc = check_desc(d)) return rc;
+  const int dim = d->dim, nv = d->nv, ne = d->ne;
   const double* X[3] = {d->x, d->y, dim == 3 ? d->z : nullptr};
 
   // --- geometric validity (host, FP64)
@@ -1071,12 +1083,69 @@ int dg_mesh_check(const dg_mesh_desc* d, dg_bsr_info* info, int* row_ptr, int* c
 
 }  // extern "C"
 
+// The geometry records of a mesh (device, written by the geometry kernels).
+static int alloc_records(dg_mesh* m, int dim, int ne, int nv, int nsub, int nf, int nhf) {
+  DevMesh& dm = m->dm;
+  DevBuf& B = m->bufs;
+  int rc = DG_OK;
+  auto alloc_d = [&](double** p, size_t n) {
+    if (rc == DG_OK && B.alloc(p, n) != cudaSuccess) rc = fail(DG_ERR_OOM, "device allocation failed");
+  };
+  auto alloc_f = [&](float** p, size_t n) {
+    if (rc == DG_OK && B.alloc(p, n) != cudaSuccess) rc = fail(DG_ERR_OOM, "device allocation failed");
+  };
+  alloc_d(&dm.lo, (size_t)dim * ne);
+  alloc_d(&dm.L, (size_t)dim * ne);
+  alloc_d(&dm.cen, (size_t)dim * ne);
+  alloc_d(&dm.vol, ne);
+  alloc_d(&dm.h, ne);
+  alloc_d(&dm.pen, ne);
+  alloc_d(&dm.eg64, (size_t)elem_vals(dim) * ne);
+  alloc_f(&dm.eg32, (size_t)elem_vals(dim) * ne);
+  if (rc == DG_OK && B.alloc(&dm.xs2, (size_t)dim * nv) != cudaSuccess) rc = fail(DG_ERR_OOM, "device allocation failed");
+  alloc_f(&dm.gx32, (size_t)elem_vals(dim) * ne);
+  alloc_d(&dm.sg64, (size_t)sub_vals(dim) * nsub);
+  alloc_f(&dm.sg32, (size_t)sub_vals(dim) * nsub);
+  alloc_d(&dm.fs64, (size_t)2 * side_vals(dim) * nf);
+  alloc_d(&dm.fsc64, (size_t)3 * nf);
+  alloc_d(&dm.hfr64, (size_t)hf_rec_vals(dim) * nhf);
+  alloc_f(&dm.hfr32, (size_t)hf_rec_vals(dim) * nhf);
+  return rc;
+}
+
+// the problem data and the context's rule tables
+static void set_problem(dg_mesh* m, const dg_ctx* ctx, const dg_mesh_desc* d) {
+  DevMesh& dm = m->dm;
+  for (int q = 0; q < 3; ++q) dm.pb.b[q] = d->b[q];
+  if (d->dim == 2) dm.pb.b[2] = 0.0;
+  dm.pb.c = d->c;
+  dm.pb.source = d->source;
+  for (int q = 0; q < 20; ++q) dm.pb.poly[q] = d->poly[q];
+  dm.pb.c_sigma = d->c_sigma;
+  dm.pb.round_copies();
+  dm.rt = ctx->rt[d->dim];
+}
+
+// algorithmic FMAs per volume point of each element (the accounting of the
+// learned rules' work lists)
+static void set_vfma(dg_mesh* m, const dg_mesh_desc* d) {
+  const int dim = d->dim, ne = d->ne;
+  const bool adv = d->b[0] != 0.0 || d->b[1] != 0.0 || (dim == 3 && d->b[2] != 0.0) || d->c != 0.0;
+  m->vfma_h.resize(ne);
+  for (int e = 0; e < ne; ++e) {
+    const double n = nbasis(dim, d->p[e]);
+    m->vfma_h[e] = dim * n * (n + 1) / 2 + (adv ? n * n + n * (dim + 1) : 0.0) + n * dim * dim + 5.0 * dim * d->p[e] + n;
+  }
+}
+
 static int upload_impl(dg_ctx* ctx, const dg_mesh_desc* d, const int8_t* owned, dg_mesh** out) {
   if (!ctx || !d || !out) return fail(DG_ERR_ARG, "dg_mesh_upload: null argument");
   *out = nullptr;
+  const auto t_start = std::chrono::steady_clock::now();
   Plan P;
   int prc = plan_mesh(d, P, owned);
   if (prc != DG_OK) return prc;
+  const double plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   const int dim = d->dim, nv = d->nv, ne = d->ne;
   const int nidx = d->elem_ptr[ne] * (dim == 2 ? 1 : 4);
   const double* X[3] = {d->x, d->y, dim == 3 ? d->z : nullptr};
@@ -1181,56 +1250,23 @@ static int upload_impl(dg_ctx* ctx, const dg_mesh_desc* d, const int8_t* owned, 
     delete m;
     return rc;
   }
-  auto alloc_d = [&](double** p, size_t n) {
-    if (rc == DG_OK && B.alloc(p, n) != cudaSuccess) rc = fail(DG_ERR_OOM, "device allocation failed");
-  };
-  auto alloc_f = [&](float** p, size_t n) {
-    if (rc == DG_OK && B.alloc(p, n) != cudaSuccess) rc = fail(DG_ERR_OOM, "device allocation failed");
-  };
-  alloc_d(&dm.lo, (size_t)dim * ne);
-  alloc_d(&dm.L, (size_t)dim * ne);
-  alloc_d(&dm.cen, (size_t)dim * ne);
-  alloc_d(&dm.vol, ne);
-  alloc_d(&dm.h, ne);
-  alloc_d(&dm.pen, ne);
-  alloc_d(&dm.eg64, (size_t)elem_vals(dim) * ne);
-  alloc_f(&dm.eg32, (size_t)elem_vals(dim) * ne);
-  if (rc == DG_OK && B.alloc(&dm.xs2, (size_t)dim * nv) != cudaSuccess) rc = fail(DG_ERR_OOM, "device allocation failed");
-  alloc_f(&dm.gx32, (size_t)elem_vals(dim) * ne);
-  alloc_d(&dm.sg64, (size_t)sub_vals(dim) * nsub);
-  alloc_f(&dm.sg32, (size_t)sub_vals(dim) * nsub);
-  alloc_d(&dm.fs64, (size_t)2 * side_vals(dim) * nf);
-  alloc_d(&dm.fsc64, (size_t)3 * nf);
-  alloc_d(&dm.hfr64, (size_t)hf_rec_vals(dim) * nhf);
-  alloc_f(&dm.hfr32, (size_t)hf_rec_vals(dim) * nhf);
+  rc = alloc_records(m, dim, ne, nv, nsub, nf, nhf);
   if (rc != DG_OK) {
     delete m;
     return rc;
   }
-  for (int q = 0; q < 3; ++q) dm.pb.b[q] = d->b[q];
-  if (dim == 2) dm.pb.b[2] = 0.0;
-  dm.pb.c = d->c;
-  dm.pb.source = d->source;
-  for (int q = 0; q < 20; ++q) dm.pb.poly[q] = d->poly[q];
-  dm.pb.c_sigma = d->c_sigma;
-  dm.pb.round_copies();
-  dm.rt = ctx->rt[dim];
+  set_problem(m, ctx, d);
 
   fill_info(d, P, m->info);
   m->p_h.assign(d->p, d->p + ne);
   m->nqf_h = e_nqf;
   m->nvq_h.resize(ne);
-  m->vfma_h.resize(ne);
-  {
-    const bool adv = d->b[0] != 0.0 || d->b[1] != 0.0 || (dim == 3 && d->b[2] != 0.0) || d->c != 0.0;
-    for (int e = 0; e < ne; ++e) {
-      int qt = 1;
-      for (int q = 0; q < dim; ++q) qt *= d->p[e] + 2;
-      m->nvq_h[e] = (d->elem_ptr[e + 1] - d->elem_ptr[e]) * qt;
-      const double n = nbasis(dim, d->p[e]);
-      m->vfma_h[e] = dim * n * (n + 1) / 2 + (adv ? n * n + n * (dim + 1) : 0.0) + n * dim * dim + 5.0 * dim * d->p[e] + n;
-    }
+  for (int e = 0; e < ne; ++e) {
+    int qt = 1;
+    for (int q = 0; q < dim; ++q) qt *= d->p[e] + 2;
+    m->nvq_h[e] = (d->elem_ptr[e + 1] - d->elem_ptr[e]) * qt;
   }
+  set_vfma(m, d);
   m->perm_fan = elem_perm;
   m->perm_h = elem_perm;
   m->perm_dev = const_cast<int*>(dm.elem_perm);
@@ -1247,13 +1283,221 @@ static int upload_impl(dg_ctx* ctx, const dg_mesh_desc* d, const int8_t* owned, 
     delete m;
     return fail(DG_ERR_CUDA, "geometry kernels: %s", cudaGetErrorString(ce));
   }
+  m->pattern_ms = plan_ms;
+  m->upload_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  *out = m;
+  return DG_OK;
+}
+
+// dg_mesh_upload with the block pattern built on the device
+// (dg_pattern.cu): the descriptor's scalar checks on the host, the inputs
+// uploaded, then faces, interfaces, block rows, half-face lists, work lists
+// and the accounting by kernels; the geometry kernels follow as on the host
+// path.  The arrays equal the host plan's bit for bit.
+static int upload_impl_device(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
+  if (!ctx || !d || !out) return fail(DG_ERR_ARG, "dg_mesh_upload: null argument");
+  *out = nullptr;
+  const auto t_start = std::chrono::steady_clock::now();
+  if (int rc = check_desc(d)) return rc;
+  const int dim = d->dim, nv = d->nv, ne = d->ne;
+  const int nidx = d->elem_ptr[ne] * (dim == 2 ? 1 : 4);
+  dg_mesh* m = new (std::nothrow) dg_mesh();
+  if (!m) return fail(DG_ERR_OOM, "out of host memory");
+  m->ctx = ctx;
+  DevMesh& dm = m->dm;
+  DevBuf& B = m->bufs;
+  int rc = DG_OK;
+  cudaSetDevice(ctx->device);
+  for (int q = 0; q < 3; ++q) {
+    dm.X[q] = nullptr;
+    if (q < dim) {
+      const double* src = q == 0 ? d->x : q == 1 ? d->y : d->z;
+      std::vector<double> v(src, src + nv);
+      const double* p = nullptr;
+      if (rc == DG_OK) rc = upload(B, &p, v);
+      dm.X[q] = p;
+      m->X[q] = const_cast<double*>(p);
+    }
+  }
+  {
+    std::vector<int> eptr(d->elem_ptr, d->elem_ptr + ne + 1), eidx(d->elem_idx, d->elem_idx + nidx), pv(d->p, d->p + ne);
+    if (rc == DG_OK) rc = upload(B, &dm.eptr, eptr);
+    if (rc == DG_OK) rc = upload(B, &dm.eidx, eidx);
+    if (rc == DG_OK) rc = upload(B, &dm.p, pv);
+    std::vector<double> av(d->a, d->a + ne);
+    if (rc == DG_OK) rc = upload(B, &dm.a, av);
+    m->a = const_cast<double*>(dm.a);
+  }
+  if (rc != DG_OK) {
+    delete m;
+    return rc;
+  }
+  const auto t_pat = std::chrono::steady_clock::now();
+  DevPattern P;
+  std::string msg;
+  auto alloc = [&](size_t bytes) -> void* {
+    char* q = nullptr;
+    return B.alloc(&q, bytes) == cudaSuccess ? static_cast<void*>(q) : nullptr;
+  };
+  rc = build_pattern_device(d, dm.eptr, dm.eidx, dm.p, dm.X, alloc, ctx->stream, &P, &msg);
+  if (rc != DG_OK) {
+    delete m;
+    return fail(rc, "dg_mesh_upload (device pattern): %s", msg.empty() ? "allocation failed" : msg.c_str());
+  }
+  m->pattern_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_pat).count();
+  m->pattern_on_device = true;
+  dm.dim = dim;
+  dm.nv = nv;
+  dm.ne = ne;
+  dm.nsub = P.nsub;
+  dm.nf = P.nf;
+  dm.ni = P.ni;
+  dm.nhf = P.nhf;
+  dm.uvptr = P.uvptr;
+  dm.uvidx = P.uvidx;
+  dm.sub_elem = P.sub_elem;
+  dm.sub_loc = nullptr;
+  dm.f_e0 = P.f_e0;
+  dm.f_e1 = P.f_e1;
+  dm.f_v = P.f_v;
+  dm.f_flip = P.f_flip;
+  dm.f_nq = P.f_nq;
+  dm.f_hf = P.f_hf;
+  dm.hf_ptr = P.hf_ptr;
+  dm.hf_face = P.hf_face;
+  dm.hf_side = P.hf_side;
+  dm.hf_qoff = P.hf_qoff;
+  dm.e_nqf = P.e_nqf;
+  dm.if_e0 = P.if_e0;
+  dm.if_e1 = P.if_e1;
+  dm.if_fptr = P.if_fptr;
+  dm.if_slot01 = P.slot01;
+  dm.if_slot10 = P.slot10;
+  dm.row_ptr = P.row_ptr;
+  dm.col = P.col;
+  dm.blk_if = P.blk_if;
+  dm.blk_off = P.blk_off;
+  dm.diag_blk = P.diag_blk;
+  dm.dof_off = P.dof_off;
+  dm.blk_rec = P.blk_rec;
+  dm.elem_perm = P.elem_perm;
+  dm.if_perm = P.if_perm;
+  for (int q = 0; q <= 8; ++q) {
+    dm.elem_pstart[q] = P.elem_pstart[q];
+    dm.if_pstart[q] = P.if_pstart[q];
+  }
+  dm.nmax = 0;
+  for (int e = 0; e < ne; ++e) dm.nmax = std::max(dm.nmax, nbasis(dim, d->p[e]));
+  m->row_ptr = std::move(P.h_row_ptr);
+  m->col = std::move(P.h_col);
+  m->blk_off = std::move(P.h_blk_off);
+  m->dof_off = std::move(P.h_dof_off);
+  std::memcpy(m->flops, P.flops, sizeof P.flops);
+  std::memcpy(m->words, P.words, sizeof P.words);
+  std::memcpy(m->mom_exec, P.mom_exec, sizeof P.mom_exec);
+  std::memcpy(m->mom_pt, P.mom_pt, sizeof P.mom_pt);
+  rc = alloc_records(m, dim, ne, nv, P.nsub, P.nf, P.nhf);
+  if (rc != DG_OK) {
+    delete m;
+    return rc;
+  }
+  set_problem(m, ctx, d);
+  m->info.ne = ne;
+  m->info.nnzb = P.nnzb;
+  m->info.nvals = P.nvals;
+  m->info.ndofs = P.ndofs;
+  m->info.nfaces = P.nf;
+  m->info.ninterfaces = P.ni;
+  m->info.nbfaces = P.nf - P.nint;
+  m->info.nsub = P.nsub;
+  m->info.nqvol = P.nqvol;
+  m->info.nqface = P.nqface;
+  m->p_h.assign(d->p, d->p + ne);
+  m->nqf_h = P.h_e_nqf;
+  m->nvq_h = P.h_nvq;
+  set_vfma(m, d);
+  m->perm_fan = P.h_perm;
+  m->perm_h = P.h_perm;
+  m->perm_dev = P.elem_perm;
+  dm.lq_ok = nullptr;
+  dm.lq64 = nullptr;
+  dm.lq32 = nullptr;
+  launch_geometry(dm, ctx->stream);
+  cudaError_t ce = cudaGetLastError();
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+  if (ce != cudaSuccess) {
+    delete m;
+    return fail(DG_ERR_CUDA, "geometry kernels: %s", cudaGetErrorString(ce));
+  }
+  m->upload_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   *out = m;
   return DG_OK;
 }
 
 extern "C" {
 
-int dg_mesh_upload(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) { return upload_impl(ctx, d, nullptr, out); }
+int dg_mesh_upload(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
+  if (ctx && ctx->pattern_device) return upload_impl_device(ctx, d, out);
+  return upload_impl(ctx, d, nullptr, out);
+}
+
+int dg_mesh_array(const dg_mesh* mesh, const char* name, void* host, int64_t cap_bytes, int64_t* bytes) {
+  if (!mesh || !name) return fail(DG_ERR_ARG, "dg_mesh_array: null argument");
+  const DevMesh& m = mesh->dm;
+  const int ne = m.ne, nf = m.nf, ni = m.ni, nhf = m.nhf, nnzb = mesh->info.nnzb, dim = m.dim;
+  struct A {
+    const char* n;
+    const void* p;
+    int64_t b;
+  };
+  const int nuv = dim == 2 ? mesh->info.nsub : (int)0;
+  int nuv3 = 0;
+  if (dim == 3) cudaMemcpy(&nuv3, m.uvptr + ne, sizeof(int), cudaMemcpyDeviceToHost);
+  const A tab[] = {
+      {"row_ptr", m.row_ptr, 4LL * (ne + 1)},    {"col", m.col, 4LL * nnzb},
+      {"blk_off", m.blk_off, 8LL * (nnzb + 1)},  {"dof_off", m.dof_off, 8LL * (ne + 1)},
+      {"blk_if", m.blk_if, 4LL * nnzb},          {"diag_blk", m.diag_blk, 4LL * ne},
+      {"blk_rec", m.blk_rec, 16LL * nnzb},       {"f_e0", m.f_e0, 4LL * nf},
+      {"f_e1", m.f_e1, 4LL * nf},                {"f_v", m.f_v, 4LL * dim * nf},
+      {"f_flip", m.f_flip, 1LL * nf},            {"f_nq", m.f_nq, 4LL * nf},
+      {"f_hf", m.f_hf, 8LL * nf},                {"hf_ptr", m.hf_ptr, 4LL * (ne + 1)},
+      {"hf_face", m.hf_face, 4LL * nhf},         {"hf_side", m.hf_side, 1LL * nhf},
+      {"hf_qoff", m.hf_qoff, 4LL * nhf},         {"e_nqf", m.e_nqf, 4LL * ne},
+      {"if_e0", m.if_e0, 4LL * ni},              {"if_e1", m.if_e1, 4LL * ni},
+      {"if_fptr", m.if_fptr, 4LL * (ni + 1)},    {"if_slot01", m.if_slot01, 4LL * ni},
+      {"if_slot10", m.if_slot10, 4LL * ni},      {"elem_perm", m.elem_perm, 4LL * ne},
+      {"if_perm", m.if_perm, 4LL * ni},          {"sub_elem", m.sub_elem, 4LL * mesh->info.nsub},
+      {"uvptr", m.uvptr, 4LL * (ne + 1)},        {"uvidx", m.uvidx, 4LL * (dim == 2 ? nuv : nuv3)},
+      {"elem_pstart", nullptr, 4LL * 9},         {"if_pstart", nullptr, 4LL * 9},
+  };
+  for (const A& a : tab) {
+    if (std::strcmp(a.n, name) != 0) continue;
+    if (bytes) *bytes = a.b;
+    if (!host) return DG_OK;
+    if (cap_bytes < a.b) return fail(DG_ERR_ARG, "dg_mesh_array: %s needs %lld bytes", name, (long long)a.b);
+    if (!a.p) {
+      std::memcpy(host, std::strcmp(name, "elem_pstart") == 0 ? m.elem_pstart : m.if_pstart, 36);
+      return DG_OK;
+    }
+    DG_CUDA_TRY(cudaMemcpy(host, a.p, a.b, cudaMemcpyDeviceToHost));
+    return DG_OK;
+  }
+  return fail(DG_ERR_ARG, "dg_mesh_array: unknown array %s", name);
+}
+
+int dg_set_pattern_device(dg_ctx* ctx, int on) {
+  if (!ctx) return fail(DG_ERR_ARG, "dg_set_pattern_device: null context");
+  ctx->pattern_device = on != 0;
+  return DG_OK;
+}
+
+int dg_mesh_timings(const dg_mesh* mesh, double* pattern_ms, double* upload_ms, int* on_device) {
+  if (!mesh) return fail(DG_ERR_ARG, "dg_mesh_timings: null mesh");
+  if (pattern_ms) *pattern_ms = mesh->pattern_ms;
+  if (upload_ms) *upload_ms = mesh->upload_ms;
+  if (on_device) *on_device = mesh->pattern_on_device ? 1 : 0;
+  return DG_OK;
+}
 
 int dg_bsr_layout(const dg_mesh* mesh, dg_bsr_info* out) {
   if (!mesh || !out) return fail(DG_ERR_ARG, "dg_bsr_layout: null argument");

@@ -4,6 +4,9 @@
 #pragma once
 
 #include <cstdint>
+#include <functional>
+#include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -272,6 +275,27 @@ int persist_layout(int dim, int* mom_ok_mask, int* gmom, int* grow);
 // that runs out sets bit 0 of *status
 void launch_wait_probe(const int* flag, int* status, long long limit_ns, cudaStream_t st);
 
+// The block-sparse pattern built on the device (dg_pattern.cu): the same
+// arrays as the host pass plan_mesh, in device memory the caller's alloc
+// provides, plus host copies of what the host keeps.
+struct DevPattern {
+  int *sub_elem = nullptr, *f_e0 = nullptr, *f_e1 = nullptr, *f_v = nullptr, *f_nq = nullptr, *f_hf = nullptr;
+  int8_t *f_flip = nullptr, *hf_side = nullptr;
+  int *hf_ptr = nullptr, *hf_face = nullptr, *hf_qoff = nullptr, *e_nqf = nullptr;
+  int *if_e0 = nullptr, *if_e1 = nullptr, *if_fptr = nullptr, *slot01 = nullptr, *slot10 = nullptr;
+  int *row_ptr = nullptr, *col = nullptr, *blk_if = nullptr, *diag_blk = nullptr;
+  int64_t *blk_off = nullptr, *dof_off = nullptr;
+  int4* blk_rec = nullptr;
+  const int *uvptr = nullptr, *uvidx = nullptr;
+  int *elem_perm = nullptr, *if_perm = nullptr;
+  int nsub = 0, nf = 0, nint = 0, ni = 0, nhf = 0, nnzb = 0;
+  int64_t nvals = 0, ndofs = 0, nqvol = 0, nqface = 0;
+  int elem_pstart[9] = {0}, if_pstart[9] = {0};
+  double flops[3][9] = {{0}}, words[3][9] = {{0}}, mom_exec[9] = {0}, mom_pt[9] = {0};
+  std::vector<int> h_row_ptr, h_col, h_e_nqf, h_nvq, h_perm;
+  std::vector<int64_t> h_blk_off, h_dof_off;
+};
+
 // learned quadrature (dg_learned.cu)
 void lq_prepare(const DevMesh& m, double* mom, double* mmom, void* feat, int* elig, cudaStream_t st);
 void lq_gn(const DevMesh& m, const double* mom, const double* mmom, const int* elig, const float* init, int iters,
@@ -279,6 +303,12 @@ void lq_gn(const DevMesh& m, const double* mom, const double* mmom, const int* e
 void lq_install(const DevMesh& m, const double* rule, const int* ok, double* lq64, float* lq32, int* lq_ok,
                 cudaStream_t st);
 void lq_targets(int ne, const double* rule, const double* mmom, float* tgt, cudaStream_t st);
+
+}  // namespace dg
+#include "../../include/dg.h"
+namespace dg {
+int build_pattern_device(const dg_mesh_desc* d, const int* eptr, const int* eidx, const int* p, const double* const* X,
+                         const std::function<void*(size_t)>& alloc, cudaStream_t st, DevPattern* P, std::string* msg);
 
 // Host: collapsed reference rule on the d-simplex with n Gauss points per
 // direction, packed as [point][d+1] = (coordinates, weight); d = 1 gives the

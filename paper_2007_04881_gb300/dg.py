@@ -126,6 +126,9 @@ def load() -> C.CDLL:
     lib.dg_graph_tiles.argtypes = [V, V, V, V]
     lib.dg_set_wait_limit.argtypes = [V, C.c_double]
     lib.dg_set_persistent.argtypes = [V, C.c_int]
+    lib.dg_set_pattern_device.argtypes = [V, C.c_int]
+    lib.dg_mesh_timings.argtypes = [V, V, V, V]
+    lib.dg_mesh_array.argtypes = [V, C.c_char_p, V, C.c_int64, C.POINTER(C.c_int64)]
     lib.dg_wait_probe.argtypes = [V, V, C.c_double]
     lib.dg_set_tile_variants.argtypes = [V, V]
     lib.dg_volume_noalloc.argtypes = [V, C.c_int, C.c_int, C.c_int, C.c_int, V, V, C.c_int, C.c_int, V, V, V,
@@ -180,7 +183,7 @@ EXPORTS = (
     "dg_slab_offsets", "dg_slab_layout", "dg_assemble_slab", "dg_slab_trace", "dg_assemble_varcoef",
     "dg_mlp_save", "dg_mlp_load", "dg_quad_learn", "dg_assemble_batch", "dg_graph_tiles",
     "dg_set_tile_variants", "dg_set_wait_limit", "dg_wait_probe",
-    "dg_set_persistent",
+    "dg_set_persistent", "dg_set_pattern_device", "dg_mesh_timings", "dg_mesh_array",
 )
 
 
@@ -247,6 +250,9 @@ class Context:
         """Row-kernel tile variant per degree (9 ints, or None for the defaults)."""
         v = None if variants is None else np.ascontiguousarray(variants, dtype=np.int32)
         _check(load().dg_set_tile_variants(self._h, _vp(v)))
+
+    def dg_set_pattern_device(self, on: bool):
+        _check(load().dg_set_pattern_device(self._h, int(bool(on))))
 
     def dg_set_persistent(self, on: bool):
         _check(load().dg_set_persistent(self._h, int(bool(on))))
@@ -457,6 +463,20 @@ class Mesh:
         do = np.zeros(n.value + 1, np.int64)
         _check(load().dg_batch_offsets(self._h, None, _vp(eo), _vp(vo), _vp(do)))
         return eo, vo, do
+
+    def dg_mesh_timings(self):
+        pm, um, od = C.c_double(), C.c_double(), C.c_int()
+        _check(load().dg_mesh_timings(self._h, C.byref(pm), C.byref(um), C.byref(od)))
+        return {"pattern_ms": pm.value, "upload_ms": um.value, "on_device": bool(od.value)}
+
+    def dg_mesh_array(self, name: str) -> np.ndarray:
+        """A copy of one of the mesh's internal arrays (dg_mesh_array)."""
+        nb = C.c_int64()
+        _check(load().dg_mesh_array(self._h, name.encode(), None, 0, C.byref(nb)))
+        dt = {"f_flip": np.int8, "hf_side": np.int8, "blk_off": np.int64, "dof_off": np.int64}.get(name, np.int32)
+        out = np.zeros(int(nb.value) // np.dtype(dt).itemsize, dt)
+        _check(load().dg_mesh_array(self._h, name.encode(), _vp(out), int(nb.value), None))
+        return out
 
     def dg_graph_create(self, prec: int, vals, rhs=None, autotune: bool = True) -> "Graph":
         h = C.c_void_p()

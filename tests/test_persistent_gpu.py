@@ -64,12 +64,32 @@ def test_persistent_2d_vs_oracle_and_launches(ctx, path):
     assert ed < TOL32 and eo < TOL32 and er < TOL32_RHS, (ed, eo, er)
 
 
-def test_persistent_3d_vs_oracle(ctx):
+def _where(m, w, vp, vs):
+    """Largest relative difference per (degree, diagonal / off-diagonal)."""
+    bp, bs = dg.to_blocks(m, vp), dg.to_blocks(m, vs)
+    out = {}
+    for e in range(m.ne):
+        d = np.abs(bp["diag"][e] - bs["diag"][e]).max() / np.abs(bs["diag"][e]).max()
+        k = ("diag", int(w.p[e]))
+        out[k] = max(out.get(k, 0.0), float(d))
+    for (r, c), blk in bs["off"].items():
+        d = np.abs(bp["off"][(r, c)] - blk).max() / max(np.abs(blk).max(), 1e-300)
+        k = ("off", int(w.p[r]))
+        out[k] = max(out.get(k, 0.0), float(d))
+    return {k: f"{v:.1e}" for k, v in sorted(out.items())}
+
+
+@pytest.mark.parametrize("path", [1, 0])
+def test_persistent_3d_vs_oracle(ctx, path):
     w = configs.small3d(8, 40, 62, 1, 3)
     m = dg.Mesh(ctx, w.mesh, w.p, w.a, dg_problem(w))
-    vp, rp = _step(ctx, m, True)
-    vs, rs = _step(ctx, m, False)
-    assert np.linalg.norm(vp - vs) <= 1e-6 * np.linalg.norm(vs)
+    ctx.dg_set_volume_path(path)
+    try:
+        vp, rp = _step(ctx, m, True)
+        vs, rs = _step(ctx, m, False)
+    finally:
+        ctx.dg_set_volume_path(1)
+    assert np.linalg.norm(vp - vs) <= 1e-6 * np.linalg.norm(vs), _where(m, w, vp, vs)
     om, ob = oracle_blocks(w)
     ed, eo, er = compare(dg.to_blocks(m, vp, rp), om, ob, w)
     assert ed < TOL32 and eo < TOL32 and er < TOL32_RHS, (ed, eo, er)
