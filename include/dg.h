@@ -386,7 +386,9 @@ int dg_graph_info(const dg_graph *graph, int *occ_cap, int *concurrent, float *t
  * the diagonal blocks and load vector its elements' moment tiles wrote: it
  * waits for their flags, a wait bounded in wall time (dg_set_wait_limit); a
  * wait that runs out skips those additions and makes the next dg_sync return
- * DG_ERR_TIMEOUT. */
+ * DG_ERR_TIMEOUT.  The work list of each volume path is kept with the mesh
+ * (recorded graphs refer to it); the flags are the mesh's, so persistent
+ * passes of one mesh must not overlap on the GPU (one stream, or events). */
 int dg_graph_tiles(const dg_graph *graph, int *tile_tm, int *trials, int *persistent);
 int dg_graph_free(dg_graph *graph);
 
@@ -615,6 +617,15 @@ int dg_slab_layout(const dg_mesh *mesh, int space, int64_t *nvals, int64_t *ndof
  * DG_ERR_ARG.  Asynchronous on the context stream. */
 int dg_assemble_slab(dg_ctx *ctx, dg_mesh *mesh, int prec, int space, double t0, double t1,
                      const void *u_prev, void *vals, void *rhs);
+
+/* The slab step of dg_assemble_slab (same arguments; vals, rhs and u_prev
+ * fixed for the graph's life) recorded as one CUDA graph: the spatial and
+ * mass passes with their degree groups on forked streams, the expansion and
+ * the load vector.  Replay with dg_graph_launch, free with dg_graph_free.
+ * The scratch of the slab pass is allocated before the capture, so the call
+ * must precede any stream capture by the caller. */
+int dg_slab_graph_create(dg_ctx *ctx, dg_mesh *mesh, int prec, int space, double t0, double t1, const void *u_prev,
+                         void *vals, void *rhs, dg_graph **out);
 
 /* The trace U(t1-) of a slab solution in the spatial basis:
  *   u_end_j = sum_k U(k, j) T_k(t1),  T_k(t1) = sqrt((2k+1)/tau),

@@ -316,8 +316,15 @@ struct dg_mesh {
   // persistent pass: queue word, pad and the elements' moment flags
   // (zeroed before each launch), the work list of tiles and what it was built for
   int* pk_sync = nullptr;
-  int4* pk_items = nullptr;
-  int pk_nitems = 0, pk_key = -1, pk_cap = 0;
+  // one work list per moment mask, kept for the mesh's life (recorded graphs
+  // hold their list's address); retired lists were built for an earlier
+  // element work list (learned rules installed or cleared)
+  struct PkList {
+    int key;
+    int4* items;
+    int n;
+  };
+  std::vector<PkList> pk_lists, pk_retired;
   // learned quadrature (2D)
   double *lq_mom = nullptr, *lq_mmom = nullptr, *lq_rule = nullptr, *lq64 = nullptr;
   float *lq32 = nullptr, *lq_resid = nullptr, *lq_out = nullptr;
@@ -335,9 +342,11 @@ struct dg_mesh {
   ~dg_mesh() {
     if (h_vals) cudaFree(h_vals);
     if (h_rhs) cudaFree(h_rhs);
-    void* q[] = {lq_mom, lq_mmom, lq_rule, lq64, lq32, lq_resid, lq_elig, lq_ok, lq_okm, lq_feat, lq_out, pk_sync, pk_items};
+    void* q[] = {lq_mom, lq_mmom, lq_rule, lq64, lq32, lq_resid, lq_elig, lq_ok, lq_okm, lq_feat, lq_out, pk_sync};
     for (void* x : q)
       if (x) cudaFree(x);
+    for (auto& l : pk_lists) cudaFree(l.items);
+    for (auto& l : pk_retired) cudaFree(l.items);
   }
 };
 
@@ -1808,18 +1817,28 @@ int dg_slab_layout(const dg_mesh* mesh, int space, int64_t* nvals, int64_t* ndof
   return DG_OK;
 }
 
-int dg_assemble_slab(dg_ctx* ctx, dg_mesh* mesh, int prec, int space, double t0, double t1, const void* u_prev,
-                     void* vals, void* rhs) {
-  if (!ctx || !mesh || !vals) return fail(DG_ERR_ARG, "dg_assemble_slab: null argument");
+static int slab_check(dg_ctx* ctx, dg_mesh* mesh, int prec, int space, double t0, double t1, void* vals,
+                      const char* who) {
+  if (!ctx || !mesh || !vals) return fail(DG_ERR_ARG, "%s: null argument", who);
   if (prec != DG_PREC_FP64 && prec != DG_PREC_FP32)
-    return fail(DG_ERR_ARG, "dg_assemble_slab: precision %d (DG_PREC_FP64 or DG_PREC_FP32)", prec);
-  if (!std::isfinite(t0) || !std::isfinite(t1) || !(t1 > t0))
-    return fail(DG_ERR_ARG, "dg_assemble_slab: the slab needs finite t0 < t1");
-  int rc = slab_prepare(ctx, mesh, space, "dg_assemble_slab");
-  if (rc != DG_OK) return rc;
+    return fail(DG_ERR_ARG, "%s: precision %d (DG_PREC_FP64 or DG_PREC_FP32)", who, prec);
+  if (!std::isfinite(t0) || !std::isfinite(t1) || !(t1 > t0)) return fail(DG_ERR_ARG, "%s: the slab needs finite t0 < t1", who);
+  return slab_prepare(ctx, mesh, space, who);
+}
+
+// One slab step on stream st: the spatial pass (B, l) and the mass pass (M),
+// each with its degree groups on forked streams (ss), then the expansion and
+// the load vector.  Everything allocated beforehand (slab_prepare), so the
+// step can be captured.
+static int issue_slab(dg_ctx* ctx, dg_mesh* mesh, int prec, int space, double t0, double t1, const void* u_prev,
+                      void* vals, void* rhs, cudaStream_t st, SideStreams* ss) {
+  int occ = 0, path = -1;
+  bool conc = false;
+  const int* tiles = nullptr;
+  step_shape(ctx, mesh, prec, &occ, &conc, &path, &tiles);
   // B and l: the spatial pass
-  rc = run_assembly(ctx, mesh, prec, kModeVol | kModeFace | (rhs ? kModeRhs : 0), mesh->slab_B,
-                    rhs ? mesh->slab_l : nullptr, true);
+  int rc = run_assembly(ctx, mesh, prec, kModeVol | kModeFace | (rhs ? kModeRhs : 0), mesh->slab_B,
+                        rhs ? mesh->slab_l : nullptr, true, true, st, false, occ, true, path, ss, tiles);
   if (rc != DG_OK) return rc;
   int n = ctx->last_launches;
   // M: the volume pass of the same rules with a = 0, b = 0, c = 1
@@ -1829,26 +1848,78 @@ int dg_assemble_slab(dg_ctx* ctx, dg_mesh* mesh, int prec, int space, double t0,
   mm.pb.round_copies();
   mm.a = mesh->slab_zero_a;
   LaunchOpts lo;
-  lo.vol_moments = ctx->vol_moments && !mesh->dm.lq_ok;
-  lo.vol_exact = lo.vol_moments && ctx->vol_exact;
-  for (int p = 0; p < 9; ++p) lo.pst[p] = ctx->stream;
+  lo.vol_moments = path >= 0 ? path >= 1 : ctx->vol_moments && !mesh->dm.lq_ok;
+  lo.vol_exact = lo.vol_moments && (path >= 0 ? path == 2 : ctx->vol_exact);
+  DG_CUDA_TRY(ss->ensure());
+  DG_CUDA_TRY(cudaEventRecord(ss->fork, st));
+  for (int i = 0; i < 4; ++i) DG_CUDA_TRY(cudaStreamWaitEvent(ss->side[i], ss->fork, 0));
+  for (int p = 0; p < 9; ++p) {
+    lo.pst[p] = ss->side[(8 - p) % 4];
+    lo.tile[p] = tiles ? tiles[p] : 0;
+  }
   n += dispatch_rows(mm, prec, kModeVol, mesh->slab_M, nullptr, ctx->sm_count, lo, &ctx->tracer);
+  for (int i = 0; i < 4; ++i) {
+    DG_CUDA_TRY(cudaEventRecord(ss->join[i], ss->side[i]));
+    DG_CUDA_TRY(cudaStreamWaitEvent(st, ss->join[i], 0));
+  }
   DG_CUDA_TRY(cudaGetLastError());
   const SlabPattern sp = slab_pattern(mesh, space);
   const SlabTimes<double> tt = slab_time_data(t0, t1);
   const bool fp32 = prec == DG_PREC_FP32;
   // per-launch timing records (no algorithmic flop or byte counts: kind kKinds)
   Tracer* tr = &ctx->tracer;
-  tr->begin(fp32 ? "slab_matrix_f32" : "slab_matrix_f64", kKinds, 0, fp32 ? 4 : 8, ctx->stream);
-  n += launch_slab_matrix(sp, tt, fp32, mesh->slab_B, mesh->slab_M, vals, ctx->sm_count, ctx->stream);
-  tr->end(ctx->stream);
+  tr->begin(fp32 ? "slab_matrix_f32" : "slab_matrix_f64", kKinds, 0, fp32 ? 4 : 8, st);
+  int pmax = 1;
+  for (int q = 1; q <= 7; ++q)
+    if (mesh->dm.elem_pstart[q + 1] > mesh->dm.elem_pstart[q]) pmax = q;
+  n += launch_slab_matrix(sp, tt, fp32, mesh->slab_B, mesh->slab_M, vals, pmax, ctx->sm_count, st);
+  tr->end(st);
   if (rhs) {
-    tr->begin(fp32 ? "slab_rhs_f32" : "slab_rhs_f64", kKinds, 0, fp32 ? 4 : 8, ctx->stream);
-    n += launch_slab_rhs(sp, tt, fp32, mesh->slab_l, mesh->slab_M, u_prev, rhs, ctx->sm_count, ctx->stream);
-    tr->end(ctx->stream);
+    tr->begin(fp32 ? "slab_rhs_f32" : "slab_rhs_f64", kKinds, 0, fp32 ? 4 : 8, st);
+    n += launch_slab_rhs(sp, tt, fp32, mesh->slab_l, mesh->slab_M, u_prev, rhs, ctx->sm_count, st);
+    tr->end(st);
   }
   DG_CUDA_TRY(cudaGetLastError());
   ctx->last_launches = n;
+  return DG_OK;
+}
+
+int dg_assemble_slab(dg_ctx* ctx, dg_mesh* mesh, int prec, int space, double t0, double t1, const void* u_prev,
+                     void* vals, void* rhs) {
+  int rc = slab_check(ctx, mesh, prec, space, t0, t1, vals, "dg_assemble_slab");
+  if (rc != DG_OK) return rc;
+  return issue_slab(ctx, mesh, prec, space, t0, t1, u_prev, vals, rhs, ctx->stream, &ctx->streams);
+}
+
+int dg_slab_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, int space, double t0, double t1, const void* u_prev,
+                         void* vals, void* rhs, dg_graph** out) {
+  if (!out) return fail(DG_ERR_ARG, "dg_slab_graph_create: null output");
+  *out = nullptr;
+  int rc = slab_check(ctx, mesh, prec, space, t0, t1, vals, "dg_slab_graph_create");
+  if (rc != DG_OK) return rc;
+  dg_graph* g = new (std::nothrow) dg_graph();
+  if (!g) return fail(DG_ERR_OOM, "out of host memory");
+  if (cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking) != cudaSuccess || g->streams.ensure() != cudaSuccess) {
+    delete g;
+    return fail(DG_ERR_CUDA, "dg_slab_graph_create: stream creation failed");
+  }
+  trace_reset(ctx, mesh);
+  if (cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    delete g;
+    return fail(DG_ERR_CUDA, "dg_slab_graph_create: begin capture failed");
+  }
+  rc = issue_slab(ctx, mesh, prec, space, t0, t1, u_prev, vals, rhs, g->stream, &g->streams);
+  cudaError_t ce = cudaStreamEndCapture(g->stream, &g->graph);
+  g->ntrace = ctx->tracer.on ? ctx->tracer.n : 0;
+  if (rc == DG_OK && ce != cudaSuccess) rc = fail(DG_ERR_CUDA, "dg_slab_graph_create: capture: %s", cudaGetErrorString(ce));
+  if (rc == DG_OK && cudaGraphInstantiate(&g->exec, g->graph, 0) != cudaSuccess)
+    rc = fail(DG_ERR_CUDA, "dg_slab_graph_create: instantiate failed");
+  if (rc != DG_OK) {
+    delete g;
+    return rc;
+  }
+  g->launches = ctx->last_launches;
+  *out = g;
   return DG_OK;
 }
 
@@ -2287,9 +2358,15 @@ static bool persist_ok(const dg_ctx* ctx, const dg_mesh* mesh, int prec, int vpa
 // The work list for mom_mask: every moment tile, then every row tile, each
 // part by estimated work (points times n^2 over the tile's elements),
 // largest first.  Built on the host and uploaded (synchronous); cached.
+static const dg_mesh::PkList* persist_list(const dg_mesh* mesh, int key) {
+  for (const auto& l : mesh->pk_lists)
+    if (l.key == key) return &l;
+  return nullptr;
+}
+
 static int persist_items(dg_ctx* ctx, dg_mesh* mesh, int mom_mask) {
   const int key = mom_mask;
-  if (mesh->pk_key == key) return DG_OK;
+  if (persist_list(mesh, key)) return DG_OK;
   int ok_mask = 0, gm[9], gr[9];
   persist_layout(mesh->dm.dim, &ok_mask, gm, gr);
   const int dim = mesh->dm.dim, ne = mesh->dm.ne;
@@ -2333,19 +2410,16 @@ static int persist_items(dg_ctx* ctx, dg_mesh* mesh, int mom_mask) {
   items.reserve(mom.size() + row.size());
   for (const auto& it : mom) items.push_back(make_int4(it.kind, it.p, it.tile, 0));
   for (const auto& it : row) items.push_back(make_int4(it.kind, it.p, it.tile, 0));
-  if ((int)items.size() > mesh->pk_cap) {
-    if (mesh->pk_items) cudaFree(mesh->pk_items);
-    mesh->pk_items = nullptr;
-    mesh->pk_cap = 0;
-    if (cudaMalloc(&mesh->pk_items, sizeof(int4) * std::max<size_t>(items.size(), 1)) != cudaSuccess)
-      return fail(DG_ERR_OOM, "persistent pass: work list");
-    mesh->pk_cap = (int)items.size();
-  }
   if (!mesh->pk_sync && cudaMalloc(&mesh->pk_sync, sizeof(int) * (2 + (size_t)ne)) != cudaSuccess)
     return fail(DG_ERR_OOM, "persistent pass: flags");
-  DG_CUDA_TRY(cudaMemcpy(mesh->pk_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice));
-  mesh->pk_nitems = (int)items.size();
-  mesh->pk_key = key;
+  int4* dev = nullptr;
+  if (cudaMalloc(&dev, sizeof(int4) * std::max<size_t>(items.size(), 1)) != cudaSuccess)
+    return fail(DG_ERR_OOM, "persistent pass: work list");
+  if (cudaMemcpy(dev, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+    cudaFree(dev);
+    return fail(DG_ERR_CUDA, "persistent pass: work list upload");
+  }
+  mesh->pk_lists.push_back({key, dev, (int)items.size()});
   (void)ctx;
   return DG_OK;
 }
@@ -2356,12 +2430,13 @@ static int issue_persist_rows(dg_ctx* ctx, dg_mesh* mesh, int prec, int mode, vo
                               int vpath) {
   int mom_mask = 0;
   if (!persist_ok(ctx, mesh, prec, vpath, &mom_mask)) return fail(DG_ERR_ARG, "the persistent pass does not serve this mesh");
-  if (mesh->pk_key != mom_mask) return fail(DG_ERR_ARG, "persistent pass: work list not built");
+  const dg_mesh::PkList* list = persist_list(mesh, mom_mask);
+  if (!list) return fail(DG_ERR_ARG, "persistent pass: work list not built");
   const int ne = mesh->dm.ne;
   DG_CUDA_TRY(cudaMemsetAsync(mesh->pk_sync, 0, sizeof(int) * (2 + (size_t)ne), st));
   PersistArgs a{};
-  a.items = mesh->pk_items;
-  a.nitems = mesh->pk_nitems;
+  a.items = list->items;
+  a.nitems = list->n;
   a.queue = mesh->pk_sync;
   a.vdone = mesh->pk_sync + 2;
   a.status = ctx->status_dev;
@@ -2527,13 +2602,16 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
   }
   if (!autotune && ctx->persist) {
     int mask = 0;
-    if (persist_ok(ctx, mesh, prec, best_path, &mask)) {
-      const int rc = persist_items(ctx, mesh, mask);
-      if (rc != DG_OK) {
-        ctx->tracer.on = was_on;
-        return bail(rc);
-      }
-      best_persist = 1;
+    if (persist_ok(ctx, mesh, prec, best_path, &mask)) best_persist = 1;
+  }
+  if (best_persist) {
+    // the work list of the recorded path, built before the capture
+    int mask = 0;
+    persist_ok(ctx, mesh, prec, best_path, &mask);
+    const int rc = persist_items(ctx, mesh, mask);
+    if (rc != DG_OK) {
+      ctx->tracer.on = was_on;
+      return bail(rc);
     }
   }
   g->occ_cap = best_occ;
@@ -2735,7 +2813,9 @@ static int rebuild_worklist(dg_ctx* ctx, dg_mesh* mesh, const std::vector<int>& 
   DG_CUDA_TRY(cudaMemcpyAsync(mesh->perm_dev, perm.data(), sizeof(int) * perm.size(), cudaMemcpyHostToDevice,
                               ctx->stream));
   mesh->perm_h = perm;
-  mesh->pk_key = -1;  // the persistent pass's tiles follow the work list
+  // the persistent pass's tiles follow the work list: new lists from now on
+  mesh->pk_retired.insert(mesh->pk_retired.end(), mesh->pk_lists.begin(), mesh->pk_lists.end());
+  mesh->pk_lists.clear();
   DG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
   return DG_OK;
 }

@@ -16,14 +16,20 @@ namespace {
 
 constexpr int kSlabThreads = 256;
 
-// one warp per element row, grid-strided
+// one warp per element row, grid-strided; the time matrix and the dof
+// decode tables of degrees 1..pmax in shared memory
 template <typename T>
-__global__ void __launch_bounds__(kSlabThreads) slab_matrix_kernel(SlabPattern sp, SlabTimes<T> tt,
+__global__ void __launch_bounds__(kSlabThreads) slab_matrix_kernel(SlabPattern sp, SlabTimes<T> tt, int pmax,
                                                                    const T* __restrict__ B, const T* __restrict__ M,
                                                                    T* __restrict__ vals) {
+  __shared__ T sD[kSlabKMax * kSlabKMax];
+  __shared__ SlabDecode dec;
+  for (int i = threadIdx.x; i < kSlabKMax * kSlabKMax; i += blockDim.x) sD[i] = tt.D[i / kSlabKMax][i % kSlabKMax];
+  slab_decode_tables(sp.dim, sp.space, pmax, dec, threadIdx.x, blockDim.x);
+  __syncthreads();
   const int nwarps = gridDim.x * (kSlabThreads / 32);
   for (int r = blockIdx.x * (kSlabThreads / 32) + (threadIdx.x >> 5); r < sp.ne; r += nwarps)
-    slab_matrix_row<T>(sp, tt, B, M, vals, r, threadIdx.x & 31, 32);
+    slab_matrix_row<T>(sp, sD, dec, B, M, vals, r, threadIdx.x & 31, 32);
 }
 
 template <typename T>
@@ -65,14 +71,15 @@ int slab_grid(int ne, int sm_count) {
 }  // namespace
 
 int launch_slab_matrix(const SlabPattern& sp, const SlabTimes<double>& tt, bool fp32, const void* B, const void* M,
-                       void* vals, int sm_count, cudaStream_t st) {
+                       void* vals, int pmax, int sm_count, cudaStream_t st) {
   if (sp.ne <= 0) return 0;
   const int grid = slab_grid(sp.ne, sm_count);
   if (fp32)
-    slab_matrix_kernel<float><<<grid, kSlabThreads, 0, st>>>(sp, cast_times<float>(tt), static_cast<const float*>(B),
+    slab_matrix_kernel<float><<<grid, kSlabThreads, 0, st>>>(sp, cast_times<float>(tt), pmax,
+                                                             static_cast<const float*>(B),
                                                              static_cast<const float*>(M), static_cast<float*>(vals));
   else
-    slab_matrix_kernel<double><<<grid, kSlabThreads, 0, st>>>(sp, tt, static_cast<const double*>(B),
+    slab_matrix_kernel<double><<<grid, kSlabThreads, 0, st>>>(sp, tt, pmax, static_cast<const double*>(B),
                                                               static_cast<const double*>(M),
                                                               static_cast<double*>(vals));
   return 1;

@@ -77,6 +77,35 @@ inline SlabTimes<double> slab_time_data(double t0, double t1) {
   return tt;
 }
 
+// Decode tables of every degree's prism dofs: kj[off[p] + i] = (k << 8) | j
+// for dof i of a prism of degree p, i < slab_count(p) (the expansion takes
+// both indices of an entry from two table reads instead of a division and a
+// loop).  2D PQ_6 needs 196 entries; all degrees of either dimension and
+// space fit in kSlabDecMax.
+constexpr int kSlabDecMax = 512;
+struct SlabDecode {
+  unsigned short kj[kSlabDecMax];
+  int off[kSlabKMax + 1];
+};
+
+// fill the decode tables for degrees 1..pmax (entries [off[p], off[p+1]))
+__host__ __device__ inline void slab_decode_tables(int dim, int space, int pmax, SlabDecode& t, int tid, int nthreads) {
+  int o = 0;
+  for (int p = 0; p <= pmax && p < kSlabKMax; ++p) {
+    t.off[p] = o;
+    o += p == 0 ? 0 : slab_count(dim, p, space);
+  }
+  for (int p = pmax + 1; p <= kSlabKMax; ++p) t.off[p] = o;
+  for (int p = 1; p <= pmax && p < kSlabKMax; ++p) {
+    const int n = slab_count(dim, p, space);
+    for (int i = tid; i < n; i += nthreads) {
+      int k, j;
+      slab_decode(dim, p, space, i, k, j);
+      t.kj[t.off[p] + i] = (unsigned short)((k << 8) | j);
+    }
+  }
+}
+
 // The block pattern and spatial offsets the slab kernels read (device pointers).
 struct SlabPattern {
   int dim, ne, space;
@@ -94,32 +123,43 @@ struct SlabPattern {
 // this is `lane` (a warp in the kernels).  Plain loads and stores, no
 // synchronisation between the lanes.
 
-// slab blocks of row r: [k = l] B[j, m] + [r = s] D_kl M[j, m]
+// slab blocks of row r: [k = l] B[j, m] + [r = s] D_kl M[j, m].  Entry x
+// of a block sits at row i = x / nts, column q = x % nts; a lane steps x by
+// lanes, so (i, q) advance by (lanes / nts, lanes % nts) with one carry, and
+// (k, j), (l, m) come from the decode tables.  D: the time matrix, [k][l]
+// with stride kSlabKMax.  Stores are contiguous over the lanes.
 template <typename T>
-__host__ __device__ inline void slab_matrix_row(const SlabPattern& sp, const SlabTimes<T>& tt, const T* B,
+__host__ __device__ inline void slab_matrix_row(const SlabPattern& sp, const T* D, const SlabDecode& dec, const T* B,
                                                 const T* M, T* vals, int r, int lane, int lanes) {
   const int pr = sp.p[r];
   const int ntr = slab_count(sp.dim, pr, sp.space);
+  const unsigned short* dr = dec.kj + dec.off[pr];
   for (int b = sp.row_ptr[r]; b < sp.row_ptr[r + 1]; ++b) {
     const int s = sp.col[b];
     const int ps = sp.p[s];
     const int nbs = nbasis(sp.dim, ps);
     const int nts = slab_count(sp.dim, ps, sp.space);
+    const unsigned short* ds = dec.kj + dec.off[ps];
     const T* Bb = B + sp.blk_off[b];
     const T* Mb = M + sp.blk_off[b];  // the mass matrix sits in the diagonal blocks' places
     T* out = vals + sp.sblk_off[b];
     const bool diag = s == r;
     const int n = ntr * nts;
+    const int si = lanes / nts, sq = lanes - si * nts;
+    int i = lane / nts, q = lane - (lane / nts) * nts;
     for (int x = lane; x < n; x += lanes) {
-      const int i = x / nts;
-      const int q = x - i * nts;
-      int k, j, l, m;
-      slab_decode(sp.dim, pr, sp.space, i, k, j);
-      slab_decode(sp.dim, ps, sp.space, q, l, m);
+      const int kj = dr[i], lm = ds[q];
+      const int k = kj >> 8, j = kj & 255, l = lm >> 8, m = lm & 255;
       const int at = j * nbs + m;
       T v = k == l ? Bb[at] : T(0);
-      if (diag) v += tt.D[k][l] * Mb[at];
+      if (diag) v += D[k * kSlabKMax + l] * Mb[at];
       out[x] = v;
+      i += si;
+      q += sq;
+      if (q >= nts) {
+        q -= nts;
+        ++i;
+      }
     }
   }
 }
@@ -168,7 +208,7 @@ __host__ __device__ inline void slab_trace_row(const SlabPattern& sp, const Slab
 // Launchers (dg_slab.cu); each returns the number of launches (0 for ne = 0).
 // fp32 selects float buffers and SlabTimes<float>, else double.
 int launch_slab_matrix(const SlabPattern& sp, const SlabTimes<double>& tt, bool fp32, const void* B, const void* M,
-                       void* vals, int sm_count, cudaStream_t st);
+                       void* vals, int pmax, int sm_count, cudaStream_t st);
 int launch_slab_rhs(const SlabPattern& sp, const SlabTimes<double>& tt, bool fp32, const void* l, const void* M,
                     const void* u_prev, void* rhs, int sm_count, cudaStream_t st);
 int launch_slab_trace(const SlabPattern& sp, const SlabTimes<double>& tt, bool fp32, const void* U, void* u_end,

@@ -127,6 +127,7 @@ def load() -> C.CDLL:
     lib.dg_set_wait_limit.argtypes = [V, C.c_double]
     lib.dg_set_persistent.argtypes = [V, C.c_int]
     lib.dg_set_pattern_device.argtypes = [V, C.c_int]
+    lib.dg_slab_graph_create.argtypes = [V, V, C.c_int, C.c_int, C.c_double, C.c_double, V, V, V, C.POINTER(V)]
     lib.dg_mesh_timings.argtypes = [V, V, V, V]
     lib.dg_mesh_array.argtypes = [V, C.c_char_p, V, C.c_int64, C.POINTER(C.c_int64)]
     lib.dg_wait_probe.argtypes = [V, V, C.c_double]
@@ -184,6 +185,7 @@ EXPORTS = (
     "dg_mlp_save", "dg_mlp_load", "dg_quad_learn", "dg_assemble_batch", "dg_graph_tiles",
     "dg_set_tile_variants", "dg_set_wait_limit", "dg_wait_probe",
     "dg_set_persistent", "dg_set_pattern_device", "dg_mesh_timings", "dg_mesh_array",
+    "dg_slab_graph_create",
 )
 
 
@@ -531,6 +533,13 @@ class Mesh:
     def dg_assemble_slab(self, prec: int, space: int, t0: float, t1: float, vals, rhs=None, u_prev=None):
         _check(load().dg_assemble_slab(self.ctx._h, self._h, prec, int(space), float(t0), float(t1), _vp(u_prev),
                                        _vp(vals), _vp(rhs)))
+
+    def dg_slab_graph_create(self, prec: int, space: int, t0: float, t1: float, vals, rhs=None, u_prev=None):
+        """The slab step recorded as one CUDA graph (replay: Graph.dg_graph_launch)."""
+        h = C.c_void_p()
+        _check(load().dg_slab_graph_create(self.ctx._h, self._h, prec, int(space), float(t0), float(t1),
+                                           _vp(u_prev), _vp(vals), _vp(rhs), C.byref(h)))
+        return Graph(self.ctx, h)
 
     def dg_slab_trace(self, prec: int, space: int, t0: float, t1: float, U, u_end):
         _check(load().dg_slab_trace(self.ctx._h, self._h, prec, int(space), float(t0), float(t1), _vp(U),

@@ -33,8 +33,15 @@ void host_slab_matrix(int dim, int ne, int space, const int* p, const int* row_p
                       const int64_t* sdof_off, double t0, double t1, const double* B, const double* M, double* vals) {
   const SlabPattern sp = pattern(dim, ne, space, p, row_ptr, col, diag_blk, blk_off, dof_off, sblk_off, sdof_off);
   const SlabTimes<double> tt = slab_time_data(t0, t1);
+  // the kernel's shared tables, built by the same code, one thread
+  static SlabDecode dec;
+  int pmax = 1;
+  for (int e = 0; e < ne; ++e) pmax = p[e] > pmax ? p[e] : pmax;
+  slab_decode_tables(dim, space, pmax, dec, 0, 1);
+  double D[kSlabKMax * kSlabKMax];
+  for (int i = 0; i < kSlabKMax * kSlabKMax; ++i) D[i] = tt.D[i / kSlabKMax][i % kSlabKMax];
   for (int r = 0; r < ne; ++r)
-    for (int lane = 0; lane < kLanes; ++lane) slab_matrix_row<double>(sp, tt, B, M, vals, r, lane, kLanes);
+    for (int lane = 0; lane < kLanes; ++lane) slab_matrix_row<double>(sp, D, dec, B, M, vals, r, lane, kLanes);
 }
 
 void host_slab_rhs(int dim, int ne, int space, const int* p, const int* row_ptr, const int* col, const int* diag_blk,
