@@ -2567,7 +2567,7 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
     // its row kernel against the best so far (one pass of coordinate descent)
     for (int p = 1; rc == DG_OK && p <= 7; ++p) {
       if (mesh->dm.elem_pstart[p + 1] <= mesh->dm.elem_pstart[p]) continue;
-      for (int v = 1; rc == DG_OK && row_tile_tm(mesh->dm.dim, p, prec, v) > 0; ++v) {
+      for (int v = 1; rc == DG_OK && v < 3 && row_tile_tm(mesh->dm.dim, p, prec, v) > 0; ++v) {
         int cand[9];
         std::copy(best_tiles, best_tiles + 9, cand);
         cand[p] = v;

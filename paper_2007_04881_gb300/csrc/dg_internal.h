@@ -236,7 +236,8 @@ struct LaunchOpts {
 };
 
 // Edge TM of the register tiles of tile variant v of the (dim, p) row kernel
-// in precision prec (DG_PREC_*); 0 when there is no such variant.
+// in precision prec (DG_PREC_*); 0 when there is no such variant.  v = 3 is
+// the persistent pass's tile.
 int row_tile_tm(int dim, int p, int prec, int v);
 
 int launch_row2d_f64(const DevMesh& m, int mode, double* vals, double* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr);

@@ -15,8 +15,11 @@ int launch_row2d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm
 }
 
 namespace {
+// variants 0 .. tile_variants - 1 of the row kernel; 3 = the persistent
+// pass's tiles
 template <int D, int P, typename T>
 int tm_of(int v) {
+  if (v == 3) return tile_tm<D, P, T>(3);
   return v < tile_variants<D, P, T>() ? tile_tm<D, P, T>(v) : 0;
 }
 template <int D, typename T>
