@@ -51,6 +51,7 @@ class _Problem(C.Structure):
         ("poly", C.c_double * 20),
         ("c_sigma", C.c_double),
         ("coef", C.c_int),
+        ("neumann", C.c_int),
     ]
 
 
@@ -165,9 +166,11 @@ def basis(dim: int, p: int, lo, hi, x):
     return phi, grad.reshape(n, dim)
 
 
-def make_problem(dim, b=(0.0, 0.0, 0.0), c=0.0, source=0, poly=None, c_sigma=10.0, coef=0) -> _Problem:
+def make_problem(dim, b=(0.0, 0.0, 0.0), c=0.0, source=0, poly=None, c_sigma=10.0, coef=0, neumann=0) -> _Problem:
     """coef 0: constant b and c; coef 1: the fields b_d = 1 + x_d, c = 3 + prod x_d of
-    the paper's 3D advection-diffusion-reaction test (Sec. 4.2)."""
+    the paper's 3D advection-diffusion-reaction test (Sec. 4.2).  neumann: bit
+    2d + s marks the side x_d = min (s = 0) / max (s = 1) of the vertices'
+    bounding box as Neumann boundary (Eq. (2.2)); the rest is Dirichlet."""
     pb = _Problem()
     pb.dim = dim
     for i in range(3):
@@ -179,6 +182,7 @@ def make_problem(dim, b=(0.0, 0.0, 0.0), c=0.0, source=0, poly=None, c_sigma=10.
         pb.poly[i] = float(poly[i]) if i < len(poly) else 0.0
     pb.c_sigma = float(c_sigma)
     pb.coef = int(coef)
+    pb.neumann = int(neumann)
     return pb
 
 

@@ -215,6 +215,10 @@ typedef struct {
   double c_sigma;  /* penalty constant */
   int coef;        /* 0: b and c the constants above; 1: the fields of the paper's 3D
                       advection-diffusion-reaction test (Sec. 4.2), see coef_at */
+  int neumann;     /* Neumann part of the boundary (Eq. (2.2)): bit 2d + s marks the side
+                      x_d = min (s = 0) or x_d = max (s = 1) of the vertices' bounding box;
+                      a boundary face all of whose vertices lie on a marked side is a
+                      Neumann face, every other boundary face a Dirichlet face */
 } orc_problem;
 
 /* Advection and reaction at x.  coef 1 is the paper's multi-GPU test problem
@@ -355,6 +359,15 @@ static double dirichlet_g(const orc_problem *pb, const double *x) {
   return u;
 }
 
+/* g_N = n . (A grad u) = a grad u . n (Eq. (2.2), A = a I) at x for the
+ * unit normal n. */
+static double neumann_g(const orc_problem *pb, double a, const double *x, const double *n) {
+  double u, gu[3], lap, g = 0.0;
+  exact_u(pb, x, &u, gu, &lap);
+  for (int d = 0; d < pb->dim; ++d) g += gu[d] * n[d];
+  return a * g;
+}
+
 double orc_exact_u(const orc_problem *pb, const double *x) { return dirichlet_g(pb, x); }
 double orc_source_f(const orc_problem *pb, double a, const double *x) { return source_f(pb, a, x); }
 
@@ -384,6 +397,7 @@ typedef struct orc_mesh {
   int ni;
   int *ifptr; /* faces of interface k: f[ifptr[k] .. ifptr[k+1]) */
   int nbf;    /* number of boundary faces (they follow the interior ones) */
+  double dlo[3], dhi[3]; /* bounding box of all vertices (the Neumann sides) */
 } orc_mesh;
 
 static double dist(const double *a, const double *b, int dim) {
@@ -664,6 +678,13 @@ orc_mesh *orc_mesh_new(int dim, int nv, const double *x, const double *y, const 
   m->cen = (double *)malloc(sizeof(double) * (size_t)ne * dim);
   m->lo = (double *)malloc(sizeof(double) * (size_t)ne * dim);
   m->hi = (double *)malloc(sizeof(double) * (size_t)ne * dim);
+  for (int d = 0; d < dim; ++d) {
+    m->dlo[d] = m->dhi[d] = nv > 0 ? m->X[d][0] : 0.0;
+    for (int v = 1; v < nv; ++v) {
+      if (m->X[d][v] < m->dlo[d]) m->dlo[d] = m->X[d][v];
+      if (m->X[d][v] > m->dhi[d]) m->dhi[d] = m->X[d][v];
+    }
+  }
   element_geometry(m);
   if (build_faces(m) != 0) {
     return NULL;
@@ -854,6 +875,24 @@ static void volume_block(const orc_mesh *m, int e, int p, double a, const orc_pr
   free(wq);
 }
 
+/* Is boundary face f on the Neumann part of the boundary?  Its vertices
+ * (2 in 2D, 3 in 3D) all lie on one marked side of the domain's box, compared
+ * exactly. */
+static int neumann_face(const orc_mesh *m, const orc_face *f, const orc_problem *pb) {
+  if (f->e[1] >= 0 || pb->neumann == 0) return 0;
+  int nvf = m->dim == 2 ? 2 : 3;
+  for (int d = 0; d < m->dim; ++d)
+    for (int s = 0; s < 2; ++s) {
+      if (!(pb->neumann >> (2 * d + s) & 1)) continue;
+      double side = s ? m->dhi[d] : m->dlo[d];
+      int on = 1;
+      for (int i = 0; i < nvf; ++i)
+        if (m->X[d][f->v[i]] != side) on = 0;
+      if (on) return 1;
+    }
+  return 0;
+}
+
 /* Contribution of one face to the blocks (r, c) with r, c in {0,1} (0 = the
  * face's first element, whose outward normal is nF).  From Eq. (2.4):
  *   - {a grad w} . [v] - {a grad v} . [w] + sigma [w] . [v]
@@ -867,6 +906,10 @@ static void face_blocks(const orc_mesh *m, const orc_face *f, const int *p, cons
   int dim = m->dim;
   int bnd = f->e[1] < 0;
   int ns = bnd ? 1 : 2;
+  /* Eq. (2.4): the face integrals run over Gamma_int and the Dirichlet part
+   * only, the boundary inflow term over the inflow part of the Dirichlet
+   * boundary only; a Neumann face adds nothing to B */
+  if (neumann_face(m, f, pb)) return;
   int pp[2] = {p[f->e[0]], bnd ? 0 : p[f->e[1]]};
   int pmax = pp[0] > pp[1] ? pp[0] : pp[1];
   int nb[2] = {orc_nbasis(dim, pp[0]), bnd ? 0 : orc_nbasis(dim, pp[1])};
@@ -920,14 +963,24 @@ static void face_blocks(const orc_mesh *m, const orc_face *f, const int *p, cons
 }
 
 /* Boundary-face part of l (Eq. (2.5)) for the element of boundary face f:
- *   - (b . n) g_D v on the inflow part,  - g_D (a grad v . n - sigma v). */
+ * on a Dirichlet face
+ *   - (b . n) g_D v on the inflow part,  - g_D (a grad v . n - sigma v),
+ * on a Neumann face  g_N v. */
 static void face_rhs(const orc_mesh *m, const orc_face *f, const int *p, const double *a,
                      const orc_problem *pb, double *out) {
   int dim = m->dim, e = f->e[0], pe = p[e], n = orc_nbasis(dim, pe);
-  double sig = penalty(m, f, p, a, pb->c_sigma);
   double xq[4096 * 3], wq[4096];
   int nq = face_points(m, f, pe + 1, xq, wq);
   double phi[ORC_NMAX], grad[ORC_NMAX * 3];
+  if (neumann_face(m, f, pb)) {
+    for (int q = 0; q < nq; ++q) {
+      double g = neumann_g(pb, a[e], &xq[q * dim], f->n);
+      elem_basis(m, e, pe, &xq[q * dim], phi, grad);
+      for (int i = 0; i < n; ++i) out[i] += wq[q] * g * phi[i];
+    }
+    return;
+  }
+  double sig = penalty(m, f, p, a, pb->c_sigma);
   for (int q = 0; q < nq; ++q) {
     double b[3], c, bn = 0.0;
     coef_at(pb, &xq[q * dim], b, &c);

@@ -56,6 +56,22 @@ MUTATIONS = {
         "double avg = bnd ? 1.0 : 0.5;",
         "double avg = 0.5;",
     ),
+    "neumann_face_keeps_face_terms": (
+        "if (neumann_face(m, f, pb)) return;",
+        "/* dropped */",
+    ),
+    "neumann_data_sign": (
+        "return a * g;",
+        "return -a * g;",
+    ),
+    "neumann_side_bit": (
+        "if (!(pb->neumann >> (2 * d + s) & 1)) continue;",
+        "if (!(pb->neumann >> (d + 2 * s) & 1)) continue;",
+    ),
+    "neumann_data_without_a": (
+        "double g = neumann_g(pb, a[e], &xq[q * dim], f->n);",
+        "double g = neumann_g(pb, 1.0, &xq[q * dim], f->n);",
+    ),
 }
 
 
@@ -131,6 +147,40 @@ def _pins_pass(O) -> bool:
             xq, _ = om.volume_points(e, 3)
             for x in xq[::7]:
                 phi, _ = O.basis(2, 2, om.lo[e], om.hi[e], x)
+                if abs(phi @ U[off[e]:off[e + 1]] - O.exact_u(pb, x)) > 1e-9:
+                    return False
+        # Neumann sides: the constant in the kernel of pure diffusion with the
+        # whole boundary Neumann; with x = max Dirichlet, B 1 nonzero exactly
+        # on the elements with a face there
+        mesh = mg.voronoi_square(24, 11)
+        om = O.Mesh(mesh)
+        p = mg.draw_degrees(om.ne, 11, 1, 3).astype(np.int32)
+        a = mg.draw_log_uniform(om.ne, 11, -1, 1)
+        c1 = np.concatenate([np.eye(O.nbasis(2, int(p[e])))[0] * math.sqrt(np.prod(om.hi[e] - om.lo[e]))
+                             for e in range(om.ne)])
+        for mask in (0b1111, 0b1101):
+            A, _, off = O.global_matrix(om, p, om.assemble(p, a, O.make_problem(2, neumann=mask)))
+            r = A @ c1
+            s = np.abs(A).max()
+            xmax = np.asarray(mesh.x).max()
+            for e in range(om.ne):
+                loop = mesh.elem_v[mesh.elem_vptr[e]:mesh.elem_vptr[e + 1]]
+                on = mask == 0b1101 and any(mesh.x[loop[i]] == xmax and mesh.x[loop[(i + 1) % len(loop)]] == xmax
+                                            for i in range(len(loop)))
+                re = np.abs(r[off[e]:off[e + 1]]).max()
+                if (re > 1e-8 * s) != on:
+                    return False
+        # ... and reproduction with outflow sides Neumann, a != 1
+        om = O.Mesh(mg.voronoi_square(24, 7))
+        p = mg.draw_degrees(om.ne, 7, 2, 3).astype(np.int32)
+        a = np.full(om.ne, 0.6)
+        pb = O.make_problem(2, b=(0.9, 0.5), c=0.7, source=2, poly=[1, 0.5, -1, 0.3, 0.2, -0.4], neumann=0b1010)
+        A, F, off = O.global_matrix(om, p, om.assemble(p, a, pb))
+        U = np.linalg.solve(A, F)
+        for e in range(om.ne):
+            xq, _ = om.volume_points(e, 3)
+            for x in xq[::7]:
+                phi, _ = O.basis(2, int(p[e]), om.lo[e], om.hi[e], x)
                 if abs(phi @ U[off[e]:off[e + 1]] - O.exact_u(pb, x)) > 1e-9:
                     return False
         return True

@@ -549,3 +549,133 @@ def test_polynomial_reproduction_3d(b, c):
     poly = [1, 0.5, -1, 2, 0.3, 0, 0.7, -0.4, 0.2, 0.1]
     pb = O.make_problem(3, b=b, c=c, source=2, poly=poly, c_sigma=10.0)
     assert _solve_and_error(om, p, a, pb, npts=3) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# Neumann boundary (Eq. (2.2), Eq. (2.4), Eq. (2.5))
+# ---------------------------------------------------------------------------
+
+
+def _const_coeffs(om, p):
+    """Coefficients of the constant function 1: sqrt(|bbox|) on phi_0."""
+    out = []
+    for e in range(om.ne):
+        v = np.zeros(O.nbasis(om.dim, int(p[e])))
+        v[0] = math.sqrt(np.prod(om.hi[e] - om.lo[e]))
+        out.append(v)
+    return np.concatenate(out)
+
+
+def _elements_on_side(mesh, d, hi):
+    """Elements with a boundary face on the side x_d = min / max, found from
+    the mesh's own loops (2D) or tetrahedra (3D) by exact comparison."""
+    X = [np.asarray(mesh.x), np.asarray(mesh.y)] + ([np.asarray(mesh.z)] if mesh.dim == 3 else [])
+    side = X[d].max() if hi else X[d].min()
+    on = set()
+    if mesh.dim == 2:
+        for e in range(len(mesh.elem_vptr) - 1):
+            loop = mesh.elem_v[mesh.elem_vptr[e]:mesh.elem_vptr[e + 1]]
+            for i in range(len(loop)):
+                if X[d][loop[i]] == side and X[d][loop[(i + 1) % len(loop)]] == side:
+                    on.add(e)
+    else:
+        for e in range(len(mesh.elem_tptr) - 1):
+            for t in range(mesh.elem_tptr[e], mesh.elem_tptr[e + 1]):
+                if sum(X[d][v] == side for v in mesh.tet_v[4 * t:4 * t + 4]) >= 3:
+                    on.add(e)
+    return on
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_neumann_faces_add_nothing_to_the_operator(dim):
+    """Pure diffusion (b = 0, c = 0): grad 1 = 0 and [1] = 0 on interior faces,
+    so with the whole boundary Neumann the constant lies in the kernel of B
+    (Eq. (2.4) has no Neumann face terms).  With one side Dirichlet, B 1 is
+    nonzero exactly on the elements with a face on that side (the penalty
+    sees 1 there) and zero on all others."""
+    if dim == 2:
+        mesh = mg.voronoi_square(64, 5)
+        om = O.Mesh(mesh)
+        p = mg.draw_degrees(om.ne, 5, 1, 3).astype(np.int32)
+    else:
+        mesh = mg.kuhn_cube_agglomerated(3, 6, seed=2)
+        om = O.Mesh(mesh)
+        p = mg.draw_degrees(om.ne, 7, 1, 2).astype(np.int32)
+    a = mg.draw_log_uniform(om.ne, 6, -1, 1)
+    c1 = _const_coeffs(om, p)
+    allsides = (1 << (2 * dim)) - 1
+    A, _, off = _assemble_dense(om, p, a, O.make_problem(dim, neumann=allsides))
+    s = np.abs(A).max()
+    assert np.abs(A @ c1).max() < 1e-12 * s
+    for d in range(dim):
+        for hi in (0, 1):
+            bit = 1 << (2 * d + hi)
+            A, _, off = _assemble_dense(om, p, a, O.make_problem(dim, neumann=allsides & ~bit))
+            r = A @ c1
+            on = _elements_on_side(mesh, d, hi)
+            assert on
+            for e in range(om.ne):
+                re = np.abs(r[off[e]:off[e + 1]]).max()
+                if e in on:
+                    assert re > 1e-8 * s, (d, hi, e)
+                else:
+                    assert re < 1e-12 * s, (d, hi, e)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_neumann_data_balances_the_source(dim):
+    """Pure diffusion with uniform a and the whole boundary Neumann: testing
+    l with v = 1 gives int f + int g_N = int (-a Lap u) + int a grad u . n = 0
+    (divergence theorem); the source part alone is not zero (int Lap u =
+    0.7 in 2D and 2.2 in 3D for the polynomials below)."""
+    if dim == 2:
+        om = O.Mesh(mg.voronoi_square(64, 5))
+        poly = [1, 1, 0.5, 1, -0.7, 0.4, 0.3, 0, 0, -1]  # Lap u = 2.8 + 1.8x - 6y
+        p = mg.draw_degrees(om.ne, 5, 1, 3).astype(np.int32)
+        lap_int = 0.7
+    else:
+        om = O.Mesh(mg.kuhn_cube_agglomerated(3, 6, seed=2))
+        poly = [1, 0.5, -1, 2, 0.3, 0, 0.7, -0.4, 0.2, 0.1]  # Lap u = 2 (0.3 + 0.7 + 0.1)
+        p = np.full(om.ne, 2, dtype=np.int32)
+        lap_int = 2.2
+    a = np.full(om.ne, 0.37)
+    c1 = _const_coeffs(om, p)
+    allsides = (1 << (2 * dim)) - 1
+    pb = O.make_problem(dim, source=2, poly=poly, neumann=allsides)
+    _, F, _ = _assemble_dense(om, p, a, pb)
+    assert abs(F @ c1) < 1e-12
+    # the volume part alone: int f = -a int Lap u
+    pb0 = O.make_problem(dim, source=2, poly=poly, neumann=0)
+    vol = 0.0
+    for e in range(om.ne):
+        xq, wq = om.volume_points(e, 4)
+        vol += sum(w * O.source_f(pb0, 0.37, x) for x, w in zip(xq, wq))
+    assert abs(vol + 0.37 * lap_int) < 1e-12
+
+
+@pytest.mark.parametrize(
+    "dim,b,c,neumann",
+    [
+        (2, (1.0, 0.5), 1.0, 0b1010),  # outflow sides x = 1, y = 1 Neumann
+        (2, (0.0, 0.0), 0.0, 0b1110),  # only x = 0 Dirichlet
+        (2, (0.6, -0.8), 0.5, 0b0110),  # x = 1 and y = 0 (outflow) Neumann
+        (3, (1.0, -0.5, 0.25), 1.0, 0b100110),  # x = 1, y = 0, z = 1 Neumann
+        (3, (0.0, 0.0, 0.0), 0.0, 0b111011),  # only y = 1 Dirichlet
+    ],
+)
+def test_polynomial_reproduction_mixed_boundary(dim, b, c, neumann):
+    """dG consistency with Dirichlet and Neumann sides (b . n >= 0 on the
+    Neumann ones, as Eq. (2.2) assumes): u in P_p, g_D = u on the Dirichlet
+    faces and g_N = a grad u . n on the Neumann faces => the discrete solution
+    is u."""
+    if dim == 2:
+        om = O.Mesh(mg.voronoi_square(40, 21))
+        p = mg.draw_degrees(om.ne, 21, 3, 4).astype(np.int32)
+        poly = [1, 1, 0.5, 1, -0.7, 0.4, 0.3, 0, 0, -1]
+    else:
+        om = O.Mesh(mg.kuhn_cube_agglomerated(3, 6, seed=2))
+        p = np.full(om.ne, 2, dtype=np.int32)
+        poly = [1, 0.5, -1, 2, 0.3, 0, 0.7, -0.4, 0.2, 0.1]
+    a = np.full(om.ne, 0.37)
+    pb = O.make_problem(dim, b=b, c=c, source=2, poly=poly, c_sigma=10.0, neumann=neumann)
+    assert _solve_and_error(om, p, a, pb, npts=3) < 1e-9
