@@ -117,6 +117,14 @@ typedef struct {
   int source;              /* DG_SRC_* */
   double poly[20];         /* coefficients for DG_SRC_POLY */
   double c_sigma;          /* penalty constant C_sigma (> 0; the configs use 10) */
+  int neumann;             /* Neumann part of the boundary (Eq. (2.2)): bit 2d + s marks the
+                              side x_d = min (s = 0) or x_d = max (s = 1) of the bounding box
+                              of the vertices.  A boundary face all of whose vertices lie on a
+                              marked side (coordinates compared exactly) is a Neumann face:
+                              it adds no term to the matrix (Eq. (2.4)) and g_N v, g_N = a
+                              grad u . n of the manufactured u, to the load vector (Eq.
+                              (2.5)); every other boundary face is a Dirichlet face.  0: the
+                              whole boundary is Dirichlet.  Bits past 2 dim are an error. */
 } dg_mesh_desc;
 
 /* Sizes of the block-sparse layout of a mesh. */

@@ -161,7 +161,7 @@ def learned_training_meshes(n_meshes: int = 16, n_sites: int = 65536, base_seed:
 
 
 def small2d(n_sites: int, seed: int, plo: int, phi: int, b=(0.8, -0.45), c: float = 0.7,
-            source: int = SRC_SINPROD, poly=()) -> Workload:
+            source: int = SRC_SINPROD, poly=(), neumann: int = 0) -> Workload:
     """Small mixed-degree 2D case for parity tests."""
     m = mg.voronoi_square(n_sites, seed)
     return Workload(
@@ -169,12 +169,12 @@ def small2d(n_sites: int, seed: int, plo: int, phi: int, b=(0.8, -0.45), c: floa
         mesh=m,
         p=mg.draw_degrees(m.ne, seed, plo, phi),
         a=mg.draw_log_uniform(m.ne, seed, -2.0, 2.0),
-        problem=dict(b=(b[0], b[1], 0.0), c=c, source=source, poly=list(poly), c_sigma=10.0),
+        problem=dict(b=(b[0], b[1], 0.0), c=c, source=source, poly=list(poly), c_sigma=10.0, neumann=neumann),
     )
 
 
 def small3d(n: int, clusters: int, seed: int, plo: int, phi: int, b=(0.6, -0.3, 0.45), c: float = 0.5,
-            source: int = SRC_SINPROD, poly=()) -> Workload:
+            source: int = SRC_SINPROD, poly=(), neumann: int = 0) -> Workload:
     """Small agglomerated 3D case for parity tests."""
     m = mg.kuhn_cube_agglomerated(n, clusters, seed)
     return Workload(
@@ -182,5 +182,5 @@ def small3d(n: int, clusters: int, seed: int, plo: int, phi: int, b=(0.6, -0.3, 
         mesh=m,
         p=mg.draw_degrees(m.ne, seed, plo, phi),
         a=mg.draw_log_uniform(m.ne, seed, -1.0, 1.0),
-        problem=dict(b=tuple(b), c=c, source=source, poly=list(poly), c_sigma=10.0),
+        problem=dict(b=tuple(b), c=c, source=source, poly=list(poly), c_sigma=10.0, neumann=neumann),
     )

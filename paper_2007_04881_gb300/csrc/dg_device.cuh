@@ -21,7 +21,10 @@
 //     A_10: U = [Phi^1; DN^1], V = W [ a_0 DN^0/2 - sigma Phi^0 - max(b.n0,0) Phi^0; -a_1 Phi^0/2]
 // and the load vector (Eq. (2.5)) is s_i sum_rows U_i R with
 //     R = W f on volume points (Phi row),
-//     R = W [sigma g - min(b.n,0) g;  -a g] on boundary-face points.
+//     R = W [sigma g - min(b.n,0) g;  -a g] on Dirichlet boundary-face points,
+//     R = W [g_N; 0], g_N = a grad u . n_k, on Neumann boundary-face points,
+// whose V rows are zero (no face term of Eq. (2.4); their records carry
+// sigma = -1 and b . n = 0, so kappa = 0 and the penalty is dropped).
 // Geometry (bounding boxes, sub-simplex maps, Jacobians, normals, penalty)
 // comes from the geometry kernels as records in T: FP64, or for the reduced
 // forms FP32 records equal to the rounded FP64 ones; T is the contraction
@@ -678,10 +681,13 @@ __global__ void __launch_bounds__(kWarps * 32)
         const T* rec = HFR + (size_t)hf * RS;
         const T J = rec[2 * FV], sig = rec[2 * FV + 1], bn = rec[2 * FV + 2], nqs = rec[2 * FV + 3];
         const bool bnd = nqs < T(0);
+        const bool neu = sig < T(0);  // Neumann face
         const int nq = (int)(bnd ? -nqs : nqs);
         const int qf = D == 2 ? nq : nq * nq;
         if (!mat_face && !bnd) continue;
-        const T kap = bnd ? T(1) : T(0.5);
+        if (neu && !do_rhs) continue;
+        const T kap = neu ? T(0) : bnd ? T(1) : T(0.5);
+        const T sgf = neu ? T(0) : sig;
         const T upw = bn < T(0) ? bn : T(0);
         for (int lq = 0; lq < qf; ++lq) {
           const T* fr = FR + (size_t)(m.rt.face_off[nq] + lq) * (D == 2 ? 2 : 3);
@@ -697,21 +703,29 @@ __global__ void __launch_bounds__(kWarps * 32)
             for (int d = 0; d < D; ++d) v += np[d] * Dd[d][i];
             dn[i] = v;
           }
-          if (mat_face) {
+          if (mat_face && !neu) {
 #pragma unroll
             for (int j = 0; j < N; ++j) {
-              const T v0 = W * (-kap * q.a * dn[j] + (sig - upw) * Phi[j]);
+              const T v0 = W * (-kap * q.a * dn[j] + (sgf - upw) * Phi[j]);
               const T v1 = W * (-kap * q.a * Phi[j]);
 #pragma unroll
               for (int i = 0; i < N; ++i) acc[i][j] = fma(Phi[i], v0, fma(dn[i], v1, acc[i][j]));
             }
           }
           if (do_rhs && bnd) {
-            T x[D];
+            T x[D], gu[3], lap;
 #pragma unroll
             for (int d = 0; d < D; ++d) x[d] = q.lo[d] + (xi[d] + T(1)) * T(0.5) * q.L[d];
-            const T gd = dirichlet_g<D, T>(m.pb, x);
-            const T r0 = W * (sig - upw) * gd, r1 = -W * q.a * gd;
+            const T gd = exact_u<D, T>(m.pb, x, gu, &lap);
+            T r0 = W * (sgf - upw) * gd, r1 = -W * q.a * gd;
+            if (neu) {
+              // g_N = a grad u . n_k, n_k = n' L / 2
+              T gn = T(0);
+#pragma unroll
+              for (int d = 0; d < D; ++d) gn += gu[d] * np[d] * q.L[d];
+              r0 = W * T(0.5) * q.a * gn;
+              r1 = T(0);
+            }
 #pragma unroll
             for (int i = 0; i < N; ++i) racc[i] = fma(Phi[i], r0, fma(dn[i], r1, racc[i]));
           }
@@ -1051,9 +1065,10 @@ __device__ __forceinline__ void row_tile(const DevMesh& m, int mode, T* __restri
             T xi[D], np[D];
             hf_point<D, T>(rec, fr, xi, np);
             const T W = fr[D == 2 ? 1 : 2] * sc[0];
-            const T sig = sc[1];
+            const bool neu = sc[1] < T(0);  // Neumann face
+            const T sig = neu ? T(0) : sc[1];
             const T bn = sc[2];
-            const T kap = bnd ? T(1) : T(0.5);
+            const T kap = neu ? T(0) : bnd ? T(1) : T(0.5);
             const T a = pt[X + kPtA];
             const T upw = bn < T(0) ? bn : T(0);
             T Phi[N], Dd[D][N], dn[N], V0[N], V1[N];
@@ -1073,12 +1088,20 @@ __device__ __forceinline__ void row_tile(const DevMesh& m, int mode, T* __restri
             store_groups<T, N, TM, TMP, TR>(Vr + ROW, V1);
             if (do_rhs) {
               if (bnd) {
-                T x[D];
+                T x[D], gu[3], lap;
 #pragma unroll
                 for (int d = 0; d < D; ++d) x[d] = pt[2 * D + d] + (xi[d] + T(1)) * T(0.5) * pt[3 * D + d];
-                const T gd = dirichlet_g<D, T>(m.pb, x);
+                const T gd = exact_u<D, T>(m.pb, x, gu, &lap);
                 Rr[0] = W * (sig - upw) * gd;
                 Rr[1] = -W * a * gd;
+                if (neu) {
+                  // g_N = a grad u . n_k, n_k = n' L / 2
+                  T gn = T(0);
+#pragma unroll
+                  for (int d = 0; d < D; ++d) gn += gu[d] * np[d] * pt[3 * D + d];
+                  Rr[0] = W * T(0.5) * a * gn;
+                  Rr[1] = T(0);
+                }
               } else {
                 Rr[0] = T(0);
                 Rr[1] = T(0);

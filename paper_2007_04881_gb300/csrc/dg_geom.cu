@@ -397,6 +397,24 @@ __device__ __forceinline__ void write_hf_records(const DevMesh& m, int f, const 
   }
 }
 
+// Boundary face f on the Neumann part of the boundary (Eq. (2.2)): all its
+// vertices on one marked side of the vertex box, compared exactly.  Its
+// records carry sigma = -1 and b . n = 0: the row kernels add no matrix
+// term there (Eq. (2.4)) and take g_N v into the load vector (Eq. (2.5)).
+template <int D>
+__device__ __forceinline__ bool neumann_face(const DevMesh& m, int f) {
+  if (m.pb.neumann == 0 || m.f_e1[f] >= 0) return false;
+  for (int d = 0; d < D; ++d)
+    for (int s = 0; s < 2; ++s) {
+      if (!((m.pb.neumann >> (2 * d + s)) & 1)) continue;
+      const double side = s ? m.pb.dhi[d] : m.pb.dlo[d];
+      bool on = true;
+      for (int i = 0; i < D; ++i) on = on && m.X[d][m.f_v[D * f + i]] == side;
+      if (on) return true;
+    }
+  return false;
+}
+
 template <int D>
 __device__ __forceinline__ void face_geom(const DevMesh& m, int wmask, int f) {
   const int es[2] = {m.f_e0[f], m.f_e1[f]};
@@ -447,6 +465,10 @@ __device__ __forceinline__ void face_geom(const DevMesh& m, int wmask, int f) {
   sigma *= m.pb.c_sigma;
   double bn = 0.0;
   for (int d = 0; d < D; ++d) bn += m.pb.b[d] * n[d];
+  if (neumann_face<D>(m, f)) {
+    sigma = -1.0;
+    bn = 0.0;
+  }
   const double sc[3] = {J, sigma, bn};
   if (wmask & 1)
     for (int j = 0; j < 3; ++j) m.fsc64[(size_t)j * m.nf + f] = sc[j];
@@ -815,7 +837,12 @@ __global__ void face_geom_f32_kernel(DevMesh m) {
   }
   float bn = 0.f;
   for (int d = 0; d < D; ++d) bn = fmaf(m.pb.bf[d], n[d], bn);
-  write_hf_records<D>(m, f, sv, J, sigma * m.pb.c_sigmaf, bn, m.hfr32);
+  sigma *= m.pb.c_sigmaf;
+  if (neumann_face<D>(m, f)) {
+    sigma = -1.f;
+    bn = 0.f;
+  }
+  write_hf_records<D>(m, f, sv, J, sigma, bn, m.hfr32);
 }
 
 inline int nblk(int n, int t) { return (n + t - 1) / t; }

@@ -588,6 +588,8 @@ static int check_desc(const dg_mesh_desc* d) {
   if (d->source < 0 || d->source > 2) return fail(DG_ERR_ARG, "unknown source %d", d->source);
   if (!(d->c_sigma > 0.0)) return fail(DG_ERR_MESH, "C_sigma must be positive");
   if (!(d->c >= 0.0)) return fail(DG_ERR_MESH, "c must be >= 0");
+  if (d->neumann < 0 || d->neumann >= (1 << (2 * dim)))
+    return fail(DG_ERR_ARG, "neumann mask 0x%x names a side past dimension %d", (unsigned)d->neumann, dim);
   const int nv = d->nv, ne = d->ne;
   const int pmax = dim == 2 ? kPMax2 : kPMax3;
   if (d->elem_ptr[0] != 0) return fail(DG_ERR_MESH, "elem_ptr[0] must be 0");
@@ -1122,8 +1124,23 @@ static int alloc_records(dg_mesh* m, int dim, int ne, int nv, int nsub, int nf, 
   return rc;
 }
 
-// the problem data and the context's rule tables
-static void set_problem(dg_mesh* m, const dg_ctx* ctx, const dg_mesh_desc* d) {
+// bounding box of a descriptor's vertices (the sides the Neumann bits name)
+static void vertex_box(const dg_mesh_desc* d, double* lo, double* hi) {
+  const double* X[3] = {d->x, d->y, d->z};
+  for (int q = 0; q < 3; ++q) {
+    lo[q] = hi[q] = 0.0;
+    if (q >= d->dim) continue;
+    lo[q] = hi[q] = X[q][0];
+    for (int v = 1; v < d->nv; ++v) {
+      lo[q] = std::min(lo[q], X[q][v]);
+      hi[q] = std::max(hi[q], X[q][v]);
+    }
+  }
+}
+
+// the problem data and the context's rule tables; box (lo[3], hi[3]) the
+// vertex box the Neumann sides refer to, null = the descriptor's own
+static void set_problem(dg_mesh* m, const dg_ctx* ctx, const dg_mesh_desc* d, const double* box = nullptr) {
   DevMesh& dm = m->dm;
   for (int q = 0; q < 3; ++q) dm.pb.b[q] = d->b[q];
   if (d->dim == 2) dm.pb.b[2] = 0.0;
@@ -1131,6 +1148,13 @@ static void set_problem(dg_mesh* m, const dg_ctx* ctx, const dg_mesh_desc* d) {
   dm.pb.source = d->source;
   for (int q = 0; q < 20; ++q) dm.pb.poly[q] = d->poly[q];
   dm.pb.c_sigma = d->c_sigma;
+  dm.pb.neumann = d->neumann;
+  vertex_box(d, dm.pb.dlo, dm.pb.dhi);
+  if (box)
+    for (int q = 0; q < 3; ++q) {
+      dm.pb.dlo[q] = box[q];
+      dm.pb.dhi[q] = box[3 + q];
+    }
   dm.pb.round_copies();
   dm.rt = ctx->rt[d->dim];
 }
@@ -1147,7 +1171,8 @@ static void set_vfma(dg_mesh* m, const dg_mesh_desc* d) {
   }
 }
 
-static int upload_impl(dg_ctx* ctx, const dg_mesh_desc* d, const int8_t* owned, dg_mesh** out) {
+static int upload_impl(dg_ctx* ctx, const dg_mesh_desc* d, const int8_t* owned, dg_mesh** out,
+                       const double* box = nullptr) {
   if (!ctx || !d || !out) return fail(DG_ERR_ARG, "dg_mesh_upload: null argument");
   *out = nullptr;
   const auto t_start = std::chrono::steady_clock::now();
@@ -1264,7 +1289,7 @@ static int upload_impl(dg_ctx* ctx, const dg_mesh_desc* d, const int8_t* owned, 
     delete m;
     return rc;
   }
-  set_problem(m, ctx, d);
+  set_problem(m, ctx, d, box);
 
   fill_info(d, P, m->info);
   m->p_h.assign(d->p, d->p + ne);
@@ -2016,10 +2041,21 @@ int dg_batch_upload(dg_ctx* ctx, const dg_mesh_desc* const* descs, int n, dg_mes
     const dg_mesh_desc* d = descs[k];
     if (!d || d->dim != dim) return fail(DG_ERR_ARG, "dg_batch_upload: descriptor %d null or of another dimension", k);
     if (d->c != d0->c || d->source != d0->source || d->c_sigma != d0->c_sigma || d->b[0] != d0->b[0] ||
-        d->b[1] != d0->b[1] || d->b[2] != d0->b[2] || std::memcmp(d->poly, d0->poly, sizeof d->poly) != 0)
+        d->b[1] != d0->b[1] || d->b[2] != d0->b[2] || std::memcmp(d->poly, d0->poly, sizeof d->poly) != 0 ||
+        d->neumann != d0->neumann)
       return fail(DG_ERR_ARG, "dg_batch_upload: descriptor %d has different problem data", k);
-    if (d->nv <= 0 || d->ne <= 0 || !d->elem_ptr || !d->elem_idx)
+    if (d->nv <= 0 || d->ne <= 0 || !d->elem_ptr || !d->elem_idx || !d->x || !d->y || (dim == 3 && !d->z))
       return fail(DG_ERR_ARG, "dg_batch_upload: descriptor %d is empty", k);
+    if (d->neumann != 0) {
+      // the sides are those of each member's vertex box; the union keeps them
+      // only where every member spans the same box
+      double lo0[3], hi0[3], lo[3], hi[3];
+      vertex_box(d0, lo0, hi0);
+      vertex_box(d, lo, hi);
+      for (int q = 0; q < dim; ++q)
+        if (lo[q] != lo0[q] || hi[q] != hi0[q])
+          return fail(DG_ERR_ARG, "dg_batch_upload: descriptor %d with Neumann sides spans another box than descriptor 0", k);
+    }
     nv += d->nv;
     ne += d->ne;
     nidx += (int64_t)d->elem_ptr[d->ne] * (dim == 2 ? 1 : 4);
@@ -2301,7 +2337,10 @@ int dg_mesh_upload_part(dg_ctx* ctx, const dg_mesh_desc* d, const int* part, int
   PartMesh L;
   int rc = build_part(d, part, my_part, L, "dg_mesh_upload_part");
   if (rc != DG_OK) return rc;
-  rc = upload_impl(ctx, &L.d, L.owned.data(), out);
+  // the Neumann sides are those of the whole mesh's vertex box
+  double box[6];
+  vertex_box(d, box, box + 3);
+  rc = upload_impl(ctx, &L.d, L.owned.data(), out, box);
   if (rc != DG_OK) return rc;
   (*out)->part_elem = L.elem_global;
   (*out)->part_vert = L.vert_global;

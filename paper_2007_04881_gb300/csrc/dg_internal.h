@@ -69,6 +69,10 @@ struct Problem {
   int source;
   double poly[20];
   double c_sigma;
+  // Neumann sides (bit 2d + s: x_d = dlo[d] for s = 0, dhi[d] for s = 1)
+  // and the bounding box of the vertices they refer to
+  int neumann;
+  double dlo[3], dhi[3];
   // the same constants rounded to FP32, for the FP32 kernels: on a part whose
   // FP64 rate is 1/64 of FP32 a per-point conversion occupies the FP64 pipe
   float bf[3], cf, polyf[20], c_sigmaf;

@@ -520,9 +520,10 @@ __global__ void __launch_bounds__(kWarps * 32, MmaCfg<D, P, K>::MINB)
             float xi[D], np[D];
             hf_point<D, float>(rec, fr, xi, np);
             const float W = fr[D == 2 ? 1 : 2] * sc[0];
-            const float sig = sc[1];
+            const bool neu = sc[1] < 0.f;  // Neumann face: no matrix term, g_N in the load
+            const float sig = neu ? 0.f : sc[1];
             const float bn = sc[2];
-            const float kap = bnd ? 1.f : 0.5f;
+            const float kap = neu ? 0.f : bnd ? 1.f : 0.5f;
             const float a = pt[X + kPtA];
             const float upw = bn < 0.f ? bn : 0.f;
             float Phi[N], Dd[D][N], dn[N], V0[N], V1[N];
@@ -538,12 +539,20 @@ __global__ void __launch_bounds__(kWarps * 32, MmaCfg<D, P, K>::MINB)
             }
             float R0 = 0.f, R1 = 0.f;
             if (do_rhs && bnd) {
-              float x[D];
+              float x[D], gu[3], lap;
 #pragma unroll
               for (int d = 0; d < D; ++d) x[d] = pt[2 * D + d] + (xi[d] + 1.f) * 0.5f * pt[3 * D + d];
-              const float gd = dirichlet_g<D, float>(m.pb, x);
+              const float gd = exact_u<D, float>(m.pb, x, gu, &lap);
               R0 = W * (sig - upw) * gd;
               R1 = -W * a * gd;
+              if (neu) {
+                // g_N = a grad u . n_k, n_k = n' L / 2
+                float gn = 0.f;
+#pragma unroll
+                for (int d = 0; d < D; ++d) gn += gu[d] * np[d] * pt[3 * D + d];
+                R0 = W * 0.5f * a * gn;
+                R1 = 0.f;
+              }
             }
             put_row<K, SU, ZU, 16 * MT, N>(Ug, UPL, c, Phi, 0.f);
             put_row<K, SU, ZU, 16 * MT, N>(Ug, UPL, C + c, dn, 0.f);

@@ -291,6 +291,7 @@ extern "C" int dg_volume_noalloc(void* stream, int device, int prec, int p, int 
   m.pb.c = c;
   m.pb.source = DG_SRC_ZERO;
   m.pb.c_sigma = 10.0;
+  m.pb.neumann = 0;
   m.pb.round_copies();
   m.rt = nd->rt;
 

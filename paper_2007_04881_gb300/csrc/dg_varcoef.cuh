@@ -11,7 +11,8 @@
 //           b(x) . n_r < 0 with n_r out of r (b . n = 0 is outflow):
 //             A_rr += -(b . n_r) phi^r_j phi^r_i,  A_r,nb += (b . n_r) phi^nb_j phi^r_i,
 //   load    sum_q W (b . grad u + c u)(x_q) phi_i on the volume points and
-//           -(b . n_r) g phi_i at the inflow points of boundary faces (g = u),
+//           -(b . n_r) g phi_i at the inflow points of Dirichlet boundary
+//           faces (g = u); Neumann faces carry no b term (Eq. (2.4), (2.5)),
 // with the volume and face rules and the geometry records of the row kernels.
 //
 // The row bodies are host/device functions: a warp runs one element row in
@@ -135,7 +136,7 @@ struct VcView {
   const double* eg;    // [3D+1][ne]: lo, L, 1/L, R
   const double* sg;    // [sub_vals(D)][nsub]: xi0, edge vectors, |J|
   const double* fs;    // [2][side_vals(D)][nf]: per side xi(v0), xi(v_i) - xi(v0), n' = 2 n0 / L
-  const double* fsc;   // [3][nf]: J, sigma, b.n (J only)
+  const double* fsc;   // [3][nf]: J, sigma, b.n (J, and sigma < 0 marking a Neumann face)
   const int* f_e0;     // [nf]
   const int* f_e1;     // [nf], -1 on the boundary
   const int* f_nq;     // [nf] face points per direction
@@ -245,6 +246,7 @@ __host__ __device__ inline double vc_face_entry(const VcView& v, const VcElem<D>
   const double* rule = v.face_rule + (size_t)v.face_off[n] * D;
   const int nq = v.face_n[n];
   const double J = v.fsc[f];
+  if (v.fsc[(size_t)v.nf + f] < 0.0) return 0.0;  // Neumann face: no inflow term (Eq. (2.4))
   const double sg = sr == 0 ? 1.0 : -1.0;  // n_r = sg n0
   double acc = 0.0;
   for (int q = 0; q < nq; ++q) {
@@ -334,6 +336,7 @@ __host__ __device__ inline void vc_rhs_row(const VcView& v, double* rhs, int r, 
       for (int h = v.hf_ptr[r]; h < v.hf_ptr[r + 1]; ++h) {
         const int f = v.hf_face[h];
         if (v.f_e1[f] >= 0) continue;  // boundary faces only (the element is their side 0)
+        if (v.fsc[(size_t)v.nf + f] < 0.0) continue;  // Dirichlet faces only (Eq. (2.5))
         const int n = v.f_nq[f];
         const double* fr = v.face_rule + (size_t)v.face_off[n] * D;
         for (int q = 0; q < v.face_n[n]; ++q) {

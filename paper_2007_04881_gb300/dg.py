@@ -60,6 +60,7 @@ class dg_mesh_desc(C.Structure):
         ("source", C.c_int),
         ("poly", C.c_double * 20),
         ("c_sigma", C.c_double),
+        ("neumann", C.c_int),
     ]
 
 
@@ -211,13 +212,16 @@ def _vp(x) -> Optional[int]:
 
 @dataclass
 class Problem:
-    """Constant problem data of Eq. (2.1): advection b, reaction c, source."""
+    """Constant problem data of Eq. (2.1): advection b, reaction c, source;
+    ``neumann``: bit 2d + s marks the side x_d = min (s = 0) / max (s = 1) of
+    the vertices' bounding box as Neumann boundary (Eq. (2.2))."""
 
     b: Sequence[float] = (0.0, 0.0, 0.0)
     c: float = 0.0
     source: int = DG_SRC_ZERO
     poly: Sequence[float] = field(default_factory=list)
     c_sigma: float = 10.0
+    neumann: int = 0
 
 
 class Context:
@@ -314,6 +318,7 @@ def make_desc(mesh, p, a, problem: Problem):
     for i in range(20):
         d.poly[i] = float(problem.poly[i]) if i < len(problem.poly) else 0.0
     d.c_sigma = float(problem.c_sigma)
+    d.neumann = int(getattr(problem, "neumann", 0))
     return d, keep
 
 

@@ -10,12 +10,14 @@ from paper_2007_04881_gb300 import dg
 
 def oracle_problem(wl):
     pb = wl.problem
-    return O.make_problem(wl.dim, b=pb["b"], c=pb["c"], source=pb["source"], poly=pb["poly"], c_sigma=pb["c_sigma"])
+    return O.make_problem(wl.dim, b=pb["b"], c=pb["c"], source=pb["source"], poly=pb["poly"], c_sigma=pb["c_sigma"],
+                          coef=pb.get("coef", 0), neumann=pb.get("neumann", 0))
 
 
 def dg_problem(wl):
     pb = wl.problem
-    return dg.Problem(b=pb["b"], c=pb["c"], source=pb["source"], poly=pb["poly"], c_sigma=pb["c_sigma"])
+    return dg.Problem(b=pb["b"], c=pb["c"], source=pb["source"], poly=pb["poly"], c_sigma=pb["c_sigma"],
+                      neumann=pb.get("neumann", 0))
 
 
 def oracle_blocks(wl, elems=None, ifaces=None, om=None, rhs=True):

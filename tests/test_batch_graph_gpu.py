@@ -151,7 +151,6 @@ def test_autotuner_records_tiles(ctx):
 
     w = configs.small2d(600, 93, 1, 5, b=(1.0, 0.5), c=1.0)
     m = dg.Mesh(ctx, w.mesh, w.p, w.a, dg_problem(w))
-    v_ref, r_ref = _assemble(ctx, m, dg.DG_PREC_FP32)
     v = torch.zeros(m.nvals, dtype=torch.float32, device="cuda")
     r = torch.zeros(m.ndofs, dtype=torch.float32, device="cuda")
     g = m.dg_graph_create(dg.DG_PREC_FP32, v, r, autotune=True)
@@ -160,6 +159,16 @@ def test_autotuner_records_tiles(ctx):
     assert sorted(int(k[1:]) for k in info["tile_tm"]) == present
     assert info["tile_tm"]["p4"] in (8, 5, 4) and info["tile_tm"]["p3"] in (5, 4)
     assert info["tuner_trials"] >= 12 + 1 + 2 + 2
+    # the reference: the direct pass on the volume path and pass the tuner
+    # chose (tile variants do not change the bits; the paths do)
+    path = {"per-point": 0, "moments": 1, "exact-moments": 2}[info["volume_path"]]
+    ctx.dg_set_volume_path(path)
+    ctx.dg_set_persistent(info["persistent"])
+    try:
+        v_ref, r_ref = _assemble(ctx, m, dg.DG_PREC_FP32)
+    finally:
+        ctx.dg_set_volume_path(1)
+        ctx.dg_set_persistent(False)
     g.dg_graph_launch()
     ctx.dg_sync()
     assert np.array_equal(v.double().cpu().numpy(), v_ref)
