@@ -313,6 +313,17 @@ int dg_set_volume_path(dg_ctx *ctx, int path);
  * order, so the results are bitwise those of the default tiles. */
 int dg_set_tile_variants(dg_ctx *ctx, const int *variants);
 
+/* Parts of each degree group (split[p], 9 entries, 1..4; NULL: all 1) for
+ * the calls without a tuned launch shape that run the degree groups
+ * concurrently (dg_assemble_step / dg_assemble_host on an untuned mesh,
+ * the slab step's spatial pass).  A group in k parts is k contiguous runs
+ * of equal element count, each with its own moment launch and row launch on
+ * a stream of its own, so that the chains of the largest groups run side by
+ * side instead of one after the other.  Every element is computed by the
+ * same kernel as without parts: the results are bitwise the same.
+ * DG_ERR_ARG for a value outside 1..4. */
+int dg_set_group_split(dg_ctx *ctx, const int *split);
+
 /* Partitions (Sec. 4.2: the elements are split across GPUs, each GPU builds
  * and assembles its own rows, faces on a cut are computed by both owners, and
  * assembly needs no communication).
@@ -398,6 +409,10 @@ int dg_graph_info(const dg_graph *graph, int *occ_cap, int *concurrent, float *t
  * (recorded graphs refer to it); the flags are the mesh's, so persistent
  * passes of one mesh must not overlap on the GPU (one stream, or events). */
 int dg_graph_tiles(const dg_graph *graph, int *tile_tm, int *trials, int *persistent);
+/* The parts per degree group of a recorded pass (split[9]; all 1 for a
+ * serial or persistent pass): the autotuner tries 2..4 parts for each degree
+ * present, from the highest, after the tiles (see dg_set_group_split). */
+int dg_graph_splits(const dg_graph *graph, int *split);
 int dg_graph_free(dg_graph *graph);
 
 /* Learned reduced volume rules (2D).  For each element mapped to its

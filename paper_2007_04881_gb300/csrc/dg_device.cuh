@@ -999,6 +999,9 @@ __device__ __forceinline__ void row_tile(const DevMesh& m, int mode, T* __restri
               for (int d = 0; d < D; ++d) Rr[1 + d] = T(0);
             }
           } else {
+            // both rows: an unstaged U slot holds whatever the shared memory
+            // held before (possibly a NaN pattern), and NaN * 0 is NaN
+            zero_groups<T, TMP>(Ur, NT * ROW);
             zero_groups<T, TMP>(Vr, NT * ROW);
 #pragma unroll
             for (int t = 0; t < NT; ++t) Rr[t] = T(0);
@@ -1108,6 +1111,7 @@ __device__ __forceinline__ void row_tile(const DevMesh& m, int mode, T* __restri
               }
             }
           } else {
+            zero_groups<T, TMP>(Ur, 2 * ROW);
             zero_groups<T, TMP>(Vr, 2 * ROW);
             Rr[0] = T(0);
             Rr[1] = T(0);

@@ -160,19 +160,20 @@ int fail_na_impl(int code, const char* msg) { return fail(code, "%s", msg); }
 // captures through a set of its own, so that a recorded pass does not depend
 // on what the context's streams did before it.
 struct SideStreams {
-  cudaStream_t side[4] = {nullptr, nullptr, nullptr, nullptr};
-  cudaEvent_t fork = nullptr, join[4] = {nullptr, nullptr, nullptr, nullptr};
+  static constexpr int kN = 8;
+  cudaStream_t side[kN] = {};
+  cudaEvent_t fork = nullptr, join[kN] = {};
   cudaError_t ensure() {
     if (fork) return cudaSuccess;
     cudaError_t e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
-    for (int i = 0; i < 4 && e == cudaSuccess; ++i) {
+    for (int i = 0; i < kN && e == cudaSuccess; ++i) {
       e = cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking);
       if (e == cudaSuccess) e = cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming);
     }
     return e;
   }
   ~SideStreams() {
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < kN; ++i) {
       if (side[i]) cudaStreamDestroy(side[i]);
       if (join[i]) cudaEventDestroy(join[i]);
     }
@@ -191,6 +192,7 @@ struct dg_ctx {
   bool vol_moments = true;  // volume blocks through Legendre-product moments
   bool vol_exact = false;   // 2D: those moments exact, by Green's theorem along the edges
   int tiles[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // row-kernel tile variants of untuned passes
+  int splits[9] = {1, 1, 1, 1, 1, 1, 1, 1, 1};  // parts of each degree group in untuned concurrent passes
   int* status_dev = nullptr;  // bit 0: a bounded device wait ran out (read and cleared by dg_sync)
   long long wait_ns = 2000000000LL;  // bound of one device wait
   bool persist = false;  // untuned per-step passes and untuned graphs take the persistent pass
@@ -231,6 +233,7 @@ struct dg_graph {
   int vol_path = 1;
   int tiles[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // tile variant per degree
   int tile_tm[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // its tile edge (0: no group of that degree)
+  int split[9] = {1, 1, 1, 1, 1, 1, 1, 1, 1};  // parts per degree group (concurrent shape)
   int trials = 0;  // passes the autotuner timed
   int persist = 0;  // 1: the row work is the persistent pass
   float tuned_ms = 0.f;
@@ -248,9 +251,9 @@ void Tracer::begin(const char* name, int kind, int p, size_t tsize, cudaStream_t
   if (!on || n >= cap) return;
   LaunchRec& r = recs[n];
   snprintf(r.name, sizeof r.name, "%s", name);
-  r.flops = (kind < kKinds && flops) ? flops[kind * 9 + p] : 0.0;
-  r.xflops = (kind == 2 && xflops) ? xflops[p] : r.flops;
-  r.bytes = (kind < kKinds && words) ? words[kind * 9 + p] * (double)tsize : 0.0;
+  r.flops = ((kind < kKinds && flops) ? flops[kind * 9 + p] : 0.0) * scale;
+  r.xflops = (kind == 2 && xflops) ? xflops[p] * scale : r.flops;
+  r.bytes = ((kind < kKinds && words) ? words[kind * 9 + p] * (double)tsize : 0.0) * scale;
   record(r.ev0, st);
 }
 void Tracer::begin_counts(const char* name, double fl, double xfl, double by, cudaStream_t st) {
@@ -298,6 +301,7 @@ struct dg_mesh {
   int shape_path[4] = {-1, -1, -1, -1}, shape_vm[4] = {0, 0, 0, 0};
   int shape_tile[4][9] = {{0}};  // tuned tile variant per degree
   int shape_persist[4] = {0, 0, 0, 0};  // tuned: the persistent pass
+  int shape_split[4][9] = {{0}};  // tuned parts per degree group (0 = 1)
   double* X[3] = {nullptr, nullptr, nullptr};
   double* a = nullptr;
   double flops[kKinds][9] = {{0}}, words[kKinds][9] = {{0}};
@@ -1592,7 +1596,7 @@ static int dispatch_rows(const DevMesh& m, int prec, int mode, void* vals, void*
 static int run_assembly(dg_ctx* ctx, const dg_mesh* mesh, int prec, int mode, void* vals, void* rhs, bool iface,
                         bool reset = true, cudaStream_t st = nullptr, bool use_ctx_stream = true, int occ_cap = 0,
                         bool concurrent = false, int vpath = -1, SideStreams* ss = nullptr,
-                        const int* tiles = nullptr) {
+                        const int* tiles = nullptr, const int* splits = nullptr) {
   if (!ctx || !mesh) return fail(DG_ERR_ARG, "null context or mesh");
   if (prec < DG_PREC_FP64 || prec > DG_PREC_TF32X3) return fail(DG_ERR_ARG, "unknown precision %d", prec);
   if ((mode & (kModeVol | kModeFace)) && !vals) return fail(DG_ERR_ARG, "vals is null");
@@ -1614,13 +1618,22 @@ static int run_assembly(dg_ctx* ctx, const dg_mesh* mesh, int prec, int mode, vo
   if (concurrent) {
     DG_CUDA_TRY(ss->ensure());
     DG_CUDA_TRY(cudaEventRecord(ss->fork, st));
-    for (int i = 0; i < 4; ++i) DG_CUDA_TRY(cudaStreamWaitEvent(ss->side[i], ss->fork, 0));
-    // highest degrees (longest launches) first on their own streams
-    for (int p = 1; p < 9; ++p) lo.pst[p] = ss->side[(8 - p) % 4];
+    for (int i = 0; i < SideStreams::kN; ++i) DG_CUDA_TRY(cudaStreamWaitEvent(ss->side[i], ss->fork, 0));
+    // highest degrees (longest launches) first, each part of a split group
+    // on a stream of its own
+    int k = 0;
+    for (int p = 7; p >= 1; --p) {
+      const int parts = splits ? std::max(1, std::min(kMaxSplit, splits[p])) : ctx->splits[p];
+      lo.split[p] = parts;
+      lo.pst[p] = ss->side[k % SideStreams::kN];
+      for (int i = 0; i < parts; ++i) lo.part[p][i] = ss->side[(k + i) % SideStreams::kN];
+      if (m.elem_pstart[p + 1] > m.elem_pstart[p]) k += parts;
+    }
+    lo.pst[8] = lo.pst[0] = ss->side[0];
   }
   const int n = dispatch_rows(m, prec, mode, vals, rhs, ctx->sm_count, lo, tr);
   if (concurrent) {
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < SideStreams::kN; ++i) {
       DG_CUDA_TRY(cudaEventRecord(ss->join[i], ss->side[i]));
       DG_CUDA_TRY(cudaStreamWaitEvent(st, ss->join[i], 0));
     }
@@ -1659,19 +1672,22 @@ int dg_assemble(dg_ctx* ctx, const dg_mesh* mesh, int prec, void* vals, void* rh
 static bool persist_ok(const dg_ctx* ctx, const dg_mesh* mesh, int prec, int vpath, int* mom_mask);
 
 static void step_shape(const dg_ctx* ctx, const dg_mesh* mesh, int prec, int* occ, bool* conc, int* path,
-                       const int** tiles, bool* persist = nullptr) {
+                       const int** tiles, bool* persist = nullptr, const int** splits = nullptr) {
   *tiles = ctx->tiles;
+  if (splits) *splits = ctx->splits;
   if (persist) *persist = false;
   if (mesh->shape_set[prec] && mesh->shape_vm[prec] == ctx_vol_path(ctx)) {
     *occ = mesh->shape_occ[prec];
     *conc = mesh->shape_conc[prec] != 0;
     *path = mesh->shape_path[prec];
     *tiles = mesh->shape_tile[prec];
+    if (splits) *splits = mesh->shape_split[prec];
     if (persist) *persist = mesh->shape_persist[prec] != 0;
     return;
   }
   int groups = 0;
   for (int q = 1; q + 1 < 9; ++q) groups += mesh->dm.elem_pstart[q + 1] > mesh->dm.elem_pstart[q];
+  for (int q = 1; q + 1 < 9; ++q) groups += ctx->splits[q] > 1 ? 1 : 0;
   *occ = 0;
   *conc = groups > 1;
   *path = -1;
@@ -1708,11 +1724,12 @@ int dg_assemble_host(dg_ctx* ctx, dg_mesh* mesh, int prec, const double* x, cons
   bool conc = false;
   const int* tiles = nullptr;
   bool persist = false;
-  step_shape(ctx, mesh, prec, &occ, &conc, &path, &tiles, &persist);
+  const int* splits = nullptr;
+  step_shape(ctx, mesh, prec, &occ, &conc, &path, &tiles, &persist, &splits);
   const int mode = kModeVol | kModeFace | (rhs_host ? kModeRhs : 0);
   int rc = persist ? issue_persist_step(ctx, mesh, prec, mode, mesh->h_vals, rhs_host ? mesh->h_rhs : nullptr, path)
                    : run_assembly(ctx, mesh, prec, mode, mesh->h_vals, rhs_host ? mesh->h_rhs : nullptr, true, false,
-                                  nullptr, true, occ, conc, path, nullptr, tiles);
+                                  nullptr, true, occ, conc, path, nullptr, tiles, splits);
   if (rc != DG_OK) return rc;
   // one copy each: several parts on parallel streams measured no faster
   DG_CUDA_TRY(cudaMemcpyAsync(vals_host, mesh->h_vals, es * mesh->info.nvals, cudaMemcpyDeviceToHost, ctx->stream));
@@ -1734,10 +1751,12 @@ int dg_assemble_step(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs
   bool conc = false;
   const int* tiles = nullptr;
   bool persist = false;
-  step_shape(ctx, mesh, prec, &occ, &conc, &path, &tiles, &persist);
+  const int* splits = nullptr;
+  step_shape(ctx, mesh, prec, &occ, &conc, &path, &tiles, &persist, &splits);
   const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
   if (persist) return issue_persist_step(ctx, mesh, prec, mode, vals, rhs, path);
-  return run_assembly(ctx, mesh, prec, mode, vals, rhs, true, false, nullptr, true, occ, conc, path, nullptr, tiles);
+  return run_assembly(ctx, mesh, prec, mode, vals, rhs, true, false, nullptr, true, occ, conc, path, nullptr, tiles,
+                      splits);
 }
 
 // ---------------------------------------------------------------------------
@@ -1860,10 +1879,11 @@ static int issue_slab(dg_ctx* ctx, dg_mesh* mesh, int prec, int space, double t0
   int occ = 0, path = -1;
   bool conc = false;
   const int* tiles = nullptr;
-  step_shape(ctx, mesh, prec, &occ, &conc, &path, &tiles);
+  const int* splits = nullptr;
+  step_shape(ctx, mesh, prec, &occ, &conc, &path, &tiles, nullptr, &splits);
   // B and l: the spatial pass
   int rc = run_assembly(ctx, mesh, prec, kModeVol | kModeFace | (rhs ? kModeRhs : 0), mesh->slab_B,
-                        rhs ? mesh->slab_l : nullptr, true, true, st, false, occ, true, path, ss, tiles);
+                        rhs ? mesh->slab_l : nullptr, true, true, st, false, occ, true, path, ss, tiles, splits);
   if (rc != DG_OK) return rc;
   int n = ctx->last_launches;
   // M: the volume pass of the same rules with a = 0, b = 0, c = 1
@@ -2522,7 +2542,8 @@ static int issue_persist_step(dg_ctx* ctx, dg_mesh* mesh, int prec, int mode, vo
 
 // One whole pass (geometry + row kernels) on stream st with a launch shape.
 static int issue_pass(dg_ctx* ctx, dg_mesh* mesh, int prec, int gmask, void* vals, void* rhs, cudaStream_t st,
-                      int occ_cap, bool concurrent, int vpath, SideStreams* ss, const int* tiles, bool persist = false) {
+                      int occ_cap, bool concurrent, int vpath, SideStreams* ss, const int* tiles, bool persist = false,
+                      const int* splits = nullptr) {
   int n = launch_geometry(mesh->dm, st, nullptr, gmask);
   DG_CUDA_TRY(cudaGetLastError());
   const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
@@ -2533,7 +2554,8 @@ static int issue_pass(dg_ctx* ctx, dg_mesh* mesh, int prec, int gmask, void* val
     ctx->last_launches = n + 1;
     return DG_OK;
   }
-  int rc = run_assembly(ctx, mesh, prec, mode, vals, rhs, true, true, st, false, occ_cap, concurrent, vpath, ss, tiles);
+  int rc = run_assembly(ctx, mesh, prec, mode, vals, rhs, true, true, st, false, occ_cap, concurrent, vpath, ss, tiles,
+                        splits);
   if (rc != DG_OK) return rc;
   ctx->last_launches += n;
   return DG_OK;
@@ -2562,6 +2584,7 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
   int best_occ = 0, best_conc = 0, best_path = def_path;
   int best_tiles[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
   int best_persist = 0;
+  int best_split[9] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
   float best = 1e30f;
   if (autotune) {
     const int occs[3] = {0, 1, 2};
@@ -2570,12 +2593,13 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     // one candidate: best of 3 timed passes after a warm-up pass
-    auto time_shape = [&](int occ, int conc, int vpath, const int* tiles, float* out, bool persist = false) -> int {
+    auto time_shape = [&](int occ, int conc, int vpath, const int* tiles, float* out, bool persist = false,
+                          const int* splits = nullptr) -> int {
       float t = 1e30f;
       for (int rep = 0; rep < 4; ++rep) {
         cudaEventRecord(e0, g->stream);
         int rc = issue_pass(ctx, mesh, prec, gmask, vals, rhs, g->stream, occ, conc != 0, vpath, &g->streams, tiles,
-                            persist);
+                            persist, splits ? splits : best_split);
         if (rc != DG_OK) return rc;
         cudaEventRecord(e1, g->stream);
         if (cudaEventSynchronize(e1) != cudaSuccess) return fail(DG_ERR_CUDA, "dg_graph_create: tuning pass failed");
@@ -2615,6 +2639,24 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
         if (rc == DG_OK && t < best) {
           best = t;
           best_tiles[p] = v;
+        }
+      }
+    }
+    // degree groups in parts (concurrent shape): for each degree present,
+    // from the highest, 2..kMaxSplit parts against the best so far, so that
+    // the long moment-then-rows chains of the big groups run side by side
+    for (int p = 7; rc == DG_OK && p >= 1; --p) {
+      if (mesh->dm.elem_pstart[p + 1] <= mesh->dm.elem_pstart[p]) continue;
+      for (int s = 2; rc == DG_OK && s <= kMaxSplit; ++s) {
+        int cand[9];
+        std::copy(best_split, best_split + 9, cand);
+        cand[p] = s;
+        float t = 0.f;
+        rc = time_shape(best_occ, 1, best_path, best_tiles, &t, false, cand);
+        if (rc == DG_OK && t < best) {
+          best = t;
+          best_conc = 1;
+          best_split[p] = s;
         }
       }
     }
@@ -2660,6 +2702,7 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
   g->tuned_ms = autotune ? best : 0.f;
   for (int p = 0; p < 9; ++p) {
     g->tiles[p] = best_tiles[p];
+    g->split[p] = autotune ? (best_conc ? best_split[p] : 1) : ctx->splits[p];
     const bool present = p >= 1 && p <= 7 && mesh->dm.elem_pstart[p + 1] > mesh->dm.elem_pstart[p];
     g->tile_tm[p] = present ? row_tile_tm(mesh->dm.dim, p, prec, best_persist ? 3 : best_tiles[p]) : 0;
   }
@@ -2670,6 +2713,7 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
     mesh->shape_path[prec] = best_path;
     mesh->shape_vm[prec] = ctx_vol_path(ctx);
     std::copy(best_tiles, best_tiles + 9, mesh->shape_tile[prec]);
+    std::copy(g->split, g->split + 9, mesh->shape_split[prec]);
     mesh->shape_persist[prec] = best_persist;
   }
   // with timing enabled the per-launch events are recorded into the graph
@@ -2686,7 +2730,7 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
       ctx->last_launches = 1;
     } else {
       rc = run_assembly(ctx, mesh, prec, mode, vals, rhs, true, false, g->stream, false, g->occ_cap,
-                        g->concurrent != 0, g->vol_path, &g->streams, g->tiles);
+                        g->concurrent != 0, g->vol_path, &g->streams, g->tiles, g->split);
     }
     ctx->last_launches += gl;
   }
@@ -2790,6 +2834,12 @@ int dg_graph_tiles(const dg_graph* g, int* tile_tm, int* trials, int* persistent
   if (tile_tm) std::copy(g->tile_tm, g->tile_tm + 9, tile_tm);
   if (trials) *trials = g->trials;
   if (persistent) *persistent = g->persist;
+  return DG_OK;
+}
+
+int dg_graph_splits(const dg_graph* g, int* split) {
+  if (!g || !split) return fail(DG_ERR_ARG, "dg_graph_splits: null argument");
+  for (int p = 0; p < 9; ++p) split[p] = g->concurrent && !g->persist ? g->split[p] : 1;
   return DG_OK;
 }
 
@@ -3025,6 +3075,17 @@ int dg_set_tile_variants(dg_ctx* ctx, const int* variants) {
     if (v < 0 || v > 2) return fail(DG_ERR_ARG, "dg_set_tile_variants: variant %d of degree %d outside 0..2", v, p);
   }
   for (int p = 0; p < 9; ++p) ctx->tiles[p] = variants ? variants[p] : 0;
+  return DG_OK;
+}
+
+int dg_set_group_split(dg_ctx* ctx, const int* split) {
+  if (!ctx) return fail(DG_ERR_ARG, "dg_set_group_split: null context");
+  for (int p = 0; p < 9; ++p) {
+    const int v = split ? split[p] : 1;
+    if (v < 1 || v > kMaxSplit)
+      return fail(DG_ERR_ARG, "dg_set_group_split: %d parts for degree %d outside 1..%d", v, p, kMaxSplit);
+  }
+  for (int p = 0; p < 9; ++p) ctx->splits[p] = split ? split[p] : 1;
   return DG_OK;
 }
 

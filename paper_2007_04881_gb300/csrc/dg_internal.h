@@ -213,6 +213,9 @@ struct Tracer {
   const double* flops = nullptr;   // [kKinds][9]
   const double* words = nullptr;   // [kKinds][9]
   const double* xflops = nullptr;  // [9]: flops the kind-2 launch executes
+  // share of its degree group's counts the next begin() records (a group
+  // launched as several parts)
+  double scale = 1.0;
   void begin(const char* name, int kind, int p, size_t tsize, cudaStream_t st);
   // a launch with its counts given directly
   void begin_counts(const char* name, double fl, double xfl, double by, cudaStream_t st);
@@ -231,12 +234,18 @@ struct Tracer {
 int launch_geometry(const DevMesh& m, cudaStream_t st, Tracer* tr = nullptr, int wmask = 3);
 // Launch shape of the row kernels: cap on co-resident CTAs per SM (0: the
 // occupancy limit) and the stream of each degree's launch (index p).
+constexpr int kMaxSplit = 4;  // parts of one degree group
 struct LaunchOpts {
   int occ_cap = 0;
   bool vol_moments = true;  // volume blocks through Legendre-product moments where supported
   bool vol_exact = false;   // 2D: those moments exact, from the element's edges
   int tile[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // register-tile variant of each degree's row kernel
   cudaStream_t pst[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  // each degree group as split[p] (1..kMaxSplit) contiguous parts of equal
+  // element count, part i on stream part[p][i] (part[p][0] = pst[p]): the
+  // parts' moment-then-rows chains run side by side
+  int split[9] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
+  cudaStream_t part[9][kMaxSplit] = {};
 };
 
 // Edge TM of the register tiles of tile variant v of the (dim, p) row kernel

@@ -63,7 +63,37 @@ int launch_row_tile(const DevMesh& m, int mode, T* vals, T* rhs, int sm_count, c
 DG_ROW_TILE_VARIANTS(DG_EXTERN_ROW_TILE)
 
 template <int D, int P, typename T>
+inline int launch_row_range(const DevMesh& m, int mode, T* vals, T* rhs, int sm_count, const LaunchOpts& lo,
+                            Tracer* tr);
+
+// One degree group: in lo.split[P] parts of equal element count, each a copy
+// of the mesh view whose range [elem_pstart[P], elem_pstart[P+1]) is the
+// part's (every kernel takes its elements from that range), on its own stream.
+template <int D, int P, typename T>
 inline int launch_row_p(const DevMesh& m, int mode, T* vals, T* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr) {
+  const int count = m.elem_pstart[P + 1] - m.elem_pstart[P];
+  if (count <= 0) return 0;
+  const int parts = lo.split[P] < 1 ? 1 : lo.split[P] > kMaxSplit ? kMaxSplit : lo.split[P];
+  if (parts == 1) return launch_row_range<D, P, T>(m, mode, vals, rhs, sm_count, lo, tr);
+  int n = 0;
+  const int base = m.elem_pstart[P];
+  for (int i = 0; i < parts; ++i) {
+    DevMesh mp = m;
+    mp.elem_pstart[P] = base + (int)((int64_t)count * i / parts);
+    mp.elem_pstart[P + 1] = base + (int)((int64_t)count * (i + 1) / parts);
+    if (mp.elem_pstart[P + 1] <= mp.elem_pstart[P]) continue;
+    LaunchOpts lp = lo;
+    if (lo.part[P][i]) lp.pst[P] = lo.part[P][i];
+    if (tr) tr->scale = (double)(mp.elem_pstart[P + 1] - mp.elem_pstart[P]) / count;
+    n += launch_row_range<D, P, T>(mp, mode, vals, rhs, sm_count, lp, tr);
+  }
+  if (tr) tr->scale = 1.0;
+  return n;
+}
+
+template <int D, int P, typename T>
+inline int launch_row_range(const DevMesh& m, int mode, T* vals, T* rhs, int sm_count, const LaunchOpts& lo,
+                            Tracer* tr) {
   const int count = m.elem_pstart[P + 1] - m.elem_pstart[P];
   if (count <= 0) return 0;
   cudaStream_t st = lo.pst[P];

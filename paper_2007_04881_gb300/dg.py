@@ -133,6 +133,8 @@ def load() -> C.CDLL:
     lib.dg_mesh_array.argtypes = [V, C.c_char_p, V, C.c_int64, C.POINTER(C.c_int64)]
     lib.dg_wait_probe.argtypes = [V, V, C.c_double]
     lib.dg_set_tile_variants.argtypes = [V, V]
+    lib.dg_set_group_split.argtypes = [V, V]
+    lib.dg_graph_splits.argtypes = [V, V]
     lib.dg_volume_noalloc.argtypes = [V, C.c_int, C.c_int, C.c_int, C.c_int, V, V, C.c_int, C.c_int, V, V, V,
                                       C.c_double, C.c_double, C.c_double, V, V]
     lib.dg_quad_prepare.argtypes = [V, V]
@@ -184,7 +186,7 @@ EXPORTS = (
     "dg_partition", "dg_mesh_upload_part", "dg_part_map", "dg_part_check", "dg_set_volume_path",
     "dg_slab_offsets", "dg_slab_layout", "dg_assemble_slab", "dg_slab_trace", "dg_assemble_varcoef",
     "dg_mlp_save", "dg_mlp_load", "dg_quad_learn", "dg_assemble_batch", "dg_graph_tiles",
-    "dg_set_tile_variants", "dg_set_wait_limit", "dg_wait_probe",
+    "dg_set_tile_variants", "dg_set_group_split", "dg_graph_splits", "dg_set_wait_limit", "dg_wait_probe",
     "dg_set_persistent", "dg_set_pattern_device", "dg_mesh_timings", "dg_mesh_array",
     "dg_slab_graph_create",
 )
@@ -256,6 +258,11 @@ class Context:
         """Row-kernel tile variant per degree (9 ints, or None for the defaults)."""
         v = None if variants is None else np.ascontiguousarray(variants, dtype=np.int32)
         _check(load().dg_set_tile_variants(self._h, _vp(v)))
+
+    def dg_set_group_split(self, split=None):
+        """Parts (1..4) per degree group of untuned concurrent passes (9 ints, or None for all 1)."""
+        v = None if split is None else np.ascontiguousarray(split, dtype=np.int32)
+        _check(load().dg_set_group_split(self._h, _vp(v)))
 
     def dg_set_pattern_device(self, on: bool):
         _check(load().dg_set_pattern_device(self._h, int(bool(on))))
@@ -677,10 +684,13 @@ class Graph:
         tm = np.zeros(9, np.int32)
         tr, pk = C.c_int(), C.c_int()
         _check(load().dg_graph_tiles(self._h, _vp(tm), C.byref(tr), C.byref(pk)))
+        sp = np.ones(9, np.int32)
+        _check(load().dg_graph_splits(self._h, _vp(sp)))
         return {"occ_cap": occ.value, "concurrent": bool(conc.value), "tuned_ms": ms.value, "launches": nl.value,
                 "volume_path": {0: "per-point", 1: "moments", 2: "exact-moments"}.get(vp.value, "per-point"),
                 "tile_tm": {f"p{p}": int(tm[p]) for p in range(9) if tm[p] != 0}, "tuner_trials": tr.value,
-                "persistent": bool(pk.value)}
+                "persistent": bool(pk.value),
+                "split": {f"p{p}": int(sp[p]) for p in range(9) if tm[p] != 0}}
 
     def close(self):
         if getattr(self, "_h", None):

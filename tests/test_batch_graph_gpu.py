@@ -174,3 +174,24 @@ def test_autotuner_records_tiles(ctx):
     assert np.array_equal(v.double().cpu().numpy(), v_ref)
     assert np.array_equal(r.double().cpu().numpy(), r_ref)
     g.close()
+
+
+@pytest.mark.parametrize("which", ["2d", "3d"])
+def test_group_split_bitwise(ctx, which):
+    """Degree groups in parts on their own streams: every element is computed
+    by the same kernel, so the system is bitwise that of whole groups."""
+    if which == "2d":
+        w = configs.small2d(700, 95, 1, 5, b=(1.0, 0.5), c=1.0)
+    else:
+        w = configs.small3d(6, 60, 96, 3, 3)  # one degree group: parts alone make it concurrent
+    m = dg.Mesh(ctx, w.mesh, w.p, w.a, dg_problem(w))
+    v0, r0 = _assemble(ctx, m, dg.DG_PREC_FP32)
+    try:
+        for split in ([1, 2, 3, 4, 2, 3, 1, 1, 1], [1, 4, 4, 4, 4, 4, 4, 1, 1]):
+            ctx.dg_set_group_split(split)
+            v, r = _assemble(ctx, m, dg.DG_PREC_FP32)
+            assert np.array_equal(v, v0) and np.array_equal(r, r0), split
+        with pytest.raises(dg.DGError):
+            ctx.dg_set_group_split([1, 5, 1, 1, 1, 1, 1, 1, 1])
+    finally:
+        ctx.dg_set_group_split(None)
