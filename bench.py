@@ -606,16 +606,7 @@ def run_ours(args):
     dom64 = ("row_pass", kstats64["row_pass"]) if "row_pass" in kstats64 else max(kstats64.items(), key=lambda kv: kv[1][0])
     n64, (tm64, c64, fl64, _) = dom64
     ach64 = fl64 / (tm64 / c64 * 1e-3) / 1e12
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tfile):
-        try:
-            tj = json.load(open(tfile))
-            ent = tj.get(args.workload, {}).get(name)
-            if ent and ent.get("source_sha") == _kernel_source_sha():
-                traffic = ent.get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    traffic = _traffic_entry(args.workload, name) if name in TRAFFIC_GROUPS else None
 
     line = {
         "metric": METRIC,
@@ -817,7 +808,7 @@ def run_slab(args):
         "matrix_gbs": (nv + nd) * 4 / (ms_step * 1e-3) / 1e9,
         "roofline": {
             "bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": _traffic_entry(args.workload, "slab_matrix"),
             "unit_note": f"algorithmic bytes per launch = 4 x (slab entries written {nv} + spatial entries read "
                          f"{int(info.nvals)} + mass-matrix entries read {diag_entries}); peak hbm_gbs of "
                          f"MEASURED_PEAKS.json ({peak_src})",
@@ -835,17 +826,87 @@ def run_slab(args):
     return 0
 
 
-def _kernel_source_sha() -> str:
-    """Hash of the sources the row-pass kernels are compiled from: the
-    dg_row*.cu translation units and every header they include."""
+# kernel groups whose DRAM traffic --record-traffic stores: the ncu kernel
+# names they match, and the sources they are compiled from (translation
+# units by name prefix, and the headers they include)
+TRAFFIC_GROUPS = {
+    "row_pass": {"units": ("dg_row",), "headers": ("dg_device.cuh", "dg_moment.cuh", "dg_launch.cuh",
+                                                   "dg_internal.h"),
+                 "match": ("row_lane_kernel", "row_kernel", "vol_moment_kernel")},
+    "slab_matrix": {"units": ("dg_slab",), "headers": ("dg_slab.cuh", "dg_internal.h"),
+                    "match": ("slab_matrix_kernel",)},
+}
+
+
+def _kernel_source_sha(group="row_pass") -> str:
+    """Hash of the sources a kernel group is compiled from: its translation
+    units, its headers and the library header."""
     import hashlib
 
+    g = TRAFFIC_GROUPS[group]
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2007_04881_gb300", "csrc")
     for fn in sorted(os.listdir(csrc)):
-        if fn.endswith((".cuh", ".h")) or (fn.startswith("dg_row") and fn.endswith(".cu")):
+        if fn in g["headers"] or (fn.startswith(g["units"]) and fn.endswith(".cu")):
             h.update(open(os.path.join(csrc, fn), "rb").read())
+    h.update(open(os.path.join(ROOT, "include", "dg.h"), "rb").read())
     return h.hexdigest()[:16]
+
+
+def _traffic_entry(workload: str, group: str):
+    """Bytes per launch of a kernel group from profiles/traffic.json, or
+    None when absent or taken on other sources."""
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        ent = json.load(open(tfile)).get(workload, {}).get(group)
+        if ent and ent.get("source_sha") == _kernel_source_sha(group):
+            return ent.get("bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def record_traffic(csv_path: str, workload: str, group: str, launches: int) -> int:
+    """Store in profiles/traffic.json the DRAM bytes (read + write) of one
+    launch group from an ncu CSV log (--metrics dram__bytes_read.sum,
+    dram__bytes_write.sum --csv --log-file): the first ``launches`` captured
+    launches of the group's kernels, summed, per kernel name as well, with the
+    hash of the sources they were built from."""
+    import csv
+
+    rows = {}
+    with open(csv_path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for r in csv.DictReader(lines):
+        name = r.get("Kernel Name", "")
+        if not any(name.startswith(k) or (k + "<") in name for k in TRAFFIC_GROUPS[group]["match"]):
+            continue
+        lid = r.get("ID")
+        ent = rows.setdefault(lid, {"kernel": name, "bytes": 0.0})
+        if r.get("Metric Name") in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1024, "MB": 1024 ** 2,
+                     "GB": 1024 ** 3}.get(r.get("Metric Unit", "byte"), 1)
+            ent["bytes"] += float(r["Metric Value"].replace(",", "")) * scale
+    ids = sorted(rows, key=lambda k: int(k))[:launches]
+    if len(ids) < launches:
+        print(f"record-traffic: {len(ids)} launches of {group} in {csv_path}, expected {launches}")
+        return 1
+    per = {}
+    for k in ids:
+        per[rows[k]["kernel"]] = per.get(rows[k]["kernel"], 0) + int(rows[k]["bytes"])
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    tj = json.load(open(tfile)) if os.path.exists(tfile) else {}
+    tj.setdefault(workload, {})[group] = {
+        "bytes_per_launch": int(sum(per.values())),
+        "source_sha": _kernel_source_sha(group),
+        "launches": launches,
+        "per_kernel": per,
+        "note": "dram__bytes_read.sum + dram__bytes_write.sum of the group's captured launches of one pass, "
+                "summed; ncu flushes the caches before each captured launch",
+    }
+    json.dump(tj, open(tfile, "w"), indent=1)
+    print(json.dumps(tj[workload][group]))
+    return 0
 
 
 def run_learned(args):
@@ -1025,7 +1086,13 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=sorted(PRECS),
                     help="form of the timed pass: FP32 contractions, or split-BF16 / 3xTF32 tensor-core contractions")
     ap.add_argument("--epochs", type=int, default=40, help="training epochs of the learned-rule workload")
+    ap.add_argument("--record-traffic", metavar="CSV", help="store the DRAM traffic of --traffic-group from an ncu "
+                    "CSV log in profiles/traffic.json for --workload, and exit")
+    ap.add_argument("--traffic-group", default="row_pass", choices=sorted(TRAFFIC_GROUPS))
+    ap.add_argument("--traffic-launches", type=int, default=6, help="captured launches that make one pass")
     args = ap.parse_args()
+    if args.record_traffic:
+        return record_traffic(args.record_traffic, args.workload, args.traffic_group, args.traffic_launches)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

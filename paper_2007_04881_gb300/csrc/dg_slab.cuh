@@ -127,10 +127,13 @@ struct SlabPattern {
 // of a block sits at row i = x / nts, column q = x % nts; a lane steps x by
 // lanes, so (i, q) advance by (lanes / nts, lanes % nts) with one carry, and
 // (k, j), (l, m) come from the decode tables.  D: the time matrix, [k][l]
-// with stride kSlabKMax.  Stores are contiguous over the lanes.
+// with stride kSlabKMax.  Stores are contiguous over the lanes.  A lane
+// takes four of its entries per round: their indices first, then their four
+// loads, then their four stores, so that four loads are in flight at once.
 template <typename T>
-__host__ __device__ inline void slab_matrix_row(const SlabPattern& sp, const T* D, const SlabDecode& dec, const T* B,
-                                                const T* M, T* vals, int r, int lane, int lanes) {
+__host__ __device__ inline void slab_matrix_row(const SlabPattern& sp, const T* __restrict__ D, const SlabDecode& dec,
+                                                const T* __restrict__ B, const T* __restrict__ M,
+                                                T* __restrict__ vals, int r, int lane, int lanes) {
   const int pr = sp.p[r];
   const int ntr = slab_count(sp.dim, pr, sp.space);
   const unsigned short* dr = dec.kj + dec.off[pr];
@@ -147,7 +150,38 @@ __host__ __device__ inline void slab_matrix_row(const SlabPattern& sp, const T* 
     const int n = ntr * nts;
     const int si = lanes / nts, sq = lanes - si * nts;
     int i = lane / nts, q = lane - (lane / nts) * nts;
-    for (int x = lane; x < n; x += lanes) {
+    int x = lane;
+    for (; x + 3 * lanes < n; x += 4 * lanes) {
+      int at[4], kl[4];
+      bool same[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int kj = dr[i], lm = ds[q];
+        const int k = kj >> 8, l = lm >> 8;
+        at[u] = (kj & 255) * nbs + (lm & 255);
+        kl[u] = k * kSlabKMax + l;
+        same[u] = k == l;
+        i += si;
+        q += sq;
+        if (q >= nts) {
+          q -= nts;
+          ++i;
+        }
+      }
+      T v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) v[u] = same[u] ? Bb[at[u]] : T(0);
+      if (diag) {
+        T w[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) w[u] = Mb[at[u]];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] += D[kl[u]] * w[u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) out[x + u * lanes] = v[u];
+    }
+    for (; x < n; x += lanes) {
       const int kj = dr[i], lm = ds[q];
       const int k = kj >> 8, j = kj & 255, l = lm >> 8, m = lm & 255;
       const int at = j * nbs + m;
