@@ -52,6 +52,9 @@ class _Problem(C.Structure):
         ("c_sigma", C.c_double),
         ("coef", C.c_int),
         ("neumann", C.c_int),
+        ("fb0", C.c_double * 3),
+        ("fbx", C.c_double * 9),
+        ("fc", C.c_double * 20),
     ]
 
 
@@ -166,11 +169,15 @@ def basis(dim: int, p: int, lo, hi, x):
     return phi, grad.reshape(n, dim)
 
 
-def make_problem(dim, b=(0.0, 0.0, 0.0), c=0.0, source=0, poly=None, c_sigma=10.0, coef=0, neumann=0) -> _Problem:
+def make_problem(dim, b=(0.0, 0.0, 0.0), c=0.0, source=0, poly=None, c_sigma=10.0, coef=0, neumann=0,
+                 fields=None) -> _Problem:
     """coef 0: constant b and c; coef 1: the fields b_d = 1 + x_d, c = 3 + prod x_d of
-    the paper's 3D advection-diffusion-reaction test (Sec. 4.2).  neumann: bit
-    2d + s marks the side x_d = min (s = 0) / max (s = 1) of the vertices'
-    bounding box as Neumann boundary (Eq. (2.2)); the rest is Dirichlet."""
+    the paper's 3D advection-diffusion-reaction test (Sec. 4.2).  fields =
+    (b0[3], bx[3][3], c[20]) sets coef 2: b_d = b0[d] + sum_e bx[d][e] x_e and c
+    the polynomial with coefficients c on the graded monomials of poly.
+    neumann: bit 2d + s marks the side x_d = min (s = 0) / max (s = 1) of the
+    vertices' bounding box as Neumann boundary (Eq. (2.2)); the rest is
+    Dirichlet."""
     pb = _Problem()
     pb.dim = dim
     for i in range(3):
@@ -183,6 +190,16 @@ def make_problem(dim, b=(0.0, 0.0, 0.0), c=0.0, source=0, poly=None, c_sigma=10.
     pb.c_sigma = float(c_sigma)
     pb.coef = int(coef)
     pb.neumann = int(neumann)
+    if fields is not None:
+        b0, bx, cc = fields
+        pb.coef = 2
+        bx = np.asarray(bx, dtype=np.float64).reshape(3, 3)
+        for i in range(3):
+            pb.fb0[i] = float(b0[i]) if i < len(b0) else 0.0
+            for j in range(3):
+                pb.fbx[3 * i + j] = float(bx[i, j])
+        for i in range(20):
+            pb.fc[i] = float(cc[i]) if i < len(cc) else 0.0
     return pb
 
 

@@ -219,12 +219,37 @@ typedef struct {
                       x_d = min (s = 0) or x_d = max (s = 1) of the vertices' bounding box;
                       a boundary face all of whose vertices lie on a marked side is a
                       Neumann face, every other boundary face a Dirichlet face */
+  double fb0[3];   /* coef 2: b_d(x) = fb0[d] + sum_e fbx[3 d + e] x_e */
+  double fbx[9];
+  double fc[20];   /* coef 2: c(x) = sum_k fc[k] m_k(x), m_k the graded monomials of degree <= 3
+                      in the order of poly (2D: the first 10) */
 } orc_problem;
+
+static int poly_exps(int dim, int e[][3]);
+static double ipow(double x, int k);
 
 /* Advection and reaction at x.  coef 1 is the paper's multi-GPU test problem
  * (Sec. 4.2: b = (1+x, 1+y, 1+z), c = 3 + xyz), written for any dimension as
- * b_d = 1 + x_d and c = 3 + prod_d x_d. */
+ * b_d = 1 + x_d and c = 3 + prod_d x_d.  coef 2: an affine b and a cubic c
+ * given by their coefficients (fb0, fbx, fc). */
 static void coef_at(const orc_problem *pb, const double *x, double *b, double *c) {
+  if (pb->coef == 2) {
+    for (int d = 0; d < pb->dim; ++d) {
+      double v = pb->fb0[d];
+      for (int e = 0; e < pb->dim; ++e) v += pb->fbx[3 * d + e] * x[e];
+      b[d] = v;
+    }
+    int ex[20][3];
+    int m = poly_exps(pb->dim, ex);
+    double s = 0.0;
+    for (int k = 0; k < m; ++k) {
+      double v = pb->fc[k];
+      for (int d = 0; d < pb->dim; ++d) v *= ipow(x[d], ex[k][d]);
+      s += v;
+    }
+    *c = s;
+    return;
+  }
   if (pb->coef == 1) {
     double prod = 1.0;
     for (int d = 0; d < pb->dim; ++d) {

@@ -68,6 +68,10 @@ MUTATIONS = {
         "if (!(pb->neumann >> (2 * d + s) & 1)) continue;",
         "if (!(pb->neumann >> (d + 2 * s) & 1)) continue;",
     ),
+    "field_table_transposed_gradient": (
+        "for (int e = 0; e < pb->dim; ++e) v += pb->fbx[3 * d + e] * x[e];",
+        "for (int e = 0; e < pb->dim; ++e) v += pb->fbx[3 * e + d] * x[e];",
+    ),
     "neumann_data_without_a": (
         "double g = neumann_g(pb, a[e], &xq[q * dim], f->n);",
         "double g = neumann_g(pb, 1.0, &xq[q * dim], f->n);",
@@ -183,6 +187,19 @@ def _pins_pass(O) -> bool:
                 phi, _ = O.basis(2, int(p[e]), om.lo[e], om.hi[e], x)
                 if abs(phi @ U[off[e]:off[e + 1]] - O.exact_u(pb, x)) > 1e-9:
                     return False
+        # a table of fields (affine b with a non-symmetric gradient, quadratic c)
+        # through the source term
+        b0, B, cc = np.array([0.3, -0.2, 0.0]), np.array([[0.4, -0.7, 0], [0.2, 0.1, 0], [0, 0, 0]]), np.zeros(20)
+        cc[:6] = [1.0, 0.2, -0.5, 0.3, 0.7, -0.1]
+        pbt = O.make_problem(2, source=1, fields=(b0, B, cc))
+        x = np.array([0.3, 0.7])
+        sx, cx = np.sin(np.pi * x), np.cos(np.pi * x)
+        grad = np.pi * np.array([cx[0] * sx[1], sx[0] * cx[1]])
+        bb = b0[:2] + B[:2, :2] @ x
+        c = cc[0] + cc[1] * x[0] + cc[2] * x[1] + cc[3] * x[0] ** 2 + cc[4] * x[0] * x[1] + cc[5] * x[1] ** 2
+        f = 0.5 * 2 * np.pi ** 2 * sx.prod() + bb @ grad + c * sx.prod()
+        if abs(O.source_f(pbt, 0.5, x) - f) > 1e-12 * abs(f):
+            return False
         return True
     except Exception:
         return False
