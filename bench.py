@@ -64,6 +64,10 @@ WORKLOADS = {
                      "kappa x (0, 0.01], space P_p (space-time total degree <= p, p~U{1..4}), FP32: the slab "
                      "matrix and load vector with the previous slab's trace"),
     "slab2d_65k_pq": ("slab2d_65k_pq: as slab2d_65k_p in the space PQ_p (degree <= p in t and in x)"),
+    "adr3d_varcoef": ("adr3d_varcoef: the 3D test problem of Sec. 4.2 (A=0.01 I, b=(1+x,1+y,1+z), c=3+xyz, "
+                      "u=sin(pi x)sin(pi y)sin(pi z)) on 50^3 cubes x 6 Kuhn tets (750,000 tets) grown into polyhedra "
+                      "of about 4 tets (seeded greedy region growing across faces), p=3, FP32: the row pass without b "
+                      "and c, then the variable-coefficient kernels"),
 }
 
 
@@ -103,6 +107,8 @@ def make_workload(name):
         return _Batch(configs.batch2d())
     if name == "learned2d_262k":
         return configs.learned2d()
+    if name == "adr3d_varcoef":
+        return configs.adr3d_varcoef()
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -702,6 +708,178 @@ def slab_cpu_sample(space_name: str, n_sites: int = 40):
                       f"(one thread), {dt:.1f} s"}
 
 
+def varcoef_flops(mesh, p, dim: int) -> float:
+    """Contraction flops of the variable-coefficient kernels over one pass:
+    2 N^2 per volume point and per own-face point of each element, 2 N N_k
+    per interface point of each off-diagonal block (the kernel contracts
+    every point; outflow points carry zero rows), and 2 N per point of the
+    load vector."""
+    from math import comb
+
+    ne = mesh.ne
+    p = np.asarray(p, dtype=np.int64)
+    nb = np.array([comb(int(q) + dim, dim) for q in p], dtype=np.float64)
+    sub = np.bincount(mesh.dg_mesh_array("sub_elem"), minlength=ne).astype(np.float64)
+    nvol = sub * (p + 2.0) ** dim
+    nqf = mesh.dg_mesh_array("e_nqf").astype(np.float64)
+    hf_ptr = mesh.dg_mesh_array("hf_ptr")
+    hf_qoff = mesh.dg_mesh_array("hf_qoff").astype(np.int64)
+    nhf = int(hf_ptr[-1])
+    owner = np.repeat(np.arange(ne), np.diff(hf_ptr))
+    nxt = np.append(hf_qoff[1:], 0)
+    last = np.zeros(nhf, dtype=bool)
+    last[hf_ptr[1:][np.diff(hf_ptr) > 0] - 1] = True
+    pts = np.where(last, nqf[owner].astype(np.int64), nxt) - hf_qoff
+    rec = mesh.dg_mesh_array("blk_rec").reshape(-1, 4)
+    row_ptr = mesh.dg_mesh_array("row_ptr")
+    rows = np.repeat(np.arange(ne), np.diff(row_ptr))
+    off = rec[:, 0] >= 0
+    cs = np.concatenate([[0], np.cumsum(pts)])
+    bpts = cs[rec[off, 1] + rec[off, 2]] - cs[rec[off, 1]]
+    nk = np.array([comb(int(q) + dim, dim) for q in rec[off, 3]], dtype=np.float64)
+    fl = float(np.sum((nvol + nqf) * 2.0 * nb * nb) + np.sum(bpts * 2.0 * nb[rows[off]] * nk) +
+               np.sum((nvol + nqf) * 2.0 * nb))
+    return fl
+
+
+def run_varcoef(args):
+    """The 3D test problem of Sec. 4.2 through dg_assemble_varcoef_form."""
+    wl = make_workload(args.workload)
+    import torch
+
+    from paper_2007_04881_gb300 import build as B
+    from paper_2007_04881_gb300 import dg
+
+    ws, rank, local = dist_setup(True)
+    dev = local if ws > 1 else 0
+    torch.cuda.set_device(dev)
+    B.build()
+    stream = torch.cuda.current_stream()
+    ctx = dg.Context(dev, stream.cuda_stream)
+    mesh = dg.Mesh(ctx, wl.mesh, wl.p, wl.a, dg.Problem(**wl.problem))
+    info = mesh.info
+    prec = dg.DG_PREC_FP32
+    vals = torch.empty(info.nvals, dtype=torch.float32, device="cuda")
+    rhs = torch.empty(info.ndofs, dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    step = lambda: mesh.dg_assemble_varcoef(vals, rhs, prec=prec)  # noqa: E731
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    ctx.dg_set_timing(True)
+    step()
+    torch.cuda.synchronize()
+    launches_per_step = ctx.launches()
+    sampler = ClockSampler(dev)
+    barrier(ws)
+    torch.cuda.synchronize()
+    sampler.start()
+    t_wall = time.perf_counter()
+    times, kstats = time_steps(torch, stream, step, flush, args.steps, ctx)
+    t_wall = time.perf_counter() - t_wall
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop()
+    ctx.dg_set_timing(False)
+    ms_step = max_over_ranks(sum(times) / len(times), ws)
+    value = ws * info.ne / (ms_step * 1e-3)
+
+    # the FP64 form (few steps: FP64 runs at 1/64 of the FP32 rate on this part)
+    v64 = torch.empty(info.nvals, dtype=torch.float64, device="cuda")
+    r64 = torch.empty(info.ndofs, dtype=torch.float64, device="cuda")
+    mesh.dg_assemble_varcoef(v64, r64, prec=dg.DG_PREC_FP64)
+    torch.cuda.synchronize()
+    t64 = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        e0.record(stream)
+        mesh.dg_assemble_varcoef(v64, r64, prec=dg.DG_PREC_FP64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t64.append(e0.elapsed_time(e1))
+    err = {"matrix_rel_fro": float(torch.linalg.norm(vals.double() - v64) / torch.linalg.norm(v64)),
+           "rhs_rel_fro": float(torch.linalg.norm(rhs.double() - r64) / torch.linalg.norm(r64))}
+
+    # end to end through the public calls: the field table from the host, the
+    # system back to pinned host memory
+    hv = torch.empty(info.nvals, dtype=torch.float32).pin_memory()
+    hr = torch.empty(info.ndofs, dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        mesh.dg_mesh_set_fields((1.0, 1.0, 1.0), np.eye(3), [3.0] + [0.0] * 14 + [1.0])
+        mesh.dg_assemble_varcoef(vals, rhs, prec=prec)
+        hv.copy_(vals, non_blocking=True)
+        hr.copy_(rhs, non_blocking=True)
+        torch.cuda.synchronize()
+
+    e2e_steps = max(3, min(args.steps, 10))
+    e2e_step()
+    barrier(ws)
+    t = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    e2e_s = max_over_ranks((time.perf_counter() - t) / e2e_steps, ws)
+    if rank != 0:
+        return 0
+
+    kname = "varcoef_terms_f32"
+    kt = kstats.get(kname)
+    avg_ms = kt[0] / kt[1] if kt else float("nan")
+    flops = varcoef_flops(mesh, wl.p, wl.dim)
+    peaks, peak_src = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    sms = device_sms()
+    alu_peak = fp32_alu_peak_tflops(sm_max, sms)
+    achieved = flops / (avg_ms * 1e-3) / 1e12
+    kern = {k: {"avg_ms": v[0] / v[1], "launches": v[1]} for k, v in sorted(kstats.items())}
+    cfg = workload_config(wl, info, args.workload)
+    cfg["fields"] = "b = (1+x, 1+y, 1+z), c = 3 + xyz (Sec. 4.2), A = 0.01 I"
+    cfg["l2"] = "system larger than L2; L2 flushed between timed steps (256 MiB write, outside the timed region)"
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "elements/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": cfg,
+        "matrix_gbs": (info.nvals + info.ndofs) * 4 / (ms_step * 1e-3) / 1e9,
+        "roofline": {
+            "bound": "alu", "kernel": kname, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+            "frac": achieved / alu_peak, "traffic": None,
+            "peak_note": f"FP32 FMA peak = {sms} SMs x 128 lanes x 2 flops x {sm_max:.0f} MHz (sm_max from "
+                         f"MEASURED_PEAKS.json, {peak_src})",
+            "unit_note": f"{flops:.4g} contraction flops per launch group (2 N^2 per volume and own-face point, "
+                         "2 N N_k per interface point, 2 N per load point) / the launch group's event time",
+        },
+        "kernels": kern,
+        "fp64_form": {"ms_per_step": sum(t64) / len(t64), "value": info.ne / (sum(t64) / len(t64) * 1e-3)},
+        "fp32_vs_fp64": err,
+        "e2e": {"value": ws * info.ne / e2e_s, "unit": "elements/s", "h2d_bytes_per_step": 8 * 32,
+                "d2h_bytes_per_step": (info.nvals + info.ndofs) * 4, "ms_per_step": 1e3 * e2e_s},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks,
+        "timed_wall_s": t_wall,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        import copy
+
+        wo = copy.copy(wl)
+        wo.problem = dict(wl.problem, coef=1)
+        cb, (om, ob) = cpu_baseline_sample(wo, seconds_target=8.0)
+        line["cpu_baseline"] = cb
+        line["error_vs_oracle"] = oracle_error(mesh, vals.double().cpu().numpy(), rhs.double().cpu().numpy(), om, ob)
+    print(json.dumps(line))
+    return 0
+
+
 def run_slab(args):
     """One space-time slab step (dg_assemble_slab) over the adr2d_65k mesh."""
     wl = make_workload(args.workload)
@@ -1101,6 +1279,8 @@ def main():
         return run_learned(args)
     if args.workload.startswith("slab2d"):
         return run_slab(args)
+    if args.workload == "adr3d_varcoef":
+        return run_varcoef(args)
     return run_ours(args)
 
 

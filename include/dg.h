@@ -7,9 +7,10 @@
  *
  * Problem (Sec. 2.1, Eq. (2.1)):  -div(a grad u) + b . grad u + c u = f,
  * with a > 0 piecewise constant per element (A = a I), b and c constant (or,
- * through dg_assemble_varcoef, the variable fields of Sec. 4.2), and
- * u = g_D on the whole boundary (a > 0 makes every boundary point part of
- * the Dirichlet boundary, Sec. 2.1).
+ * through dg_assemble_varcoef, an affine b and a cubic c such as the fields
+ * of Sec. 4.2), u = g_D on the Dirichlet boundary and a grad u . n = g_N on
+ * the Neumann boundary (Eq. (2.2); sides marked in dg_mesh_desc.neumann, the
+ * whole boundary Dirichlet by default).
  * Discretisation (Sec. 2.2): B(u_h, v) = l(v) with the bilinear form of
  * Eq. (2.4) and the load functional of Eq. (2.5); the local space on element
  * k is P_{p_k}, spanned by tensorised orthonormal Legendre polynomials of
@@ -564,20 +565,42 @@ int dg_volume_noalloc(void *stream, int device, int prec, int p, int nv, const d
                       int ne, int nsub, const int *elem_ptr, const int *elem_idx, const double *a, double bx,
                       double by, double c, void *blocks, int *status);
 
-/* Variable advection and reaction, the fields of the paper's multi-GPU test
- * problem (Sec. 4.2): b_d(x) = 1 + x_d and c(x) = 3 + prod_d x_d, evaluated
- * at every quadrature point, with the inflow part of each face decided
- * point by point (b . n < 0; b . n = 0 is outflow).  The mesh must be
- * uploaded with b = 0 and c = 0 (DG_ERR_ARG otherwise): its a, C_sigma and
- * source (DG_SRC_ZERO, or DG_SRC_SINPROD with f = a d pi^2 u + b(x).grad u
- * + c(x) u and g_D = u) apply, and the call supplies b(x) and c(x).
- * vals (device, nvals doubles) and rhs (device, ndofs doubles, may be NULL)
- * are OVERWRITTEN with the whole FP64 system: the row kernels write every
- * term without b and c, then one warp per element row adds the b and c
- * terms of its blocks and load-vector entries (volume points, and the
- * inflow points of its faces).  2D and 3D meshes from dg_mesh_upload or
- * dg_batch_upload without learned rules; DG_ERR_ARG otherwise.
- * Asynchronous on the context stream. */
+/* Advection and reaction fields for dg_assemble_varcoef: an affine b and a
+ * cubic c,
+ *   b_d(x) = b0[d] + sum_e bx[d][e] x_e,   c(x) = sum_k c[k] m_k(x),
+ * m_k the graded monomials of total degree <= 3 in the order of DG_SRC_POLY
+ * (2D: the first 10; the z entries are ignored).  The fields of the paper's
+ * multi-GPU test problem (Sec. 4.2) are b0 = (1, 1, 1), bx = I and c = 3 +
+ * prod_d x_d (c[0] = 3, and c[4] = 1 in 2D, c[15] = 1 in 3D). */
+typedef struct {
+  double b0[3];
+  double bx[3][3];
+  double c[20];
+} dg_fields;
+
+/* The fields dg_assemble_varcoef uses on this mesh (copied; NULL: the Sec.
+ * 4.2 fields, the default).  DG_ERR_ARG for a non-finite coefficient. */
+int dg_mesh_set_fields(dg_mesh *mesh, const dg_fields *fields);
+
+/* Variable advection and reaction: the mesh's fields (dg_mesh_set_fields)
+ * evaluated at every quadrature point, with the inflow part of each face
+ * decided point by point (b . n < 0; b . n = 0 is outflow) and no inflow
+ * term on Neumann faces (Eq. (2.4)).  The mesh must be uploaded with b = 0
+ * and c = 0 (DG_ERR_ARG otherwise): its a, C_sigma, Neumann sides and source
+ * (DG_SRC_ZERO, DG_SRC_SINPROD or DG_SRC_POLY, with f = -a Lap u + b(x) .
+ * grad u + c(x) u, g_D = u, g_N = a grad u . n) apply, and the call supplies
+ * b(x) and c(x).  vals (device, nvals values) and rhs (device, ndofs values,
+ * may be NULL) are OVERWRITTEN with the whole system in prec (DG_PREC_FP64,
+ * or DG_PREC_FP32: FP32 geometry records, field table, basis and
+ * accumulation): the row kernels write every term without b and c, then one
+ * warp per element row adds the b and c terms of its blocks and load-vector
+ * entries.  Each lane of that warp stages one quadrature point of a chunk of
+ * 32 (basis values, weighted field row, load term) in shared memory; 25
+ * lanes then contract the chunk into register tiles of the block.  2D and
+ * 3D meshes from dg_mesh_upload or dg_batch_upload without learned rules;
+ * DG_ERR_ARG otherwise.  Asynchronous on the context stream. */
+int dg_assemble_varcoef_form(dg_ctx *ctx, dg_mesh *mesh, int prec, void *vals, void *rhs);
+/* dg_assemble_varcoef_form with DG_PREC_FP64. */
 int dg_assemble_varcoef(dg_ctx *ctx, dg_mesh *mesh, void *vals, void *rhs);
 
 /* Space-time slabs (Sec. 2.3).  The slab (t0, t1] x D over an uploaded mesh

@@ -88,6 +88,8 @@ def _load():
         lib.orc_geometry.argtypes = [C.c_void_p, _D, _D, _D, _D, _D]
         lib.orc_volume_points.argtypes = [C.c_void_p, C.c_int, C.c_int, _D, _D]
         lib.orc_volume_points.restype = C.c_int
+        lib.orc_volume_point_count.argtypes = [C.c_void_p, C.c_int, C.c_int]
+        lib.orc_volume_point_count.restype = C.c_int
         lib.orc_face_penalty.argtypes = [C.c_void_p, C.c_int, _I, _D, C.c_double]
         lib.orc_face_penalty.restype = C.c_double
         lib.orc_diag_block.argtypes = [C.c_void_p, C.c_int, _I, _D, C.POINTER(_Problem), _D]
@@ -265,7 +267,7 @@ class Mesh:
             pass
 
     def volume_points(self, e: int, n: int):
-        cap = 65536
+        cap = _load().orc_volume_point_count(self._h, int(e), int(n))
         xq = np.zeros(cap * self.dim)
         wq = np.zeros(cap)
         q = _load().orc_volume_points(self._h, int(e), int(n), _dp(xq), _dp(wq))

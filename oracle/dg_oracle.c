@@ -763,6 +763,13 @@ void orc_geometry(const orc_mesh *m, double *vol, double *cen, double *lo, doubl
 /* Volume rule of element e with n Gauss points per collapsed direction:
  * 2D fan triangles (centroid, v_k, v_{k+1}), 3D the element's tetrahedra.
  * Returns the number of points written (x: [q*dim], w: physical weights). */
+/* Number of points orc_volume_points writes for element e: n^dim per
+ * sub-simplex (2D: one triangle per loop edge; 3D: the element's tets). */
+int orc_volume_point_count(const orc_mesh *m, int e, int n) {
+  int per = m->dim == 2 ? n * n : n * n * n;
+  return (m->eptr[e + 1] - m->eptr[e]) * per;
+}
+
 int orc_volume_points(const orc_mesh *m, int e, int n, double *xq, double *wq) {
   int dim = m->dim, q = 0;
   if (dim == 2) {
@@ -865,7 +872,6 @@ double orc_face_penalty(const orc_mesh *m, int face, const int *p, const double 
 /* ------------------------------------------------------------------------ */
 
 #define ORC_NMAX 128
-#define ORC_QMAX 65536
 
 static void elem_basis(const orc_mesh *m, int e, int p, const double *x, double *phi, double *grad) {
   orc_basis(m->dim, p, &m->lo[e * m->dim], &m->hi[e * m->dim], x, phi, grad);
@@ -878,8 +884,9 @@ static void elem_basis(const orc_mesh *m, int e, int p, const double *x, double 
 static void volume_block(const orc_mesh *m, int e, int p, double a, const orc_problem *pb,
                          double *out) {
   int dim = m->dim, n = orc_nbasis(dim, p);
-  double *xq = (double *)malloc(sizeof(double) * ORC_QMAX * 3);
-  double *wq = (double *)malloc(sizeof(double) * ORC_QMAX);
+  int nq_cap = orc_volume_point_count(m, e, p + 2);
+  double *xq = (double *)malloc(sizeof(double) * (size_t)nq_cap * 3);
+  double *wq = (double *)malloc(sizeof(double) * (size_t)nq_cap);
   int nq = orc_volume_points(m, e, p + 2, xq, wq);
   double phi[ORC_NMAX], grad[ORC_NMAX * 3];
   for (int q = 0; q < nq; ++q) {
@@ -1026,8 +1033,9 @@ static void face_rhs(const orc_mesh *m, const orc_face *f, const int *p, const d
 static void volume_rhs(const orc_mesh *m, int e, int p, double a, const orc_problem *pb,
                        double *out) {
   int dim = m->dim, n = orc_nbasis(dim, p);
-  double *xq = (double *)malloc(sizeof(double) * ORC_QMAX * 3);
-  double *wq = (double *)malloc(sizeof(double) * ORC_QMAX);
+  int nq_cap = orc_volume_point_count(m, e, p + 2);
+  double *xq = (double *)malloc(sizeof(double) * (size_t)nq_cap * 3);
+  double *wq = (double *)malloc(sizeof(double) * (size_t)nq_cap);
   int nq = orc_volume_points(m, e, p + 2, xq, wq);
   double phi[ORC_NMAX];
   for (int q = 0; q < nq; ++q) {
@@ -1120,8 +1128,9 @@ int orc_max_threads(void) {
 
 /* int_e x^i y^j (z^k) with the element's volume rule (n points/direction). */
 double orc_moment_rule(const orc_mesh *m, int e, int n, int i, int j, int k) {
-  double *xq = (double *)malloc(sizeof(double) * ORC_QMAX * 3);
-  double *wq = (double *)malloc(sizeof(double) * ORC_QMAX);
+  int nq_cap = orc_volume_point_count(m, e, n);
+  double *xq = (double *)malloc(sizeof(double) * (size_t)nq_cap * 3);
+  double *wq = (double *)malloc(sizeof(double) * (size_t)nq_cap);
   int nq = orc_volume_points(m, e, n, xq, wq), dim = m->dim;
   double s = 0.0;
   for (int q = 0; q < nq; ++q) {

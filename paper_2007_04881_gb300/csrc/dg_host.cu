@@ -286,6 +286,10 @@ struct dg_mesh {
   dg_ctx* ctx = nullptr;
   DevBuf bufs;
   DevMesh dm{};
+  // advection and reaction fields of dg_assemble_varcoef (dg_mesh_set_fields;
+  // default the Sec. 4.2 fields)
+  VcFields fields{};
+  bool fields_set = false;
   dg_bsr_info info{};
   std::vector<int> row_ptr, col;
   std::vector<int64_t> blk_off, dof_off;
@@ -1985,69 +1989,66 @@ int dg_slab_trace(dg_ctx* ctx, const dg_mesh* mesh, int prec, int space, double 
 }
 
 // ---------------------------------------------------------------------------
-// Variable advection and reaction (Sec. 4.2): b_d = 1 + x_d, c = 3 + prod x_d
-// at every point, added by the variable-coefficient kernels (dg_varcoef.cu)
-// to a row pass without b and c.
+// Variable advection and reaction (Sec. 4.2 fields, or an affine b and a
+// cubic c from a table) at every point, added by the variable-coefficient
+// kernels (dg_varcoef_kernel.cuh) to a row pass without b and c.
 // ---------------------------------------------------------------------------
 
-static VcView varcoef_view(const DevMesh& m) {
-  VcView v;
-  v.ne = m.ne;
-  v.nf = m.nf;
-  v.nsub = m.nsub;
-  v.source = m.pb.source;
-  v.p = m.p;
-  v.eptr = m.eptr;
-  v.eg = m.eg64;
-  v.sg = m.sg64;
-  v.fs = m.fs64;
-  v.fsc = m.fsc64;
-  v.f_e0 = m.f_e0;
-  v.f_e1 = m.f_e1;
-  v.f_nq = m.f_nq;
-  v.hf_ptr = m.hf_ptr;
-  v.hf_face = m.hf_face;
-  v.hf_side = m.hf_side;
-  v.if_fptr = m.if_fptr;
-  v.row_ptr = m.row_ptr;
-  v.col = m.col;
-  v.blk_if = m.blk_if;
-  v.blk_off = m.blk_off;
-  v.dof_off = m.dof_off;
-  v.vol_rule = m.rt.vol64;
-  v.face_rule = m.rt.face64;
-  for (int k = 0; k < 8; ++k) {
-    v.vol_off[k] = m.rt.vol_off[k];
-    v.vol_n[k] = m.rt.vol_n[k];
+int dg_mesh_set_fields(dg_mesh* mesh, const dg_fields* f) {
+  if (!mesh) return fail(DG_ERR_ARG, "dg_mesh_set_fields: null mesh");
+  if (!f) {
+    mesh->fields_set = false;
+    return DG_OK;
   }
-  for (int k = 0; k < 10; ++k) {
-    v.face_off[k] = m.rt.face_off[k];
-    v.face_n[k] = m.rt.face_n[k];
+  VcFields v{};
+  for (int d = 0; d < 3; ++d) {
+    v.b0[d] = f->b0[d];
+    for (int e = 0; e < 3; ++e) v.bx[d][e] = f->bx[d][e];
   }
-  return v;
+  for (int k = 0; k < 20; ++k) v.c[k] = f->c[k];
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(v.b0[k]) || !std::isfinite(v.bx[k][0]) || !std::isfinite(v.bx[k][1]) || !std::isfinite(v.bx[k][2]))
+      return fail(DG_ERR_ARG, "dg_mesh_set_fields: non-finite b coefficient");
+  for (int k = 0; k < 20; ++k)
+    if (!std::isfinite(v.c[k])) return fail(DG_ERR_ARG, "dg_mesh_set_fields: non-finite c coefficient");
+  // the third coordinate does not exist in 2D
+  if (mesh->dm.dim == 2) {
+    v.b0[2] = 0.0;
+    for (int e = 0; e < 3; ++e) v.bx[2][e] = v.bx[e][2] = 0.0;
+    for (int k = 10; k < 20; ++k) v.c[k] = 0.0;
+  }
+  v.round_copies();
+  mesh->fields = v;
+  mesh->fields_set = true;
+  return DG_OK;
 }
 
-int dg_assemble_varcoef(dg_ctx* ctx, dg_mesh* mesh, void* vals, void* rhs) {
+int dg_assemble_varcoef_form(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs) {
   if (!ctx || !mesh || !vals) return fail(DG_ERR_ARG, "dg_assemble_varcoef: null argument");
+  if (prec != DG_PREC_FP64 && prec != DG_PREC_FP32)
+    return fail(DG_ERR_ARG, "dg_assemble_varcoef: precision %d (DG_PREC_FP64 or DG_PREC_FP32)", prec);
   const DevMesh& m = mesh->dm;
   if (!mesh->part_elem.empty()) return fail(DG_ERR_ARG, "dg_assemble_varcoef: partition meshes are not supported");
   if (m.pb.b[0] != 0.0 || m.pb.b[1] != 0.0 || m.pb.b[2] != 0.0 || m.pb.c != 0.0)
     return fail(DG_ERR_ARG, "dg_assemble_varcoef: upload the mesh with b = 0 and c = 0 (the call supplies b(x), c(x))");
-  if (m.pb.source != DG_SRC_ZERO && m.pb.source != DG_SRC_SINPROD)
-    return fail(DG_ERR_ARG, "dg_assemble_varcoef: source %d (DG_SRC_ZERO or DG_SRC_SINPROD)", m.pb.source);
   if (m.lq_ok) return fail(DG_ERR_ARG, "dg_assemble_varcoef: learned volume rules are installed");
   // every term without b and c: the row kernels
-  int rc = run_assembly(ctx, mesh, DG_PREC_FP64, kModeVol | kModeFace | (rhs ? kModeRhs : 0), vals, rhs, true);
+  int rc = run_assembly(ctx, mesh, prec, kModeVol | kModeFace | (rhs ? kModeRhs : 0), vals, rhs, true);
   if (rc != DG_OK) return rc;
   int n = ctx->last_launches;
+  const VcFields f = mesh->fields_set ? mesh->fields : vc_sec42_fields(m.dim);
   Tracer* tr = &ctx->tracer;
-  tr->begin("varcoef_terms_f64", kKinds, 0, 8, ctx->stream);
-  n += launch_varcoef(varcoef_view(m), m.dim, static_cast<double*>(vals), static_cast<double*>(rhs), ctx->sm_count,
-                      ctx->stream);
+  const bool fp32 = prec == DG_PREC_FP32;
+  tr->begin(fp32 ? "varcoef_terms_f32" : "varcoef_terms_f64", kKinds, 0, fp32 ? 4 : 8, ctx->stream);
+  n += launch_varcoef(m, f, fp32, vals, rhs, ctx->sm_count, ctx->stream);
   tr->end(ctx->stream);
   DG_CUDA_TRY(cudaGetLastError());
   ctx->last_launches = n;
   return DG_OK;
+}
+
+int dg_assemble_varcoef(dg_ctx* ctx, dg_mesh* mesh, void* vals, void* rhs) {
+  return dg_assemble_varcoef_form(ctx, mesh, DG_PREC_FP64, vals, rhs);
 }
 
 int dg_batch_upload(dg_ctx* ctx, const dg_mesh_desc* const* descs, int n, dg_mesh** out) {

@@ -73,6 +73,10 @@ class dg_quad_stats(C.Structure):
                 ("max_accepted_residual", C.c_float)]
 
 
+class dg_fields(C.Structure):
+    _fields_ = [("b0", C.c_double * 3), ("bx", (C.c_double * 3) * 3), ("c", C.c_double * 20)]
+
+
 class dg_bsr_info(C.Structure):
     _fields_ = [
         ("ne", C.c_int),
@@ -168,6 +172,8 @@ def load() -> C.CDLL:
     lib.dg_assemble_slab.argtypes = [V, V, C.c_int, C.c_int, C.c_double, C.c_double, V, V, V]
     lib.dg_slab_trace.argtypes = [V, V, C.c_int, C.c_int, C.c_double, C.c_double, V, V]
     lib.dg_assemble_varcoef.argtypes = [V, V, V, V]
+    lib.dg_assemble_varcoef_form.argtypes = [V, V, C.c_int, V, V]
+    lib.dg_mesh_set_fields.argtypes = [V, V]
     _lib = lib
     return lib
 
@@ -184,7 +190,7 @@ EXPORTS = (
     "dg_mlp_create", "dg_mlp_free", "dg_mlp_num_params", "dg_mlp_get_params", "dg_mlp_set_params",
     "dg_mlp_get_state", "dg_mlp_set_state", "dg_mlp_forward", "dg_mlp_grad", "dg_mlp_train_step",
     "dg_partition", "dg_mesh_upload_part", "dg_part_map", "dg_part_check", "dg_set_volume_path",
-    "dg_slab_offsets", "dg_slab_layout", "dg_assemble_slab", "dg_slab_trace", "dg_assemble_varcoef",
+    "dg_slab_offsets", "dg_slab_layout", "dg_assemble_slab", "dg_slab_trace", "dg_assemble_varcoef", "dg_assemble_varcoef_form", "dg_mesh_set_fields",
     "dg_mlp_save", "dg_mlp_load", "dg_quad_learn", "dg_assemble_batch", "dg_graph_tiles",
     "dg_set_tile_variants", "dg_set_group_split", "dg_graph_splits", "dg_set_wait_limit", "dg_wait_probe",
     "dg_set_persistent", "dg_set_pattern_device", "dg_mesh_timings", "dg_mesh_array",
@@ -527,9 +533,32 @@ class Mesh:
     def dg_quad_clear(self):
         _check(load().dg_quad_clear(self.ctx._h, self._h))
 
-    def dg_assemble_varcoef(self, vals, rhs=None):
-        """FP64 system with b(x) = 1 + x, c(x) = 3 + prod x (the mesh uploaded with b = 0, c = 0)."""
-        _check(load().dg_assemble_varcoef(self.ctx._h, self._h, _vp(vals), _vp(rhs)))
+    def dg_assemble_varcoef(self, vals, rhs=None, prec=None):
+        """The system with the mesh's fields b(x), c(x) (dg_mesh_set_fields; the
+        Sec. 4.2 fields by default) in prec (FP64 by default, or FP32); the
+        mesh is uploaded with b = 0, c = 0."""
+        if prec is None:
+            _check(load().dg_assemble_varcoef(self.ctx._h, self._h, _vp(vals), _vp(rhs)))
+        else:
+            _check(load().dg_assemble_varcoef_form(self.ctx._h, self._h, int(prec), _vp(vals), _vp(rhs)))
+
+    def dg_mesh_set_fields(self, b0=None, bx=None, c=None):
+        """Fields b_d = b0[d] + sum_e bx[d][e] x_e and c = sum_k c[k] m_k(x) (graded
+        monomials of degree <= 3); no arguments: the Sec. 4.2 fields."""
+        if b0 is None and bx is None and c is None:
+            _check(load().dg_mesh_set_fields(self._h, None))
+            return
+        f = dg_fields()
+        b0 = list(b0) if b0 is not None else [0.0] * 3
+        bx = np.zeros((3, 3)) if bx is None else np.asarray(bx, dtype=np.float64).reshape(3, 3)
+        c = list(c) if c is not None else []
+        for d in range(3):
+            f.b0[d] = float(b0[d]) if d < len(b0) else 0.0
+            for e in range(3):
+                f.bx[d][e] = float(bx[d, e])
+        for k in range(20):
+            f.c[k] = float(c[k]) if k < len(c) else 0.0
+        _check(load().dg_mesh_set_fields(self._h, C.byref(f)))
 
     def dg_slab_layout(self, space: int):
         """(nvals, ndofs) of the space-time slab system over this mesh."""

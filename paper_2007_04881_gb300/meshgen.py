@@ -411,6 +411,74 @@ def kuhn_cube_agglomerated(n: int, n_clusters: int, seed: int, iters: int = 10) 
     return Mesh3D(x=d["x"], y=d["y"], z=d["z"], elem_tptr=d["elem_tptr"], tet_v=d["tet_v"])
 
 
+def kuhn_cube_grown(n: int, size: int, seed: int) -> Mesh3D:
+    """Agglomerate the Kuhn tetrahedra of an n^3 cube mesh into small
+    polyhedra of about ``size`` tetrahedra each, by greedy region growing:
+    the tetrahedra are visited in a seeded random order, and each one not yet
+    taken starts a new element that grows breadth-first across shared faces
+    until it holds ``size`` tetrahedra or has no free neighbour left.  An
+    element that stays a single tetrahedron joins the smallest element it
+    shares a face with.  Every element is face-connected by construction and
+    holds at most 2 size - 1 tetrahedra (k-means with a few tetrahedra per
+    cluster fragments, and its repair can chain fragments into very large
+    elements)."""
+
+    def build():
+        from collections import deque
+
+        x, y, z, T = kuhn_cube_tets(n)
+        nt = T.shape[0]
+        adj = _tet_face_adjacency(T)
+        a = np.concatenate([adj[:, 0], adj[:, 1]])
+        b = np.concatenate([adj[:, 1], adj[:, 0]])
+        o = np.argsort(a, kind="stable")
+        nbr = b[o].astype(np.int64)
+        ptr = np.zeros(nt + 1, dtype=np.int64)
+        ptr[1:] = np.cumsum(np.bincount(a, minlength=nt))
+        nbr_l, ptr_l = nbr.tolist(), ptr.tolist()
+        order = np.random.default_rng(seed).permutation(nt).tolist()
+        lab = [-1] * nt
+        sizes = []
+        for t in order:
+            if lab[t] >= 0:
+                continue
+            c = len(sizes)
+            lab[t] = c
+            cnt = 1
+            q = deque([t])
+            while q and cnt < size:
+                u = q.popleft()
+                for v in nbr_l[ptr_l[u]:ptr_l[u + 1]]:
+                    if lab[v] < 0 and cnt < size:
+                        lab[v] = c
+                        cnt += 1
+                        q.append(v)
+            sizes.append(cnt)
+        # single tetrahedra join their smallest neighbouring element
+        for t in range(nt):
+            c = lab[t]
+            if sizes[c] != 1:
+                continue
+            best = -1
+            for v in nbr_l[ptr_l[t]:ptr_l[t + 1]]:
+                if lab[v] != c and sizes[lab[v]] < size * 2 - 1 and (best < 0 or sizes[lab[v]] < sizes[best]):
+                    best = lab[v]
+            if best >= 0:
+                sizes[best] += 1
+                sizes[c] = 0
+                lab[t] = best
+        lab = np.asarray(lab, dtype=np.int64)
+        used, lab = np.unique(lab, return_inverse=True)
+        order_t = np.argsort(lab, kind="stable")
+        cnt = np.bincount(lab, minlength=used.size)
+        tptr = np.zeros(used.size + 1, dtype=np.int32)
+        tptr[1:] = np.cumsum(cnt)
+        return {"x": x, "y": y, "z": z, "elem_tptr": tptr, "tet_v": T[order_t].ravel().astype(np.int32)}
+
+    d = _cached(f"kuhn3d_grown:{n}:{size}:{seed}:v1", build)
+    return Mesh3D(x=d["x"], y=d["y"], z=d["z"], elem_tptr=d["elem_tptr"], tet_v=d["tet_v"])
+
+
 def box_tets(nx: int, ny: int, nz: int, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)) -> Mesh3D:
     """Structured box mesh: one element per cube, each cube = 6 Kuhn tets."""
     xs = np.linspace(lo[0], hi[0], nx + 1)

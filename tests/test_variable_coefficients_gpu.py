@@ -9,8 +9,14 @@ the same fields (oracle coef 1).
   bound of the constant-coefficient path).
 - The full-size 65,536-cell mesh: a seeded sample of 300 elements and
   interfaces against oracle blocks computed one by one.
-- The argument checks: a mesh uploaded with b or c, the polynomial source
-  and a partition mesh are refused.
+- Fields from a table (dg_mesh_set_fields: an affine b with a full
+  gradient, a cubic c) against the oracle's coef 2, FP64 at 1e-12 and the
+  FP32 form at the FP32 tolerances of the other parity tests (5e-5 per
+  block, 1e-4 per load-vector segment).
+- Polynomial reproduction through the GPU system with table fields and
+  mixed Dirichlet/Neumann sides.
+- The argument checks: a mesh uploaded with b or c, a precision other than
+  FP64/FP32 and a partition mesh are refused.
 """
 import numpy as np
 import pytest
@@ -105,12 +111,94 @@ def test_argument_checks(ctx):
 
     wl = configs.small2d(60, 3, 1, 3)
     v = torch.zeros(1 << 16, dtype=torch.float64, device="cuda")
-    for pb in (dg.Problem(b=(1.0, 0.0, 0.0), source=1), dg.Problem(c=0.5, source=1), dg.Problem(source=2)):
+    for pb in (dg.Problem(b=(1.0, 0.0, 0.0), source=1), dg.Problem(c=0.5, source=1)):
         m = dg.Mesh(ctx, wl.mesh, wl.p, wl.a, pb)
         with pytest.raises(dg.DGError) as ei:
             m.dg_assemble_varcoef(v)
         assert ei.value.code == -1
+    m = dg.Mesh(ctx, wl.mesh, wl.p, wl.a, dg.Problem(source=1))
+    with pytest.raises(dg.DGError):
+        m.dg_assemble_varcoef(v, prec=dg.DG_PREC_BF16X3)
+    with pytest.raises(dg.DGError):
+        m.dg_mesh_set_fields(b0=(float("nan"), 0, 0))
     part = dg.dg_partition(wl.mesh, wl.p, wl.a, dg.Problem(source=1), 2)
     mp = dg.Mesh(ctx, wl.mesh, wl.p, wl.a, dg.Problem(source=1), part=part, my_part=0)
     with pytest.raises(dg.DGError):
         mp.dg_assemble_varcoef(v)
+
+
+TOL32 = 5e-5
+TOL32_RHS = 1e-4
+# an affine b with every gradient entry set and a cubic c (2D: the first 10
+# monomials; 3D: all 20)
+FIELDS = {
+    2: ((0.7, -0.4, 0.0), [[0.3, -0.2, 0.0], [0.5, 0.1, 0.0], [0.0, 0.0, 0.0]],
+        [1.0, 0.5, -0.3, 0.2, 0.1, 0.3, 0.2, -0.1, 0.15, 0.05]),
+    3: ((0.8, -0.3, 0.5), [[0.2, 0.1, -0.1], [0.0, 0.3, 0.2], [-0.2, 0.1, 0.1]],
+        [1.5, 0.2, -0.1, 0.3, 0.1, 0.05, 0.2, -0.1, 0.1, 0.05, 0.1, 0.0, 0.05, 0.1, -0.05, 0.2, 0.0, 0.1, 0.05, 0.1]),
+}
+
+
+def _run_fields(ctx, wl, prec, fields, source, neumann=0, poly=()):
+    import torch
+
+    m = dg.Mesh(ctx, wl.mesh, wl.p, wl.a, dg.Problem(source=source, poly=list(poly), neumann=neumann))
+    if fields is not None:
+        m.dg_mesh_set_fields(*fields)
+    dt = torch.float64 if prec == dg.DG_PREC_FP64 else torch.float32
+    vals = torch.full((m.nvals,), float("nan"), dtype=dt, device="cuda")
+    rhs = torch.full((m.ndofs,), float("nan"), dtype=dt, device="cuda")
+    m.dg_assemble_varcoef(vals, rhs, prec=prec)
+    ctx.dg_sync()
+    v, r = vals.double().cpu().numpy(), rhs.double().cpu().numpy()
+    assert np.isfinite(v).all() and np.isfinite(r).all()
+    return m, v, r
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("prec", [dg.DG_PREC_FP64, dg.DG_PREC_FP32])
+@pytest.mark.parametrize("table", [False, True])
+def test_fields_and_forms_vs_oracle(ctx, dim, prec, table):
+    from .helpers import compare
+
+    wl = configs.small2d(180, 7, 1, 6) if dim == 2 else configs.small3d(4, 10, 5, 1, 4)
+    fields = FIELDS[dim] if table else None
+    m, v, r = _run_fields(ctx, wl, prec, fields, configs.SRC_SINPROD)
+    om = O.Mesh(wl.mesh)
+    pb = O.make_problem(dim, source=1, c_sigma=10.0, coef=1, fields=fields)
+    ob = om.assemble(np.asarray(wl.p, np.int32), wl.a, pb)
+    ed, eo, er = compare(dg.to_blocks(m, v, r), om, ob, wl)
+    if prec == dg.DG_PREC_FP64:
+        assert ed < TOL64 and eo < TOL64 and er < TOL64, (ed, eo, er)
+    else:
+        assert ed < TOL32 and eo < TOL32 and er < TOL32_RHS, (ed, eo, er)
+
+
+@pytest.mark.parametrize("neumann", [0, 0b10])
+def test_fields_polynomial_reproduction_through_gpu(ctx, neumann):
+    """u in P_p with table fields (quadratic c, so the 2D rules stay exact)
+    and, optionally, the outflow side x = 1 Neumann: the GPU system's
+    solution is u (dG consistency of Eq. (2.4), (2.5) with variable b, c)."""
+    poly = [1, 1, 0.5, 1, -0.7, 0.4, 0.3, 0, 0, -1]
+    fields = ((0.7, -0.4, 0.0), [[0.3, -0.2, 0], [0.5, 0.1, 0], [0, 0, 0]], [1.0, 0.5, -0.3, 0.2, 0.1, 0.0])
+    wl = configs.small2d(40, 21, 3, 4)
+    wl.a[:] = 0.37
+    m, v, r = _run_fields(ctx, wl, dg.DG_PREC_FP64, fields, configs.SRC_POLY, neumann=neumann, poly=poly)
+    row_ptr, col, blk_off, dof_off = m.dg_bsr_pattern()
+    N = int(dof_off[-1])
+    A = np.zeros((N, N))
+    for rr in range(m.ne):
+        for k in range(row_ptr[rr], row_ptr[rr + 1]):
+            cc = col[k]
+            A[dof_off[rr]:dof_off[rr + 1], dof_off[cc]:dof_off[cc + 1]] = v[blk_off[k]:blk_off[k + 1]].reshape(
+                dof_off[rr + 1] - dof_off[rr], dof_off[cc + 1] - dof_off[cc])
+    U = np.linalg.solve(A, r)
+    om = O.Mesh(wl.mesh)
+    pb = O.make_problem(2, source=2, poly=poly)
+    err = 0.0
+    for e in range(om.ne):
+        xq, _ = om.volume_points(e, 3)
+        for x in xq[::4]:
+            phi, _ = O.basis(2, int(wl.p[e]), om.lo[e], om.hi[e], x)
+            err = max(err, abs(phi @ U[dof_off[e]:dof_off[e + 1]] - O.exact_u(pb, x)))
+    assert err < 1e-9, err
