@@ -104,6 +104,8 @@ def _load():
         lib.orc_moment_rule.restype = C.c_double
         lib.orc_moment_divergence2d.argtypes = [C.c_int, _D, _D, C.c_int, C.c_int]
         lib.orc_moment_divergence2d.restype = C.c_double
+        lib.orc_moment_divergence3d.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]
+        lib.orc_moment_divergence3d.restype = C.c_double
         lib.orc_volume_block.argtypes = [C.c_void_p, C.c_int, _I, _D, C.POINTER(_Problem), _D]
         lib.orc_face_info.argtypes = [C.c_void_p, C.c_int, _I, _I, _D, _D]
         lib.orc_face_points.argtypes = [C.c_void_p, C.c_int, C.c_int, _D, _D]
@@ -275,6 +277,10 @@ class Mesh:
 
     def moment_rule(self, e: int, n: int, i: int, j: int, k: int = 0) -> float:
         return _load().orc_moment_rule(self._h, int(e), int(n), int(i), int(j), int(k))
+
+    def moment_divergence3d(self, e: int, i: int, j: int, k: int) -> float:
+        """int_e x^i y^j z^k by the divergence theorem over the element's boundary triangles."""
+        return _load().orc_moment_divergence3d(self._h, int(e), int(i), int(j), int(k))
 
     def assemble(self, p, a, pb: _Problem, elems=None, ifaces=None, rhs=True, diag=True, nthreads=0):
         """Oracle blocks for the listed elements (default all) and interfaces."""

@@ -1164,6 +1164,32 @@ double orc_moment_divergence2d(int nvert, const double *xs, const double *ys, in
   return s / (i + 1);
 }
 
+/* 3D: int_e x^i y^j z^k = 1/(i+1) * sum over the element's boundary
+ * triangles F of int_F x^(i+1) y^j z^k n_x dS (divergence theorem with the
+ * field (x^(i+1) y^j z^k / (i+1), 0, 0)), n the unit normal out of e; each
+ * triangle integral by the collapsed rule with enough points for degree
+ * i+j+k+1 (exact to 2n-2). */
+double orc_moment_divergence3d(const orc_mesh *m, int e, int i, int j, int k) {
+  int deg = i + j + k + 1, n = deg / 2 + 2;
+  double r[1024], sq[1024], w[1024];
+  int nq = orc_tri_rule(n, r, sq, w);
+  double s = 0.0;
+  for (int t = m->efptr[e]; t < m->efptr[e + 1]; ++t) {
+    const orc_face *f = &m->f[m->ef[t]];
+    double nx = f->e[0] == e ? f->n[0] : -f->n[0];
+    double A[3], B[3], C[3];
+    vtx(m, f->v[0], A);
+    vtx(m, f->v[1], B);
+    vtx(m, f->v[2], C);
+    for (int q = 0; q < nq; ++q) {
+      double x[3];
+      for (int d = 0; d < 3; ++d) x[d] = A[d] + r[q] * (B[d] - A[d]) + sq[q] * (C[d] - A[d]);
+      s += w[q] * 2.0 * f->area * ipow(x[0], i + 1) * ipow(x[1], j) * ipow(x[2], k) * nx;
+    }
+  }
+  return s / (i + 1);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Per-piece access for the pins                                             */
 /* ------------------------------------------------------------------------ */

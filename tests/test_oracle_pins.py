@@ -766,3 +766,101 @@ def test_field_table_through_the_source():
             c = float(np.dot(cc[:len(mons)], mons))
             f = a * dim * np.pi ** 2 * u + b @ grad + c * u
             assert abs(O.source_f(pb, a, x) - f) < 1e-12 * (1 + abs(f)), (dim, x)
+
+
+# ---------------------------------------------------------------------------
+# 3D moments by the divergence theorem (the exact-moment volume path)
+# ---------------------------------------------------------------------------
+
+
+@pytest.mark.parametrize("p", [1, 2, 3])
+def test_tet_rule_moments_match_divergence_theorem_3d(p):
+    """The sub-tetrahedron rule ((p+2)^3 collapsed points per tet) integrates
+    every monomial of degree <= 2p+1 over an agglomerated polyhedron exactly:
+    equal to the divergence theorem over the element's boundary triangles."""
+    om = O.Mesh(mg.kuhn_cube_agglomerated(4, 10, seed=5))
+    for e in range(0, om.ne, 3):
+        for i in range(2 * p + 2):
+            for j in range(2 * p + 2 - i):
+                for k in range(2 * p + 2 - i - j):
+                    ex = om.moment_divergence3d(e, i, j, k)
+                    got = om.moment_rule(e, p + 2, i, j, k)
+                    assert abs(got - ex) <= 1e-13 * abs(om.vol[e]), (e, i, j, k, got, ex)
+
+
+def _boundary_triangles(mesh, e):
+    """The element's boundary triangles (tet faces seen once inside the
+    element), each oriented with its normal pointing out of the element."""
+    T = mesh.tet_v.reshape(-1, 4)[mesh.elem_tptr[e]:mesh.elem_tptr[e + 1]]
+    X = np.c_[mesh.x, mesh.y, mesh.z]
+    seen = {}
+    for t in T:
+        for o in range(4):
+            f = [t[i] for i in range(4) if i != o]
+            seen.setdefault(tuple(sorted(f)), []).append((f, t[o]))
+    out = []
+    for lst in seen.values():
+        if len(lst) != 1:
+            continue
+        f, opp = lst[0]
+        A, B, C = X[f[0]], X[f[1]], X[f[2]]
+        n = np.cross(B - A, C - A)
+        if np.dot(n, X[opp] - A) > 0:
+            B, C = C, B
+        out.append((A, B, C))
+    return out
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_divergence_legendre_moments_3d_with_p_plus_2_triangle_points(p):
+    """The identity behind the 3D exact-moment volume path.  With the
+    element's box coordinates xi = 2 (x - lo) / L - 1, the integral of
+    P_c(xi) P_d(eta) P_e(zeta) over the polyhedron equals the sum over its
+    boundary triangles of the integral of (L_x / 2) Q_c(xi) P_d(eta) P_e(zeta)
+    n_x dS, with Q_c the antiderivative of P_c (Q_0 = P_1, Q_c = (P_{c+1} -
+    P_{c-1}) / (2c + 1)).  On a triangle that integrand has degree
+    c + d + e + 1 <= 2p + 1, so the collapsed rule with p + 2 points per
+    direction (exact to 2p + 2) is exact.  The reference is the sub-tet rule
+    written out here with numpy."""
+    from numpy.polynomial import legendre as npl
+
+    def leg(k, x):
+        return npl.legval(x, [0.0] * k + [1.0])
+
+    def qleg(c, x):
+        return x if c == 0 else (leg(c + 1, x) - leg(c - 1, x)) / (2 * c + 1)
+
+    mesh = mg.kuhn_cube_agglomerated(4, 10, seed=5)
+    tr, ts, tt, tw = O.tet_rule(p + 2)
+    fr, fs, fw = O.tri_rule(p + 2)
+    q = 2 * p
+    X = np.c_[mesh.x, mesh.y, mesh.z]
+    for e in range(0, mesh.ne, 2):
+        T = mesh.tet_v.reshape(-1, 4)[mesh.elem_tptr[e]:mesh.elem_tptr[e + 1]]
+        V = X[np.unique(T)]
+        lo, L = V.min(axis=0), V.max(axis=0) - V.min(axis=0)
+        # volume points of the sub-tet rule, in box coordinates
+        VP, VW = [], []
+        for t in T:
+            P0, P1, P2, P3 = X[t]
+            J = abs(np.dot(P1 - P0, np.cross(P2 - P0, P3 - P0)))
+            VP.append(P0 + np.outer(tr, P1 - P0) + np.outer(ts, P2 - P0) + np.outer(tt, P3 - P0))
+            VW.append(tw * J)
+        VP = 2 * (np.concatenate(VP) - lo) / L - 1
+        VW = np.concatenate(VW)
+        # boundary points with the weight (L_x / 2) n_x dS
+        BP, BW = [], []
+        for A, B, C in _boundary_triangles(mesh, e):
+            n = np.cross(B - A, C - A)
+            area2 = np.linalg.norm(n)
+            BP.append(A + np.outer(fr, B - A) + np.outer(fs, C - A))
+            BW.append(fw * area2 * (n[0] / area2) * L[0] / 2)
+        BP = 2 * (np.concatenate(BP) - lo) / L - 1
+        BW = np.concatenate(BW)
+        scale = np.sum(VW)
+        for c in range(q + 1):
+            for d in range(q + 1 - c):
+                for f in range(q + 1 - c - d):
+                    vol = np.sum(VW * leg(c, VP[:, 0]) * leg(d, VP[:, 1]) * leg(f, VP[:, 2]))
+                    div = np.sum(BW * qleg(c, BP[:, 0]) * leg(d, BP[:, 1]) * leg(f, BP[:, 2]))
+                    assert abs(div - vol) < 1e-12 * scale, (e, c, d, f, div, vol)
