@@ -291,13 +291,17 @@ int dg_batch_offsets(const dg_mesh *mesh, int *nmesh, int *elem_off, int64_t *va
  *     in FP64; 3D p = 2, 3 in FP32, p = 2 in FP64) in the FP32 and FP64
  *     forms; the diagonal block is then written by a separate moment
  *     launch and the row kernel adds the face terms to it.
- *   path 2: as path 1, but in 2D the moments are exact, by Green's theorem
- *     along the element's loop: mu_cd = (L_1 L_2 / 4) times the closed
- *     integral of Q_c(xi) P_d(eta) d eta, Q_c an antiderivative of P_c, with
- *     the (p + 1)-point Gauss rule on each edge (exact: degree <= 2p + 1).
- *     For the polynomial volume integrands of constant coefficients this is
- *     the sub-triangle rule's value up to rounding; the load vector (a
- *     general source) keeps the rule's points.  3D as path 1.
+ *   path 2: as path 1, but the moments are exact, from the element's
+ *     boundary (Sec. 1 and Sec. 3: integrals of homogeneous functions moved
+ *     to the boundary).  2D, by Green's theorem along the loop: mu_cd =
+ *     (L_1 L_2 / 4) times the closed integral of Q_c(xi) P_d(eta) d eta, Q_c
+ *     an antiderivative of P_c, with the (p + 1)-point Gauss rule on each
+ *     edge (exact: degree <= 2p + 1).  3D, by the divergence theorem with
+ *     the field (L_1 / 2) Q_c P_d P_e e_1 over the element's boundary
+ *     triangles, with the collapsed rule of p + 2 points per direction
+ *     (exact: degree <= 2p + 2).  For the polynomial volume integrands of
+ *     constant coefficients this is the sub-simplex rule's value up to
+ *     rounding; the load vector (a general source) keeps the rule's points.
  *   path 0: the per-point block contraction in the row kernels throughout.
  * The tensor-core forms always take their own contraction.  A mesh with
  * learned rules installed (28 points per element) takes the per-point path

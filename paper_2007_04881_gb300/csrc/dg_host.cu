@@ -190,7 +190,7 @@ struct dg_ctx {
   RuleTables rt[4];  // indexed by dim (2, 3)
   Tracer tracer;
   bool vol_moments = true;  // volume blocks through Legendre-product moments
-  bool vol_exact = false;   // 2D: those moments exact, by Green's theorem along the edges
+  bool vol_exact = false;   // those moments exact (2D: Green's theorem along the edges; 3D: the divergence theorem on the boundary triangles)
   int tiles[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // row-kernel tile variants of untuned passes
   int splits[9] = {1, 1, 1, 1, 1, 1, 1, 1, 1};  // parts of each degree group in untuned concurrent passes
   int* status_dev = nullptr;  // bit 0: a bounded device wait ran out (read and cleared by dg_sync)
@@ -2504,7 +2504,7 @@ static int issue_persist_rows(dg_ctx* ctx, dg_mesh* mesh, int prec, int mode, vo
   a.mode = mode;
   a.mom_mask = mom_mask;
   const bool exact = vpath >= 0 ? vpath == 2 : ctx->vol_exact;
-  a.exact = exact && mesh->dm.dim == 2 ? kModeExactMom : 0;
+  a.exact = exact ? kModeExactMom : 0;
   int pmax = 0;
   for (int p = 1; p <= 7; ++p)
     if (mesh->dm.elem_pstart[p + 1] > mesh->dm.elem_pstart[p]) pmax = p;

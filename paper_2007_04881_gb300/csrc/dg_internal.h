@@ -186,7 +186,7 @@ enum : int {
   kModeRhs = 4,    // load vector
   kModeAccum = 8,  // add to the diagonal block instead of overwriting it
   kModeSkipVol = 16,  // volume terms done by the moment kernel: faces only, load vector added
-  kModeExactMom = 32,  // 2D moment launch: volume moments by Green's theorem along the edges
+  kModeExactMom = 32,  // moment launch: volume moments exact (2D: Green's theorem along the edges; 3D: the divergence theorem on the boundary triangles)
 };
 
 // Optional per-launch timing: CUDA events recorded on the launch stream
@@ -238,7 +238,7 @@ constexpr int kMaxSplit = 4;  // parts of one degree group
 struct LaunchOpts {
   int occ_cap = 0;
   bool vol_moments = true;  // volume blocks through Legendre-product moments where supported
-  bool vol_exact = false;   // 2D: those moments exact, from the element's edges
+  bool vol_exact = false;   // those moments exact, from the element's boundary (edges / triangles)
   int tile[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // register-tile variant of each degree's row kernel
   cudaStream_t pst[9] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
   // each degree group as split[p] (1..kMaxSplit) contiguous parts of equal
@@ -274,7 +274,7 @@ struct PersistArgs {
   long long limit_ns;  // bound of one wait
   int mode;            // assembly mode of the pass (kModeVol | kModeFace | kModeRhs)
   int mom_mask;        // bit p: degree p takes the moment path
-  int exact;           // kModeExactMom for the moment tiles (2D volume path 2), else 0
+  int exact;           // kModeExactMom for the moment tiles (volume path 2), else 0
   int warp_bytes;      // shared memory per warp (set by the launcher)
 };
 // FP32 persistent passes: the launch (1, or -1 when the shared memory does

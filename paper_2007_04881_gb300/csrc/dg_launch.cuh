@@ -113,7 +113,7 @@ inline int launch_row_range(const DevMesh& m, int mode, T* vals, T* rhs, int sm_
       auto k = vol_moment_kernel<D, P, T>;
       const int ngroups = (count + MC::G - 1) / MC::G;
       const int grid = resident_grid(k, MC::total, sm_count, (ngroups + kWarps - 1) / kWarps, lo.occ_cap);
-      const int xm = D == 2 && lo.vol_exact ? kModeExactMom : 0;
+      const int xm = lo.vol_exact ? kModeExactMom : 0;
       k<<<grid, kWarps * 32, MC::total, st>>>(m, (mode & (kModeVol | kModeRhs | kModeAccum)) | xm, vals, rhs);
       if (tr && tr->on) tr->end(st);
       ++n;

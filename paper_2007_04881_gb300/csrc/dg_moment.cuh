@@ -123,8 +123,8 @@ __device__ __forceinline__ void mom_tile(const DevMesh& m, int mode, T* __restri
     for (int k = 0; k < NM; ++k) mu[k] = T(0);
 #pragma unroll
     for (int i = 0; i < N; ++i) racc[i] = T(0);
-    // exact moments (2D, kModeExactMom): the points carry only the load vector
-    const bool exact = D == 2 && active && (mode & kModeExactMom) && !lrn;
+    // exact moments (kModeExactMom): the points carry only the load vector
+    const bool exact = active && (mode & kModeExactMom) && !lrn;
     const int npl = exact && !do_rhs ? 0 : npts;
     for (int qv = lig; qv < npl; qv += LPE) {
       T xi[D], W;
@@ -263,6 +263,61 @@ __device__ __forceinline__ void mom_tile(const DevMesh& m, int mode, T* __restri
               for (int d = 0; c + d <= Q; ++d) {
                 const int s = c + d;
                 mu[s * (s + 1) / 2 + d] = fma(wc, py[d], mu[s * (s + 1) / 2 + d]);
+              }
+            }
+          }
+        }
+      }
+    }
+    // exact moments in 3D by the divergence theorem with the field
+    // (L_1 / 2) Q_c(xi) P_d(eta) P_e(zeta) e_1, whose divergence is
+    // P_c P_d P_e: mu_cde = sum over the element's boundary triangles (its
+    // half faces) of the integral of (L_1 / 2) n_1 Q_c P_d P_e dS, n the
+    // physical unit normal out of the element (n_1 = n'_1 L_1 / 2 from the
+    // record's scaled normal).  On a triangle the integrand has degree
+    // c + 1 + d + e <= 2p + 1, so the collapsed rule with p + 2 points per
+    // direction (exact to 2p + 2) integrates it exactly.
+    if constexpr (D == 3) {
+      if (exact && mat_vol) {
+        constexpr int NQ = P + 2, QF = NQ * NQ;
+        constexpr int FV = side_vals(3), RS = hf_rec_vals(3);
+        const T* HFR = pick<T>(m.hfr64, m.hfr32);
+        const T* fr0 = pick<T>(m.rt.face64, m.rt.face32) + (size_t)m.rt.face_off[NQ] * 3;
+        const int h0 = m.hf_ptr[e], npt = (m.hf_ptr[e + 1] - h0) * QF;
+        const T lx = T(0.25) * q.L[0] * q.L[0];
+        for (int idx = lig; idx < npt; idx += LPE) {
+          const int h = h0 + idx / QF, g = idx - (idx / QF) * QF;
+          const T* rec = HFR + (size_t)h * RS;
+          const T* fr = fr0 + 3 * g;
+          T xi[3], np[3];
+          hf_point<3, T>(rec, fr, xi, np);
+          const T w = fr[2] * rec[2 * FV] * np[0] * lx;
+          T px[Q + 2], py[Q + 1], pz[Q + 1];
+          px[0] = py[0] = pz[0] = T(1);
+          px[1] = xi[0];
+          py[1] = xi[1];
+          pz[1] = xi[2];
+#pragma unroll
+          for (int k = 1; k <= Q; ++k) {
+            const T a1 = T(2 * k + 1) / T(k + 1), a0 = T(k) / T(k + 1);
+            px[k + 1] = a1 * xi[0] * px[k] - a0 * px[k - 1];
+            if (k < Q) {
+              py[k + 1] = a1 * xi[1] * py[k] - a0 * py[k - 1];
+              pz[k + 1] = a1 * xi[2] * pz[k] - a0 * pz[k - 1];
+            }
+          }
+#pragma unroll
+          for (int c = 0; c <= Q; ++c) {
+            const T qc = c == 0 ? px[1] : (px[c + 1] - px[c - 1]) * (T(1) / T(2 * c + 1));
+            const T wc = w * qc;
+#pragma unroll
+            for (int d = 0; c + d <= Q; ++d) {
+              const T wcd = wc * py[d];
+#pragma unroll
+              for (int ee = 0; c + d + ee <= Q; ++ee) {
+                const int s = c + d + ee, t = d + ee;
+                const int k = s * (s + 1) * (s + 2) / 6 + t * (t + 1) / 2 + ee;
+                mu[k] = fma(wcd, pz[ee], mu[k]);
               }
             }
           }

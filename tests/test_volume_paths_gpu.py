@@ -1,11 +1,12 @@
 """The ways of forming the volume blocks, against the FP64 oracle: the
 per-point contraction in the row kernels (path 0), the Legendre-product
-moments over the quadrature points (path 1, the default) and, in 2D, the same
-moments exact by Green's theorem along the element's edges (path 2), in FP64
+moments over the quadrature points (path 1, the default) and the same moments
+exact from the element's boundary (path 2: in 2D by Green's theorem along the
+edges, in 3D by the divergence theorem on the boundary triangles), in FP64
 and FP32, with every degree, with learned rules, and through the separate
 volume / faces / load-vector calls.  The moment path adds the same quadrature
 terms in another order, and for the polynomial volume integrands of constant
-coefficients the sub-triangle rule is exact, so path 2 equals it up to
+coefficients the sub-simplex rule is exact, so path 2 equals it up to
 rounding: the tolerances are those of the other parity tests."""
 import numpy as np
 import pytest
@@ -119,3 +120,42 @@ def test_exact_moments_long_loop(ctx, p, prec):
         m, v, r = run(ctx, wl, prec, path)
         ed, eo, er = compare(dg.to_blocks(m, v, r), om, ob, wl)
         assert ed < TOL[prec] and er < TOL_RHS[prec], (path, ed, er)
+
+
+@pytest.mark.parametrize("prec", [dg.DG_PREC_FP64, dg.DG_PREC_FP32])
+def test_exact_moments_3d_match_quadrature_moments(ctx, prec):
+    """3D, degrees 2 and 3 (the moment path's 3D degrees), advection and
+    reaction, polyhedra of about 40 tetrahedra: the divergence-theorem moments
+    and the sub-tet quadrature moments give the same system up to rounding,
+    and both match the oracle"""
+    wl = configs.small3d(6, 24, 31, 2, 3, b=(0.7, -0.4, 0.3), c=1.5)
+    m, v1, r1 = run(ctx, wl, prec, 1)
+    _, v2, r2 = run(ctx, wl, prec, 2, m=m)
+    assert np.abs(v2 - v1).max() <= TOL[prec] * np.abs(v1).max()
+    assert np.abs(r2 - r1).max() <= TOL_RHS[prec] * np.abs(r1).max()  # the load vector keeps the rule's points
+    om, ob = oracle_blocks(wl)
+    ed, eo, er = compare(dg.to_blocks(m, v2, r2), om, ob, wl)
+    assert ed < TOL[prec] and eo < TOL[prec] and er < TOL_RHS[prec], (ed, eo, er)
+
+
+def test_exact_moments_3d_persistent(ctx):
+    """The persistent pass on volume path 2 in 3D (FP32) against the oracle."""
+    import torch
+
+    wl = configs.small3d(6, 24, 32, 1, 3, b=(0.7, -0.4, 0.3), c=1.5)
+    m = dg.Mesh(ctx, wl.mesh, wl.p, wl.a, dg_problem(wl))
+    ctx.dg_set_volume_path(2)
+    ctx.dg_set_persistent(True)
+    try:
+        v = torch.full((m.nvals,), float("nan"), dtype=torch.float32, device="cuda")
+        r = torch.full((m.ndofs,), float("nan"), dtype=torch.float32, device="cuda")
+        m.dg_assemble_step(dg.DG_PREC_FP32, v, r)
+        ctx.dg_sync()
+    finally:
+        ctx.dg_set_persistent(False)
+        ctx.dg_set_volume_path(1)
+    v, r = v.double().cpu().numpy(), r.double().cpu().numpy()
+    om, ob = oracle_blocks(wl)
+    ed, eo, er = compare(dg.to_blocks(m, v, r), om, ob, wl)
+    tol, tr = TOL[dg.DG_PREC_FP32], TOL_RHS[dg.DG_PREC_FP32]
+    assert ed < tol and eo < tol and er < tr, (ed, eo, er)
