@@ -112,6 +112,17 @@ def make_workload(name):
     raise SystemExit(f"unknown workload {name}")
 
 
+def emit(line: dict) -> None:
+    """Print the bench line; with --jsonl, also append it (with the time and
+    the command line) to that run log, one JSON object per line."""
+    print(json.dumps(line))
+    path = getattr(emit, "jsonl", None)
+    if path:
+        rec = dict(line, logged_at=time.strftime("%Y-%m-%dT%H:%M:%S"), argv=sys.argv[1:])
+        with open(path, "a") as f:
+            f.write(json.dumps(rec) + "\n")
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -255,7 +266,9 @@ def run_reference(args):
         batch_ne = wl.ne
         wl = max(wl.members, key=lambda w: w.ne)
     om = O.Mesh(wl.mesh)
-    pb = O.make_problem(wl.dim, **wl.problem)
+    # the variable-coefficient workload: the oracle with the Sec. 4.2 fields
+    coef = {"coef": 1} if args.workload == "adr3d_varcoef" else {}
+    pb = O.make_problem(wl.dim, **wl.problem, **coef)
     p = wl.p.astype(np.int32)
     cores = os.cpu_count() or 1
     # per step: a contiguous sample of elements and the same share of interfaces
@@ -299,7 +312,7 @@ def run_reference(args):
         "cpu_baseline": {"value": value, "unit": "elements/s", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line))
+    emit(line)
     return 0
 
 
@@ -319,7 +332,7 @@ def run_reference_slab(args, ws):
         "cpu_baseline": dict(runs[0], value=value),
         "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line))
+    emit(line)
     return 0
 
 
@@ -682,7 +695,7 @@ def run_ours(args):
     elif ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"], _ = cpu_baseline_sample(wl.members[0])
         line["cpu_baseline"]["sample"] = "batch member 0: " + line["cpu_baseline"]["sample"]
-    print(json.dumps(line))
+    emit(line)
     return 0
 
 
@@ -876,7 +889,7 @@ def run_varcoef(args):
         cb, (om, ob) = cpu_baseline_sample(wo, seconds_target=8.0)
         line["cpu_baseline"] = cb
         line["error_vs_oracle"] = oracle_error(mesh, vals.double().cpu().numpy(), rhs.double().cpu().numpy(), om, ob)
-    print(json.dumps(line))
+    emit(line)
     return 0
 
 
@@ -1000,7 +1013,7 @@ def run_slab(args):
     }
     if ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = slab_cpu_sample("PQ" if space else "P")
-    print(json.dumps(line))
+    emit(line)
     return 0
 
 
@@ -1248,7 +1261,7 @@ def run_learned(args):
         "gpu_launches": mesh.ctx.launches() * args.steps,
         "clocks": clocks,
     }
-    print(json.dumps(line))
+    emit(line)
     return 0
 
 
@@ -1264,11 +1277,13 @@ def main():
     ap.add_argument("--prec", default="fp32", choices=sorted(PRECS),
                     help="form of the timed pass: FP32 contractions, or split-BF16 / 3xTF32 tensor-core contractions")
     ap.add_argument("--epochs", type=int, default=40, help="training epochs of the learned-rule workload")
+    ap.add_argument("--jsonl", metavar="FILE", help="also append each bench line to this JSONL run log")
     ap.add_argument("--record-traffic", metavar="CSV", help="store the DRAM traffic of --traffic-group from an ncu "
                     "CSV log in profiles/traffic.json for --workload, and exit")
     ap.add_argument("--traffic-group", default="row_pass", choices=sorted(TRAFFIC_GROUPS))
     ap.add_argument("--traffic-launches", type=int, default=6, help="captured launches that make one pass")
     args = ap.parse_args()
+    emit.jsonl = args.jsonl
     if args.record_traffic:
         return record_traffic(args.record_traffic, args.workload, args.traffic_group, args.traffic_launches)
     if args.warmup < 3:

@@ -55,6 +55,7 @@ extern "C" {
 #define DG_ERR_OOM (-4)     /* device or host allocation failed */
 #define DG_ERR_ORDER (-5)   /* dg_assemble_faces called before dg_assemble_volume */
 #define DG_ERR_TIMEOUT (-6) /* a bounded device-side wait ran out */
+#define DG_ERR_BOUNDS (-7)  /* builds with DG_CHECK_BOUNDS: a kernel found an output range outside its array */
 
 /* precision flags (prec argument) */
 #define DG_PREC_FP64 0 /* everything in FP64; vals are double */
@@ -317,6 +318,11 @@ int dg_set_volume_path(dg_ctx *ctx, int path);
  * Every variant sums each block entry over the same points in the same
  * order, so the results are bitwise those of the default tiles. */
 int dg_set_tile_variants(dg_ctx *ctx, const int *variants);
+
+/* on != 0: NVTX ranges (host markers read by profilers) around the later
+ * calls of this context that upload, assemble, tune or record, and around
+ * their stages (host or device pattern, geometry).  Off by default. */
+int dg_set_nvtx(dg_ctx *ctx, int on);
 
 /* Parts of each degree group (split[p], 9 entries, 1..4; NULL: all 1) for
  * the calls without a tuned launch shape that run the degree groups

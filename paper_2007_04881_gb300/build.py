@@ -13,13 +13,18 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
-OUT_DIR = os.path.join(HERE, "_build")
+# DG_CHECK_BOUNDS=1 in the environment selects the checked build: every
+# kernel tests its output ranges before writing (an error word instead of a
+# fault, reported by dg_sync as DG_ERR_BOUNDS), in a library of its own
+CHECKED = os.environ.get("DG_CHECK_BOUNDS", "0") not in ("", "0")
+OUT_DIR = os.path.join(HERE, "_build_checked" if CHECKED else "_build")
 LIB = os.path.join(OUT_DIR, "libdg.so")
 ROOT = os.path.dirname(HERE)
 
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")]
+FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + os.path.join(ROOT, "include")] + (
+    ["-DDG_CHECK_BOUNDS"] if CHECKED else [])
 
 
 def _sources():

@@ -292,6 +292,25 @@ __device__ __forceinline__ const float* pick<float>(const double*, const float* 
 
 __host__ __device__ constexpr size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Builds with DG_CHECK_BOUNDS: a range [off, off + n) checked against
+// [0, cap) before the kernel writes it; outside, bit 1 of the status word is
+// set (dg_sync returns DG_ERR_BOUNDS) and the caller skips the write.
+// Without the flag: true, and no code.
+__device__ __forceinline__ bool dg_in_range(int* status, int64_t off, int64_t n, int64_t cap) {
+#ifdef DG_CHECK_BOUNDS
+  if (off < 0 || n < 0 || off + n > cap) {
+    if (status) atomicOr(status, 2);
+    return false;
+  }
+#else
+  (void)status;
+  (void)off;
+  (void)n;
+  (void)cap;
+#endif
+  return true;
+}
+
 // --------------------------------------------------------------------------
 // tile loads from shared memory (vectorised where the padded stride allows)
 // --------------------------------------------------------------------------
@@ -524,6 +543,7 @@ __device__ __forceinline__ void lane_offdiag(const DevMesh& m, const ElemPar<D, 
       }
     }
   }
+  if (!dg_in_range(m.status, off, (int64_t)N * NK, m.nvals)) return;
   T* out = vals + off;
   const T RR = q.R * Rk;
 #pragma unroll
@@ -732,7 +752,7 @@ __global__ void __launch_bounds__(kWarps * 32)
         }
       }
     }
-    if (mat_vol || mat_face) {
+    if ((mat_vol || mat_face) && dg_in_range(m.status, m.blk_off[m.diag_blk[e]], (int64_t)N * N, m.nvals)) {
       T* out = vals + m.blk_off[m.diag_blk[e]];
       const T RR = q.R * q.R;
 #pragma unroll
@@ -743,7 +763,7 @@ __global__ void __launch_bounds__(kWarps * 32)
           out[i * N + j] = accum ? out[i * N + j] + v : v;
         }
     }
-    if (do_rhs) {
+    if (do_rhs && dg_in_range(m.status, m.dof_off[e], N, m.ndofs)) {
 #pragma unroll
       for (int i = 0; i < N; ++i) rhs[m.dof_off[e] + i] = q.R * ctab[i] * racc[i];
     }
@@ -1156,7 +1176,7 @@ __device__ __forceinline__ void row_tile(const DevMesh& m, int mode, T* __restri
     if (wr) {
       const int e = PIv[g_me * PI + kPiElem];
       const T Re = PTv[g_me * PT + X + kPtR];
-      if (mat_vol || mat_face) {
+      if ((mat_vol || mat_face) && dg_in_range(m.status, m.blk_off[m.diag_blk[e]], (int64_t)N * N, m.nvals)) {
         T* out = vals + m.blk_off[m.diag_blk[e]];
         const T RR = Re * Re;
 #pragma unroll
@@ -1175,7 +1195,7 @@ __device__ __forceinline__ void row_tile(const DevMesh& m, int mode, T* __restri
           }
         }
       }
-      if (do_rhs && tc == 0) {
+      if (do_rhs && tc == 0 && dg_in_range(m.status, m.dof_off[e], N, m.ndofs)) {
         T* out = rhs + m.dof_off[e];
 #pragma unroll
         for (int a = 0; a < TM; ++a) {
@@ -1305,7 +1325,7 @@ __device__ __forceinline__ void row_tile(const DevMesh& m, int mode, T* __restri
           if (active) {
             const int* pi = PIv + g_me * PI;
             const int nk = pi[kPiSNk];
-            if (col0 < nk) {
+            if (col0 < nk && dg_in_range(m.status, m.blk_off[pi[kPiSBlk]], (int64_t)N * nk, m.nvals)) {
               T* out = vals + m.blk_off[pi[kPiSBlk]];
               const T RR = PTv[g_me * PT + X + kPtR] * PTv[g_me * PT + X + kPtRk];
 #pragma unroll

@@ -24,6 +24,8 @@
 #include "dg_slab.cuh"
 #include "dg_varcoef.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 using namespace dg;
 
 namespace {
@@ -193,10 +195,11 @@ struct dg_ctx {
   bool vol_exact = false;   // those moments exact (2D: Green's theorem along the edges; 3D: the divergence theorem on the boundary triangles)
   int tiles[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};  // row-kernel tile variants of untuned passes
   int splits[9] = {1, 1, 1, 1, 1, 1, 1, 1, 1};  // parts of each degree group in untuned concurrent passes
-  int* status_dev = nullptr;  // bit 0: a bounded device wait ran out (read and cleared by dg_sync)
+  int* status_dev = nullptr;  // bit 0: a bounded device wait ran out; bit 1: a DG_CHECK_BOUNDS check failed (read and cleared by dg_sync)
   long long wait_ns = 2000000000LL;  // bound of one device wait
   bool persist = false;  // untuned per-step passes and untuned graphs take the persistent pass
   bool pattern_device = false;  // dg_mesh_upload builds the block pattern on the device
+  bool nvtx = false;  // NVTX ranges around the calls and their stages (dg_set_nvtx)
   std::vector<LaunchRec> recs;
   SideStreams streams;  // the direct launches' forked streams
   ~dg_ctx() {
@@ -206,6 +209,20 @@ struct dg_ctx {
       cudaEventDestroy(r.ev1);
     }
   }
+};
+
+// An NVTX range over a call or a stage (host markers for a profiler's
+// timeline; no effect without a tool attached, none at all when off).
+struct NvtxRange {
+  bool on;
+  NvtxRange(const dg_ctx* ctx, const char* name) : on(ctx && ctx->nvtx) {
+    if (on) nvtxRangePushA(name);
+  }
+  ~NvtxRange() {
+    if (on) nvtxRangePop();
+  }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 // the context's volume path: 0 per-point, 1 quadrature moments, 2 exact 2D moments
@@ -1185,7 +1202,11 @@ static int upload_impl(dg_ctx* ctx, const dg_mesh_desc* d, const int8_t* owned, 
   *out = nullptr;
   const auto t_start = std::chrono::steady_clock::now();
   Plan P;
-  int prc = plan_mesh(d, P, owned);
+  int prc;
+  {
+    NvtxRange nv_plan(ctx, "pattern (host)");
+    prc = plan_mesh(d, P, owned);
+  }
   if (prc != DG_OK) return prc;
   const double plan_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   const int dim = d->dim, nv = d->nv, ne = d->ne;
@@ -1316,9 +1337,15 @@ static int upload_impl(dg_ctx* ctx, const dg_mesh_desc* d, const int8_t* owned, 
   dm.lq_ok = nullptr;
   dm.lq64 = nullptr;
   dm.lq32 = nullptr;
+  dm.status = ctx->status_dev;
+  dm.nvals = m->info.nvals;
+  dm.ndofs = m->info.ndofs;
 
   cudaSetDevice(ctx->device);
-  launch_geometry(dm, ctx->stream);
+  {
+    NvtxRange nv_geo(ctx, "geometry");
+    launch_geometry(dm, ctx->stream);
+  }
   cudaError_t ce = cudaGetLastError();
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
   if (ce != cudaSuccess) {
@@ -1381,7 +1408,10 @@ static int upload_impl_device(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out)
     char* q = nullptr;
     return B.alloc(&q, bytes) == cudaSuccess ? static_cast<void*>(q) : nullptr;
   };
-  rc = build_pattern_device(d, dm.eptr, dm.eidx, dm.p, dm.X, alloc, ctx->stream, &P, &msg);
+  {
+    NvtxRange nv_pat(ctx, "pattern (device)");
+    rc = build_pattern_device(d, dm.eptr, dm.eidx, dm.p, dm.X, alloc, ctx->stream, &P, &msg);
+  }
   if (rc != DG_OK) {
     delete m;
     return fail(rc, "dg_mesh_upload (device pattern): %s", msg.empty() ? "allocation failed" : msg.c_str());
@@ -1464,7 +1494,13 @@ static int upload_impl_device(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out)
   dm.lq_ok = nullptr;
   dm.lq64 = nullptr;
   dm.lq32 = nullptr;
-  launch_geometry(dm, ctx->stream);
+  dm.status = ctx->status_dev;
+  dm.nvals = m->info.nvals;
+  dm.ndofs = m->info.ndofs;
+  {
+    NvtxRange nv_geo(ctx, "geometry");
+    launch_geometry(dm, ctx->stream);
+  }
   cudaError_t ce = cudaGetLastError();
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
   if (ce != cudaSuccess) {
@@ -1479,6 +1515,7 @@ static int upload_impl_device(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out)
 extern "C" {
 
 int dg_mesh_upload(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
+  NvtxRange nv_(ctx, "dg_mesh_upload");
   if (ctx && ctx->pattern_device) return upload_impl_device(ctx, d, out);
   return upload_impl(ctx, d, nullptr, out);
 }
@@ -1557,6 +1594,7 @@ int dg_bsr_pattern(const dg_mesh* mesh, int* row_ptr, int* col, int64_t* blk_off
 }
 
 int dg_geometry(dg_ctx* ctx, dg_mesh* mesh) {
+  NvtxRange nv_(ctx, "dg_geometry");
   if (!ctx || !mesh) return fail(DG_ERR_ARG, "dg_geometry: null argument");
   trace_reset(ctx, mesh);
   ctx->last_launches = launch_geometry(mesh->dm, ctx->stream, &ctx->tracer);
@@ -1565,6 +1603,7 @@ int dg_geometry(dg_ctx* ctx, dg_mesh* mesh) {
 }
 
 int dg_mesh_update(dg_ctx* ctx, dg_mesh* mesh, const double* x, const double* y, const double* z, const double* a) {
+  NvtxRange nv_(ctx, "dg_mesh_update");
   if (!ctx || !mesh) return fail(DG_ERR_ARG, "dg_mesh_update: null argument");
   const int nv = mesh->dm.nv, ne = mesh->dm.ne;
   const double* src[3] = {x, y, z};
@@ -1648,12 +1687,14 @@ static int run_assembly(dg_ctx* ctx, const dg_mesh* mesh, int prec, int mode, vo
 }
 
 int dg_assemble_volume(dg_ctx* ctx, const dg_mesh* mesh, int prec, void* vals) {
+  NvtxRange nv_(ctx, "dg_assemble_volume");
   int rc = run_assembly(ctx, mesh, prec, kModeVol, vals, nullptr, false);
   if (rc == DG_OK) const_cast<dg_mesh*>(mesh)->vol_vals = vals;
   return rc;
 }
 
 int dg_assemble_faces(dg_ctx* ctx, const dg_mesh* mesh, int prec, void* vals) {
+  NvtxRange nv_(ctx, "dg_assemble_faces");
   if (!mesh || mesh->vol_vals != vals || !vals)
     return fail(DG_ERR_ORDER, "dg_assemble_faces: call dg_assemble_volume on the same vals first");
   int rc = run_assembly(ctx, mesh, prec, kModeFace | kModeAccum, vals, nullptr, true);
@@ -1662,10 +1703,12 @@ int dg_assemble_faces(dg_ctx* ctx, const dg_mesh* mesh, int prec, void* vals) {
 }
 
 int dg_assemble_rhs(dg_ctx* ctx, const dg_mesh* mesh, int prec, void* rhs) {
+  NvtxRange nv_(ctx, "dg_assemble_rhs");
   return run_assembly(ctx, mesh, prec, kModeRhs, nullptr, rhs, false);
 }
 
 int dg_assemble(dg_ctx* ctx, const dg_mesh* mesh, int prec, void* vals, void* rhs) {
+  NvtxRange nv_(ctx, "dg_assemble");
   const int mode = kModeVol | kModeFace | (rhs ? kModeRhs : 0);
   return run_assembly(ctx, mesh, prec, mode, vals, rhs, true);
 }
@@ -1703,6 +1746,7 @@ static int issue_persist_step(dg_ctx* ctx, dg_mesh* mesh, int prec, int mode, vo
 
 int dg_assemble_host(dg_ctx* ctx, dg_mesh* mesh, int prec, const double* x, const double* y, const double* z,
                      const double* a, void* vals_host, void* rhs_host) {
+  NvtxRange nv_(ctx, "dg_assemble_host");
   if (!ctx || !mesh || !vals_host) return fail(DG_ERR_ARG, "dg_assemble_host: null argument");
   const int gmask = pass_geometry(&prec);
   if (gmask < 0) return fail(DG_ERR_ARG, "unknown precision %d", prec);
@@ -1744,6 +1788,7 @@ int dg_assemble_host(dg_ctx* ctx, dg_mesh* mesh, int prec, const double* x, cons
 }
 
 int dg_assemble_step(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs) {
+  NvtxRange nv_(ctx, "dg_assemble_step");
   if (!ctx || !mesh) return fail(DG_ERR_ARG, "dg_assemble_step: null argument");
   const int gmask = pass_geometry(&prec);
   if (gmask < 0) return fail(DG_ERR_ARG, "unknown precision %d", prec);
@@ -1935,6 +1980,7 @@ static int issue_slab(dg_ctx* ctx, dg_mesh* mesh, int prec, int space, double t0
 
 int dg_assemble_slab(dg_ctx* ctx, dg_mesh* mesh, int prec, int space, double t0, double t1, const void* u_prev,
                      void* vals, void* rhs) {
+  NvtxRange nv_(ctx, "dg_assemble_slab");
   int rc = slab_check(ctx, mesh, prec, space, t0, t1, vals, "dg_assemble_slab");
   if (rc != DG_OK) return rc;
   return issue_slab(ctx, mesh, prec, space, t0, t1, u_prev, vals, rhs, ctx->stream, &ctx->streams);
@@ -1942,6 +1988,7 @@ int dg_assemble_slab(dg_ctx* ctx, dg_mesh* mesh, int prec, int space, double t0,
 
 int dg_slab_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, int space, double t0, double t1, const void* u_prev,
                          void* vals, void* rhs, dg_graph** out) {
+  NvtxRange nv_(ctx, "dg_slab_graph_create");
   if (!out) return fail(DG_ERR_ARG, "dg_slab_graph_create: null output");
   *out = nullptr;
   int rc = slab_check(ctx, mesh, prec, space, t0, t1, vals, "dg_slab_graph_create");
@@ -2024,6 +2071,7 @@ int dg_mesh_set_fields(dg_mesh* mesh, const dg_fields* f) {
 }
 
 int dg_assemble_varcoef_form(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs) {
+  NvtxRange nv_(ctx, "dg_assemble_varcoef_form");
   if (!ctx || !mesh || !vals) return fail(DG_ERR_ARG, "dg_assemble_varcoef: null argument");
   if (prec != DG_PREC_FP64 && prec != DG_PREC_FP32)
     return fail(DG_ERR_ARG, "dg_assemble_varcoef: precision %d (DG_PREC_FP64 or DG_PREC_FP32)", prec);
@@ -2052,6 +2100,7 @@ int dg_assemble_varcoef(dg_ctx* ctx, dg_mesh* mesh, void* vals, void* rhs) {
 }
 
 int dg_batch_upload(dg_ctx* ctx, const dg_mesh_desc* const* descs, int n, dg_mesh** out) {
+  NvtxRange nv_(ctx, "dg_batch_upload");
   if (!ctx || !descs || n <= 0 || !out) return fail(DG_ERR_ARG, "dg_batch_upload: bad argument");
   *out = nullptr;
   const dg_mesh_desc* d0 = descs[0];
@@ -2353,6 +2402,7 @@ int dg_part_check(const dg_mesh_desc* d, const int* part, int my_part, dg_bsr_in
 }
 
 int dg_mesh_upload_part(dg_ctx* ctx, const dg_mesh_desc* d, const int* part, int my_part, dg_mesh** out) {
+  NvtxRange nv_(ctx, "dg_mesh_upload_part");
   if (!ctx || !out) return fail(DG_ERR_ARG, "dg_mesh_upload_part: null argument");
   *out = nullptr;
   PartMesh L;
@@ -2563,6 +2613,7 @@ static int issue_pass(dg_ctx* ctx, dg_mesh* mesh, int prec, int gmask, void* val
 }
 
 int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs, int autotune, dg_graph** out) {
+  NvtxRange nv_(ctx, "dg_graph_create");
   if (!ctx || !mesh || !vals || !out) return fail(DG_ERR_ARG, "dg_graph_create: null argument");
   const int gmask = pass_geometry(&prec);
   if (gmask < 0) return fail(DG_ERR_ARG, "unknown precision %d", prec);
@@ -2753,6 +2804,7 @@ int dg_graph_create(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, void* rhs,
 // graph, launches it and frees it.
 int dg_assemble_batch(dg_ctx* ctx, dg_mesh* const* meshes, int nmesh, int prec, void* const* vals,
                       void* const* rhs, int use_graph) {
+  NvtxRange nv_(ctx, "dg_assemble_batch");
   if (!ctx || !meshes || !vals || nmesh <= 0) return fail(DG_ERR_ARG, "dg_assemble_batch: bad argument");
   int base = prec;
   const int gmask = pass_geometry(&base);
@@ -2813,6 +2865,7 @@ int dg_assemble_batch(dg_ctx* ctx, dg_mesh* const* meshes, int nmesh, int prec, 
 }
 
 int dg_graph_launch(dg_ctx* ctx, dg_graph* g) {
+  NvtxRange nv_(ctx, "dg_graph_launch");
   if (!ctx || !g) return fail(DG_ERR_ARG, "dg_graph_launch: null argument");
   DG_CUDA_TRY(cudaGraphLaunch(g->exec, ctx->stream));
   ctx->last_launches = g->launches;
@@ -2854,6 +2907,7 @@ int dg_graph_free(dg_graph* g) {
 // ---------------------------------------------------------------------------
 
 int dg_quad_prepare(dg_ctx* ctx, dg_mesh* mesh) {
+  NvtxRange nv_(ctx, "dg_quad_prepare");
   if (!ctx || !mesh) return fail(DG_ERR_ARG, "dg_quad_prepare: null argument");
   if (mesh->dm.dim != 2) return fail(DG_ERR_ARG, "dg_quad_prepare: learned rules are 2D only");
   const int ne = mesh->dm.ne;
@@ -2911,6 +2965,7 @@ static int rebuild_worklist(dg_ctx* ctx, dg_mesh* mesh, const std::vector<int>& 
 }
 
 int dg_quad_fit(dg_ctx* ctx, dg_mesh* mesh, const float* init, int iters, int install, dg_quad_stats* stats) {
+  NvtxRange nv_(ctx, "dg_quad_fit");
   if (!ctx || !mesh || iters < 0) return fail(DG_ERR_ARG, "dg_quad_fit: bad argument");
   if (!mesh->lq_mom) return fail(DG_ERR_ARG, "dg_quad_fit: call dg_quad_prepare first");
   const int ne = mesh->dm.ne;
@@ -2959,6 +3014,7 @@ int dg_quad_fit(dg_ctx* ctx, dg_mesh* mesh, const float* init, int iters, int in
 }
 
 int dg_quad_learn(dg_ctx* ctx, dg_mesh* mesh, dg_mlp* net, int iters, dg_quad_stats* stats) {
+  NvtxRange nv_(ctx, "dg_quad_learn");
   if (!ctx || !mesh || iters < 0) return fail(DG_ERR_ARG, "dg_quad_learn: bad argument");
   int rc = dg_quad_prepare(ctx, mesh);
   if (rc != DG_OK) return rc;
@@ -3079,6 +3135,12 @@ int dg_set_tile_variants(dg_ctx* ctx, const int* variants) {
   return DG_OK;
 }
 
+int dg_set_nvtx(dg_ctx* ctx, int on) {
+  if (!ctx) return fail(DG_ERR_ARG, "dg_set_nvtx: null context");
+  ctx->nvtx = on != 0;
+  return DG_OK;
+}
+
 int dg_set_group_split(dg_ctx* ctx, const int* split) {
   if (!ctx) return fail(DG_ERR_ARG, "dg_set_group_split: null context");
   for (int p = 0; p < 9; ++p) {
@@ -3105,6 +3167,8 @@ int dg_sync(dg_ctx* ctx) {
   DG_CUDA_TRY(cudaMemcpy(&st, ctx->status_dev, sizeof(int), cudaMemcpyDeviceToHost));
   if (st) {
     DG_CUDA_TRY(cudaMemset(ctx->status_dev, 0, sizeof(int)));
+    if (st & 2)
+      return fail(DG_ERR_BOUNDS, "a kernel found an output range outside its array and skipped it (status 0x%x)", st);
     return fail(DG_ERR_TIMEOUT, "a bounded device wait ran out (status 0x%x); the pass's results are incomplete", st);
   }
   return DG_OK;

@@ -177,6 +177,10 @@ struct DevMesh {
   const int* lq_ok;
   const double* lq64;  // [ne][84]
   const float* lq32;
+  // the context's status word (bit 0 a bounded wait ran out, bit 1 an index
+  // range failed a DG_CHECK_BOUNDS check) and the output sizes it checks
+  int* status;
+  int64_t nvals, ndofs;
 };
 
 // mode bits of the element kernel

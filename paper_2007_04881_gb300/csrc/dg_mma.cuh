@@ -588,6 +588,9 @@ __global__ void __launch_bounds__(kWarps * 32, MmaCfg<D, P, K>::MINB)
     for (int g = 0; g < G; ++g) {
       if (g >= gcount) continue;
       const int e = PIv[g * PI + kPiElem];
+      if (((mat_vol || mat_face) && !dg_in_range(m.status, m.blk_off[m.diag_blk[e]], (int64_t)N * N, m.nvals)) ||
+          (do_rhs && !dg_in_range(m.status, m.dof_off[e], N, m.ndofs)))
+        continue;
       const float Re = PTv[g * PT + X + kPtR];
       const float RR = Re * Re;
       float* out = vals + ((mat_vol || mat_face) ? m.blk_off[m.diag_blk[e]] : 0);
@@ -732,6 +735,7 @@ __global__ void __launch_bounds__(kWarps * 32, MmaCfg<D, P, K>::MINB)
             const int* pi = PIv + g * PI;
             const int nk = pi[kPiSNk];
             if (col0 >= nk) continue;
+            if (!dg_in_range(m.status, m.blk_off[pi[kPiSBlk]], (int64_t)N * nk, m.nvals)) continue;
             float* out = vals + m.blk_off[pi[kPiSBlk]];
             const float RR = PTv[g * PT + X + kPtR] * PTv[g * PT + X + kPtRk];
 #pragma unroll

@@ -338,7 +338,7 @@ __device__ __forceinline__ void mom_tile(const DevMesh& m, int mode, T* __restri
     }
 
     // ---- load vector (volume term): overwritten
-    if (active && do_rhs) {
+    if (active && do_rhs && dg_in_range(m.status, m.dof_off[e], N, m.ndofs)) {
       T* out = rhs + m.dof_off[e];
 #pragma unroll
       for (int i = 0; i < N; ++i)
@@ -388,7 +388,7 @@ __device__ __forceinline__ void mom_tile(const DevMesh& m, int mode, T* __restri
         }
       }
       __syncwarp();
-      if (active) {
+      if (active && dg_in_range(m.status, m.blk_off[m.diag_blk[e]], (int64_t)N * N, m.nvals)) {
         T* out = vals + m.blk_off[m.diag_blk[e]];
         const T RR = q.R * q.R;
         for (int ent = lig; ent < N * N; ent += LPE) {

@@ -258,7 +258,8 @@ __global__ void __launch_bounds__(kVcWarps * 32)
         __syncwarp();
       }
     }
-    if (tl) {
+    if (tl && dg_in_range(m.status, m.blk_off[m.diag_blk[e]], (int64_t)N * N, m.nvals) &&
+        (!do_rhs || dg_in_range(m.status, m.dof_off[e], N, m.ndofs))) {
       T* out = vals + m.blk_off[m.diag_blk[e]];
       const T RR = q.R * q.R;
 #pragma unroll
@@ -318,7 +319,7 @@ __global__ void __launch_bounds__(kVcWarps * 32)
           __syncwarp();
         }
       }
-      if (tl) {
+      if (tl && dg_in_range(m.status, m.blk_off[bk], (int64_t)N * nk, m.nvals)) {
         T* out = vals + m.blk_off[bk];
         const T Rk = EG[(size_t)(3 * D) * m.ne + br.x];
         const T RR = q.R * Rk;

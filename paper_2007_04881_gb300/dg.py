@@ -15,7 +15,9 @@ from typing import Optional, Sequence
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libdg.so")
+# DG_CHECK_BOUNDS=1: the checked build (paper_2007_04881_gb300/build.py)
+LIB_PATH = os.path.join(_HERE, "_build_checked" if os.environ.get("DG_CHECK_BOUNDS", "0") not in ("", "0")
+                        else "_build", "libdg.so")
 
 DG_OK = 0
 DG_ERR = {
@@ -25,8 +27,10 @@ DG_ERR = {
     -4: "DG_ERR_OOM",
     -5: "DG_ERR_ORDER",
     -6: "DG_ERR_TIMEOUT",
+    -7: "DG_ERR_BOUNDS",
 }
 DG_ERR_ARG, DG_ERR_MESH, DG_ERR_CUDA, DG_ERR_OOM, DG_ERR_ORDER, DG_ERR_TIMEOUT = -1, -2, -3, -4, -5, -6
+DG_ERR_BOUNDS = -7
 DG_PREC_FP64 = 0
 DG_PREC_FP32 = 1
 DG_PREC_BF16X3 = 2
@@ -138,6 +142,7 @@ def load() -> C.CDLL:
     lib.dg_wait_probe.argtypes = [V, V, C.c_double]
     lib.dg_set_tile_variants.argtypes = [V, V]
     lib.dg_set_group_split.argtypes = [V, V]
+    lib.dg_set_nvtx.argtypes = [V, C.c_int]
     lib.dg_graph_splits.argtypes = [V, V]
     lib.dg_volume_noalloc.argtypes = [V, C.c_int, C.c_int, C.c_int, C.c_int, V, V, C.c_int, C.c_int, V, V, V,
                                       C.c_double, C.c_double, C.c_double, V, V]
@@ -192,7 +197,7 @@ EXPORTS = (
     "dg_partition", "dg_mesh_upload_part", "dg_part_map", "dg_part_check", "dg_set_volume_path",
     "dg_slab_offsets", "dg_slab_layout", "dg_assemble_slab", "dg_slab_trace", "dg_assemble_varcoef", "dg_assemble_varcoef_form", "dg_mesh_set_fields",
     "dg_mlp_save", "dg_mlp_load", "dg_quad_learn", "dg_assemble_batch", "dg_graph_tiles",
-    "dg_set_tile_variants", "dg_set_group_split", "dg_graph_splits", "dg_set_wait_limit", "dg_wait_probe",
+    "dg_set_tile_variants", "dg_set_group_split", "dg_graph_splits", "dg_set_nvtx", "dg_set_wait_limit", "dg_wait_probe",
     "dg_set_persistent", "dg_set_pattern_device", "dg_mesh_timings", "dg_mesh_array",
     "dg_slab_graph_create",
 )
@@ -264,6 +269,10 @@ class Context:
         """Row-kernel tile variant per degree (9 ints, or None for the defaults)."""
         v = None if variants is None else np.ascontiguousarray(variants, dtype=np.int32)
         _check(load().dg_set_tile_variants(self._h, _vp(v)))
+
+    def dg_set_nvtx(self, on: bool = True):
+        """NVTX ranges around this context's calls and their stages."""
+        _check(load().dg_set_nvtx(self._h, int(on)))
 
     def dg_set_group_split(self, split=None):
         """Parts (1..4) per degree group of untuned concurrent passes (9 ints, or None for all 1)."""
