@@ -1294,6 +1294,8 @@ __device__ __forceinline__ void row_tile(const DevMesh& m, int mode, T* __restri
                   };
                   nbr_basis<D, T>(pi[kPiSPk], xk, sink);
                 } else {
+                  // both rows (an unstaged U slot may hold a NaN pattern)
+                  zero_groups<T, TMP>(Ur, 2 * ROW);
                   for (int j = 0; j < VS; ++j) {
                     Vr[j] = T(0);
                     Vr[VS + j] = T(0);
