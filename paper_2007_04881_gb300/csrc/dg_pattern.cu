@@ -572,54 +572,71 @@ __global__ void account_elem_kernel(int ne, int dim, bool adv, bool advb, const 
                                     const int* __restrict__ f_e1, const int* __restrict__ nsub_e,
                                     const double* __restrict__ pt_ops, const double* __restrict__ map_ops,
                                     double* __restrict__ acc /* [3][9] flops, [3][9] words, [9] mom */) {
+  // per-CTA sums in shared memory, then one global add per bin: the values
+  // are integers or halves, exact in double, so the order of the adds does
+  // not change the result
+  __shared__ double sacc[63];
+  for (int t = threadIdx.x; t < 63; t += blockDim.x) sacc[t] = 0.0;
+  __syncthreads();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= ne) return;
-  const int SV = sub_vals(dim), FV = side_vals(dim);
-  const int pe = p[e];
-  const double n = nbasis(dim, pe);
-  const double basis = n * dim * dim + 5.0 * dim * pe;
-  const double nv = nvq[e];
-  const double vol_direct = nv * (dim * n * (n + 1) / 2 + (adv ? n * n + n * (dim + 1) : 0.0) + basis + n);
-  double fma = vol_direct;
-  const double vol_words = n * n + n + (double)nsub_e[e] * SV + 2 * dim + 2;
-  double w = vol_words;
-  for (int k = hf_ptr[e]; k < hf_ptr[e + 1]; ++k) {
-    const int f = hf_face[k];
-    const double qf = dim == 2 ? f_nq[f] : (double)f_nq[f] * f_nq[f];
-    const bool bnd = f_e1[f] < 0;
-    fma += qf * (3 * n * n + (advb ? (bnd ? n * n : n * n / 2) : 0.0) + basis + (bnd ? 2 * n : 0.0));
-    w += FV + 3;
+  if (e < ne) {
+    const int SV = sub_vals(dim), FV = side_vals(dim);
+    const int pe = p[e];
+    const double n = nbasis(dim, pe);
+    const double basis = n * dim * dim + 5.0 * dim * pe;
+    const double nv = nvq[e];
+    const double vol_direct = nv * (dim * n * (n + 1) / 2 + (adv ? n * n + n * (dim + 1) : 0.0) + basis + n);
+    double fma = vol_direct;
+    const double vol_words = n * n + n + (double)nsub_e[e] * SV + 2 * dim + 2;
+    double w = vol_words;
+    for (int k = hf_ptr[e]; k < hf_ptr[e + 1]; ++k) {
+      const int f = hf_face[k];
+      const double qf = dim == 2 ? f_nq[f] : (double)f_nq[f] * f_nq[f];
+      const bool bnd = f_e1[f] < 0;
+      fma += qf * (3 * n * n + (advb ? (bnd ? n * n : n * n / 2) : 0.0) + basis + (bnd ? 2 * n : 0.0));
+      w += FV + 3;
+    }
+    atomicAdd(&sacc[0 * 9 + pe], 2.0 * fma);
+    atomicAdd(&sacc[27 + 0 * 9 + pe], w);
+    // the moment path's launches: volume to kind 2, the rest to kind 1
+    atomicAdd(&sacc[1 * 9 + pe], 2.0 * (fma - vol_direct));
+    atomicAdd(&sacc[27 + 1 * 9 + pe], w - vol_words);
+    atomicAdd(&sacc[2 * 9 + pe], 2.0 * vol_direct);
+    atomicAdd(&sacc[27 + 2 * 9 + pe], vol_words);
+    atomicAdd(&sacc[54 + pe], 2.0 * (nv * pt_ops[pe] + map_ops[pe]));
   }
-  atomicAdd(&acc[0 * 9 + pe], 2.0 * fma);
-  atomicAdd(&acc[27 + 0 * 9 + pe], w);
-  // the moment path's launches: volume to kind 2, the rest to kind 1
-  atomicAdd(&acc[1 * 9 + pe], 2.0 * (fma - vol_direct));
-  atomicAdd(&acc[27 + 1 * 9 + pe], w - vol_words);
-  atomicAdd(&acc[2 * 9 + pe], 2.0 * vol_direct);
-  atomicAdd(&acc[27 + 2 * 9 + pe], vol_words);
-  atomicAdd(&acc[54 + pe], 2.0 * (nv * pt_ops[pe] + map_ops[pe]));
+  __syncthreads();
+  for (int t = threadIdx.x; t < 63; t += blockDim.x)
+    if (sacc[t] != 0.0) atomicAdd(&acc[t], sacc[t]);
 }
 
 __global__ void account_iface_kernel(int ni, int dim, bool advb, const int* __restrict__ if_e0,
                                      const int* __restrict__ if_e1, const int* __restrict__ if_fptr,
                                      const int* __restrict__ f_nq, const int* __restrict__ p, double* __restrict__ acc) {
+  __shared__ double sacc[63];  // per-CTA sums, as in account_elem_kernel
+  for (int t = threadIdx.x; t < 63; t += blockDim.x) sacc[t] = 0.0;
+  __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= ni) return;
-  const int FV = side_vals(dim);
-  for (int side = 0; side < 2; ++side) {
-    const int e = side == 0 ? if_e0[i] : if_e1[i], k = side == 0 ? if_e1[i] : if_e0[i];
-    const double ne_ = nbasis(dim, p[e]), nk = nbasis(dim, p[k]);
-    double fma = 0.0, w = ne_ * nk;
-    for (int f = if_fptr[i]; f < if_fptr[i + 1]; ++f) {
-      const double qf = dim == 2 ? f_nq[f] : (double)f_nq[f] * f_nq[f];
-      fma += qf * (3 * ne_ * nk + (advb ? ne_ * nk / 2 : 0.0));
-      w += 2 * FV + 3;
+  if (i < ni) {
+    const int FV = side_vals(dim);
+    for (int side = 0; side < 2; ++side) {
+      const int e = side == 0 ? if_e0[i] : if_e1[i], k = side == 0 ? if_e1[i] : if_e0[i];
+      const double ne_ = nbasis(dim, p[e]), nk = nbasis(dim, p[k]);
+      double fma = 0.0, w = ne_ * nk;
+      for (int f = if_fptr[i]; f < if_fptr[i + 1]; ++f) {
+        const double qf = dim == 2 ? f_nq[f] : (double)f_nq[f] * f_nq[f];
+        fma += qf * (3 * ne_ * nk + (advb ? ne_ * nk / 2 : 0.0));
+        w += 2 * FV + 3;
+      }
+      atomicAdd(&sacc[0 * 9 + p[e]], 2.0 * fma);
+      atomicAdd(&sacc[27 + 0 * 9 + p[e]], w);
+      atomicAdd(&sacc[1 * 9 + p[e]], 2.0 * fma);
+      atomicAdd(&sacc[27 + 1 * 9 + p[e]], w);
     }
-    atomicAdd(&acc[0 * 9 + p[e]], 2.0 * fma);
-    atomicAdd(&acc[27 + 0 * 9 + p[e]], w);
-    atomicAdd(&acc[1 * 9 + p[e]], 2.0 * fma);
-    atomicAdd(&acc[27 + 1 * 9 + p[e]], w);
   }
+  __syncthreads();
+  for (int t = threadIdx.x; t < 63; t += blockDim.x)
+    if (sacc[t] != 0.0) atomicAdd(&acc[t], sacc[t]);
 }
 
 __global__ void nsub_kernel(const int* __restrict__ eptr, int ne, int* __restrict__ out) {
