@@ -68,6 +68,8 @@ WORKLOADS = {
                       "u=sin(pi x)sin(pi y)sin(pi z)) on 50^3 cubes x 6 Kuhn tets (750,000 tets) grown into polyhedra "
                       "of about 4 tets (seeded greedy region growing across faces), p=3, FP32: the row pass without b "
                       "and c, then the variable-coefficient kernels"),
+    "adr3d_varcoef_12k": ("adr3d_varcoef_12k: the adr3d_varcoef recipe on 20^3 cubes x 6 Kuhn tets (48,000 tets), "
+                          "the small case of the variable-coefficient kernel profiles"),
 }
 
 
@@ -109,6 +111,8 @@ def make_workload(name):
         return configs.learned2d()
     if name == "adr3d_varcoef":
         return configs.adr3d_varcoef()
+    if name == "adr3d_varcoef_12k":
+        return configs.adr3d_varcoef(n=20)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -267,7 +271,7 @@ def run_reference(args):
         wl = max(wl.members, key=lambda w: w.ne)
     om = O.Mesh(wl.mesh)
     # the variable-coefficient workload: the oracle with the Sec. 4.2 fields
-    coef = {"coef": 1} if args.workload == "adr3d_varcoef" else {}
+    coef = {"coef": 1} if args.workload.startswith("adr3d_varcoef") else {}
     pb = O.make_problem(wl.dim, **wl.problem, **coef)
     p = wl.p.astype(np.int32)
     cores = os.cpu_count() or 1
@@ -1294,7 +1298,7 @@ def main():
         return run_learned(args)
     if args.workload.startswith("slab2d"):
         return run_slab(args)
-    if args.workload == "adr3d_varcoef":
+    if args.workload.startswith("adr3d_varcoef"):
         return run_varcoef(args)
     return run_ours(args)
 
