@@ -892,6 +892,9 @@ __device__ __forceinline__ void row_tile(const DevMesh& m, int mode, T* __restri
   const bool accum = mode & kModeAccum;
   // volume terms already written by the moment kernel: faces only, load vector added
   const bool skip_vol = mode & kModeSkipVol;
+  // diagonal block and load vector complete (the moment launch took the own
+  // faces too): the off-diagonal blocks only
+  const bool off_only = mode & kModeOffDiag;
   // with b = 0 and c = 0 the Phi row of a volume point carries no matrix term
   const bool no_adv = m.pb.b[0] == 0.0 && m.pb.b[1] == 0.0 && m.pb.b[2] == 0.0 && m.pb.c == 0.0;
   const int base = m.elem_pstart[P], count = m.elem_pstart[P + 1] - base;
@@ -1058,7 +1061,7 @@ __device__ __forceinline__ void row_tile(const DevMesh& m, int mode, T* __restri
     }
 
     // ---- own-face points (diagonal-block face terms, boundary load terms)
-    if (mat_face || do_rhs) {
+    if ((mat_face || do_rhs) && !off_only) {
       for (int ch = 0; ch < nfch; ++ch) {
         for (int idx = lane; idx < G * C; idx += 32) {
           const int g = idx / C, c = idx - g * C, qv = ch * C + c;
@@ -1168,8 +1171,8 @@ __device__ __forceinline__ void row_tile(const DevMesh& m, int mode, T* __restri
 
     // ---- write the diagonal block and the load vector (in the persistent
     // pass, once the element's moment item has written them)
-    bool wr = active;
-    if (wc && active && skip_vol && !wait_flag(wc->vdone + PIv[g_me * PI + kPiElem], wc->limit_ns)) {
+    bool wr = active && !off_only;
+    if (wc && wr && skip_vol && !wait_flag(wc->vdone + PIv[g_me * PI + kPiElem], wc->limit_ns)) {
       atomicOr(wc->status, 1);
       wr = false;
     }

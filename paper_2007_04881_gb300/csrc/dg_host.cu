@@ -269,7 +269,7 @@ void Tracer::begin(const char* name, int kind, int p, size_t tsize, cudaStream_t
   LaunchRec& r = recs[n];
   snprintf(r.name, sizeof r.name, "%s", name);
   r.flops = ((kind < kKinds && flops) ? flops[kind * 9 + p] : 0.0) * scale;
-  r.xflops = (kind == 2 && xflops) ? xflops[p] * scale : r.flops;
+  r.xflops = ((kind == 2 || kind == 3) && xflops) ? xflops[(kind - 2) * 9 + p] * scale : r.flops;
   r.bytes = ((kind < kKinds && words) ? words[kind * 9 + p] * (double)tsize : 0.0) * scale;
   record(r.ev0, st);
 }
@@ -287,6 +287,49 @@ void Tracer::end(cudaStream_t st) {
   record(recs[n].ev1, st);
   ++n;
 }
+// FMA-equivalent operations the moment launch executes, by degree pp
+// (q = 2 pp, nmom moments c + d (+ e) <= q, nn basis functions):
+//   pt   per volume point: 2 d (q - 1) for the Legendre values to degree q,
+//        q + 1 weighted values, one update per moment (in 3D also the
+//        (q+1)(q+2)/2 partial products), nn d for the load vector;
+//   map  per element: 3 per moment combination of every block entry (in 3D
+//        also 3 per (c, d) pair), 3 d per exponent pair and degree for the
+//        coefficient tables;
+//   fpt  per own-face point: 3 d (q - 1) for the Legendre values and
+//        derivatives, d + 2 weights, 2 per degree c (in 3D 3, and 4 per
+//        (c, d) pair), 2 per moment;
+//   bnd  per boundary-face point: 3 (pp + 1) + 3 nn for the load terms;
+//   mapf per element: the face moments' share of the combination (2D: one
+//        more FMA per stage-one term; 3D: 2 per moment combination).
+void moment_op_tables(int dim, MomentOps& o) {
+  o = MomentOps{};
+  for (int pp = 1; pp <= 8; ++pp) {
+    const int q = 2 * pp, nn = nbasis(dim, pp);
+    const double nmom = dim == 2 ? (q + 1) * (q + 2) / 2.0 : (q + 1) * (q + 2) * (q + 3) / 6.0;
+    const double npair = dim == 3 ? (q + 1) * (q + 2) / 2.0 : 0.0;
+    o.pt[pp] = 2.0 * dim * (q - 1) + (q + 1) + nmom + npair + nn * dim;
+    o.fpt[pp] = 3.0 * dim * (q - 1) + (dim + 2) + (dim == 2 ? 2.0 : 3.0) * (q + 1) + 4.0 * npair + 2.0 * nmom;
+    o.bnd[pp] = 3.0 * (pp + 1) + 3.0 * nn;
+    std::vector<std::array<int, 3>> al;
+    for (int k = 0; k <= pp; ++k)
+      for (int l = 0; l <= (dim == 3 ? k : 0); ++l)
+        for (int j = 0; j <= k - l; ++j) al.push_back({k - j - l, j, l});
+    double ops = 3.0 * dim * (pp + 1) * (pp + 1) * (q + 1), opf = 0.0;
+    for (const auto& a : al)
+      for (const auto& b : al) {
+        const double cx = a[0] + b[0] + 1, cy = a[1] + b[1] + 1, cz = dim == 3 ? a[2] + b[2] + 1 : 1;
+        ops += dim == 2 ? 3.0 * cx * cy : 3.0 * cx * cy * cz + 3.0 * cx * cy;
+        if (dim == 3) opf += 2.0 * cx * cy * cz;
+      }
+    if (dim == 2)
+      for (int c = 0; c <= q; ++c)
+        for (int b = 0; b <= pp; ++b)
+          for (int bp = 0; bp <= pp; ++bp) opf += std::min(b + bp, q - c) + 1;
+    o.map[pp] = ops;
+    o.mapf[pp] = opf;
+  }
+}
+
 // Inside a stream capture the record becomes an external event node, so the
 // event is stamped on every replay of the graph and stays timeable.
 void Tracer::record(cudaEvent_t ev, cudaStream_t st) {
@@ -326,7 +369,7 @@ struct dg_mesh {
   double* X[3] = {nullptr, nullptr, nullptr};
   double* a = nullptr;
   double flops[kKinds][9] = {{0}}, words[kKinds][9] = {{0}};
-  double mom_exec[9] = {0}, mom_pt[9] = {0};
+  double mom_exec[2][9] = {{0}}, mom_pt[9] = {0};
   std::vector<int> batch_elem_off;  // element offset of each batch member (empty: one mesh)
   // partition meshes: local -> global element and vertex ids, owned flags
   std::vector<int> part_elem, part_vert;
@@ -379,7 +422,7 @@ static void trace_reset(dg_ctx* ctx, const dg_mesh* mesh) {
   ctx->tracer.n = 0;
   ctx->tracer.flops = &mesh->flops[0][0];
   ctx->tracer.words = &mesh->words[0][0];
-  ctx->tracer.xflops = mesh->mom_exec;
+  ctx->tracer.xflops = &mesh->mom_exec[0][0];
 }
 
 namespace {
@@ -553,7 +596,7 @@ struct Plan {
   // algorithmic flops / words per launch group [kind][p] (kind 0: row
   // kernel of degree p, whole block rows and load vector)
   double flops[kKinds][9] = {{0}}, words[kKinds][9] = {{0}};
-  double mom_exec[9] = {0};  // moment form: executed flops of the volume launch, by degree
+  double mom_exec[2][9] = {{0}};  // moment form: executed flops of the volume launch (without, with the own faces), by degree
   double mom_pt[9] = {0};    // moment form: executed flops per volume point, by degree
 };
 
@@ -1015,6 +1058,8 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P, const int8_t* owned = nullp
       }
       P.flops[0][pe] += 2.0 * fma;
       P.words[0][pe] += w;
+      P.flops[3][pe] += 2.0 * fma;
+      P.words[3][pe] += w;
     }
     for (int i = 0; i < ni; ++i) {
       for (int side = 0; side < 2; ++side) {
@@ -1029,36 +1074,20 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P, const int8_t* owned = nullp
         }
         P.flops[0][d->p[e]] += 2.0 * fma;
         P.words[0][d->p[e]] += w;
+        P.flops[4][d->p[e]] += 2.0 * fma;
+        P.words[4][d->p[e]] += w;
       }
     }
-    // The launches of the moment path: the volume launch (kind 2) is credited
-    // with the volume terms' algorithmic work above (the quadrature sums it
-    // evaluates), the row kernel's faces-only launch beside it (kind 1) with
-    // the rest.  What the moment form executes instead, FMA-equivalent
-    // operations, is mom_exec: per volume point 2 d (2p - 1) for the Legendre
-    // values to degree 2p, 2p + 1 weighted values, one update per moment
-    // (c + d (+ e) <= 2p; in 3D also the (2p+1)(2p+2)/2 partial products) and
-    // n d for the load vector; per element 3 per moment combination of every
-    // block entry (in 3D also 3 per (c, d) pair) and 3 d per exponent pair
-    // and degree for the coefficient tables.  It is reported as the
-    // "row_pass_executed" record beside "row_pass".
-    double map_ops[9] = {0}, pt_ops[9] = {0};
-    for (int pp = 1; pp <= 8; ++pp) {
-      const int q = 2 * pp, nn = nbasis(dim, pp);
-      const double nmom = dim == 2 ? (q + 1) * (q + 2) / 2.0 : (q + 1) * (q + 2) * (q + 3) / 6.0;
-      pt_ops[pp] = 2.0 * dim * (q - 1) + (q + 1) + nmom + (dim == 3 ? (q + 1) * (q + 2) / 2.0 : 0.0) + nn * dim;
-      std::vector<std::array<int, 3>> al;
-      for (int k = 0; k <= pp; ++k)
-        for (int l = 0; l <= (dim == 3 ? k : 0); ++l)
-          for (int j = 0; j <= k - l; ++j) al.push_back({k - j - l, j, l});
-      double ops = 3.0 * dim * (pp + 1) * (pp + 1) * (q + 1);
-      for (const auto& a : al)
-        for (const auto& b : al) {
-          const double cx = a[0] + b[0] + 1, cy = a[1] + b[1] + 1, cz = dim == 3 ? a[2] + b[2] + 1 : 1;
-          ops += dim == 2 ? 3.0 * cx * cy : 3.0 * cx * cy * cz + 3.0 * cx * cy;
-        }
-      map_ops[pp] = ops;
-    }
+    // The launches of the moment path.  Without the own faces, the volume
+    // launch (kind 2) is credited with the volume terms' algorithmic work
+    // above (the quadrature sums it evaluates) and the row kernel's
+    // faces-only launch beside it (kind 1) with the rest; with them, the
+    // moment launch (kind 3) takes the element's volume and own-face terms
+    // and the off-diagonal launch (kind 4) the interface terms.  What the
+    // moment form executes instead is mom_exec (moment_op_tables).  It is
+    // reported as the "row_pass_executed" record beside "row_pass".
+    MomentOps ops;
+    moment_op_tables(dim, ops);
     for (int e = 0; e < ne; ++e) {
       if (!own(e)) continue;
       const int pe = d->p[e];
@@ -1069,16 +1098,25 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P, const int8_t* owned = nullp
       const double vol_direct = nvq * (dim * n * (n + 1) / 2 + (adv ? n * n + n * (dim + 1) : 0.0) +
                                        n * dim * dim + 5.0 * dim * pe + n);
       const double vol_words = n * n + n + (double)(d->elem_ptr[e + 1] - d->elem_ptr[e]) * SV + 2 * dim + 2;
+      double nfq = 0.0, nbq = 0.0;  // own-face points, boundary-face points
+      for (int k = hf_ptr[e]; k < hf_ptr[e + 1]; ++k) {
+        const int f = hf_face[k];
+        const double qf = dim == 2 ? f_nq[f] : (double)f_nq[f] * f_nq[f];
+        nfq += qf;
+        if (F[f].e1 < 0) nbq += qf;
+      }
       P.flops[1][pe] -= 2.0 * vol_direct;
       P.words[1][pe] -= vol_words;
       P.flops[2][pe] += 2.0 * vol_direct;
       P.words[2][pe] += vol_words;
-      P.mom_exec[pe] += 2.0 * (nvq * pt_ops[pe] + map_ops[pe]);
+      const double vx = nvq * ops.pt[pe] + ops.map[pe];
+      P.mom_exec[0][pe] += 2.0 * vx;
+      P.mom_exec[1][pe] += 2.0 * (vx + nfq * ops.fpt[pe] + nbq * ops.bnd[pe] + ops.mapf[pe]);
     }
     for (int pp = 0; pp <= 8; ++pp) {
       P.flops[1][pp] += P.flops[0][pp];
       P.words[1][pp] += P.words[0][pp];
-      P.mom_pt[pp] = 2.0 * pt_ops[pp];
+      P.mom_pt[pp] = 2.0 * ops.pt[pp];
     }
   }
   P.nsub = nsub;
@@ -2567,7 +2605,7 @@ static int issue_persist_rows(dg_ctx* ctx, dg_mesh* mesh, int prec, int mode, vo
     for (int p = 1; p <= 8; ++p) {
       fl += mesh->flops[0][p];
       by += mesh->words[0][p] * sizeof(float);
-      xfl += ((mom_mask >> p) & 1) ? mesh->mom_exec[p] + mesh->flops[1][p] : mesh->flops[0][p];
+      xfl += ((mom_mask >> p) & 1) ? mesh->mom_exec[0][p] + mesh->flops[1][p] : mesh->flops[0][p];
     }
     tr->begin_counts(mesh->dm.dim == 2 ? "row_persist2d_f32" : "row_persist3d_f32", fl, xfl, by, st);
   }
@@ -3006,7 +3044,8 @@ int dg_quad_fit(dg_ctx* ctx, dg_mesh* mesh, const float* init, int iters, int in
         if (ok[e] && (mesh->owned_h.empty() || mesh->owned_h[e])) {
           mesh->flops[0][mesh->p_h[e]] -= 2.0 * (mesh->nvq_h[e] - 28) * mesh->vfma_h[e];
           mesh->flops[2][mesh->p_h[e]] -= 2.0 * (mesh->nvq_h[e] - 28) * mesh->vfma_h[e];
-          mesh->mom_exec[mesh->p_h[e]] -= (mesh->nvq_h[e] - 28) * mesh->mom_pt[mesh->p_h[e]];
+          mesh->flops[3][mesh->p_h[e]] -= 2.0 * (mesh->nvq_h[e] - 28) * mesh->vfma_h[e];
+          for (int k = 0; k < 2; ++k) mesh->mom_exec[k][mesh->p_h[e]] -= (mesh->nvq_h[e] - 28) * mesh->mom_pt[mesh->p_h[e]];
         }
     }
   }
@@ -3046,7 +3085,8 @@ int dg_quad_clear(dg_ctx* ctx, dg_mesh* mesh) {
       if (okd[e] && (mesh->owned_h.empty() || mesh->owned_h[e])) {
         mesh->flops[0][mesh->p_h[e]] += 2.0 * (mesh->nvq_h[e] - 28) * mesh->vfma_h[e];
         mesh->flops[2][mesh->p_h[e]] += 2.0 * (mesh->nvq_h[e] - 28) * mesh->vfma_h[e];
-        mesh->mom_exec[mesh->p_h[e]] += (mesh->nvq_h[e] - 28) * mesh->mom_pt[mesh->p_h[e]];
+        mesh->flops[3][mesh->p_h[e]] += 2.0 * (mesh->nvq_h[e] - 28) * mesh->vfma_h[e];
+        for (int k = 0; k < 2; ++k) mesh->mom_exec[k][mesh->p_h[e]] += (mesh->nvq_h[e] - 28) * mesh->mom_pt[mesh->p_h[e]];
       }
     int rc = rebuild_worklist(ctx, mesh, ok);
     if (rc != DG_OK) return rc;

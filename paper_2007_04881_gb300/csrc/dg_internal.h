@@ -191,6 +191,12 @@ enum : int {
   kModeAccum = 8,  // add to the diagonal block instead of overwriting it
   kModeSkipVol = 16,  // volume terms done by the moment kernel: faces only, load vector added
   kModeExactMom = 32,  // moment launch: volume moments exact (2D: Green's theorem along the edges; 3D: the divergence theorem on the boundary triangles)
+  // moment launch: the own-face terms too, the diagonal block's through face
+  // moments (with kModeFace) and the boundary load terms per point (with
+  // kModeRhs), so that the block row's only other writer is the row kernel's
+  // off-diagonal launch (kModeOffDiag)
+  kModeMomFace = 64,
+  kModeOffDiag = 128,  // row kernel: the off-diagonal blocks only (diagonal block and load vector untouched)
 };
 
 // Optional per-launch timing: CUDA events recorded on the launch stream
@@ -204,7 +210,7 @@ struct LaunchRec {
   cudaEvent_t ev0, ev1;
 };
 
-constexpr int kKinds = 3;
+constexpr int kKinds = 5;
 struct Tracer {
   bool on = false;
   LaunchRec* recs = nullptr;  // capacity cap, filled from n
@@ -212,11 +218,12 @@ struct Tracer {
   int n = 0;
   // per launch-group algorithmic counts, indexed [kind][p]; kind 0 = row
   // kernel of degree p (volume and faces), 1 = its faces-only launch next to
-  // the moment kernel, 2 = the moment volume kernel; words = values written +
-  // read, scaled by sizeof(T)
+  // the moment kernel, 2 = the moment volume kernel, 3 = the moment kernel
+  // with the own-face terms, 4 = the row kernel's off-diagonal launch beside
+  // it; words = values written + read, scaled by sizeof(T)
   const double* flops = nullptr;   // [kKinds][9]
   const double* words = nullptr;   // [kKinds][9]
-  const double* xflops = nullptr;  // [9]: flops the kind-2 launch executes
+  const double* xflops = nullptr;  // [2][9]: flops the kind-2 and kind-3 launches execute
   // share of its degree group's counts the next begin() records (a group
   // launched as several parts)
   double scale = 1.0;
@@ -226,6 +233,12 @@ struct Tracer {
   void end(cudaStream_t st);
   static void record(cudaEvent_t ev, cudaStream_t st);
 };
+
+// Executed-operation tables of the moment launch by degree (dg_host.cu).
+struct MomentOps {
+  double pt[9] = {0}, map[9] = {0}, fpt[9] = {0}, bnd[9] = {0}, mapf[9] = {0};
+};
+void moment_op_tables(int dim, MomentOps& o);
 
 // Launchers (defined in the kernel translation units).  Each returns the
 // number of kernel launches issued.
@@ -309,7 +322,7 @@ struct DevPattern {
   int nsub = 0, nf = 0, nint = 0, ni = 0, nhf = 0, nnzb = 0;
   int64_t nvals = 0, ndofs = 0, nqvol = 0, nqface = 0;
   int elem_pstart[9] = {0}, if_pstart[9] = {0};
-  double flops[3][9] = {{0}}, words[3][9] = {{0}}, mom_exec[9] = {0}, mom_pt[9] = {0};
+  double flops[kKinds][9] = {{0}}, words[kKinds][9] = {{0}}, mom_exec[2][9] = {{0}}, mom_pt[9] = {0};
   std::vector<int> h_row_ptr, h_col, h_e_nqf, h_nvq, h_perm;
   std::vector<int64_t> h_blk_off, h_dof_off;
 };

@@ -22,7 +22,8 @@ inline int resident_grid(K kernel, size_t smem, int sm_count, int want_blocks, i
 }
 
 // The row-kernel launch of one degree group with tile variant V (kind: the
-// tracer's accounting kind, 0 whole rows, 1 faces next to the moment launch).
+// tracer's accounting kind, 0 whole rows, 4 off-diagonal blocks next to the
+// moment launch).
 template <int D, int P, typename T, int V>
 int launch_row_tile(const DevMesh& m, int mode, T* vals, T* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr,
                     int kind) {
@@ -66,6 +67,19 @@ template <int D, int P, typename T>
 inline int launch_row_range(const DevMesh& m, int mode, T* vals, T* rhs, int sm_count, const LaunchOpts& lo,
                             Tracer* tr);
 
+// the row-kernel launch in the tile variant lo.tile[P]
+template <int D, int P, typename T>
+inline int launch_row_variant(const DevMesh& m, int mode, T* vals, T* rhs, int sm_count, const LaunchOpts& lo,
+                              Tracer* tr, int kind) {
+  constexpr int NV = tile_variants<D, P, T>();
+  const int v = lo.tile[P] < NV ? lo.tile[P] : 0;
+  if constexpr (NV > 2)
+    if (v == 2) return launch_row_tile<D, P, T, 2>(m, mode, vals, rhs, sm_count, lo, tr, kind);
+  if constexpr (NV > 1)
+    if (v == 1) return launch_row_tile<D, P, T, 1>(m, mode, vals, rhs, sm_count, lo, tr, kind);
+  return launch_row_tile<D, P, T, 0>(m, mode, vals, rhs, sm_count, lo, tr, kind);
+}
+
 // One degree group: in lo.split[P] parts of equal element count, each a copy
 // of the mesh view whose range [elem_pstart[P], elem_pstart[P+1]) is the
 // part's (every kernel takes its elements from that range), on its own stream.
@@ -101,34 +115,31 @@ inline int launch_row_range(const DevMesh& m, int mode, T* vals, T* rhs, int sm_
   int n = 0, kind = 0;
   if constexpr (TileCfg<D, P, T>::TPE != 1 && moment_volume_ok<D, P, T>()) {
     // the moment path needs the linearisation tables of the rule set
-    if (lo.vol_moments && m.rt.lin32 && m.rt.lin64 && (mode & (kModeVol | kModeRhs))) {
-      // volume terms through the moments, then the faces added by the row kernel
+    if (lo.vol_moments && m.rt.lin32 && m.rt.lin64 && (mode & (kModeVol | kModeFace | kModeRhs))) {
+      // volume and own-face terms through the moments (the diagonal block and
+      // the load vector complete), then the off-diagonal blocks by the row
+      // kernel, which no longer reads what the moment launch writes
       using MC = MomCfg<D, P, T>;
       static_assert(MC::total <= 227 * 1024, "moment kernel shared memory exceeds 227 KB");
       if (tr && tr->on) {
         char name[48];
         snprintf(name, sizeof name, "row%dd_vol_p%d_%s", D, P, tn);
-        tr->begin(name, 2, P, sizeof(T), st);
+        tr->begin(name, 3, P, sizeof(T), st);
       }
       auto k = vol_moment_kernel<D, P, T>;
       const int ngroups = (count + MC::G - 1) / MC::G;
       const int grid = resident_grid(k, MC::total, sm_count, (ngroups + kWarps - 1) / kWarps, lo.occ_cap);
       const int xm = lo.vol_exact ? kModeExactMom : 0;
-      k<<<grid, kWarps * 32, MC::total, st>>>(m, (mode & (kModeVol | kModeRhs | kModeAccum)) | xm, vals, rhs);
+      k<<<grid, kWarps * 32, MC::total, st>>>(
+          m, (mode & (kModeVol | kModeFace | kModeRhs | kModeAccum)) | xm | kModeMomFace, vals, rhs);
       if (tr && tr->on) tr->end(st);
       ++n;
-      if (!(mode & (kModeFace | kModeRhs))) return n;
-      mode = (mode & ~kModeVol) | kModeSkipVol | ((mode & kModeVol) ? kModeAccum : 0);
-      kind = 1;
+      if (!(mode & kModeFace)) return n;
+      mode = kModeFace | kModeSkipVol | kModeOffDiag;
+      kind = 4;
     }
   }
-  constexpr int NV = tile_variants<D, P, T>();
-  const int v = lo.tile[P] < NV ? lo.tile[P] : 0;
-  if constexpr (NV > 2)
-    if (v == 2) return n + launch_row_tile<D, P, T, 2>(m, mode, vals, rhs, sm_count, lo, tr, kind);
-  if constexpr (NV > 1)
-    if (v == 1) return n + launch_row_tile<D, P, T, 1>(m, mode, vals, rhs, sm_count, lo, tr, kind);
-  return n + launch_row_tile<D, P, T, 0>(m, mode, vals, rhs, sm_count, lo, tr, kind);
+  return n + launch_row_variant<D, P, T>(m, mode, vals, rhs, sm_count, lo, tr, kind);
 }
 
 }  // namespace dg

@@ -25,6 +25,18 @@
 // The load vector's volume term (non-polynomial f) is accumulated per point
 // as before.
 //
+// Own-face terms (kModeMomFace).  On the element's faces the diagonal block
+// gains sum_q W [(sigma - min(b.n, 0)) Phi_i Phi_j - kappa a (Phi_i DN_j +
+// DN_i Phi_j)] with DN = n' . grad_xi: the derivative part is the normal
+// derivative of the product Phi_i Phi_j, so with the same linearisation
+//   A_ij += sum_{c,d(,e)} X0(c) Y0(d) (Z0(e)) F_cd(e),
+//   F_cd = sum_q W [(sigma - upw) P_c P_d - kappa a (n'_1 P'_c P_d + n'_2 P_c P'_d)]
+// (3D: one more derivative term), one moment set for all the faces of the
+// element, summed over the face rule of each face (exact for the products,
+// degree 2p along a face).  The boundary faces' load terms (Eq. (2.5): the
+// Dirichlet data or the Neumann flux times Phi_i and DN_i) are added per
+// point.  The row kernel then writes only the off-diagonal blocks.
+//
 // Layout: LPE lanes per element.  Each lane accumulates the moments and the
 // load vector of every LPE-th point in registers; a butterfly reduction over
 // the lanes gives the sums (a fixed order, no atomics).  The lanes then write
@@ -63,9 +75,9 @@ struct MomCfg {
   static constexpr int CL = 2 * kPMaxLin + 1;
   static constexpr int NLIN = 3 * PL * PL * CL;  // G, G1, G2
   static constexpr int NPAIR = (P + 1) * (P + 1);
-  // per element: moments, and three [NPAIR][Q+1] tables: Xa, then in 2D the
-  // stage-one sums T and U, in 3D Yb and Zs
-  static constexpr int PER_ELEM = NM + 3 * NPAIR * (Q + 1);
+  // per element: moments, face moments, and three [NPAIR][Q+1] tables: Xa,
+  // then in 2D the stage-one sums T and U, in 3D Yb and Zs
+  static constexpr int PER_ELEM = 2 * NM + 3 * NPAIR * (Q + 1);
   static constexpr int NMAXC = nbasis(D, D == 2 ? kPMax2 : kPMax3);
   // linearisation tables, rule, basis scales, then the exponents of the
   // degree's basis functions (int, [N][3])
@@ -100,11 +112,16 @@ __device__ __forceinline__ void mom_tile(const DevMesh& m, int mode, T* __restri
 
   const T* SG = pick<T>(m.sg64, m.sg32);
   const bool mat_vol = mode & kModeVol, do_rhs = mode & kModeRhs, accum = mode & kModeAccum;
+  // own-face terms here (the row kernel then writes the off-diagonal blocks only)
+  const bool mface = mode & kModeMomFace;
+  const bool mat_face = mface && (mode & kModeFace);
+  const bool mat_any = mat_vol || mat_face;
   const int lane = threadIdx.x & 31;
   const int grp = lane / LPE, lig = lane % LPE;
   T* my = pw + (size_t)grp * Cfg::PER_ELEM;  // this element's scratch
   T* smu = my;
-  T* sXa = my + NM;                // [NPAIR][Q+1] per exponent pair (a, a') of dimension 0
+  T* sF = my + NM;                 // face moments
+  T* sXa = sF + NM;                // [NPAIR][Q+1] per exponent pair (a, a') of dimension 0
   T* sYb = sXa + NPAIR * (Q + 1);  // 3D: dimension 1 [NPAIR][Q+1]; 2D: T [Q+1][NPAIR]
   T* sZs = sYb + NPAIR * (Q + 1);  // 3D: dimension 2 [NPAIR][Q+1]; 2D: U [Q+1][NPAIR]
   const int base = m.elem_pstart[P], count = m.elem_pstart[P + 1] - base;
@@ -324,14 +341,168 @@ __device__ __forceinline__ void mom_tile(const DevMesh& m, int mode, T* __restri
         }
       }
     }
-    // butterfly sums over the element's lanes (fixed order)
+    // butterfly sums over the element's lanes (fixed order); the volume
+    // moments go to shared memory (zeros without kModeVol)
+    if (mat_vol) {
 #pragma unroll
-    for (int off = LPE / 2; off > 0; off >>= 1) {
-      if (mat_vol) {
+      for (int off = LPE / 2; off > 0; off >>= 1) {
 #pragma unroll
         for (int k = 0; k < NM; ++k) mu[k] += __shfl_xor_sync(0xffffffffu, mu[k], off);
       }
-      if (do_rhs) {
+    }
+    if (mat_any) {
+      __syncwarp();
+      if (active) {
+#pragma unroll
+        for (int k = 0; k < NM; ++k)
+          if (k % LPE == lig) smu[k] = mu[k];
+      }
+    }
+
+    // ---- own-face terms (kModeMomFace): face moments in the registers of mu,
+    // boundary load terms into racc; one lane per face point
+    if (mface && (mat_face || do_rhs)) {
+      constexpr int FV = side_vals(D), RS = hf_rec_vals(D);
+      const T* HFR = pick<T>(m.hfr64, m.hfr32);
+      const T* FRb = pick<T>(m.rt.face64, m.rt.face32);
+#pragma unroll
+      for (int k = 0; k < NM; ++k) mu[k] = T(0);
+      const int h0 = active ? m.hf_ptr[e] : 0;
+      const int nhf = active ? m.hf_ptr[e + 1] - h0 : 0;
+      const int nfp = active ? m.e_nqf[e] : 0;
+      for (int qv = lig; qv < nfp; qv += LPE) {
+        // the point's half face: the last one whose first point is <= qv
+        int lo_ = h0, hi_ = h0 + nhf - 1;
+        while (lo_ < hi_) {
+          const int mid = (lo_ + hi_ + 1) >> 1;
+          if (m.hf_qoff[mid] <= qv)
+            lo_ = mid;
+          else
+            hi_ = mid - 1;
+        }
+        // own side, then J, sigma (-1: Neumann), b.n, nq (negative: boundary)
+        const T* rec = HFR + (size_t)lo_ * RS;
+        const T J = rec[2 * FV], s1 = rec[2 * FV + 1], bn = rec[2 * FV + 2], s3 = rec[2 * FV + 3];
+        const bool bnd = s3 < T(0);
+        if (!mat_face && !bnd) continue;  // an interior face has no load term
+        const int nq = (int)(bnd ? -s3 : s3);
+        const T* fr = FRb + (size_t)(m.rt.face_off[nq] + qv - m.hf_qoff[lo_]) * (D == 2 ? 2 : 3);
+        T xi[D], np[D];
+        hf_point<D, T>(rec, fr, xi, np);
+        const T W = fr[D == 2 ? 1 : 2] * J;
+        const bool neu = s1 < T(0);
+        const T sig = neu ? T(0) : s1;
+        const T kap = neu ? T(0) : bnd ? T(1) : T(0.5);
+        const T upw = bn < T(0) ? bn : T(0);
+        // P_0..P_q and P'_0..P'_q per coordinate (P'_{k+1} = P'_{k-1} + (2k+1) P_k)
+        T Lv[3][Q + 1], dL[3][Q + 1];
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          Lv[d][0] = T(1);
+          dL[d][0] = T(0);
+          Lv[d][1] = xi[d];
+          dL[d][1] = T(1);
+#pragma unroll
+          for (int k = 1; k < Q; ++k) {
+            Lv[d][k + 1] = (T(2 * k + 1) / T(k + 1)) * xi[d] * Lv[d][k] - (T(k) / T(k + 1)) * Lv[d][k - 1];
+            dL[d][k + 1] = fma(T(2 * k + 1), Lv[d][k], dL[d][k - 1]);
+          }
+        }
+        if (mat_face) {
+          const T w0 = W * (sig - upw);
+          T wn[3];
+#pragma unroll
+          for (int d = 0; d < D; ++d) wn[d] = -W * kap * q.a * np[d];
+          if constexpr (D == 2) {
+            // F_cd += P_d (w0 P_c + wn_1 P'_c) + (wn_2 P_c) P'_d
+#pragma unroll
+            for (int c = 0; c <= Q; ++c) {
+              const T A = fma(w0, Lv[0][c], wn[0] * dL[0][c]);
+              const T B = wn[1] * Lv[0][c];
+#pragma unroll
+              for (int d = 0; c + d <= Q; ++d) {
+                const int s = c + d, k = s * (s + 1) / 2 + d;
+                mu[k] = fma(A, Lv[1][d], fma(B, dL[1][d], mu[k]));
+              }
+            }
+          } else {
+            // F_cde += P_e [P_d (w0 P_c + wn_1 P'_c) + wn_2 P_c P'_d] + (wn_3 P_c P_d) P'_e
+#pragma unroll
+            for (int c = 0; c <= Q; ++c) {
+              const T A0 = fma(w0, Lv[0][c], wn[0] * dL[0][c]);
+              const T B0 = Lv[0][c];
+#pragma unroll
+              for (int d = 0; c + d <= Q; ++d) {
+                const T A = fma(A0, Lv[1][d], wn[1] * B0 * dL[1][d]);
+                const T B = wn[2] * B0 * Lv[1][d];
+#pragma unroll
+                for (int ee = 0; c + d + ee <= Q; ++ee) {
+                  const int s = c + d + ee, t = d + ee;
+                  const int k = s * (s + 1) * (s + 2) / 6 + t * (t + 1) / 2 + ee;
+                  mu[k] = fma(A, Lv[2][ee], fma(B, dL[2][ee], mu[k]));
+                }
+              }
+            }
+          }
+        }
+        if (do_rhs && bnd) {
+          // Dirichlet: R0 = W (sigma - upw) g, R1 = -W a g; Neumann: R0 = W g_N,
+          // g_N = a grad u . n (n = n' L / 2), R1 = 0; r_i += R0 Phi_i + R1 DN_i
+          T x[D], gu[3], lap;
+#pragma unroll
+          for (int d = 0; d < D; ++d) x[d] = q.lo[d] + (xi[d] + T(1)) * T(0.5) * q.L[d];
+          const T gd = exact_u<D, T>(m.pb, x, gu, &lap);
+          T R0 = W * (sig - upw) * gd, R1 = -W * q.a * gd;
+          if (neu) {
+            T gn = T(0);
+#pragma unroll
+            for (int d = 0; d < D; ++d) gn += gu[d] * np[d] * q.L[d];
+            R0 = W * T(0.5) * q.a * gn;
+            R1 = T(0);
+          }
+          T ax[P + 1];
+#pragma unroll
+          for (int a = 0; a <= P; ++a) ax[a] = fma(R0, Lv[0][a], R1 * np[0] * dL[0][a]);
+          int i = 0;
+#pragma unroll
+          for (int k = 0; k <= P; ++k) {
+            if constexpr (D == 2) {
+#pragma unroll
+              for (int j = 0; j <= k; ++j) {
+                const int a = k - j;
+                racc[i] = fma(ax[a], Lv[1][j], fma(R1 * np[1] * Lv[0][a], dL[1][j], racc[i]));
+                ++i;
+              }
+            } else {
+#pragma unroll
+              for (int l = 0; l <= k; ++l)
+#pragma unroll
+                for (int j = 0; j <= k - l; ++j) {
+                  const int a = k - j - l;
+                  const T yz1 = R1 * fma(np[1], dL[1][j] * Lv[2][l], np[2] * Lv[1][j] * dL[2][l]);
+                  racc[i] = fma(ax[a], Lv[1][j] * Lv[2][l], fma(Lv[0][a], yz1, racc[i]));
+                  ++i;
+                }
+            }
+          }
+        }
+      }
+      if (mat_face) {
+#pragma unroll
+        for (int off = LPE / 2; off > 0; off >>= 1) {
+#pragma unroll
+          for (int k = 0; k < NM; ++k) mu[k] += __shfl_xor_sync(0xffffffffu, mu[k], off);
+        }
+        if (active) {
+#pragma unroll
+          for (int k = 0; k < NM; ++k)
+            if (k % LPE == lig) sF[k] = mu[k];
+        }
+      }
+    }
+    if (do_rhs) {
+#pragma unroll
+      for (int off = LPE / 2; off > 0; off >>= 1) {
 #pragma unroll
         for (int i = 0; i < N; ++i) racc[i] += __shfl_xor_sync(0xffffffffu, racc[i], off);
       }
@@ -346,12 +517,9 @@ __device__ __forceinline__ void mom_tile(const DevMesh& m, int mode, T* __restri
     }
 
     // ---- diagonal block from the moments
-    if (mat_vol) {
+    if (mat_any) {
       __syncwarp();
       if (active) {
-#pragma unroll
-        for (int k = 0; k < NM; ++k)
-          if (k % LPE == lig) smu[k] = mu[k];
         // per exponent pair (a, a'): the element's coefficient combinations
         for (int k = lig; k < NPAIR * (Q + 1); k += LPE) {
           const int pr = k / (Q + 1), c = k - pr * (Q + 1);
@@ -376,11 +544,21 @@ __device__ __forceinline__ void mom_tile(const DevMesh& m, int mode, T* __restri
             const T* g2 = lin + 2 * PL * PL * CL + (b * PL + bp) * CL;  // G2(b, b', d)
             int mi = c * (c + 1) / 2;  // moment (c, 0); (c, d + 1) is c + d + 2 further
             T t0 = T(0), u0 = T(0);
-            for (int d = 0; d <= dm; ++d) {
-              const T mu_cd = smu[mi];
-              mi += c + d + 2;
-              t0 = fma(mu_cd, g0[d], t0);
-              u0 = fma(mu_cd, q.bp[1] * g1[d] + q.ap[1] * g2[d], u0);
+            if (mat_face) {
+              // the face moments enter with X0(c) Y0(d), beside the volume's X0(c) Yb(d)
+              for (int d = 0; d <= dm; ++d) {
+                const T mu_cd = smu[mi], f_cd = sF[mi];
+                mi += c + d + 2;
+                t0 = fma(mu_cd, g0[d], t0);
+                u0 = fma(mu_cd, q.bp[1] * g1[d] + q.ap[1] * g2[d], fma(f_cd, g0[d], u0));
+              }
+            } else {
+              for (int d = 0; d <= dm; ++d) {
+                const T mu_cd = smu[mi];
+                mi += c + d + 2;
+                t0 = fma(mu_cd, g0[d], t0);
+                u0 = fma(mu_cd, q.bp[1] * g1[d] + q.ap[1] * g2[d], u0);
+              }
             }
             sYb[k] = t0;
             sZs[k] = u0;
@@ -414,8 +592,16 @@ __device__ __forceinline__ void mom_tile(const DevMesh& m, int mode, T* __restri
                 const T y0 = L0(ai[1], aj[1], d);
                 const T k1 = y0 * xa + x0 * sYb[py * (Q + 1) + d], k2 = x0 * y0;
                 T s = T(0);
-                for (int ee = 0; ee <= emax; ++ee)
-                  s = fma(smu[mom3(c, d, ee)], L0(ai[2], aj[2], ee) * k1 + sZs[pz * (Q + 1) + ee] * k2, s);
+                if (mat_face) {
+                  for (int ee = 0; ee <= emax; ++ee) {
+                    const int k = mom3(c, d, ee);
+                    const T z0 = L0(ai[2], aj[2], ee);
+                    s = fma(smu[k], z0 * k1 + sZs[pz * (Q + 1) + ee] * k2, fma(sF[k], z0 * k2, s));
+                  }
+                } else {
+                  for (int ee = 0; ee <= emax; ++ee)
+                    s = fma(smu[mom3(c, d, ee)], L0(ai[2], aj[2], ee) * k1 + sZs[pz * (Q + 1) + ee] * k2, s);
+                }
                 acc += s;
               }
             }

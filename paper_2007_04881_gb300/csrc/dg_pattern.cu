@@ -565,18 +565,21 @@ __global__ void uverts_kernel(const int* __restrict__ eptr, const int* __restric
 
 // Algorithmic work per launch group, the host's accounting (plan_mesh) in
 // kernels: every term is an integer or a half integer, so the double
-// atomics are exact and the sums do not depend on the order
+// atomics are exact and the sums do not depend on the order.  acc layout:
+// flops [kKinds][9], words [kKinds][9], executed [2][9] (kAccN values).
+constexpr int kAccW = kKinds * 9, kAccX = 2 * kKinds * 9, kAccN = 2 * kKinds * 9 + 18;
+
 __global__ void account_elem_kernel(int ne, int dim, bool adv, bool advb, const int* __restrict__ p,
                                     const int* __restrict__ nvq, const int* __restrict__ hf_ptr,
                                     const int* __restrict__ hf_face, const int* __restrict__ f_nq,
                                     const int* __restrict__ f_e1, const int* __restrict__ nsub_e,
-                                    const double* __restrict__ pt_ops, const double* __restrict__ map_ops,
-                                    double* __restrict__ acc /* [3][9] flops, [3][9] words, [9] mom */) {
+                                    const double* __restrict__ tabs /* pt, map, fpt, bnd, mapf [9] */,
+                                    double* __restrict__ acc) {
   // per-CTA sums in shared memory, then one global add per bin: the values
   // are integers or halves, exact in double, so the order of the adds does
   // not change the result
-  __shared__ double sacc[63];
-  for (int t = threadIdx.x; t < 63; t += blockDim.x) sacc[t] = 0.0;
+  __shared__ double sacc[kAccN];
+  for (int t = threadIdx.x; t < kAccN; t += blockDim.x) sacc[t] = 0.0;
   __syncthreads();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e < ne) {
@@ -588,33 +591,40 @@ __global__ void account_elem_kernel(int ne, int dim, bool adv, bool advb, const 
     const double vol_direct = nv * (dim * n * (n + 1) / 2 + (adv ? n * n + n * (dim + 1) : 0.0) + basis + n);
     double fma = vol_direct;
     const double vol_words = n * n + n + (double)nsub_e[e] * SV + 2 * dim + 2;
-    double w = vol_words;
+    double w = vol_words, nfq = 0.0, nbq = 0.0;
     for (int k = hf_ptr[e]; k < hf_ptr[e + 1]; ++k) {
       const int f = hf_face[k];
       const double qf = dim == 2 ? f_nq[f] : (double)f_nq[f] * f_nq[f];
       const bool bnd = f_e1[f] < 0;
       fma += qf * (3 * n * n + (advb ? (bnd ? n * n : n * n / 2) : 0.0) + basis + (bnd ? 2 * n : 0.0));
       w += FV + 3;
+      nfq += qf;
+      if (bnd) nbq += qf;
     }
     atomicAdd(&sacc[0 * 9 + pe], 2.0 * fma);
-    atomicAdd(&sacc[27 + 0 * 9 + pe], w);
-    // the moment path's launches: volume to kind 2, the rest to kind 1
+    atomicAdd(&sacc[kAccW + 0 * 9 + pe], w);
+    // the moment path's launches: volume to kind 2, the rest to kind 1; with
+    // the own faces, the element's terms to kind 3
     atomicAdd(&sacc[1 * 9 + pe], 2.0 * (fma - vol_direct));
-    atomicAdd(&sacc[27 + 1 * 9 + pe], w - vol_words);
+    atomicAdd(&sacc[kAccW + 1 * 9 + pe], w - vol_words);
     atomicAdd(&sacc[2 * 9 + pe], 2.0 * vol_direct);
-    atomicAdd(&sacc[27 + 2 * 9 + pe], vol_words);
-    atomicAdd(&sacc[54 + pe], 2.0 * (nv * pt_ops[pe] + map_ops[pe]));
+    atomicAdd(&sacc[kAccW + 2 * 9 + pe], vol_words);
+    atomicAdd(&sacc[3 * 9 + pe], 2.0 * fma);
+    atomicAdd(&sacc[kAccW + 3 * 9 + pe], w);
+    const double vx = nv * tabs[pe] + tabs[9 + pe];
+    atomicAdd(&sacc[kAccX + pe], 2.0 * vx);
+    atomicAdd(&sacc[kAccX + 9 + pe], 2.0 * (vx + nfq * tabs[18 + pe] + nbq * tabs[27 + pe] + tabs[36 + pe]));
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < 63; t += blockDim.x)
+  for (int t = threadIdx.x; t < kAccN; t += blockDim.x)
     if (sacc[t] != 0.0) atomicAdd(&acc[t], sacc[t]);
 }
 
 __global__ void account_iface_kernel(int ni, int dim, bool advb, const int* __restrict__ if_e0,
                                      const int* __restrict__ if_e1, const int* __restrict__ if_fptr,
                                      const int* __restrict__ f_nq, const int* __restrict__ p, double* __restrict__ acc) {
-  __shared__ double sacc[63];  // per-CTA sums, as in account_elem_kernel
-  for (int t = threadIdx.x; t < 63; t += blockDim.x) sacc[t] = 0.0;
+  __shared__ double sacc[kAccN];  // per-CTA sums, as in account_elem_kernel
+  for (int t = threadIdx.x; t < kAccN; t += blockDim.x) sacc[t] = 0.0;
   __syncthreads();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < ni) {
@@ -629,13 +639,15 @@ __global__ void account_iface_kernel(int ni, int dim, bool advb, const int* __re
         w += 2 * FV + 3;
       }
       atomicAdd(&sacc[0 * 9 + p[e]], 2.0 * fma);
-      atomicAdd(&sacc[27 + 0 * 9 + p[e]], w);
+      atomicAdd(&sacc[kAccW + 0 * 9 + p[e]], w);
       atomicAdd(&sacc[1 * 9 + p[e]], 2.0 * fma);
-      atomicAdd(&sacc[27 + 1 * 9 + p[e]], w);
+      atomicAdd(&sacc[kAccW + 1 * 9 + p[e]], w);
+      atomicAdd(&sacc[4 * 9 + p[e]], 2.0 * fma);
+      atomicAdd(&sacc[kAccW + 4 * 9 + p[e]], w);
     }
   }
   __syncthreads();
-  for (int t = threadIdx.x; t < 63; t += blockDim.x)
+  for (int t = threadIdx.x; t < kAccN; t += blockDim.x)
     if (sacc[t] != 0.0) atomicAdd(&acc[t], sacc[t]);
 }
 
@@ -897,55 +909,43 @@ int build_pattern_device(const dg_mesh_desc* d, const int* eptr, const int* eidx
   }
 
   // ---- accounting (the host's formulas)
-  double* acc = (double*)tmp(sizeof(double) * 63);
-  double* tabs = (double*)tmp(sizeof(double) * 18);
+  double* acc = (double*)tmp(sizeof(double) * kAccN);
+  double* tabs = (double*)tmp(sizeof(double) * 45);
   int* nsub_e = (int*)tmp(sizeof(int) * (size_t)ne);
   if (int rc = bad()) return rc;
   {
-    double pt_ops[9] = {0}, map_ops[9] = {0};
-    for (int pp = 1; pp <= 8; ++pp) {
-      const int q = 2 * pp, nn = nbasis(dim, pp);
-      const double nmom = dim == 2 ? (q + 1) * (q + 2) / 2.0 : (q + 1) * (q + 2) * (q + 3) / 6.0;
-      pt_ops[pp] = 2.0 * dim * (q - 1) + (q + 1) + nmom + (dim == 3 ? (q + 1) * (q + 2) / 2.0 : 0.0) + nn * dim;
-      std::vector<std::array<int, 3>> al;
-      for (int k = 0; k <= pp; ++k)
-        for (int l = 0; l <= (dim == 3 ? k : 0); ++l)
-          for (int j = 0; j <= k - l; ++j) al.push_back({k - j - l, j, l});
-      double ops = 3.0 * dim * (pp + 1) * (pp + 1) * (q + 1);
-      for (const auto& a : al)
-        for (const auto& b : al) {
-          const double cx = a[0] + b[0] + 1, cy = a[1] + b[1] + 1, cz = dim == 3 ? a[2] + b[2] + 1 : 1;
-          ops += dim == 2 ? 3.0 * cx * cy : 3.0 * cx * cy * cz + 3.0 * cx * cy;
-        }
-      map_ops[pp] = ops;
-      P->mom_pt[pp] = 2.0 * pt_ops[pp];
-    }
-    P->mom_pt[0] = 0.0;
-    double h[18];
+    MomentOps ops;
+    moment_op_tables(dim, ops);
+    double h[45];
     for (int i = 0; i < 9; ++i) {
-      h[i] = pt_ops[i];
-      h[9 + i] = map_ops[i];
+      h[i] = ops.pt[i];
+      h[9 + i] = ops.map[i];
+      h[18 + i] = ops.fpt[i];
+      h[27 + i] = ops.bnd[i];
+      h[36 + i] = ops.mapf[i];
+      P->mom_pt[i] = 2.0 * ops.pt[i];
     }
     cudaMemcpyAsync(tabs, h, sizeof h, cudaMemcpyHostToDevice, st);
-    cudaMemsetAsync(acc, 0, sizeof(double) * 63, st);
+    cudaMemsetAsync(acc, 0, sizeof(double) * kAccN, st);
     const bool advb = d->b[0] != 0.0 || d->b[1] != 0.0 || (dim == 3 && d->b[2] != 0.0);
     const bool adv = advb || d->c != 0.0;
     nsub_kernel<<<nblk(ne), kT, 0, st>>>(eptr, ne, nsub_e);
     account_elem_kernel<<<nblk(ne), kT, 0, st>>>(ne, dim, adv, advb, p, nvq, P->hf_ptr, P->hf_face, P->f_nq,
-                                                 P->f_e1, nsub_e, tabs, tabs + 9, acc);
+                                                 P->f_e1, nsub_e, tabs, acc);
     if (ni > 0)
       account_iface_kernel<<<nblk(ni), kT, 0, st>>>(ni, dim, advb, P->if_e0, P->if_e1, P->if_fptr, P->f_nq, p, acc);
-    double hacc[63];
+    double hacc[kAccN];
     int hp[18];
     cudaMemcpyAsync(hacc, acc, sizeof hacc, cudaMemcpyDeviceToHost, st);
     cudaMemcpyAsync(hp, pcnt, sizeof hp, cudaMemcpyDeviceToHost, st);
     cudaStreamSynchronize(st);
-    for (int k = 0; k < 3; ++k)
+    for (int k = 0; k < kKinds; ++k)
       for (int q = 0; q < 9; ++q) {
         P->flops[k][q] = hacc[k * 9 + q];
-        P->words[k][q] = hacc[27 + k * 9 + q];
+        P->words[k][q] = hacc[kAccW + k * 9 + q];
       }
-    for (int q = 0; q < 9; ++q) P->mom_exec[q] = hacc[54 + q];
+    for (int k = 0; k < 2; ++k)
+      for (int q = 0; q < 9; ++q) P->mom_exec[k][q] = hacc[kAccX + k * 9 + q];
     P->elem_pstart[0] = P->if_pstart[0] = 0;
     for (int q = 0; q < 8; ++q) {
       P->elem_pstart[q + 1] = P->elem_pstart[q] + hp[q];

@@ -14,6 +14,12 @@ pytestmark = pytest.mark.gpu
 
 TOL32 = 5e-5      # block max-norm relative, FP32 contractions against the FP64 oracle
 TOL32_RHS = 1e-4  # per-element load vector (sin source evaluated in FP32)
+# Persistent pass against the per-degree launches, relative Frobenius.  On
+# the moment volume paths the per-degree launches form the own-face terms
+# through face moments and the persistent pass per face point: the same
+# sums in FP32 in another order, each within about 1e-6 of the FP64 form
+# (2e-7 and 8e-7 on the 3D bench mesh), so the two differ by up to the sum.
+TOL_PASS = 3e-6
 
 
 @pytest.fixture(scope="module")
@@ -47,7 +53,7 @@ def _step(ctx, mesh, persistent, prec=dg.DG_PREC_FP32):
 def test_persistent_2d_vs_oracle_and_launches(ctx, path):
     """Degrees 1..5 mixed, each volume path: every block against the oracle
     at the FP32 tolerance, and the whole matrix against the per-degree
-    launches (relative Frobenius 1e-6)."""
+    launches (relative Frobenius TOL_PASS)."""
     w = configs.small2d(700, 61, 1, 5, b=(1.0, 0.5), c=1.0)
     m = dg.Mesh(ctx, w.mesh, w.p, w.a, dg_problem(w))
     ctx.dg_set_volume_path(path)
@@ -57,8 +63,8 @@ def test_persistent_2d_vs_oracle_and_launches(ctx, path):
     finally:
         ctx.dg_set_volume_path(1)
     assert np.isfinite(vp).all() and np.isfinite(rp).all()
-    assert np.linalg.norm(vp - vs) <= 1e-6 * np.linalg.norm(vs)
-    assert np.linalg.norm(rp - rs) <= 1e-6 * np.linalg.norm(rs)
+    assert np.linalg.norm(vp - vs) <= TOL_PASS * np.linalg.norm(vs)
+    assert np.linalg.norm(rp - rs) <= TOL_PASS * np.linalg.norm(rs)
     om, ob = oracle_blocks(w)
     ed, eo, er = compare(dg.to_blocks(m, vp, rp), om, ob, w)
     assert ed < TOL32 and eo < TOL32 and er < TOL32_RHS, (ed, eo, er)
@@ -89,7 +95,7 @@ def test_persistent_3d_vs_oracle(ctx, path):
         vs, rs = _step(ctx, m, False)
     finally:
         ctx.dg_set_volume_path(1)
-    assert np.linalg.norm(vp - vs) <= 1e-6 * np.linalg.norm(vs), _where(m, w, vp, vs)
+    assert np.linalg.norm(vp - vs) <= TOL_PASS * np.linalg.norm(vs), _where(m, w, vp, vs)
     om, ob = oracle_blocks(w)
     ed, eo, er = compare(dg.to_blocks(m, vp, rp), om, ob, w)
     assert ed < TOL32 and eo < TOL32 and er < TOL32_RHS, (ed, eo, er)
@@ -163,4 +169,4 @@ def test_bounded_wait_reports_timeout(ctx):
     m = dg.Mesh(ctx, w.mesh, w.p, w.a, dg_problem(w))
     vp, _ = _step(ctx, m, True)
     vs, _ = _step(ctx, m, False)
-    assert np.linalg.norm(vp - vs) <= 1e-6 * np.linalg.norm(vs)
+    assert np.linalg.norm(vp - vs) <= TOL_PASS * np.linalg.norm(vs)
