@@ -1214,9 +1214,11 @@ __device__ __forceinline__ void row_tile(const DevMesh& m, int mode, T* __restri
         __syncwarp();
         if (lane < G) {
           int* pi = PIv + lane * PI;
-          if (lane < gcount && sl < pi[kPiNslot]) {
-            const int bk = pi[kPiRow0] + sl + (sl >= pi[kPiDpos] ? 1 : 0);
-            const int4 br = m.blk_rec[bk];  // neighbour, first half face, faces, neighbour degree
+          const int bk = lane < gcount && sl < pi[kPiNslot] ? pi[kPiRow0] + sl + (sl >= pi[kPiDpos] ? 1 : 0) : -1;
+          const int4 br = bk >= 0 ? m.blk_rec[bk] : make_int4(0, 0, 0, 0);  // neighbour, first half face, faces, its degree
+          // with kModeOffDiag: the interface kernel writes the block when the
+          // interface's larger degree is in the mask
+          if (bk >= 0 && !(off_only && ((mode >> (kModeMaskShift + (P > br.w ? P : br.w))) & 1))) {
             const int k = br.x, pk = br.w;
             const int nq = (P > pk ? P : pk) + 1;
             const int qf = D == 2 ? nq : nq * nq;

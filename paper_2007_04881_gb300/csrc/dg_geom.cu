@@ -852,7 +852,7 @@ inline int nblk(int n, int t) { return (n + t - 1) / t; }
 int launch_geometry(const DevMesh& m, cudaStream_t st, Tracer* tr, int wmask) {
   const int T = 128;
   // no algorithmic flop count of its own (kind past the counted ones)
-  if (tr && tr->on) tr->begin(m.dim == 2 ? "geometry2d" : "geometry3d", kKinds, 0, 8, st);
+  if (tr && tr->on) tr->begin(m.dim == 2 ? "geometry2d" : "geometry3d", kNoCounts, 0, 8, st);
   const int nsf = m.nsub + m.nf;
   if (wmask == 2 && m.xs2 && m.gx32) {
     if (m.nv > 0) vertex_split_kernel<<<nblk(m.dim * m.nv, T), T, 0, st>>>(m);

@@ -269,8 +269,32 @@ void Tracer::begin(const char* name, int kind, int p, size_t tsize, cudaStream_t
   LaunchRec& r = recs[n];
   snprintf(r.name, sizeof r.name, "%s", name);
   r.flops = ((kind < kKinds && flops) ? flops[kind * 9 + p] : 0.0) * scale;
-  r.xflops = ((kind == 2 || kind == 3) && xflops) ? xflops[(kind - 2) * 9 + p] * scale : r.flops;
   r.bytes = ((kind < kKinds && words) ? words[kind * 9 + p] * (double)tsize : 0.0) * scale;
+  if ((kind == 4 || kind == 5) && offd) {
+    // kind 4: blocks of degree-p rows whose interface's larger degree is not
+    // in imask; kind 5: interfaces of larger degree p, the blocks of their
+    // rows in imask
+    double fl = 0.0, wd = 0.0;
+    for (int q = 1; q <= 8; ++q) {
+      if (kind == 4 && !((imask >> std::max(p, q)) & 1)) {
+        fl += offd[p * 9 + q];
+        wd += offd[81 + p * 9 + q];
+      }
+      if (kind == 5 && q <= p) {
+        if ((imask >> p) & 1) {
+          fl += offd[p * 9 + q];
+          wd += offd[81 + p * 9 + q];
+        }
+        if (q < p && ((imask >> q) & 1)) {
+          fl += offd[q * 9 + p];
+          wd += offd[81 + q * 9 + p];
+        }
+      }
+    }
+    r.flops = fl * scale;
+    r.bytes = wd * (double)tsize * scale;
+  }
+  r.xflops = ((kind == 2 || kind == 3) && xflops) ? xflops[(kind - 2) * 9 + p] * scale : r.flops;
   record(r.ev0, st);
 }
 void Tracer::begin_counts(const char* name, double fl, double xfl, double by, cudaStream_t st) {
@@ -370,6 +394,7 @@ struct dg_mesh {
   double* a = nullptr;
   double flops[kKinds][9] = {{0}}, words[kKinds][9] = {{0}};
   double mom_exec[2][9] = {{0}}, mom_pt[9] = {0};
+  double offd[2][9][9] = {{{0}}};
   std::vector<int> batch_elem_off;  // element offset of each batch member (empty: one mesh)
   // partition meshes: local -> global element and vertex ids, owned flags
   std::vector<int> part_elem, part_vert;
@@ -423,6 +448,7 @@ static void trace_reset(dg_ctx* ctx, const dg_mesh* mesh) {
   ctx->tracer.flops = &mesh->flops[0][0];
   ctx->tracer.words = &mesh->words[0][0];
   ctx->tracer.xflops = &mesh->mom_exec[0][0];
+  ctx->tracer.offd = &mesh->offd[0][0][0];
 }
 
 namespace {
@@ -598,6 +624,7 @@ struct Plan {
   double flops[kKinds][9] = {{0}}, words[kKinds][9] = {{0}};
   double mom_exec[2][9] = {{0}};  // moment form: executed flops of the volume launch (without, with the own faces), by degree
   double mom_pt[9] = {0};    // moment form: executed flops per volume point, by degree
+  double offd[2][9][9] = {{{0}}};  // interface terms of degree-p rows by neighbour degree: flops, words
 };
 
 extern "C" {
@@ -1074,8 +1101,8 @@ static int plan_mesh(const dg_mesh_desc* d, Plan& P, const int8_t* owned = nullp
         }
         P.flops[0][d->p[e]] += 2.0 * fma;
         P.words[0][d->p[e]] += w;
-        P.flops[4][d->p[e]] += 2.0 * fma;
-        P.words[4][d->p[e]] += w;
+        P.offd[0][d->p[e]][d->p[k]] += 2.0 * fma;
+        P.offd[1][d->p[e]][d->p[k]] += w;
       }
     }
     // The launches of the moment path.  Without the own faces, the volume
@@ -1260,6 +1287,7 @@ static int upload_impl(dg_ctx* ctx, const dg_mesh_desc* d, const int8_t* owned, 
   std::memcpy(m->words, P.words, sizeof P.words);
   std::memcpy(m->mom_exec, P.mom_exec, sizeof P.mom_exec);
   std::memcpy(m->mom_pt, P.mom_pt, sizeof P.mom_pt);
+  std::memcpy(m->offd, P.offd, sizeof P.offd);
   m->blk_off = P.blk_off;
   m->dof_off = P.dof_off;
   DevMesh& dm = m->dm;
@@ -1342,7 +1370,11 @@ static int upload_impl(dg_ctx* ctx, const dg_mesh_desc* d, const int8_t* owned, 
   up_i(&dm.col, P.col);
   up_i(&dm.blk_if, P.blk_if);
   dm.nmax = 0;
-  for (int e = 0; e < ne; ++e) dm.nmax = std::max(dm.nmax, nbasis(dim, d->p[e]));
+  dm.pmask = 0;
+  for (int e = 0; e < ne; ++e) {
+    dm.nmax = std::max(dm.nmax, nbasis(dim, d->p[e]));
+    dm.pmask |= 1 << d->p[e];
+  }
   up_i(&dm.diag_blk, diag_blk);
   if (rc == DG_OK) rc = upload(B, &dm.dof_off, m->dof_off);
   up_i(&dm.elem_perm, elem_perm);
@@ -1497,7 +1529,11 @@ static int upload_impl_device(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out)
     dm.if_pstart[q] = P.if_pstart[q];
   }
   dm.nmax = 0;
-  for (int e = 0; e < ne; ++e) dm.nmax = std::max(dm.nmax, nbasis(dim, d->p[e]));
+  dm.pmask = 0;
+  for (int e = 0; e < ne; ++e) {
+    dm.nmax = std::max(dm.nmax, nbasis(dim, d->p[e]));
+    dm.pmask |= 1 << d->p[e];
+  }
   m->row_ptr = std::move(P.h_row_ptr);
   m->col = std::move(P.h_col);
   m->blk_off = std::move(P.h_blk_off);
@@ -1506,6 +1542,7 @@ static int upload_impl_device(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out)
   std::memcpy(m->words, P.words, sizeof P.words);
   std::memcpy(m->mom_exec, P.mom_exec, sizeof P.mom_exec);
   std::memcpy(m->mom_pt, P.mom_pt, sizeof P.mom_pt);
+  std::memcpy(m->offd, P.offd, sizeof P.offd);
   rc = alloc_records(m, dim, ne, nv, P.nsub, P.nf, P.nhf);
   if (rc != DG_OK) {
     delete m;
@@ -1998,16 +2035,16 @@ static int issue_slab(dg_ctx* ctx, dg_mesh* mesh, int prec, int space, double t0
   const SlabPattern sp = slab_pattern(mesh, space);
   const SlabTimes<double> tt = slab_time_data(t0, t1);
   const bool fp32 = prec == DG_PREC_FP32;
-  // per-launch timing records (no algorithmic flop or byte counts: kind kKinds)
+  // per-launch timing records (no algorithmic flop or byte counts: kind kNoCounts)
   Tracer* tr = &ctx->tracer;
-  tr->begin(fp32 ? "slab_matrix_f32" : "slab_matrix_f64", kKinds, 0, fp32 ? 4 : 8, st);
+  tr->begin(fp32 ? "slab_matrix_f32" : "slab_matrix_f64", kNoCounts, 0, fp32 ? 4 : 8, st);
   int pmax = 1;
   for (int q = 1; q <= 7; ++q)
     if (mesh->dm.elem_pstart[q + 1] > mesh->dm.elem_pstart[q]) pmax = q;
   n += launch_slab_matrix(sp, tt, fp32, mesh->slab_B, mesh->slab_M, vals, pmax, ctx->sm_count, st);
   tr->end(st);
   if (rhs) {
-    tr->begin(fp32 ? "slab_rhs_f32" : "slab_rhs_f64", kKinds, 0, fp32 ? 4 : 8, st);
+    tr->begin(fp32 ? "slab_rhs_f32" : "slab_rhs_f64", kNoCounts, 0, fp32 ? 4 : 8, st);
     n += launch_slab_rhs(sp, tt, fp32, mesh->slab_l, mesh->slab_M, u_prev, rhs, ctx->sm_count, st);
     tr->end(st);
   }
@@ -2125,7 +2162,7 @@ int dg_assemble_varcoef_form(dg_ctx* ctx, dg_mesh* mesh, int prec, void* vals, v
   const VcFields f = mesh->fields_set ? mesh->fields : vc_sec42_fields(m.dim);
   Tracer* tr = &ctx->tracer;
   const bool fp32 = prec == DG_PREC_FP32;
-  tr->begin(fp32 ? "varcoef_terms_f32" : "varcoef_terms_f64", kKinds, 0, fp32 ? 4 : 8, ctx->stream);
+  tr->begin(fp32 ? "varcoef_terms_f32" : "varcoef_terms_f64", kNoCounts, 0, fp32 ? 4 : 8, ctx->stream);
   n += launch_varcoef(m, f, fp32, vals, rhs, ctx->sm_count, ctx->stream);
   tr->end(ctx->stream);
   DG_CUDA_TRY(cudaGetLastError());

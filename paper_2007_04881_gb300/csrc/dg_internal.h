@@ -164,7 +164,8 @@ struct DevMesh {
   const int64_t* blk_off;
   const int* diag_blk;
   const int64_t* dof_off;
-  int nmax;  // largest basis size in the mesh
+  int nmax;   // largest basis size in the mesh
+  int pmask;  // bit p: an element of degree p in the mesh (a neighbour's, too, in a partition)
   // work lists
   const int* elem_perm;  // elements grouped by degree, each group cost-descending
   int elem_pstart[9];    // group of degree p: elem_perm[elem_pstart[p] .. elem_pstart[p+1])
@@ -198,6 +199,9 @@ enum : int {
   kModeMomFace = 64,
   kModeOffDiag = 128,  // row kernel: the off-diagonal blocks only (diagonal block and load vector untouched)
 };
+// with kModeOffDiag, bits kModeMaskShift + q: neighbours of degree q are
+// skipped (their interfaces are assembled by the interface kernel)
+constexpr int kModeMaskShift = 8;
 
 // Optional per-launch timing: CUDA events recorded on the launch stream
 // around each kernel, with the kernel's label and its algorithmic flop and
@@ -210,7 +214,8 @@ struct LaunchRec {
   cudaEvent_t ev0, ev1;
 };
 
-constexpr int kKinds = 5;
+constexpr int kKinds = 4;
+constexpr int kNoCounts = 99;  // Tracer::begin kind of a launch with no algorithmic counts
 struct Tracer {
   bool on = false;
   LaunchRec* recs = nullptr;  // capacity cap, filled from n
@@ -219,11 +224,16 @@ struct Tracer {
   // per launch-group algorithmic counts, indexed [kind][p]; kind 0 = row
   // kernel of degree p (volume and faces), 1 = its faces-only launch next to
   // the moment kernel, 2 = the moment volume kernel, 3 = the moment kernel
-  // with the own-face terms, 4 = the row kernel's off-diagonal launch beside
-  // it; words = values written + read, scaled by sizeof(T)
+  // with the own-face terms; words = values written + read, scaled by
+  // sizeof(T).  Kinds 4 (the row kernel's off-diagonal launch: the blocks of
+  // degree-p rows whose neighbour degree is not in imask) and 5 (the
+  // interface launch of larger degree p: interfaces with both degrees in
+  // imask) take their counts from offd.
   const double* flops = nullptr;   // [kKinds][9]
   const double* words = nullptr;   // [kKinds][9]
   const double* xflops = nullptr;  // [2][9]: flops the kind-2 and kind-3 launches execute
+  const double* offd = nullptr;    // [2][9][9]: interface-term flops, words of degree-p rows by neighbour degree
+  int imask = 0;
   // share of its degree group's counts the next begin() records (a group
   // launched as several parts)
   double scale = 1.0;
@@ -263,6 +273,11 @@ struct LaunchOpts {
   // parts' moment-then-rows chains run side by side
   int split[9] = {1, 1, 1, 1, 1, 1, 1, 1, 1};
   cudaStream_t part[9][kMaxSplit] = {};
+  bool iface = true;  // interfaces between two off-diagonal rows by the interface kernel (FP32)
+  // set by the launchers: the degrees in the mesh (neighbours included) and
+  // the degrees whose block rows leave their off-diagonal blocks to the
+  // interface kernel
+  int present = 0, imask = 0;
 };
 
 // Edge TM of the register tiles of tile variant v of the (dim, p) row kernel
@@ -323,6 +338,7 @@ struct DevPattern {
   int64_t nvals = 0, ndofs = 0, nqvol = 0, nqface = 0;
   int elem_pstart[9] = {0}, if_pstart[9] = {0};
   double flops[kKinds][9] = {{0}}, words[kKinds][9] = {{0}}, mom_exec[2][9] = {{0}}, mom_pt[9] = {0};
+  double offd[2][9][9] = {{{0}}};
   std::vector<int> h_row_ptr, h_col, h_e_nqf, h_nvq, h_perm;
   std::vector<int64_t> h_blk_off, h_dof_off;
 };

@@ -6,6 +6,7 @@
 #include <cstdio>
 
 #include "dg_device.cuh"
+#include "dg_iface.cuh"
 #include "dg_moment.cuh"
 
 namespace dg {
@@ -87,7 +88,8 @@ template <int D, int P, typename T>
 inline int launch_row_p(const DevMesh& m, int mode, T* vals, T* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr) {
   const int count = m.elem_pstart[P + 1] - m.elem_pstart[P];
   if (count <= 0) return 0;
-  const int parts = lo.split[P] < 1 ? 1 : lo.split[P] > kMaxSplit ? kMaxSplit : lo.split[P];
+  int parts = lo.split[P] < 1 ? 1 : lo.split[P] > kMaxSplit ? kMaxSplit : lo.split[P];
+  if (parts > count) parts = count;  // no empty part
   if (parts == 1) return launch_row_range<D, P, T>(m, mode, vals, rhs, sm_count, lo, tr);
   int n = 0;
   const int base = m.elem_pstart[P];
@@ -135,11 +137,91 @@ inline int launch_row_range(const DevMesh& m, int mode, T* vals, T* rhs, int sm_
       if (tr && tr->on) tr->end(st);
       ++n;
       if (!(mode & kModeFace)) return n;
-      mode = kModeFace | kModeSkipVol | kModeOffDiag;
+      // the off-diagonal blocks: those of interfaces whose larger degree is in
+      // imask come from the interface launch (launch_iface_all), the rest
+      // (neighbours of a higher degree outside imask) from here
+      if ((lo.imask >> P) & 1 && !(lo.present & ~lo.imask & ~((2 << P) - 1))) return n;
+      mode = kModeFace | kModeSkipVol | kModeOffDiag | (lo.imask << kModeMaskShift);
       kind = 4;
     }
   }
   return n + launch_row_variant<D, P, T>(m, mode, vals, rhs, sm_count, lo, tr, kind);
+}
+
+// whether the block rows of degree P take the off-diagonal launch when the
+// moment path is on (the moment launch completing their diagonal blocks)
+template <int D, int P, typename T>
+__host__ __device__ constexpr bool offdiag_rows() {
+  return TileCfg<D, P, T>::TPE != 1 && moment_volume_ok<D, P, T>();
+}
+
+// lo.present and lo.imask of one pass (interfaces by the interface kernel:
+// FP32, moment path, face terms requested)
+template <int D, typename T>
+inline void iface_setup(const DevMesh& m, int mode, LaunchOpts& lo, Tracer* tr) {
+  lo.present = m.pmask;  // the neighbours' degrees count: ghost elements of a partition
+  lo.imask = 0;
+  if (sizeof(T) == 4 && lo.iface && lo.vol_moments && m.rt.lin32 && m.rt.lin64 && (mode & kModeFace)) {
+    if (offdiag_rows<D, 1, T>()) lo.imask |= 1 << 1;
+    if (offdiag_rows<D, 2, T>()) lo.imask |= 1 << 2;
+    if (offdiag_rows<D, 3, T>()) lo.imask |= 1 << 3;
+    if (offdiag_rows<D, 4, T>()) lo.imask |= 1 << 4;
+    if (D == 2 && offdiag_rows<D, 5, T>()) lo.imask |= 1 << 5;
+    if (D == 2 && offdiag_rows<D, 6, T>()) lo.imask |= 1 << 6;
+  }
+  if (tr) tr->imask = lo.imask;
+}
+
+// The interface launches of larger degree P: if_perm[if_pstart[P] ..
+// if_pstart[P + 1]) in lo.split[P] contiguous parts on the group's streams.
+template <int D, int P, typename T>
+inline int launch_iface_p(const DevMesh& m, T* vals, int sm_count, const LaunchOpts& lo, Tracer* tr) {
+  if constexpr (!offdiag_rows<D, P, T>() || sizeof(T) != 4) {
+    return 0;
+  } else {
+    if (!((lo.imask >> P) & 1)) return 0;
+    const int b = m.if_pstart[P], count = m.if_pstart[P + 1] - b;
+    if (count <= 0) return 0;
+    using Cfg = IfaceCfg<D, P, T>;
+    static_assert(Cfg::total(kWarps) <= 227 * 1024, "interface kernel shared memory exceeds 227 KB");
+    int parts = lo.split[P] < 1 ? 1 : lo.split[P] > kMaxSplit ? kMaxSplit : lo.split[P];
+    if (parts > count) parts = count;
+    auto k = iface_kernel<D, P, T>;
+    const size_t smem = Cfg::total(kWarps);
+    int n = 0;
+    for (int i = 0; i < parts; ++i) {
+      const int i0 = b + (int)((int64_t)count * i / parts), i1 = b + (int)((int64_t)count * (i + 1) / parts);
+      cudaStream_t st = lo.part[P][i] ? lo.part[P][i] : lo.pst[P];
+      if (tr && tr->on) {
+        char name[48];
+        snprintf(name, sizeof name, "row%dd_iface_p%d_f32", D, P);
+        tr->scale = (double)(i1 - i0) / count;
+        tr->begin(name, 5, P, sizeof(T), st);
+        tr->scale = 1.0;
+      }
+      const int ntiles = (i1 - i0 + Cfg::G - 1) / Cfg::G;
+      const int grid = resident_grid(k, smem, sm_count, (ntiles + kWarps - 1) / kWarps, lo.occ_cap);
+      k<<<grid, kWarps * 32, smem, st>>>(m, lo.imask, i0, i1, vals);
+      if (tr && tr->on) tr->end(st);
+      ++n;
+    }
+    return n;
+  }
+}
+
+template <int D, typename T>
+inline int launch_iface_all(const DevMesh& m, T* vals, int sm_count, const LaunchOpts& lo, Tracer* tr) {
+  if (!lo.imask) return 0;
+  int n = 0;
+  n += launch_iface_p<D, 1, T>(m, vals, sm_count, lo, tr);
+  n += launch_iface_p<D, 2, T>(m, vals, sm_count, lo, tr);
+  n += launch_iface_p<D, 3, T>(m, vals, sm_count, lo, tr);
+  n += launch_iface_p<D, 4, T>(m, vals, sm_count, lo, tr);
+  if constexpr (D == 2) {
+    n += launch_iface_p<D, 5, T>(m, vals, sm_count, lo, tr);
+    n += launch_iface_p<D, 6, T>(m, vals, sm_count, lo, tr);
+  }
+  return n;
 }
 
 }  // namespace dg

@@ -284,6 +284,7 @@ extern "C" int dg_volume_noalloc(void* stream, int device, int prec, int p, int 
   m.diag_blk = reinterpret_cast<const int*>(b + o_diag);
   m.elem_perm = reinterpret_cast<const int*>(b + o_perm);
   m.nmax = n;
+  m.pmask = 1 << p;
   m.nvals = (int64_t)ne * n * n;  // the caller's block array (a checked build tests writes against it)
   for (int q = 0; q <= 8; ++q) m.elem_pstart[q] = q <= p ? 0 : ne;
   m.pb.b[0] = bx;

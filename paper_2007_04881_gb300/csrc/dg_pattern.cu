@@ -566,8 +566,9 @@ __global__ void uverts_kernel(const int* __restrict__ eptr, const int* __restric
 // Algorithmic work per launch group, the host's accounting (plan_mesh) in
 // kernels: every term is an integer or a half integer, so the double
 // atomics are exact and the sums do not depend on the order.  acc layout:
-// flops [kKinds][9], words [kKinds][9], executed [2][9] (kAccN values).
-constexpr int kAccW = kKinds * 9, kAccX = 2 * kKinds * 9, kAccN = 2 * kKinds * 9 + 18;
+// flops [kKinds][9], words [kKinds][9], executed [2][9], interface terms by
+// row and neighbour degree [2][9][9] (kAccN values).
+constexpr int kAccW = kKinds * 9, kAccX = 2 * kKinds * 9, kAccO = kAccX + 18, kAccN = kAccO + 162;
 
 __global__ void account_elem_kernel(int ne, int dim, bool adv, bool advb, const int* __restrict__ p,
                                     const int* __restrict__ nvq, const int* __restrict__ hf_ptr,
@@ -642,8 +643,8 @@ __global__ void account_iface_kernel(int ni, int dim, bool advb, const int* __re
       atomicAdd(&sacc[kAccW + 0 * 9 + p[e]], w);
       atomicAdd(&sacc[1 * 9 + p[e]], 2.0 * fma);
       atomicAdd(&sacc[kAccW + 1 * 9 + p[e]], w);
-      atomicAdd(&sacc[4 * 9 + p[e]], 2.0 * fma);
-      atomicAdd(&sacc[kAccW + 4 * 9 + p[e]], w);
+      atomicAdd(&sacc[kAccO + p[e] * 9 + p[k]], 2.0 * fma);
+      atomicAdd(&sacc[kAccO + 81 + p[e] * 9 + p[k]], w);
     }
   }
   __syncthreads();
@@ -946,6 +947,9 @@ int build_pattern_device(const dg_mesh_desc* d, const int* eptr, const int* eidx
       }
     for (int k = 0; k < 2; ++k)
       for (int q = 0; q < 9; ++q) P->mom_exec[k][q] = hacc[kAccX + k * 9 + q];
+    for (int k = 0; k < 2; ++k)
+      for (int q = 0; q < 9; ++q)
+        for (int r = 0; r < 9; ++r) P->offd[k][q][r] = hacc[kAccO + k * 81 + q * 9 + r];
     P->elem_pstart[0] = P->if_pstart[0] = 0;
     for (int q = 0; q < 8; ++q) {
       P->elem_pstart[q + 1] = P->elem_pstart[q] + hp[q];

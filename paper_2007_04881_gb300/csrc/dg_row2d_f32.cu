@@ -3,7 +3,9 @@
 
 namespace dg {
 
-int launch_row2d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, const LaunchOpts& lo, Tracer* tr) {
+int launch_row2d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm_count, const LaunchOpts& lo0, Tracer* tr) {
+  LaunchOpts lo = lo0;
+  iface_setup<2, float>(m, mode, lo, tr);
   int n = 0;
   n += launch_row_p<2, 1, float>(m, mode, vals, rhs, sm_count, lo, tr);
   n += launch_row_p<2, 2, float>(m, mode, vals, rhs, sm_count, lo, tr);
@@ -11,6 +13,7 @@ int launch_row2d_f32(const DevMesh& m, int mode, float* vals, float* rhs, int sm
   n += launch_row_p<2, 4, float>(m, mode, vals, rhs, sm_count, lo, tr);
   n += launch_row_p<2, 5, float>(m, mode, vals, rhs, sm_count, lo, tr);
   n += launch_row_p<2, 6, float>(m, mode, vals, rhs, sm_count, lo, tr);
+  n += launch_iface_all<2, float>(m, vals, sm_count, lo, tr);
   return n;
 }
 
