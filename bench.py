@@ -1026,8 +1026,8 @@ def run_slab(args):
 # units by name prefix, and the headers they include)
 TRAFFIC_GROUPS = {
     "row_pass": {"units": ("dg_row",), "headers": ("dg_device.cuh", "dg_moment.cuh", "dg_launch.cuh",
-                                                   "dg_internal.h"),
-                 "match": ("row_lane_kernel", "row_kernel", "vol_moment_kernel")},
+                                                   "dg_iface.cuh", "dg_internal.h"),
+                 "match": ("row_lane_kernel", "row_kernel", "vol_moment_kernel", "iface_kernel")},
     "slab_matrix": {"units": ("dg_slab",), "headers": ("dg_slab.cuh", "dg_internal.h"),
                     "match": ("slab_matrix_kernel",)},
 }
