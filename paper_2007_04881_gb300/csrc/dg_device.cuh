@@ -489,8 +489,8 @@ __device__ __forceinline__ void zero_groups(T* __restrict__ dst, int words) {
 }
 
 // --------------------------------------------------------------------------
-// lane kernel: one thread assembles the whole block row of one element
-// (degree 1: the n x n block fits in registers, no staging needed)
+// lane kernel: a few lanes assemble the whole block row of one element, each
+// holding the whole n x n block in registers (low degrees: no staging needed)
 // --------------------------------------------------------------------------
 
 template <int D, int P, int PK, typename T>
@@ -552,11 +552,36 @@ __device__ __forceinline__ void lane_offdiag(const DevMesh& m, const ElemPar<D, 
     for (int j = 0; j < NK; ++j) out[i * NK + j] = RR * ctab[i] * ctab[j] * acc[i][j];
 }
 
+// lanes per element of the lane kernel
 template <int D, int P, typename T>
+__host__ __device__ constexpr int lane_lpe() {
+  return 8;
+}
+// CTAs of kWarps warps that cover `count` elements of the lane kernel: one
+// warp per part (1: the diagonal part alone, 2: both) per 32 / lane_lpe
+// elements
+template <int D, int P, typename T>
+__host__ __device__ constexpr int lane_blocks(int count, int parts) {
+  return ((count + 32 / lane_lpe<D, P, T>() - 1) / (32 / lane_lpe<D, P, T>()) * parts + kWarps - 1) / kWarps;
+}
+
+// Each element is taken by L = lane_lpe lanes of two warps: part 0 the
+// diagonal block and the load vector, part 1 the off-diagonal blocks (they
+// write disjoint blocks).  In part 0 the element's lanes take every L-th
+// volume point and every L-th own-face point, each into a whole n x n
+// register block, and a butterfly over the L lanes sums them (a fixed order:
+// an element's result does not depend on which mesh or launch holds it); in
+// part 1 each lane takes every L-th block of the row, less the blocks of
+// interfaces whose larger degree has its bit in the mode (kModeMaskShift:
+// the interface kernel writes those).  PARTS = 1: part 0 alone (kModeDiagOnly),
+// compiled without part 1, whose neighbour blocks need far more registers.
+template <int D, int P, typename T, int PARTS>
 __global__ void __launch_bounds__(kWarps * 32)
     row_lane_kernel(const DevMesh m, int mode, T* __restrict__ vals, T* __restrict__ rhs) {
   constexpr int N = nbasis(D, P), QT = ipow_c(P + 2, D), SV = sub_vals(D);
   constexpr int NMAXC = nbasis(D, D == 2 ? kPMax2 : kPMax3);
+  constexpr int L = lane_lpe<D, P, T>(), EW = 32 / L;
+  static_assert(32 % L == 0, "lanes per element divide the warp");
   __shared__ T rule[QT * (D + 1)];
   __shared__ T ctab[NMAXC];
   const T* vrule = pick<T>(m.rt.vol64, m.rt.vol32) + (size_t)m.rt.vol_off[P] * (D + 1);
@@ -570,22 +595,23 @@ __global__ void __launch_bounds__(kWarps * 32)
   const bool mat_vol = mode & kModeVol, mat_face = mode & kModeFace, do_rhs = mode & kModeRhs;
   const bool accum = mode & kModeAccum;
   const int base = m.elem_pstart[P], count = m.elem_pstart[P + 1] - base;
-  // two threads per element, in different warps (each warp takes one part of
-  // 32 elements): part 0 the diagonal block and the load vector (volume and
-  // own faces), part 1 the off-diagonal blocks of the row; they write
-  // disjoint blocks
-  const int span = (count + 31) / 32 * 64;
-  for (int w2 = blockIdx.x * blockDim.x + threadIdx.x; w2 < span; w2 += gridDim.x * blockDim.x) {
-    const int part = (w2 >> 5) & 1, w = (w2 >> 6) * 32 + (w2 & 31);
-    if (w >= count) continue;
-    const int e = m.elem_perm[base + w];
+  const int lane = threadIdx.x & 31, lig = lane % L;
+  // warp-uniform loop: warp gw takes part gw % parts of elements
+  // (gw / parts) * EW ..
+  static_assert(PARTS == 1 || PARTS == 2, "one or two parts");
+  const int nw = (count + EW - 1) / EW * PARTS;
+  const int wstride = (gridDim.x * blockDim.x) >> 5;
+  for (int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; gw < nw; gw += wstride) {
+    const int part = gw % PARTS, slot = (gw / PARTS) * EW + lane / L;
+    const bool active = slot < count;
+    const int e = active ? m.elem_perm[base + slot] : 0;
     ElemPar<D, T> q;
-    load_elem_par<D, T>(m, e, q);
-    if (part == 1) {
-      if (mat_face) {
-        for (int bk = m.row_ptr[e]; bk < m.row_ptr[e + 1]; ++bk) {
+    if (active) load_elem_par<D, T>(m, e, q);
+    if (PARTS == 2 && part == 1) {
+      if (mat_face && active) {
+        for (int bk = m.row_ptr[e] + lig; bk < m.row_ptr[e + 1]; bk += L) {
           const int4 br = m.blk_rec[bk];  // neighbour, first half face, faces, neighbour degree
-          if (br.x < 0) continue;
+          if (br.x < 0 || ((mode >> (kModeMaskShift + (P > br.w ? P : br.w))) & 1)) continue;
           const int64_t off = m.blk_off[bk];
           switch (br.w) {
             case 1: lane_offdiag<D, P, 1, T>(m, q, br, off, HFR, FR, ctab, vals); break;
@@ -607,165 +633,153 @@ __global__ void __launch_bounds__(kWarps * 32)
 #pragma unroll
       for (int j = 0; j < N; ++j) acc[i][j] = T(0);
     }
-    const bool learned = m.lq_ok && m.lq_ok[e];
-    if ((mat_vol || do_rhs) && learned) {
-      const T* LQ = pick<T>(m.lq64, m.lq32) + (size_t)e * 84;
-      for (int r = 0; r < 28; ++r) {
-        T xi[D];
-        xi[0] = LQ[r];
-        xi[1] = LQ[28 + r];
-        const T W = LQ[56 + r];
-        T Phi[N], Dd[D][N];
-        basis_eval<D, P, T>(xi, Phi, Dd);
-        if (mat_vol) {
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            T adv = q.c * Phi[j];
-            T vd[D];
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-              adv += q.bp[d] * Dd[d][j];
-              vd[d] = W * q.ap[d] * Dd[d][j];
-            }
-            adv *= W;
-#pragma unroll
-            for (int i = 0; i < N; ++i) {
-              T s = fma(Phi[i], adv, acc[i][j]);
-#pragma unroll
-              for (int d = 0; d < D; ++d) s = fma(Dd[d][i], vd[d], s);
-              acc[i][j] = s;
-            }
-          }
-        }
-        if (do_rhs) {
-          T x[D];
-#pragma unroll
-          for (int d = 0; d < D; ++d) x[d] = q.lo[d] + (xi[d] + T(1)) * T(0.5) * q.L[d];
-          const T fw = W * source_f<D, T>(m.pb, q.a, x);
-#pragma unroll
-          for (int i = 0; i < N; ++i) racc[i] = fma(Phi[i], fw, racc[i]);
-        }
-      }
-    }
-    if ((mat_vol || do_rhs) && !learned) {
-      for (int sub = m.eptr[e]; sub < m.eptr[e + 1]; ++sub) {
+    const bool learned = active && m.lq_ok && m.lq_ok[e];
+    const int nvol = !active || !(mat_vol || do_rhs) ? 0 : learned ? 28 : (m.eptr[e + 1] - m.eptr[e]) * QT;
+    for (int qv = lig; qv < nvol; qv += L) {
+      T xi[D], W;
+      if (learned) {
+        const T* LQ = pick<T>(m.lq64, m.lq32) + (size_t)e * 84;
+        xi[0] = LQ[qv];
+        xi[1 % D] = LQ[28 + qv];
+        W = LQ[56 + qv];
+      } else {
+        const int t = qv / QT, r = qv - t * QT;
+        const int sub = m.eptr[e] + t;
         T sv[SV];
 #pragma unroll
         for (int k = 0; k < SV; ++k) sv[k] = SG[(size_t)k * m.nsub + sub];
-        for (int r = 0; r < QT; ++r) {
-          const T* rr = rule + r * (D + 1);
-          T xi[D];
+        const T* rr = rule + r * (D + 1);
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+          T v = sv[d] + rr[0] * sv[D + d] + rr[1] * sv[2 * D + d];
+          if constexpr (D == 3) v += rr[2] * sv[3 * D + d];
+          xi[d] = v;
+        }
+        W = rr[D] * sv[SV - 1];
+      }
+      T Phi[N], Dd[D][N];
+      basis_eval<D, P, T>(xi, Phi, Dd);
+      if (mat_vol) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          T adv = q.c * Phi[j];
+          T vd[D];
 #pragma unroll
           for (int d = 0; d < D; ++d) {
-            T v = sv[d] + rr[0] * sv[D + d] + rr[1] * sv[2 * D + d];
-            if constexpr (D == 3) v += rr[2] * sv[3 * D + d];
-            xi[d] = v;
+            adv += q.bp[d] * Dd[d][j];
+            vd[d] = W * q.ap[d] * Dd[d][j];
           }
-          const T W = rr[D] * sv[SV - 1];
-          T Phi[N], Dd[D][N];
-          basis_eval<D, P, T>(xi, Phi, Dd);
-          if (mat_vol) {
-#pragma unroll
-            for (int j = 0; j < N; ++j) {
-              T adv = q.c * Phi[j];
-              T vd[D];
-#pragma unroll
-              for (int d = 0; d < D; ++d) {
-                adv += q.bp[d] * Dd[d][j];
-                vd[d] = W * q.ap[d] * Dd[d][j];
-              }
-              adv *= W;
-#pragma unroll
-              for (int i = 0; i < N; ++i) {
-                T s = fma(Phi[i], adv, acc[i][j]);
-#pragma unroll
-                for (int d = 0; d < D; ++d) s = fma(Dd[d][i], vd[d], s);
-                acc[i][j] = s;
-              }
-            }
-          }
-          if (do_rhs) {
-            T x[D];
-#pragma unroll
-            for (int d = 0; d < D; ++d) x[d] = q.lo[d] + (xi[d] + T(1)) * T(0.5) * q.L[d];
-            const T fw = W * source_f<D, T>(m.pb, q.a, x);
-#pragma unroll
-            for (int i = 0; i < N; ++i) racc[i] = fma(Phi[i], fw, racc[i]);
-          }
-        }
-      }
-    }
-    if (mat_face || do_rhs) {
-      for (int hf = m.hf_ptr[e]; hf < m.hf_ptr[e + 1]; ++hf) {
-        // the half face's record: own side, then J, sigma, b.n, nq (signed)
-        const T* rec = HFR + (size_t)hf * RS;
-        const T J = rec[2 * FV], sig = rec[2 * FV + 1], bn = rec[2 * FV + 2], nqs = rec[2 * FV + 3];
-        const bool bnd = nqs < T(0);
-        const bool neu = sig < T(0);  // Neumann face
-        const int nq = (int)(bnd ? -nqs : nqs);
-        const int qf = D == 2 ? nq : nq * nq;
-        if (!mat_face && !bnd) continue;
-        if (neu && !do_rhs) continue;
-        const T kap = neu ? T(0) : bnd ? T(1) : T(0.5);
-        const T sgf = neu ? T(0) : sig;
-        const T upw = bn < T(0) ? bn : T(0);
-        for (int lq = 0; lq < qf; ++lq) {
-          const T* fr = FR + (size_t)(m.rt.face_off[nq] + lq) * (D == 2 ? 2 : 3);
-          T xi[D], np[D];
-          hf_point<D, T>(rec, fr, xi, np);
-          const T W = fr[D == 2 ? 1 : 2] * J;
-          T Phi[N], Dd[D][N], dn[N];
-          basis_eval<D, P, T>(xi, Phi, Dd);
+          adv *= W;
 #pragma unroll
           for (int i = 0; i < N; ++i) {
-            T v = T(0);
+            T s = fma(Phi[i], adv, acc[i][j]);
 #pragma unroll
-            for (int d = 0; d < D; ++d) v += np[d] * Dd[d][i];
-            dn[i] = v;
-          }
-          if (mat_face && !neu) {
-#pragma unroll
-            for (int j = 0; j < N; ++j) {
-              const T v0 = W * (-kap * q.a * dn[j] + (sgf - upw) * Phi[j]);
-              const T v1 = W * (-kap * q.a * Phi[j]);
-#pragma unroll
-              for (int i = 0; i < N; ++i) acc[i][j] = fma(Phi[i], v0, fma(dn[i], v1, acc[i][j]));
-            }
-          }
-          if (do_rhs && bnd) {
-            T x[D], gu[3], lap;
-#pragma unroll
-            for (int d = 0; d < D; ++d) x[d] = q.lo[d] + (xi[d] + T(1)) * T(0.5) * q.L[d];
-            const T gd = exact_u<D, T>(m.pb, x, gu, &lap);
-            T r0 = W * (sgf - upw) * gd, r1 = -W * q.a * gd;
-            if (neu) {
-              // g_N = a grad u . n_k, n_k = n' L / 2
-              T gn = T(0);
-#pragma unroll
-              for (int d = 0; d < D; ++d) gn += gu[d] * np[d] * q.L[d];
-              r0 = W * T(0.5) * q.a * gn;
-              r1 = T(0);
-            }
-#pragma unroll
-            for (int i = 0; i < N; ++i) racc[i] = fma(Phi[i], r0, fma(dn[i], r1, racc[i]));
+            for (int d = 0; d < D; ++d) s = fma(Dd[d][i], vd[d], s);
+            acc[i][j] = s;
           }
         }
       }
+      if (do_rhs) {
+        T x[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) x[d] = q.lo[d] + (xi[d] + T(1)) * T(0.5) * q.L[d];
+        const T fw = W * source_f<D, T>(m.pb, q.a, x);
+#pragma unroll
+        for (int i = 0; i < N; ++i) racc[i] = fma(Phi[i], fw, racc[i]);
+      }
     }
+    // own-face points, numbered over the element's half faces (hf_qoff: the
+    // first point of each, from 0 per element)
+    const int h0 = active ? m.hf_ptr[e] : 0;
+    const int nhf = active ? m.hf_ptr[e + 1] - h0 : 0;
+    const int nfp = active && (mat_face || do_rhs) ? m.e_nqf[e] : 0;
+    for (int qv = lig; qv < nfp; qv += L) {
+      int hf = h0, hi = h0 + nhf - 1;
+      while (hf < hi) {
+        const int mid = (hf + hi + 1) >> 1;
+        if (m.hf_qoff[mid] <= qv)
+          hf = mid;
+        else
+          hi = mid - 1;
+      }
+      // the half face's record: own side, then J, sigma, b.n, nq (signed)
+      const T* rec = HFR + (size_t)hf * RS;
+      const T J = rec[2 * FV], sig = rec[2 * FV + 1], bn = rec[2 * FV + 2], nqs = rec[2 * FV + 3];
+      const bool bnd = nqs < T(0);
+      const bool neu = sig < T(0);  // Neumann face
+      if (!mat_face && !bnd) continue;
+      if (neu && !do_rhs) continue;
+      const int nq = (int)(bnd ? -nqs : nqs);
+      const T kap = neu ? T(0) : bnd ? T(1) : T(0.5);
+      const T sgf = neu ? T(0) : sig;
+      const T upw = bn < T(0) ? bn : T(0);
+      const T* fr = FR + (size_t)(m.rt.face_off[nq] + qv - m.hf_qoff[hf]) * (D == 2 ? 2 : 3);
+      T xi[D], np[D];
+      hf_point<D, T>(rec, fr, xi, np);
+      const T W = fr[D == 2 ? 1 : 2] * J;
+      T Phi[N], Dd[D][N], dn[N];
+      basis_eval<D, P, T>(xi, Phi, Dd);
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        T v = T(0);
+#pragma unroll
+        for (int d = 0; d < D; ++d) v += np[d] * Dd[d][i];
+        dn[i] = v;
+      }
+      if (mat_face && !neu) {
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const T v0 = W * (-kap * q.a * dn[j] + (sgf - upw) * Phi[j]);
+          const T v1 = W * (-kap * q.a * Phi[j]);
+#pragma unroll
+          for (int i = 0; i < N; ++i) acc[i][j] = fma(Phi[i], v0, fma(dn[i], v1, acc[i][j]));
+        }
+      }
+      if (do_rhs && bnd) {
+        T x[D], gu[3], lap;
+#pragma unroll
+        for (int d = 0; d < D; ++d) x[d] = q.lo[d] + (xi[d] + T(1)) * T(0.5) * q.L[d];
+        const T gd = exact_u<D, T>(m.pb, x, gu, &lap);
+        T r0 = W * (sgf - upw) * gd, r1 = -W * q.a * gd;
+        if (neu) {
+          // g_N = a grad u . n_k, n_k = n' L / 2
+          T gn = T(0);
+#pragma unroll
+          for (int d = 0; d < D; ++d) gn += gu[d] * np[d] * q.L[d];
+          r0 = W * T(0.5) * q.a * gn;
+          r1 = T(0);
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) racc[i] = fma(Phi[i], r0, fma(dn[i], r1, racc[i]));
+      }
+    }
+    // butterfly over the element's L lanes (every lane of the warp takes part)
+#pragma unroll
+    for (int off = L / 2; off > 0; off >>= 1) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        racc[i] += __shfl_xor_sync(0xffffffffu, racc[i], off);
+#pragma unroll
+        for (int j = 0; j < N; ++j) acc[i][j] += __shfl_xor_sync(0xffffffffu, acc[i][j], off);
+      }
+    }
+    if (!active) continue;
     if ((mat_vol || mat_face) && dg_in_range(m.status, m.blk_off[m.diag_blk[e]], (int64_t)N * N, m.nvals)) {
       T* out = vals + m.blk_off[m.diag_blk[e]];
       const T RR = q.R * q.R;
 #pragma unroll
       for (int i = 0; i < N; ++i)
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-          const T v = RR * ctab[i] * ctab[j] * acc[i][j];
-          out[i * N + j] = accum ? out[i * N + j] + v : v;
-        }
+        for (int j = 0; j < N; ++j)
+          if ((i * N + j) % L == lig) {
+            const T v = RR * ctab[i] * ctab[j] * acc[i][j];
+            out[i * N + j] = accum ? out[i * N + j] + v : v;
+          }
     }
     if (do_rhs && dg_in_range(m.status, m.dof_off[e], N, m.ndofs)) {
 #pragma unroll
-      for (int i = 0; i < N; ++i) rhs[m.dof_off[e] + i] = q.R * ctab[i] * racc[i];
+      for (int i = 0; i < N; ++i)
+        if (i % L == lig) rhs[m.dof_off[e] + i] = q.R * ctab[i] * racc[i];
     }
   }
 }

@@ -270,6 +270,17 @@ void Tracer::begin(const char* name, int kind, int p, size_t tsize, cudaStream_t
   snprintf(r.name, sizeof r.name, "%s", name);
   r.flops = ((kind < kKinds && flops) ? flops[kind * 9 + p] : 0.0) * scale;
   r.bytes = ((kind < kKinds && words) ? words[kind * 9 + p] * (double)tsize : 0.0) * scale;
+  if (kind == 6) {
+    // the lane kernel's rows less the blocks the interface kernel writes
+    double fl = flops ? flops[p] : 0.0, wd = words ? words[p] : 0.0;
+    for (int q = 1; q <= 8 && offd; ++q)
+      if ((imask >> std::max(p, q)) & 1) {
+        fl -= offd[p * 9 + q];
+        wd -= offd[81 + p * 9 + q];
+      }
+    r.flops = fl * scale;
+    r.bytes = wd * (double)tsize * scale;
+  }
   if ((kind == 4 || kind == 5) && offd) {
     // kind 4: blocks of degree-p rows whose interface's larger degree is not
     // in imask; kind 5: interfaces of larger degree p, the blocks of their

@@ -199,9 +199,13 @@ enum : int {
   kModeMomFace = 64,
   kModeOffDiag = 128,  // row kernel: the off-diagonal blocks only (diagonal block and load vector untouched)
 };
-// with kModeOffDiag, bits kModeMaskShift + q: neighbours of degree q are
-// skipped (their interfaces are assembled by the interface kernel)
+// with kModeOffDiag (row kernel) and in the lane kernel, bits
+// kModeMaskShift + q: the interfaces whose larger degree is q are assembled
+// by the interface kernel (the row skips their blocks)
 constexpr int kModeMaskShift = 8;
+// lane kernel: the diagonal block and the load vector only (every
+// off-diagonal block of the rows comes from the interface kernel)
+constexpr int kModeDiagOnly = 1 << 20;
 
 // Optional per-launch timing: CUDA events recorded on the launch stream
 // around each kernel, with the kernel's label and its algorithmic flop and
@@ -228,7 +232,9 @@ struct Tracer {
   // sizeof(T).  Kinds 4 (the row kernel's off-diagonal launch: the blocks of
   // degree-p rows whose neighbour degree is not in imask) and 5 (the
   // interface launch of larger degree p: interfaces with both degrees in
-  // imask) take their counts from offd.
+  // imask) take their counts from offd, and so does kind 6 (the lane kernel
+  // of degree p with the interface kernel on: kind 0 less the blocks of
+  // interfaces whose larger degree is in imask).
   const double* flops = nullptr;   // [kKinds][9]
   const double* words = nullptr;   // [kKinds][9]
   const double* xflops = nullptr;  // [2][9]: flops the kind-2 and kind-3 launches execute

@@ -33,13 +33,27 @@ int launch_row_tile(const DevMesh& m, int mode, T* vals, T* rhs, int sm_count, c
   if (tr && tr->on) {
     char name[48];
     snprintf(name, sizeof name, "row%dd_p%d_%s", D, P, sizeof(T) == 8 ? "f64" : "f32");
-    tr->begin(name, kind, P, sizeof(T), st);
+    const bool lane_if = TileCfg<D, P, T, V>::TPE == 1 && ((lo.imask >> P) & 1);
+    tr->begin(name, lane_if ? 6 : kind, P, sizeof(T), st);
   }
   if constexpr (TileCfg<D, P, T, V>::TPE == 1) {
-    // one element per thread, no staging
-    auto k = row_lane_kernel<D, P, T>;
-    const int grid = resident_grid(k, 0, sm_count, ((count + 31) / 32 * 64 + kWarps * 32 - 1) / (kWarps * 32), lo.occ_cap);
-    k<<<grid, kWarps * 32, 0, st>>>(m, mode, vals, rhs);
+    // a few lanes per element, no staging; the blocks of interfaces whose
+    // larger degree is in imask come from the interface launch, and when
+    // that leaves none (no neighbour degree above P outside imask) only the
+    // diagonal part is launched
+    if ((lo.imask >> P) & 1) {
+      mode |= lo.imask << kModeMaskShift;
+      if (!(lo.present & ~lo.imask & ~((2 << P) - 1))) mode |= kModeDiagOnly;
+    }
+    if (mode & kModeDiagOnly) {
+      auto k = row_lane_kernel<D, P, T, 1>;
+      const int grid = resident_grid(k, 0, sm_count, lane_blocks<D, P, T>(count, 1), lo.occ_cap);
+      k<<<grid, kWarps * 32, 0, st>>>(m, mode, vals, rhs);
+    } else {
+      auto k = row_lane_kernel<D, P, T, 2>;
+      const int grid = resident_grid(k, 0, sm_count, lane_blocks<D, P, T>(count, 2), lo.occ_cap);
+      k<<<grid, kWarps * 32, 0, st>>>(m, mode, vals, rhs);
+    }
   } else {
     using SM = RowSmem<D, P, T, V>;
     constexpr int G = TileCfg<D, P, T, V>::G;
@@ -154,6 +168,12 @@ template <int D, int P, typename T>
 __host__ __device__ constexpr bool offdiag_rows() {
   return TileCfg<D, P, T>::TPE != 1 && moment_volume_ok<D, P, T>();
 }
+// whether the interface kernel serves degree P (FP32): the rows above, and
+// the lane kernel's degrees, whose diagonal part stays in the lane kernel
+template <int D, int P, typename T>
+__host__ __device__ constexpr bool iface_rows() {
+  return sizeof(T) == 4 && (offdiag_rows<D, P, T>() || TileCfg<D, P, T>::TPE == 1);
+}
 
 // lo.present and lo.imask of one pass (interfaces by the interface kernel:
 // FP32, moment path, face terms requested)
@@ -162,12 +182,12 @@ inline void iface_setup(const DevMesh& m, int mode, LaunchOpts& lo, Tracer* tr) 
   lo.present = m.pmask;  // the neighbours' degrees count: ghost elements of a partition
   lo.imask = 0;
   if (sizeof(T) == 4 && lo.iface && lo.vol_moments && m.rt.lin32 && m.rt.lin64 && (mode & kModeFace)) {
-    if (offdiag_rows<D, 1, T>()) lo.imask |= 1 << 1;
-    if (offdiag_rows<D, 2, T>()) lo.imask |= 1 << 2;
-    if (offdiag_rows<D, 3, T>()) lo.imask |= 1 << 3;
-    if (offdiag_rows<D, 4, T>()) lo.imask |= 1 << 4;
-    if (D == 2 && offdiag_rows<D, 5, T>()) lo.imask |= 1 << 5;
-    if (D == 2 && offdiag_rows<D, 6, T>()) lo.imask |= 1 << 6;
+    if (iface_rows<D, 1, T>()) lo.imask |= 1 << 1;
+    if (iface_rows<D, 2, T>()) lo.imask |= 1 << 2;
+    if (iface_rows<D, 3, T>()) lo.imask |= 1 << 3;
+    if (iface_rows<D, 4, T>()) lo.imask |= 1 << 4;
+    if (D == 2 && iface_rows<D, 5, T>()) lo.imask |= 1 << 5;
+    if (D == 2 && iface_rows<D, 6, T>()) lo.imask |= 1 << 6;
   }
   if (tr) tr->imask = lo.imask;
 }
@@ -176,7 +196,7 @@ inline void iface_setup(const DevMesh& m, int mode, LaunchOpts& lo, Tracer* tr) 
 // if_pstart[P + 1]) in lo.split[P] contiguous parts on the group's streams.
 template <int D, int P, typename T>
 inline int launch_iface_p(const DevMesh& m, T* vals, int sm_count, const LaunchOpts& lo, Tracer* tr) {
-  if constexpr (!offdiag_rows<D, P, T>() || sizeof(T) != 4) {
+  if constexpr (!iface_rows<D, P, T>()) {
     return 0;
   } else {
     if (!((lo.imask >> P) & 1)) return 0;

@@ -768,8 +768,8 @@ inline int launch_row_mma_p(const DevMesh& m, int mode, float* vals, float* rhs,
   }
   if constexpr (P == 1) {
     // degree 1 (n = 3 or 4) is too small for 16-row tiles: the FP32 lane kernel
-    auto k = row_lane_kernel<D, P, float>;
-    const int grid = resident_grid(k, 0, sm_count, ((count + 31) / 32 * 64 + kWarps * 32 - 1) / (kWarps * 32), lo.occ_cap);
+    auto k = row_lane_kernel<D, P, float, 2>;
+    const int grid = resident_grid(k, 0, sm_count, lane_blocks<D, P, float>(count, 2), lo.occ_cap);
     k<<<grid, kWarps * 32, 0, st>>>(m, mode, vals, rhs);
   } else {
     using Cfg = MmaCfg<D, P, K>;

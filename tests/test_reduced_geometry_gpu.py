@@ -9,7 +9,7 @@ and these tests hold them to that:
 - accuracy parity: on mixed-degree 2D and 3D meshes and a batch of meshes
   the reduced pass is as close to the FP64 form as the FP32 pass on the FP64
   geometry's records (relative Frobenius of the matrix and the load vector,
-  within 1.25x + 2e-8);
+  within 1.25x + 2e-8; a single element within 1.25x + 2 FP32 epsilons);
 - element by element: no element's load vector or diagonal block is more
   than 2x + 1e-6 (block max-norm relative) further from the FP64 form than
   the FP32 pass on FP64 records.  With a strong penalty (a = 100, p = 6) a
@@ -85,12 +85,17 @@ def diag_offsets(m):
     return np.array(starts), np.array(ends)
 
 
-def check_against_fp64_records(ctx, m):
+def check_against_fp64_records(ctx, m, floor=2e-8):
+    """floor: the additive slack of the accuracy-parity check.  On a mesh of
+    many elements the relative Frobenius errors average the rounding of many
+    blocks, and 2e-8 holds; a single element's error is one sample of FP32
+    rounding (about eps = 6e-8 relative), so two such samples, on two sets of
+    records, differ by a few eps whatever the records."""
     v64, r64 = assemble(ctx, m, FP64, False)
     v_old, r_old = assemble(ctx, m, FP32, False)  # FP32 pass on the FP64 geometry's records
     v_new, r_new = assemble(ctx, m, FP32, True)  # reduced-precision geometry
     for got, ref, old in ((v_new, v64, v_old), (r_new, r64, r_old)):
-        assert rel(got, ref) <= 1.25 * rel(old, ref) + 2e-8, (rel(got, ref), rel(old, ref))
+        assert rel(got, ref) <= 1.25 * rel(old, ref) + floor, (rel(got, ref), rel(old, ref))
     dof = m.dg_bsr_pattern()[3]
     e_new, e_old = seg_rel_max(r_new, r64, dof), seg_rel_max(r_old, r64, dof)
     bad = np.nonzero(e_new > 2 * e_old + 1e-6)[0]
@@ -122,7 +127,7 @@ def test_long_loop(ctx, p):
     keeps in registers, so its runtime-length branch runs"""
     wl = polygon_workload(20, p)
     m = dg.Mesh(ctx, wl.mesh, wl.p, wl.a, dg_problem(wl))
-    check_against_fp64_records(ctx, m)
+    check_against_fp64_records(ctx, m, floor=2 * float(np.finfo(np.float32).eps))
 
 
 def test_small3d(ctx):
