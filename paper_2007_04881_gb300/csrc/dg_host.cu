@@ -1222,6 +1222,16 @@ static int alloc_records(dg_mesh* m, int dim, int ne, int nv, int nsub, int nf, 
   alloc_d(&dm.fsc64, (size_t)3 * nf);
   alloc_d(&dm.hfr64, (size_t)hf_rec_vals(dim) * nhf);
   alloc_f(&dm.hfr32, (size_t)hf_rec_vals(dim) * nhf);
+  // the interface records (the topology and degrees are in place on both
+  // upload paths by now)
+  dm.if_rec = nullptr;
+  if (rc == DG_OK && dm.ni > 0) {
+    int4* rec = nullptr;
+    if (B.alloc(&rec, (size_t)2 * dm.ni) != cudaSuccess) return fail(DG_ERR_OOM, "device allocation failed");
+    launch_iface_recs(dm, rec, m->ctx->stream);
+    if (cudaGetLastError() != cudaSuccess) return fail(DG_ERR_CUDA, "interface records: launch failed");
+    dm.if_rec = rec;
+  }
   return rc;
 }
 

@@ -95,23 +95,25 @@ __device__ __forceinline__ void iface_tile(const DevMesh& m, int imask, int i0, 
     T* fp = FP + lane * NF;
     int npts = 0;
     if (lane < gcount) {
-      const int i = m.if_perm[i0 + tile * G + lane];
-      const int e0 = m.if_e0[i], e1 = m.if_e1[i];
-      const int p0 = m.p[e0], p1 = m.p[e1];
+      // the interface's record (if_rec, in if_perm order): its elements, the
+      // first half face on e0's side, its faces, both slots, both degrees
+      const int k = i0 + tile * G + lane;
+      const int4 r0 = m.if_rec[2 * k], r1 = m.if_rec[2 * k + 1];
+      const int e0 = r0.x, e1 = r0.y;
+      const int p0 = r1.z & 255, p1 = r1.z >> 8;
       // a block of the interface is written here when its row is owned and
       // its row's degree is in imask (slot -1: not owned)
-      const int s01 = (imask >> p0) & 1 ? m.if_slot01[i] : -1, s10 = (imask >> p1) & 1 ? m.if_slot10[i] : -1;
+      const int s01 = (imask >> p0) & 1 ? r1.x : -1, s10 = (imask >> p1) & 1 ? r1.y : -1;
       if (s01 >= 0 || s10 >= 0) {
         // the interface's faces are consecutive in e0's half-face list
-        const int f0 = m.if_fptr[i];
         ip[kIfA] = e0;
         ip[kIfB] = e1;
         ip[kIfBkAB] = s01;
         ip[kIfBkBA] = s10;
-        ip[kIfHf0] = m.f_hf[f0];
+        ip[kIfHf0] = r0.z;
         ip[kIfPA] = p0;
         ip[kIfPB] = p1;
-        npts = (m.if_fptr[i + 1] - f0) * qf;
+        npts = r0.w * qf;
         fp[kIfAA] = T(m.a[e0]);
         fp[kIfAB] = T(m.a[e1]);
         fp[kIfRA] = EG[(size_t)(3 * D) * m.ne + e0];

@@ -153,6 +153,10 @@ struct DevMesh {
   const int* if_fptr;  // [ni+1] faces of interface i (consecutive in face order)
   const int* if_slot01;
   const int* if_slot10;
+  // per interface position k of if_perm, two int4: {e0, e1, e0's half face of
+  // the first face, faces}, {slot01, slot10, p[e0] | p[e1] << 8, 0}; the
+  // interface kernel's parameters in one coalesced load (built at upload)
+  const int4* if_rec;
   // BSR
   const int* row_ptr;  // [ne+1]
   const int* col;      // [nnzb]
@@ -362,6 +366,8 @@ void lq_targets(int ne, const double* rule, const double* mmom, float* tgt, cuda
 namespace dg {
 int build_pattern_device(const dg_mesh_desc* d, const int* eptr, const int* eidx, const int* p, const double* const* X,
                          const std::function<void*(size_t)>& alloc, cudaStream_t st, DevPattern* P, std::string* msg);
+// the interface records dm.if_rec[2 * ni] from the topology arrays (stream st)
+void launch_iface_recs(const DevMesh& dm, int4* rec, cudaStream_t st);
 
 // Host: collapsed reference rule on the d-simplex with n Gauss points per
 // direction, packed as [point][d+1] = (coordinates, weight); d = 1 gives the

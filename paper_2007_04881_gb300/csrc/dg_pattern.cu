@@ -994,4 +994,23 @@ int build_pattern_device(const dg_mesh_desc* d, const int* eptr, const int* eidx
   return fin(DG_OK);
 }
 
+namespace {
+__global__ void iface_rec_kernel(int ni, const int* __restrict__ if_perm, const int* __restrict__ if_e0,
+                                 const int* __restrict__ if_e1, const int* __restrict__ if_fptr,
+                                 const int* __restrict__ f_hf, const int* __restrict__ s01, const int* __restrict__ s10,
+                                 const int* __restrict__ p, int4* __restrict__ rec) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= ni) return;
+  const int i = if_perm[k], e0 = if_e0[i], e1 = if_e1[i], f0 = if_fptr[i];
+  rec[2 * k] = make_int4(e0, e1, f_hf[f0], if_fptr[i + 1] - f0);
+  rec[2 * k + 1] = make_int4(s01[i], s10[i], p[e0] | (p[e1] << 8), 0);
+}
+}  // namespace
+
+void launch_iface_recs(const DevMesh& dm, int4* rec, cudaStream_t st) {
+  if (dm.ni <= 0) return;
+  iface_rec_kernel<<<(dm.ni + 255) / 256, 256, 0, st>>>(dm.ni, dm.if_perm, dm.if_e0, dm.if_e1, dm.if_fptr, dm.f_hf,
+                                                       dm.if_slot01, dm.if_slot10, dm.p, rec);
+}
+
 }  // namespace dg
