@@ -243,6 +243,37 @@ int dg_assemble(dg_ctx *ctx, const dg_mesh *mesh, int prec, void *vals, void *rh
 int dg_assemble_host(dg_ctx *ctx, dg_mesh *mesh, int prec, const double *x, const double *y,
                      const double *z, const double *a, void *vals_host, void *rhs_host);
 
+/* Pipelined form of dg_assemble_host, for a sequence of independent
+ * assemblies on one mesh (new coefficients a or coordinates each time):
+ * the system of Eq. (2.4) and the load vector of Eq. (2.5), as
+ * dg_assemble_host computes them, with the copy back of one assembly
+ * running beside the next one's pass.
+ *
+ * dg_assemble_host_submit queues, on the context's stream, the copies of
+ * x, y, z, a (host; NULL keeps the device copy) and the pass into one of
+ * two library-owned device slots. On a copy stream of the mesh it then
+ * queues the copy of vals (host, nvals entries) and rhs (host, ndofs
+ * entries, or NULL) back. It returns without waiting, with *ticket (0, 1,
+ * 2, ...) naming the submission.
+ *
+ * dg_assemble_host_wait blocks until that submission's vals and rhs are in
+ * host memory.
+ *
+ * Ownership: the caller keeps x, y, z, a, vals_host and rhs_host valid and
+ * unchanged until the ticket's wait returns. Page-locked host buffers let
+ * the copies run asynchronously.
+ *
+ * Ordering: submissions run in order. A slot is reused two submissions
+ * later, after its copy back. A change of prec between submissions waits
+ * for every queued copy and reallocates the slots.
+ *
+ * Errors: DG_ERR_ARG for a null argument, or a ticket not submitted on this
+ * mesh; DG_ERR_OOM or DG_ERR_CUDA as in dg_assemble_host. */
+int dg_assemble_host_submit(dg_ctx *ctx, dg_mesh *mesh, int prec, const double *x, const double *y,
+                            const double *z, const double *a, void *vals_host, void *rhs_host,
+                            long long *ticket);
+int dg_assemble_host_wait(dg_ctx *ctx, dg_mesh *mesh, long long ticket);
+
 /* One pass of the whole hot path on device-resident inputs: the geometry
  * kernels in the pass's precision followed by the row kernels, in the
  * launch shape of dg_assemble_host.  Asynchronous.

@@ -393,6 +393,15 @@ struct dg_mesh {
   void* h_vals = nullptr;
   void* h_rhs = nullptr;
   int h_prec = -1;
+  // pipelined host entry points (dg_assemble_host_submit / _wait): two device
+  // slots for the system, a copy stream, and per slot the events of its pass
+  // (computed, on the context's stream) and of its copy back (done)
+  void* hp_vals[2] = {nullptr, nullptr};
+  void* hp_rhs[2] = {nullptr, nullptr};
+  int hp_prec = -1;
+  cudaStream_t hp_copy = nullptr;
+  cudaEvent_t hp_computed[2] = {nullptr, nullptr}, hp_done[2] = {nullptr, nullptr};
+  long long hp_next = 0;
   // launch shape per precision, recorded by dg_graph_create's autotuner and
   // used by the per-step entry points (dg_assemble_step, dg_assemble_host)
   // (kept with the context's volume-path setting it was tuned under)
@@ -446,6 +455,14 @@ struct dg_mesh {
   ~dg_mesh() {
     if (h_vals) cudaFree(h_vals);
     if (h_rhs) cudaFree(h_rhs);
+    if (hp_copy) cudaStreamSynchronize(hp_copy);
+    for (int i = 0; i < 2; ++i) {
+      if (hp_vals[i]) cudaFree(hp_vals[i]);
+      if (hp_rhs[i]) cudaFree(hp_rhs[i]);
+      if (hp_computed[i]) cudaEventDestroy(hp_computed[i]);
+      if (hp_done[i]) cudaEventDestroy(hp_done[i]);
+    }
+    if (hp_copy) cudaStreamDestroy(hp_copy);
     void* q[] = {lq_mom, lq_mmom, lq_rule, lq64, lq32, lq_resid, lq_elig, lq_ok, lq_okm, lq_feat, lq_out, pk_sync};
     for (void* x : q)
       if (x) cudaFree(x);
@@ -1880,6 +1897,84 @@ int dg_assemble_host(dg_ctx* ctx, dg_mesh* mesh, int prec, const double* x, cons
   if (rhs_host)
     DG_CUDA_TRY(cudaMemcpyAsync(rhs_host, mesh->h_rhs, es * mesh->info.ndofs, cudaMemcpyDeviceToHost, ctx->stream));
   DG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  return DG_OK;
+}
+
+int dg_assemble_host_submit(dg_ctx* ctx, dg_mesh* mesh, int prec, const double* x, const double* y,
+                            const double* z, const double* a, void* vals_host, void* rhs_host, long long* ticket) {
+  NvtxRange nv_(ctx, "dg_assemble_host_submit");
+  if (!ctx || !mesh || !vals_host || !ticket) return fail(DG_ERR_ARG, "dg_assemble_host_submit: null argument");
+  const int gmask = pass_geometry(&prec);
+  if (gmask < 0) return fail(DG_ERR_ARG, "unknown precision %d", prec);
+  const size_t es = prec == DG_PREC_FP64 ? 8 : 4;
+  if (!mesh->hp_copy) {
+    DG_CUDA_TRY(cudaStreamCreateWithFlags(&mesh->hp_copy, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      DG_CUDA_TRY(cudaEventCreateWithFlags(&mesh->hp_computed[i], cudaEventDisableTiming));
+      DG_CUDA_TRY(cudaEventCreateWithFlags(&mesh->hp_done[i], cudaEventDisableTiming));
+    }
+  }
+  if (mesh->hp_prec != prec) {
+    // a change of precision: every submitted copy ends before the slots go
+    DG_CUDA_TRY(cudaStreamSynchronize(mesh->hp_copy));
+    DG_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < 2; ++i) {
+      if (mesh->hp_vals[i]) cudaFree(mesh->hp_vals[i]);
+      if (mesh->hp_rhs[i]) cudaFree(mesh->hp_rhs[i]);
+      mesh->hp_vals[i] = mesh->hp_rhs[i] = nullptr;
+    }
+    mesh->hp_prec = -1;
+    for (int i = 0; i < 2; ++i) {
+      DG_CUDA_TRY(cudaMalloc(&mesh->hp_vals[i], es * std::max<int64_t>(mesh->info.nvals, 1)));
+      DG_CUDA_TRY(cudaMalloc(&mesh->hp_rhs[i], es * std::max<int64_t>(mesh->info.ndofs, 1)));
+    }
+    mesh->hp_prec = prec;
+  }
+  const int slot = (int)(mesh->hp_next & 1);
+  void* dv = mesh->hp_vals[slot];
+  void* dr = rhs_host ? mesh->hp_rhs[slot] : nullptr;
+  // the slot's previous copy back ends before this pass overwrites it (an
+  // event never recorded is already complete)
+  DG_CUDA_TRY(cudaStreamWaitEvent(ctx->stream, mesh->hp_done[slot], 0));
+  const int nv = mesh->dm.nv, ne = mesh->dm.ne;
+  const double* src[3] = {x, y, z};
+  for (int q = 0; q < mesh->dm.dim; ++q)
+    if (src[q]) DG_CUDA_TRY(cudaMemcpyAsync(mesh->X[q], src[q], sizeof(double) * nv, cudaMemcpyHostToDevice, ctx->stream));
+  if (a) DG_CUDA_TRY(cudaMemcpyAsync(mesh->a, a, sizeof(double) * ne, cudaMemcpyHostToDevice, ctx->stream));
+  trace_reset(ctx, mesh);
+  ctx->last_launches = launch_geometry(mesh->dm, ctx->stream, &ctx->tracer, gmask);
+  DG_CUDA_TRY(cudaGetLastError());
+  int occ = 0, path = -1;
+  bool conc = false;
+  const int* tiles = nullptr;
+  bool persist = false;
+  const int* splits = nullptr;
+  step_shape(ctx, mesh, prec, &occ, &conc, &path, &tiles, &persist, &splits);
+  const int mode = kModeVol | kModeFace | (rhs_host ? kModeRhs : 0);
+  int rc = persist ? issue_persist_step(ctx, mesh, prec, mode, dv, dr, path)
+                   : run_assembly(ctx, mesh, prec, mode, dv, dr, true, false, nullptr, true, occ, conc, path, nullptr,
+                                  tiles, splits);
+  if (rc != DG_OK) return rc;
+  // the copy back on the mesh's copy stream, after this pass: the next
+  // submit's pass runs beside it
+  DG_CUDA_TRY(cudaEventRecord(mesh->hp_computed[slot], ctx->stream));
+  DG_CUDA_TRY(cudaStreamWaitEvent(mesh->hp_copy, mesh->hp_computed[slot], 0));
+  DG_CUDA_TRY(cudaMemcpyAsync(vals_host, dv, es * mesh->info.nvals, cudaMemcpyDeviceToHost, mesh->hp_copy));
+  if (rhs_host)
+    DG_CUDA_TRY(cudaMemcpyAsync(rhs_host, dr, es * mesh->info.ndofs, cudaMemcpyDeviceToHost, mesh->hp_copy));
+  DG_CUDA_TRY(cudaEventRecord(mesh->hp_done[slot], mesh->hp_copy));
+  *ticket = mesh->hp_next++;
+  return DG_OK;
+}
+
+int dg_assemble_host_wait(dg_ctx* ctx, dg_mesh* mesh, long long ticket) {
+  NvtxRange nv_(ctx, "dg_assemble_host_wait");
+  if (!ctx || !mesh) return fail(DG_ERR_ARG, "dg_assemble_host_wait: null argument");
+  if (ticket < 0 || ticket >= mesh->hp_next)
+    return fail(DG_ERR_ARG, "dg_assemble_host_wait: ticket %lld was not submitted on this mesh", ticket);
+  // the slot's event holds this ticket's copy or a later one on the same copy
+  // stream; either way this ticket's copy has ended once it completes
+  DG_CUDA_TRY(cudaEventSynchronize(mesh->hp_done[ticket & 1]));
   return DG_OK;
 }
 

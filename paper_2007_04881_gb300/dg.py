@@ -123,6 +123,8 @@ def load() -> C.CDLL:
         getattr(lib, n).argtypes = [V, V, C.c_int, V]
     lib.dg_assemble.argtypes = [V, V, C.c_int, V, V]
     lib.dg_assemble_host.argtypes = [V, V, C.c_int, V, V, V, V, V, V]
+    lib.dg_assemble_host_submit.argtypes = [V, V, C.c_int, V, V, V, V, V, V, C.POINTER(C.c_longlong)]
+    lib.dg_assemble_host_wait.argtypes = [V, V, C.c_longlong]
     lib.dg_assemble_step.argtypes = [V, V, C.c_int, V, V]
     lib.dg_set_timing.argtypes = [V, C.c_int]
     lib.dg_kernel_stats.argtypes = [V, C.POINTER(dg_kernel_stat), C.c_int]
@@ -188,7 +190,8 @@ EXPORTS = (
     "dg_create", "dg_destroy", "dg_last_error", "dg_mesh_upload", "dg_mesh_free", "dg_mesh_check",
     "dg_mesh_update",
     "dg_geometry", "dg_bsr_layout", "dg_bsr_pattern", "dg_assemble_volume", "dg_assemble_faces",
-    "dg_assemble_rhs", "dg_assemble", "dg_assemble_host", "dg_sync", "dg_last_launch_count",
+    "dg_assemble_rhs", "dg_assemble", "dg_assemble_host", "dg_assemble_host_submit", "dg_assemble_host_wait",
+    "dg_sync", "dg_last_launch_count",
     "dg_assemble_step", "dg_set_timing", "dg_kernel_stats", "dg_batch_upload", "dg_batch_offsets",
     "dg_graph_create", "dg_graph_launch", "dg_graph_info", "dg_graph_free", "dg_volume_noalloc",
     "dg_quad_prepare", "dg_quad_fit", "dg_quad_targets", "dg_quad_buffers", "dg_quad_clear",
@@ -607,6 +610,17 @@ class Mesh:
     def dg_assemble_host(self, prec: int, vals_host, rhs_host=None, x=None, y=None, z=None, a=None):
         _check(load().dg_assemble_host(self.ctx._h, self._h, prec, _vp(x), _vp(y), _vp(z), _vp(a),
                                        _vp(vals_host), _vp(rhs_host)))
+
+    def dg_assemble_host_submit(self, prec: int, vals_host, rhs_host=None, x=None, y=None, z=None, a=None) -> int:
+        """Queue one host-buffer assembly; returns its ticket (the buffers stay
+        in use until dg_assemble_host_wait(ticket) returns)."""
+        t = C.c_longlong(-1)
+        _check(load().dg_assemble_host_submit(self.ctx._h, self._h, prec, _vp(x), _vp(y), _vp(z), _vp(a),
+                                              _vp(vals_host), _vp(rhs_host), C.byref(t)))
+        return t.value
+
+    def dg_assemble_host_wait(self, ticket: int):
+        _check(load().dg_assemble_host_wait(self.ctx._h, self._h, C.c_longlong(int(ticket))))
 
 
 def dg_volume_noalloc(stream, device: int, prec: int, p: int, x, y, elem_ptr, elem_idx, a, bx: float, by: float,
