@@ -2088,6 +2088,7 @@ static SlabPattern slab_pattern(const dg_mesh* mesh, int space) {
   sp.dof_off = m.dof_off;
   sp.sblk_off = mesh->slab_blk[space];
   sp.sdof_off = mesh->slab_dof[space];
+  sp.order = m.elem_perm;
   return sp;
 }
 

@@ -16,8 +16,8 @@ namespace {
 
 constexpr int kSlabThreads = 256;
 
-// one warp per element row, grid-strided; the time matrix and the dof
-// decode tables of degrees 1..pmax in shared memory
+// one warp per element row, grid-strided over the rows largest first; the
+// time matrix and the dof decode tables of degrees 1..pmax in shared memory
 template <typename T>
 __global__ void __launch_bounds__(kSlabThreads) slab_matrix_kernel(SlabPattern sp, SlabTimes<T> tt, int pmax,
                                                                    const T* __restrict__ B, const T* __restrict__ M,
@@ -28,8 +28,10 @@ __global__ void __launch_bounds__(kSlabThreads) slab_matrix_kernel(SlabPattern s
   slab_decode_tables(sp.dim, sp.space, pmax, dec, threadIdx.x, blockDim.x);
   __syncthreads();
   const int nwarps = gridDim.x * (kSlabThreads / 32);
-  for (int r = blockIdx.x * (kSlabThreads / 32) + (threadIdx.x >> 5); r < sp.ne; r += nwarps)
+  for (int w = blockIdx.x * (kSlabThreads / 32) + (threadIdx.x >> 5); w < sp.ne; w += nwarps) {
+    const int r = sp.order ? sp.order[sp.ne - 1 - w] : w;
     slab_matrix_row<T>(sp, sD, dec, B, M, vals, r, threadIdx.x & 31, 32);
+  }
 }
 
 template <typename T>

@@ -117,6 +117,10 @@ struct SlabPattern {
   const int64_t* dof_off;   // [ne+1] spatial dofs
   const int64_t* sblk_off;  // [nnzb+1] slab blocks
   const int64_t* sdof_off;  // [ne+1] slab dofs
+  // [ne] rows by degree, ascending (the mesh's work list); the expansion's
+  // warps take them from the end, the largest rows first, so that the rows
+  // of many sizes share out evenly over the grid-strided warps
+  const int* order;
 };
 
 // The work of one element row r, shared out over `lanes` threads of which
