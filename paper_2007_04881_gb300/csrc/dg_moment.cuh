@@ -79,11 +79,38 @@ struct MomCfg {
   // then in 2D the stage-one sums T and U, in 3D Yb and Zs
   static constexpr int PER_ELEM = 2 * NM + 3 * NPAIR * (Q + 1);
   static constexpr int NMAXC = nbasis(D, D == 2 ? kPMax2 : kPMax3);
-  // linearisation tables, rule, basis scales, then the exponents of the
-  // degree's basis functions (int, [N][3])
-  static constexpr size_t head_elems = NLIN + QT * (D + 1) + NMAXC + (3 * N * sizeof(int) + sizeof(T) - 1) / sizeof(T);
+  // the (P + 1)^3 entries of each [NPAIR][Q+1] coefficient table and of the
+  // 2D stage-one sums that the block reads (MomLists)
+  static constexpr int NX = (P + 1) * (P + 1) * (P + 1);
+  // linearisation tables, rule, basis scales, the exponents of the degree's
+  // basis functions (int, [N][3]), then the two entry lists (unsigned short)
+  static constexpr size_t head_elems = NLIN + QT * (D + 1) + NMAXC + (3 * N * sizeof(int) + sizeof(T) - 1) / sizeof(T) +
+                                       (2 * NX * sizeof(unsigned short) + sizeof(T) - 1) / sizeof(T);
   static constexpr size_t total = align_up(sizeof(T) * (head_elems + (size_t)kWarps * G * PER_ELEM), 16);
 };
+
+// The entries of the per-element tables that the block's entries read.  A
+// coefficient table [pair (a, a')][c] (Xa; in 3D also Yb, Zs) is read at
+// c <= a + a' only (c <= ai + aj): xl lists those (P + 1)^3 indices.  The 2D
+// stage-one sums [c][pair (b, b')] are read at c <= ai + aj <= 2p - b - b'
+// only: sl lists those (P + 1)^3 indices.  The lanes of an element take the
+// lists instead of the whole tables (225 entries each at 2D p = 4, 125 of
+// them read); the entries computed are the same, so are the blocks.
+template <int D, int P>
+__device__ inline void mom_lists(unsigned short* xl, unsigned short* sl, int tid, int nthreads) {
+  constexpr int NP = (P + 1) * (P + 1), Q = 2 * P;
+  for (int pr = tid; pr < NP; pr += nthreads) {
+    const int a = pr / (P + 1), ap = pr - a * (P + 1);
+    int bx = 0, bs = 0;  // entries of the pairs before pr in each list
+    for (int q = 0; q < pr; ++q) {
+      const int qa = q / (P + 1), qb = q - qa * (P + 1);
+      bx += qa + qb + 1;
+      bs += Q - qa - qb + 1;
+    }
+    for (int c = 0; c <= a + ap; ++c) xl[bx + c] = (unsigned short)(pr * (Q + 1) + c);
+    for (int c = 0; c <= Q - a - ap; ++c) sl[bs + c] = (unsigned short)(c * NP + pr);
+  }
+}
 
 // whether the moment path serves (D, P, T): moments held in registers
 template <int D, int P, typename T>
@@ -101,7 +128,8 @@ template <int D, int P, typename T>
 __device__ __forceinline__ void mom_tile(const DevMesh& m, int mode, T* __restrict__ vals, T* __restrict__ rhs,
                                          int tile, const T* __restrict__ lin, const T* __restrict__ rule,
                                          const T* __restrict__ ctab, const int* __restrict__ alf, T* pw,
-                                         const WaitCtl* wc) {
+                                         const WaitCtl* wc, const unsigned short* xl = nullptr,
+                                         const unsigned short* sl = nullptr) {
   using Cfg = MomCfg<D, P, T>;
   constexpr int N = Cfg::N, Q = Cfg::Q, NM = Cfg::NM, LPE = Cfg::LPE, G = Cfg::G, QT = Cfg::QT;
   constexpr int PL = Cfg::PL, CL = Cfg::CL, NPAIR = Cfg::NPAIR;
@@ -521,7 +549,7 @@ __device__ __forceinline__ void mom_tile(const DevMesh& m, int mode, T* __restri
       __syncwarp();
       if (active) {
         // per exponent pair (a, a'): the element's coefficient combinations
-        for (int k = lig; k < NPAIR * (Q + 1); k += LPE) {
+        auto xa_entry = [&](int k) {
           const int pr = k / (Q + 1), c = k - pr * (Q + 1);
           const int a = pr / (P + 1), ap = pr - a * (P + 1);
           sXa[k] = q.c * L0(a, ap, c) + q.bp[0] * L1(ap, a, c) + q.ap[0] * L2(a, ap, c);
@@ -529,13 +557,20 @@ __device__ __forceinline__ void mom_tile(const DevMesh& m, int mode, T* __restri
             sYb[k] = q.bp[1 % D] * L1(ap, a, c) + q.ap[1 % D] * L2(a, ap, c);
             sZs[k] = q.bp[2 % D] * L1(ap, a, c) + q.ap[2 % D] * L2(a, ap, c);
           }
+        };
+        if (xl) {
+          for (int t = lig; t < Cfg::NX; t += LPE) xa_entry(xl[t]);
+        } else {
+          for (int k = lig; k < NPAIR * (Q + 1); k += LPE) xa_entry(k);
         }
       }
       if constexpr (D == 2) {
         __syncwarp();
         // stage one: T(c, pair) and U(c, pair) over d <= b + b', c + d <= 2p
         if (active) {
-          for (int k = lig; k < NPAIR * (Q + 1); k += LPE) {
+          const int nst = sl ? Cfg::NX : NPAIR * (Q + 1);
+          for (int t = lig; t < nst; t += LPE) {
+            const int k = sl ? sl[t] : t;
             const int c = k / NPAIR, pr = k - c * NPAIR;
             const int b = pr / (P + 1), bp = pr - b * (P + 1);
             const int dm = min(b + bp, Q - c);
@@ -630,6 +665,8 @@ __global__ void __launch_bounds__(kWarps * 32)
   T* rule = lin + NLIN;
   T* ctab = rule + QT * (D + 1);
   int* alf = reinterpret_cast<int*>(ctab + Cfg::NMAXC);       // exponents [N][3]
+  unsigned short* xl = reinterpret_cast<unsigned short*>(alf + 3 * N);  // entry lists [NX], [NX]
+  unsigned short* sl = xl + Cfg::NX;
   T* pe = reinterpret_cast<T*>(smem_raw) + Cfg::head_elems;  // per element scratch
   const T* glin = pick<T>(m.rt.lin64, m.rt.lin32);
   for (int i = threadIdx.x; i < NLIN; i += blockDim.x) lin[i] = glin[i];
@@ -643,13 +680,14 @@ __global__ void __launch_bounds__(kWarps * 32)
     alf[3 * i + 1] = al[1];
     alf[3 * i + 2] = al[2];
   }
+  mom_lists<D, P>(xl, sl, threadIdx.x, blockDim.x);
   __syncthreads();
   const int warp = threadIdx.x >> 5;
   T* pw = pe + (size_t)warp * G * Cfg::PER_ELEM;
   const int count = m.elem_pstart[P + 1] - m.elem_pstart[P];
   const int ngroups = (count + G - 1) / G;
   for (int tile = blockIdx.x * kWarps + warp; tile < ngroups; tile += gridDim.x * kWarps)
-    mom_tile<D, P, T>(m, mode, vals, rhs, tile, lin, rule, ctab, alf, pw, nullptr);
+    mom_tile<D, P, T>(m, mode, vals, rhs, tile, lin, rule, ctab, alf, pw, nullptr, xl, D == 2 ? sl : nullptr);
 }
 
 }  // namespace dg
