@@ -626,6 +626,9 @@ __global__ void __launch_bounds__(kWarps * 32)
       }
       continue;
     }
+    // the off-diagonal launch next to the moment launch: the diagonal block
+    // and the load vector are the moment launch's (warp-uniform)
+    if (mode & kModeOffDiag) continue;
     T acc[N][N], racc[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) {

@@ -129,7 +129,9 @@ inline int launch_row_range(const DevMesh& m, int mode, T* vals, T* rhs, int sm_
   cudaStream_t st = lo.pst[P];
   const char* tn = sizeof(T) == 8 ? "f64" : "f32";
   int n = 0, kind = 0;
-  if constexpr (TileCfg<D, P, T>::TPE != 1 && moment_volume_ok<D, P, T>()) {
+  // every degree the moment path serves takes it, the lane kernel's degree 2
+  // (2D FP32) included: its off-diagonal blocks come from the interface launch
+  if constexpr (moment_volume_ok<D, P, T>()) {
     // the moment path needs the linearisation tables of the rule set
     if (lo.vol_moments && m.rt.lin32 && m.rt.lin64 && (mode & (kModeVol | kModeFace | kModeRhs))) {
       // volume and own-face terms through the moments (the diagonal block and
