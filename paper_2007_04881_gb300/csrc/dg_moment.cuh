@@ -115,7 +115,7 @@ __device__ inline void mom_lists(unsigned short* xl, unsigned short* sl, int tid
 // whether the moment path serves (D, P, T): moments held in registers
 template <int D, int P, typename T>
 __host__ __device__ constexpr bool moment_volume_ok() {
-  return P >= 2 && P <= kPMaxLin && nmom<D>(2 * P) <= (sizeof(T) == 4 ? 96 : 56);
+  return P >= 1 && P <= kPMaxLin && nmom<D>(2 * P) <= (sizeof(T) == 4 ? 96 : 56);
 }
 
 // One tile of the moment kernel: G elements of degree P on this warp, LPE
