@@ -33,7 +33,10 @@ int launch_row_tile(const DevMesh& m, int mode, T* vals, T* rhs, int sm_count, c
   if (tr && tr->on) {
     char name[48];
     snprintf(name, sizeof name, "row%dd_p%d_%s", D, P, sizeof(T) == 8 ? "f64" : "f32");
-    const bool lane_if = TileCfg<D, P, T, V>::TPE == 1 && ((lo.imask >> P) & 1);
+    // the lane kernel's own launch with the interface kernel on: its rows
+    // less the interface launch's blocks (kind 6); next to a moment launch it
+    // is the off-diagonal launch (kind 4)
+    const bool lane_if = TileCfg<D, P, T, V>::TPE == 1 && ((lo.imask >> P) & 1) && kind == 0;
     tr->begin(name, lane_if ? 6 : kind, P, sizeof(T), st);
   }
   if constexpr (TileCfg<D, P, T, V>::TPE == 1) {
@@ -164,17 +167,12 @@ inline int launch_row_range(const DevMesh& m, int mode, T* vals, T* rhs, int sm_
   return n + launch_row_variant<D, P, T>(m, mode, vals, rhs, sm_count, lo, tr, kind);
 }
 
-// whether the block rows of degree P take the off-diagonal launch when the
-// moment path is on (the moment launch completing their diagonal blocks)
-template <int D, int P, typename T>
-__host__ __device__ constexpr bool offdiag_rows() {
-  return TileCfg<D, P, T>::TPE != 1 && moment_volume_ok<D, P, T>();
-}
-// whether the interface kernel serves degree P (FP32): the rows above, and
-// the lane kernel's degrees, whose diagonal part stays in the lane kernel
+// whether the interface kernel serves degree P: the FP32 degrees of the
+// moment path, whose moment launch completes the diagonal blocks (a pass off
+// the moment path leaves every block to the row and lane kernels)
 template <int D, int P, typename T>
 __host__ __device__ constexpr bool iface_rows() {
-  return sizeof(T) == 4 && (offdiag_rows<D, P, T>() || TileCfg<D, P, T>::TPE == 1);
+  return sizeof(T) == 4 && moment_volume_ok<D, P, T>();
 }
 
 // lo.present and lo.imask of one pass (interfaces by the interface kernel:
