@@ -40,6 +40,23 @@ def test_create_fails_loudly_without_gpu(lib):
     assert ei.value.code in (-1, -3)
 
 
+def test_pipelined_host_calls_reject_null_arguments(lib):
+    """dg_assemble_host_submit / _wait check their arguments before any CUDA
+    call: a null context, mesh, output or ticket pointer is DG_ERR_ARG, with
+    the message naming the call."""
+    import ctypes as C
+
+    t = C.c_longlong(-7)
+    assert lib.dg_assemble_host_submit(None, None, dg.DG_PREC_FP32, None, None, None, None, None, None,
+                                       C.byref(t)) == dg.DG_ERR_ARG
+    assert "dg_assemble_host_submit" in lib.dg_last_error().decode()
+    assert t.value == -7  # no ticket issued
+    assert lib.dg_assemble_host_submit(None, None, dg.DG_PREC_FP32, None, None, None, None, None, None,
+                                       None) == dg.DG_ERR_ARG
+    assert lib.dg_assemble_host_wait(None, None, C.c_longlong(0)) == dg.DG_ERR_ARG
+    assert "dg_assemble_host_wait" in lib.dg_last_error().decode()
+
+
 def _check(wl):
     return dg.dg_mesh_check(wl.mesh, wl.p, wl.a, dg.Problem(**wl.problem), pattern=True)
 
